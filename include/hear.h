@@ -1,0 +1,200 @@
+/*
+ * hear.h -- C ABI of the GB300 (sm_103a) RNS-CKKS library for encrypted inference in the
+ * style of HEAR / Fast-HEAR ("Secure Human Action Recognition by Encrypted Neural
+ * Network Inference", arXiv 2104.09164).
+ *
+ * The calls follow the paper's statement of the problem (Results, "Overview of HEAR",
+ * and the Fig. 1 caption): the monitoring provider generates the keys (secret key,
+ * public key, evaluation keys for ciphertext products and rotations) and decrypts
+ * results; the end-user encrypts with the public key; the cloud evaluates the network on
+ * ciphertexts with the evaluation keys only.  The scheme is the RNS variant of CKKS
+ * (Methods, "Algorithmic and cryptographic optimizations").
+ *
+ * Conventions
+ *   - Every call returns hear_status: HEAR_OK (0) or a negative error code; the
+ *     thread-local message of the last error is available from hear_last_error().
+ *   - Handles are created by the library and released by the caller with the matching
+ *     *_destroy call (NULL is accepted and ignored).
+ *   - Host arrays passed in are borrowed for the duration of the call only.  Output arrays
+ *     are caller-allocated with a capacity `cap` (in elements) and the count written to
+ *     *n; a short capacity returns HEAR_E_INVAL with the required count in *n.
+ *   - `stream` is a cudaStream_t (NULL = the context's own stream).  Calls that return
+ *     device-resident handles enqueue their work on that stream; calls that fill host
+ *     arrays synchronise it before returning.
+ *   - Ciphertexts live in device memory (HBM) in the library's NTT domain, laid out as
+ *     uint64_t[n_poly][level+1][N], one word per residue.  Exported/imported ciphertexts
+ *     use the coefficient domain with the same layout.
+ *   - Keys and models are immutable after creation and may be shared by concurrent
+ *     evaluations on different streams.  After a CUDA error the context is poisoned:
+ *     every later call on it returns HEAR_E_CUDA.
+ *   - No C++ exception crosses this interface and nothing aborts the process.
+ *   - There is no CPU fallback: all ring arithmetic runs in the library's CUDA kernels.
+ */
+#ifndef HEAR_H
+#define HEAR_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int hear_status;
+#define HEAR_OK 0
+#define HEAR_E_INVAL (-1)       /* bad argument (pointer, size, capacity)            */
+#define HEAR_E_NOMEM (-2)       /* host or device allocation failed                   */
+#define HEAR_E_CUDA (-3)        /* CUDA error; the context is poisoned                */
+#define HEAR_E_LEVEL (-4)       /* ciphertext has no level left for the operation     */
+#define HEAR_E_SCALE (-5)       /* operands at different scales or levels             */
+#define HEAR_E_NOKEY (-6)       /* missing rotation or relinearisation key            */
+#define HEAR_E_STATE (-7)       /* handle from another context / wrong kind           */
+#define HEAR_E_FORMAT (-8)      /* malformed import buffer                            */
+#define HEAR_E_UNSUPPORTED (-9) /* parameter outside the supported range              */
+
+typedef struct hear_context hear_context;
+typedef struct hear_secret_key hear_secret_key;
+typedef struct hear_public_key hear_public_key;
+typedef struct hear_eval_keys hear_eval_keys;
+typedef struct hear_ciphertext hear_ciphertext;
+typedef struct hear_model hear_model;
+
+/* Encryption parameters.  The ciphertext modulus is Q = q_0 * ... * q_{n_q-1} (top level
+ * L = n_q - 1); the n_p special primes p_0..p_{K-1} are used by key switching only.
+ * Prime rule: for each bit size in the order q_0, q_1.., p_0.. take the largest prime
+ * below 2^bits that is 1 mod 2N and not yet taken.  Hybrid key switching uses digits of
+ * alpha = n_p consecutive limbs.  Supported: log_n in [10, 16], bit sizes in
+ * [log_n + 2, 60], n_q + n_p <= 48.  sigma: standard deviation of the discrete Gaussian
+ * errors (tail cut at floor(6 sigma)). */
+typedef struct hear_params_desc {
+    uint32_t log_n;
+    uint32_t n_q;
+    const uint32_t *q_bits;
+    uint32_t n_p;
+    const uint32_t *p_bits;
+    double log2_scale;  /* encoding scale of fresh inputs, e.g. 40 */
+    double sigma;       /* e.g. 3.2 */
+} hear_params_desc;
+
+const char *hear_last_error(void);
+
+/* ---- context: primes, NTT tables and basis-conversion constants on `device` ---- */
+hear_status hear_context_create(const hear_params_desc *params, int cuda_device, hear_context **out);
+void hear_context_destroy(hear_context *ctx);
+/* primes in chain order q_0..q_{n_q-1}, p_0..p_{K-1} */
+hear_status hear_context_primes(const hear_context *ctx, uint64_t *out, size_t cap, size_t *n);
+/* discrete-Gaussian CDT thresholds used by the samplers (for cross-checking) */
+hear_status hear_context_cdt(const hear_context *ctx, uint64_t *out, size_t cap, size_t *n);
+
+/* ---- key generation (monitoring provider).  All randomness is drawn from the
+ * counter-based ChaCha20 generator (RFC 8439) keyed by `seed`.  One rotation key is
+ * generated per entry of rot_steps (left rotation by that many slots); duplicates are
+ * ignored.  The keys stay resident in device memory. ---- */
+hear_status hear_keygen(hear_context *ctx, uint64_t seed, const int32_t *rot_steps, size_t n_steps,
+                        hear_secret_key **sk, hear_public_key **pk, hear_eval_keys **evk);
+void hear_secret_key_destroy(hear_secret_key *);
+void hear_public_key_destroy(hear_public_key *);
+void hear_eval_keys_destroy(hear_eval_keys *);
+/* the ternary secret s (N coefficients in {-1,0,1}) -- test and audit use only */
+hear_status hear_secret_key_export(const hear_secret_key *sk, int8_t *out, size_t cap, size_t *n);
+/* public key (b, a) over Q_L, coefficient domain uint64[2][n_q][N] */
+hear_status hear_public_key_export(const hear_public_key *pk, uint64_t *out, size_t cap, size_t *n);
+/* switching key for `galois` (1 = relinearisation key, else the key of X -> X^galois),
+ * coefficient domain uint64[dnum][2][n_q+n_p][N] */
+hear_status hear_eval_key_export(const hear_eval_keys *evk, uint32_t galois, uint64_t *out, size_t cap,
+                                 size_t *n);
+
+/* ---- encoding / encryption (end-user) ---- */
+/* round(scale * tau^-1(z)) for n_slots = N/2 real values (canonical embedding, slot j at
+ * the root exp(i*pi*5^j/N)), computed in double-double arithmetic, ties away from zero */
+hear_status hear_encode(const hear_context *ctx, const double *z, size_t n_slots, double scale,
+                        int64_t *m_out, size_t cap, size_t *n);
+/* encrypt N/2 slot values at `scale` (0 = the context's default scale) at the top level.
+ * The encryption randomness is stream `ct_id` of `seed`. */
+hear_status hear_encrypt(hear_context *ctx, const hear_public_key *pk, const double *z, size_t n_slots,
+                         double scale, uint64_t seed, uint64_t ct_id, hear_ciphertext **out, void *stream);
+/* Data encryption with interlaced copies (Methods, "Data encryption"): n_clips row-major
+ * clips of clip_dim values (clip_dim a power of two dividing N/2); with k = (N/2)/clip_dim
+ * lanes, slot p*k + c holds clip (c mod n_clips)[p]; requires 1 <= n_clips <= k. */
+hear_status hear_encrypt_clips(hear_context *ctx, const hear_public_key *pk, const double *clips,
+                               size_t n_clips, size_t clip_dim, uint64_t seed, uint64_t ct_id,
+                               hear_ciphertext **out, void *stream);
+/* decrypt + decode to N/2 real slot values */
+hear_status hear_decrypt(hear_context *ctx, const hear_secret_key *sk, const hear_ciphertext *ct,
+                         double *out, size_t cap, size_t *n);
+void hear_ciphertext_destroy(hear_ciphertext *);
+hear_status hear_ciphertext_info(const hear_ciphertext *ct, uint32_t *level, uint32_t *n_poly, double *scale);
+/* coefficient domain uint64[n_poly][level+1][N] */
+hear_status hear_ciphertext_export(const hear_ciphertext *ct, uint64_t *out, size_t cap, size_t *n);
+hear_status hear_ciphertext_import(hear_context *ctx, const uint64_t *words, size_t n_words, uint32_t level,
+                                   uint32_t n_poly, double scale, hear_ciphertext **out, void *stream);
+
+/* ---- primitive homomorphic operations (cloud) ---- */
+/* rho^step: left rotation of the slots by `step` (negative = right), via X -> X^(5^step) */
+hear_status hear_rotate(const hear_eval_keys *evk, const hear_ciphertext *ct, int32_t step,
+                        hear_ciphertext **out, void *stream);
+/* several rotations of one ciphertext sharing a single ModUp (hoisting, Methods,
+ * "Algorithmic and cryptographic optimizations" item (i)); out[i] = rho^steps[i](ct) */
+hear_status hear_rotate_hoisted(const hear_eval_keys *evk, const hear_ciphertext *ct, const int32_t *steps,
+                                size_t n_steps, hear_ciphertext **out, void *stream);
+/* divide by the last prime and drop it (lazy rescaling uses it once per sum) */
+hear_status hear_rescale(const hear_ciphertext *ct, hear_ciphertext **out, void *stream);
+hear_status hear_add(const hear_ciphertext *a, const hear_ciphertext *b, hear_ciphertext **out, void *stream);
+/* MultPlain(ct, pt): multiply by the plaintext encoding of N/2 slot values at pt_scale
+ * (level-aware: the plaintext carries only the limbs of ct's level) -- no rescale */
+hear_status hear_mulplain(const hear_ciphertext *ct, const double *z, size_t n_slots, double pt_scale,
+                          hear_ciphertext **out, void *stream);
+/* ciphertext product: tensor, then relinearisation with the s^2 key -- no rescale */
+hear_status hear_multiply_relin(const hear_eval_keys *evk, const hear_ciphertext *a, const hear_ciphertext *b,
+                                hear_ciphertext **out, void *stream);
+
+/* ---- network (cloud) ---- */
+#define HEAR_LAYER_FC 1          /* y = W x (d_out x d_in, row-major), optional bias       */
+#define HEAR_LAYER_SQUARE 2      /* y = x^2 (polynomial activation)                       */
+#define HEAR_LAYER_FC_SQ_FC 3    /* y = W2 (W1 x)^2 evaluated as one collapsed quadratic    */
+typedef struct hear_layer_desc {
+    uint32_t kind;
+    uint32_t d_out, d_in;   /* W: d_out x d_in; powers of two with d_out | d_in            */
+    const double *w;        /* row-major                                                   */
+    const double *bias;     /* d_out values or NULL (FC only)                              */
+    uint32_t d_out2;        /* FC_SQ_FC: W2 is d_out2 x d_out                               */
+    const double *w2;
+} hear_layer_desc;
+
+/* Encode the network for ciphertexts packed by hear_encrypt_clips with clip_dim inputs.
+ * FC layers are evaluated as baby-step/giant-step diagonal products: D = d_out extended
+ * diagonals diag_i[p] = W[p mod d_out][(p+i) mod d_in], n1 = smallest power of two with
+ * n1^2 >= D, n2 = ceil(D/n1); hoisted baby rotations rho^(i k), plaintexts pre-rotated by
+ * rho^(-j n1 k) and encoded at the level of use with scale q_level, non-hoisted giant
+ * rotations rho^(j n1 k), one rescale, then rotate-and-sum by d_out 2^t k
+ * (Methods, "Algorithmic and cryptographic optimizations"; "Non-convolutional layers"). */
+hear_status hear_model_create(hear_context *ctx, const hear_layer_desc *layers, size_t n_layers,
+                              uint32_t clip_dim, hear_model **out);
+void hear_model_destroy(hear_model *);
+/* rotation steps (slots) the model needs keys for */
+hear_status hear_model_rotations(const hear_model *m, int32_t *steps, size_t cap, size_t *n);
+/* pos of logit c in the pos space (slot = pos * k + clip) */
+hear_status hear_model_output_positions(const hear_model *m, uint32_t *pos, size_t cap, size_t *n);
+/* evaluate the whole network on n_ct ciphertexts (one batch; all at the top level) */
+hear_status hear_evaluate(const hear_model *m, const hear_eval_keys *evk, hear_ciphertext *const *in, size_t n_ct,
+                          hear_ciphertext **out, void *stream);
+/* evaluate layer `layer` only (input at that layer's level) */
+hear_status hear_evaluate_layer(const hear_model *m, size_t layer, const hear_eval_keys *evk,
+                                hear_ciphertext *const *in, size_t n_ct, hear_ciphertext **out, void *stream);
+/* end-to-end from host buffers: n_ct input ciphertexts in the coefficient domain
+ * (uint64[n_ct][2][n_q][N], top level, `scale`) -> the result ciphertexts in the
+ * coefficient domain (uint64[n_ct][2][level_out+1][N]); copies both ways are included */
+hear_status hear_evaluate_host(const hear_model *m, const hear_eval_keys *evk, const uint64_t *in_words,
+                               size_t n_ct, double scale, uint64_t *out_words, size_t cap, size_t *n,
+                               uint32_t *level_out, double *scale_out, void *stream);
+
+/* ---- debug: ring products through the NTT kernels (tests only) ---- */
+/* out = a * b in Z_q[X]/(X^N+1) for limb prime index `prime` (0..n_q+n_p-1), coefficient domain */
+hear_status hear_dbg_poly_mul(hear_context *ctx, uint32_t prime, const uint64_t *a, const uint64_t *b,
+                              uint64_t *out);
+/* forward+inverse NTT round trip of n_limb limbs (prime i % (n_q+n_p)) in place */
+hear_status hear_dbg_ntt_roundtrip(hear_context *ctx, uint64_t *limbs, size_t n_limb);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

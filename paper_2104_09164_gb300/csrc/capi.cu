@@ -1,0 +1,492 @@
+// capi.cu -- the extern "C" boundary (include/hear.h): argument checks, error capture,
+// handle management.  No C++ exception crosses it.
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include "ckks.h"
+
+using namespace hear;
+
+namespace {
+thread_local std::string g_last_error;
+
+hear_status fail(hear_status code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+template <class F>
+hear_status guard(hear_context *ctx, F &&f) {
+    if (ctx && ctx->poisoned) return fail(HEAR_E_CUDA, "context is poisoned by an earlier CUDA error");
+    try {
+        if (ctx) HEAR_CHECK_CUDA(cudaSetDevice(ctx->device));
+        f();
+        return HEAR_OK;
+    } catch (const Error &e) {
+        if (e.code == HEAR_E_CUDA && ctx) ctx->poisoned = true;
+        return fail(e.code, e.what());
+    } catch (const std::bad_alloc &) {
+        return fail(HEAR_E_NOMEM, "host allocation failed");
+    } catch (const std::exception &e) {
+        return fail(HEAR_E_INVAL, e.what());
+    } catch (...) {
+        return fail(HEAR_E_INVAL, "unknown error");
+    }
+}
+
+cudaStream_t stream_of(hear_context *c, void *s) { return s ? static_cast<cudaStream_t>(s) : c->stream; }
+
+template <class T>
+hear_status copy_out(const std::vector<T> &v, T *out, size_t cap, size_t *n) {
+    if (n) *n = v.size();
+    if (!out || cap < v.size()) return fail(HEAR_E_INVAL, "output capacity too small");
+    std::copy(v.begin(), v.end(), out);
+    return HEAR_OK;
+}
+
+hear_ciphertext *new_ct(hear_context *c, uint32_t level, uint32_t n_poly, double scale) {
+    auto ct = new hear_ciphertext();
+    ct->ctx = c;
+    ct->level = level;
+    ct->n_poly = n_poly;
+    ct->scale = scale;
+    try {
+        ct->d = DevBuf((size_t)n_poly * (level + 1) * c->n * 8, nullptr);
+    } catch (...) {
+        delete ct;
+        throw;
+    }
+    return ct;
+}
+
+// coefficient-domain host words -> NTT-domain device batch (n_polys polynomials at level)
+void to_device_ntt(hear_context *c, const uint64_t *words, uint32_t level, uint32_t n_polys, uint64_t *d,
+                   cudaStream_t st) {
+    const size_t words_n = (size_t)n_polys * (level + 1) * c->n;
+    HEAR_CHECK_CUDA(cudaMemcpyAsync(d, words, words_n * 8, cudaMemcpyHostToDevice, st));
+    ntt_forward(c, d, n_polys * (level + 1), map_q(level, c->n_q), st);
+}
+}  // namespace
+
+extern "C" {
+
+const char *hear_last_error(void) { return g_last_error.c_str(); }
+
+hear_status hear_context_create(const hear_params_desc *params, int cuda_device, hear_context **out) {
+    if (!out || !params) return fail(HEAR_E_INVAL, "null argument");
+    auto c = new hear_context();
+    hear_status s = guard(nullptr, [&] { build_context(c, params, cuda_device); });
+    if (s != HEAR_OK) {
+        delete c;
+        return s;
+    }
+    *out = c;
+    return HEAR_OK;
+}
+
+void hear_context_destroy(hear_context *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    forget_encoder(ctx);
+    ctx->levels.clear();
+    ctx->d_primes.reset();
+    ctx->d_tw.reset();
+    ctx->d_cdt.reset();
+    if (ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+hear_status hear_context_primes(const hear_context *ctx, uint64_t *out, size_t cap, size_t *n) {
+    if (!ctx) return fail(HEAR_E_INVAL, "null context");
+    return copy_out(ctx->primes, out, cap, n);
+}
+
+hear_status hear_context_cdt(const hear_context *ctx, uint64_t *out, size_t cap, size_t *n) {
+    if (!ctx) return fail(HEAR_E_INVAL, "null context");
+    return copy_out(ctx->cdt, out, cap, n);
+}
+
+hear_status hear_keygen(hear_context *ctx, uint64_t seed, const int32_t *rot_steps, size_t n_steps,
+                        hear_secret_key **sk, hear_public_key **pk, hear_eval_keys **evk) {
+    if (!ctx || !sk || !pk || !evk || (n_steps && !rot_steps)) return fail(HEAR_E_INVAL, "null argument");
+    return guard(ctx, [&] { keygen(ctx, seed, rot_steps, n_steps, sk, pk, evk); });
+}
+
+void hear_secret_key_destroy(hear_secret_key *k) {
+    if (k) cudaSetDevice(k->ctx->device);
+    delete k;
+}
+void hear_public_key_destroy(hear_public_key *k) {
+    if (k) cudaSetDevice(k->ctx->device);
+    delete k;
+}
+void hear_eval_keys_destroy(hear_eval_keys *k) {
+    if (k) cudaSetDevice(k->ctx->device);
+    delete k;
+}
+
+hear_status hear_secret_key_export(const hear_secret_key *sk, int8_t *out, size_t cap, size_t *n) {
+    if (!sk) return fail(HEAR_E_INVAL, "null key");
+    return copy_out(sk->s, out, cap, n);
+}
+
+hear_status hear_public_key_export(const hear_public_key *pk, uint64_t *out, size_t cap, size_t *n) {
+    if (!pk) return fail(HEAR_E_INVAL, "null key");
+    hear_context *c = pk->ctx;
+    const size_t words = 2ull * c->n_q * c->n;
+    if (n) *n = words;
+    if (!out || cap < words) return fail(HEAR_E_INVAL, "output capacity too small");
+    return guard(c, [&] {
+        cudaStream_t st = c->stream;
+        DevBuf t(words * 8, st);
+        HEAR_CHECK_CUDA(cudaMemcpyAsync(t.p, pk->pk_mont.p, words * 8, cudaMemcpyDeviceToDevice, st));
+        LimbMap m = map_q(c->L, c->n_q);
+        from_mont(c, t.u64(), 2 * c->n_q, m, st);
+        ntt_inverse(c, t.u64(), 2 * c->n_q, m, st);
+        HEAR_CHECK_CUDA(cudaMemcpyAsync(out, t.p, words * 8, cudaMemcpyDeviceToHost, st));
+        HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+hear_status hear_eval_key_export(const hear_eval_keys *evk, uint32_t galois, uint64_t *out, size_t cap, size_t *n) {
+    if (!evk) return fail(HEAR_E_INVAL, "null key");
+    hear_context *c = evk->ctx;
+    const uint64_t *k = evk->key(galois);
+    if (!k) return fail(HEAR_E_NOKEY, "no key for this galois element");
+    const size_t words = (size_t)c->dnum_max() * 2 * c->nqp() * c->n;
+    if (n) *n = words;
+    if (!out || cap < words) return fail(HEAR_E_INVAL, "output capacity too small");
+    return guard(c, [&] {
+        cudaStream_t st = c->stream;
+        DevBuf t(words * 8, st);
+        HEAR_CHECK_CUDA(cudaMemcpyAsync(t.p, k, words * 8, cudaMemcpyDeviceToDevice, st));
+        LimbMap m;
+        m.per_group = c->nqp();
+        m.q_count = c->n_q;
+        m.n_q = c->n_q;
+        const uint32_t limbs = c->dnum_max() * 2 * c->nqp();
+        from_mont(c, t.u64(), limbs, m, st);
+        ntt_inverse(c, t.u64(), limbs, m, st);
+        HEAR_CHECK_CUDA(cudaMemcpyAsync(out, t.p, words * 8, cudaMemcpyDeviceToHost, st));
+        HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+hear_status hear_encode(const hear_context *ctx, const double *z, size_t n_slots, double scale, int64_t *m_out,
+                        size_t cap, size_t *n) {
+    if (!ctx || !z || !m_out) return fail(HEAR_E_INVAL, "null argument");
+    if (n) *n = ctx->n;
+    if (n_slots != ctx->n / 2) return fail(HEAR_E_INVAL, "n_slots must be N/2");
+    if (cap < ctx->n) return fail(HEAR_E_INVAL, "output capacity too small");
+    hear_context *c = const_cast<hear_context *>(ctx);
+    return guard(c, [&] { encode_dd(*encoder(c), z, scale, m_out); });
+}
+
+hear_status hear_encrypt(hear_context *ctx, const hear_public_key *pk, const double *z, size_t n_slots, double scale,
+                         uint64_t seed, uint64_t ct_id, hear_ciphertext **out, void *stream) {
+    if (!ctx || !pk || !z || !out) return fail(HEAR_E_INVAL, "null argument");
+    if (pk->ctx != ctx) return fail(HEAR_E_STATE, "key from another context");
+    if (n_slots != ctx->n / 2) return fail(HEAR_E_INVAL, "n_slots must be N/2");
+    return guard(ctx, [&] {
+        double sc = scale > 0 ? scale : ctx->default_scale;
+        *out = encrypt_slots(ctx, pk, z, sc, seed, ct_id, stream_of(ctx, stream));
+    });
+}
+
+hear_status hear_encrypt_clips(hear_context *ctx, const hear_public_key *pk, const double *clips, size_t n_clips,
+                               size_t clip_dim, uint64_t seed, uint64_t ct_id, hear_ciphertext **out, void *stream) {
+    if (!ctx || !pk || !clips || !out) return fail(HEAR_E_INVAL, "null argument");
+    const size_t slots = ctx->n / 2;
+    if (!clip_dim || (clip_dim & (clip_dim - 1)) || clip_dim > slots)
+        return fail(HEAR_E_INVAL, "clip_dim must be a power of two <= N/2");
+    const size_t k = slots / clip_dim;
+    if (n_clips < 1 || n_clips > k) return fail(HEAR_E_INVAL, "n_clips must be in [1, N/2 / clip_dim]");
+    std::vector<double> z(slots);
+    for (size_t c = 0; c < k; c++)
+        for (size_t p = 0; p < clip_dim; p++) z[p * k + c] = clips[(c % n_clips) * clip_dim + p];
+    return hear_encrypt(ctx, pk, z.data(), slots, 0.0, seed, ct_id, out, stream);
+}
+
+hear_status hear_decrypt(hear_context *ctx, const hear_secret_key *sk, const hear_ciphertext *ct, double *out,
+                         size_t cap, size_t *n) {
+    if (!ctx || !sk || !ct) return fail(HEAR_E_INVAL, "null argument");
+    if (n) *n = ctx->n / 2;
+    if (!out || cap < ctx->n / 2) return fail(HEAR_E_INVAL, "output capacity too small");
+    if (ct->n_poly != 2) return fail(HEAR_E_STATE, "decrypt needs a 2-polynomial ciphertext");
+    return guard(ctx, [&] { decrypt_slots(ctx, sk, ct, out); });
+}
+
+void hear_ciphertext_destroy(hear_ciphertext *ct) {
+    if (ct) cudaSetDevice(ct->ctx->device);
+    delete ct;
+}
+
+hear_status hear_ciphertext_info(const hear_ciphertext *ct, uint32_t *level, uint32_t *n_poly, double *scale) {
+    if (!ct) return fail(HEAR_E_INVAL, "null ciphertext");
+    if (level) *level = ct->level;
+    if (n_poly) *n_poly = ct->n_poly;
+    if (scale) *scale = ct->scale;
+    return HEAR_OK;
+}
+
+hear_status hear_ciphertext_export(const hear_ciphertext *ct, uint64_t *out, size_t cap, size_t *n) {
+    if (!ct) return fail(HEAR_E_INVAL, "null ciphertext");
+    hear_context *c = ct->ctx;
+    const size_t words = (size_t)ct->n_poly * (ct->level + 1) * c->n;
+    if (n) *n = words;
+    if (!out || cap < words) return fail(HEAR_E_INVAL, "output capacity too small");
+    return guard(c, [&] {
+        cudaStream_t st = c->stream;
+        DevBuf t(words * 8, st);
+        HEAR_CHECK_CUDA(cudaMemcpyAsync(t.p, ct->d.p, words * 8, cudaMemcpyDeviceToDevice, st));
+        ntt_inverse(c, t.u64(), ct->n_poly * (ct->level + 1), map_q(ct->level, c->n_q), st);
+        HEAR_CHECK_CUDA(cudaMemcpyAsync(out, t.p, words * 8, cudaMemcpyDeviceToHost, st));
+        HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+hear_status hear_ciphertext_import(hear_context *ctx, const uint64_t *words, size_t n_words, uint32_t level,
+                                   uint32_t n_poly, double scale, hear_ciphertext **out, void *stream) {
+    if (!ctx || !words || !out) return fail(HEAR_E_INVAL, "null argument");
+    if (level > ctx->L || n_poly < 2 || n_poly > 3) return fail(HEAR_E_FORMAT, "bad level or polynomial count");
+    if (n_words != (size_t)n_poly * (level + 1) * ctx->n) return fail(HEAR_E_FORMAT, "word count mismatch");
+    return guard(ctx, [&] {
+        for (size_t i = 0; i < (size_t)n_poly * (level + 1); i++) {
+            uint64_t q = ctx->primes[i % (level + 1)];
+            const uint64_t *w = words + i * ctx->n;
+            for (uint32_t k = 0; k < ctx->n; k++)
+                HEAR_REQUIRE(w[k] < q, HEAR_E_FORMAT, "residue not reduced");
+        }
+        hear_ciphertext *ct = new_ct(ctx, level, n_poly, scale);
+        try {
+            to_device_ntt(ctx, words, level, n_poly, ct->d.u64(), stream_of(ctx, stream));
+        } catch (...) {
+            delete ct;
+            throw;
+        }
+        *out = ct;
+    });
+}
+
+hear_status hear_rotate_hoisted(const hear_eval_keys *evk, const hear_ciphertext *ct, const int32_t *steps,
+                                size_t n_steps, hear_ciphertext **out, void *stream) {
+    if (!evk || !ct || !out || (n_steps && !steps)) return fail(HEAR_E_INVAL, "null argument");
+    hear_context *c = ct->ctx;
+    if (evk->ctx != c) return fail(HEAR_E_STATE, "key from another context");
+    if (ct->n_poly != 2) return fail(HEAR_E_STATE, "rotation needs a 2-polynomial ciphertext");
+    return guard(c, [&] {
+        cudaStream_t st = stream_of(c, stream);
+        std::vector<Rot> rots;
+        for (size_t i = 0; i < n_steps; i++) {
+            uint32_t g = galois_of(c, steps[i]);
+            const uint64_t *k = evk->key(g);
+            HEAR_REQUIRE(k, HEAR_E_NOKEY, "missing rotation key for step " + std::to_string(steps[i]));
+            rots.push_back(Rot{k, g});
+        }
+        std::vector<std::unique_ptr<hear_ciphertext>> res;
+        std::vector<uint64_t *> outs;
+        for (size_t i = 0; i < n_steps; i++) {
+            res.emplace_back(new_ct(c, ct->level, 2, ct->scale));
+            outs.push_back(res.back()->d.u64());
+        }
+        rotate_hoisted(c, ct->level, 1, ct->d.u64(), rots, outs, st);
+        for (size_t i = 0; i < n_steps; i++) out[i] = res[i].release();
+    });
+}
+
+hear_status hear_rotate(const hear_eval_keys *evk, const hear_ciphertext *ct, int32_t step, hear_ciphertext **out,
+                        void *stream) {
+    return hear_rotate_hoisted(evk, ct, &step, 1, out, stream);
+}
+
+hear_status hear_rescale(const hear_ciphertext *ct, hear_ciphertext **out, void *stream) {
+    if (!ct || !out) return fail(HEAR_E_INVAL, "null argument");
+    hear_context *c = ct->ctx;
+    if (ct->level == 0) return fail(HEAR_E_LEVEL, "ciphertext at level 0 cannot be rescaled");
+    return guard(c, [&] {
+        cudaStream_t st = stream_of(c, stream);
+        const size_t words = (size_t)ct->n_poly * (ct->level + 1) * c->n;
+        DevBuf in(words * 8, st), tmp((size_t)ct->n_poly * ct->level * c->n * 8, st);
+        HEAR_CHECK_CUDA(cudaMemcpyAsync(in.p, ct->d.p, words * 8, cudaMemcpyDeviceToDevice, st));
+        std::unique_ptr<hear_ciphertext> r(new_ct(c, ct->level - 1, ct->n_poly, ct->scale / (double)c->primes[ct->level]));
+        rescale(c, ct->level, ct->n_poly, in.u64(), r->d.u64(), tmp.u64(), st);
+        *out = r.release();
+    });
+}
+
+hear_status hear_add(const hear_ciphertext *a, const hear_ciphertext *b, hear_ciphertext **out, void *stream) {
+    if (!a || !b || !out) return fail(HEAR_E_INVAL, "null argument");
+    hear_context *c = a->ctx;
+    if (b->ctx != c) return fail(HEAR_E_STATE, "operands from different contexts");
+    if (a->level != b->level || a->n_poly != b->n_poly) return fail(HEAR_E_SCALE, "operands at different levels");
+    return guard(c, [&] {
+        std::unique_ptr<hear_ciphertext> r(new_ct(c, a->level, a->n_poly, a->scale));
+        add_ct(c, a->level, a->n_poly, a->d.u64(), b->d.u64(), r->d.u64(), stream_of(c, stream));
+        *out = r.release();
+    });
+}
+
+hear_status hear_mulplain(const hear_ciphertext *ct, const double *z, size_t n_slots, double pt_scale,
+                          hear_ciphertext **out, void *stream) {
+    if (!ct || !z || !out) return fail(HEAR_E_INVAL, "null argument");
+    hear_context *c = ct->ctx;
+    if (n_slots != c->n / 2) return fail(HEAR_E_INVAL, "n_slots must be N/2");
+    if (ct->n_poly != 2) return fail(HEAR_E_STATE, "MultPlain needs a 2-polynomial ciphertext");
+    return guard(c, [&] {
+        cudaStream_t st = stream_of(c, stream);
+        DevBuf pt = encode_plain(c, z, pt_scale, ct->level, st);
+        std::unique_ptr<hear_ciphertext> r(new_ct(c, ct->level, 2, ct->scale * pt_scale));
+        mulplain(c, ct->level, 1, ct->d.u64(), pt.u64(), r->d.u64(), st);
+        HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
+        *out = r.release();
+    });
+}
+
+hear_status hear_multiply_relin(const hear_eval_keys *evk, const hear_ciphertext *a, const hear_ciphertext *b,
+                                hear_ciphertext **out, void *stream) {
+    if (!evk || !a || !b || !out) return fail(HEAR_E_INVAL, "null argument");
+    hear_context *c = a->ctx;
+    if (b->ctx != c || evk->ctx != c) return fail(HEAR_E_STATE, "operands from different contexts");
+    if (a->level != b->level || a->n_poly != 2 || b->n_poly != 2) return fail(HEAR_E_SCALE, "operand mismatch");
+    const uint64_t *rk = evk->key(1);
+    if (!rk) return fail(HEAR_E_NOKEY, "missing relinearisation key");
+    return guard(c, [&] {
+        std::unique_ptr<hear_ciphertext> r(new_ct(c, a->level, 2, a->scale * b->scale));
+        mul_relin(c, a->level, 1, a->d.u64(), b->d.u64(), rk, r->d.u64(), stream_of(c, stream));
+        *out = r.release();
+    });
+}
+
+hear_status hear_model_create(hear_context *ctx, const hear_layer_desc *layers, size_t n_layers, uint32_t clip_dim,
+                              hear_model **out) {
+    if (!ctx || !layers || !out) return fail(HEAR_E_INVAL, "null argument");
+    return guard(ctx, [&] { *out = model_create(ctx, layers, n_layers, clip_dim); });
+}
+
+void hear_model_destroy(hear_model *m) {
+    if (m) cudaSetDevice(m->ctx->device);
+    delete m;
+}
+
+hear_status hear_model_rotations(const hear_model *m, int32_t *steps, size_t cap, size_t *n) {
+    if (!m) return fail(HEAR_E_INVAL, "null model");
+    return copy_out(m->rotations, steps, cap, n);
+}
+
+hear_status hear_model_output_positions(const hear_model *m, uint32_t *pos, size_t cap, size_t *n) {
+    if (!m) return fail(HEAR_E_INVAL, "null model");
+    return copy_out(m->out_pos, pos, cap, n);
+}
+
+static hear_status evaluate_range(const hear_model *m, size_t l0, size_t l1, const hear_eval_keys *evk,
+                                  hear_ciphertext *const *in, size_t n_ct, hear_ciphertext **out, void *stream) {
+    if (!m || !evk || !in || !out || n_ct == 0) return fail(HEAR_E_INVAL, "null argument");
+    hear_context *c = m->ctx;
+    if (evk->ctx != c) return fail(HEAR_E_STATE, "keys from another context");
+    const uint32_t lin = m->layers[l0].level_in;
+    for (size_t i = 0; i < n_ct; i++) {
+        if (!in[i] || in[i]->ctx != c) return fail(HEAR_E_STATE, "ciphertext from another context");
+        if (in[i]->level != lin || in[i]->n_poly != 2) return fail(HEAR_E_LEVEL, "input not at the layer's level");
+        if (in[i]->scale != in[0]->scale) return fail(HEAR_E_SCALE, "inputs at different scales");
+    }
+    return guard(c, [&] {
+        cudaStream_t st = stream_of(c, stream);
+        const uint64_t ctw = 2ull * (lin + 1) * c->n;
+        DevBuf X((size_t)n_ct * ctw * 8, st);
+        for (size_t i = 0; i < n_ct; i++)
+            HEAR_CHECK_CUDA(cudaMemcpyAsync(X.u64() + i * ctw, in[i]->d.p, ctw * 8, cudaMemcpyDeviceToDevice, st));
+        uint32_t lout;
+        double sout;
+        DevBuf Y = evaluate_batch(m, evk, l0, l1, X.u64(), (uint32_t)n_ct, &lout, in[0]->scale, &sout, st);
+        const uint64_t otw = 2ull * (lout + 1) * c->n;
+        std::vector<std::unique_ptr<hear_ciphertext>> res;
+        for (size_t i = 0; i < n_ct; i++) {
+            res.emplace_back(new_ct(c, lout, 2, sout));
+            HEAR_CHECK_CUDA(cudaMemcpyAsync(res.back()->d.p, Y.u64() + i * otw, otw * 8, cudaMemcpyDeviceToDevice, st));
+        }
+        for (size_t i = 0; i < n_ct; i++) out[i] = res[i].release();
+    });
+}
+
+hear_status hear_evaluate(const hear_model *m, const hear_eval_keys *evk, hear_ciphertext *const *in, size_t n_ct,
+                          hear_ciphertext **out, void *stream) {
+    if (!m) return fail(HEAR_E_INVAL, "null model");
+    return evaluate_range(m, 0, m->layers.size(), evk, in, n_ct, out, stream);
+}
+
+hear_status hear_evaluate_layer(const hear_model *m, size_t layer, const hear_eval_keys *evk,
+                                hear_ciphertext *const *in, size_t n_ct, hear_ciphertext **out, void *stream) {
+    if (!m || layer >= m->layers.size()) return fail(HEAR_E_INVAL, "bad layer index");
+    return evaluate_range(m, layer, layer + 1, evk, in, n_ct, out, stream);
+}
+
+hear_status hear_evaluate_host(const hear_model *m, const hear_eval_keys *evk, const uint64_t *in_words, size_t n_ct,
+                               double scale, uint64_t *out_words, size_t cap, size_t *n, uint32_t *level_out,
+                               double *scale_out, void *stream) {
+    if (!m || !evk || !in_words || n_ct == 0) return fail(HEAR_E_INVAL, "null argument");
+    hear_context *c = m->ctx;
+    const uint32_t lout_expect = m->layers.back().level_out;
+    const size_t out_words_n = n_ct * 2ull * (lout_expect + 1) * c->n;
+    if (n) *n = out_words_n;
+    if (!out_words || cap < out_words_n) return fail(HEAR_E_INVAL, "output capacity too small");
+    return guard(c, [&] {
+        cudaStream_t st = stream_of(c, stream);
+        const uint32_t lin = m->layers[0].level_in;
+        const uint64_t ctw = 2ull * (lin + 1) * c->n;
+        DevBuf X((size_t)n_ct * ctw * 8, st);
+        to_device_ntt(c, in_words, lin, (uint32_t)(2 * n_ct), X.u64(), st);
+        uint32_t lout;
+        double sout;
+        DevBuf Y = evaluate_batch(m, evk, 0, m->layers.size(), X.u64(), (uint32_t)n_ct, &lout, scale, &sout, st);
+        ntt_inverse(c, Y.u64(), (uint32_t)(2 * n_ct) * (lout + 1), map_q(lout, c->n_q), st);
+        HEAR_CHECK_CUDA(cudaMemcpyAsync(out_words, Y.p, out_words_n * 8, cudaMemcpyDeviceToHost, st));
+        HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
+        if (level_out) *level_out = lout;
+        if (scale_out) *scale_out = sout;
+    });
+}
+
+hear_status hear_dbg_poly_mul(hear_context *ctx, uint32_t prime, const uint64_t *a, const uint64_t *b, uint64_t *out) {
+    if (!ctx || !a || !b || !out) return fail(HEAR_E_INVAL, "null argument");
+    if (prime >= ctx->nqp()) return fail(HEAR_E_INVAL, "bad prime index");
+    return guard(ctx, [&] {
+        cudaStream_t st = ctx->stream;
+        const uint32_t n = ctx->n;
+        DevBuf d(3ull * n * 8, st);
+        HEAR_CHECK_CUDA(cudaMemcpyAsync(d.p, a, n * 8, cudaMemcpyHostToDevice, st));
+        HEAR_CHECK_CUDA(cudaMemcpyAsync(d.u64() + n, b, n * 8, cudaMemcpyHostToDevice, st));
+        LimbMap m;
+        m.per_group = 1;
+        m.q_base = prime < ctx->n_q ? prime : 0;
+        m.q_count = prime < ctx->n_q ? 1 : 0;
+        m.n_q = ctx->n_q + (prime < ctx->n_q ? 0 : prime - ctx->n_q);
+        ntt_forward(ctx, d.u64(), 2, m, st);
+        // b -> Montgomery form, then a * b
+        to_mont(ctx, d.u64() + n, 1, m, st);
+        pointwise_mont(ctx, 1, m, d.u64(), d.u64() + n, d.u64() + 2 * n, st);
+        ntt_inverse(ctx, d.u64() + 2 * n, 1, m, st);
+        HEAR_CHECK_CUDA(cudaMemcpyAsync(out, d.u64() + 2 * n, n * 8, cudaMemcpyDeviceToHost, st));
+        HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+hear_status hear_dbg_ntt_roundtrip(hear_context *ctx, uint64_t *limbs, size_t n_limb) {
+    if (!ctx || !limbs || n_limb == 0) return fail(HEAR_E_INVAL, "null argument");
+    return guard(ctx, [&] {
+        cudaStream_t st = ctx->stream;
+        const size_t words = n_limb * ctx->n;
+        DevBuf d(words * 8, st);
+        HEAR_CHECK_CUDA(cudaMemcpyAsync(d.p, limbs, words * 8, cudaMemcpyHostToDevice, st));
+        LimbMap m;
+        m.per_group = ctx->nqp();
+        m.q_count = ctx->n_q;
+        m.n_q = ctx->n_q;
+        ntt_forward(ctx, d.u64(), (uint32_t)n_limb, m, st);
+        ntt_inverse(ctx, d.u64(), (uint32_t)n_limb, m, st);
+        HEAR_CHECK_CUDA(cudaMemcpyAsync(limbs, d.p, words * 8, cudaMemcpyDeviceToHost, st));
+        HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+}  // extern "C"

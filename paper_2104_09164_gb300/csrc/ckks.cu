@@ -1,0 +1,504 @@
+// ckks.cu -- RNS-CKKS key generation, encryption, decryption and the batched homomorphic
+// operations the encrypted network is made of, composed from the kernels of ntt.cu and
+// kernels.cu.  Everything between the host encode and the host CRT lift runs on the GPU.
+#include <algorithm>
+#include <cstring>
+#include <set>
+#include "ckks.h"
+
+namespace hear {
+
+// randomness streams (purpose ids of the ChaCha20 nonce)
+enum Purpose : uint32_t {
+    kSk = 1, kPkA = 2, kPkE = 3, kKskA = 4, kKskE = 5, kEncV = 8, kEncE0 = 9, kEncE1 = 10
+};
+
+namespace {
+std::mutex g_enc_mu;
+std::map<hear_context *, std::shared_ptr<EncoderTables>> g_enc;
+
+DevBuf upload(const void *host, size_t bytes, cudaStream_t st) {
+    DevBuf b(bytes, st);
+    HEAR_CHECK_CUDA(cudaMemcpyAsync(b.p, host, bytes, cudaMemcpyHostToDevice, st));
+    return b;
+}
+}  // namespace
+
+std::shared_ptr<EncoderTables> encoder(hear_context *ctx) {
+    std::lock_guard<std::mutex> g(g_enc_mu);
+    auto it = g_enc.find(ctx);
+    if (it != g_enc.end()) return it->second;
+    auto t = make_encoder_tables(ctx->log_n);
+    g_enc[ctx] = t;
+    return t;
+}
+void forget_encoder(hear_context *ctx) {
+    std::lock_guard<std::mutex> g(g_enc_mu);
+    g_enc.erase(ctx);
+}
+
+uint32_t galois_of(const hear_context *c, int64_t step) {
+    const int64_t slots = c->n / 2;
+    int64_t r = ((step % slots) + slots) % slots;
+    return (uint32_t)hm::powmod(5, (uint64_t)r, 2ull * c->n);
+}
+
+// ------------------------------------------------------------------ keys
+void keygen(hear_context *c, uint64_t seed, const int32_t *steps, size_t n_steps, hear_secret_key **sk_out,
+            hear_public_key **pk_out, hear_eval_keys **evk_out) {
+    cudaStream_t st = c->stream;
+    const uint32_t n = c->n, nqp = c->nqp(), nq = c->n_q;
+    LimbMap all;   // every prime, in index order
+    all.per_group = nqp;
+    all.q_count = nq;
+    all.n_q = nq;
+    const LimbMap mq = map_q(c->L, nq);
+
+    auto sk = std::make_unique<hear_secret_key>();
+    sk->ctx = c;
+    DevBuf s8(n, st);
+    sample_small(c, seed, kSk, 0, kTernary, (int8_t *)s8.p, st);
+    sk->s.resize(n);
+    HEAR_CHECK_CUDA(cudaMemcpyAsync(sk->s.data(), s8.p, n, cudaMemcpyDeviceToHost, st));
+    DevBuf s_ntt((size_t)nqp * n * 8, st);
+    small_to_limbs(c, (const int8_t *)s8.p, s_ntt.u64(), nqp, all, st);
+    ntt_forward(c, s_ntt.u64(), nqp, all, st);
+    sk->s_mont = DevBuf((size_t)nqp * n * 8, nullptr);
+    HEAR_CHECK_CUDA(cudaMemcpyAsync(sk->s_mont.p, s_ntt.p, (size_t)nqp * n * 8, cudaMemcpyDeviceToDevice, st));
+    to_mont(c, sk->s_mont.u64(), nqp, all, st);
+
+    // public key (b, a) = (-a s + e, a) over Q_L
+    auto pk = std::make_unique<hear_public_key>();
+    pk->ctx = c;
+    pk->pk_mont = DevBuf(2ull * nq * n * 8, nullptr);
+    uint64_t *pb = pk->pk_mont.u64(), *pa = pb + (size_t)nq * n;
+    DevBuf e8(n, st), en((size_t)nqp * n * 8, st);
+    sample_uniform(c, seed, kPkA, 0, pa, nq, mq, st);
+    ntt_forward(c, pa, nq, mq, st);
+    sample_small(c, seed, kPkE, 0, kGauss, (int8_t *)e8.p, st);
+    small_to_limbs(c, (const int8_t *)e8.p, en.u64(), nq, mq, st);
+    ntt_forward(c, en.u64(), nq, mq, st);
+    pk_combine(c, pa, sk->s_mont.u64(), en.u64(), pb, st);
+    LimbMap two_q = mq;
+    to_mont(c, pb, 2 * nq, two_q, st);
+
+    // switching keys: relinearisation (s^2) and one per rotation (sigma_g(s))
+    auto evk = std::make_unique<hear_eval_keys>();
+    evk->ctx = c;
+    std::vector<uint64_t> pmod(nqp, 0);
+    for (uint32_t t = 0; t < nq; t++) {
+        uint64_t v = 1;
+        for (uint32_t k = 0; k < c->K; k++) v = hm::mulmod(v, c->primes[nq + k] % c->primes[t], c->primes[t]);
+        pmod[t] = v;
+    }
+    DevBuf d_pmod = upload(pmod.data(), pmod.size() * 8, st);
+    std::vector<uint32_t> gals{1u};
+    std::set<uint32_t> seen{1u};
+    for (size_t i = 0; i < n_steps; i++) {
+        uint32_t g = galois_of(c, steps[i]);
+        if (g != 1 && seen.insert(g).second) gals.push_back(g);
+    }
+    const uint32_t dnum = c->dnum_max();
+    const size_t plane = (size_t)nqp * n;
+    DevBuf sp((size_t)nqp * n * 8, st), a_tmp(plane * 8, st);
+    for (uint32_t g : gals) {
+        if (g == 1) pointwise_mont(c, nqp, all, s_ntt.u64(), sk->s_mont.u64(), sp.u64(), st);   // s^2
+        else automorphism(c, nqp - 1, 1, g, s_ntt.u64(), sp.u64(), st);                          // sigma_g(s)
+        to_mont(c, sp.u64(), nqp, all, st);
+        DevBuf key((size_t)dnum * 2 * plane * 8, nullptr);
+        for (uint32_t j = 0; j < dnum; j++) {
+            uint64_t base = ((uint64_t)g << 16) | ((uint64_t)j << 8);
+            uint64_t *kb = key.u64() + (size_t)j * 2 * plane, *ka = kb + plane;
+            sample_uniform(c, seed, kKskA, base, ka, nqp, all, st);
+            ntt_forward(c, ka, nqp, all, st);
+            sample_small(c, seed, kKskE, base, kGauss, (int8_t *)e8.p, st);
+            small_to_limbs(c, (const int8_t *)e8.p, en.u64(), nqp, all, st);
+            ntt_forward(c, en.u64(), nqp, all, st);
+            swk_combine(c, ka, sk->s_mont.u64(), en.u64(), sp.u64(), d_pmod.u64(), j, kb, st);
+        }
+        LimbMap km = all;
+        to_mont(c, key.u64(), dnum * 2 * nqp, km, st);
+        evk->keys.emplace(g, std::move(key));
+    }
+    HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
+    *sk_out = sk.release();
+    *pk_out = pk.release();
+    *evk_out = evk.release();
+}
+
+// ------------------------------------------------------------------ encryption
+hear_ciphertext *encrypt_slots(hear_context *c, const hear_public_key *pk, const double *z, double scale,
+                               uint64_t seed, uint64_t ct_id, cudaStream_t st) {
+    const uint32_t n = c->n, nq = c->n_q;
+    const LimbMap mq = map_q(c->L, nq);
+    std::vector<int64_t> m(n);
+    encode_dd(*encoder(c), z, scale, m.data());
+    DevBuf dm = upload(m.data(), n * 8, st);
+    const size_t limbs = (size_t)nq * n;
+    DevBuf buf(4 * limbs * 8, st), e8(n, st);
+    uint64_t *mn = buf.u64(), *vn = mn + limbs, *e0 = vn + limbs, *e1 = e0 + limbs;
+    i64_to_limbs(c, (const int64_t *)dm.p, mn, nq, mq, st);
+    sample_small(c, seed, kEncV, ct_id, kTernary, (int8_t *)e8.p, st);
+    small_to_limbs(c, (const int8_t *)e8.p, vn, nq, mq, st);
+    sample_small(c, seed, kEncE0, ct_id, kGauss, (int8_t *)e8.p, st);
+    small_to_limbs(c, (const int8_t *)e8.p, e0, nq, mq, st);
+    sample_small(c, seed, kEncE1, ct_id, kGauss, (int8_t *)e8.p, st);
+    small_to_limbs(c, (const int8_t *)e8.p, e1, nq, mq, st);
+    LimbMap four = mq;
+    ntt_forward(c, mn, 4 * nq, four, st);
+    auto ct = std::make_unique<hear_ciphertext>();
+    ct->ctx = c;
+    ct->level = c->L;
+    ct->n_poly = 2;
+    ct->scale = scale;
+    ct->d = DevBuf(2 * limbs * 8, nullptr);
+    encrypt_combine(c, vn, e0, e1, mn, pk->pk_mont.u64(), ct->d.u64(), st);
+    return ct.release();
+}
+
+void decrypt_slots(hear_context *c, const hear_secret_key *sk, const hear_ciphertext *ct, double *out) {
+    cudaStream_t st = c->stream;
+    const uint32_t n = c->n, L1 = ct->level + 1;
+    DevBuf m((size_t)L1 * n * 8, st);
+    decrypt_combine(c, ct->level, ct->d.u64(), sk->s_mont.u64(), m.u64(), st);
+    ntt_inverse(c, m.u64(), L1, map_q(ct->level, c->n_q), st);
+    std::vector<uint64_t> res((size_t)L1 * n);
+    HEAR_CHECK_CUDA(cudaMemcpyAsync(res.data(), m.p, res.size() * 8, cudaMemcpyDeviceToHost, st));
+    HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
+    std::vector<double> v(n);
+    crt_to_double(res.data(), c->primes.data(), L1, n, 1.0 / ct->scale, v.data());
+    decode_double(c->log_n, v.data(), out);
+}
+
+DevBuf encode_plain(hear_context *c, const double *z, double scale, uint32_t level, cudaStream_t st) {
+    const uint32_t n = c->n, L1 = level + 1;
+    std::vector<int64_t> m(n);
+    encode_dd(*encoder(c), z, scale, m.data());
+    DevBuf dm = upload(m.data(), n * 8, st);
+    DevBuf pt((size_t)L1 * n * 8, nullptr);
+    i64_to_limbs(c, (const int64_t *)dm.p, pt.u64(), L1, map_q(level, c->n_q), st);
+    ntt_forward(c, pt.u64(), L1, map_q(level, c->n_q), st);
+    to_mont(c, pt.u64(), L1, map_q(level, c->n_q), st);
+    HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
+    return pt;
+}
+
+// ------------------------------------------------------------------ key switching compositions
+namespace {
+struct RotTable {
+    DevBuf d;
+    const uint64_t *const *keys(size_t r, uint32_t n_ct) const {
+        return reinterpret_cast<const uint64_t *const *>(d.u64() + r * n_ct);
+    }
+    const uint32_t *gals(size_t off_words, size_t r, uint32_t n_ct) const {
+        return reinterpret_cast<const uint32_t *>(d.u64() + off_words) + r * n_ct;
+    }
+};
+}  // namespace
+
+void rotate_hoisted(hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *x, const std::vector<Rot> &rots,
+                    const std::vector<uint64_t *> &outs, cudaStream_t st) {
+    if (rots.empty()) return;
+    const uint32_t n = c->n, L1 = level + 1, W = L1 + c->K, dnum = c->dnum(level);
+    const uint64_t plane = (uint64_t)L1 * n, ctw = 2 * plane;
+    DevBuf ext((size_t)n_ct * dnum * W * n * 8, st), tmp((size_t)n_ct * ctw * 8, st),
+        acc((size_t)n_ct * 2 * W * n * 8, st);
+    modup(c, level, n_ct, x + plane, ctw, ext.u64(), tmp.u64(), st);
+    // per rotation: n_ct key pointers and n_ct galois elements
+    const size_t R = rots.size();
+    const size_t key_words = R * n_ct, gal_words = (R * n_ct + 1) / 2;
+    std::vector<uint64_t> host(key_words + gal_words, 0);
+    uint32_t *g32 = reinterpret_cast<uint32_t *>(host.data() + key_words);
+    for (size_t r = 0; r < R; r++)
+        for (uint32_t i = 0; i < n_ct; i++) {
+            host[r * n_ct + i] = (uint64_t)(uintptr_t)rots[r].key;
+            g32[r * n_ct + i] = rots[r].galois;
+        }
+    RotTable tab{upload(host.data(), host.size() * 8, st)};
+    for (size_t r = 0; r < R; r++) {
+        ks_inner(c, level, n_ct, ext.u64(), tab.keys(r, n_ct), tab.gals(key_words, r, n_ct), acc.u64(), st);
+        moddown(c, level, n_ct, acc.u64(), outs[r], x, ctw, 1u, tab.gals(key_words, r, n_ct), tmp.u64(), st);
+    }
+}
+
+void rotate_each(hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *x, const std::vector<Rot> &rots,
+                 uint64_t *out, cudaStream_t st) {
+    const uint32_t n = c->n, L1 = level + 1, W = L1 + c->K, dnum = c->dnum(level);
+    const uint64_t plane = (uint64_t)L1 * n, ctw = 2 * plane;
+    DevBuf ext((size_t)n_ct * dnum * W * n * 8, st), tmp((size_t)n_ct * ctw * 8, st),
+        acc((size_t)n_ct * 2 * W * n * 8, st);
+    modup(c, level, n_ct, x + plane, ctw, ext.u64(), tmp.u64(), st);
+    const size_t key_words = n_ct, gal_words = (n_ct + 1) / 2;
+    std::vector<uint64_t> host(key_words + gal_words, 0);
+    uint32_t *g32 = reinterpret_cast<uint32_t *>(host.data() + key_words);
+    for (uint32_t i = 0; i < n_ct; i++) {
+        host[i] = (uint64_t)(uintptr_t)rots[i].key;
+        g32[i] = rots[i].galois;
+    }
+    RotTable tab{upload(host.data(), host.size() * 8, st)};
+    ks_inner(c, level, n_ct, ext.u64(), tab.keys(0, n_ct), tab.gals(key_words, 0, n_ct), acc.u64(), st);
+    moddown(c, level, n_ct, acc.u64(), out, x, ctw, 1u, tab.gals(key_words, 0, n_ct), tmp.u64(), st);
+}
+
+void mul_relin(hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *a, const uint64_t *b,
+               const uint64_t *relin_key, uint64_t *out, cudaStream_t st) {
+    const uint32_t n = c->n, L1 = level + 1, W = L1 + c->K, dnum = c->dnum(level);
+    const uint64_t plane = (uint64_t)L1 * n;
+    DevBuf d3((size_t)n_ct * 3 * plane * 8, st);
+    tensor_ct(c, level, n_ct, a, b, d3.u64(), st);
+    DevBuf ext((size_t)n_ct * dnum * W * n * 8, st), tmp((size_t)n_ct * 2 * plane * 8, st),
+        acc((size_t)n_ct * 2 * W * n * 8, st);
+    modup(c, level, n_ct, d3.u64() + 2 * plane, 3 * plane, ext.u64(), tmp.u64(), st);
+    std::vector<uint64_t> host(n_ct, (uint64_t)(uintptr_t)relin_key);
+    DevBuf keys = upload(host.data(), host.size() * 8, st);
+    ks_inner(c, level, n_ct, ext.u64(), reinterpret_cast<const uint64_t *const *>(keys.p), nullptr, acc.u64(), st);
+    moddown(c, level, n_ct, acc.u64(), out, d3.u64(), 3 * plane, 3u, nullptr, tmp.u64(), st);
+}
+
+// ------------------------------------------------------------------ network
+namespace {
+
+void build_fc(hear_context *c, hear_model::Fc &fc, const double *W, uint32_t d_out, uint32_t d_in, uint32_t level,
+              uint32_t k, uint32_t M) {
+    HEAR_REQUIRE(d_out && d_in && (d_out & (d_out - 1)) == 0 && (d_in & (d_in - 1)) == 0 && d_in % d_out == 0 &&
+                     M % d_in == 0,
+                 HEAR_E_INVAL, "FC dimensions must be powers of two with d_out | d_in | clip_dim");
+    HEAR_REQUIRE(level >= 1, HEAR_E_LEVEL, "not enough levels for the network");
+    cudaStream_t st = c->stream;
+    fc.d_out = d_out;
+    fc.d_in = d_in;
+    fc.D = d_out;
+    fc.level = level;
+    uint32_t n1 = 1;
+    while (n1 * n1 < fc.D) n1 *= 2;
+    n1 = std::min(n1, fc.D);
+    fc.n1 = n1;
+    fc.n2 = (fc.D + n1 - 1) / n1;
+    const uint32_t n = c->n, slots = n / 2, L1 = level + 1;
+    const double ql = (double)c->primes[level];
+    // diagonal plaintexts, pre-rotated by rho^(-j n1) (baby-step strategy re-association)
+    std::vector<std::pair<uint32_t, uint32_t>> jobs;
+    for (uint32_t j = 0; j < fc.n2; j++)
+        for (uint32_t b = 0; b < n1; b++)
+            if (j * n1 + b < fc.D) jobs.push_back({j, b});
+    fc.pts.clear();
+    fc.pts.resize((size_t)fc.n2 * n1);
+    std::vector<uint64_t> ptrs((size_t)fc.n2 * n1, 0);
+    auto enc = encoder(c);
+    const size_t chunk = 64;
+    std::vector<double> z;
+    std::vector<int64_t> m;
+    std::vector<double> scales;
+    for (size_t s0 = 0; s0 < jobs.size(); s0 += chunk) {
+        size_t cnt = std::min(chunk, jobs.size() - s0);
+        z.assign(cnt * slots, 0.0);
+        m.assign(cnt * n, 0);
+        scales.assign(cnt, ql);
+        for (size_t q = 0; q < cnt; q++) {
+            uint32_t j = jobs[s0 + q].first, b = jobs[s0 + q].second, i = j * n1 + b;
+            double *zz = &z[q * slots];
+            for (uint32_t p = 0; p < M; p++) {
+                uint32_t src = (p + M - (j * n1) % M) % M;       // rho^(-j n1)(diag_i)[p] = diag_i[p - j n1]
+                double v = W[(size_t)(src % d_out) * d_in + (src + i) % d_in];
+                for (uint32_t cc = 0; cc < k; cc++) zz[(size_t)p * k + cc] = v;
+            }
+        }
+        encode_many(*enc, z.data(), cnt, scales.data(), m.data());
+        DevBuf dm = upload(m.data(), m.size() * 8, st);
+        for (size_t q = 0; q < cnt; q++) {
+            uint32_t j = jobs[s0 + q].first, b = jobs[s0 + q].second;
+            DevBuf pt((size_t)L1 * n * 8, nullptr);
+            i64_to_limbs(c, (const int64_t *)dm.p + q * n, pt.u64(), L1, map_q(level, c->n_q), st);
+            ntt_forward(c, pt.u64(), L1, map_q(level, c->n_q), st);
+            to_mont(c, pt.u64(), L1, map_q(level, c->n_q), st);
+            ptrs[(size_t)j * n1 + b] = (uint64_t)(uintptr_t)pt.p;
+            fc.pts[(size_t)j * n1 + b] = std::move(pt);
+        }
+        HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
+    }
+    fc.d_pt_ptrs = DevBuf(ptrs.size() * 8, nullptr);
+    HEAR_CHECK_CUDA(cudaMemcpy(fc.d_pt_ptrs.p, ptrs.data(), ptrs.size() * 8, cudaMemcpyHostToDevice));
+    fc.rotsum.clear();
+    for (uint32_t s = d_out; s < d_in; s *= 2) fc.rotsum.push_back((int32_t)(s * k));
+}
+
+void fc_rotations(const hear_model::Fc &fc, uint32_t k, std::set<int32_t> &out) {
+    for (uint32_t b = 1; b < fc.n1; b++) out.insert((int32_t)(b * k));
+    for (uint32_t j = 1; j < fc.n2; j++) out.insert((int32_t)(j * fc.n1 * k));
+    for (int32_t s : fc.rotsum) out.insert(s);
+}
+
+const uint64_t *need_key(const hear_eval_keys *evk, uint32_t g) {
+    const uint64_t *k = evk->key(g);
+    HEAR_REQUIRE(k, HEAR_E_NOKEY, "missing switching key for galois element " + std::to_string(g));
+    return k;
+}
+
+// rotate-and-sum x <- x + rho^s(x) for each step s
+void rotsum(hear_context *c, const hear_eval_keys *evk, uint32_t level, uint32_t n_ct, uint64_t *x,
+            const std::vector<int32_t> &steps, cudaStream_t st) {
+    const uint64_t ctw = 2ull * (level + 1) * c->n;
+    DevBuf r((size_t)n_ct * ctw * 8, st);
+    for (int32_t s : steps) {
+        uint32_t g = galois_of(c, s);
+        std::vector<Rot> rots(n_ct, Rot{need_key(evk, g), g});
+        rotate_each(c, level, n_ct, x, rots, r.u64(), st);
+        add_ct(c, level, 2 * n_ct, x, r.u64(), x, st);
+    }
+}
+
+DevBuf eval_fc(const hear_model *m, const hear_model::Fc &fc, const hear_eval_keys *evk, const uint64_t *x,
+               uint32_t n_ct, cudaStream_t st) {
+    hear_context *c = m->ctx;
+    const uint32_t level = fc.level, n = c->n, L1 = level + 1, n1 = fc.n1, n2 = fc.n2, k = m->k;
+    const uint64_t ctw = 2ull * L1 * n, batch = (uint64_t)n_ct * ctw;
+    // baby steps rho^(b k)(x), b < n1, hoisted
+    DevBuf babies((size_t)(n1 > 1 ? n1 - 1 : 1) * batch * 8, st);
+    std::vector<const uint64_t *> in_ptrs(n1);
+    in_ptrs[0] = x;
+    std::vector<Rot> rots;
+    std::vector<uint64_t *> outs;
+    for (uint32_t b = 1; b < n1; b++) {
+        uint32_t g = galois_of(c, (int64_t)b * k);
+        rots.push_back(Rot{need_key(evk, g), g});
+        outs.push_back(babies.u64() + (b - 1) * batch);
+        in_ptrs[b] = outs.back();
+    }
+    rotate_hoisted(c, level, n_ct, x, rots, outs, st);
+    // giant-step inner sums sum_b pt_{j,b} (.) baby_b (lazy: no rescale yet)
+    DevBuf G((size_t)n2 * batch * 8, st);
+    std::vector<uint64_t> ptr_host(n1 + n2);
+    for (uint32_t b = 0; b < n1; b++) ptr_host[b] = (uint64_t)(uintptr_t)in_ptrs[b];
+    for (uint32_t j = 0; j < n2; j++) ptr_host[n1 + j] = (uint64_t)(uintptr_t)(G.u64() + j * batch);
+    DevBuf d_ptrs = upload(ptr_host.data(), ptr_host.size() * 8, st);
+    lincomb(c, level, n_ct, n1, n2, reinterpret_cast<const uint64_t *const *>(d_ptrs.p),
+            reinterpret_cast<const uint64_t *const *>(fc.d_pt_ptrs.p),
+            reinterpret_cast<uint64_t *const *>(d_ptrs.u64() + n1), st);
+    // giant rotations rho^(j n1 k), j >= 1, of the un-rescaled sums, then accumulate
+    if (n2 > 1) {
+        const uint32_t cnt = (n2 - 1) * n_ct;
+        std::vector<Rot> gr;
+        for (uint32_t j = 1; j < n2; j++) {
+            uint32_t g = galois_of(c, (int64_t)j * n1 * k);
+            const uint64_t *key = need_key(evk, g);
+            for (uint32_t i = 0; i < n_ct; i++) gr.push_back(Rot{key, g});
+        }
+        DevBuf R((size_t)cnt * ctw * 8, st);
+        rotate_each(c, level, cnt, G.u64() + batch, gr, R.u64(), st);
+        for (uint32_t j = 0; j + 1 < n2; j++) add_ct(c, level, 2 * n_ct, G.u64(), R.u64() + j * batch, G.u64(), st);
+    }
+    // one rescale (lazy rescaling), then rotate-and-sum over the d_in / d_out blocks
+    DevBuf Y((size_t)n_ct * 2 * level * n * 8, st), tmp((size_t)n_ct * 2 * level * n * 8, st);
+    rescale(c, level, 2 * n_ct, G.u64(), Y.u64(), tmp.u64(), st);
+    rotsum(c, evk, level - 1, n_ct, Y.u64(), fc.rotsum, st);
+    return Y;
+}
+
+}  // namespace
+
+hear_model *model_create(hear_context *c, const hear_layer_desc *layers, size_t n_layers, uint32_t clip_dim) {
+    HEAR_REQUIRE(layers && n_layers > 0, HEAR_E_INVAL, "no layers");
+    const uint32_t slots = c->n / 2;
+    HEAR_REQUIRE(clip_dim && (clip_dim & (clip_dim - 1)) == 0 && clip_dim <= slots, HEAR_E_INVAL,
+                 "clip_dim must be a power of two <= N/2");
+    auto m = std::make_unique<hear_model>();
+    m->ctx = c;
+    m->clip_dim = clip_dim;
+    m->k = slots / clip_dim;
+    m->M = clip_dim;
+    uint32_t level = c->L, dim = clip_dim;
+    std::set<int32_t> rots;
+    for (size_t li = 0; li < n_layers; li++) {
+        const hear_layer_desc &d = layers[li];
+        hear_model::Layer L;
+        L.kind = d.kind;
+        L.level_in = level;
+        if (d.kind == HEAR_LAYER_FC) {
+            HEAR_REQUIRE(d.w && d.d_in == dim, HEAR_E_INVAL, "FC input dimension mismatch");
+            HEAR_REQUIRE(!d.bias, HEAR_E_UNSUPPORTED, "bias is not supported");
+            build_fc(c, L.fc, d.w, d.d_out, d.d_in, level, m->k, m->M);
+            fc_rotations(L.fc, m->k, rots);
+            level -= 1;
+            dim = d.d_out;
+        } else if (d.kind == HEAR_LAYER_SQUARE) {
+            HEAR_REQUIRE(level >= 1, HEAR_E_LEVEL, "not enough levels for the network");
+            level -= 1;
+        } else if (d.kind == HEAR_LAYER_FC_SQ_FC) {
+            HEAR_REQUIRE(d.w && d.w2 && d.d_in == dim && li + 1 == n_layers, HEAR_E_INVAL,
+                         "FC_SQ_FC must be the last layer and match the input dimension");
+            HEAR_REQUIRE(level >= 2, HEAR_E_LEVEL, "not enough levels for the network");
+            const uint32_t d1 = d.d_out, d2 = d.d_out2;
+            build_fc(c, L.fc, d.w, d1, d.d_in, level, m->k, m->M);
+            std::vector<double> U((size_t)d2 * d1 * d.d_in);
+            for (uint32_t cc = 0; cc < d2; cc++)
+                for (uint32_t r = 0; r < d1; r++)
+                    for (uint32_t col = 0; col < d.d_in; col++)
+                        U[((size_t)cc * d1 + r) * d.d_in + col] = d.w2[(size_t)cc * d1 + r] * d.w[(size_t)r * d.d_in + col];
+            build_fc(c, L.fc2, U.data(), d2 * d1, d.d_in, level, m->k, m->M);
+            fc_rotations(L.fc, m->k, rots);
+            fc_rotations(L.fc2, m->k, rots);
+            for (uint32_t s = 1; s < d1; s *= 2) L.final_rotsum.push_back((int32_t)(s * m->k));
+            for (int32_t s : L.final_rotsum) rots.insert(s);
+            level -= 2;
+            for (uint32_t cc = 0; cc < d2; cc++) m->out_pos.push_back(cc * d1);
+            dim = 0;
+        } else {
+            throw Error(HEAR_E_INVAL, "unknown layer kind");
+        }
+        L.level_out = level;
+        m->layers.push_back(std::move(L));
+    }
+    if (m->out_pos.empty())
+        for (uint32_t cc = 0; cc < dim; cc++) m->out_pos.push_back(cc);
+    m->rotations.assign(rots.begin(), rots.end());
+    return m.release();
+}
+
+DevBuf evaluate_batch(const hear_model *m, const hear_eval_keys *evk, size_t l0, size_t l1, const uint64_t *x,
+                      uint32_t n_ct, uint32_t *level_out, double scale_in, double *scale_out, cudaStream_t st) {
+    hear_context *c = m->ctx;
+    const uint32_t n = c->n;
+    DevBuf cur;
+    const uint64_t *xin = x;
+    double scale = scale_in;
+    uint32_t level = m->layers[l0].level_in;
+    for (size_t li = l0; li < l1; li++) {
+        const hear_model::Layer &L = m->layers[li];
+        DevBuf next;
+        if (L.kind == HEAR_LAYER_FC) {
+            const double ql = (double)c->primes[L.fc.level];
+            next = eval_fc(m, L.fc, evk, xin, n_ct, st);
+            scale = scale * ql / ql;
+        } else if (L.kind == HEAR_LAYER_SQUARE) {
+            const uint64_t *rk = need_key(evk, 1);
+            DevBuf prod((size_t)n_ct * 2 * (level + 1) * n * 8, st);
+            mul_relin(c, level, n_ct, xin, xin, rk, prod.u64(), st);
+            next = DevBuf((size_t)n_ct * 2 * level * n * 8, st);
+            DevBuf tmp((size_t)n_ct * 2 * level * n * 8, st);
+            rescale(c, level, 2 * n_ct, prod.u64(), next.u64(), tmp.u64(), st);
+            scale = scale * scale / (double)c->primes[level];
+        } else {
+            const double ql = (double)c->primes[L.fc.level];
+            DevBuf y = eval_fc(m, L.fc, evk, xin, n_ct, st);
+            DevBuf u = eval_fc(m, L.fc2, evk, xin, n_ct, st);
+            const double s1 = scale * ql / ql;
+            const uint32_t lv = level - 1;
+            const uint64_t *rk = need_key(evk, 1);
+            DevBuf prod((size_t)n_ct * 2 * (lv + 1) * n * 8, st);
+            mul_relin(c, lv, n_ct, y.u64(), u.u64(), rk, prod.u64(), st);
+            next = DevBuf((size_t)n_ct * 2 * lv * n * 8, st);
+            DevBuf tmp((size_t)n_ct * 2 * lv * n * 8, st);
+            rescale(c, lv, 2 * n_ct, prod.u64(), next.u64(), tmp.u64(), st);
+            scale = s1 * s1 / (double)c->primes[lv];
+            rotsum(c, evk, lv - 1, n_ct, next.u64(), L.final_rotsum, st);
+        }
+        level = L.level_out;
+        cur = std::move(next);
+        xin = cur.u64();
+    }
+    *level_out = level;
+    *scale_out = scale;
+    return cur;
+}
+
+}  // namespace hear

@@ -1,0 +1,73 @@
+// ckks.h -- batched RNS-CKKS operations and the encoded network (internal).
+#pragma once
+#include <memory>
+#include <mutex>
+#include <vector>
+#include "internal.h"
+#include "kernels.cuh"
+#include "encode.h"
+
+// Encoded network (Methods, "Non-convolutional layers" and "Algorithmic and cryptographic
+// optimizations").
+struct hear_model {
+    struct Fc {
+        uint32_t d_out = 0, d_in = 0, D = 0, n1 = 0, n2 = 0, level = 0;
+        std::vector<hear::DevBuf> pts;              // [n2*n1] (empty buffer = no diagonal)
+        hear::DevBuf d_pt_ptrs;                     // device array of n2*n1 pointers (null = skip)
+        hear::DevBuf bias;                          // plaintext at level-1 (Montgomery), or empty
+        std::vector<int32_t> rotsum;                // slot steps of rotate-and-sum
+    };
+    struct Layer {
+        uint32_t kind = 0;
+        uint32_t level_in = 0, level_out = 0;
+        Fc fc, fc2;                                 // FC; FC_SQ_FC: fc = W1, fc2 = collapsed U
+        std::vector<int32_t> final_rotsum;          // FC_SQ_FC: sum over r
+    };
+    hear_context *ctx = nullptr;
+    uint32_t clip_dim = 0, k = 0, M = 0;
+    std::vector<Layer> layers;
+    std::vector<uint32_t> out_pos;
+    std::vector<int32_t> rotations;
+};
+
+namespace hear {
+
+void forget_encoder(hear_context *ctx);
+std::shared_ptr<EncoderTables> encoder(hear_context *ctx);
+std::vector<uint64_t> make_cdt(double sigma);
+void build_context(hear_context *c, const hear_params_desc *d, int device);
+
+uint32_t galois_of(const hear_context *c, int64_t step);
+
+// keygen / encryption / decryption
+void keygen(hear_context *c, uint64_t seed, const int32_t *steps, size_t n_steps, hear_secret_key **sk,
+            hear_public_key **pk, hear_eval_keys **evk);
+hear_ciphertext *encrypt_slots(hear_context *c, const hear_public_key *pk, const double *z, double scale,
+                               uint64_t seed, uint64_t ct_id, cudaStream_t st);
+void decrypt_slots(hear_context *c, const hear_secret_key *sk, const hear_ciphertext *ct, double *out);
+
+// batched primitives on contiguous batches [n_ct][n_poly][level+1][N]
+struct Rot {
+    const uint64_t *key;
+    uint32_t galois;
+};
+// out_r (batch) = rho(x) for each rotation r, sharing one ModUp of x's c1 (hoisting)
+void rotate_hoisted(hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *x,
+                    const std::vector<Rot> &rots, const std::vector<uint64_t *> &outs, cudaStream_t st);
+// out[c] = rho_{rot[c]}(x[c]): independent rotations of the n_ct ciphertexts of x
+void rotate_each(hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *x, const std::vector<Rot> &rots,
+                 uint64_t *out, cudaStream_t st);
+// tensor + relinearise (no rescale): out [n_ct][2][level+1][N]
+void mul_relin(hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *a, const uint64_t *b,
+               const uint64_t *relin_key, uint64_t *out, cudaStream_t st);
+
+// encoded plaintext helpers
+DevBuf encode_plain(hear_context *c, const double *z, double scale, uint32_t level, cudaStream_t st);
+
+// network
+hear_model *model_create(hear_context *c, const hear_layer_desc *layers, size_t n_layers, uint32_t clip_dim);
+// evaluate layers [l0, l1) on a batch x at the first layer's level; returns the output batch
+DevBuf evaluate_batch(const hear_model *m, const hear_eval_keys *evk, size_t l0, size_t l1, const uint64_t *x,
+                      uint32_t n_ct, uint32_t *level_out, double scale_in, double *scale_out, cudaStream_t st);
+
+}  // namespace hear

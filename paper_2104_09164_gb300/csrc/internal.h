@@ -1,0 +1,174 @@
+// internal.h -- shared declarations of the CUDA library (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+#include "../../include/hear.h"
+
+namespace hear {
+
+constexpr int kMaxPrimes = 48;
+
+// Error carried to the C ABI boundary.
+struct Error : std::runtime_error {
+    hear_status code;
+    Error(hear_status c, const std::string &m) : std::runtime_error(m), code(c) {}
+};
+#define HEAR_CHECK_CUDA(expr)                                                              \
+    do {                                                                                   \
+        cudaError_t e__ = (expr);                                                          \
+        if (e__ != cudaSuccess)                                                            \
+            throw ::hear::Error(HEAR_E_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e__)); \
+    } while (0)
+#define HEAR_REQUIRE(cond, code, msg)                                                      \
+    do {                                                                                   \
+        if (!(cond)) throw ::hear::Error((code), (msg));                                   \
+    } while (0)
+
+// Per-prime constants, device resident.
+struct DevPrime {
+    uint64_t q;
+    uint64_t qinv;       // q^-1 mod 2^64 (Montgomery)
+    uint64_t r2;         // 2^128 mod q (into Montgomery form)
+    uint64_t ratio_hi;   // floor(2^128 / q), high word (Barrett)
+    uint64_t ratio_lo;   //                   low word
+    uint64_t n_inv;      // N^-1 mod q
+    uint64_t n_inv_sh;   // Shoup companion of n_inv
+    uint64_t one_sh;     // Shoup companion of 1 = floor(2^64 / q)
+};
+
+// Device memory owned through the stream-ordered allocator.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaStream_t s = nullptr;
+    DevBuf() = default;
+    DevBuf(size_t b, cudaStream_t st);
+    ~DevBuf();
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept { *this = std::move(o); }
+    DevBuf &operator=(DevBuf &&o) noexcept;
+    uint64_t *u64() const { return static_cast<uint64_t *>(p); }
+    void reset();
+};
+
+// Basis-conversion constants of one level (ModUp / ModDown / rescale), device resident.
+// ModUp, digit j (source limbs i in I_j = [j*alpha, min((j+1)*alpha, l+1))):
+//   y_i = a_i * qhat_inv_i mod q_i, conv_t = sum_i y_i * qhat_mod[j][i - j*alpha][t] mod t.
+// ModDown: y_k = x_k * phat_inv_k mod p_k, conv_i = sum_k y_k * phat_mod[k][i] mod q_i,
+//   out_i = (x_i - conv_i) * P^-1 mod q_i.
+// Rescale (to l-1): out_i = (c_i - [c_l]_centred) * q_l^-1 mod q_i.
+struct LevelConsts {
+    uint32_t level = 0, dnum = 0, width = 0;  // width = l+1+K
+    DevBuf d;                                  // all tables of this level, packed
+    // offsets (in uint64 words) into d; each table entry is a (value, Shoup) pair
+    size_t off_qhat_inv = 0;   // [l+1] pairs (mod the limb's own prime)
+    size_t off_qhat_mod = 0;   // [dnum][alpha][width] pairs (mod target prime)
+    size_t off_phat_inv = 0;   // [K] pairs
+    size_t off_phat_mod = 0;   // [K][l+1] pairs
+    size_t off_p_inv = 0;      // [l+1] pairs: P^-1 mod q_i
+    size_t off_ql_inv = 0;     // [l] pairs: q_l^-1 mod q_i (rescale from level l)
+    size_t off_nql_half = 0;   // unused
+};
+
+}  // namespace hear
+
+// ------------------------------------------------------------------ handles
+struct hear_context {
+    int device = 0;
+    uint32_t log_n = 0, n = 0, n_q = 0, n_p = 0, L = 0, K = 0, alpha = 0;
+    double default_scale = 0, sigma = 0;
+    std::vector<uint64_t> primes;          // n_q + n_p
+    std::vector<uint64_t> psi;             // primitive 2N-th roots used by the tables
+    std::vector<uint64_t> cdt;             // CDT thresholds
+    cudaStream_t stream = nullptr;         // default stream of the context
+    cudaMemPool_t pool = nullptr;
+    hear::DevBuf d_primes;                 // DevPrime[n_q+n_p]
+    hear::DevBuf d_tw;                     // [4][n_q+n_p][N]: fwd, fwd_sh, inv, inv_sh
+    hear::DevBuf d_cdt;                    // CDT on device
+    std::vector<std::unique_ptr<hear::LevelConsts>> levels;  // per level 0..L
+    bool poisoned = false;
+    const hear::DevPrime *dev_primes() const { return static_cast<const hear::DevPrime *>(d_primes.p); }
+    uint32_t nqp() const { return n_q + n_p; }
+    uint32_t dnum(uint32_t level) const { return (level + 1 + alpha - 1) / alpha; }
+    uint32_t dnum_max() const { return dnum(L); }
+};
+
+struct hear_secret_key {
+    hear_context *ctx = nullptr;
+    std::vector<int8_t> s;         // ternary coefficients
+    hear::DevBuf s_mont;           // s in NTT + Montgomery form over all n_q+n_p primes
+};
+
+struct hear_public_key {
+    hear_context *ctx = nullptr;
+    hear::DevBuf pk_mont;          // [2][n_q][N] NTT + Montgomery form
+};
+
+struct hear_eval_keys {
+    hear_context *ctx = nullptr;
+    // galois element -> [dnum_max][2][n_q+n_p][N] NTT + Montgomery form; 1 = relin
+    std::map<uint32_t, hear::DevBuf> keys;
+    const uint64_t *key(uint32_t g) const {
+        auto it = keys.find(g);
+        return it == keys.end() ? nullptr : it->second.u64();
+    }
+};
+
+struct hear_ciphertext {
+    hear_context *ctx = nullptr;
+    uint32_t level = 0, n_poly = 2;
+    double scale = 1.0;
+    hear::DevBuf d;                // [n_poly][level+1][N], NTT domain
+};
+
+namespace hear {
+
+// ------------------------------------------------------------------ kernels (launchers)
+// Limb maps: limb b of a launch lives in group g = b / per_group at position
+// t = b % per_group, address data + g * group_stride + t * N, and has the prime
+// q_base + t if t < q_count, else the special prime n_q + (t - q_count).
+struct LimbMap {
+    uint32_t per_group = 1;
+    uint32_t q_base = 0;
+    uint32_t q_count = 1;
+    uint32_t n_q = 0;
+    uint64_t group_stride = 0;   // words; 0 = per_group * N
+    uint32_t skip_dnum = 0;      // if nonzero: group g is digit j = g % skip_dnum and limbs
+    uint32_t alpha = 0;          //   t in [j*alpha, (j+1)*alpha) with t < q_count are skipped
+    __host__ __device__ inline bool resolve(uint32_t b, uint32_t *prime) const {
+        uint32_t t = b % per_group;
+        if (skip_dnum) {
+            uint32_t j = (b / per_group) % skip_dnum;
+            if (t >= j * alpha && t < (j + 1) * alpha && t < q_count) return false;
+        }
+        *prime = t < q_count ? q_base + t : n_q + (t - q_count);
+        return true;
+    }
+    __host__ __device__ inline uint64_t offset(uint32_t b, uint32_t n) const {
+        uint32_t g = b / per_group, t = b % per_group;
+        uint64_t gs = group_stride ? group_stride : (uint64_t)per_group * n;
+        return g * gs + (uint64_t)t * n;
+    }
+};
+
+// limbs of polynomials at level l (groups of l+1 limbs q_0..q_l)
+inline LimbMap map_q(uint32_t level, uint32_t n_q) {
+    LimbMap m; m.per_group = level + 1; m.q_count = level + 1; m.n_q = n_q; return m;
+}
+// limbs of polynomials over Q_l u P (groups of l+1+K limbs)
+inline LimbMap map_qp(uint32_t level, uint32_t n_q, uint32_t K) {
+    LimbMap m; m.per_group = level + 1 + K; m.q_count = level + 1; m.n_q = n_q; return m;
+}
+
+void ntt_forward(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, LimbMap map, cudaStream_t s);
+void ntt_inverse(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, LimbMap map, cudaStream_t s);
+
+// The other launchers are declared in kernels.cuh.
+}  // namespace hear

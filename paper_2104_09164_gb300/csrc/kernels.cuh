@@ -1,0 +1,73 @@
+// kernels.cuh -- launchers of the elementwise, sampling and basis-conversion kernels.
+#pragma once
+#include "internal.h"
+
+namespace hear {
+
+enum SmallKind { kTernary = 0, kGauss = 1 };
+
+// ---- representation changes ----
+void to_mont(const hear_context *c, uint64_t *d, uint32_t n_limbs, LimbMap m, cudaStream_t s);
+void from_mont(const hear_context *c, uint64_t *d, uint32_t n_limbs, LimbMap m, cudaStream_t s);
+void small_to_limbs(const hear_context *c, const int8_t *e, uint64_t *out, uint32_t n_limbs, LimbMap m,
+                    cudaStream_t s);
+void i64_to_limbs(const hear_context *c, const int64_t *v, uint64_t *out, uint32_t n_limbs, LimbMap m,
+                  cudaStream_t s);
+
+// ---- ChaCha20 samplers ----
+void sample_small(const hear_context *c, uint64_t seed, uint32_t purpose, uint64_t index, SmallKind kind,
+                  int8_t *out, cudaStream_t s);
+void sample_uniform(const hear_context *c, uint64_t seed, uint32_t purpose, uint64_t index_base,
+                    uint64_t *out, uint32_t n_limbs, LimbMap m, cudaStream_t s);
+
+// ---- key / encryption combines ----
+// pk: b = e - a*s (a, e NTT normal form, s Montgomery)
+void pk_combine(const hear_context *c, const uint64_t *a, const uint64_t *s_mont, const uint64_t *e,
+                uint64_t *b, cudaStream_t st);
+// switching key digit j: b = e - a*s + [t in digit] (P mod q_t) * s'   over all n_q+n_p primes
+void swk_combine(const hear_context *c, const uint64_t *a, const uint64_t *s_mont, const uint64_t *e,
+                 const uint64_t *sp_mont, const uint64_t *p_mod, uint32_t digit, uint64_t *b, cudaStream_t st);
+void encrypt_combine(const hear_context *c, const uint64_t *v, const uint64_t *e0, const uint64_t *e1,
+                     const uint64_t *m, const uint64_t *pk_mont, uint64_t *ct, cudaStream_t st);
+void decrypt_combine(const hear_context *c, uint32_t level, const uint64_t *ct, const uint64_t *s_mont,
+                     uint64_t *out, cudaStream_t st);
+
+// ---- ciphertext arithmetic (NTT domain), batch of n_ct ciphertexts of n_poly polys ----
+void add_ct(const hear_context *c, uint32_t level, uint32_t n_polys_total, const uint64_t *a, const uint64_t *b,
+            uint64_t *out, cudaStream_t st);
+void tensor_ct(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *a, const uint64_t *b,
+               uint64_t *out3, cudaStream_t st);
+// out = sigma_g(in) for n_polys_total polynomials at `level`
+void automorphism(const hear_context *c, uint32_t level, uint32_t n_polys_total, uint32_t galois,
+                  const uint64_t *in, uint64_t *out, cudaStream_t st);
+// BSGS inner sums: for every ciphertext c < n_ct and output j < n_out:
+//   out[j] (batch) = sum_{i < n_in, pt[j*n_in+i] != 0} in[i] (batch) (.) pt[j*n_in+i]
+// in[i], out[j]: device pointers to batches [n_ct][2][level+1][N]; pt: [level+1][N] Montgomery
+void lincomb(const hear_context *c, uint32_t level, uint32_t n_ct, uint32_t n_in, uint32_t n_out,
+             const uint64_t *const *d_in, const uint64_t *const *d_pt, uint64_t *const *d_out, cudaStream_t st);
+// out (batch [n_ct][2][level+1][N]) = ct (batch) (.) pt   (pt Montgomery, no accumulation)
+void mulplain(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *ct, const uint64_t *pt,
+              uint64_t *out, cudaStream_t st);
+
+// ---- key switching ----
+// ext [n_ct][dnum][W][N] from c1 (NTT, [n_ct] polys at stride c1_stride words); tmp: n_ct*(l+1)*N words
+void modup(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *c1, uint64_t c1_stride,
+           uint64_t *ext, uint64_t *tmp, cudaStream_t st);
+// out [n_ct][2][W][N] = sum_j sigma_{g_c}(ext_j) (.) key_c[j]; d_keys[c], d_galois[c] per ciphertext
+void ks_inner(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *ext,
+              const uint64_t *const *d_keys, const uint32_t *d_galois, uint64_t *out, cudaStream_t st);
+// ModDown of acc [n_ct][2][W][N] (destroys its P limbs) into out [n_ct][2][l+1][N], adding
+// addend (ciphertext c at addend + c*add_stride, polys [2][l+1][N], poly p only if add_mask bit p)
+// gathered through sigma_{g_c}
+// (d_galois may be null = identity).  tmp: n_ct*2*(l+1)*N words
+void moddown(const hear_context *c, uint32_t level, uint32_t n_ct, uint64_t *acc, uint64_t *out,
+             const uint64_t *addend, uint64_t add_stride, uint32_t add_mask, const uint32_t *d_galois,
+             uint64_t *tmp, cudaStream_t st);
+// out = a (.) b_mont over n_limbs limbs (Montgomery product: a * b)
+void pointwise_mont(const hear_context *c, uint32_t n_limbs, LimbMap m, const uint64_t *a, const uint64_t *b_mont,
+                    uint64_t *out, cudaStream_t st);
+// rescale batch [n_polys][l+1][N] -> out [n_polys][l][N]; destroys limb l of `in`; tmp n_polys*l*N words
+void rescale(const hear_context *c, uint32_t level, uint32_t n_polys, uint64_t *in, uint64_t *out, uint64_t *tmp,
+             cudaStream_t st);
+
+}  // namespace hear

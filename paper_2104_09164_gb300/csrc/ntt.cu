@@ -1,0 +1,235 @@
+// ntt.cu -- batched negacyclic NTT / inverse NTT over word-size primes on sm_103a.
+//
+// Forward: Cooley-Tukey, natural-order input, bit-reversed output, twiddle table
+// fwd[k] = psi^brv(k) (psi a primitive 2N-th root); output index i holds the evaluation
+// a(psi^(2 brv(i) + 1)).  Inverse: Gentleman-Sande with inv[k] = psi^-brv(k), bit-reversed
+// input, natural output, times N^-1.  The NTT of the input ciphertext limbs is the
+// "NTT conversion" the paper shares across rotations by hoisting (Methods, "Algorithmic
+// and cryptographic optimizations", item (i)).
+//
+// Layout: N = 2^a * 2^b.  Pass A runs stages 0..a-1 on strided sub-problems (column c:
+// elements c + u*2^b, u < 2^a), pass B runs stages a..logN-1 on contiguous blocks of 2^b.
+// A CTA stages a 2048-word tile in shared memory; each thread applies up to three
+// stages at a time to 8 words held in registers (radix-2^3 units), with Harvey lazy
+// butterflies (values kept in [0, 4q) forward and [0, 2q) inverse) and Shoup products by
+// the precomputed twiddle companions.
+#include "internal.h"
+#include "modarith.cuh"
+
+namespace hear {
+namespace {
+
+constexpr int kTile = 2048;      // words per CTA tile (16 KiB)
+constexpr int kThreads = 256;
+
+struct PassArgs {
+    uint64_t *data;
+    uint32_t n_limbs;
+    uint32_t log_n;
+    uint32_t tiles_per_limb;
+    LimbMap map;
+    const DevPrime *primes;
+    const uint64_t *tw;      // twiddle table [n_primes][N]
+    const uint64_t *tw_sh;   // Shoup companions
+    uint32_t n;              // N
+};
+
+// One group of W stages on a tile.  FWD: stages ls0, ls0+1, ...; INV: ls0, ls0-1, ...
+// PASSA: sub-problems are the C columns of an R x C tile (sidx = u*C + c); else they are
+// S contiguous blocks of R words (sidx = sp*R + u).
+template <int LOGR, int W, bool FWD, bool PASSA>
+__device__ __forceinline__ void stage_group(uint64_t *s, int ls0, uint32_t s_off, uint32_t blk_base,
+                                            const uint64_t *__restrict__ tw,
+                                            const uint64_t *__restrict__ tws, uint64_t q) {
+    constexpr int R = 1 << LOGR;
+    constexpr int E = 1 << W;
+    constexpr int NSP = kTile / R;               // sub-problems per tile
+    constexpr int UPS = R >> W;                  // units per sub-problem
+    const int p_lo = FWD ? (LOGR - ls0 - W) : (LOGR - 1 - ls0);
+    const uint64_t two_q = 2 * q;
+    for (int id = threadIdx.x; id < NSP * UPS; id += blockDim.x) {
+        int sp, ub;
+        if (PASSA) { sp = id % NSP; ub = id / NSP; }
+        else       { ub = id % UPS; sp = id / UPS; }
+        const uint32_t lowmask = (1u << p_lo) - 1;
+        const uint32_t u_base = ((ub & ~lowmask) << W) | (ub & lowmask);
+        uint64_t x[E];
+#pragma unroll
+        for (int e = 0; e < E; e++) {
+            uint32_t u = u_base + (e << p_lo);
+            x[e] = s[PASSA ? (u * NSP + sp) : (sp * R + u)];
+        }
+        const uint32_t blk = PASSA ? 0u : (blk_base + sp);
+#pragma unroll
+        for (int i = 0; i < W; i++) {
+            const int ls = FWD ? (ls0 + i) : (ls0 - i);
+            const int half = FWD ? (E >> (i + 1)) : (1 << i);
+#pragma unroll
+            for (int e = 0; e < E; e++) {
+                if (e & half) continue;
+                const uint32_t u = u_base + (e << p_lo);
+                const uint32_t idx = (1u << (s_off + ls)) + (blk << ls) + (u >> (LOGR - ls));
+                const uint64_t w = __ldg(tw + idx), wsh = __ldg(tws + idx);
+                uint64_t X = x[e], Y = x[e + half];
+                if (FWD) {
+                    X = X >= two_q ? X - two_q : X;
+                    uint64_t T = shoup_lazy(Y, w, wsh, q);
+                    x[e] = X + T;
+                    x[e + half] = X - T + two_q;
+                } else {
+                    uint64_t S = X + Y;
+                    x[e] = S >= two_q ? S - two_q : S;
+                    x[e + half] = shoup_lazy(X - Y + two_q, w, wsh, q);
+                }
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < E; e++) {
+            uint32_t u = u_base + (e << p_lo);
+            s[PASSA ? (u * NSP + sp) : (sp * R + u)] = x[e];
+        }
+    }
+}
+
+template <int LOGR, bool FWD, bool PASSA>
+__device__ __forceinline__ void all_groups(uint64_t *s, uint32_t s_off, uint32_t blk_base,
+                                           const uint64_t *tw, const uint64_t *tws, uint64_t q) {
+    constexpr int G3 = LOGR / 3, REM = LOGR % 3;
+#pragma unroll
+    for (int g = 0; g < G3; g++) {
+        const int ls0 = FWD ? 3 * g : LOGR - 1 - 3 * g;
+        stage_group<LOGR, 3, FWD, PASSA>(s, ls0, s_off, blk_base, tw, tws, q);
+        __syncthreads();
+    }
+    if constexpr (REM > 0) {
+        const int ls0 = FWD ? 3 * G3 : REM - 1;
+        stage_group<LOGR, REM, FWD, PASSA>(s, ls0, s_off, blk_base, tw, tws, q);
+        __syncthreads();
+    }
+}
+
+// Pass A: strided columns, stages 0..LOGR-1 (forward) or LOGR-1..0 (inverse, + N^-1).
+template <int LOGR, bool FWD>
+__global__ void __launch_bounds__(kThreads) ntt_pass_a(PassArgs a) {
+    __shared__ uint64_t s[kTile];
+    constexpr int R = 1 << LOGR;
+    constexpr int C = kTile / R;
+    const uint32_t limb = blockIdx.x / a.tiles_per_limb;
+    const uint32_t tile = blockIdx.x % a.tiles_per_limb;
+    uint32_t pi;
+    if (limb >= a.n_limbs || !a.map.resolve(limb, &pi)) return;
+    const DevPrime P = a.primes[pi];
+    uint64_t *g = a.data + a.map.offset(limb, a.n);
+    const uint32_t cols = a.n >> LOGR;
+    const uint32_t c0 = tile * C;
+    for (int i = threadIdx.x; i < kTile; i += blockDim.x) {
+        int u = i / C, c = i % C;
+        s[i] = g[c0 + c + (size_t)u * cols];
+    }
+    __syncthreads();
+    const uint64_t *tw = a.tw + (size_t)pi * a.n, *tws = a.tw_sh + (size_t)pi * a.n;
+    all_groups<LOGR, FWD, true>(s, 0, 0, tw, tws, P.q);
+    for (int i = threadIdx.x; i < kTile; i += blockDim.x) {
+        int u = i / C, c = i % C;
+        uint64_t v = s[i];
+        if (!FWD) {
+            v = shoup_lazy(v, P.n_inv, P.n_inv_sh, P.q);
+            v = v >= P.q ? v - P.q : v;
+        }
+        g[c0 + c + (size_t)u * cols] = v;
+    }
+}
+
+// Pass B: contiguous blocks of R words, stages s_off..s_off+LOGR-1.
+template <int LOGR, bool FWD>
+__global__ void __launch_bounds__(kThreads) ntt_pass_b(PassArgs a, uint32_t s_off) {
+    __shared__ uint64_t s[kTile];
+    constexpr int R = 1 << LOGR;
+    constexpr int S = kTile / R;
+    const uint32_t limb = blockIdx.x / a.tiles_per_limb;
+    const uint32_t tile = blockIdx.x % a.tiles_per_limb;
+    uint32_t pi;
+    if (limb >= a.n_limbs || !a.map.resolve(limb, &pi)) return;
+    const DevPrime P = a.primes[pi];
+    uint64_t *g = a.data + a.map.offset(limb, a.n) + (size_t)tile * kTile;
+    for (int i = threadIdx.x; i < kTile / 2; i += blockDim.x) {
+        reinterpret_cast<ulonglong2 *>(s)[i] = reinterpret_cast<const ulonglong2 *>(g)[i];
+    }
+    __syncthreads();
+    const uint64_t *tw = a.tw + (size_t)pi * a.n, *tws = a.tw_sh + (size_t)pi * a.n;
+    all_groups<LOGR, FWD, false>(s, s_off, tile * S, tw, tws, P.q);
+    const uint64_t q = P.q, two_q = 2 * q;
+    for (int i = threadIdx.x; i < kTile / 2; i += blockDim.x) {
+        ulonglong2 v = reinterpret_cast<ulonglong2 *>(s)[i];
+        if (FWD) {
+            v.x = v.x >= two_q ? v.x - two_q : v.x;
+            v.x = v.x >= q ? v.x - q : v.x;
+            v.y = v.y >= two_q ? v.y - two_q : v.y;
+            v.y = v.y >= q ? v.y - q : v.y;
+        }
+        reinterpret_cast<ulonglong2 *>(g)[i] = v;
+    }
+}
+
+template <int A, int B>
+void launch_fwd(const PassArgs &a, cudaStream_t st) {
+    dim3 grid(a.n_limbs * a.tiles_per_limb);
+    ntt_pass_a<A, true><<<grid, kThreads, 0, st>>>(a);
+    ntt_pass_b<B, true><<<grid, kThreads, 0, st>>>(a, A);
+}
+template <int A, int B>
+void launch_inv(const PassArgs &a, cudaStream_t st) {
+    dim3 grid(a.n_limbs * a.tiles_per_limb);
+    ntt_pass_b<B, false><<<grid, kThreads, 0, st>>>(a, A);
+    ntt_pass_a<A, false><<<grid, kThreads, 0, st>>>(a);
+}
+
+PassArgs make_args(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, LimbMap map, bool fwd) {
+    PassArgs a;
+    a.data = data;
+    a.n_limbs = n_limbs;
+    a.log_n = ctx->log_n;
+    a.n = ctx->n;
+    a.tiles_per_limb = ctx->n / kTile;
+    a.map = map;
+    a.primes = ctx->dev_primes();
+    const size_t plane = (size_t)ctx->nqp() * ctx->n;
+    const uint64_t *base = ctx->d_tw.u64();
+    a.tw = base + (fwd ? 0 : 2 * plane);
+    a.tw_sh = base + (fwd ? plane : 3 * plane);
+    return a;
+}
+
+}  // namespace
+
+void ntt_forward(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, LimbMap map, cudaStream_t s) {
+    if (n_limbs == 0) return;
+    PassArgs a = make_args(ctx, data, n_limbs, map, true);
+    switch (ctx->log_n) {
+    case 11: launch_fwd<6, 5>(a, s); break;
+    case 12: launch_fwd<6, 6>(a, s); break;
+    case 13: launch_fwd<7, 6>(a, s); break;
+    case 14: launch_fwd<7, 7>(a, s); break;
+    case 15: launch_fwd<8, 7>(a, s); break;
+    case 16: launch_fwd<8, 8>(a, s); break;
+    default: throw Error(HEAR_E_UNSUPPORTED, "log_n outside [11, 16]");
+    }
+    HEAR_CHECK_CUDA(cudaGetLastError());
+}
+
+void ntt_inverse(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, LimbMap map, cudaStream_t s) {
+    if (n_limbs == 0) return;
+    PassArgs a = make_args(ctx, data, n_limbs, map, false);
+    switch (ctx->log_n) {
+    case 11: launch_inv<6, 5>(a, s); break;
+    case 12: launch_inv<6, 6>(a, s); break;
+    case 13: launch_inv<7, 6>(a, s); break;
+    case 14: launch_inv<7, 7>(a, s); break;
+    case 15: launch_inv<8, 7>(a, s); break;
+    case 16: launch_inv<8, 8>(a, s); break;
+    default: throw Error(HEAR_E_UNSUPPORTED, "log_n outside [11, 16]");
+    }
+    HEAR_CHECK_CUDA(cudaGetLastError());
+}
+
+}  // namespace hear

@@ -1,0 +1,364 @@
+"""Python binding of the C ABI in include/hear.h (argument marshalling only).
+
+Every function has the name of the C entry point it calls.  All ring arithmetic runs in
+the CUDA library ``libhear.so``; if it cannot be loaded the import of this module fails --
+there is no CPU fallback.  Handles are opaque integers; release them with the matching
+``*_destroy`` call.  ``stream`` arguments accept None (the context's stream), an integer
+cudaStream_t, or any object with a ``cuda_stream`` attribute (e.g. ``torch.cuda.Stream``).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhear.so")
+
+HEAR_LAYER_FC = 1
+HEAR_LAYER_SQUARE = 2
+HEAR_LAYER_FC_SQ_FC = 3
+
+_vp = ctypes.c_void_p
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_i8p = ctypes.POINTER(ctypes.c_int8)
+_dp = ctypes.POINTER(ctypes.c_double)
+_szp = ctypes.POINTER(ctypes.c_size_t)
+
+
+class hear_params_desc(ctypes.Structure):
+    _fields_ = [("log_n", ctypes.c_uint32), ("n_q", ctypes.c_uint32), ("q_bits", _u32p),
+                ("n_p", ctypes.c_uint32), ("p_bits", _u32p), ("log2_scale", ctypes.c_double),
+                ("sigma", ctypes.c_double)]
+
+
+class hear_layer_desc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_uint32), ("d_out", ctypes.c_uint32), ("d_in", ctypes.c_uint32),
+                ("w", _dp), ("bias", _dp), ("d_out2", ctypes.c_uint32), ("w2", _dp)]
+
+
+class HearError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("hear error %d: %s" % (code, msg))
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libhear.so is not built (run paper_2104_09164_gb300/build.py); "
+                          "there is no CPU fallback")
+    L = ctypes.CDLL(LIB_PATH)
+    st = ctypes.c_int
+    sig = {
+        "hear_last_error": (ctypes.c_char_p, []),
+        "hear_context_create": (st, [ctypes.POINTER(hear_params_desc), ctypes.c_int, ctypes.POINTER(_vp)]),
+        "hear_context_destroy": (None, [_vp]),
+        "hear_context_primes": (st, [_vp, _u64p, ctypes.c_size_t, _szp]),
+        "hear_context_cdt": (st, [_vp, _u64p, ctypes.c_size_t, _szp]),
+        "hear_keygen": (st, [_vp, ctypes.c_uint64, _i32p, ctypes.c_size_t, ctypes.POINTER(_vp),
+                             ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
+        "hear_secret_key_destroy": (None, [_vp]),
+        "hear_public_key_destroy": (None, [_vp]),
+        "hear_eval_keys_destroy": (None, [_vp]),
+        "hear_secret_key_export": (st, [_vp, _i8p, ctypes.c_size_t, _szp]),
+        "hear_public_key_export": (st, [_vp, _u64p, ctypes.c_size_t, _szp]),
+        "hear_eval_key_export": (st, [_vp, ctypes.c_uint32, _u64p, ctypes.c_size_t, _szp]),
+        "hear_encode": (st, [_vp, _dp, ctypes.c_size_t, ctypes.c_double, _i64p, ctypes.c_size_t, _szp]),
+        "hear_encrypt": (st, [_vp, _vp, _dp, ctypes.c_size_t, ctypes.c_double, ctypes.c_uint64,
+                              ctypes.c_uint64, ctypes.POINTER(_vp), _vp]),
+        "hear_encrypt_clips": (st, [_vp, _vp, _dp, ctypes.c_size_t, ctypes.c_size_t, ctypes.c_uint64,
+                                    ctypes.c_uint64, ctypes.POINTER(_vp), _vp]),
+        "hear_decrypt": (st, [_vp, _vp, _vp, _dp, ctypes.c_size_t, _szp]),
+        "hear_ciphertext_destroy": (None, [_vp]),
+        "hear_ciphertext_info": (st, [_vp, _u32p, _u32p, _dp]),
+        "hear_ciphertext_export": (st, [_vp, _u64p, ctypes.c_size_t, _szp]),
+        "hear_ciphertext_import": (st, [_vp, _u64p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_uint32,
+                                        ctypes.c_double, ctypes.POINTER(_vp), _vp]),
+        "hear_rotate": (st, [_vp, _vp, ctypes.c_int32, ctypes.POINTER(_vp), _vp]),
+        "hear_rotate_hoisted": (st, [_vp, _vp, _i32p, ctypes.c_size_t, ctypes.POINTER(_vp), _vp]),
+        "hear_rescale": (st, [_vp, ctypes.POINTER(_vp), _vp]),
+        "hear_add": (st, [_vp, _vp, ctypes.POINTER(_vp), _vp]),
+        "hear_mulplain": (st, [_vp, _dp, ctypes.c_size_t, ctypes.c_double, ctypes.POINTER(_vp), _vp]),
+        "hear_multiply_relin": (st, [_vp, _vp, _vp, ctypes.POINTER(_vp), _vp]),
+        "hear_model_create": (st, [_vp, ctypes.POINTER(hear_layer_desc), ctypes.c_size_t, ctypes.c_uint32,
+                                   ctypes.POINTER(_vp)]),
+        "hear_model_destroy": (None, [_vp]),
+        "hear_model_rotations": (st, [_vp, _i32p, ctypes.c_size_t, _szp]),
+        "hear_model_output_positions": (st, [_vp, _u32p, ctypes.c_size_t, _szp]),
+        "hear_evaluate": (st, [_vp, _vp, ctypes.POINTER(_vp), ctypes.c_size_t, ctypes.POINTER(_vp), _vp]),
+        "hear_evaluate_layer": (st, [_vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp), ctypes.c_size_t,
+                                     ctypes.POINTER(_vp), _vp]),
+        "hear_evaluate_host": (st, [_vp, _vp, _u64p, ctypes.c_size_t, ctypes.c_double, _u64p, ctypes.c_size_t,
+                                    _szp, _u32p, _dp, _vp]),
+        "hear_dbg_poly_mul": (st, [_vp, ctypes.c_uint32, _u64p, _u64p, _u64p]),
+        "hear_dbg_ntt_roundtrip": (st, [_vp, _u64p, ctypes.c_size_t]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+lib = _load()
+
+
+def _check(rc):
+    if rc != 0:
+        raise HearError(rc, lib.hear_last_error().decode(errors="replace"))
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return _vp(s.cuda_stream)
+    return _vp(int(s))
+
+
+def _arr(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t)
+
+
+# ---------------------------------------------------------------- context
+def hear_context_create(log_n, q_bits, p_bits, log2_scale=40.0, sigma=3.2, device=0):
+    qb = _arr(q_bits, np.uint32)
+    pb = _arr(p_bits, np.uint32)
+    d = hear_params_desc(log_n, len(qb), _p(qb, _u32p), len(pb), _p(pb, _u32p), float(log2_scale), float(sigma))
+    h = _vp()
+    _check(lib.hear_context_create(ctypes.byref(d), int(device), ctypes.byref(h)))
+    return h.value
+
+
+def hear_context_destroy(ctx):
+    lib.hear_context_destroy(ctx)
+
+
+def _vec_out(fn, handle, dtype, ptr_t, *pre):
+    n = ctypes.c_size_t(0)
+    fn(handle, *pre, None, 0, ctypes.byref(n))
+    out = np.empty(n.value, dtype=dtype)
+    _check(fn(handle, *pre, _p(out, ptr_t), n.value, ctypes.byref(n)))
+    return out
+
+
+def hear_context_primes(ctx):
+    return [int(x) for x in _vec_out(lib.hear_context_primes, ctx, np.uint64, _u64p)]
+
+
+def hear_context_cdt(ctx):
+    return [int(x) for x in _vec_out(lib.hear_context_cdt, ctx, np.uint64, _u64p)]
+
+
+# ---------------------------------------------------------------- keys
+def hear_keygen(ctx, seed, rot_steps=()):
+    steps = _arr(list(rot_steps), np.int32)
+    sk, pk, evk = _vp(), _vp(), _vp()
+    _check(lib.hear_keygen(ctx, int(seed), _p(steps, _i32p) if len(steps) else None, len(steps),
+                           ctypes.byref(sk), ctypes.byref(pk), ctypes.byref(evk)))
+    return sk.value, pk.value, evk.value
+
+
+def hear_secret_key_destroy(h):
+    lib.hear_secret_key_destroy(h)
+
+
+def hear_public_key_destroy(h):
+    lib.hear_public_key_destroy(h)
+
+
+def hear_eval_keys_destroy(h):
+    lib.hear_eval_keys_destroy(h)
+
+
+def hear_secret_key_export(sk):
+    return _vec_out(lib.hear_secret_key_export, sk, np.int8, _i8p)
+
+
+def hear_public_key_export(pk):
+    return _vec_out(lib.hear_public_key_export, pk, np.uint64, _u64p)
+
+
+def hear_eval_key_export(evk, galois):
+    return _vec_out(lib.hear_eval_key_export, evk, np.uint64, _u64p, ctypes.c_uint32(galois))
+
+
+# ---------------------------------------------------------------- encoding / encryption
+def hear_encode(ctx, z, scale):
+    z = _arr(z, np.float64)
+    n = ctypes.c_size_t(0)
+    out = np.empty(2 * len(z), dtype=np.int64)
+    _check(lib.hear_encode(ctx, _p(z, _dp), len(z), float(scale), _p(out, _i64p), len(out), ctypes.byref(n)))
+    return out
+
+
+def hear_encrypt(ctx, pk, z, scale, seed, ct_id, stream=None):
+    z = _arr(z, np.float64)
+    h = _vp()
+    _check(lib.hear_encrypt(ctx, pk, _p(z, _dp), len(z), float(scale), int(seed), int(ct_id), ctypes.byref(h),
+                            _stream(stream)))
+    return h.value
+
+
+def hear_encrypt_clips(ctx, pk, clips, seed, ct_id, stream=None):
+    c = _arr(np.atleast_2d(clips), np.float64)
+    h = _vp()
+    _check(lib.hear_encrypt_clips(ctx, pk, _p(c, _dp), c.shape[0], c.shape[1], int(seed), int(ct_id),
+                                  ctypes.byref(h), _stream(stream)))
+    return h.value
+
+
+def hear_decrypt(ctx, sk, ct):
+    n = ctypes.c_size_t(0)
+    lib.hear_decrypt(ctx, sk, ct, None, 0, ctypes.byref(n))
+    out = np.empty(n.value, dtype=np.float64)
+    _check(lib.hear_decrypt(ctx, sk, ct, _p(out, _dp), n.value, ctypes.byref(n)))
+    return out
+
+
+def hear_ciphertext_destroy(ct):
+    lib.hear_ciphertext_destroy(ct)
+
+
+def hear_ciphertext_info(ct):
+    lv, npl, sc = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_double()
+    _check(lib.hear_ciphertext_info(ct, ctypes.byref(lv), ctypes.byref(npl), ctypes.byref(sc)))
+    return lv.value, npl.value, sc.value
+
+
+def hear_ciphertext_export(ct):
+    lv, npl, _ = hear_ciphertext_info(ct)
+    flat = _vec_out(lib.hear_ciphertext_export, ct, np.uint64, _u64p)
+    return flat.reshape(npl, lv + 1, -1)
+
+
+def hear_ciphertext_import(ctx, words, level, n_poly, scale, stream=None):
+    w = _arr(words, np.uint64).reshape(-1)
+    h = _vp()
+    _check(lib.hear_ciphertext_import(ctx, _p(w, _u64p), w.size, int(level), int(n_poly), float(scale),
+                                      ctypes.byref(h), _stream(stream)))
+    return h.value
+
+
+# ---------------------------------------------------------------- primitive operations
+def hear_rotate(evk, ct, step, stream=None):
+    h = _vp()
+    _check(lib.hear_rotate(evk, ct, int(step), ctypes.byref(h), _stream(stream)))
+    return h.value
+
+
+def hear_rotate_hoisted(evk, ct, steps, stream=None):
+    s = _arr(list(steps), np.int32)
+    outs = (_vp * len(s))()
+    _check(lib.hear_rotate_hoisted(evk, ct, _p(s, _i32p), len(s), outs, _stream(stream)))
+    return [o for o in outs]
+
+
+def hear_rescale(ct, stream=None):
+    h = _vp()
+    _check(lib.hear_rescale(ct, ctypes.byref(h), _stream(stream)))
+    return h.value
+
+
+def hear_add(a, b, stream=None):
+    h = _vp()
+    _check(lib.hear_add(a, b, ctypes.byref(h), _stream(stream)))
+    return h.value
+
+
+def hear_mulplain(ct, z, pt_scale, stream=None):
+    z = _arr(z, np.float64)
+    h = _vp()
+    _check(lib.hear_mulplain(ct, _p(z, _dp), len(z), float(pt_scale), ctypes.byref(h), _stream(stream)))
+    return h.value
+
+
+def hear_multiply_relin(evk, a, b, stream=None):
+    h = _vp()
+    _check(lib.hear_multiply_relin(evk, a, b, ctypes.byref(h), _stream(stream)))
+    return h.value
+
+
+# ---------------------------------------------------------------- network
+def hear_model_create(ctx, layers, clip_dim):
+    """layers: sequence of ("fc", W) | ("square",) | ("fc_sq_fc", W1, W2) with float64 matrices"""
+    descs = (hear_layer_desc * len(layers))()
+    keep = []
+    for i, layer in enumerate(layers):
+        d = descs[i]
+        if layer[0] == "fc":
+            W = _arr(layer[1], np.float64)
+            keep.append(W)
+            d.kind, d.d_out, d.d_in, d.w = HEAR_LAYER_FC, W.shape[0], W.shape[1], _p(W, _dp)
+        elif layer[0] == "square":
+            d.kind = HEAR_LAYER_SQUARE
+        elif layer[0] == "fc_sq_fc":
+            W1, W2 = _arr(layer[1], np.float64), _arr(layer[2], np.float64)
+            keep += [W1, W2]
+            d.kind, d.d_out, d.d_in, d.w = HEAR_LAYER_FC_SQ_FC, W1.shape[0], W1.shape[1], _p(W1, _dp)
+            d.d_out2, d.w2 = W2.shape[0], _p(W2, _dp)
+        else:
+            raise ValueError(layer[0])
+    h = _vp()
+    _check(lib.hear_model_create(ctx, descs, len(layers), int(clip_dim), ctypes.byref(h)))
+    return h.value
+
+
+def hear_model_destroy(m):
+    lib.hear_model_destroy(m)
+
+
+def hear_model_rotations(m):
+    return [int(x) for x in _vec_out(lib.hear_model_rotations, m, np.int32, _i32p)]
+
+
+def hear_model_output_positions(m):
+    return [int(x) for x in _vec_out(lib.hear_model_output_positions, m, np.uint32, _u32p)]
+
+
+def hear_evaluate(m, evk, cts, stream=None):
+    ins = (_vp * len(cts))(*cts)
+    outs = (_vp * len(cts))()
+    _check(lib.hear_evaluate(m, evk, ins, len(cts), outs, _stream(stream)))
+    return [o for o in outs]
+
+
+def hear_evaluate_layer(m, layer, evk, cts, stream=None):
+    ins = (_vp * len(cts))(*cts)
+    outs = (_vp * len(cts))()
+    _check(lib.hear_evaluate_layer(m, int(layer), evk, ins, len(cts), outs, _stream(stream)))
+    return [o for o in outs]
+
+
+def hear_evaluate_host(m, evk, in_words, n_ct, scale, out=None, stream=None):
+    w = _arr(in_words, np.uint64).reshape(-1)
+    n = ctypes.c_size_t(0)
+    lv, sc = ctypes.c_uint32(), ctypes.c_double()
+    if out is None:
+        lib.hear_evaluate_host(m, evk, _p(w, _u64p), int(n_ct), float(scale), None, 0, ctypes.byref(n),
+                               None, None, None)
+        out = np.empty(n.value, dtype=np.uint64)
+    _check(lib.hear_evaluate_host(m, evk, _p(w, _u64p), int(n_ct), float(scale), _p(out, _u64p), out.size,
+                                  ctypes.byref(n), ctypes.byref(lv), ctypes.byref(sc), _stream(stream)))
+    return out, lv.value, sc.value
+
+
+# ---------------------------------------------------------------- debug
+def hear_dbg_poly_mul(ctx, prime, a, b):
+    a, b = _arr(a, np.uint64), _arr(b, np.uint64)
+    out = np.empty_like(a)
+    _check(lib.hear_dbg_poly_mul(ctx, int(prime), _p(a, _u64p), _p(b, _u64p), _p(out, _u64p)))
+    return out
+
+
+def hear_dbg_ntt_roundtrip(ctx, limbs):
+    """limbs: [n_limb][N]; limb i uses prime i mod (n_q + n_p)"""
+    x = _arr(limbs, np.uint64).copy()
+    _check(lib.hear_dbg_ntt_roundtrip(ctx, _p(x, _u64p), x.shape[0]))
+    return x
