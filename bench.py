@@ -1,0 +1,385 @@
+"""Encrypted-inference benchmark: RNS-CKKS evaluation of the fall-detection networks on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload small|large|toy]
+                    [--impl hear|reference] [--no-batched] [--no-cpu-baseline]
+
+One step = one pass of the whole hot path (every layer of the encrypted network) over one
+batch of ciphertexts already resident in HBM:
+  * small (default, the quoted configuration): N = 2^14, 60 + 7x40-bit ciphertext primes,
+    one 60-bit special prime, one clip of 16x128 features per ciphertext, FC 2048->128 ->
+    x^2 -> FC 128->2, batch 1 (one request);
+  * large: N = 2^15, 60 + 14x40-bit primes, two 60-bit special primes, 256 clips packed
+    8 per ciphertext (32 ciphertexts in one batch), FC 2048->512 -> x^2 -> FC 512->128 ->
+    x^2 -> FC 128->2.
+Unless --no-batched, the JSON line also carries the batched large network as "batched".
+Rank 0 prints one JSON line.  Under torchrun every rank evaluates its own replica (no
+collective on the data path; weak scaling) and the slowest rank's time is reported.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "encrypted inferences/s & p50/p99 latency (N=2^14/2^15), batched vs plain on GB300"
+UNIT = "inferences/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="small", choices=["small", "large", "toy"])
+    ap.add_argument("--impl", default="hear", choices=["hear", "reference"])
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def describe(w):
+    nets = {"toy": "FC 64->16 -> x^2 -> FC 16->2 (collapsed)", "small": "FC 2048->128 -> x^2 -> FC 128->2",
+            "large": "FC 2048->512 -> x^2 -> FC 512->128 -> x^2 -> FC 128->2"}
+    qb = "%d+%dx%d" % (w.q_bits[0], len(w.q_bits) - 1, w.q_bits[1])
+    return ("%s: RNS-CKKS N=2^%d, q=%s bits, p=%s bits, scale 2^40, %s, %d clip(s) of %d features, "
+            "%d clips per ciphertext, %d ciphertext(s) per batch" %
+            (w.name, w.log_n, qb, "+".join(map(str, w.p_bits)), nets[w.name], w.n_clips, w.clip_dim,
+             min(w.clips_per_ct, w.n_clips), w.n_ct))
+
+
+# ------------------------------------------------------------------ distributed plumbing
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(self.local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", self.local))
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x):
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.th.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if len(r) > 5 + i and r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------ peaks
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ oracle CPU timing
+def oracle_sample(w, steps_keys, seconds_budget=25.0):
+    """Time the CPU oracle (as it stands) evaluating whole ciphertexts of the workload.
+    Returns (inferences/s, cores, description)."""
+    from oracle import oracle as O
+    o = O.Oracle(w.log_n, w.q_bits, w.p_bits, w.sigma)
+    cores = O.lib().or_set_threads(0)
+    z, k = O.pack_clips(w.ct_clips(0), w.slots)
+    keys = o.keygen(301, [O.galois_for_step(s, o.n) for s in steps_keys])
+    ct = o.encrypt(keys.pk, z, 401, 0, 2.0 ** w.log2_scale)
+    clips = min(w.clips_per_ct, w.n_clips)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        o.evaluate(w.layers, ct, k, keys)
+        n += 1
+        el = time.perf_counter() - t0
+        if el > seconds_budget or n >= 3:
+            break
+    return n * clips / el, cores, "%d whole ciphertext evaluation(s) of %d clip(s) each, %.1f s" % (n, clips, el)
+
+
+# ------------------------------------------------------------------ GPU arm
+class Setup:
+    def __init__(self, H, w, stream, device):
+        from oracle.oracle import pack_clips  # noqa: F401  (packing rule is also in hear_encrypt_clips)
+        self.H, self.w = H, w
+        self.ctx = H.hear_context_create(w.log_n, w.q_bits, w.p_bits, w.log2_scale, w.sigma, device)
+        self.model = H.hear_model_create(self.ctx, w.layers, w.clip_dim)
+        self.steps = H.hear_model_rotations(self.model)
+        self.sk, self.pk, self.evk = H.hear_keygen(self.ctx, 301, self.steps)
+        self.cts = [H.hear_encrypt_clips(self.ctx, self.pk, w.ct_clips(i), 401, i, stream) for i in range(w.n_ct)]
+        self.clips_per_step = w.n_clips
+
+    def step(self, stream):
+        outs = self.H.hear_evaluate(self.model, self.evk, self.cts, stream)
+        return outs
+
+    def close(self):
+        H = self.H
+        for c in self.cts:
+            H.hear_ciphertext_destroy(c)
+        H.hear_model_destroy(self.model)
+        H.hear_eval_keys_destroy(self.evk)
+        H.hear_public_key_destroy(self.pk)
+        H.hear_secret_key_destroy(self.sk)
+        H.hear_context_destroy(self.ctx)
+
+
+def run_gpu(S, steps, warmup, dist, torch, stream, sampler_device):
+    H = S.H
+    for _ in range(warmup):
+        for o in S.step(stream):
+            H.hear_ciphertext_destroy(o)
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    launches0 = H.hear_launch_count()
+    with ClockSampler(sampler_device) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(steps):
+            ev[i][0].record(stream)
+            outs = S.step(stream)
+            ev[i][1].record(stream)
+            for o in outs:
+                H.hear_ciphertext_destroy(o)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    launches = H.hear_launch_count() - launches0
+    dist.barrier()
+    torch.cuda.synchronize()
+    total_ms = t_start.elapsed_time(t_end)
+    lat = sorted(a.elapsed_time(b) for a, b in ev)
+    return total_ms, lat, launches, clk.summary()
+
+
+def profile_stages(S, stream, torch, steps=2):
+    H = S.H
+    H.hear_profile_begin(S.ctx)
+    for _ in range(steps):
+        for o in S.step(stream):
+            H.hear_ciphertext_destroy(o)
+    torch.cuda.synchronize()
+    return H.hear_profile_end(S.ctx), steps
+
+
+def run_e2e(S, steps, warmup, torch, stream):
+    """through hear_evaluate_host: H2D of the coefficient-domain inputs from pinned host
+    memory, evaluation, D2H of the result ciphertexts -- every step"""
+    H, w = S.H, S.w
+    words = np.concatenate([H.hear_ciphertext_export(c).reshape(-1) for c in S.cts])
+    pin_in = torch.empty(words.size, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+    pin_in[:] = words
+    out0, lv, sc = H.hear_evaluate_host(S.model, S.evk, pin_in, len(S.cts), 2.0 ** w.log2_scale, None, stream)
+    pin_out = torch.empty(out0.size, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+    for _ in range(warmup):
+        H.hear_evaluate_host(S.model, S.evk, pin_in, len(S.cts), 2.0 ** w.log2_scale, pin_out, stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        H.hear_evaluate_host(S.model, S.evk, pin_in, len(S.cts), 2.0 ** w.log2_scale, pin_out, stream)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    return el, pin_in.nbytes, pin_out.nbytes
+
+
+def main_gpu(a):
+    import torch
+    dist = Dist()
+    device = dist.local if dist.world > 1 else 0
+    torch.cuda.set_device(device)
+    from paper_2104_09164_gb300.build import build
+    build()
+    from paper_2104_09164_gb300 import hear as H
+    from paper_2104_09164_gb300.workloads import make_workload
+    stream = torch.cuda.Stream(device=device)
+    w = make_workload(a.workload)
+    S = Setup(H, w, stream, device)
+    total_ms, lat, launches, clocks = run_gpu(S, a.steps, a.warmup, dist, torch, stream, device)
+    total_ms = dist.max(total_ms)
+    value = dist.world * a.steps * S.clips_per_step / (total_ms / 1e3)
+    stages, psteps = profile_stages(S, stream, torch)
+    e2e_s, bi, bo = run_e2e(S, max(3, a.steps // 2), 1, torch, stream)
+    e2e_value = dist.world * max(3, a.steps // 2) * S.clips_per_step / dist.max(e2e_s)
+    result = None
+    if dist.rank == 0:
+        hbm, how = peaks()
+        # dominant stage by device time
+        top = max(stages.items(), key=lambda kv: kv[1][1])
+        name, (nl, ms, byts) = top
+        ntt = {k: v for k, v in stages.items() if k.startswith("ntt")}
+        nl_ntt = sum(v[0] for v in ntt.values())
+        ms_ntt = sum(v[1] for v in ntt.values())
+        by_ntt = sum(v[2] for v in ntt.values())
+        achieved = byts / (ms / 1e3) / 1e9
+        total_stage_ms = sum(v[1] for v in stages.values())
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": describe(w), "parallelism": "replicas" if dist.world > 1 else "single",
+                       "l2": "no flush: the per-step working set (switching keys %.0f MB plus plaintext "
+                             "diagonals) is larger than the 129 MB L2" % _key_mb(w, len(S.steps))},
+            "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
+            "roofline": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "peak_kind": how, "traffic": None,
+                         "launches_per_step": nl / psteps, "stage_share": ms / total_stage_ms},
+            "ntt": {"achieved_gbs": by_ntt / (ms_ntt / 1e3) / 1e9 if ms_ntt else None,
+                    "launches_per_step": nl_ntt / psteps, "share": ms_ntt / total_stage_ms},
+            "stages_ms_per_step": {k: v[1] / psteps for k, v in sorted(stages.items(), key=lambda kv: -kv[1][1])},
+            "clocks": clocks, "gpu_launches": launches,
+        }
+    if not a.no_batched and a.workload == "small":
+        S.close()
+        wl = make_workload("large")
+        SL = Setup(H, wl, stream, device)
+        bsteps = max(3, a.steps // 4)
+        tms, blat, bl, bclk = run_gpu(SL, bsteps, 2, dist, torch, stream, device)
+        tms = dist.max(tms)
+        bst, bps = profile_stages(SL, stream, torch, 1)
+        if result is not None:
+            result["batched"] = {"workload": describe(wl), "value": dist.world * bsteps * SL.clips_per_step / (tms / 1e3),
+                                 "unit": UNIT, "ms_per_step": tms / bsteps, "steps": bsteps,
+                                 "p50_ms": blat[len(blat) // 2], "gpu_launches": bl, "clocks": bclk,
+                                 "stages_ms_per_step": {k: v[1] / bps for k, v in
+                                                        sorted(bst.items(), key=lambda kv: -kv[1][1])[:8]}}
+            result["batched"]["vs_plain"] = result["batched"]["value"] / result["value"]
+        SL.close()
+    else:
+        S.close()
+    if result is not None and not a.no_cpu_baseline and dist.world == 1:
+        v, cores, desc = oracle_sample(w, H_steps_for(w))
+        result["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+    if result is not None:
+        print(json.dumps(result), flush=True)
+    dist.close()
+
+
+def _key_mb(w, n_rot):
+    n = 1 << w.log_n
+    nq, npp = len(w.q_bits), len(w.p_bits)
+    dnum = (nq + npp - 1) // npp
+    return (n_rot + 1) * dnum * 2 * (nq + npp) * n * 8 / 1e6
+
+
+def H_steps_for(w):
+    from oracle import oracle as O
+    k = w.slots // w.clip_dim
+    return O.rotation_steps(w.layers, w.clip_dim, k)
+
+
+def main_reference(a):
+    """The oracle on the host cores, same metric and workload, each step one whole
+    ciphertext of the workload (bounded sample)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2104_09164_gb300.workloads import make_workload
+    from oracle import oracle as O
+    w = make_workload(a.workload)
+    o = O.Oracle(w.log_n, w.q_bits, w.p_bits, w.sigma)
+    cores = O.lib().or_set_threads(0)
+    z, k = O.pack_clips(w.ct_clips(0), w.slots)
+    steps = O.rotation_steps(w.layers, w.clip_dim, k)
+    keys = o.keygen(301, [O.galois_for_step(s, o.n) for s in steps])
+    ct = o.encrypt(keys.pk, z, 401, 0, 2.0 ** w.log2_scale)
+    clips = min(w.clips_per_ct, w.n_clips)
+    for _ in range(a.warmup):
+        o.evaluate(w.layers, ct, k, keys)
+    lat = []
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        t1 = time.perf_counter()
+        o.evaluate(w.layers, ct, k, keys)
+        lat.append((time.perf_counter() - t1) * 1e3)
+    el = time.perf_counter() - t0
+    value = a.steps * clips / el
+    lat.sort()
+    desc = "one ciphertext (%d clip(s)) of the %s workload per step" % (clips, w.name)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": el * 1e3 / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": describe(w)}, "p50_ms": lat[len(lat) // 2],
+        "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+if __name__ == "__main__":
+    args = parse()
+    if args.impl == "reference":
+        main_reference(args)
+    else:
+        main_gpu(args)

@@ -187,6 +187,23 @@ hear_status hear_evaluate_host(const hear_model *m, const hear_eval_keys *evk, c
                                size_t n_ct, double scale, uint64_t *out_words, size_t cap, size_t *n,
                                uint32_t *level_out, double *scale_out, void *stream);
 
+/* ---- tracing: CUDA-event stage profiler and launch counter ---- */
+/* One entry per stage (kernel name): how many kernel launches it made, their summed
+ * device time (CUDA events recorded on the launching stream around each launch) and
+ * the algorithmic HBM bytes they move (each residue read or written once). */
+typedef struct hear_profile_entry {
+    char name[48];
+    uint64_t launches;
+    double total_ms;
+    double bytes;
+} hear_profile_entry;
+/* start recording every launch of this context (clears earlier records) */
+hear_status hear_profile_begin(hear_context *ctx);
+/* wait for the recorded launches, aggregate them per stage and stop recording */
+hear_status hear_profile_end(hear_context *ctx, hear_profile_entry *out, size_t cap, size_t *n);
+/* kernel launches issued by the library (all contexts) since it was loaded */
+uint64_t hear_launch_count(void);
+
 /* ---- debug: ring products through the NTT kernels (tests only) ---- */
 /* out = a * b in Z_q[X]/(X^N+1) for limb prime index `prime` (0..n_q+n_p-1), coefficient domain */
 hear_status hear_dbg_poly_mul(hear_context *ctx, uint32_t prime, const uint64_t *a, const uint64_t *b,

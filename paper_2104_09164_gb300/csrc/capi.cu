@@ -2,6 +2,8 @@
 // handle management.  No C++ exception crosses it.
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include "ckks.h"
 
@@ -446,6 +448,46 @@ hear_status hear_evaluate_host(const hear_model *m, const hear_eval_keys *evk, c
         if (scale_out) *scale_out = sout;
     });
 }
+
+hear_status hear_profile_begin(hear_context *ctx) {
+    if (!ctx) return fail(HEAR_E_INVAL, "null context");
+    return guard(ctx, [&] {
+        std::lock_guard<std::mutex> g(ctx->prof.mu);
+        ctx->prof.clear();
+        ctx->prof.on = true;
+    });
+}
+
+hear_status hear_profile_end(hear_context *ctx, hear_profile_entry *out, size_t cap, size_t *n) {
+    if (!ctx) return fail(HEAR_E_INVAL, "null context");
+    std::vector<hear_profile_entry> agg;
+    hear_status s = guard(ctx, [&] {
+        std::lock_guard<std::mutex> g(ctx->prof.mu);
+        ctx->prof.on = false;
+        std::map<std::string, size_t> idx;
+        for (auto &r : ctx->prof.recs) {
+            HEAR_CHECK_CUDA(cudaEventSynchronize(r.b));
+            float ms = 0;
+            HEAR_CHECK_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+            auto it = idx.find(r.name);
+            if (it == idx.end()) {
+                hear_profile_entry e{};
+                std::strncpy(e.name, r.name, sizeof(e.name) - 1);
+                it = idx.emplace(r.name, agg.size()).first;
+                agg.push_back(e);
+            }
+            hear_profile_entry &e = agg[it->second];
+            e.launches += r.launches;
+            e.total_ms += ms;
+            e.bytes += r.bytes;
+        }
+        ctx->prof.clear();
+    });
+    if (s != HEAR_OK) return s;
+    return copy_out(agg, out, cap, n);
+}
+
+uint64_t hear_launch_count(void) { return hear::g_launches.load(); }
 
 hear_status hear_dbg_poly_mul(hear_context *ctx, uint32_t prime, const uint64_t *a, const uint64_t *b, uint64_t *out) {
     if (!ctx || !a || !b || !out) return fail(HEAR_E_INVAL, "null argument");

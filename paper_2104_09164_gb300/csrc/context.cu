@@ -42,6 +42,44 @@ DevBuf &DevBuf::operator=(DevBuf &&o) noexcept {
     return *this;
 }
 
+std::atomic<uint64_t> g_launches{0};
+
+cudaEvent_t Profiler::get() {
+    if (!spare.empty()) {
+        cudaEvent_t e = spare.back();
+        spare.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    HEAR_CHECK_CUDA(cudaEventCreate(&e));
+    return e;
+}
+void Profiler::clear() {
+    for (auto &r : recs) {
+        spare.push_back(r.a);
+        spare.push_back(r.b);
+    }
+    recs.clear();
+}
+
+ProfScope::ProfScope(const hear_context *ctx, const char *nm, cudaStream_t st, double algo_bytes, uint32_t n_launch)
+    : c(ctx), name(nm), s(st), bytes(algo_bytes), launches(n_launch) {
+    g_launches += n_launch;
+    if (c->prof.on) {
+        std::lock_guard<std::mutex> g(c->prof.mu);
+        a = c->prof.get();
+        cudaEventRecord(a, s);
+    }
+}
+ProfScope::~ProfScope() {
+    if (a) {
+        std::lock_guard<std::mutex> g(c->prof.mu);
+        cudaEvent_t b = c->prof.get();
+        cudaEventRecord(b, s);
+        c->prof.recs.push_back(Profiler::Rec{name, a, b, bytes, launches});
+    }
+}
+
 namespace {
 
 uint32_t bitrev(uint32_t x, uint32_t bits) {

@@ -3,8 +3,10 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstddef>
+#include <atomic>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -77,6 +79,26 @@ struct LevelConsts {
     size_t off_nql_half = 0;   // unused
 };
 
+// Stage profiler: when enabled, every kernel launch of the context is bracketed by CUDA
+// events on its stream and tagged with a stage name and its algorithmic HBM bytes.
+struct Profiler {
+    struct Rec {
+        const char *name;
+        cudaEvent_t a, b;
+        double bytes;
+        uint32_t launches;
+    };
+    bool on = false;
+    std::mutex mu;
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> spare;
+    cudaEvent_t get();
+    void clear();
+};
+
+// total kernel launches issued by the library since it was loaded
+extern std::atomic<uint64_t> g_launches;
+
 }  // namespace hear
 
 // ------------------------------------------------------------------ handles
@@ -94,6 +116,7 @@ struct hear_context {
     hear::DevBuf d_cdt;                    // CDT on device
     std::vector<std::unique_ptr<hear::LevelConsts>> levels;  // per level 0..L
     bool poisoned = false;
+    mutable hear::Profiler prof;
     const hear::DevPrime *dev_primes() const { return static_cast<const hear::DevPrime *>(d_primes.p); }
     uint32_t nqp() const { return n_q + n_p; }
     uint32_t dnum(uint32_t level) const { return (level + 1 + alpha - 1) / alpha; }
@@ -169,6 +192,18 @@ inline LimbMap map_qp(uint32_t level, uint32_t n_q, uint32_t K) {
 
 void ntt_forward(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, LimbMap map, cudaStream_t s);
 void ntt_inverse(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, LimbMap map, cudaStream_t s);
+
+// RAII bracket of one or more kernel launches for the profiler
+struct ProfScope {
+    const hear_context *c;
+    const char *name;
+    cudaStream_t s;
+    double bytes;
+    uint32_t launches;
+    cudaEvent_t a = nullptr;
+    ProfScope(const hear_context *ctx, const char *nm, cudaStream_t st, double algo_bytes, uint32_t n_launch = 1);
+    ~ProfScope();
+};
 
 // The other launchers are declared in kernels.cuh.
 }  // namespace hear

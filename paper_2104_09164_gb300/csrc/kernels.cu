@@ -410,11 +410,15 @@ __global__ void k_rescale_combine(const uint64_t *in, const uint64_t *tmp, uint6
 
 }  // namespace
 
-#define LAUNCH(kernel, total, st, ...)                                                      \
+// launch with the profiler bracket; the stage name is the kernel's, the algorithmic bytes
+// are those of one residue read or written per element unless a launcher says otherwise
+#define LAUNCH_B(kernel, total, st, bytes, ...)                                           \
     do {                                                                                  \
+        ProfScope ps__(c, #kernel, st, (double)(bytes));                                   \
         kernel<<<grid_for(total), kBlock, 0, st>>>(__VA_ARGS__);                           \
         HEAR_CHECK_CUDA(cudaGetLastError());                                               \
     } while (0)
+#define LAUNCH(kernel, total, st, ...) LAUNCH_B(kernel, total, st, 16.0 * (double)(total), __VA_ARGS__)
 
 void to_mont(const hear_context *c, uint64_t *d, uint32_t n_limbs, LimbMap m, cudaStream_t s) {
     LAUNCH(k_to_mont, (uint64_t)n_limbs * c->n, s, d, n_limbs, m, c->dev_primes(), c->n, 1);
@@ -511,8 +515,10 @@ void modup(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t 
 void ks_inner(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *ext,
               const uint64_t *const *d_keys, const uint32_t *d_galois, uint64_t *out, cudaStream_t st) {
     const uint32_t L1 = level + 1, W = L1 + c->K;
-    LAUNCH(k_ks_inner, (uint64_t)n_ct * W * c->n, st, ext, d_keys, d_galois, out, L1, W, c->dnum(level), c->n_q,
-           c->nqp(), c->log_n, c->dev_primes(), n_ct);
+    const double dn = c->dnum(level), wn = (double)W * c->n * 8.0;
+    // keys are read once per distinct key; the batch shares them when n_ct > 1 and the key is common
+    LAUNCH_B(k_ks_inner, (uint64_t)n_ct * W * c->n, st, 2.0 * dn * wn + n_ct * (dn + 2.0) * wn, ext, d_keys,
+             d_galois, out, L1, W, c->dnum(level), c->n_q, c->nqp(), c->log_n, c->dev_primes(), n_ct);
 }
 
 void moddown(const hear_context *c, uint32_t level, uint32_t n_ct, uint64_t *acc, uint64_t *out,

@@ -202,8 +202,17 @@ PassArgs make_args(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, Li
 
 }  // namespace
 
+// algorithmic bytes of one NTT over the limbs a launch transforms: each residue read once
+// and written once
+double ntt_bytes(const hear_context *ctx, uint32_t n_limbs, const LimbMap &map) {
+    uint32_t active = 0, pi;
+    for (uint32_t b = 0; b < n_limbs; b++) active += map.resolve(b, &pi) ? 1 : 0;
+    return 16.0 * (double)ctx->n * active;
+}
+
 void ntt_forward(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, LimbMap map, cudaStream_t s) {
     if (n_limbs == 0) return;
+    ProfScope ps(ctx, "ntt_fwd", s, ntt_bytes(ctx, n_limbs, map), 2);
     PassArgs a = make_args(ctx, data, n_limbs, map, true);
     switch (ctx->log_n) {
     case 11: launch_fwd<6, 5>(a, s); break;
@@ -219,6 +228,7 @@ void ntt_forward(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, Limb
 
 void ntt_inverse(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, LimbMap map, cudaStream_t s) {
     if (n_limbs == 0) return;
+    ProfScope ps(ctx, "ntt_inv", s, ntt_bytes(ctx, n_limbs, map), 2);
     PassArgs a = make_args(ctx, data, n_limbs, map, false);
     switch (ctx->log_n) {
     case 11: launch_inv<6, 5>(a, s); break;

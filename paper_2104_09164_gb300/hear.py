@@ -39,6 +39,11 @@ class hear_layer_desc(ctypes.Structure):
                 ("w", _dp), ("bias", _dp), ("d_out2", ctypes.c_uint32), ("w2", _dp)]
 
 
+class hear_profile_entry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
+
+
 class HearError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("hear error %d: %s" % (code, msg))
@@ -92,6 +97,9 @@ def _load():
                                      ctypes.POINTER(_vp), _vp]),
         "hear_evaluate_host": (st, [_vp, _vp, _u64p, ctypes.c_size_t, ctypes.c_double, _u64p, ctypes.c_size_t,
                                     _szp, _u32p, _dp, _vp]),
+        "hear_profile_begin": (st, [_vp]),
+        "hear_profile_end": (st, [_vp, ctypes.POINTER(hear_profile_entry), ctypes.c_size_t, _szp]),
+        "hear_launch_count": (ctypes.c_uint64, []),
         "hear_dbg_poly_mul": (st, [_vp, ctypes.c_uint32, _u64p, _u64p, _u64p]),
         "hear_dbg_ntt_roundtrip": (st, [_vp, _u64p, ctypes.c_size_t]),
     }
@@ -347,6 +355,24 @@ def hear_evaluate_host(m, evk, in_words, n_ct, scale, out=None, stream=None):
     _check(lib.hear_evaluate_host(m, evk, _p(w, _u64p), int(n_ct), float(scale), _p(out, _u64p), out.size,
                                   ctypes.byref(n), ctypes.byref(lv), ctypes.byref(sc), _stream(stream)))
     return out, lv.value, sc.value
+
+
+# ---------------------------------------------------------------- tracing
+def hear_profile_begin(ctx):
+    _check(lib.hear_profile_begin(ctx))
+
+
+def hear_profile_end(ctx):
+    """-> {stage: (launches, total_ms, algorithmic_bytes)}"""
+    n = ctypes.c_size_t(0)
+    buf = (hear_profile_entry * 256)()
+    _check(lib.hear_profile_end(ctx, buf, 256, ctypes.byref(n)))
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms), float(buf[i].bytes))
+            for i in range(n.value)}
+
+
+def hear_launch_count():
+    return int(lib.hear_launch_count())
 
 
 # ---------------------------------------------------------------- debug
