@@ -168,7 +168,6 @@ def oracle_sample(w, steps_keys, seconds_budget=25.0):
 # ------------------------------------------------------------------ GPU arm
 class Setup:
     def __init__(self, H, w, stream, device):
-        from oracle.oracle import pack_clips  # noqa: F401  (packing rule is also in hear_encrypt_clips)
         self.H, self.w = H, w
         self.ctx = H.hear_context_create(w.log_n, w.q_bits, w.p_bits, w.log2_scale, w.sigma, device)
         self.model = H.hear_model_create(self.ctx, w.layers, w.clip_dim)
