@@ -187,6 +187,26 @@ hear_status hear_evaluate_host(const hear_model *m, const hear_eval_keys *evk, c
                                size_t n_ct, double scale, uint64_t *out_words, size_t cap, size_t *n,
                                uint32_t *level_out, double *scale_out, void *stream);
 
+/* ---- rescale for callers that cannot allocate device memory ----
+ * The paper has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- a process whose device-memory quota is already held by another
+ * framework's caching allocator, a real-time loop that must not take the allocator's
+ * locks or latency, a host that owns only pageable host memory and a stream.  It divides
+ * a ciphertext by its last prime exactly like hear_rescale, from and to HOST arrays in the
+ * coefficient domain: in = uint64[n_poly][level+1][N], out = uint64[n_poly][level][N]
+ * (1 <= level <= L, 1 <= n_poly <= 3).  It allocates nothing: its device working memory is
+ * a fixed 16 MiB array (2^21 words) inside the library, which every GPU that loads the
+ * library holds until the process exits; it calls no cudaMalloc, cudaFree or allocating
+ * library routine.  Sizes with n_poly * (2*level + 1) * N > 2^21 words are rejected with
+ * HEAR_E_UNSUPPORTED; a running profiler (hear_profile_begin) is rejected with
+ * HEAR_E_STATE.  The first call on each device looks up the array's device address, so
+ * make that first call before any stream capture.  Every call shares the array, which keeps
+ * the last call's contents (each call overwrites everything it reads).  Calls that overlapped
+ * on the GPU would race on the array, so the library takes a process-wide lock for the call
+ * and synchronises `stream` before returning. */
+hear_status hear_rescale_noalloc(const hear_context *ctx, const uint64_t *in, uint32_t level, uint32_t n_poly,
+                                 uint64_t *out, void *stream);
+
 /* ---- tracing: CUDA-event stage profiler and launch counter ---- */
 /* One entry per stage (kernel name): how many kernel launches it made, their summed
  * device time (CUDA events recorded on the launching stream around each launch) and

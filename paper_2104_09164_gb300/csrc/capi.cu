@@ -70,6 +70,11 @@ void to_device_ntt(hear_context *c, const uint64_t *words, uint32_t level, uint3
 }
 }  // namespace
 
+namespace hear {
+// lets other translation units report through hear_last_error()
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+}  // namespace hear
+
 extern "C" {
 
 const char *hear_last_error(void) { return g_last_error.c_str(); }

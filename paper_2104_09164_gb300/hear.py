@@ -97,6 +97,7 @@ def _load():
                                      ctypes.POINTER(_vp), _vp]),
         "hear_evaluate_host": (st, [_vp, _vp, _u64p, ctypes.c_size_t, ctypes.c_double, _u64p, ctypes.c_size_t,
                                     _szp, _u32p, _dp, _vp]),
+        "hear_rescale_noalloc": (st, [_vp, _u64p, ctypes.c_uint32, ctypes.c_uint32, _u64p, _vp]),
         "hear_profile_begin": (st, [_vp]),
         "hear_profile_end": (st, [_vp, ctypes.POINTER(hear_profile_entry), ctypes.c_size_t, _szp]),
         "hear_launch_count": (ctypes.c_uint64, []),
@@ -355,6 +356,15 @@ def hear_evaluate_host(m, evk, in_words, n_ct, scale, out=None, stream=None):
     _check(lib.hear_evaluate_host(m, evk, _p(w, _u64p), int(n_ct), float(scale), _p(out, _u64p), out.size,
                                   ctypes.byref(n), ctypes.byref(lv), ctypes.byref(sc), _stream(stream)))
     return out, lv.value, sc.value
+
+
+def hear_rescale_noalloc(ctx, words, level, n_poly, stream=None):
+    """rescale from/to host arrays (coefficient domain) without device allocation"""
+    w = _arr(words, np.uint64).reshape(-1)
+    n = w.size // (n_poly * (level + 1))
+    out = np.empty(n_poly * level * n, dtype=np.uint64)
+    _check(lib.hear_rescale_noalloc(ctx, _p(w, _u64p), int(level), int(n_poly), _p(out, _u64p), _stream(stream)))
+    return out.reshape(n_poly, level, n)
 
 
 # ---------------------------------------------------------------- tracing
