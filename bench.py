@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--impl", default="hear", choices=["hear", "reference"])
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clips", type=int, default=None, help="clips in the batch (default: the workload's)")
     return ap.parse_args()
 
 
@@ -261,7 +262,7 @@ def main_gpu(a):
     from paper_2104_09164_gb300 import hear as H
     from paper_2104_09164_gb300.workloads import make_workload
     stream = torch.cuda.Stream(device=device)
-    w = make_workload(a.workload)
+    w = make_workload(a.workload, a.clips)
     S = Setup(H, w, stream, device)
     total_ms, lat, launches, clocks = run_gpu(S, a.steps, a.warmup, dist, torch, stream, device)
     total_ms = dist.max(total_ms)
@@ -298,7 +299,7 @@ def main_gpu(a):
             "stages_ms_per_step": {k: v[1] / psteps for k, v in sorted(stages.items(), key=lambda kv: -kv[1][1])},
             "clocks": clocks, "gpu_launches": launches,
         }
-    if not a.no_batched and a.workload == "small":
+    if not a.no_batched and a.workload == "small" and a.clips is None:
         S.close()
         wl = make_workload("large")
         SL = Setup(H, wl, stream, device)

@@ -20,7 +20,10 @@
  *     *n; a short capacity returns HEAR_E_INVAL with the required count in *n.
  *   - `stream` is a cudaStream_t (NULL = the context's own stream).  Calls that return
  *     device-resident handles enqueue their work on that stream; calls that fill host
- *     arrays synchronise it before returning.
+ *     arrays synchronise it before returning.  A ciphertext's memory comes from the
+ *     stream-ordered allocator of the stream it was produced on and goes back to it when
+ *     the handle is destroyed, so that stream must outlive the handle, and work queued on
+ *     other streams must be complete (or ordered before that stream) when it is destroyed.
  *   - Ciphertexts live in device memory (HBM) in the library's NTT domain, laid out as
  *     uint64_t[n_poly][level+1][N], one word per residue.  Exported/imported ciphertexts
  *     use the coefficient domain with the same layout.

@@ -1,6 +1,7 @@
 // capi.cu -- the extern "C" boundary (include/hear.h): argument checks, error capture,
 // handle management.  No C++ exception crosses it.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -38,6 +39,16 @@ hear_status guard(hear_context *ctx, F &&f) {
 
 cudaStream_t stream_of(hear_context *c, void *s) { return s ? static_cast<cudaStream_t>(s) : c->stream; }
 
+// Whole evaluations replay a captured CUDA graph unless the stage profiler is on (it brackets
+// each launch with events) or HEAR_NO_GRAPH is set in the environment.
+bool use_graphs(const hear_context *c) {
+    static const bool off = [] {
+        const char *v = std::getenv("HEAR_NO_GRAPH");
+        return v && *v && *v != '0';
+    }();
+    return !off && !c->prof.on;
+}
+
 template <class T>
 hear_status copy_out(const std::vector<T> &v, T *out, size_t cap, size_t *n) {
     if (n) *n = v.size();
@@ -46,14 +57,16 @@ hear_status copy_out(const std::vector<T> &v, T *out, size_t cap, size_t *n) {
     return HEAR_OK;
 }
 
-hear_ciphertext *new_ct(hear_context *c, uint32_t level, uint32_t n_poly, double scale) {
+// ciphertext memory comes from the stream-ordered pool of the stream the ciphertext is
+// produced on and is returned to it when the handle is destroyed
+hear_ciphertext *new_ct(hear_context *c, uint32_t level, uint32_t n_poly, double scale, cudaStream_t st) {
     auto ct = new hear_ciphertext();
     ct->ctx = c;
     ct->level = level;
     ct->n_poly = n_poly;
     ct->scale = scale;
     try {
-        ct->d = DevBuf((size_t)n_poly * (level + 1) * c->n * 8, nullptr);
+        ct->d = DevBuf((size_t)n_poly * (level + 1) * c->n * 8, st);
     } catch (...) {
         delete ct;
         throw;
@@ -173,6 +186,12 @@ hear_status hear_eval_key_export(const hear_eval_keys *evk, uint32_t galois, uin
         m.q_count = c->n_q;
         m.n_q = c->n_q;
         const uint32_t limbs = c->dnum_max() * 2 * c->nqp();
+        if (galois != 1) {
+            // rotation keys are stored sigma_g^{-1}-permuted; undo it
+            DevBuf u(words * 8, st);
+            automorphism(c, c->nqp() - 1, c->dnum_max() * 2, galois, t.u64(), u.u64(), st);
+            HEAR_CHECK_CUDA(cudaMemcpyAsync(t.p, u.p, words * 8, cudaMemcpyDeviceToDevice, st));
+        }
         from_mont(c, t.u64(), limbs, m, st);
         ntt_inverse(c, t.u64(), limbs, m, st);
         HEAR_CHECK_CUDA(cudaMemcpyAsync(out, t.p, words * 8, cudaMemcpyDeviceToHost, st));
@@ -265,7 +284,7 @@ hear_status hear_ciphertext_import(hear_context *ctx, const uint64_t *words, siz
             for (uint32_t k = 0; k < ctx->n; k++)
                 HEAR_REQUIRE(w[k] < q, HEAR_E_FORMAT, "residue not reduced");
         }
-        hear_ciphertext *ct = new_ct(ctx, level, n_poly, scale);
+        hear_ciphertext *ct = new_ct(ctx, level, n_poly, scale, stream_of(ctx, stream));
         try {
             to_device_ntt(ctx, words, level, n_poly, ct->d.u64(), stream_of(ctx, stream));
         } catch (...) {
@@ -291,13 +310,14 @@ hear_status hear_rotate_hoisted(const hear_eval_keys *evk, const hear_ciphertext
             HEAR_REQUIRE(k, HEAR_E_NOKEY, "missing rotation key for step " + std::to_string(steps[i]));
             rots.push_back(Rot{k, g});
         }
+        const uint64_t ctw = 2ull * (ct->level + 1) * c->n;
+        DevBuf all((size_t)n_steps * ctw * 8, st);
+        rotate_hoisted(c, ct->level, 1, ct->d.u64(), rots, all.u64(), st);
         std::vector<std::unique_ptr<hear_ciphertext>> res;
-        std::vector<uint64_t *> outs;
         for (size_t i = 0; i < n_steps; i++) {
-            res.emplace_back(new_ct(c, ct->level, 2, ct->scale));
-            outs.push_back(res.back()->d.u64());
+            res.emplace_back(new_ct(c, ct->level, 2, ct->scale, st));
+            HEAR_CHECK_CUDA(cudaMemcpyAsync(res.back()->d.p, all.u64() + i * ctw, ctw * 8, cudaMemcpyDeviceToDevice, st));
         }
-        rotate_hoisted(c, ct->level, 1, ct->d.u64(), rots, outs, st);
         for (size_t i = 0; i < n_steps; i++) out[i] = res[i].release();
     });
 }
@@ -316,7 +336,8 @@ hear_status hear_rescale(const hear_ciphertext *ct, hear_ciphertext **out, void 
         const size_t words = (size_t)ct->n_poly * (ct->level + 1) * c->n;
         DevBuf in(words * 8, st), tmp((size_t)ct->n_poly * ct->level * c->n * 8, st);
         HEAR_CHECK_CUDA(cudaMemcpyAsync(in.p, ct->d.p, words * 8, cudaMemcpyDeviceToDevice, st));
-        std::unique_ptr<hear_ciphertext> r(new_ct(c, ct->level - 1, ct->n_poly, ct->scale / (double)c->primes[ct->level]));
+        std::unique_ptr<hear_ciphertext> r(
+            new_ct(c, ct->level - 1, ct->n_poly, ct->scale / (double)c->primes[ct->level], st));
         rescale(c, ct->level, ct->n_poly, in.u64(), r->d.u64(), tmp.u64(), st);
         *out = r.release();
     });
@@ -328,8 +349,9 @@ hear_status hear_add(const hear_ciphertext *a, const hear_ciphertext *b, hear_ci
     if (b->ctx != c) return fail(HEAR_E_STATE, "operands from different contexts");
     if (a->level != b->level || a->n_poly != b->n_poly) return fail(HEAR_E_SCALE, "operands at different levels");
     return guard(c, [&] {
-        std::unique_ptr<hear_ciphertext> r(new_ct(c, a->level, a->n_poly, a->scale));
-        add_ct(c, a->level, a->n_poly, a->d.u64(), b->d.u64(), r->d.u64(), stream_of(c, stream));
+        cudaStream_t st = stream_of(c, stream);
+        std::unique_ptr<hear_ciphertext> r(new_ct(c, a->level, a->n_poly, a->scale, st));
+        add_ct(c, a->level, a->n_poly, a->d.u64(), b->d.u64(), r->d.u64(), st);
         *out = r.release();
     });
 }
@@ -343,7 +365,7 @@ hear_status hear_mulplain(const hear_ciphertext *ct, const double *z, size_t n_s
     return guard(c, [&] {
         cudaStream_t st = stream_of(c, stream);
         DevBuf pt = encode_plain(c, z, pt_scale, ct->level, st);
-        std::unique_ptr<hear_ciphertext> r(new_ct(c, ct->level, 2, ct->scale * pt_scale));
+        std::unique_ptr<hear_ciphertext> r(new_ct(c, ct->level, 2, ct->scale * pt_scale, st));
         mulplain(c, ct->level, 1, ct->d.u64(), pt.u64(), r->d.u64(), st);
         HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
         *out = r.release();
@@ -359,8 +381,9 @@ hear_status hear_multiply_relin(const hear_eval_keys *evk, const hear_ciphertext
     const uint64_t *rk = evk->key(1);
     if (!rk) return fail(HEAR_E_NOKEY, "missing relinearisation key");
     return guard(c, [&] {
-        std::unique_ptr<hear_ciphertext> r(new_ct(c, a->level, 2, a->scale * b->scale));
-        mul_relin(c, a->level, 1, a->d.u64(), b->d.u64(), rk, r->d.u64(), stream_of(c, stream));
+        cudaStream_t st = stream_of(c, stream);
+        std::unique_ptr<hear_ciphertext> r(new_ct(c, a->level, 2, a->scale * b->scale, st));
+        mul_relin(c, a->level, 1, a->d.u64(), b->d.u64(), rk, r->d.u64(), st);
         *out = r.release();
     });
 }
@@ -400,6 +423,25 @@ static hear_status evaluate_range(const hear_model *m, size_t l0, size_t l1, con
     return guard(c, [&] {
         cudaStream_t st = stream_of(c, stream);
         const uint64_t ctw = 2ull * (lin + 1) * c->n;
+        if (use_graphs(c)) {
+            std::lock_guard<std::mutex> g(m->plan_mu);
+            hear_model::Plan *p = graph_plan(m, evk, l0, l1, (uint32_t)n_ct, in[0]->scale, st);
+            HEAR_CHECK_CUDA(cudaStreamWaitEvent(st, p->done, 0));
+            for (size_t i = 0; i < n_ct; i++)
+                HEAR_CHECK_CUDA(cudaMemcpyAsync(p->X.u64() + i * ctw, in[i]->d.p, ctw * 8, cudaMemcpyDeviceToDevice, st));
+            HEAR_CHECK_CUDA(cudaGraphLaunch(p->exec, st));
+            g_launches += p->launches;
+            const uint64_t otw = 2ull * (p->level_out + 1) * c->n;
+            std::vector<std::unique_ptr<hear_ciphertext>> res;
+            for (size_t i = 0; i < n_ct; i++) {
+                res.emplace_back(new_ct(c, p->level_out, 2, p->scale_out, st));
+                HEAR_CHECK_CUDA(
+                    cudaMemcpyAsync(res.back()->d.p, p->Y.u64() + i * otw, otw * 8, cudaMemcpyDeviceToDevice, st));
+            }
+            HEAR_CHECK_CUDA(cudaEventRecord(p->done, st));
+            for (size_t i = 0; i < n_ct; i++) out[i] = res[i].release();
+            return;
+        }
         DevBuf X((size_t)n_ct * ctw * 8, st);
         for (size_t i = 0; i < n_ct; i++)
             HEAR_CHECK_CUDA(cudaMemcpyAsync(X.u64() + i * ctw, in[i]->d.p, ctw * 8, cudaMemcpyDeviceToDevice, st));
@@ -409,7 +451,7 @@ static hear_status evaluate_range(const hear_model *m, size_t l0, size_t l1, con
         const uint64_t otw = 2ull * (lout + 1) * c->n;
         std::vector<std::unique_ptr<hear_ciphertext>> res;
         for (size_t i = 0; i < n_ct; i++) {
-            res.emplace_back(new_ct(c, lout, 2, sout));
+            res.emplace_back(new_ct(c, lout, 2, sout, st));
             HEAR_CHECK_CUDA(cudaMemcpyAsync(res.back()->d.p, Y.u64() + i * otw, otw * 8, cudaMemcpyDeviceToDevice, st));
         }
         for (size_t i = 0; i < n_ct; i++) out[i] = res[i].release();
@@ -441,6 +483,23 @@ hear_status hear_evaluate_host(const hear_model *m, const hear_eval_keys *evk, c
         cudaStream_t st = stream_of(c, stream);
         const uint32_t lin = m->layers[0].level_in;
         const uint64_t ctw = 2ull * (lin + 1) * c->n;
+        if (use_graphs(c)) {
+            std::lock_guard<std::mutex> g(m->plan_mu);
+            hear_model::Plan *p = graph_plan(m, evk, 0, m->layers.size(), (uint32_t)n_ct, scale, st);
+            HEAR_CHECK_CUDA(cudaStreamWaitEvent(st, p->done, 0));
+            to_device_ntt(c, in_words, lin, (uint32_t)(2 * n_ct), p->X.u64(), st);
+            HEAR_CHECK_CUDA(cudaGraphLaunch(p->exec, st));
+            g_launches += p->launches;
+            DevBuf Y(out_words_n * 8, st);
+            HEAR_CHECK_CUDA(cudaMemcpyAsync(Y.p, p->Y.p, out_words_n * 8, cudaMemcpyDeviceToDevice, st));
+            HEAR_CHECK_CUDA(cudaEventRecord(p->done, st));
+            ntt_inverse(c, Y.u64(), (uint32_t)(2 * n_ct) * (p->level_out + 1), map_q(p->level_out, c->n_q), st);
+            HEAR_CHECK_CUDA(cudaMemcpyAsync(out_words, Y.p, out_words_n * 8, cudaMemcpyDeviceToHost, st));
+            HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
+            if (level_out) *level_out = p->level_out;
+            if (scale_out) *scale_out = p->scale_out;
+            return;
+        }
         DevBuf X((size_t)n_ct * ctw * 8, st);
         to_device_ntt(c, in_words, lin, (uint32_t)(2 * n_ct), X.u64(), st);
         uint32_t lout;

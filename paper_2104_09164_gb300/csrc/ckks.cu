@@ -37,6 +37,11 @@ void forget_encoder(hear_context *ctx) {
     g_enc.erase(ctx);
 }
 
+uint32_t galois_inverse(const hear_context *c, uint32_t g) {
+    // the units of Z/2N form a group of order N, so g^(N-1) = g^-1
+    return (uint32_t)hm::powmod(g, c->n - 1, 2ull * c->n);
+}
+
 uint32_t galois_of(const hear_context *c, int64_t step) {
     const int64_t slots = c->n / 2;
     int64_t r = ((step % slots) + slots) % slots;
@@ -85,6 +90,8 @@ void keygen(hear_context *c, uint64_t seed, const int32_t *steps, size_t n_steps
     // switching keys: relinearisation (s^2) and one per rotation (sigma_g(s))
     auto evk = std::make_unique<hear_eval_keys>();
     evk->ctx = c;
+    static std::atomic<uint64_t> serials{0};
+    evk->serial = ++serials;
     std::vector<uint64_t> pmod(nqp, 0);
     for (uint32_t t = 0; t < nq; t++) {
         uint64_t v = 1;
@@ -118,6 +125,13 @@ void keygen(hear_context *c, uint64_t seed, const int32_t *steps, size_t n_steps
         }
         LimbMap km = all;
         to_mont(c, key.u64(), dnum * 2 * nqp, km, st);
+        if (g != 1) {
+            // stored sigma_g^{-1}-permuted: the inner product then reads keys and digits
+            // coalesced and applies sigma_g to its output instead of to every digit
+            DevBuf perm((size_t)dnum * 2 * plane * 8, nullptr);
+            automorphism(c, nqp - 1, dnum * 2, galois_inverse(c, g), key.u64(), perm.u64(), st);
+            key = std::move(perm);
+        }
         evk->keys.emplace(g, std::move(key));
     }
     HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
@@ -151,7 +165,7 @@ hear_ciphertext *encrypt_slots(hear_context *c, const hear_public_key *pk, const
     ct->level = c->L;
     ct->n_poly = 2;
     ct->scale = scale;
-    ct->d = DevBuf(2 * limbs * 8, nullptr);
+    ct->d = DevBuf(2 * limbs * 8, st);
     encrypt_combine(c, vn, e0, e1, mn, pk->pk_mont.u64(), ct->d.u64(), st);
     return ct.release();
 }
@@ -185,59 +199,62 @@ DevBuf encode_plain(hear_context *c, const double *z, double scale, uint32_t lev
 
 // ------------------------------------------------------------------ key switching compositions
 namespace {
-struct RotTable {
-    DevBuf d;
-    const uint64_t *const *keys(size_t r, uint32_t n_ct) const {
-        return reinterpret_cast<const uint64_t *const *>(d.u64() + r * n_ct);
-    }
-    const uint32_t *gals(size_t off_words, size_t r, uint32_t n_ct) const {
-        return reinterpret_cast<const uint32_t *>(d.u64() + off_words) + r * n_ct;
-    }
+// device table of R jobs: key pointers, inverse galois elements, galois elements
+struct JobTable {
+    const uint64_t *d = nullptr;
+    uint32_t R = 0;
+    const uint64_t *const *keys() const { return reinterpret_cast<const uint64_t *const *>(d); }
+    const uint32_t *ginv() const { return reinterpret_cast<const uint32_t *>(d + R); }
+    const uint32_t *gal() const { return ginv() + R; }
 };
+JobTable make_jobs(hear_context *c, const std::vector<Rot> &rots, cudaStream_t st) {
+    JobTable t;
+    t.R = (uint32_t)rots.size();
+    std::vector<uint64_t> host(t.R + (2 * t.R + 1) / 2, 0);
+    uint32_t *g32 = reinterpret_cast<uint32_t *>(host.data() + t.R);
+    for (uint32_t r = 0; r < t.R; r++) {
+        host[r] = (uint64_t)(uintptr_t)rots[r].key;
+        g32[r] = galois_inverse(c, rots[r].galois);
+        g32[t.R + r] = rots[r].galois;
+    }
+    std::lock_guard<std::mutex> g(c->tab_mu);
+    auto it = c->job_tables.find(host);
+    if (it == c->job_tables.end()) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        HEAR_CHECK_CUDA(cudaStreamIsCapturing(st, &cs));
+        HEAR_REQUIRE(cs == cudaStreamCaptureStatusNone, HEAR_E_STATE, "key-switch table missing during capture");
+        DevBuf d(host.size() * 8, nullptr);
+        HEAR_CHECK_CUDA(cudaMemcpy(d.p, host.data(), host.size() * 8, cudaMemcpyHostToDevice));
+        it = c->job_tables.emplace(host, std::move(d)).first;
+    }
+    t.d = it->second.u64();
+    return t;
+}
 }  // namespace
 
 void rotate_hoisted(hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *x, const std::vector<Rot> &rots,
-                    const std::vector<uint64_t *> &outs, cudaStream_t st) {
+                    uint64_t *out, cudaStream_t st) {
     if (rots.empty()) return;
-    const uint32_t n = c->n, L1 = level + 1, W = L1 + c->K, dnum = c->dnum(level);
+    const uint32_t n = c->n, L1 = level + 1, W = L1 + c->K, dnum = c->dnum(level), R = (uint32_t)rots.size();
     const uint64_t plane = (uint64_t)L1 * n, ctw = 2 * plane;
-    DevBuf ext((size_t)n_ct * dnum * W * n * 8, st), tmp((size_t)n_ct * ctw * 8, st),
-        acc((size_t)n_ct * 2 * W * n * 8, st);
+    DevBuf ext((size_t)n_ct * dnum * W * n * 8, st), tmp((size_t)R * n_ct * ctw * 8, st),
+        acc((size_t)R * n_ct * 2 * W * n * 8, st);
     modup(c, level, n_ct, x + plane, ctw, ext.u64(), tmp.u64(), st);
-    // per rotation: n_ct key pointers and n_ct galois elements
-    const size_t R = rots.size();
-    const size_t key_words = R * n_ct, gal_words = (R * n_ct + 1) / 2;
-    std::vector<uint64_t> host(key_words + gal_words, 0);
-    uint32_t *g32 = reinterpret_cast<uint32_t *>(host.data() + key_words);
-    for (size_t r = 0; r < R; r++)
-        for (uint32_t i = 0; i < n_ct; i++) {
-            host[r * n_ct + i] = (uint64_t)(uintptr_t)rots[r].key;
-            g32[r * n_ct + i] = rots[r].galois;
-        }
-    RotTable tab{upload(host.data(), host.size() * 8, st)};
-    for (size_t r = 0; r < R; r++) {
-        ks_inner(c, level, n_ct, ext.u64(), tab.keys(r, n_ct), tab.gals(key_words, r, n_ct), acc.u64(), st);
-        moddown(c, level, n_ct, acc.u64(), outs[r], x, ctw, 1u, tab.gals(key_words, r, n_ct), tmp.u64(), st);
-    }
+    JobTable jobs = make_jobs(c, rots, st);
+    ks_inner(c, level, R, n_ct, ext.u64(), false, jobs.keys(), jobs.ginv(), acc.u64(), st);
+    moddown(c, level, R * n_ct, acc.u64(), out, x, ctw, 1u, true, jobs.gal(), n_ct, tmp.u64(), st);
 }
 
-void rotate_each(hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *x, const std::vector<Rot> &rots,
-                 uint64_t *out, cudaStream_t st) {
-    const uint32_t n = c->n, L1 = level + 1, W = L1 + c->K, dnum = c->dnum(level);
+void rotate_each(hear_context *c, uint32_t level, uint32_t R, uint32_t C, const uint64_t *x,
+                 const std::vector<Rot> &rots, uint64_t *out, cudaStream_t st) {
+    const uint32_t n = c->n, L1 = level + 1, W = L1 + c->K, dnum = c->dnum(level), n_ct = R * C;
     const uint64_t plane = (uint64_t)L1 * n, ctw = 2 * plane;
     DevBuf ext((size_t)n_ct * dnum * W * n * 8, st), tmp((size_t)n_ct * ctw * 8, st),
         acc((size_t)n_ct * 2 * W * n * 8, st);
     modup(c, level, n_ct, x + plane, ctw, ext.u64(), tmp.u64(), st);
-    const size_t key_words = n_ct, gal_words = (n_ct + 1) / 2;
-    std::vector<uint64_t> host(key_words + gal_words, 0);
-    uint32_t *g32 = reinterpret_cast<uint32_t *>(host.data() + key_words);
-    for (uint32_t i = 0; i < n_ct; i++) {
-        host[i] = (uint64_t)(uintptr_t)rots[i].key;
-        g32[i] = rots[i].galois;
-    }
-    RotTable tab{upload(host.data(), host.size() * 8, st)};
-    ks_inner(c, level, n_ct, ext.u64(), tab.keys(0, n_ct), tab.gals(key_words, 0, n_ct), acc.u64(), st);
-    moddown(c, level, n_ct, acc.u64(), out, x, ctw, 1u, tab.gals(key_words, 0, n_ct), tmp.u64(), st);
+    JobTable jobs = make_jobs(c, rots, st);
+    ks_inner(c, level, R, C, ext.u64(), true, jobs.keys(), jobs.ginv(), acc.u64(), st);
+    moddown(c, level, n_ct, acc.u64(), out, x, ctw, 1u, false, jobs.gal(), C, tmp.u64(), st);
 }
 
 void mul_relin(hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *a, const uint64_t *b,
@@ -249,10 +266,9 @@ void mul_relin(hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *a
     DevBuf ext((size_t)n_ct * dnum * W * n * 8, st), tmp((size_t)n_ct * 2 * plane * 8, st),
         acc((size_t)n_ct * 2 * W * n * 8, st);
     modup(c, level, n_ct, d3.u64() + 2 * plane, 3 * plane, ext.u64(), tmp.u64(), st);
-    std::vector<uint64_t> host(n_ct, (uint64_t)(uintptr_t)relin_key);
-    DevBuf keys = upload(host.data(), host.size() * 8, st);
-    ks_inner(c, level, n_ct, ext.u64(), reinterpret_cast<const uint64_t *const *>(keys.p), nullptr, acc.u64(), st);
-    moddown(c, level, n_ct, acc.u64(), out, d3.u64(), 3 * plane, 3u, nullptr, tmp.u64(), st);
+    JobTable jobs = make_jobs(c, {Rot{relin_key, 1u}}, st);
+    ks_inner(c, level, 1, n_ct, ext.u64(), false, jobs.keys(), jobs.ginv(), acc.u64(), st);
+    moddown(c, level, n_ct, acc.u64(), out, d3.u64(), 3 * plane, 3u, false, nullptr, 1, tmp.u64(), st);
 }
 
 // ------------------------------------------------------------------ network
@@ -281,9 +297,9 @@ void build_fc(hear_context *c, hear_model::Fc &fc, const double *W, uint32_t d_o
     for (uint32_t j = 0; j < fc.n2; j++)
         for (uint32_t b = 0; b < n1; b++)
             if (j * n1 + b < fc.D) jobs.push_back({j, b});
-    fc.pts.clear();
-    fc.pts.resize((size_t)fc.n2 * n1);
-    std::vector<uint64_t> ptrs((size_t)fc.n2 * n1, 0);
+    const uint64_t plane = (uint64_t)L1 * n;
+    fc.pts = DevBuf((size_t)fc.n2 * n1 * plane * 8, nullptr);
+    HEAR_CHECK_CUDA(cudaMemsetAsync(fc.pts.p, 0, fc.pts.bytes, st));
     auto enc = encoder(c);
     const size_t chunk = 64;
     std::vector<double> z;
@@ -307,17 +323,13 @@ void build_fc(hear_context *c, hear_model::Fc &fc, const double *W, uint32_t d_o
         DevBuf dm = upload(m.data(), m.size() * 8, st);
         for (size_t q = 0; q < cnt; q++) {
             uint32_t j = jobs[s0 + q].first, b = jobs[s0 + q].second;
-            DevBuf pt((size_t)L1 * n * 8, nullptr);
-            i64_to_limbs(c, (const int64_t *)dm.p + q * n, pt.u64(), L1, map_q(level, c->n_q), st);
-            ntt_forward(c, pt.u64(), L1, map_q(level, c->n_q), st);
-            to_mont(c, pt.u64(), L1, map_q(level, c->n_q), st);
-            ptrs[(size_t)j * n1 + b] = (uint64_t)(uintptr_t)pt.p;
-            fc.pts[(size_t)j * n1 + b] = std::move(pt);
+            uint64_t *pt = fc.pts.u64() + ((size_t)j * n1 + b) * plane;
+            i64_to_limbs(c, (const int64_t *)dm.p + q * n, pt, L1, map_q(level, c->n_q), st);
+            ntt_forward(c, pt, L1, map_q(level, c->n_q), st);
+            to_mont(c, pt, L1, map_q(level, c->n_q), st);
         }
         HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
     }
-    fc.d_pt_ptrs = DevBuf(ptrs.size() * 8, nullptr);
-    HEAR_CHECK_CUDA(cudaMemcpy(fc.d_pt_ptrs.p, ptrs.data(), ptrs.size() * 8, cudaMemcpyHostToDevice));
     fc.rotsum.clear();
     for (uint32_t s = d_out; s < d_in; s *= 2) fc.rotsum.push_back((int32_t)(s * k));
 }
@@ -341,8 +353,7 @@ void rotsum(hear_context *c, const hear_eval_keys *evk, uint32_t level, uint32_t
     DevBuf r((size_t)n_ct * ctw * 8, st);
     for (int32_t s : steps) {
         uint32_t g = galois_of(c, s);
-        std::vector<Rot> rots(n_ct, Rot{need_key(evk, g), g});
-        rotate_each(c, level, n_ct, x, rots, r.u64(), st);
+        rotate_each(c, level, 1, n_ct, x, {Rot{need_key(evk, g), g}}, r.u64(), st);
         add_ct(c, level, 2 * n_ct, x, r.u64(), x, st);
     }
 }
@@ -352,40 +363,30 @@ DevBuf eval_fc(const hear_model *m, const hear_model::Fc &fc, const hear_eval_ke
     hear_context *c = m->ctx;
     const uint32_t level = fc.level, n = c->n, L1 = level + 1, n1 = fc.n1, n2 = fc.n2, k = m->k;
     const uint64_t ctw = 2ull * L1 * n, batch = (uint64_t)n_ct * ctw;
-    // baby steps rho^(b k)(x), b < n1, hoisted
-    DevBuf babies((size_t)(n1 > 1 ? n1 - 1 : 1) * batch * 8, st);
-    std::vector<const uint64_t *> in_ptrs(n1);
-    in_ptrs[0] = x;
+    // baby steps rho^(b k)(x), b < n1, hoisted; slot 0 holds x itself so that the inner
+    // sums read one contiguous [n1][n_ct] batch
+    DevBuf babies((size_t)n1 * batch * 8, st);
+    HEAR_CHECK_CUDA(cudaMemcpyAsync(babies.p, x, batch * 8, cudaMemcpyDeviceToDevice, st));
     std::vector<Rot> rots;
-    std::vector<uint64_t *> outs;
     for (uint32_t b = 1; b < n1; b++) {
         uint32_t g = galois_of(c, (int64_t)b * k);
         rots.push_back(Rot{need_key(evk, g), g});
-        outs.push_back(babies.u64() + (b - 1) * batch);
-        in_ptrs[b] = outs.back();
     }
-    rotate_hoisted(c, level, n_ct, x, rots, outs, st);
+    rotate_hoisted(c, level, n_ct, x, rots, babies.u64() + batch, st);
     // giant-step inner sums sum_b pt_{j,b} (.) baby_b (lazy: no rescale yet)
     DevBuf G((size_t)n2 * batch * 8, st);
-    std::vector<uint64_t> ptr_host(n1 + n2);
-    for (uint32_t b = 0; b < n1; b++) ptr_host[b] = (uint64_t)(uintptr_t)in_ptrs[b];
-    for (uint32_t j = 0; j < n2; j++) ptr_host[n1 + j] = (uint64_t)(uintptr_t)(G.u64() + j * batch);
-    DevBuf d_ptrs = upload(ptr_host.data(), ptr_host.size() * 8, st);
-    lincomb(c, level, n_ct, n1, n2, reinterpret_cast<const uint64_t *const *>(d_ptrs.p),
-            reinterpret_cast<const uint64_t *const *>(fc.d_pt_ptrs.p),
-            reinterpret_cast<uint64_t *const *>(d_ptrs.u64() + n1), st);
+    lincomb(c, level, n_ct, n1, n2, babies.u64(), fc.pts.u64(), G.u64(), st);
     // giant rotations rho^(j n1 k), j >= 1, of the un-rescaled sums, then accumulate
     if (n2 > 1) {
-        const uint32_t cnt = (n2 - 1) * n_ct;
         std::vector<Rot> gr;
         for (uint32_t j = 1; j < n2; j++) {
             uint32_t g = galois_of(c, (int64_t)j * n1 * k);
-            const uint64_t *key = need_key(evk, g);
-            for (uint32_t i = 0; i < n_ct; i++) gr.push_back(Rot{key, g});
+            gr.push_back(Rot{need_key(evk, g), g});
         }
-        DevBuf R((size_t)cnt * ctw * 8, st);
-        rotate_each(c, level, cnt, G.u64() + batch, gr, R.u64(), st);
-        for (uint32_t j = 0; j + 1 < n2; j++) add_ct(c, level, 2 * n_ct, G.u64(), R.u64() + j * batch, G.u64(), st);
+        DevBuf R((size_t)(n2 - 1) * batch * 8, st);
+        rotate_each(c, level, n2 - 1, n_ct, G.u64() + batch, gr, R.u64(), st);
+        sum_ct(c, level, 2 * n_ct, R.u64(), batch, n2 - 1, R.u64(), st);
+        add_ct(c, level, 2 * n_ct, G.u64(), R.u64(), G.u64(), st);
     }
     // one rescale (lazy rescaling), then rotate-and-sum over the d_in / d_out blocks
     DevBuf Y((size_t)n_ct * 2 * level * n * 8, st), tmp((size_t)n_ct * 2 * level * n * 8, st);
@@ -501,4 +502,61 @@ DevBuf evaluate_batch(const hear_model *m, const hear_eval_keys *evk, size_t l0,
     return cur;
 }
 
+hear_model::Plan *graph_plan(const hear_model *m, const hear_eval_keys *evk, size_t l0, size_t l1, uint32_t n_ct,
+                             double scale_in, cudaStream_t st) {
+    for (auto &p : m->plans)
+        if (p->evk_serial == evk->serial && p->l0 == l0 && p->l1 == l1 && p->n_ct == n_ct && p->scale_in == scale_in) return p.get();
+    hear_context *c = m->ctx;
+    auto plan = std::make_unique<hear_model::Plan>();
+    plan->evk_serial = evk->serial;
+    plan->l0 = l0;
+    plan->l1 = l1;
+    plan->n_ct = n_ct;
+    plan->scale_in = scale_in;
+    const uint32_t lin = m->layers[l0].level_in;
+    plan->level_out = m->layers[l1 - 1].level_out;
+    const uint64_t in_words = (uint64_t)n_ct * 2 * (lin + 1) * c->n;
+    const uint64_t out_words = (uint64_t)n_ct * 2 * (plan->level_out + 1) * c->n;
+    plan->X = DevBuf(in_words * 8, nullptr);
+    plan->Y = DevBuf(out_words * 8, nullptr);
+    HEAR_CHECK_CUDA(cudaMemsetAsync(plan->X.p, 0, in_words * 8, st));
+    {   // direct run: builds every key-switch table the capture will need
+        uint32_t lo;
+        double so;
+        DevBuf y = evaluate_batch(m, evk, l0, l1, plan->X.u64(), n_ct, &lo, scale_in, &so, st);
+    }
+    HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
+    cudaStream_t cs;
+    HEAR_CHECK_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    const uint64_t launches0 = g_launches.load();
+    cudaGraph_t graph = nullptr;
+    HEAR_CHECK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    try {
+        uint32_t lo;
+        double so;
+        DevBuf y = evaluate_batch(m, evk, l0, l1, plan->X.u64(), n_ct, &lo, scale_in, &so, cs);
+        plan->scale_out = so;
+        HEAR_CHECK_CUDA(cudaMemcpyAsync(plan->Y.p, y.p, out_words * 8, cudaMemcpyDeviceToDevice, cs));
+    } catch (...) {
+        cudaStreamEndCapture(cs, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+        throw;
+    }
+    HEAR_CHECK_CUDA(cudaStreamEndCapture(cs, &graph));
+    plan->launches = g_launches.load() - launches0;
+    cudaError_t e = cudaGraphInstantiate(&plan->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    HEAR_CHECK_CUDA(e);
+    HEAR_CHECK_CUDA(cudaEventCreateWithFlags(&plan->done, cudaEventDisableTiming));
+    m->plans.push_back(std::move(plan));
+    return m->plans.back().get();
+}
+
 }  // namespace hear
+
+hear_model::Plan::~Plan() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (done) cudaEventDestroy(done);
+}

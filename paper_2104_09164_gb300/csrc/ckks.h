@@ -12,8 +12,7 @@
 struct hear_model {
     struct Fc {
         uint32_t d_out = 0, d_in = 0, D = 0, n1 = 0, n2 = 0, level = 0;
-        std::vector<hear::DevBuf> pts;              // [n2*n1] (empty buffer = no diagonal)
-        hear::DevBuf d_pt_ptrs;                     // device array of n2*n1 pointers (null = skip)
+        hear::DevBuf pts;                           // [n2*n1][level+1][N] Montgomery, zero = no diagonal
         hear::DevBuf bias;                          // plaintext at level-1 (Montgomery), or empty
         std::vector<int32_t> rotsum;                // slot steps of rotate-and-sum
     };
@@ -23,8 +22,23 @@ struct hear_model {
         Fc fc, fc2;                                 // FC; FC_SQ_FC: fc = W1, fc2 = collapsed U
         std::vector<int32_t> final_rotsum;          // FC_SQ_FC: sum over r
     };
+    // CUDA graph of one evaluation (layers [l0, l1) for n_ct ciphertexts with given keys and
+    // input scale), replayed from a fixed input/output workspace
+    struct Plan {
+        uint64_t evk_serial = 0;   // keys the graph reads (never reused after they are freed)
+        size_t l0 = 0, l1 = 0;
+        uint32_t n_ct = 0, level_out = 0;
+        double scale_in = 0, scale_out = 0;
+        hear::DevBuf X, Y;
+        cudaGraphExec_t exec = nullptr;
+        cudaEvent_t done = nullptr;
+        uint64_t launches = 0;
+        ~Plan();
+    };
     hear_context *ctx = nullptr;
     uint32_t clip_dim = 0, k = 0, M = 0;
+    mutable std::mutex plan_mu;
+    mutable std::vector<std::unique_ptr<Plan>> plans;
     std::vector<Layer> layers;
     std::vector<uint32_t> out_pos;
     std::vector<int32_t> rotations;
@@ -38,6 +52,7 @@ std::vector<uint64_t> make_cdt(double sigma);
 void build_context(hear_context *c, const hear_params_desc *d, int device);
 
 uint32_t galois_of(const hear_context *c, int64_t step);
+uint32_t galois_inverse(const hear_context *c, uint32_t g);
 
 // keygen / encryption / decryption
 void keygen(hear_context *c, uint64_t seed, const int32_t *steps, size_t n_steps, hear_secret_key **sk,
@@ -51,12 +66,13 @@ struct Rot {
     const uint64_t *key;
     uint32_t galois;
 };
-// out_r (batch) = rho(x) for each rotation r, sharing one ModUp of x's c1 (hoisting)
+// out[r*n_ct + c] = rho_r(x[c]) for every rotation r, sharing one ModUp of the c1 of each
+// x[c] (hoisting); out is contiguous [R][n_ct][2][level+1][N]
 void rotate_hoisted(hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *x,
-                    const std::vector<Rot> &rots, const std::vector<uint64_t *> &outs, cudaStream_t st);
-// out[c] = rho_{rot[c]}(x[c]): independent rotations of the n_ct ciphertexts of x
-void rotate_each(hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *x, const std::vector<Rot> &rots,
-                 uint64_t *out, cudaStream_t st);
+                    const std::vector<Rot> &rots, uint64_t *out, cudaStream_t st);
+// out[r*C + c] = rho_r(x[r*C + c]): job r rotates its C ciphertexts with rots[r]
+void rotate_each(hear_context *c, uint32_t level, uint32_t R, uint32_t C, const uint64_t *x,
+                 const std::vector<Rot> &rots, uint64_t *out, cudaStream_t st);
 // tensor + relinearise (no rescale): out [n_ct][2][level+1][N]
 void mul_relin(hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *a, const uint64_t *b,
                const uint64_t *relin_key, uint64_t *out, cudaStream_t st);
@@ -69,5 +85,9 @@ hear_model *model_create(hear_context *c, const hear_layer_desc *layers, size_t 
 // evaluate layers [l0, l1) on a batch x at the first layer's level; returns the output batch
 DevBuf evaluate_batch(const hear_model *m, const hear_eval_keys *evk, size_t l0, size_t l1, const uint64_t *x,
                       uint32_t n_ct, uint32_t *level_out, double scale_in, double *scale_out, cudaStream_t st);
+// graph plan for (evk, l0, l1, n_ct, scale_in): built on first use (one direct warm-up run,
+// then stream capture); the caller fills plan->X, launches plan->exec and reads plan->Y
+hear_model::Plan *graph_plan(const hear_model *m, const hear_eval_keys *evk, size_t l0, size_t l1, uint32_t n_ct,
+                             double scale_in, cudaStream_t st);
 
 }  // namespace hear

@@ -155,6 +155,11 @@ void build_context(hear_context *c, const hear_params_desc *d, int device) {
     c->sigma = d->sigma;
     HEAR_CHECK_CUDA(cudaSetDevice(device));
     HEAR_CHECK_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    // keep freed stream-ordered memory cached in this process's pool (the default threshold
+    // of zero hands it back at every synchronisation)
+    HEAR_CHECK_CUDA(cudaDeviceGetDefaultMemPool(&c->pool, device));
+    uint64_t keep = ~0ull;
+    HEAR_CHECK_CUDA(cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep));
 
     // ---- primes: largest unused prime below 2^bits that is 1 mod 2N, chain order
     std::vector<uint32_t> bits(d->q_bits, d->q_bits + d->n_q);

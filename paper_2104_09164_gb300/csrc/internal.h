@@ -117,6 +117,10 @@ struct hear_context {
     std::vector<std::unique_ptr<hear::LevelConsts>> levels;  // per level 0..L
     bool poisoned = false;
     mutable hear::Profiler prof;
+    // device tables of key-switching jobs (key pointers, galois elements), keyed by content;
+    // built outside stream capture and reused, so a captured evaluation uploads nothing
+    mutable std::mutex tab_mu;
+    mutable std::map<std::vector<uint64_t>, hear::DevBuf> job_tables;
     const hear::DevPrime *dev_primes() const { return static_cast<const hear::DevPrime *>(d_primes.p); }
     uint32_t nqp() const { return n_q + n_p; }
     uint32_t dnum(uint32_t level) const { return (level + 1 + alpha - 1) / alpha; }
@@ -136,6 +140,7 @@ struct hear_public_key {
 
 struct hear_eval_keys {
     hear_context *ctx = nullptr;
+    uint64_t serial = 0;           // unique per key set (graph plans are keyed by it)
     // galois element -> [dnum_max][2][n_q+n_p][N] NTT + Montgomery form; 1 = relin
     std::map<uint32_t, hear::DevBuf> keys;
     const uint64_t *key(uint32_t g) const {

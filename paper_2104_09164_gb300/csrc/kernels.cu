@@ -1,8 +1,9 @@
 // kernels.cu -- elementwise, sampling and basis-conversion kernels of RNS-CKKS on sm_103a.
 //
-// All kernels are HBM-streaming: one thread per 64-bit residue (grid-stride), coalesced
-// along the coefficient index.  The NTT domain ordering is that of ntt.cu: index i holds
-// the evaluation at psi^(2 brv(i) + 1).
+// Grids are 3-D: x covers the coefficient index of a limb (256 consecutive residues per
+// CTA, so every warp reads and writes 256 contiguous bytes), y and z cover limbs and
+// ciphertexts, so no thread ever divides a 64-bit index.  The NTT-domain ordering is that
+// of ntt.cu: index i holds the evaluation at psi^(2 brv(i) + 1).
 #include "kernels.cuh"
 #include "modarith.cuh"
 
@@ -11,15 +12,11 @@ namespace {
 
 constexpr int kBlock = 256;
 
-inline unsigned grid_for(uint64_t total) {
-    uint64_t g = (total + kBlock - 1) / kBlock;
-    return (unsigned)(g > 0x7fffffffULL ? 0x7fffffffULL : (g ? g : 1));
-}
+// grid for n coefficients x ny x nz; ny, nz <= 65535 is checked by the launchers
+inline dim3 grid3(uint32_t n, uint32_t ny, uint32_t nz) { return dim3(n / kBlock, ny, nz); }
+#define COEF() (blockIdx.x * kBlock + threadIdx.x)
 
-#define GRID_STRIDE(i, total) for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (total); \
-                                   i += (uint64_t)gridDim.x * blockDim.x)
-
-// NTT-domain index of sigma_g: out[i] = in[perm(i)]
+// NTT-domain index of sigma_g: (sigma_g a)[i] = a[auto_index(i, g)]
 __device__ __forceinline__ uint32_t auto_index(uint32_t i, uint32_t galois, uint32_t log_n) {
     const uint32_t n2 = 2u << log_n;
     uint32_t e = 2 * (__brev(i) >> (32 - log_n)) + 1;
@@ -27,50 +24,45 @@ __device__ __forceinline__ uint32_t auto_index(uint32_t i, uint32_t galois, uint
     return __brev((e2 - 1) >> 1) >> (32 - log_n);
 }
 
+// limb index of a LimbMap launch: y + z * gridDim.y
+__device__ __forceinline__ uint32_t limb_yz() { return blockIdx.y + blockIdx.z * gridDim.y; }
+
 // ------------------------------------------------------------------ representation
 __global__ void k_to_mont(uint64_t *d, uint32_t n_limbs, LimbMap m, const DevPrime *P, uint32_t n, int dir) {
-    GRID_STRIDE(i, (uint64_t)n_limbs * n) {
-        uint32_t b = (uint32_t)(i / n), k = (uint32_t)(i % n), pi;
-        if (!m.resolve(b, &pi)) continue;
-        const DevPrime p = P[pi];
-        uint64_t &x = d[m.offset(b, n) + k];
-        x = dir ? mont_mul(x, p.r2, p.q, p.qinv) : mont_mul(x, 1, p.q, p.qinv);
-    }
+    uint32_t b = limb_yz(), pi;
+    if (b >= n_limbs || !m.resolve(b, &pi)) return;
+    const DevPrime p = P[pi];
+    uint64_t &x = d[m.offset(b, n) + COEF()];
+    x = dir ? mont_mul(x, p.r2, p.q, p.qinv) : mont_mul(x, 1, p.q, p.qinv);
 }
 
 __global__ void k_pointwise_mont(const uint64_t *a, const uint64_t *b, uint64_t *out, uint32_t n_limbs, LimbMap m,
                                  const DevPrime *P, uint32_t n) {
-    GRID_STRIDE(i, (uint64_t)n_limbs * n) {
-        uint32_t bb = (uint32_t)(i / n), k = (uint32_t)(i % n), pi;
-        if (!m.resolve(bb, &pi)) continue;
-        const DevPrime p = P[pi];
-        uint64_t off = m.offset(bb, n) + k;
-        out[off] = mont_mul(a[off], b[off], p.q, p.qinv);
-    }
+    uint32_t bb = limb_yz(), pi;
+    if (bb >= n_limbs || !m.resolve(bb, &pi)) return;
+    const DevPrime p = P[pi];
+    uint64_t off = m.offset(bb, n) + COEF();
+    out[off] = mont_mul(a[off], b[off], p.q, p.qinv);
 }
 
 __global__ void k_small_to_limbs(const int8_t *e, uint64_t *out, uint32_t n_limbs, LimbMap m, const DevPrime *P,
                                  uint32_t n) {
-    GRID_STRIDE(i, (uint64_t)n_limbs * n) {
-        uint32_t b = (uint32_t)(i / n), k = (uint32_t)(i % n), pi;
-        if (!m.resolve(b, &pi)) continue;
-        int v = e[k];
-        uint64_t q = P[pi].q;
-        out[m.offset(b, n) + k] = v < 0 ? q - (uint64_t)(-v) : (uint64_t)v;
-    }
+    uint32_t b = limb_yz(), pi, k = COEF();
+    if (b >= n_limbs || !m.resolve(b, &pi)) return;
+    int v = e[k];
+    uint64_t q = P[pi].q;
+    out[m.offset(b, n) + k] = v < 0 ? q - (uint64_t)(-v) : (uint64_t)v;
 }
 
 __global__ void k_i64_to_limbs(const int64_t *v, uint64_t *out, uint32_t n_limbs, LimbMap m, const DevPrime *P,
                                uint32_t n) {
-    GRID_STRIDE(i, (uint64_t)n_limbs * n) {
-        uint32_t b = (uint32_t)(i / n), k = (uint32_t)(i % n), pi;
-        if (!m.resolve(b, &pi)) continue;
-        const DevPrime p = P[pi];
-        int64_t x = v[k];
-        uint64_t mag = x < 0 ? (uint64_t)0 - (uint64_t)x : (uint64_t)x;
-        uint64_t r = reduce64(mag, p);
-        out[m.offset(b, n) + k] = (x < 0) ? neg_mod(r, p.q) : r;
-    }
+    uint32_t b = limb_yz(), pi, k = COEF();
+    if (b >= n_limbs || !m.resolve(b, &pi)) return;
+    const DevPrime p = P[pi];
+    int64_t x = v[k];
+    uint64_t mag = x < 0 ? (uint64_t)0 - (uint64_t)x : (uint64_t)x;
+    uint64_t r = reduce64(mag, p);
+    out[m.offset(b, n) + k] = (x < 0) ? neg_mod(r, p.q) : r;
 }
 
 // ------------------------------------------------------------------ ChaCha20 (RFC 8439)
@@ -108,119 +100,116 @@ __device__ void chacha_words(uint64_t seed, uint32_t purpose, uint64_t index, ui
 
 __global__ void k_sample_small(uint64_t seed, uint32_t purpose, uint64_t index, uint32_t n, int kind,
                                const uint64_t *cdt, uint32_t cdt_n, int8_t *out) {
-    GRID_STRIDE(blk, (uint64_t)n / 8) {
-        uint64_t w[8];
-        chacha_words(seed, purpose, index, (uint32_t)blk, w);
+    uint32_t blk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (blk >= n / 8) return;
+    uint64_t w[8];
+    chacha_words(seed, purpose, index, blk, w);
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
-            int v;
-            if (kind == kTernary) {
-                v = (int)(w[j] % 3) - 1;
-            } else {
-                uint64_t u = w[j] >> 1;
-                int mag = 0;
-                while (mag + 1 < (int)cdt_n && !(u < cdt[mag])) mag++;
-                v = (w[j] & 1) ? -mag : mag;
-            }
-            out[blk * 8 + j] = (int8_t)v;
+    for (int j = 0; j < 8; j++) {
+        int v;
+        if (kind == kTernary) {
+            v = (int)(w[j] % 3) - 1;
+        } else {
+            uint64_t u = w[j] >> 1;
+            int mag = 0;
+            while (mag + 1 < (int)cdt_n && !(u < cdt[mag])) mag++;
+            v = (w[j] & 1) ? -mag : mag;
         }
+        out[blk * 8 + j] = (int8_t)v;
     }
 }
 
 // uniform residues: coefficient k of limb b is (w_{2k+1} 2^64 + w_{2k}) mod q, stream index
-// index_base | prime(b)
+// index_base | prime(b); one thread per ChaCha20 block (four coefficients)
 __global__ void k_sample_uniform(uint64_t seed, uint32_t purpose, uint64_t index_base, uint64_t *out,
                                  uint32_t n_limbs, LimbMap m, const DevPrime *P, uint32_t n) {
-    const uint32_t blocks_per_limb = n / 4;
-    GRID_STRIDE(i, (uint64_t)n_limbs * blocks_per_limb) {
-        uint32_t b = (uint32_t)(i / blocks_per_limb), blk = (uint32_t)(i % blocks_per_limb), pi;
-        if (!m.resolve(b, &pi)) continue;
-        const DevPrime p = P[pi];
-        uint64_t w[8];
-        chacha_words(seed, purpose, index_base | pi, blk, w);
-        uint64_t *o = out + m.offset(b, n) + (uint64_t)blk * 4;
+    uint32_t b = limb_yz(), pi, blk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_limbs || blk >= n / 4 || !m.resolve(b, &pi)) return;
+    const DevPrime p = P[pi];
+    uint64_t w[8];
+    chacha_words(seed, purpose, index_base | pi, blk, w);
+    uint64_t *o = out + m.offset(b, n) + (uint64_t)blk * 4;
 #pragma unroll
-        for (int j = 0; j < 4; j++) o[j] = barrett_reduce(u128{w[2 * j], w[2 * j + 1]}, p.q, p.ratio_hi, p.ratio_lo);
-    }
+    for (int j = 0; j < 4; j++) o[j] = barrett_reduce(u128{w[2 * j], w[2 * j + 1]}, p.q, p.ratio_hi, p.ratio_lo);
 }
 
 // ------------------------------------------------------------------ keys and encryption
+// y = limb (prime index == limb index in these layouts)
 __global__ void k_pk_combine(const uint64_t *a, const uint64_t *s_mont, const uint64_t *e, uint64_t *b,
-                             uint32_t n_q, const DevPrime *P, uint32_t n) {
-    GRID_STRIDE(i, (uint64_t)n_q * n) {
-        const DevPrime p = P[i / n];
-        uint64_t as = mont_mul(a[i], s_mont[i], p.q, p.qinv);
-        b[i] = sub_mod(e[i], as, p.q);
-    }
+                             const DevPrime *P, uint32_t n) {
+    const DevPrime p = P[blockIdx.y];
+    uint64_t i = (uint64_t)blockIdx.y * n + COEF();
+    b[i] = sub_mod(e[i], mont_mul(a[i], s_mont[i], p.q, p.qinv), p.q);
 }
 
 __global__ void k_swk_combine(const uint64_t *a, const uint64_t *s_mont, const uint64_t *e, const uint64_t *sp_mont,
-                              const uint64_t *p_mod, uint32_t lo, uint32_t hi, uint32_t nqp, const DevPrime *P,
-                              uint32_t n, uint64_t *b) {
-    GRID_STRIDE(i, (uint64_t)nqp * n) {
-        uint32_t t = (uint32_t)(i / n);
-        const DevPrime p = P[t];
-        uint64_t v = sub_mod(e[i], mont_mul(a[i], s_mont[i], p.q, p.qinv), p.q);
-        if (t >= lo && t < hi) v = add_mod(v, mont_mul(p_mod[t], sp_mont[i], p.q, p.qinv), p.q);
-        b[i] = v;
-    }
+                              const uint64_t *p_mod, uint32_t lo, uint32_t hi, const DevPrime *P, uint32_t n,
+                              uint64_t *b) {
+    const uint32_t t = blockIdx.y;
+    const DevPrime p = P[t];
+    uint64_t i = (uint64_t)t * n + COEF();
+    uint64_t v = sub_mod(e[i], mont_mul(a[i], s_mont[i], p.q, p.qinv), p.q);
+    if (t >= lo && t < hi) v = add_mod(v, mont_mul(p_mod[t], sp_mont[i], p.q, p.qinv), p.q);
+    b[i] = v;
 }
 
 __global__ void k_encrypt_combine(const uint64_t *v, const uint64_t *e0, const uint64_t *e1, const uint64_t *m,
-                                  const uint64_t *pk_mont, uint64_t *ct, uint32_t n_q, const DevPrime *P,
+                                  const uint64_t *pk_mont, uint64_t *ct, uint64_t limbs, const DevPrime *P,
                                   uint32_t n) {
-    const uint64_t limbs = (uint64_t)n_q * n;
-    GRID_STRIDE(i, limbs) {
-        const DevPrime p = P[i / n];
-        uint64_t c0 = add_mod(add_mod(mont_mul(v[i], pk_mont[i], p.q, p.qinv), e0[i], p.q), m[i], p.q);
-        uint64_t c1 = add_mod(mont_mul(v[i], pk_mont[limbs + i], p.q, p.qinv), e1[i], p.q);
-        ct[i] = c0;
-        ct[limbs + i] = c1;
-    }
+    const DevPrime p = P[blockIdx.y];
+    uint64_t i = (uint64_t)blockIdx.y * n + COEF();
+    ct[i] = add_mod(add_mod(mont_mul(v[i], pk_mont[i], p.q, p.qinv), e0[i], p.q), m[i], p.q);
+    ct[limbs + i] = add_mod(mont_mul(v[i], pk_mont[limbs + i], p.q, p.qinv), e1[i], p.q);
 }
 
-__global__ void k_decrypt_combine(const uint64_t *ct, const uint64_t *s_mont, uint64_t *out, uint32_t L1,
+__global__ void k_decrypt_combine(const uint64_t *ct, const uint64_t *s_mont, uint64_t *out, uint64_t limbs,
                                   const DevPrime *P, uint32_t n) {
-    const uint64_t limbs = (uint64_t)L1 * n;
-    GRID_STRIDE(i, limbs) {
-        const DevPrime p = P[i / n];
-        out[i] = add_mod(ct[i], mont_mul(ct[limbs + i], s_mont[i], p.q, p.qinv), p.q);
-    }
+    const DevPrime p = P[blockIdx.y];
+    uint64_t i = (uint64_t)blockIdx.y * n + COEF();
+    out[i] = add_mod(ct[i], mont_mul(ct[limbs + i], s_mont[i], p.q, p.qinv), p.q);
 }
 
 // ------------------------------------------------------------------ ciphertext arithmetic
-__global__ void k_add(const uint64_t *a, const uint64_t *b, uint64_t *out, uint32_t L1, uint64_t total,
+// y = limb t, z = polynomial
+__global__ void k_add(const uint64_t *a, const uint64_t *b, uint64_t *out, uint32_t L1, const DevPrime *P,
+                      uint32_t n) {
+    uint64_t i = ((uint64_t)blockIdx.z * L1 + blockIdx.y) * n + COEF();
+    out[i] = add_mod(a[i], b[i], P[blockIdx.y].q);
+}
+
+// out = a_0 + a_1 + ... + a_{cnt-1} (batches at stride `stride` words); y = limb, z = polynomial
+__global__ void k_sum(const uint64_t *a, uint64_t stride, uint32_t cnt, uint64_t *out, uint32_t L1,
                       const DevPrime *P, uint32_t n) {
-    GRID_STRIDE(i, total) {
-        uint32_t t = (uint32_t)((i / n) % L1);
-        out[i] = add_mod(a[i], b[i], P[t].q);
-    }
+    uint64_t i = ((uint64_t)blockIdx.z * L1 + blockIdx.y) * n + COEF();
+    const uint64_t q = P[blockIdx.y].q;
+    uint64_t s = a[i];
+    for (uint32_t j = 1; j < cnt; j++) s = add_mod(s, a[j * stride + i], q);
+    out[i] = s;
 }
 
-__global__ void k_tensor(const uint64_t *a, const uint64_t *b, uint64_t *out, uint32_t L1, uint32_t n_ct,
-                         const DevPrime *P, uint32_t n) {
-    const uint64_t plane = (uint64_t)L1 * n;
-    GRID_STRIDE(i, (uint64_t)n_ct * plane) {
-        uint64_t c = i / plane, r = i % plane;
-        const DevPrime p = P[r / n];
-        const uint64_t *ac = a + c * 2 * plane, *bc = b + c * 2 * plane;
-        uint64_t *oc = out + c * 3 * plane;
-        uint64_t a0 = ac[r], a1 = ac[plane + r], b0 = bc[r], b1 = bc[plane + r];
-        oc[r] = mul_mod(a0, b0, p);
-        u128 s = mul_wide(a0, b1);
-        add_to(s, mul_wide(a1, b0));
-        oc[plane + r] = barrett_reduce(s, p.q, p.ratio_hi, p.ratio_lo);
-        oc[2 * plane + r] = mul_mod(a1, b1, p);
-    }
+// y = limb t, z = ciphertext
+__global__ void k_tensor(const uint64_t *a, const uint64_t *b, uint64_t *out, uint32_t L1, const DevPrime *P,
+                         uint32_t n) {
+    const uint64_t plane = (uint64_t)L1 * n, c = blockIdx.z;
+    const uint64_t r = (uint64_t)blockIdx.y * n + COEF();
+    const DevPrime p = P[blockIdx.y];
+    const uint64_t *ac = a + c * 2 * plane, *bc = b + c * 2 * plane;
+    uint64_t *oc = out + c * 3 * plane;
+    uint64_t a0 = ac[r], a1 = ac[plane + r], b0 = bc[r], b1 = bc[plane + r];
+    oc[r] = mul_mod(a0, b0, p);
+    u128 s = mul_wide(a0, b1);
+    add_to(s, mul_wide(a1, b0));
+    oc[plane + r] = barrett_reduce(s, p.q, p.ratio_hi, p.ratio_lo);
+    oc[2 * plane + r] = mul_mod(a1, b1, p);
 }
 
-__global__ void k_automorphism(const uint64_t *in, uint64_t *out, uint64_t total, uint32_t galois, uint32_t log_n) {
-    const uint32_t n = 1u << log_n;
-    GRID_STRIDE(i, total) {
-        uint64_t base = i & ~(uint64_t)(n - 1);
-        uint32_t k = (uint32_t)(i & (n - 1));
-        out[i] = in[base + auto_index(k, galois, log_n)];
-    }
+// y + z * gridDim.y = limb of the whole batch
+__global__ void k_automorphism(const uint64_t *in, uint64_t *out, uint32_t n_limbs, uint32_t galois,
+                               uint32_t log_n) {
+    uint32_t b = limb_yz(), k = COEF();
+    if (b >= n_limbs) return;
+    const uint64_t base = (uint64_t)b << log_n;
+    out[base + k] = in[base + auto_index(k, galois, log_n)];
 }
 
 // lazily accumulate x*y into acc keeping acc.hi < q (so the final Montgomery reduce is valid)
@@ -229,315 +218,422 @@ __device__ __forceinline__ void mac_lazy(u128 &acc, uint64_t x, uint64_t y, uint
     if (acc.hi >= q) acc.hi -= q;
 }
 
-template <int JB>
-__global__ void k_lincomb(uint32_t L1, uint32_t n_ct, uint32_t n_in, uint32_t n_out, uint32_t j0,
-                          const uint64_t *const *in, const uint64_t *const *pt, uint64_t *const *out,
-                          const DevPrime *P, uint32_t n) {
-    const uint64_t plane = (uint64_t)L1 * n;          // one polynomial
-    GRID_STRIDE(i, (uint64_t)n_ct * plane) {
-        uint64_t c = i / plane, r = i % plane;
-        const DevPrime p = P[r / n];
-        u128 acc0[JB], acc1[JB];
+// BSGS inner sums out[j][c] = sum_b pt[j][b] (.) baby[b][c] on contiguous storage:
+// baby [n1][C][2][L1][N], pt [n2*n1][L1][N] (Montgomery), out [n2][C][2][L1][N].
+// CTA = 8 warps, each one polynomial (c, poly) of the batch; lanes over 32 consecutive
+// coefficients.  Grid x = group of 8 polynomials (fastest), y = coefficient tile, z = limb:
+// all CTAs of one (limb, tile) run back to back, so the plaintext tile they share comes
+// from HBM once and from L2 (and, within a CTA, L1) afterwards.  Each thread walks the
+// giant steps in chunks of four accumulators; its baby words stay in L1/L2 across chunks.
+__global__ void __launch_bounds__(256, 4) k_lincomb(uint32_t L1, uint32_t C, uint32_t n1, uint32_t n2,
+                                                 const uint64_t *__restrict__ baby, const uint64_t *__restrict__ pt,
+                                                 uint64_t *__restrict__ out, const DevPrime *P, uint32_t n) {
+    const uint32_t cp = blockIdx.x * 8 + (threadIdx.x >> 5);   // c * 2 + poly
+    if (cp >= 2 * C) return;
+    const uint32_t t = blockIdx.z, k = blockIdx.y * 32 + (threadIdx.x & 31);
+    const uint64_t plane = (uint64_t)L1 * n, r = (uint64_t)t * n + k;
+    const uint64_t q = P[t].q, qinv = P[t].qinv;
+    const uint64_t bstride = 2ull * C * plane;                    // between baby steps / giant outputs
+    const uint64_t *bp = baby + (uint64_t)cp * plane + r;
+    for (uint32_t j0 = 0; j0 < n2; j0 += 4) {
+        u128 acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+        const uint64_t *pp = pt + ((uint64_t)j0 * n1) * plane + r;
+        const uint32_t jn = min(4u, n2 - j0);
+        uint32_t b = 0;
+        // two baby steps per iteration: ten independent loads in flight per thread
+        for (; b + 2 <= n1; b += 2) {
+            const uint64_t x0 = bp[(uint64_t)b * bstride], x1 = bp[(uint64_t)(b + 1) * bstride];
+            uint64_t w0[4], w1[4];
 #pragma unroll
-        for (int jj = 0; jj < JB; jj++) acc0[jj] = acc1[jj] = u128{0, 0};
-        for (uint32_t b = 0; b < n_in; b++) {
-            const uint64_t *src = in[b] + c * 2 * plane;
-            uint64_t x0 = src[r], x1 = src[plane + r];
+            for (int jj = 0; jj < 4; jj++) {
+                if (jj < (int)jn) {
+                    w0[jj] = __ldg(pp + ((uint64_t)jj * n1 + b) * plane);
+                    w1[jj] = __ldg(pp + ((uint64_t)jj * n1 + b + 1) * plane);
+                }
+            }
 #pragma unroll
-            for (int jj = 0; jj < JB; jj++) {
-                uint32_t j = j0 + jj;
-                if (j >= n_out) break;
-                const uint64_t *w = pt[j * n_in + b];
-                if (!w) continue;
-                uint64_t wv = w[r];
-                mac_lazy(acc0[jj], x0, wv, p.q);
-                mac_lazy(acc1[jj], x1, wv, p.q);
+            for (int jj = 0; jj < 4; jj++) {
+                if (jj < (int)jn) {
+                    mac_lazy(acc[jj], x0, w0[jj], q);
+                    mac_lazy(acc[jj], x1, w1[jj], q);
+                }
             }
         }
+        for (; b < n1; b++) {
+            const uint64_t x = bp[(uint64_t)b * bstride];
 #pragma unroll
-        for (int jj = 0; jj < JB; jj++) {
-            uint32_t j = j0 + jj;
-            if (j >= n_out) break;
-            uint64_t *dst = out[j] + c * 2 * plane;
-            dst[r] = mont_reduce(acc0[jj], p.q, p.qinv);
-            dst[plane + r] = mont_reduce(acc1[jj], p.q, p.qinv);
+            for (int jj = 0; jj < 4; jj++)
+                if (jj < (int)jn) mac_lazy(acc[jj], x, __ldg(pp + ((uint64_t)jj * n1 + b) * plane), q);
         }
+        uint64_t *op = out + (uint64_t)j0 * bstride + (uint64_t)cp * plane + r;
+#pragma unroll
+        for (int jj = 0; jj < 4; jj++)
+            if (j0 + jj < n2) op[(uint64_t)jj * bstride] = mont_reduce(acc[jj], q, qinv);
     }
 }
 
-__global__ void k_mulplain(const uint64_t *ct, const uint64_t *pt, uint64_t *out, uint32_t L1, uint32_t n_ct,
-                           const DevPrime *P, uint32_t n) {
-    const uint64_t plane = (uint64_t)L1 * n;
-    GRID_STRIDE(i, (uint64_t)n_ct * 2 * plane) {
-        uint64_t r = i % plane;
-        const DevPrime p = P[r / n];
-        out[i] = mont_mul(ct[i], pt[r], p.q, p.qinv);
-    }
+// y = poly*L1 + limb, z = ciphertext
+__global__ void k_mulplain(const uint64_t *ct, const uint64_t *pt, uint64_t *out, uint32_t L1, const DevPrime *P,
+                           uint32_t n) {
+    const uint32_t t = blockIdx.y % L1;
+    const DevPrime p = P[t];
+    const uint64_t i = ((uint64_t)blockIdx.z * 2 * L1 + blockIdx.y) * n + COEF();
+    out[i] = mont_mul(ct[i], pt[(uint64_t)t * n + COEF()], p.q, p.qinv);
 }
 
 // ------------------------------------------------------------------ key switching
-// ext[c][j][t][k]: limbs t in I_j copy c1 (NTT domain); other limbs get the basis
-// conversion of the (scaled) coefficient-domain digit limbs y (NTT applied afterwards).
+// ModUp conversion, one thread per (ciphertext c = z, digit j = y, coefficient): the
+// digit's alpha residues y_i = a_i * qhat_inv_i are formed once, then every target limb t
+// outside the digit receives sum_i y_i * [Q_j/q_i]_t mod t; the digit's own limbs copy c1
+// (NTT domain).
 __global__ void k_modup_conv(const uint64_t *c1, uint64_t c1_stride, const uint64_t *y, uint64_t *ext,
                              uint32_t L1, uint32_t W, uint32_t dnum, uint32_t alpha, uint32_t n_q,
-                             const uint64_t *qhat_inv, const uint64_t *qhat_mod, const DevPrime *P, uint32_t n,
-                             uint32_t n_ct) {
-    GRID_STRIDE(i, (uint64_t)n_ct * dnum * W * n) {
-        uint32_t k = (uint32_t)(i % n);
-        uint64_t rest = i / n;
-        uint32_t t = (uint32_t)(rest % W);
-        rest /= W;
-        uint32_t j = (uint32_t)(rest % dnum);
-        uint32_t c = (uint32_t)(rest / dnum);
-        uint32_t lo = j * alpha, hi = min(lo + alpha, L1);
-        if (t >= lo && t < hi) {
-            ext[i] = c1[c * c1_stride + (uint64_t)t * n + k];
-            continue;
-        }
-        uint32_t pt = t < L1 ? t : n_q + (t - L1);
-        const DevPrime p = P[pt];
-        uint64_t acc = 0;
-        for (uint32_t src = lo; src < hi; src++) {
+                             const uint64_t *qhat_inv, const uint64_t *qhat_mod, const DevPrime *P, uint32_t n) {
+    const uint32_t k = COEF(), j = blockIdx.y, c = blockIdx.z;
+    const uint32_t lo = j * alpha, hi = min(lo + alpha, L1);
+    uint64_t *e = ext + ((uint64_t)c * dnum + j) * W * n + k;
+    uint64_t ys[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int ii = 0; ii < 4; ii++) {
+        const uint32_t src = lo + ii;
+        if (src < hi) {
             const DevPrime ps = P[src];
-            uint64_t a = y[((uint64_t)c * L1 + src) * n + k];
-            uint64_t yi = shoup(a, qhat_inv[2 * src], qhat_inv[2 * src + 1], ps.q);
-            const uint64_t *wm = qhat_mod + 2 * (((uint64_t)j * alpha + (src - lo)) * W + t);
-            acc = add_mod(acc, shoup(yi, wm[0], wm[1], p.q), p.q);
+            ys[ii] = shoup(y[((uint64_t)c * L1 + src) * n + k], qhat_inv[2 * src], qhat_inv[2 * src + 1], ps.q);
+            e[(uint64_t)src * n] = c1[c * c1_stride + (uint64_t)src * n + k];
         }
-        ext[i] = acc;
+    }
+    for (uint32_t t = 0; t < W; t++) {
+        if (t >= lo && t < hi) continue;
+        const uint32_t pt = t < L1 ? t : n_q + (t - L1);
+        const uint64_t q = P[pt].q;
+        uint64_t acc = 0;
+#pragma unroll
+        for (int ii = 0; ii < 4; ii++) {
+            if (lo + ii >= hi) break;
+            const uint64_t *wm = qhat_mod + 2 * (((uint64_t)j * alpha + ii) * W + t);
+            acc = add_mod(acc, shoup(ys[ii], wm[0], wm[1], q), q);
+        }
+        e[(uint64_t)t * n] = acc;
     }
 }
 
-__global__ void k_ks_inner(const uint64_t *ext, const uint64_t *const *keys, const uint32_t *galois,
-                           uint64_t *out, uint32_t L1, uint32_t W, uint32_t dnum, uint32_t n_q, uint32_t nqp,
-                           uint32_t log_n, const DevPrime *P, uint32_t n_ct) {
-    const uint32_t n = 1u << log_n;
-    GRID_STRIDE(i, (uint64_t)n_ct * W * n) {
-        uint32_t k = (uint32_t)(i % n);
-        uint32_t t = (uint32_t)((i / n) % W);
-        uint32_t c = (uint32_t)(i / ((uint64_t)W * n));
-        uint32_t pt = t < L1 ? t : n_q + (t - L1);
-        const DevPrime p = P[pt];
-        uint32_t g = galois ? galois[c] : 1u;
-        uint32_t kk = g == 1 ? k : auto_index(k, g, log_n);
-        const uint64_t *key = keys[c];
-        const uint64_t key_plane = (uint64_t)nqp * n;
+// Key inner product for R jobs of C ciphertexts.  Job r uses the switching key keys[r],
+// stored sigma_{g_r}^{-1}-permuted, so sum_j ext_j[k] key'_j[k] is formed with coalesced
+// reads and written to position sigma_{g_r}^{-1}(k) of the output, which equals
+// sum_j sigma_{g_r}(ext_j) (.) key_j (the automorphism applied to the extended digits).
+// The 2*dnum key words of a coefficient are loaded once and reused for all C ciphertexts.
+// y = limb t of Q_l u P.
+template <int MAXD>
+__global__ void __launch_bounds__(256, 3) k_ks_inner(const uint64_t *ext, int ext_per_job, const uint64_t *const *keys, const uint32_t *ginv,
+                           uint64_t *out, uint32_t C, uint32_t L1, uint32_t W, uint32_t dnum, uint32_t n_q,
+                           uint32_t nqp, uint32_t log_n, const DevPrime *P) {
+    // grid y = job (varies before the limb, so the jobs of one limb run together and
+    // share that limb's digit slice in L2), z = limb t of Q_l u P
+    const uint32_t n = 1u << log_n, k = COEF(), r = blockIdx.y, t = blockIdx.z;
+    const uint32_t pt = t < L1 ? t : n_q + (t - L1);
+    const uint64_t q = P[pt].q, qinv = P[pt].qinv;
+    const uint64_t key_plane = (uint64_t)nqp * n;
+    const uint64_t *key = keys[r] + (uint64_t)pt * n + k;
+    uint64_t k0[MAXD], k1[MAXD];
+#pragma unroll
+    for (int j = 0; j < MAXD; j++) {
+        if (j < (int)dnum) {
+            k0[j] = __ldg(key + (uint64_t)j * 2 * key_plane);
+            k1[j] = __ldg(key + (uint64_t)j * 2 * key_plane + key_plane);
+        }
+    }
+    const uint32_t g = ginv[r];
+    const uint32_t kk = g == 1 ? k : auto_index(k, g, log_n);
+    const uint64_t ext_ct = (uint64_t)dnum * W * n, out_ct = 2ull * W * n;
+    for (uint32_t c = 0; c < C; c++) {
+        const uint64_t *e = ext + (ext_per_job ? (uint64_t)r * C + c : c) * ext_ct + (uint64_t)t * n + k;
+        uint64_t xs[MAXD];
+#pragma unroll
+        for (int j = 0; j < MAXD; j++)      // all digit loads issued before the products
+            if (j < (int)dnum) xs[j] = e[(uint64_t)j * W * n];
         u128 a0{0, 0}, a1{0, 0};
-        for (uint32_t j = 0; j < dnum; j++) {
-            uint64_t x = ext[(((uint64_t)c * dnum + j) * W + t) * n + kk];
-            const uint64_t *kj = key + (uint64_t)j * 2 * key_plane + (uint64_t)pt * n + k;
-            mac_lazy(a0, x, kj[0], p.q);
-            mac_lazy(a1, x, kj[key_plane], p.q);
+#pragma unroll
+        for (int j = 0; j < MAXD; j++) {
+            if (j < (int)dnum) {
+                mac_lazy(a0, xs[j], k0[j], q);
+                mac_lazy(a1, xs[j], k1[j], q);
+            }
         }
-        uint64_t *o = out + (uint64_t)c * 2 * W * n + (uint64_t)t * n + k;
-        o[0] = mont_reduce(a0, p.q, p.qinv);
-        o[(uint64_t)W * n] = mont_reduce(a1, p.q, p.qinv);
+        uint64_t *o = out + ((uint64_t)r * C + c) * out_ct + (uint64_t)t * n + kk;
+        o[0] = mont_reduce(a0, q, qinv);
+        o[(uint64_t)W * n] = mont_reduce(a1, q, qinv);
     }
 }
 
-// conv_i = sum_k [x_{p_k} * phat_inv_k]_{p_k} * phat_mod[k][i] mod q_i (x_P coefficient domain)
-__global__ void k_moddown_conv(const uint64_t *acc, uint64_t *tmp, uint32_t L1, uint32_t W, uint32_t K,
-                               uint32_t n_q, const uint64_t *phat_inv, const uint64_t *phat_mod,
-                               const DevPrime *P, uint32_t n, uint32_t n_groups) {
-    GRID_STRIDE(i, (uint64_t)n_groups * L1 * n) {
-        uint32_t k = (uint32_t)(i % n);
-        uint32_t t = (uint32_t)((i / n) % L1);
-        uint32_t g = (uint32_t)(i / ((uint64_t)L1 * n));
-        const DevPrime p = P[t];
-        uint64_t s = 0;
-        for (uint32_t kk = 0; kk < K; kk++) {
+// ModDown conversion, one thread per (group = y + z*gridDim.y, coefficient):
+// y_k = [x_{p_k} * phat_inv_k]_{p_k} once, conv_i = sum_k y_k * [P/p_k]_{q_i} mod q_i for
+// every i < L1 (x_P in the coefficient domain).
+__global__ void k_moddown_conv(const uint64_t *acc, uint64_t *tmp, uint32_t n_groups, uint32_t L1, uint32_t W,
+                               uint32_t K, uint32_t n_q, const uint64_t *phat_inv, const uint64_t *phat_mod,
+                               const DevPrime *P, uint32_t n) {
+    const uint32_t g = limb_yz(), k = COEF();
+    if (g >= n_groups) return;
+    uint64_t ys[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int kk = 0; kk < 4; kk++) {
+        if (kk < (int)K) {
             const DevPrime pk = P[n_q + kk];
-            uint64_t x = acc[((uint64_t)g * W + L1 + kk) * n + k];
-            uint64_t y = shoup(x, phat_inv[2 * kk], phat_inv[2 * kk + 1], pk.q);
-            const uint64_t *w = phat_mod + 2 * ((uint64_t)kk * L1 + t);
-            s = add_mod(s, shoup(y, w[0], w[1], p.q), p.q);
+            ys[kk] = shoup(acc[((uint64_t)g * W + L1 + kk) * n + k], phat_inv[2 * kk], phat_inv[2 * kk + 1], pk.q);
         }
-        tmp[i] = s;
+    }
+    for (uint32_t t = 0; t < L1; t++) {
+        const uint64_t q = P[t].q;
+        uint64_t s = 0;
+#pragma unroll
+        for (int kk = 0; kk < 4; kk++) {
+            if (kk < (int)K) {
+                const uint64_t *w = phat_mod + 2 * ((uint64_t)kk * L1 + t);
+                s = add_mod(s, shoup(ys[kk], w[0], w[1], q), q);
+            }
+        }
+        tmp[((uint64_t)g * L1 + t) * n + k] = s;
     }
 }
 
+// out = (x_i - conv_i) * P^-1 (+ addend gathered through sigma_g); y = limb, z = group
 __global__ void k_moddown_combine(const uint64_t *acc, const uint64_t *tmp, uint64_t *out, const uint64_t *addend,
-                                  uint64_t add_stride, uint32_t add_mask, const uint32_t *galois, uint32_t L1, uint32_t W,
-                                  const uint64_t *p_inv, const DevPrime *P, uint32_t log_n, uint32_t n_groups) {
-    const uint32_t n = 1u << log_n;
-    GRID_STRIDE(i, (uint64_t)n_groups * L1 * n) {
-        uint32_t k = (uint32_t)(i % n);
-        uint32_t t = (uint32_t)((i / n) % L1);
-        uint32_t g = (uint32_t)(i / ((uint64_t)L1 * n));
-        const DevPrime p = P[t];
-        uint64_t x = acc[((uint64_t)g * W + t) * n + k];
-        uint64_t v = shoup(x + p.q - tmp[i], p_inv[2 * t], p_inv[2 * t + 1], p.q);
-        uint32_t poly = g & 1, c = g >> 1;
-        if (addend && (add_mask >> poly & 1)) {
-            uint32_t gal = galois ? galois[c] : 1u;
-            uint32_t kk = gal == 1 ? k : auto_index(k, gal, log_n);
-            v = add_mod(v, addend[(uint64_t)c * add_stride + ((uint64_t)poly * L1 + t) * n + kk], p.q);
-        }
-        out[i] = v;
+                                  uint64_t add_stride, uint32_t add_mask, uint32_t add_shared, const uint32_t *gal,
+                                  uint32_t cts_per_job, uint32_t L1, uint32_t W, const uint64_t *p_inv,
+                                  const DevPrime *P, uint32_t log_n) {
+    const uint32_t n = 1u << log_n, k = COEF(), t = blockIdx.y, g = blockIdx.z;
+    const DevPrime p = P[t];
+    const uint64_t i = ((uint64_t)g * L1 + t) * n + k;
+    const uint64_t x = acc[((uint64_t)g * W + t) * n + k];
+    uint64_t v = shoup(x + p.q - tmp[i], p_inv[2 * t], p_inv[2 * t + 1], p.q);
+    const uint32_t poly = g & 1, c = g >> 1;
+    if (addend && (add_mask >> poly & 1)) {
+        const uint32_t ga = gal ? gal[c / cts_per_job] : 1u;
+        const uint32_t kk = ga == 1 ? k : auto_index(k, ga, log_n);
+        const uint32_t ac = add_shared ? c % cts_per_job : c;
+        v = add_mod(v, addend[(uint64_t)ac * add_stride + ((uint64_t)poly * L1 + t) * n + kk], p.q);
     }
+    out[i] = v;
 }
 
-// w_i = [c_l]_centred mod q_i for the coefficient-domain last limb c_l
-__global__ void k_rescale_lift(const uint64_t *in, uint64_t *tmp, uint32_t L1, const DevPrime *P, uint32_t n,
-                               uint32_t n_polys) {
+// w_i = [c_l]_centred mod q_i for every i < l, from the coefficient-domain last limb;
+// one thread per (polynomial = y + z*gridDim.y, coefficient)
+__global__ void k_rescale_lift(const uint64_t *in, uint64_t *tmp, uint32_t n_polys, uint32_t L1, const DevPrime *P,
+                               uint32_t n) {
+    const uint32_t g = limb_yz(), k = COEF();
+    if (g >= n_polys) return;
     const uint32_t l = L1 - 1;
     const uint64_t ql = P[l].q, half = (ql - 1) / 2;
-    GRID_STRIDE(i, (uint64_t)n_polys * l * n) {
-        uint32_t k = (uint32_t)(i % n);
-        uint32_t t = (uint32_t)((i / n) % l);
-        uint32_t g = (uint32_t)(i / ((uint64_t)l * n));
+    const uint64_t v = in[((uint64_t)g * L1 + l) * n + k];
+    const bool neg = v > half;
+    const uint64_t mag = neg ? ql - v : v;
+    for (uint32_t t = 0; t < l; t++) {
         const DevPrime p = P[t];
-        uint64_t v = in[((uint64_t)g * L1 + l) * n + k];
-        uint64_t w;
-        if (v > half) w = neg_mod(reduce64(ql - v, p), p.q);
-        else w = reduce64(v, p);
-        tmp[i] = w;
+        const uint64_t r = reduce64(mag, p);
+        tmp[((uint64_t)g * l + t) * n + k] = neg ? neg_mod(r, p.q) : r;
     }
 }
 
+// y = limb t < l, z = polynomial
 __global__ void k_rescale_combine(const uint64_t *in, const uint64_t *tmp, uint64_t *out, uint32_t L1,
-                                  const uint64_t *ql_inv, const DevPrime *P, uint32_t n, uint32_t n_polys) {
-    const uint32_t l = L1 - 1;
-    GRID_STRIDE(i, (uint64_t)n_polys * l * n) {
-        uint32_t k = (uint32_t)(i % n);
-        uint32_t t = (uint32_t)((i / n) % l);
-        uint32_t g = (uint32_t)(i / ((uint64_t)l * n));
-        const DevPrime p = P[t];
-        uint64_t x = in[((uint64_t)g * L1 + t) * n + k];
-        out[i] = shoup(x + p.q - tmp[i], ql_inv[2 * t], ql_inv[2 * t + 1], p.q);
-    }
+                                  const uint64_t *ql_inv, const DevPrime *P, uint32_t n) {
+    const uint32_t l = L1 - 1, k = COEF(), t = blockIdx.y, g = blockIdx.z;
+    const DevPrime p = P[t];
+    const uint64_t i = ((uint64_t)g * l + t) * n + k;
+    const uint64_t x = in[((uint64_t)g * L1 + t) * n + k];
+    out[i] = shoup(x + p.q - tmp[i], ql_inv[2 * t], ql_inv[2 * t + 1], p.q);
+}
+
+// split a count over grid y/z (y <= 65535)
+inline void split_yz(uint32_t count, uint32_t &ny, uint32_t &nz) {
+    if (count == 0) throw Error(HEAR_E_INVAL, "empty launch");
+    ny = count < 65535 ? count : 65535;
+    nz = (count + ny - 1) / ny;
+    if (nz > 65535) throw Error(HEAR_E_UNSUPPORTED, "launch too large");
+}
+
+void check_yz(uint32_t y, uint32_t z) {
+    if (y == 0 || z == 0) throw Error(HEAR_E_INVAL, "empty launch");
+    if (y > 65535 || z > 65535) throw Error(HEAR_E_UNSUPPORTED, "launch too large");
 }
 
 }  // namespace
 
-// launch with the profiler bracket; the stage name is the kernel's, the algorithmic bytes
-// are those of one residue read or written per element unless a launcher says otherwise
-#define LAUNCH_B(kernel, total, st, bytes, ...)                                           \
+// launch with the profiler bracket; the stage name is the kernel's, `bytes` its algorithmic
+// HBM traffic (each residue it must read or write, once)
+#define LAUNCH3(kernel, grid, block, st, bytes, ...)                                      \
     do {                                                                                  \
         ProfScope ps__(c, #kernel, st, (double)(bytes));                                   \
-        kernel<<<grid_for(total), kBlock, 0, st>>>(__VA_ARGS__);                           \
+        kernel<<<grid, block, 0, st>>>(__VA_ARGS__);                                       \
         HEAR_CHECK_CUDA(cudaGetLastError());                                               \
     } while (0)
-#define LAUNCH(kernel, total, st, ...) LAUNCH_B(kernel, total, st, 16.0 * (double)(total), __VA_ARGS__)
 
 void to_mont(const hear_context *c, uint64_t *d, uint32_t n_limbs, LimbMap m, cudaStream_t s) {
-    LAUNCH(k_to_mont, (uint64_t)n_limbs * c->n, s, d, n_limbs, m, c->dev_primes(), c->n, 1);
+    uint32_t ny, nz;
+    split_yz(n_limbs, ny, nz);
+    LAUNCH3(k_to_mont, grid3(c->n, ny, nz), kBlock, s, 16.0 * n_limbs * c->n, d, n_limbs, m, c->dev_primes(), c->n, 1);
 }
 void from_mont(const hear_context *c, uint64_t *d, uint32_t n_limbs, LimbMap m, cudaStream_t s) {
-    LAUNCH(k_to_mont, (uint64_t)n_limbs * c->n, s, d, n_limbs, m, c->dev_primes(), c->n, 0);
+    uint32_t ny, nz;
+    split_yz(n_limbs, ny, nz);
+    LAUNCH3(k_to_mont, grid3(c->n, ny, nz), kBlock, s, 16.0 * n_limbs * c->n, d, n_limbs, m, c->dev_primes(), c->n, 0);
 }
 void pointwise_mont(const hear_context *c, uint32_t n_limbs, LimbMap m, const uint64_t *a, const uint64_t *b_mont,
                     uint64_t *out, cudaStream_t st) {
-    LAUNCH(k_pointwise_mont, (uint64_t)n_limbs * c->n, st, a, b_mont, out, n_limbs, m, c->dev_primes(), c->n);
+    uint32_t ny, nz;
+    split_yz(n_limbs, ny, nz);
+    LAUNCH3(k_pointwise_mont, grid3(c->n, ny, nz), kBlock, st, 24.0 * n_limbs * c->n, a, b_mont, out, n_limbs, m,
+            c->dev_primes(), c->n);
 }
 void small_to_limbs(const hear_context *c, const int8_t *e, uint64_t *out, uint32_t n_limbs, LimbMap m,
                     cudaStream_t s) {
-    LAUNCH(k_small_to_limbs, (uint64_t)n_limbs * c->n, s, e, out, n_limbs, m, c->dev_primes(), c->n);
+    uint32_t ny, nz;
+    split_yz(n_limbs, ny, nz);
+    LAUNCH3(k_small_to_limbs, grid3(c->n, ny, nz), kBlock, s, 8.0 * n_limbs * c->n, e, out, n_limbs, m,
+            c->dev_primes(), c->n);
 }
 void i64_to_limbs(const hear_context *c, const int64_t *v, uint64_t *out, uint32_t n_limbs, LimbMap m,
                   cudaStream_t s) {
-    LAUNCH(k_i64_to_limbs, (uint64_t)n_limbs * c->n, s, v, out, n_limbs, m, c->dev_primes(), c->n);
+    uint32_t ny, nz;
+    split_yz(n_limbs, ny, nz);
+    LAUNCH3(k_i64_to_limbs, grid3(c->n, ny, nz), kBlock, s, 8.0 * n_limbs * c->n, v, out, n_limbs, m,
+            c->dev_primes(), c->n);
 }
 void sample_small(const hear_context *c, uint64_t seed, uint32_t purpose, uint64_t index, SmallKind kind,
                   int8_t *out, cudaStream_t s) {
-    LAUNCH(k_sample_small, (uint64_t)c->n / 8, s, seed, purpose, index, c->n, (int)kind, c->d_cdt.u64(),
-           (uint32_t)c->cdt.size(), out);
+    LAUNCH3(k_sample_small, dim3((c->n / 8 + kBlock - 1) / kBlock), kBlock, s, (double)c->n, seed, purpose, index,
+            c->n, (int)kind, c->d_cdt.u64(), (uint32_t)c->cdt.size(), out);
 }
 void sample_uniform(const hear_context *c, uint64_t seed, uint32_t purpose, uint64_t index_base, uint64_t *out,
                     uint32_t n_limbs, LimbMap m, cudaStream_t s) {
-    LAUNCH(k_sample_uniform, (uint64_t)n_limbs * (c->n / 4), s, seed, purpose, index_base, out, n_limbs, m,
-           c->dev_primes(), c->n);
+    uint32_t ny, nz;
+    split_yz(n_limbs, ny, nz);
+    LAUNCH3(k_sample_uniform, dim3((c->n / 4 + kBlock - 1) / kBlock, ny, nz), kBlock, s, 8.0 * n_limbs * c->n, seed,
+            purpose, index_base, out, n_limbs, m, c->dev_primes(), c->n);
 }
 void pk_combine(const hear_context *c, const uint64_t *a, const uint64_t *s_mont, const uint64_t *e, uint64_t *b,
                 cudaStream_t st) {
-    LAUNCH(k_pk_combine, (uint64_t)c->n_q * c->n, st, a, s_mont, e, b, c->n_q, c->dev_primes(), c->n);
+    LAUNCH3(k_pk_combine, grid3(c->n, c->n_q, 1), kBlock, st, 32.0 * c->n_q * c->n, a, s_mont, e, b,
+            c->dev_primes(), c->n);
 }
 void swk_combine(const hear_context *c, const uint64_t *a, const uint64_t *s_mont, const uint64_t *e,
                  const uint64_t *sp_mont, const uint64_t *p_mod, uint32_t digit, uint64_t *b, cudaStream_t st) {
     uint32_t lo = digit * c->alpha, hi = std::min(lo + c->alpha, c->n_q);
-    LAUNCH(k_swk_combine, (uint64_t)c->nqp() * c->n, st, a, s_mont, e, sp_mont, p_mod, lo, hi, c->nqp(),
-           c->dev_primes(), c->n, b);
+    LAUNCH3(k_swk_combine, grid3(c->n, c->nqp(), 1), kBlock, st, 40.0 * c->nqp() * c->n, a, s_mont, e, sp_mont,
+            p_mod, lo, hi, c->dev_primes(), c->n, b);
 }
 void encrypt_combine(const hear_context *c, const uint64_t *v, const uint64_t *e0, const uint64_t *e1,
                      const uint64_t *m, const uint64_t *pk_mont, uint64_t *ct, cudaStream_t st) {
-    LAUNCH(k_encrypt_combine, (uint64_t)c->n_q * c->n, st, v, e0, e1, m, pk_mont, ct, c->n_q, c->dev_primes(),
-           c->n);
+    const uint64_t limbs = (uint64_t)c->n_q * c->n;
+    LAUNCH3(k_encrypt_combine, grid3(c->n, c->n_q, 1), kBlock, st, 72.0 * limbs, v, e0, e1, m, pk_mont, ct, limbs,
+            c->dev_primes(), c->n);
 }
 void decrypt_combine(const hear_context *c, uint32_t level, const uint64_t *ct, const uint64_t *s_mont,
                      uint64_t *out, cudaStream_t st) {
-    LAUNCH(k_decrypt_combine, (uint64_t)(level + 1) * c->n, st, ct, s_mont, out, level + 1, c->dev_primes(),
-           c->n);
+    const uint64_t limbs = (uint64_t)(level + 1) * c->n;
+    LAUNCH3(k_decrypt_combine, grid3(c->n, level + 1, 1), kBlock, st, 32.0 * limbs, ct, s_mont, out, limbs,
+            c->dev_primes(), c->n);
 }
 void add_ct(const hear_context *c, uint32_t level, uint32_t n_polys_total, const uint64_t *a, const uint64_t *b,
             uint64_t *out, cudaStream_t st) {
-    uint64_t total = (uint64_t)n_polys_total * (level + 1) * c->n;
-    LAUNCH(k_add, total, st, a, b, out, level + 1, total, c->dev_primes(), c->n);
+    check_yz(level + 1, n_polys_total);
+    LAUNCH3(k_add, grid3(c->n, level + 1, n_polys_total), kBlock, st, 24.0 * n_polys_total * (level + 1) * c->n,
+            a, b, out, level + 1, c->dev_primes(), c->n);
+}
+void sum_ct(const hear_context *c, uint32_t level, uint32_t n_polys_total, const uint64_t *a, uint64_t stride,
+            uint32_t cnt, uint64_t *out, cudaStream_t st) {
+    check_yz(level + 1, n_polys_total);
+    LAUNCH3(k_sum, grid3(c->n, level + 1, n_polys_total), kBlock, st,
+            8.0 * (cnt + 1) * n_polys_total * (level + 1) * c->n, a, stride, cnt, out, level + 1, c->dev_primes(),
+            c->n);
 }
 void tensor_ct(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *a, const uint64_t *b,
                uint64_t *out3, cudaStream_t st) {
-    LAUNCH(k_tensor, (uint64_t)n_ct * (level + 1) * c->n, st, a, b, out3, level + 1, n_ct, c->dev_primes(), c->n);
+    check_yz(level + 1, n_ct);
+    LAUNCH3(k_tensor, grid3(c->n, level + 1, n_ct), kBlock, st, 56.0 * n_ct * (level + 1) * c->n, a, b, out3,
+            level + 1, c->dev_primes(), c->n);
 }
 void automorphism(const hear_context *c, uint32_t level, uint32_t n_polys_total, uint32_t galois,
                   const uint64_t *in, uint64_t *out, cudaStream_t st) {
-    uint64_t total = (uint64_t)n_polys_total * (level + 1) * c->n;
-    LAUNCH(k_automorphism, total, st, in, out, total, galois, c->log_n);
+    uint32_t limbs = n_polys_total * (level + 1), ny, nz;
+    split_yz(limbs, ny, nz);
+    LAUNCH3(k_automorphism, grid3(c->n, ny, nz), kBlock, st, 16.0 * limbs * c->n, in, out, limbs, galois, c->log_n);
 }
-void lincomb(const hear_context *c, uint32_t level, uint32_t n_ct, uint32_t n_in, uint32_t n_out,
-             const uint64_t *const *d_in, const uint64_t *const *d_pt, uint64_t *const *d_out, cudaStream_t st) {
-    constexpr int JB = 4;
-    for (uint32_t j0 = 0; j0 < n_out; j0 += JB)
-        LAUNCH(k_lincomb<JB>, (uint64_t)n_ct * (level + 1) * c->n, st, level + 1, n_ct, n_in, n_out, j0, d_in,
-               d_pt, d_out, c->dev_primes(), c->n);
+void lincomb(const hear_context *c, uint32_t level, uint32_t n_ct, uint32_t n1, uint32_t n2, const uint64_t *baby,
+             const uint64_t *pt, uint64_t *out, cudaStream_t st) {
+    const uint32_t L1 = level + 1;
+    dim3 grid((2 * n_ct + 7) / 8, c->n / 32, L1);
+    HEAR_REQUIRE(grid.x < (1u << 31) && L1 <= 65535, HEAR_E_UNSUPPORTED, "launch too large");
+    // algorithmic: every baby ciphertext, every plaintext and every output once
+    const double bytes = 8.0 * L1 * c->n * (2.0 * n_ct * n1 + (double)n1 * n2 + 2.0 * n_ct * n2);
+    LAUNCH3(k_lincomb, grid, 256, st, bytes, L1, n_ct, n1, n2, baby, pt, out, c->dev_primes(), c->n);
 }
 void mulplain(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *ct, const uint64_t *pt,
               uint64_t *out, cudaStream_t st) {
-    LAUNCH(k_mulplain, (uint64_t)n_ct * 2 * (level + 1) * c->n, st, ct, pt, out, level + 1, n_ct, c->dev_primes(),
-           c->n);
+    check_yz(2 * (level + 1), n_ct);
+    LAUNCH3(k_mulplain, grid3(c->n, 2 * (level + 1), n_ct), kBlock, st, 8.0 * (4.0 * n_ct + 1) * (level + 1) * c->n,
+            ct, pt, out, level + 1, c->dev_primes(), c->n);
 }
 
 void modup(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *c1, uint64_t c1_stride,
            uint64_t *ext, uint64_t *tmp, cudaStream_t st) {
     const uint32_t L1 = level + 1, W = L1 + c->K, dnum = c->dnum(level);
     const LevelConsts &lc = *c->levels[level];
+    HEAR_REQUIRE(c->alpha <= 4, HEAR_E_UNSUPPORTED, "at most 4 special primes");
     // coefficient-domain copy of the digit limbs
-    for (uint32_t i = 0; i < n_ct; i++)
-        HEAR_CHECK_CUDA(cudaMemcpyAsync(tmp + (uint64_t)i * L1 * c->n, c1 + i * c1_stride,
-                                        (size_t)L1 * c->n * 8, cudaMemcpyDeviceToDevice, st));
+    HEAR_CHECK_CUDA(cudaMemcpy2DAsync(tmp, (size_t)L1 * c->n * 8, c1, c1_stride * 8, (size_t)L1 * c->n * 8, n_ct,
+                                      cudaMemcpyDeviceToDevice, st));
     ntt_inverse(c, tmp, n_ct * L1, map_q(level, c->n_q), st);
-    LAUNCH(k_modup_conv, (uint64_t)n_ct * dnum * W * c->n, st, c1, c1_stride, tmp, ext, L1, W, dnum, c->alpha,
-           c->n_q, lc.d.u64() + lc.off_qhat_inv, lc.d.u64() + lc.off_qhat_mod, c->dev_primes(), c->n, n_ct);
+    check_yz(dnum, n_ct);
+    LAUNCH3(k_modup_conv, grid3(c->n, dnum, n_ct), kBlock, st, 8.0 * n_ct * ((double)L1 + (double)dnum * W) * c->n,
+            c1, c1_stride, tmp, ext, L1, W, dnum, c->alpha, c->n_q, lc.d.u64() + lc.off_qhat_inv,
+            lc.d.u64() + lc.off_qhat_mod, c->dev_primes(), c->n);
     LimbMap m = map_qp(level, c->n_q, c->K);
     m.skip_dnum = dnum;
     m.alpha = c->alpha;
     ntt_forward(c, ext, n_ct * dnum * W, m, st);
 }
 
-void ks_inner(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *ext,
-              const uint64_t *const *d_keys, const uint32_t *d_galois, uint64_t *out, cudaStream_t st) {
-    const uint32_t L1 = level + 1, W = L1 + c->K;
-    const double dn = c->dnum(level), wn = (double)W * c->n * 8.0;
-    // keys are read once per distinct key; the batch shares them when n_ct > 1 and the key is common
-    LAUNCH_B(k_ks_inner, (uint64_t)n_ct * W * c->n, st, 2.0 * dn * wn + n_ct * (dn + 2.0) * wn, ext, d_keys,
-             d_galois, out, L1, W, c->dnum(level), c->n_q, c->nqp(), c->log_n, c->dev_primes(), n_ct);
+void ks_inner(const hear_context *c, uint32_t level, uint32_t R, uint32_t C, const uint64_t *ext, bool ext_per_job,
+              const uint64_t *const *d_keys, const uint32_t *d_ginv, uint64_t *out, cudaStream_t st) {
+    const uint32_t L1 = level + 1, W = L1 + c->K, dnum = c->dnum(level);
+    check_yz(R, W);
+    const double dn = dnum, wn = (double)W * c->n * 8.0;
+    // algorithmic: each key once, each extended digit once (per job if not shared), each output once
+    const double bytes = R * 2.0 * dn * wn + (ext_per_job ? (double)R * C : (double)C) * dn * wn + R * C * 2.0 * wn;
+    const dim3 grid = grid3(c->n, R, W);
+    if (dnum <= 8)
+        LAUNCH3(k_ks_inner<8>, grid, kBlock, st, bytes, ext, (int)ext_per_job, d_keys, d_ginv, out, C, L1, W, dnum,
+                c->n_q, c->nqp(), c->log_n, c->dev_primes());
+    else if (dnum <= 16)
+        LAUNCH3(k_ks_inner<16>, grid, kBlock, st, bytes, ext, (int)ext_per_job, d_keys, d_ginv, out, C, L1, W, dnum,
+                c->n_q, c->nqp(), c->log_n, c->dev_primes());
+    else
+        LAUNCH3(k_ks_inner<48>, grid, kBlock, st, bytes, ext, (int)ext_per_job, d_keys, d_ginv, out, C, L1, W, dnum,
+                c->n_q, c->nqp(), c->log_n, c->dev_primes());
 }
 
 void moddown(const hear_context *c, uint32_t level, uint32_t n_ct, uint64_t *acc, uint64_t *out,
-             const uint64_t *addend, uint64_t add_stride, uint32_t add_mask, const uint32_t *d_galois,
-             uint64_t *tmp, cudaStream_t st) {
+             const uint64_t *addend, uint64_t add_stride, uint32_t add_mask, bool add_shared, const uint32_t *d_gal,
+             uint32_t cts_per_job, uint64_t *tmp, cudaStream_t st) {
     const uint32_t L1 = level + 1, W = L1 + c->K, groups = n_ct * 2;
     const LevelConsts &lc = *c->levels[level];
+    HEAR_REQUIRE(c->K <= 4, HEAR_E_UNSUPPORTED, "at most 4 special primes");
     LimbMap pm;
     pm.per_group = c->K;
     pm.q_count = 0;
     pm.n_q = c->n_q;
     pm.group_stride = (uint64_t)W * c->n;
     ntt_inverse(c, acc + (uint64_t)L1 * c->n, groups * c->K, pm, st);
-    LAUNCH(k_moddown_conv, (uint64_t)groups * L1 * c->n, st, acc, tmp, L1, W, c->K, c->n_q,
-           lc.d.u64() + lc.off_phat_inv, lc.d.u64() + lc.off_phat_mod, c->dev_primes(), c->n, groups);
+    uint32_t ny, nz;
+    split_yz(groups, ny, nz);
+    LAUNCH3(k_moddown_conv, grid3(c->n, ny, nz), kBlock, st, 8.0 * groups * ((double)c->K + L1) * c->n, acc, tmp,
+            groups, L1, W, c->K, c->n_q, lc.d.u64() + lc.off_phat_inv, lc.d.u64() + lc.off_phat_mod, c->dev_primes(),
+            c->n);
     ntt_forward(c, tmp, groups * L1, map_q(level, c->n_q), st);
-    LAUNCH(k_moddown_combine, (uint64_t)groups * L1 * c->n, st, acc, tmp, out, addend, add_stride, add_mask,
-           d_galois, L1, W,
-           lc.d.u64() + lc.off_p_inv, c->dev_primes(), c->log_n, groups);
+    check_yz(L1, groups);
+    LAUNCH3(k_moddown_combine, grid3(c->n, L1, groups), kBlock, st,
+            8.0 * groups * L1 * c->n * (3.0 + (addend ? 1.0 : 0.0)), acc, tmp, out, addend, add_stride, add_mask,
+            (uint32_t)add_shared, d_gal, cts_per_job, L1, W, lc.d.u64() + lc.off_p_inv, c->dev_primes(), c->log_n);
 }
 
 void rescale(const hear_context *c, uint32_t level, uint32_t n_polys, uint64_t *in, uint64_t *out, uint64_t *tmp,
@@ -551,10 +647,14 @@ void rescale(const hear_context *c, uint32_t level, uint32_t n_polys, uint64_t *
     lm.n_q = c->n_q;
     lm.group_stride = (uint64_t)L1 * c->n;
     ntt_inverse(c, in + (uint64_t)level * c->n, n_polys, lm, st);
-    LAUNCH(k_rescale_lift, (uint64_t)n_polys * level * c->n, st, in, tmp, L1, c->dev_primes(), c->n, n_polys);
+    uint32_t ny, nz;
+    split_yz(n_polys, ny, nz);
+    LAUNCH3(k_rescale_lift, grid3(c->n, ny, nz), kBlock, st, 8.0 * n_polys * (1.0 + level) * c->n, in, tmp, n_polys,
+            L1, c->dev_primes(), c->n);
     ntt_forward(c, tmp, n_polys * level, map_q(level - 1, c->n_q), st);
-    LAUNCH(k_rescale_combine, (uint64_t)n_polys * level * c->n, st, in, tmp, out, L1, lc.d.u64() + lc.off_ql_inv,
-           c->dev_primes(), c->n, n_polys);
+    check_yz(level, n_polys);
+    LAUNCH3(k_rescale_combine, grid3(c->n, level, n_polys), kBlock, st, 24.0 * n_polys * level * c->n, in, tmp, out,
+            L1, lc.d.u64() + lc.off_ql_inv, c->dev_primes(), c->n);
 }
 
 }  // namespace hear

@@ -40,11 +40,11 @@ void tensor_ct(const hear_context *c, uint32_t level, uint32_t n_ct, const uint6
 // out = sigma_g(in) for n_polys_total polynomials at `level`
 void automorphism(const hear_context *c, uint32_t level, uint32_t n_polys_total, uint32_t galois,
                   const uint64_t *in, uint64_t *out, cudaStream_t st);
-// BSGS inner sums: for every ciphertext c < n_ct and output j < n_out:
-//   out[j] (batch) = sum_{i < n_in, pt[j*n_in+i] != 0} in[i] (batch) (.) pt[j*n_in+i]
-// in[i], out[j]: device pointers to batches [n_ct][2][level+1][N]; pt: [level+1][N] Montgomery
-void lincomb(const hear_context *c, uint32_t level, uint32_t n_ct, uint32_t n_in, uint32_t n_out,
-             const uint64_t *const *d_in, const uint64_t *const *d_pt, uint64_t *const *d_out, cudaStream_t st);
+// BSGS inner sums on contiguous storage: out[j][c] = sum_{b < n1} pt[j*n1 + b] (.) baby[b][c]
+// baby [n1][n_ct][2][level+1][N], pt [n2*n1][level+1][N] (Montgomery; zero for missing
+// diagonals), out [n2][n_ct][2][level+1][N]
+void lincomb(const hear_context *c, uint32_t level, uint32_t n_ct, uint32_t n1, uint32_t n2, const uint64_t *baby,
+             const uint64_t *pt, uint64_t *out, cudaStream_t st);
 // out (batch [n_ct][2][level+1][N]) = ct (batch) (.) pt   (pt Montgomery, no accumulation)
 void mulplain(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *ct, const uint64_t *pt,
               uint64_t *out, cudaStream_t st);
@@ -53,16 +53,21 @@ void mulplain(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64
 // ext [n_ct][dnum][W][N] from c1 (NTT, [n_ct] polys at stride c1_stride words); tmp: n_ct*(l+1)*N words
 void modup(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *c1, uint64_t c1_stride,
            uint64_t *ext, uint64_t *tmp, cudaStream_t st);
-// out [n_ct][2][W][N] = sum_j sigma_{g_c}(ext_j) (.) key_c[j]; d_keys[c], d_galois[c] per ciphertext
-void ks_inner(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *ext,
-              const uint64_t *const *d_keys, const uint32_t *d_galois, uint64_t *out, cudaStream_t st);
-// ModDown of acc [n_ct][2][W][N] (destroys its P limbs) into out [n_ct][2][l+1][N], adding
-// addend (ciphertext c at addend + c*add_stride, polys [2][l+1][N], poly p only if add_mask bit p)
-// gathered through sigma_{g_c}
-// (d_galois may be null = identity).  tmp: n_ct*2*(l+1)*N words
+// Key inner product, R jobs of C ciphertexts: out[r*C + c] ([2][W][N]) =
+//   sum_j sigma_{g_r}(ext_j) (.) key_r[j],  ext = ext[c] (shared) or ext[r*C + c] (per job).
+// d_keys[r]: switching key stored sigma_{g_r}^{-1}-permuted; d_ginv[r] = g_r^{-1} mod 2N.
+void ks_inner(const hear_context *c, uint32_t level, uint32_t R, uint32_t C, const uint64_t *ext, bool ext_per_job,
+              const uint64_t *const *d_keys, const uint32_t *d_ginv, uint64_t *out, cudaStream_t st);
+// ModDown of acc [n_ct][2][W][N] (destroys its P limbs) into out [n_ct][2][l+1][N], adding an
+// addend ciphertext (ciphertext index c, or c mod cts_per_job if add_shared, at addend +
+// index*add_stride, polys [2][l+1][N]; poly p only if add_mask bit p) gathered through
+// sigma_g with g = d_gal[c / cts_per_job] (d_gal null = identity).  tmp: n_ct*2*(l+1)*N words
 void moddown(const hear_context *c, uint32_t level, uint32_t n_ct, uint64_t *acc, uint64_t *out,
-             const uint64_t *addend, uint64_t add_stride, uint32_t add_mask, const uint32_t *d_galois,
-             uint64_t *tmp, cudaStream_t st);
+             const uint64_t *addend, uint64_t add_stride, uint32_t add_mask, bool add_shared, const uint32_t *d_gal,
+             uint32_t cts_per_job, uint64_t *tmp, cudaStream_t st);
+// out = sum of cnt batches a + j*stride (n_polys_total polynomials at level)
+void sum_ct(const hear_context *c, uint32_t level, uint32_t n_polys_total, const uint64_t *a, uint64_t stride,
+            uint32_t cnt, uint64_t *out, cudaStream_t st);
 // out = a (.) b_mont over n_limbs limbs (Montgomery product: a * b)
 void pointwise_mont(const hear_context *c, uint32_t n_limbs, LimbMap m, const uint64_t *a, const uint64_t *b_mont,
                     uint64_t *out, cudaStream_t st);

@@ -9,24 +9,23 @@
 //
 // Layout: N = 2^a * 2^b.  Pass A runs stages 0..a-1 on strided sub-problems (column c:
 // elements c + u*2^b, u < 2^a), pass B runs stages a..logN-1 on contiguous blocks of 2^b.
-// A CTA stages a 2048-word tile in shared memory; each thread applies up to three
-// stages at a time to 8 words held in registers (radix-2^3 units), with Harvey lazy
-// butterflies (values kept in [0, 4q) forward and [0, 2q) inverse) and Shoup products by
-// the precomputed twiddle companions.
+// A CTA stages a 2048- or 4096-word tile in shared memory (XOR-swizzled, bank-conflict
+// free); each pass runs in two register rounds, each thread applying three or four stages
+// at a time to 8 or 16 words (radix-2^3 / 2^4 units), with Harvey lazy butterflies
+// (values kept in [0, 4q) forward and [0, 2q) inverse) and Shoup products by the
+// precomputed twiddle companions.
 #include "internal.h"
 #include "modarith.cuh"
 
 namespace hear {
 namespace {
 
-constexpr int kTile = 2048;      // words per CTA tile (16 KiB)
 constexpr int kThreads = 256;
 
 struct PassArgs {
     uint64_t *data;
     uint32_t n_limbs;
     uint32_t log_n;
-    uint32_t tiles_per_limb;
     LimbMap map;
     const DevPrime *primes;
     const uint64_t *tw;      // twiddle table [n_primes][N]
@@ -34,50 +33,72 @@ struct PassArgs {
     uint32_t n;              // N
 };
 
-// One group of W stages on a tile.  FWD: stages ls0, ls0+1, ...; INV: ls0, ls0-1, ...
-// PASSA: sub-problems are the C columns of an R x C tile (sidx = u*C + c); else they are
-// S contiguous blocks of R words (sidx = sp*R + u).
-template <int LOGR, int W, bool FWD, bool PASSA>
-__device__ __forceinline__ void stage_group(uint64_t *s, int ls0, uint32_t s_off, uint32_t blk_base,
+// Shared-memory word of logical tile index i: the low four bits are XORed with bits 3..6 and
+// 4..7, which makes every unit access pattern below bank-conflict free (two wavefronts per
+// warp-wide 64-bit access) and keeps each 16-word block in place.
+__device__ __forceinline__ uint32_t swz(uint32_t i) { return i ^ ((i >> 3) & 15u) ^ ((i >> 4) & 15u); }
+
+// Stage split of a pass of LOGR stages into register units of 2^W0 and 2^W1 words.
+template <int LOGR> struct Split;
+template <> struct Split<5> { static constexpr int W0 = 3, W1 = 2, TILE = 2048; };
+template <> struct Split<6> { static constexpr int W0 = 3, W1 = 3, TILE = 2048; };
+template <> struct Split<7> { static constexpr int W0 = 4, W1 = 3, TILE = 4096; };
+template <> struct Split<8> { static constexpr int W0 = 4, W1 = 4, TILE = 4096; };
+
+// One group of W stages on a tile: forward stages LS0, LS0+1, ..; inverse LS0, LS0-1, ...
+// Each thread holds the 2^W words of a unit in registers.  In the stage i of the group the
+// unit's butterflies use only 2^i (forward) or 2^(W-1-i) (inverse) distinct twiddles, which
+// are loaded once.  PASSA: sub-problems are the TILE/R columns of an R x (TILE/R) tile
+// (logical index u*NSP + sp); else TILE/R contiguous blocks of R words (sp*R + u).
+template <int LOGR, int W, int LS0, bool FWD, bool PASSA, int TILE>
+__device__ __forceinline__ void stage_group(uint64_t *s, uint32_t s_off, uint32_t blk_base,
                                             const uint64_t *__restrict__ tw,
                                             const uint64_t *__restrict__ tws, uint64_t q) {
     constexpr int R = 1 << LOGR;
     constexpr int E = 1 << W;
-    constexpr int NSP = kTile / R;               // sub-problems per tile
-    constexpr int UPS = R >> W;                  // units per sub-problem
-    const int p_lo = FWD ? (LOGR - ls0 - W) : (LOGR - 1 - ls0);
+    constexpr int NSP = TILE / R;
+    constexpr int UPS = R >> W;
+    constexpr int P_LO = FWD ? (LOGR - LS0 - W) : (LOGR - 1 - LS0);
+    constexpr uint32_t LOWMASK = (1u << P_LO) - 1;
     const uint64_t two_q = 2 * q;
     for (int id = threadIdx.x; id < NSP * UPS; id += blockDim.x) {
         int sp, ub;
         if (PASSA) { sp = id % NSP; ub = id / NSP; }
         else       { ub = id % UPS; sp = id / UPS; }
-        const uint32_t lowmask = (1u << p_lo) - 1;
-        const uint32_t u_base = ((ub & ~lowmask) << W) | (ub & lowmask);
+        const uint32_t u_base = (((uint32_t)ub & ~LOWMASK) << W) | ((uint32_t)ub & LOWMASK);
         uint64_t x[E];
 #pragma unroll
         for (int e = 0; e < E; e++) {
-            uint32_t u = u_base + (e << p_lo);
-            x[e] = s[PASSA ? (u * NSP + sp) : (sp * R + u)];
+            const uint32_t u = u_base + (e << P_LO);
+            x[e] = s[swz(PASSA ? (u * NSP + sp) : (sp * R + u))];
         }
         const uint32_t blk = PASSA ? 0u : (blk_base + sp);
 #pragma unroll
         for (int i = 0; i < W; i++) {
-            const int ls = FWD ? (ls0 + i) : (ls0 - i);
+            const int ls = FWD ? (LS0 + i) : (LS0 - i);
             const int half = FWD ? (E >> (i + 1)) : (1 << i);
+            const uint32_t base = (1u << (s_off + ls)) + (blk << ls) + (u_base >> (LOGR - ls));
+            // pair p = (e, e + half); its twiddle index m is nondecreasing in p, so a
+            // twiddle is loaded when m changes (all indices are compile-time constants)
+            uint64_t w = 0, wsh = 0;
 #pragma unroll
-            for (int e = 0; e < E; e++) {
-                if (e & half) continue;
-                const uint32_t u = u_base + (e << p_lo);
-                const uint32_t idx = (1u << (s_off + ls)) + (blk << ls) + (u >> (LOGR - ls));
-                const uint64_t w = __ldg(tw + idx), wsh = __ldg(tws + idx);
+            for (int p = 0; p < E / 2; p++) {
+                const int e = FWD ? ((p / half) * 2 * half + (p % half)) : (((p >> i) << (i + 1)) | (p & (half - 1)));
+                const int m = FWD ? (e >> (W - i)) : (p >> i);
+                const int pe = FWD ? (((p - 1) / half) * 2 * half + ((p - 1) % half)) : 0;
+                const int pm = p == 0 ? -1 : (FWD ? (pe >> (W - i)) : ((p - 1) >> i));
+                if (m != pm) {
+                    w = __ldg(tw + base + m);
+                    wsh = __ldg(tws + base + m);
+                }
                 uint64_t X = x[e], Y = x[e + half];
                 if (FWD) {
                     X = X >= two_q ? X - two_q : X;
-                    uint64_t T = shoup_lazy(Y, w, wsh, q);
+                    const uint64_t T = shoup_lazy(Y, w, wsh, q);
                     x[e] = X + T;
                     x[e + half] = X - T + two_q;
                 } else {
-                    uint64_t S = X + Y;
+                    const uint64_t S = X + Y;
                     x[e] = S >= two_q ? S - two_q : S;
                     x[e + half] = shoup_lazy(X - Y + two_q, w, wsh, q);
                 }
@@ -85,8 +106,8 @@ __device__ __forceinline__ void stage_group(uint64_t *s, int ls0, uint32_t s_off
         }
 #pragma unroll
         for (int e = 0; e < E; e++) {
-            uint32_t u = u_base + (e << p_lo);
-            s[PASSA ? (u * NSP + sp) : (sp * R + u)] = x[e];
+            const uint32_t u = u_base + (e << P_LO);
+            s[swz(PASSA ? (u * NSP + sp) : (sp * R + u))] = x[e];
         }
     }
 }
@@ -94,44 +115,39 @@ __device__ __forceinline__ void stage_group(uint64_t *s, int ls0, uint32_t s_off
 template <int LOGR, bool FWD, bool PASSA>
 __device__ __forceinline__ void all_groups(uint64_t *s, uint32_t s_off, uint32_t blk_base,
                                            const uint64_t *tw, const uint64_t *tws, uint64_t q) {
-    constexpr int G3 = LOGR / 3, REM = LOGR % 3;
-#pragma unroll
-    for (int g = 0; g < G3; g++) {
-        const int ls0 = FWD ? 3 * g : LOGR - 1 - 3 * g;
-        stage_group<LOGR, 3, FWD, PASSA>(s, ls0, s_off, blk_base, tw, tws, q);
-        __syncthreads();
-    }
-    if constexpr (REM > 0) {
-        const int ls0 = FWD ? 3 * G3 : REM - 1;
-        stage_group<LOGR, REM, FWD, PASSA>(s, ls0, s_off, blk_base, tw, tws, q);
-        __syncthreads();
-    }
+    constexpr int W0 = Split<LOGR>::W0, W1 = Split<LOGR>::W1, TILE = Split<LOGR>::TILE;
+    stage_group<LOGR, W0, FWD ? 0 : LOGR - 1, FWD, PASSA, TILE>(s, s_off, blk_base, tw, tws, q);
+    __syncthreads();
+    stage_group<LOGR, W1, FWD ? W0 : LOGR - 1 - W0, FWD, PASSA, TILE>(s, s_off, blk_base, tw, tws, q);
+    __syncthreads();
 }
 
 // Pass A: strided columns, stages 0..LOGR-1 (forward) or LOGR-1..0 (inverse, + N^-1).
 template <int LOGR, bool FWD>
-__global__ void __launch_bounds__(kThreads) ntt_pass_a(PassArgs a) {
-    __shared__ uint64_t s[kTile];
+__global__ void __launch_bounds__(kThreads, 2) ntt_pass_a(PassArgs a) {
+    constexpr int TILE = Split<LOGR>::TILE;
+    __shared__ uint64_t s[TILE];
     constexpr int R = 1 << LOGR;
-    constexpr int C = kTile / R;
-    const uint32_t limb = blockIdx.x / a.tiles_per_limb;
-    const uint32_t tile = blockIdx.x % a.tiles_per_limb;
+    constexpr int C = TILE / R;
+    const uint32_t tiles = a.n / TILE;
+    const uint32_t limb = blockIdx.x / tiles;
+    const uint32_t tile = blockIdx.x % tiles;
     uint32_t pi;
     if (limb >= a.n_limbs || !a.map.resolve(limb, &pi)) return;
     const DevPrime P = a.primes[pi];
     uint64_t *g = a.data + a.map.offset(limb, a.n);
     const uint32_t cols = a.n >> LOGR;
     const uint32_t c0 = tile * C;
-    for (int i = threadIdx.x; i < kTile; i += blockDim.x) {
-        int u = i / C, c = i % C;
-        s[i] = g[c0 + c + (size_t)u * cols];
+    for (int i = threadIdx.x; i < TILE; i += blockDim.x) {
+        const int u = i / C, c = i % C;
+        s[swz(i)] = g[c0 + c + (size_t)u * cols];
     }
     __syncthreads();
     const uint64_t *tw = a.tw + (size_t)pi * a.n, *tws = a.tw_sh + (size_t)pi * a.n;
     all_groups<LOGR, FWD, true>(s, 0, 0, tw, tws, P.q);
-    for (int i = threadIdx.x; i < kTile; i += blockDim.x) {
-        int u = i / C, c = i % C;
-        uint64_t v = s[i];
+    for (int i = threadIdx.x; i < TILE; i += blockDim.x) {
+        const int u = i / C, c = i % C;
+        uint64_t v = s[swz(i)];
         if (!FWD) {
             v = shoup_lazy(v, P.n_inv, P.n_inv_sh, P.q);
             v = v >= P.q ? v - P.q : v;
@@ -142,25 +158,31 @@ __global__ void __launch_bounds__(kThreads) ntt_pass_a(PassArgs a) {
 
 // Pass B: contiguous blocks of R words, stages s_off..s_off+LOGR-1.
 template <int LOGR, bool FWD>
-__global__ void __launch_bounds__(kThreads) ntt_pass_b(PassArgs a, uint32_t s_off) {
-    __shared__ uint64_t s[kTile];
+__global__ void __launch_bounds__(kThreads, 2) ntt_pass_b(PassArgs a, uint32_t s_off) {
+    constexpr int TILE = Split<LOGR>::TILE;
+    __shared__ uint64_t s[TILE];
     constexpr int R = 1 << LOGR;
-    constexpr int S = kTile / R;
-    const uint32_t limb = blockIdx.x / a.tiles_per_limb;
-    const uint32_t tile = blockIdx.x % a.tiles_per_limb;
+    constexpr int S = TILE / R;
+    const uint32_t tiles = a.n / TILE;
+    const uint32_t limb = blockIdx.x / tiles;
+    const uint32_t tile = blockIdx.x % tiles;
     uint32_t pi;
     if (limb >= a.n_limbs || !a.map.resolve(limb, &pi)) return;
     const DevPrime P = a.primes[pi];
-    uint64_t *g = a.data + a.map.offset(limb, a.n) + (size_t)tile * kTile;
-    for (int i = threadIdx.x; i < kTile / 2; i += blockDim.x) {
-        reinterpret_cast<ulonglong2 *>(s)[i] = reinterpret_cast<const ulonglong2 *>(g)[i];
+    uint64_t *g = a.data + a.map.offset(limb, a.n) + (size_t)tile * TILE;
+    for (int i = threadIdx.x; i < TILE / 2; i += blockDim.x) {
+        const ulonglong2 v = reinterpret_cast<const ulonglong2 *>(g)[i];
+        s[swz(2 * i)] = v.x;
+        s[swz(2 * i + 1)] = v.y;
     }
     __syncthreads();
     const uint64_t *tw = a.tw + (size_t)pi * a.n, *tws = a.tw_sh + (size_t)pi * a.n;
     all_groups<LOGR, FWD, false>(s, s_off, tile * S, tw, tws, P.q);
     const uint64_t q = P.q, two_q = 2 * q;
-    for (int i = threadIdx.x; i < kTile / 2; i += blockDim.x) {
-        ulonglong2 v = reinterpret_cast<ulonglong2 *>(s)[i];
+    for (int i = threadIdx.x; i < TILE / 2; i += blockDim.x) {
+        ulonglong2 v;
+        v.x = s[swz(2 * i)];
+        v.y = s[swz(2 * i + 1)];
         if (FWD) {
             v.x = v.x >= two_q ? v.x - two_q : v.x;
             v.x = v.x >= q ? v.x - q : v.x;
@@ -173,15 +195,13 @@ __global__ void __launch_bounds__(kThreads) ntt_pass_b(PassArgs a, uint32_t s_of
 
 template <int A, int B>
 void launch_fwd(const PassArgs &a, cudaStream_t st) {
-    dim3 grid(a.n_limbs * a.tiles_per_limb);
-    ntt_pass_a<A, true><<<grid, kThreads, 0, st>>>(a);
-    ntt_pass_b<B, true><<<grid, kThreads, 0, st>>>(a, A);
+    ntt_pass_a<A, true><<<a.n_limbs * (a.n / Split<A>::TILE), kThreads, 0, st>>>(a);
+    ntt_pass_b<B, true><<<a.n_limbs * (a.n / Split<B>::TILE), kThreads, 0, st>>>(a, A);
 }
 template <int A, int B>
 void launch_inv(const PassArgs &a, cudaStream_t st) {
-    dim3 grid(a.n_limbs * a.tiles_per_limb);
-    ntt_pass_b<B, false><<<grid, kThreads, 0, st>>>(a, A);
-    ntt_pass_a<A, false><<<grid, kThreads, 0, st>>>(a);
+    ntt_pass_b<B, false><<<a.n_limbs * (a.n / Split<B>::TILE), kThreads, 0, st>>>(a, A);
+    ntt_pass_a<A, false><<<a.n_limbs * (a.n / Split<A>::TILE), kThreads, 0, st>>>(a);
 }
 
 PassArgs make_args(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, LimbMap map, bool fwd) {
@@ -190,7 +210,6 @@ PassArgs make_args(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, Li
     a.n_limbs = n_limbs;
     a.log_n = ctx->log_n;
     a.n = ctx->n;
-    a.tiles_per_limb = ctx->n / kTile;
     a.map = map;
     a.primes = ctx->dev_primes();
     const size_t plane = (size_t)ctx->nqp() * ctx->n;

@@ -309,3 +309,27 @@ def test_small_network_per_layer_bit_exact(small):
     for h in (g, c0, whole):
         H.hear_ciphertext_destroy(h)
     H.hear_model_destroy(model)
+
+
+def test_graph_replay_equals_direct_launches(toy):
+    """Whole evaluations replay a captured CUDA graph; with the stage profiler on the same
+    kernels are launched one by one.  Both must give the same ciphertext, and the profiler
+    must account for the launches."""
+    H, w = toy.H, toy.w
+    model = H.hear_model_create(toy.ctx, w.layers, w.clip_dim)
+    ct = H.hear_encrypt_clips(toy.ctx, toy.pk, w.clips, 401, 9)
+    g1 = H.hear_evaluate(model, toy.evk, [ct])[0]        # builds and replays the graph
+    g2 = H.hear_evaluate(model, toy.evk, [ct])[0]        # replays it again
+    H.hear_profile_begin(toy.ctx)
+    n0 = H.hear_launch_count()
+    d = H.hear_evaluate(model, toy.evk, [ct])[0]         # direct launches
+    n1 = H.hear_launch_count()
+    stages = H.hear_profile_end(toy.ctx)
+    ref = H.hear_ciphertext_export(d)
+    assert np.array_equal(H.hear_ciphertext_export(g1), ref)
+    assert np.array_equal(H.hear_ciphertext_export(g2), ref)
+    assert sum(v[0] for v in stages.values()) == n1 - n0 > 0
+    assert all(v[1] >= 0 for v in stages.values()) and "ntt_fwd" in stages
+    for h in (ct, g1, g2, d):
+        H.hear_ciphertext_destroy(h)
+    H.hear_model_destroy(model)
