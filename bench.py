@@ -144,6 +144,65 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# Integer-pipe roofline of the NTT.  Peak: 152 SMs x 4 sub-partitions x 32 lanes, one
+# 32-bit integer instruction per lane per cycle, at the 2070 MHz maximum SM clock.
+# Algorithmic work: a lazy (Harvey) butterfly with a Shoup product by a precomputed
+# twiddle counts 30 32-bit integer operations (the multiply-high of two 64-bit words:
+# 4 partial products x 2 words + 4 carries = 12; two 64-bit multiply-lows: 2 x 4 = 8;
+# the correction, add and subtract of 64-bit words: 10).
+ALU_PEAK_TOPS = 152 * 4 * 32 * 2.070e9 / 1e12
+OPS_PER_BUTTERFLY = 30
+
+
+def ntt_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("ntt.cu", "modarith.cuh"):
+        with open(os.path.join(ROOT, "paper_2104_09164_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(workload):
+    """DRAM bytes per forward-NTT call from the committed ncu summary of this workload, if
+    it was taken on the current NTT source"""
+    import re
+    path = os.path.join(ROOT, "profiles", "ntt_fwd_%s.md" % workload)
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m_src = re.search(r"source_sha256_16:\s*([0-9a-f]{16})", txt)
+    m_tr = re.search(r"dram_bytes_per_call:\s*([0-9.e+]+)", txt)
+    if not m_src or not m_tr or m_src.group(1) != ntt_source_hash():
+        return None
+    return float(m_tr.group(1))
+
+
+def roofline(stages, psteps, log_n, workload):
+    hbm, how = peaks()
+    fwd = stages.get("ntt_fwd")
+    name = max(stages.items(), key=lambda kv: kv[1][1])[0]
+    if not fwd:
+        return {"bound": "hbm", "kernel": name, "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
+                "traffic": None}
+    calls, ms, byts = fwd
+    calls_per_step = calls / 2 / psteps            # two pass kernels per forward NTT
+    n = 1 << log_n
+    limbs = byts / (16.0 * n)
+    butterflies = limbs * (n // 2) * log_n
+    alu = OPS_PER_BUTTERFLY * butterflies / (ms / 1e3) / 1e12
+    gbs = byts / (ms / 1e3) / 1e9
+    total = sum(v[1] for v in stages.values())
+    return {"bound": "alu", "kernel": "ntt_fwd (forward NTT, pass A + pass B kernels)", "achieved": alu,
+            "peak": ALU_PEAK_TOPS, "unit": "Tintops/s", "frac": alu / ALU_PEAK_TOPS,
+            "traffic": committed_traffic(workload) if calls else None,
+            "algorithmic_bytes_per_call": byts / calls * 2 if calls else None,
+            "calls_per_step": calls_per_step, "avg_call_us": ms * 1e3 / (calls / 2),
+            "hbm_achieved_gbs": gbs, "hbm_peak_gbs": hbm, "hbm_peak_kind": how, "hbm_frac": gbs / hbm,
+            "stage_share": ms / total, "dominant_stage": name}
+
+
 # ------------------------------------------------------------------ oracle CPU timing
 def oracle_sample(w, steps_keys, seconds_budget=25.0):
     """Time the CPU oracle (as it stands) evaluating whole ciphertexts of the workload.
@@ -205,6 +264,7 @@ def run_gpu(S, steps, warmup, dist, torch, stream, sampler_device):
     with ClockSampler(sampler_device) as clk:
         t_start = torch.cuda.Event(enable_timing=True)
         t_end = torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("hear_timed")   # ncu --nvtx-include "hear_timed/" selects these steps
         t_start.record(stream)
         for i in range(steps):
             ev[i][0].record(stream)
@@ -214,6 +274,7 @@ def run_gpu(S, steps, warmup, dist, torch, stream, sampler_device):
                 H.hear_ciphertext_destroy(o)
         t_end.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     launches = H.hear_launch_count() - launches0
     dist.barrier()
     torch.cuda.synchronize()
@@ -272,15 +333,10 @@ def main_gpu(a):
     e2e_value = dist.world * max(3, a.steps // 2) * S.clips_per_step / dist.max(e2e_s)
     result = None
     if dist.rank == 0:
-        hbm, how = peaks()
-        # dominant stage by device time
-        top = max(stages.items(), key=lambda kv: kv[1][1])
-        name, (nl, ms, byts) = top
         ntt = {k: v for k, v in stages.items() if k.startswith("ntt")}
         nl_ntt = sum(v[0] for v in ntt.values())
         ms_ntt = sum(v[1] for v in ntt.values())
         by_ntt = sum(v[2] for v in ntt.values())
-        achieved = byts / (ms / 1e3) / 1e9
         total_stage_ms = sum(v[1] for v in stages.values())
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": a.steps,
@@ -291,9 +347,7 @@ def main_gpu(a):
                              "diagonals) is larger than the 129 MB L2" % _key_mb(w, len(S.steps))},
             "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
-            "roofline": {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "peak_kind": how, "traffic": None,
-                         "launches_per_step": nl / psteps, "stage_share": ms / total_stage_ms},
+            "roofline": roofline(stages, psteps, w.log_n, w.name if a.clips is None else w.name + "_%d" % a.clips),
             "ntt": {"achieved_gbs": by_ntt / (ms_ntt / 1e3) / 1e9 if ms_ntt else None,
                     "launches_per_step": nl_ntt / psteps, "share": ms_ntt / total_stage_ms},
             "stages_ms_per_step": {k: v[1] / psteps for k, v in sorted(stages.items(), key=lambda kv: -kv[1][1])},

@@ -38,12 +38,18 @@ struct PassArgs {
 // warp-wide 64-bit access) and keeps each 16-word block in place.
 __device__ __forceinline__ uint32_t swz(uint32_t i) { return i ^ ((i >> 3) & 15u) ^ ((i >> 4) & 15u); }
 
-// Stage split of a pass of LOGR stages into register units of 2^W0 and 2^W1 words.
+// Stage split of a pass of LOGR stages into register units of 2^W0 and 2^W1 words, and the
+// tile (words per CTA) of the wide variant; the narrow variant (for launches with too few
+// CTAs to fill the GPU) uses a quarter of the tile with a quarter of the threads.
 template <int LOGR> struct Split;
 template <> struct Split<5> { static constexpr int W0 = 3, W1 = 2, TILE = 2048; };
 template <> struct Split<6> { static constexpr int W0 = 3, W1 = 3, TILE = 2048; };
 template <> struct Split<7> { static constexpr int W0 = 4, W1 = 3, TILE = 4096; };
 template <> struct Split<8> { static constexpr int W0 = 4, W1 = 4, TILE = 4096; };
+template <int LOGR, bool NARROW> struct Tile {
+    static constexpr int WORDS = NARROW ? Split<LOGR>::TILE / 4 : Split<LOGR>::TILE;
+    static constexpr int THREADS = NARROW ? kThreads / 4 : kThreads;
+};
 
 // One group of W stages on a tile: forward stages LS0, LS0+1, ..; inverse LS0, LS0-1, ...
 // Each thread holds the 2^W words of a unit in registers.  In the stage i of the group the
@@ -112,10 +118,10 @@ __device__ __forceinline__ void stage_group(uint64_t *s, uint32_t s_off, uint32_
     }
 }
 
-template <int LOGR, bool FWD, bool PASSA>
+template <int LOGR, bool FWD, bool PASSA, int TILE>
 __device__ __forceinline__ void all_groups(uint64_t *s, uint32_t s_off, uint32_t blk_base,
                                            const uint64_t *tw, const uint64_t *tws, uint64_t q) {
-    constexpr int W0 = Split<LOGR>::W0, W1 = Split<LOGR>::W1, TILE = Split<LOGR>::TILE;
+    constexpr int W0 = Split<LOGR>::W0, W1 = Split<LOGR>::W1;
     stage_group<LOGR, W0, FWD ? 0 : LOGR - 1, FWD, PASSA, TILE>(s, s_off, blk_base, tw, tws, q);
     __syncthreads();
     stage_group<LOGR, W1, FWD ? W0 : LOGR - 1 - W0, FWD, PASSA, TILE>(s, s_off, blk_base, tw, tws, q);
@@ -123,9 +129,9 @@ __device__ __forceinline__ void all_groups(uint64_t *s, uint32_t s_off, uint32_t
 }
 
 // Pass A: strided columns, stages 0..LOGR-1 (forward) or LOGR-1..0 (inverse, + N^-1).
-template <int LOGR, bool FWD>
-__global__ void __launch_bounds__(kThreads, 2) ntt_pass_a(PassArgs a) {
-    constexpr int TILE = Split<LOGR>::TILE;
+template <int LOGR, bool FWD, bool NARROW>
+__global__ void __launch_bounds__(Tile<LOGR, NARROW>::THREADS, NARROW ? 8 : 2) ntt_pass_a(PassArgs a) {
+    constexpr int TILE = Tile<LOGR, NARROW>::WORDS;
     __shared__ uint64_t s[TILE];
     constexpr int R = 1 << LOGR;
     constexpr int C = TILE / R;
@@ -144,7 +150,7 @@ __global__ void __launch_bounds__(kThreads, 2) ntt_pass_a(PassArgs a) {
     }
     __syncthreads();
     const uint64_t *tw = a.tw + (size_t)pi * a.n, *tws = a.tw_sh + (size_t)pi * a.n;
-    all_groups<LOGR, FWD, true>(s, 0, 0, tw, tws, P.q);
+    all_groups<LOGR, FWD, true, TILE>(s, 0, 0, tw, tws, P.q);
     for (int i = threadIdx.x; i < TILE; i += blockDim.x) {
         const int u = i / C, c = i % C;
         uint64_t v = s[swz(i)];
@@ -157,9 +163,9 @@ __global__ void __launch_bounds__(kThreads, 2) ntt_pass_a(PassArgs a) {
 }
 
 // Pass B: contiguous blocks of R words, stages s_off..s_off+LOGR-1.
-template <int LOGR, bool FWD>
-__global__ void __launch_bounds__(kThreads, 2) ntt_pass_b(PassArgs a, uint32_t s_off) {
-    constexpr int TILE = Split<LOGR>::TILE;
+template <int LOGR, bool FWD, bool NARROW>
+__global__ void __launch_bounds__(Tile<LOGR, NARROW>::THREADS, NARROW ? 8 : 2) ntt_pass_b(PassArgs a, uint32_t s_off) {
+    constexpr int TILE = Tile<LOGR, NARROW>::WORDS;
     __shared__ uint64_t s[TILE];
     constexpr int R = 1 << LOGR;
     constexpr int S = TILE / R;
@@ -177,7 +183,7 @@ __global__ void __launch_bounds__(kThreads, 2) ntt_pass_b(PassArgs a, uint32_t s
     }
     __syncthreads();
     const uint64_t *tw = a.tw + (size_t)pi * a.n, *tws = a.tw_sh + (size_t)pi * a.n;
-    all_groups<LOGR, FWD, false>(s, s_off, tile * S, tw, tws, P.q);
+    all_groups<LOGR, FWD, false, TILE>(s, s_off, tile * S, tw, tws, P.q);
     const uint64_t q = P.q, two_q = 2 * q;
     for (int i = threadIdx.x; i < TILE / 2; i += blockDim.x) {
         ulonglong2 v;
@@ -193,15 +199,28 @@ __global__ void __launch_bounds__(kThreads, 2) ntt_pass_b(PassArgs a, uint32_t s
     }
 }
 
+// a launch whose wide tiles would not give every SM two CTAs runs the narrow variant
+constexpr uint32_t kNarrowBelow = 2 * 152;
+
+template <int A, int B, bool NARROW>
+void launch_fwd_t(const PassArgs &a, cudaStream_t st) {
+    ntt_pass_a<A, true, NARROW><<<a.n_limbs * (a.n / Tile<A, NARROW>::WORDS), Tile<A, NARROW>::THREADS, 0, st>>>(a);
+    ntt_pass_b<B, true, NARROW><<<a.n_limbs * (a.n / Tile<B, NARROW>::WORDS), Tile<B, NARROW>::THREADS, 0, st>>>(a, A);
+}
+template <int A, int B, bool NARROW>
+void launch_inv_t(const PassArgs &a, cudaStream_t st) {
+    ntt_pass_b<B, false, NARROW><<<a.n_limbs * (a.n / Tile<B, NARROW>::WORDS), Tile<B, NARROW>::THREADS, 0, st>>>(a, A);
+    ntt_pass_a<A, false, NARROW><<<a.n_limbs * (a.n / Tile<A, NARROW>::WORDS), Tile<A, NARROW>::THREADS, 0, st>>>(a);
+}
 template <int A, int B>
 void launch_fwd(const PassArgs &a, cudaStream_t st) {
-    ntt_pass_a<A, true><<<a.n_limbs * (a.n / Split<A>::TILE), kThreads, 0, st>>>(a);
-    ntt_pass_b<B, true><<<a.n_limbs * (a.n / Split<B>::TILE), kThreads, 0, st>>>(a, A);
+    if (a.n_limbs * (a.n / Split<A>::TILE) < kNarrowBelow) launch_fwd_t<A, B, true>(a, st);
+    else launch_fwd_t<A, B, false>(a, st);
 }
 template <int A, int B>
 void launch_inv(const PassArgs &a, cudaStream_t st) {
-    ntt_pass_b<B, false><<<a.n_limbs * (a.n / Split<B>::TILE), kThreads, 0, st>>>(a, A);
-    ntt_pass_a<A, false><<<a.n_limbs * (a.n / Split<A>::TILE), kThreads, 0, st>>>(a);
+    if (a.n_limbs * (a.n / Split<A>::TILE) < kNarrowBelow) launch_inv_t<A, B, true>(a, st);
+    else launch_inv_t<A, B, false>(a, st);
 }
 
 PassArgs make_args(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, LimbMap map, bool fwd) {
