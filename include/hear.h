@@ -233,6 +233,9 @@ hear_status hear_dbg_poly_mul(hear_context *ctx, uint32_t prime, const uint64_t 
                               uint64_t *out);
 /* forward+inverse NTT round trip of n_limb limbs (prime i % (n_q+n_p)) in place */
 hear_status hear_dbg_ntt_roundtrip(hear_context *ctx, uint64_t *limbs, size_t n_limb);
+/* device time of one forward and one inverse NTT over n_limb limbs of zero data (limb i
+ * uses prime i % (n_q+n_p)), averaged over `iters` launches after one warm-up; for tuning */
+hear_status hear_dbg_ntt_time(hear_context *ctx, size_t n_limb, int iters, float *ms_fwd, float *ms_inv);
 
 #ifdef __cplusplus
 }

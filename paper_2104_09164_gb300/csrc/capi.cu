@@ -595,4 +595,33 @@ hear_status hear_dbg_ntt_roundtrip(hear_context *ctx, uint64_t *limbs, size_t n_
     });
 }
 
+hear_status hear_dbg_ntt_time(hear_context *ctx, size_t n_limb, int iters, float *ms_fwd, float *ms_inv) {
+    if (!ctx || n_limb == 0 || iters < 1 || !ms_fwd || !ms_inv) return fail(HEAR_E_INVAL, "bad argument");
+    return guard(ctx, [&] {
+        cudaStream_t st = ctx->stream;
+        const size_t words = n_limb * ctx->n;
+        DevBuf d(words * 8, st);
+        HEAR_CHECK_CUDA(cudaMemsetAsync(d.p, 0, words * 8, st));
+        LimbMap m;
+        m.per_group = ctx->nqp();
+        m.q_count = ctx->n_q;
+        m.n_q = ctx->n_q;
+        cudaEvent_t e[3];
+        for (auto &x : e) HEAR_CHECK_CUDA(cudaEventCreate(&x));
+        ntt_forward(ctx, d.u64(), (uint32_t)n_limb, m, st);
+        ntt_inverse(ctx, d.u64(), (uint32_t)n_limb, m, st);
+        HEAR_CHECK_CUDA(cudaEventRecord(e[0], st));
+        for (int i = 0; i < iters; i++) ntt_forward(ctx, d.u64(), (uint32_t)n_limb, m, st);
+        HEAR_CHECK_CUDA(cudaEventRecord(e[1], st));
+        for (int i = 0; i < iters; i++) ntt_inverse(ctx, d.u64(), (uint32_t)n_limb, m, st);
+        HEAR_CHECK_CUDA(cudaEventRecord(e[2], st));
+        HEAR_CHECK_CUDA(cudaEventSynchronize(e[2]));
+        HEAR_CHECK_CUDA(cudaEventElapsedTime(ms_fwd, e[0], e[1]));
+        HEAR_CHECK_CUDA(cudaEventElapsedTime(ms_inv, e[1], e[2]));
+        *ms_fwd /= iters;
+        *ms_inv /= iters;
+        for (auto &x : e) cudaEventDestroy(x);
+    });
+}
+
 }  // extern "C"

@@ -217,6 +217,12 @@ __device__ __forceinline__ void mac_lazy(u128 &acc, uint64_t x, uint64_t y, uint
     add_to(acc, mul_wide(x, y));
     if (acc.hi >= q) acc.hi -= q;
 }
+// accumulate without the check: up to 8 products of residues below q < 2^61 keep acc.hi
+// below q + 8 q^2 / 2^64 < 2q; fold() then restores acc.hi < q
+__device__ __forceinline__ void mac_raw(u128 &acc, uint64_t x, uint64_t y) { add_to(acc, mul_wide(x, y)); }
+__device__ __forceinline__ void fold(u128 &acc, uint64_t q) {
+    if (acc.hi >= q) acc.hi -= q;
+}
 
 // BSGS inner sums out[j][c] = sum_b pt[j][b] (.) baby[b][c] on contiguous storage:
 // baby [n1][C][2][L1][N], pt [n2*n1][L1][N] (Montgomery), out [n2][C][2][L1][N].
@@ -254,8 +260,9 @@ __global__ void __launch_bounds__(256, 4) k_lincomb(uint32_t L1, uint32_t C, uin
 #pragma unroll
             for (int jj = 0; jj < 4; jj++) {
                 if (jj < (int)jn) {
-                    mac_lazy(acc[jj], x0, w0[jj], q);
-                    mac_lazy(acc[jj], x1, w1[jj], q);
+                    mac_raw(acc[jj], x0, w0[jj]);
+                    mac_raw(acc[jj], x1, w1[jj]);
+                    fold(acc[jj], q);
                 }
             }
         }
@@ -355,10 +362,16 @@ __global__ void __launch_bounds__(256, 3) k_ks_inner(const uint64_t *ext, int ex
 #pragma unroll
         for (int j = 0; j < MAXD; j++) {
             if (j < (int)dnum) {
-                mac_lazy(a0, xs[j], k0[j], q);
-                mac_lazy(a1, xs[j], k1[j], q);
+                mac_raw(a0, xs[j], k0[j]);
+                mac_raw(a1, xs[j], k1[j]);
+                if ((j & 7) == 7) {
+                    fold(a0, q);
+                    fold(a1, q);
+                }
             }
         }
+        fold(a0, q);
+        fold(a1, q);
         uint64_t *o = out + ((uint64_t)r * C + c) * out_ct + (uint64_t)t * n + kk;
         o[0] = mont_reduce(a0, q, qinv);
         o[(uint64_t)W * n] = mont_reduce(a1, q, qinv);

@@ -23,6 +23,7 @@ namespace {
 constexpr int kThreads = 256;
 
 struct PassArgs {
+    uint64_t small_below;    // primes below this skip the per-stage corrections
     uint64_t *data;
     uint32_t n_limbs;
     uint32_t log_n;
@@ -56,7 +57,11 @@ template <int LOGR, bool NARROW> struct Tile {
 // unit's butterflies use only 2^i (forward) or 2^(W-1-i) (inverse) distinct twiddles, which
 // are loaded once.  PASSA: sub-problems are the TILE/R columns of an R x (TILE/R) tile
 // (logical index u*NSP + sp); else TILE/R contiguous blocks of R words (sp*R + u).
-template <int LOGR, int W, int LS0, bool FWD, bool PASSA, int TILE>
+// RED = false (primes small enough, see ntt_forward / ntt_inverse): no per-stage
+// corrections.  Forward values then grow by at most 2q per stage; inverse sums double per
+// stage, so the subtraction adds 2^done * q, done = inverse stages applied before this one
+// (DONE0 before this pass).
+template <int LOGR, int W, int LS0, bool FWD, bool PASSA, int TILE, bool RED, int DONE0>
 __device__ __forceinline__ void stage_group(uint64_t *s, uint32_t s_off, uint32_t blk_base,
                                             const uint64_t *__restrict__ tw,
                                             const uint64_t *__restrict__ tws, uint64_t q) {
@@ -99,14 +104,18 @@ __device__ __forceinline__ void stage_group(uint64_t *s, uint32_t s_off, uint32_
                 }
                 uint64_t X = x[e], Y = x[e + half];
                 if (FWD) {
-                    X = X >= two_q ? X - two_q : X;
+                    if (RED) X = X >= two_q ? X - two_q : X;
                     const uint64_t T = shoup_lazy(Y, w, wsh, q);
                     x[e] = X + T;
                     x[e + half] = X - T + two_q;
-                } else {
+                } else if (RED) {
                     const uint64_t S = X + Y;
                     x[e] = S >= two_q ? S - two_q : S;
                     x[e + half] = shoup_lazy(X - Y + two_q, w, wsh, q);
+                } else {
+                    const int done = DONE0 + (LOGR - 1 - ls);
+                    x[e] = X + Y;
+                    x[e + half] = shoup_lazy(X - Y + (q << done), w, wsh, q);
                 }
             }
         }
@@ -118,18 +127,18 @@ __device__ __forceinline__ void stage_group(uint64_t *s, uint32_t s_off, uint32_
     }
 }
 
-template <int LOGR, bool FWD, bool PASSA, int TILE>
+template <int LOGR, bool FWD, bool PASSA, int TILE, bool RED, int DONE0>
 __device__ __forceinline__ void all_groups(uint64_t *s, uint32_t s_off, uint32_t blk_base,
                                            const uint64_t *tw, const uint64_t *tws, uint64_t q) {
     constexpr int W0 = Split<LOGR>::W0, W1 = Split<LOGR>::W1;
-    stage_group<LOGR, W0, FWD ? 0 : LOGR - 1, FWD, PASSA, TILE>(s, s_off, blk_base, tw, tws, q);
+    stage_group<LOGR, W0, FWD ? 0 : LOGR - 1, FWD, PASSA, TILE, RED, DONE0>(s, s_off, blk_base, tw, tws, q);
     __syncthreads();
-    stage_group<LOGR, W1, FWD ? W0 : LOGR - 1 - W0, FWD, PASSA, TILE>(s, s_off, blk_base, tw, tws, q);
+    stage_group<LOGR, W1, FWD ? W0 : LOGR - 1 - W0, FWD, PASSA, TILE, RED, DONE0>(s, s_off, blk_base, tw, tws, q);
     __syncthreads();
 }
 
 // Pass A: strided columns, stages 0..LOGR-1 (forward) or LOGR-1..0 (inverse, + N^-1).
-template <int LOGR, bool FWD, bool NARROW>
+template <int LOGR, bool FWD, bool NARROW, int DONE0>
 __global__ void __launch_bounds__(Tile<LOGR, NARROW>::THREADS, NARROW ? 8 : 2) ntt_pass_a(PassArgs a) {
     constexpr int TILE = Tile<LOGR, NARROW>::WORDS;
     __shared__ uint64_t s[TILE];
@@ -150,7 +159,8 @@ __global__ void __launch_bounds__(Tile<LOGR, NARROW>::THREADS, NARROW ? 8 : 2) n
     }
     __syncthreads();
     const uint64_t *tw = a.tw + (size_t)pi * a.n, *tws = a.tw_sh + (size_t)pi * a.n;
-    all_groups<LOGR, FWD, true, TILE>(s, 0, 0, tw, tws, P.q);
+    if (P.q < a.small_below) all_groups<LOGR, FWD, true, TILE, false, DONE0>(s, 0, 0, tw, tws, P.q);
+    else all_groups<LOGR, FWD, true, TILE, true, DONE0>(s, 0, 0, tw, tws, P.q);
     for (int i = threadIdx.x; i < TILE; i += blockDim.x) {
         const int u = i / C, c = i % C;
         uint64_t v = s[swz(i)];
@@ -183,13 +193,18 @@ __global__ void __launch_bounds__(Tile<LOGR, NARROW>::THREADS, NARROW ? 8 : 2) n
     }
     __syncthreads();
     const uint64_t *tw = a.tw + (size_t)pi * a.n, *tws = a.tw_sh + (size_t)pi * a.n;
-    all_groups<LOGR, FWD, false, TILE>(s, s_off, tile * S, tw, tws, P.q);
+    const bool small = P.q < a.small_below;
+    if (small) all_groups<LOGR, FWD, false, TILE, false, 0>(s, s_off, tile * S, tw, tws, P.q);
+    else all_groups<LOGR, FWD, false, TILE, true, 0>(s, s_off, tile * S, tw, tws, P.q);
     const uint64_t q = P.q, two_q = 2 * q;
     for (int i = threadIdx.x; i < TILE / 2; i += blockDim.x) {
         ulonglong2 v;
         v.x = s[swz(2 * i)];
         v.y = s[swz(2 * i + 1)];
-        if (FWD) {
+        if (FWD && small) {     // values below (1 + 2 logN) q: one Shoup reduction
+            v.x = shoup(v.x, 1, P.one_sh, q);
+            v.y = shoup(v.y, 1, P.one_sh, q);
+        } else if (FWD) {
             v.x = v.x >= two_q ? v.x - two_q : v.x;
             v.x = v.x >= q ? v.x - q : v.x;
             v.y = v.y >= two_q ? v.y - two_q : v.y;
@@ -204,13 +219,13 @@ constexpr uint32_t kNarrowBelow = 2 * 152;
 
 template <int A, int B, bool NARROW>
 void launch_fwd_t(const PassArgs &a, cudaStream_t st) {
-    ntt_pass_a<A, true, NARROW><<<a.n_limbs * (a.n / Tile<A, NARROW>::WORDS), Tile<A, NARROW>::THREADS, 0, st>>>(a);
+    ntt_pass_a<A, true, NARROW, 0><<<a.n_limbs * (a.n / Tile<A, NARROW>::WORDS), Tile<A, NARROW>::THREADS, 0, st>>>(a);
     ntt_pass_b<B, true, NARROW><<<a.n_limbs * (a.n / Tile<B, NARROW>::WORDS), Tile<B, NARROW>::THREADS, 0, st>>>(a, A);
 }
 template <int A, int B, bool NARROW>
 void launch_inv_t(const PassArgs &a, cudaStream_t st) {
     ntt_pass_b<B, false, NARROW><<<a.n_limbs * (a.n / Tile<B, NARROW>::WORDS), Tile<B, NARROW>::THREADS, 0, st>>>(a, A);
-    ntt_pass_a<A, false, NARROW><<<a.n_limbs * (a.n / Tile<A, NARROW>::WORDS), Tile<A, NARROW>::THREADS, 0, st>>>(a);
+    ntt_pass_a<A, false, NARROW, B><<<a.n_limbs * (a.n / Tile<A, NARROW>::WORDS), Tile<A, NARROW>::THREADS, 0, st>>>(a);
 }
 template <int A, int B>
 void launch_fwd(const PassArgs &a, cudaStream_t st) {
@@ -235,6 +250,9 @@ PassArgs make_args(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, Li
     const uint64_t *base = ctx->d_tw.u64();
     a.tw = base + (fwd ? 0 : 2 * plane);
     a.tw_sh = base + (fwd ? plane : 3 * plane);
+    // forward: values stay below (1 + 2 logN) q < 2^64 for q < 2^58; inverse: below
+    // 2^(logN+1) q < 2^64 for q < 2^(63 - logN)
+    a.small_below = fwd ? (1ull << 58) : (1ull << (63 - ctx->log_n));
     return a;
 }
 

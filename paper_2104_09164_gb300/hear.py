@@ -103,6 +103,8 @@ def _load():
         "hear_launch_count": (ctypes.c_uint64, []),
         "hear_dbg_poly_mul": (st, [_vp, ctypes.c_uint32, _u64p, _u64p, _u64p]),
         "hear_dbg_ntt_roundtrip": (st, [_vp, _u64p, ctypes.c_size_t]),
+        "hear_dbg_ntt_time": (st, [_vp, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
+                                   ctypes.POINTER(ctypes.c_float)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -398,3 +400,10 @@ def hear_dbg_ntt_roundtrip(ctx, limbs):
     x = _arr(limbs, np.uint64).copy()
     _check(lib.hear_dbg_ntt_roundtrip(ctx, _p(x, _u64p), x.shape[0]))
     return x
+
+
+def hear_dbg_ntt_time(ctx, n_limb, iters=20):
+    """-> (ms per forward NTT, ms per inverse NTT) over n_limb limbs"""
+    f, i = ctypes.c_float(), ctypes.c_float()
+    _check(lib.hear_dbg_ntt_time(ctx, int(n_limb), int(iters), ctypes.byref(f), ctypes.byref(i)))
+    return f.value, i.value
