@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clips", type=int, default=None, help="clips in the batch (default: the workload's)")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--rates", default="500,2000,8000", help="request rates (req/s) of the served sweep")
     return ap.parse_args()
 
 
@@ -313,6 +315,79 @@ def run_e2e(S, steps, warmup, torch, stream):
     return el, pin_in.nbytes, pin_out.nbytes
 
 
+def run_served(H, S, rates, seconds=2.0, max_batch=32, n_slots=2, seed=601):
+    """Poisson request stream against the continuous-batching server: each request carries
+    1-8 clips (uniform) of the small network (4 clips per ciphertext -> 1 or 2 ciphertexts);
+    returns per-rate throughput and p50/p99 latency (submit -> result ready)."""
+    w = S.w
+    k = w.slots // w.clip_dim
+    words1 = H.hear_ciphertext_export(S.cts[0]).reshape(-1)
+    scale = 2.0 ** w.log2_scale
+    rng = np.random.default_rng(seed)
+    srv = H.hear_server_create(S.model, S.evk, max_batch=max_batch, n_slots=n_slots, hbm_budget_bytes=96 << 30)
+    out = []
+    try:
+        out_words = None
+        # warm-up: every power-of-two batch size on every slot captures its graphs once
+        ids = []
+        for rep in range(2 * n_slots):
+            for b in (32, 16, 8, 4, 2, 1):
+                if b <= max_batch:
+                    ids.append((H.hear_server_submit(srv, np.tile(words1, b), b, b * k, scale), b))
+        res = {}
+        while len(res) < len(ids):
+            for rid, b in ids:
+                if rid not in res:
+                    if out_words is None:
+                        out_words = H.hear_evaluate_host(S.model, S.evk, words1, 1, scale)[0].size
+                    r = H.hear_server_poll(srv, rid, b * out_words)
+                    if r is not None:
+                        res[rid] = r
+            time.sleep(0.0005)
+        for lam in rates:
+            base = H.hear_server_stats(srv)
+            t0 = time.perf_counter()
+            t_next = t0
+            pend = {}
+            lat = []
+            clips = 0
+
+            def drain():
+                for rid in list(pend):
+                    n_ct, ts = pend[rid]
+                    if H.hear_server_poll(srv, rid, n_ct * out_words) is not None:
+                        lat.append((time.perf_counter() - ts) * 1e3)
+                        del pend[rid]
+            while True:
+                now = time.perf_counter()
+                if now - t0 >= seconds:
+                    break
+                while t_next <= now:
+                    n_clips = int(rng.integers(1, 9))
+                    n_ct = (n_clips + k - 1) // k
+                    rid = H.hear_server_submit(srv, np.tile(words1, n_ct), n_ct, n_clips, scale)
+                    pend[rid] = (n_ct, time.perf_counter())
+                    clips += n_clips
+                    t_next += rng.exponential(1.0 / lam)
+                drain()
+                time.sleep(0.0002)
+            while pend:
+                drain()
+                time.sleep(0.0002)
+            el = time.perf_counter() - t0
+            st = H.hear_server_stats(srv)
+            lat.sort()
+            out.append({"rate_req_s": lam, "offered_inferences_s": clips / seconds,
+                        "inferences_s": (st["clips_done"] - base["clips_done"]) / el,
+                        "requests": st["requests_done"] - base["requests_done"],
+                        "batches": st["batches"] - base["batches"],
+                        "p50_ms": lat[len(lat) // 2] if lat else None,
+                        "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))] if lat else None})
+    finally:
+        H.hear_server_destroy(srv)
+    return out
+
+
 def main_gpu(a):
     import torch
     dist = Dist()
@@ -353,6 +428,12 @@ def main_gpu(a):
             "stages_ms_per_step": {k: v[1] / psteps for k, v in sorted(stages.items(), key=lambda kv: -kv[1][1])},
             "clocks": clocks, "gpu_launches": launches,
         }
+    if result is not None and not a.no_served and a.workload == "small" and a.clips is None and dist.world == 1:
+        sweep = run_served(H, S, [float(x) for x in a.rates.split(",")])
+        result["served"] = {"workload": "small network, Poisson arrivals, 1-8 clips per request, "
+                                        "continuous batching (max 32 ciphertexts, 2 batches in flight)",
+                            "note": "latency = client submit -> result read back (host), per rate",
+                            "sweep": sweep}
     if not a.no_batched and a.workload == "small" and a.clips is None:
         S.close()
         wl = make_workload("large")

@@ -190,6 +190,41 @@ hear_status hear_evaluate_host(const hear_model *m, const hear_eval_keys *evk, c
                                size_t n_ct, double scale, uint64_t *out_words, size_t cap, size_t *n,
                                uint32_t *level_out, double *scale_out, void *stream);
 
+/* ---- continuous-batching server (cloud) ----
+ * Requests carry ciphertexts in the coefficient domain in host memory (the format
+ * hear_ciphertext_export produces; uint64[n_ct][2][L+1][N] at the top level, all at one
+ * scale).  A worker thread admits pending requests in arrival order while the ciphertexts
+ * in flight fit hbm_budget_bytes (each charged bytes_per_ciphertext: its share of the
+ * evaluation's device work buffers plus input and output), packs up to max_batch
+ * ciphertexts into one batch and runs it on one of n_slots streams, so batches admitted
+ * while others run overlap on the device.  Each batch replays captured CUDA graphs of the
+ * whole network (the first batch of each size captures them).  Results are the result
+ * ciphertexts in the coefficient domain, uint64[n_ct][2][level_out+1][N]; they are
+ * bit-identical to evaluating the request alone. */
+typedef struct hear_server hear_server;
+typedef struct hear_server_config {
+    uint32_t max_batch;          /* ciphertexts per launch (>= 1)                         */
+    uint32_t n_slots;            /* batches in flight, 1..8                               */
+    uint64_t hbm_budget_bytes;   /* device bytes for the ciphertexts in flight            */
+} hear_server_config;
+typedef struct hear_server_counters {
+    uint64_t requests_done, ciphertexts_done, clips_done, batches, pending;
+    uint64_t max_in_flight_ciphertexts, bytes_per_ciphertext;
+    double p50_ms, p99_ms, mean_ms;   /* submit -> result ready, completed requests      */
+} hear_server_counters;
+hear_status hear_server_create(const hear_model *m, const hear_eval_keys *evk, const hear_server_config *cfg,
+                               hear_server **out);
+/* queue a request of n_ct ciphertexts (n_clips clips, for the statistics); the words are
+ * copied before the call returns */
+hear_status hear_server_submit(hear_server *s, const uint64_t *words, size_t n_ct, uint32_t n_clips, double scale,
+                               uint64_t *request_id);
+/* *done = 1 and the result copied to out (cap words, *n written) once the request is
+ * complete (the id is then released); *done = 0 while it is queued or running */
+hear_status hear_server_poll(hear_server *s, uint64_t request_id, uint64_t *out, size_t cap, size_t *n, int *done);
+hear_status hear_server_stats(hear_server *s, hear_server_counters *stats);
+/* waits for the batches in flight, drops queued requests */
+void hear_server_destroy(hear_server *s);
+
 /* ---- rescale for callers that cannot allocate device memory ----
  * The paper has no counterpart: this entry point exists for callers that cannot call
  * cudaMalloc -- a process whose device-memory quota is already held by another

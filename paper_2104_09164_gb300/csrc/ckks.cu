@@ -503,12 +503,15 @@ DevBuf evaluate_batch(const hear_model *m, const hear_eval_keys *evk, size_t l0,
 }
 
 hear_model::Plan *graph_plan(const hear_model *m, const hear_eval_keys *evk, size_t l0, size_t l1, uint32_t n_ct,
-                             double scale_in, cudaStream_t st) {
+                             double scale_in, cudaStream_t st, uint32_t slot) {
     for (auto &p : m->plans)
-        if (p->evk_serial == evk->serial && p->l0 == l0 && p->l1 == l1 && p->n_ct == n_ct && p->scale_in == scale_in) return p.get();
+        if (p->evk_serial == evk->serial && p->l0 == l0 && p->l1 == l1 && p->n_ct == n_ct && p->scale_in == scale_in &&
+            p->slot == slot)
+            return p.get();
     hear_context *c = m->ctx;
     auto plan = std::make_unique<hear_model::Plan>();
     plan->evk_serial = evk->serial;
+    plan->slot = slot;
     plan->l0 = l0;
     plan->l1 = l1;
     plan->n_ct = n_ct;

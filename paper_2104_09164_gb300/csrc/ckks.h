@@ -28,6 +28,7 @@ struct hear_model {
         uint64_t evk_serial = 0;   // keys the graph reads (never reused after they are freed)
         size_t l0 = 0, l1 = 0;
         uint32_t n_ct = 0, level_out = 0;
+        uint32_t slot = 0;         // independent copies for concurrent users (server slots)
         double scale_in = 0, scale_out = 0;
         hear::DevBuf X, Y;
         cudaGraphExec_t exec = nullptr;
@@ -88,6 +89,6 @@ DevBuf evaluate_batch(const hear_model *m, const hear_eval_keys *evk, size_t l0,
 // graph plan for (evk, l0, l1, n_ct, scale_in): built on first use (one direct warm-up run,
 // then stream capture); the caller fills plan->X, launches plan->exec and reads plan->Y
 hear_model::Plan *graph_plan(const hear_model *m, const hear_eval_keys *evk, size_t l0, size_t l1, uint32_t n_ct,
-                             double scale_in, cudaStream_t st);
+                             double scale_in, cudaStream_t st, uint32_t slot = 0);
 
 }  // namespace hear

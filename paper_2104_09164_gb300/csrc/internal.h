@@ -10,7 +10,7 @@
 #include <stdexcept>
 #include <string>
 #include <vector>
-#include "../../include/hear.h"
+#include "hear.h"   // include/ is on the include path
 
 namespace hear {
 

@@ -139,7 +139,7 @@ __device__ __forceinline__ void all_groups(uint64_t *s, uint32_t s_off, uint32_t
 
 // Pass A: strided columns, stages 0..LOGR-1 (forward) or LOGR-1..0 (inverse, + N^-1).
 template <int LOGR, bool FWD, bool NARROW, int DONE0>
-__global__ void __launch_bounds__(Tile<LOGR, NARROW>::THREADS, NARROW ? 8 : 2) ntt_pass_a(PassArgs a) {
+__global__ void __launch_bounds__(Tile<LOGR, NARROW>::THREADS, NARROW ? 8 : 3) ntt_pass_a(PassArgs a) {
     constexpr int TILE = Tile<LOGR, NARROW>::WORDS;
     __shared__ uint64_t s[TILE];
     constexpr int R = 1 << LOGR;
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(Tile<LOGR, NARROW>::THREADS, NARROW ? 8 : 2) n
 
 // Pass B: contiguous blocks of R words, stages s_off..s_off+LOGR-1.
 template <int LOGR, bool FWD, bool NARROW>
-__global__ void __launch_bounds__(Tile<LOGR, NARROW>::THREADS, NARROW ? 8 : 2) ntt_pass_b(PassArgs a, uint32_t s_off) {
+__global__ void __launch_bounds__(Tile<LOGR, NARROW>::THREADS, NARROW ? 8 : 3) ntt_pass_b(PassArgs a, uint32_t s_off) {
     constexpr int TILE = Tile<LOGR, NARROW>::WORDS;
     __shared__ uint64_t s[TILE];
     constexpr int R = 1 << LOGR;

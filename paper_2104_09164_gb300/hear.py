@@ -44,6 +44,17 @@ class hear_profile_entry(ctypes.Structure):
                 ("bytes", ctypes.c_double)]
 
 
+class hear_server_config(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_uint32), ("n_slots", ctypes.c_uint32), ("hbm_budget_bytes", ctypes.c_uint64)]
+
+
+class hear_server_counters(ctypes.Structure):
+    _fields_ = [("requests_done", ctypes.c_uint64), ("ciphertexts_done", ctypes.c_uint64),
+                ("clips_done", ctypes.c_uint64), ("batches", ctypes.c_uint64), ("pending", ctypes.c_uint64),
+                ("max_in_flight_ciphertexts", ctypes.c_uint64), ("bytes_per_ciphertext", ctypes.c_uint64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double)]
+
+
 class HearError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("hear error %d: %s" % (code, msg))
@@ -97,6 +108,12 @@ def _load():
                                      ctypes.POINTER(_vp), _vp]),
         "hear_evaluate_host": (st, [_vp, _vp, _u64p, ctypes.c_size_t, ctypes.c_double, _u64p, ctypes.c_size_t,
                                     _szp, _u32p, _dp, _vp]),
+        "hear_server_create": (st, [_vp, _vp, ctypes.POINTER(hear_server_config), ctypes.POINTER(_vp)]),
+        "hear_server_submit": (st, [_vp, _u64p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_double,
+                                    ctypes.POINTER(ctypes.c_uint64)]),
+        "hear_server_poll": (st, [_vp, ctypes.c_uint64, _u64p, ctypes.c_size_t, _szp, ctypes.POINTER(ctypes.c_int)]),
+        "hear_server_stats": (st, [_vp, ctypes.POINTER(hear_server_counters)]),
+        "hear_server_destroy": (None, [_vp]),
         "hear_rescale_noalloc": (st, [_vp, _u64p, ctypes.c_uint32, ctypes.c_uint32, _u64p, _vp]),
         "hear_profile_begin": (st, [_vp]),
         "hear_profile_end": (st, [_vp, ctypes.POINTER(hear_profile_entry), ctypes.c_size_t, _szp]),
@@ -358,6 +375,40 @@ def hear_evaluate_host(m, evk, in_words, n_ct, scale, out=None, stream=None):
     _check(lib.hear_evaluate_host(m, evk, _p(w, _u64p), int(n_ct), float(scale), _p(out, _u64p), out.size,
                                   ctypes.byref(n), ctypes.byref(lv), ctypes.byref(sc), _stream(stream)))
     return out, lv.value, sc.value
+
+
+# ---------------------------------------------------------------- serving
+def hear_server_create(m, evk, max_batch=32, n_slots=2, hbm_budget_bytes=64 << 30):
+    cfg = hear_server_config(int(max_batch), int(n_slots), int(hbm_budget_bytes))
+    h = _vp()
+    _check(lib.hear_server_create(m, evk, ctypes.byref(cfg), ctypes.byref(h)))
+    return h.value
+
+
+def hear_server_submit(s, words, n_ct, n_clips, scale):
+    w = _arr(words, np.uint64).reshape(-1)
+    rid = ctypes.c_uint64()
+    _check(lib.hear_server_submit(s, _p(w, _u64p), int(n_ct), int(n_clips), float(scale), ctypes.byref(rid)))
+    return rid.value
+
+
+def hear_server_poll(s, request_id, out_words):
+    """-> result array (uint64, out_words words) once done, else None"""
+    out = np.empty(int(out_words), dtype=np.uint64)
+    n = ctypes.c_size_t(0)
+    done = ctypes.c_int(0)
+    _check(lib.hear_server_poll(s, int(request_id), _p(out, _u64p), out.size, ctypes.byref(n), ctypes.byref(done)))
+    return out[:n.value] if done.value else None
+
+
+def hear_server_stats(s):
+    st = hear_server_counters()
+    _check(lib.hear_server_stats(s, ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in hear_server_counters._fields_}
+
+
+def hear_server_destroy(s):
+    lib.hear_server_destroy(s)
 
 
 def hear_rescale_noalloc(ctx, words, level, n_poly, stream=None):
