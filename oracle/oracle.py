@@ -302,6 +302,21 @@ class Oracle:
         _chk(lib().or_add(self.h, a.level, a.n_poly, P(a.data), P(b.data), P(out)), "add")
         return Ct(out, a.level, a.scale)
 
+    def add_plain(self, ct: Ct, pt):
+        """ct + pt: the plaintext (same level, NTT domain) is added to c0; scale unchanged"""
+        pt = np.ascontiguousarray(pt, dtype=np.uint64)
+        assert pt.shape == (ct.level + 1, self.n)
+        out = ct.data.copy()
+        c0 = np.empty((1, ct.level + 1, self.n), dtype=np.uint64)
+        _chk(lib().or_add(self.h, ct.level, 1, P(np.ascontiguousarray(ct.data[:1])), P(pt), P(c0)), "add")
+        out[0] = c0[0]
+        return Ct(out, ct.level, ct.scale)
+
+    def drop_level(self, ct: Ct):
+        """the same ciphertext over Q_(level-1): the last residue is discarded (no division,
+        scale unchanged), which is how a ciphertext meets a partner one level down"""
+        return Ct(np.ascontiguousarray(ct.data[:, :ct.level]), ct.level - 1, ct.scale)
+
     def mulplain(self, ct: Ct, pt, pt_scale):
         out = np.empty_like(ct.data)
         pt = np.ascontiguousarray(pt, dtype=np.uint64)
