@@ -60,6 +60,7 @@ typedef struct hear_public_key hear_public_key;
 typedef struct hear_eval_keys hear_eval_keys;
 typedef struct hear_ciphertext hear_ciphertext;
 typedef struct hear_model hear_model;
+typedef struct hear_cnn hear_cnn;
 
 /* Encryption parameters.  The ciphertext modulus is Q = q_0 * ... * q_{n_q-1} (top level
  * L = n_q - 1); the n_p special primes p_0..p_{K-1} are used by key switching only.
@@ -224,6 +225,104 @@ hear_status hear_server_poll(hear_server *s, uint64_t request_id, uint64_t *out,
 hear_status hear_server_stats(hear_server *s, hear_server_counters *stats);
 /* waits for the batches in flight, drops queued requests */
 void hear_server_destroy(hear_server *s);
+
+/* ---- skeleton CNN (cloud) ----
+ * Methods, "Single-channel homomorphic convolutions", "Multi-channel homomorphic
+ * convolutions" (Eq. conv), "Fast homomorphic convolutions", "Non-convolutional layers",
+ * "Data encryption" and "Algorithmic and cryptographic optimizations" (full-step /
+ * giant-step / baby-step strategies, hoisting, lazy rescaling, level-aware encoding).
+ *
+ * Slot layout.  dist = the smallest power of two >= h*w; the N/2 slots are cbar = N/2/dist
+ * blocks of dist slots, each holding one channel map row-major with row pitch `pitch`
+ * (map position (y, x) at block offset stride*(y*pitch + x); stride > 1 after pooling).
+ * With c channels >= cbar, ciphertext i block m holds channel cbar*i + m (c must be a
+ * multiple of cbar); with c < cbar (cbar a multiple of c) one ciphertext holds copies,
+ * block m = channel m mod c.
+ *
+ * Layers (the network must already be collapsed: bias, batch normalisation and the
+ * activation of a block folded into one per-channel quadratic; the 1/2, 1/4 or 1/(h*w)
+ * of average pooling folded into the next linear layer's weights):
+ *   CONV  same-padded, stride-1 convolution, w = float64[c_out][c_in][f_h][f_w] (1D: f_h =
+ *         1), c_out a multiple of cbar.  Rotation r + dist*l for tap (du, dv), r =
+ *         stride*(du*pitch + dv), block shift l; the plaintexts carry the zero padding.
+ *         fast = 1 (input punctured, stride > 1): merge-and-conquer -- pack n_P = (stride
+ *         in 1D, stride^2 in 2D, at most the input ciphertext count, a power of two)
+ *         punctured ciphertexts into one (mask plaintext, rescale, rotation by -phase,
+ *         sum: one level), convolve, then rotate-and-sum over the phases (log2 n_P
+ *         rotations).  Strategy: how each rotation a = b + g splits into a hoisted baby
+ *         step b and a giant step g applied to the summed products:
+ *           HEAR_STRATEGY_FULL   b = a, g = 0 (every rotated input precomputed)
+ *           HEAR_STRATEGY_BABY   b = r, g = dist*l
+ *           HEAR_STRATEGY_GIANT  b = dist*l, g = r
+ *           HEAR_STRATEGY_HYBRID b = r + dist*(l mod n1), g = dist*n1*floor(l/n1)
+ *   QUAD  per-channel a, b, c (float64[c]): x <- a x^2 + b x + c at the valid map
+ *         positions, 0 elsewhere; two levels: u = rescale(x (.) a) + b, then
+ *         rescale(relin(x * u)) + c.
+ *   POOL  window 2 (1D) / 2x2 (2D), stride 2: x <- x + rho^stride(x) (2D: then
+ *         + rho^(stride*pitch)); the stride doubles and the map halves (floor).
+ *   GAP   global pooling: rotate-and-sum by stride, 2 stride, .. < dist; block start m
+ *         then holds the channel's sum (needs zeros outside the map: follows QUAD).
+ *   FC    w = float64[c_out][c] on GAP output, c_out <= cbar, optional bias
+ *         float64[c_out]; logit o lands at slot o*dist of the single output ciphertext.
+ * Every plaintext multiplied into a ciphertext at level l is encoded at scale q_l with the
+ * limbs of level l only, so slot values keep their scale through each rescale. */
+#define HEAR_CNN_CONV 1
+#define HEAR_CNN_QUAD 2
+#define HEAR_CNN_POOL 3
+#define HEAR_CNN_GAP 4
+#define HEAR_CNN_FC 5
+#define HEAR_STRATEGY_HYBRID 0
+#define HEAR_STRATEGY_FULL 1
+#define HEAR_STRATEGY_BABY 2
+#define HEAR_STRATEGY_GIANT 3
+typedef struct hear_cnn_input {
+    uint32_t conv_dims;   /* 1 or 2                                                     */
+    uint32_t c_in;        /* channels of the input map                                  */
+    uint32_t h, w;        /* map size (1D: h = 1)                                       */
+    uint32_t pitch;       /* row pitch in slots (0 = w)                                 */
+    uint32_t stride;      /* puncture of the input (1 for an encrypted input tensor)    */
+} hear_cnn_input;
+typedef struct hear_cnn_layer {
+    uint32_t kind;
+    uint32_t c_out;             /* CONV, FC                                             */
+    uint32_t f_h, f_w;          /* CONV                                                 */
+    const double *w;            /* CONV, FC                                             */
+    const double *bias;         /* FC (or NULL)                                         */
+    const double *a, *b, *c;    /* QUAD                                                 */
+    uint32_t fast;              /* CONV                                                 */
+    uint32_t strategy, n1;      /* CONV, FC (n1: HYBRID; 0 = min(4, block shifts))      */
+} hear_cnn_layer;
+/* The layers become a plan of slot-level operations; every ciphertext of a sample passes
+ * through each operation.  Operation kinds: */
+#define HEAR_CNN_OP_DIAG 1    /* sum of plaintext (.) rotation products, one rescale    */
+#define HEAR_CNN_OP_PACK 2    /* fast convolution step (i)                               */
+#define HEAR_CNN_OP_ROTSUM 3  /* rotate-and-sum (pooling, GAP, fast convolution (iii))   */
+#define HEAR_CNN_OP_QUAD 4
+#define HEAR_CNN_OP_BIAS 5
+typedef struct hear_cnn_op_info {
+    uint32_t kind;
+    uint32_t layer;                 /* index of the layer it comes from                  */
+    uint32_t n_in, n_out;           /* ciphertexts per sample before / after             */
+    uint32_t level_in, level_out;
+    uint32_t n_babies, n_giants;    /* DIAG: rotation amounts (0 included)               */
+    uint32_t n_keyswitch;           /* key switches per sample                           */
+} hear_cnn_op_info;
+hear_status hear_cnn_create(hear_context *ctx, const hear_cnn_input *input, const hear_cnn_layer *layers,
+                            size_t n_layers, hear_cnn **out);
+void hear_cnn_destroy(hear_cnn *m);
+/* rotation steps (slots, in [1, N/2)) the plan needs keys for */
+hear_status hear_cnn_rotations(const hear_cnn *m, int32_t *steps, size_t cap, size_t *n);
+hear_status hear_cnn_ops(const hear_cnn *m, hear_cnn_op_info *ops, size_t cap, size_t *n);
+/* slots of the logits in the output ciphertext (FC last), else empty */
+hear_status hear_cnn_output_slots(const hear_cnn *m, uint32_t *slots, size_t cap, size_t *n);
+/* encrypt one input tensor x = float64[c_in][h][w] (stride-1 input) into the plan's input
+ * ciphertexts (ct ids ct_id, ct_id+1, ..; one per input ciphertext); out[n_in] */
+hear_status hear_cnn_encrypt(hear_context *ctx, const hear_public_key *pk, const hear_cnn *m, const double *x,
+                             uint64_t seed, uint64_t ct_id, hear_ciphertext **out, void *stream);
+/* run operations [op0, op1) on n_samples samples: in[s * n_in + i] (n_in of op0, all at
+ * op0's input level and one scale), out[s * n_out + j] (n_out of op1-1) */
+hear_status hear_cnn_evaluate(const hear_cnn *m, const hear_eval_keys *evk, size_t op0, size_t op1,
+                              hear_ciphertext *const *in, size_t n_samples, hear_ciphertext **out, void *stream);
 
 /* ---- rescale for callers that cannot allocate device memory ----
  * The paper has no counterpart: this entry point exists for callers that cannot call

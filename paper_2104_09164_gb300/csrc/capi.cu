@@ -625,3 +625,114 @@ hear_status hear_dbg_ntt_time(hear_context *ctx, size_t n_limb, int iters, float
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ skeleton CNN
+#include "cnn.h"
+
+extern "C" {
+
+hear_status hear_cnn_create(hear_context *ctx, const hear_cnn_input *input, const hear_cnn_layer *layers,
+                            size_t n_layers, hear_cnn **out) {
+    if (!ctx || !input || !layers || !out) return fail(HEAR_E_INVAL, "null argument");
+    return guard(ctx, [&] { *out = cnn_create(ctx, input, layers, n_layers); });
+}
+
+void hear_cnn_destroy(hear_cnn *m) {
+    if (!m) return;
+    cudaSetDevice(m->ctx->device);
+    cudaDeviceSynchronize();
+    delete m;
+}
+
+hear_status hear_cnn_rotations(const hear_cnn *m, int32_t *steps, size_t cap, size_t *n) {
+    if (!m) return fail(HEAR_E_INVAL, "null model");
+    return copy_out(m->rotations, steps, cap, n);
+}
+
+hear_status hear_cnn_ops(const hear_cnn *m, hear_cnn_op_info *ops, size_t cap, size_t *n) {
+    if (!m) return fail(HEAR_E_INVAL, "null model");
+    std::vector<hear_cnn_op_info> v;
+    for (size_t k = 0; k < m->ops.size(); k++) {
+        const hear_cnn::Op &op = m->ops[k];
+        hear_cnn_op_info i{};
+        i.kind = op.kind;
+        i.layer = m->op_layer[k];
+        i.n_in = op.n_in;
+        i.n_out = op.n_out;
+        i.level_in = op.level_in;
+        i.level_out = op.level_out;
+        i.n_babies = (uint32_t)op.babies.size();
+        i.n_giants = (uint32_t)op.giants.size();
+        if (op.kind == HEAR_CNN_OP_DIAG)
+            i.n_keyswitch = op.n_in * (i.n_babies - 1) + op.n_out * (i.n_giants - 1);
+        else if (op.kind == HEAR_CNN_OP_PACK)
+            i.n_keyswitch = op.n_out * ((uint32_t)op.offs.size() - 1);
+        else if (op.kind == HEAR_CNN_OP_ROTSUM)
+            i.n_keyswitch = op.n_in * (uint32_t)op.steps.size();
+        else if (op.kind == HEAR_CNN_OP_QUAD)
+            i.n_keyswitch = op.n_in;
+        v.push_back(i);
+    }
+    return copy_out(v, ops, cap, n);
+}
+
+hear_status hear_cnn_output_slots(const hear_cnn *m, uint32_t *slots, size_t cap, size_t *n) {
+    if (!m) return fail(HEAR_E_INVAL, "null model");
+    return copy_out(m->out_slots, slots, cap, n);
+}
+
+hear_status hear_cnn_encrypt(hear_context *ctx, const hear_public_key *pk, const hear_cnn *m, const double *x,
+                             uint64_t seed, uint64_t ct_id, hear_ciphertext **out, void *stream) {
+    if (!ctx || !pk || !m || !x || !out) return fail(HEAR_E_INVAL, "null argument");
+    if (pk->ctx != ctx || m->ctx != ctx) return fail(HEAR_E_STATE, "handle from another context");
+    if (m->ops.empty()) return fail(HEAR_E_STATE, "empty model");
+    return guard(ctx, [&] {
+        std::vector<double> z = cnn_pack_input(m, x);
+        const size_t S = ctx->n / 2, n_ct = z.size() / S;
+        std::vector<std::unique_ptr<hear_ciphertext>> res;
+        for (size_t i = 0; i < n_ct; i++)
+            res.emplace_back(encrypt_slots(ctx, pk, z.data() + i * S, ctx->default_scale, seed, ct_id + i,
+                                           stream_of(ctx, stream)));
+        for (size_t i = 0; i < n_ct; i++) out[i] = res[i].release();
+    });
+}
+
+hear_status hear_cnn_evaluate(const hear_cnn *m, const hear_eval_keys *evk, size_t op0, size_t op1,
+                              hear_ciphertext *const *in, size_t n_samples, hear_ciphertext **out, void *stream) {
+    if (!m || !evk || !in || !out) return fail(HEAR_E_INVAL, "null argument");
+    hear_context *c = m->ctx;
+    if (evk->ctx != c) return fail(HEAR_E_STATE, "key from another context");
+    if (op0 >= op1 || op1 > m->ops.size()) return fail(HEAR_E_INVAL, "bad operation range");
+    if (n_samples == 0 || n_samples > 65535) return fail(HEAR_E_INVAL, "n_samples must be in [1, 65535]");
+    const hear_cnn::Op &first = m->ops[op0], &last = m->ops[op1 - 1];
+    const uint32_t n_in = first.n_in, n_out = last.n_out, C = (uint32_t)n_samples;
+    for (size_t k = 0; k < n_samples * n_in; k++) {
+        if (!in[k] || in[k]->ctx != c) return fail(HEAR_E_STATE, "ciphertext from another context");
+        if (in[k]->n_poly != 2 || in[k]->level != first.level_in)
+            return fail(HEAR_E_LEVEL, "inputs must be 2-polynomial ciphertexts at the operation's level");
+        if (in[k]->scale != in[0]->scale) return fail(HEAR_E_SCALE, "inputs at different scales");
+    }
+    return guard(c, [&] {
+        cudaStream_t st = stream_of(c, stream);
+        const uint64_t ctw = 2ull * (first.level_in + 1) * c->n;
+        DevBuf x((size_t)n_in * C * ctw * 8, st);
+        for (uint32_t s = 0; s < C; s++)
+            for (uint32_t i = 0; i < n_in; i++)
+                HEAR_CHECK_CUDA(cudaMemcpyAsync(x.u64() + ((uint64_t)i * C + s) * ctw, in[(size_t)s * n_in + i]->d.p,
+                                                ctw * 8, cudaMemcpyDeviceToDevice, st));
+        double so = 0;
+        DevBuf y = cnn_evaluate(m, evk, op0, op1, x.u64(), C, in[0]->scale, &so, st);
+        const uint64_t ctw_o = 2ull * (last.level_out + 1) * c->n;
+        std::vector<std::unique_ptr<hear_ciphertext>> res(n_out * (size_t)C);
+        for (uint32_t s = 0; s < C; s++)
+            for (uint32_t j = 0; j < n_out; j++) {
+                auto &h = res[(size_t)s * n_out + j];
+                h.reset(new_ct(c, last.level_out, 2, so, st));
+                HEAR_CHECK_CUDA(cudaMemcpyAsync(h->d.p, y.u64() + ((uint64_t)j * C + s) * ctw_o, ctw_o * 8,
+                                                cudaMemcpyDeviceToDevice, st));
+            }
+        for (size_t k = 0; k < res.size(); k++) out[k] = res[k].release();
+    });
+}
+
+}  // extern "C"

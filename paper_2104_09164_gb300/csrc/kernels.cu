@@ -54,12 +54,13 @@ __global__ void k_small_to_limbs(const int8_t *e, uint64_t *out, uint32_t n_limb
     out[m.offset(b, n) + k] = v < 0 ? q - (uint64_t)(-v) : (uint64_t)v;
 }
 
+// group g of the limb map reads v + g * v_stride (v_stride 0: one vector for every limb)
 __global__ void k_i64_to_limbs(const int64_t *v, uint64_t *out, uint32_t n_limbs, LimbMap m, const DevPrime *P,
-                               uint32_t n) {
+                               uint32_t n, uint64_t v_stride) {
     uint32_t b = limb_yz(), pi, k = COEF();
     if (b >= n_limbs || !m.resolve(b, &pi)) return;
     const DevPrime p = P[pi];
-    int64_t x = v[k];
+    int64_t x = v[(uint64_t)(b / m.per_group) * v_stride + k];
     uint64_t mag = x < 0 ? (uint64_t)0 - (uint64_t)x : (uint64_t)x;
     uint64_t r = reduce64(mag, p);
     out[m.offset(b, n) + k] = (x < 0) ? neg_mod(r, p.q) : r;
@@ -279,13 +280,23 @@ __global__ void __launch_bounds__(256, 4) k_lincomb(uint32_t L1, uint32_t C, uin
     }
 }
 
-// y = poly*L1 + limb, z = ciphertext
+// y = poly*L1 + limb, z = ciphertext; ciphertext z meets plaintext z / cts_per_pt
 __global__ void k_mulplain(const uint64_t *ct, const uint64_t *pt, uint64_t *out, uint32_t L1, const DevPrime *P,
-                           uint32_t n) {
+                           uint32_t n, uint32_t cts_per_pt) {
     const uint32_t t = blockIdx.y % L1;
     const DevPrime p = P[t];
     const uint64_t i = ((uint64_t)blockIdx.z * 2 * L1 + blockIdx.y) * n + COEF();
-    out[i] = mont_mul(ct[i], pt[(uint64_t)t * n + COEF()], p.q, p.qinv);
+    const uint64_t *pz = pt + (uint64_t)(blockIdx.z / cts_per_pt) * L1 * n;
+    out[i] = mont_mul(ct[i], pz[(uint64_t)t * n + COEF()], p.q, p.qinv);
+}
+
+// c0 of ciphertext z += plaintext z / cts_per_pt (normal NTT form); y = limb
+__global__ void k_add_plain(uint64_t *ct, const uint64_t *pt, uint32_t L1, const DevPrime *P, uint32_t n,
+                            uint32_t cts_per_pt) {
+    const uint32_t t = blockIdx.y;
+    const uint64_t i = ((uint64_t)blockIdx.z * 2 * L1 + t) * n + COEF();
+    const uint64_t *pz = pt + (uint64_t)(blockIdx.z / cts_per_pt) * L1 * n;
+    ct[i] = add_mod(ct[i], pz[(uint64_t)t * n + COEF()], P[t].q);
 }
 
 // ------------------------------------------------------------------ key switching
@@ -509,7 +520,15 @@ void i64_to_limbs(const hear_context *c, const int64_t *v, uint64_t *out, uint32
     uint32_t ny, nz;
     split_yz(n_limbs, ny, nz);
     LAUNCH3(k_i64_to_limbs, grid3(c->n, ny, nz), kBlock, s, 8.0 * n_limbs * c->n, v, out, n_limbs, m,
-            c->dev_primes(), c->n);
+            c->dev_primes(), c->n, 0ull);
+}
+void i64_to_limbs_batch(const hear_context *c, const int64_t *v, uint64_t *out, uint32_t n_polys, uint32_t level,
+                        cudaStream_t s) {
+    uint32_t ny, nz;
+    const uint32_t n_limbs = n_polys * (level + 1);
+    split_yz(n_limbs, ny, nz);
+    LAUNCH3(k_i64_to_limbs, grid3(c->n, ny, nz), kBlock, s, 8.0 * n_limbs * c->n + 8.0 * n_polys * c->n, v, out,
+            n_limbs, map_q(level, c->n_q), c->dev_primes(), c->n, (uint64_t)c->n);
 }
 void sample_small(const hear_context *c, uint64_t seed, uint32_t purpose, uint64_t index, SmallKind kind,
                   int8_t *out, cudaStream_t s) {
@@ -584,7 +603,23 @@ void mulplain(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64
               uint64_t *out, cudaStream_t st) {
     check_yz(2 * (level + 1), n_ct);
     LAUNCH3(k_mulplain, grid3(c->n, 2 * (level + 1), n_ct), kBlock, st, 8.0 * (4.0 * n_ct + 1) * (level + 1) * c->n,
-            ct, pt, out, level + 1, c->dev_primes(), c->n);
+            ct, pt, out, level + 1, c->dev_primes(), c->n, n_ct);
+}
+void mulplain_grouped(const hear_context *c, uint32_t level, uint32_t n_ct, uint32_t cts_per_pt, const uint64_t *ct,
+                      const uint64_t *pt, uint64_t *out, cudaStream_t st) {
+    check_yz(2 * (level + 1), n_ct);
+    HEAR_REQUIRE(cts_per_pt >= 1, HEAR_E_INVAL, "cts_per_pt must be positive");
+    const double n_pt = (n_ct + cts_per_pt - 1) / cts_per_pt;
+    LAUNCH3(k_mulplain, grid3(c->n, 2 * (level + 1), n_ct), kBlock, st,
+            8.0 * (4.0 * n_ct + n_pt) * (level + 1) * c->n, ct, pt, out, level + 1, c->dev_primes(), c->n, cts_per_pt);
+}
+void add_plain(const hear_context *c, uint32_t level, uint32_t n_ct, uint32_t cts_per_pt, uint64_t *ct,
+               const uint64_t *pt, cudaStream_t st) {
+    check_yz(level + 1, n_ct);
+    HEAR_REQUIRE(cts_per_pt >= 1, HEAR_E_INVAL, "cts_per_pt must be positive");
+    const double n_pt = (n_ct + cts_per_pt - 1) / cts_per_pt;
+    LAUNCH3(k_add_plain, grid3(c->n, level + 1, n_ct), kBlock, st, 8.0 * (2.0 * n_ct + n_pt) * (level + 1) * c->n, ct,
+            pt, level + 1, c->dev_primes(), c->n, cts_per_pt);
 }
 
 void modup(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *c1, uint64_t c1_stride,

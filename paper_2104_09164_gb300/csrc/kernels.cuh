@@ -13,6 +13,9 @@ void small_to_limbs(const hear_context *c, const int8_t *e, uint64_t *out, uint3
                     cudaStream_t s);
 void i64_to_limbs(const hear_context *c, const int64_t *v, uint64_t *out, uint32_t n_limbs, LimbMap m,
                   cudaStream_t s);
+// n_polys polynomials at `level`, polynomial g from v + g*N (int64 coefficients)
+void i64_to_limbs_batch(const hear_context *c, const int64_t *v, uint64_t *out, uint32_t n_polys, uint32_t level,
+                        cudaStream_t s);
 
 // ---- ChaCha20 samplers ----
 void sample_small(const hear_context *c, uint64_t seed, uint32_t purpose, uint64_t index, SmallKind kind,
@@ -48,6 +51,12 @@ void lincomb(const hear_context *c, uint32_t level, uint32_t n_ct, uint32_t n1, 
 // out (batch [n_ct][2][level+1][N]) = ct (batch) (.) pt   (pt Montgomery, no accumulation)
 void mulplain(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *ct, const uint64_t *pt,
               uint64_t *out, cudaStream_t st);
+// out[z] = ct[z] (.) pt[z / cts_per_pt]  (plaintexts [.][level+1][N], Montgomery)
+void mulplain_grouped(const hear_context *c, uint32_t level, uint32_t n_ct, uint32_t cts_per_pt, const uint64_t *ct,
+                      const uint64_t *pt, uint64_t *out, cudaStream_t st);
+// c0 of ct[z] += pt[z / cts_per_pt]  (plaintexts in normal NTT form), in place
+void add_plain(const hear_context *c, uint32_t level, uint32_t n_ct, uint32_t cts_per_pt, uint64_t *ct,
+               const uint64_t *pt, cudaStream_t st);
 
 // ---- key switching ----
 // ext [n_ct][dnum][W][N] from c1 (NTT, [n_ct] polys at stride c1_stride words); tmp: n_ct*(l+1)*N words

@@ -17,6 +17,9 @@ LIB_PATH = os.path.join(_HERE, "libhear.so")
 HEAR_LAYER_FC = 1
 HEAR_LAYER_SQUARE = 2
 HEAR_LAYER_FC_SQ_FC = 3
+HEAR_CNN_CONV, HEAR_CNN_QUAD, HEAR_CNN_POOL, HEAR_CNN_GAP, HEAR_CNN_FC = 1, 2, 3, 4, 5
+HEAR_STRATEGY_HYBRID, HEAR_STRATEGY_FULL, HEAR_STRATEGY_BABY, HEAR_STRATEGY_GIANT = 0, 1, 2, 3
+HEAR_CNN_OP_DIAG, HEAR_CNN_OP_PACK, HEAR_CNN_OP_ROTSUM, HEAR_CNN_OP_QUAD, HEAR_CNN_OP_BIAS = 1, 2, 3, 4, 5
 
 _vp = ctypes.c_void_p
 _u64p = ctypes.POINTER(ctypes.c_uint64)
@@ -53,6 +56,23 @@ class hear_server_counters(ctypes.Structure):
                 ("clips_done", ctypes.c_uint64), ("batches", ctypes.c_uint64), ("pending", ctypes.c_uint64),
                 ("max_in_flight_ciphertexts", ctypes.c_uint64), ("bytes_per_ciphertext", ctypes.c_uint64),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double)]
+
+
+class hear_cnn_input(ctypes.Structure):
+    _fields_ = [("conv_dims", ctypes.c_uint32), ("c_in", ctypes.c_uint32), ("h", ctypes.c_uint32),
+                ("w", ctypes.c_uint32), ("pitch", ctypes.c_uint32), ("stride", ctypes.c_uint32)]
+
+
+class hear_cnn_layer(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_uint32), ("c_out", ctypes.c_uint32), ("f_h", ctypes.c_uint32),
+                ("f_w", ctypes.c_uint32), ("w", _dp), ("bias", _dp), ("a", _dp), ("b", _dp), ("c", _dp),
+                ("fast", ctypes.c_uint32), ("strategy", ctypes.c_uint32), ("n1", ctypes.c_uint32)]
+
+
+class hear_cnn_op_info(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_uint32), ("layer", ctypes.c_uint32), ("n_in", ctypes.c_uint32),
+                ("n_out", ctypes.c_uint32), ("level_in", ctypes.c_uint32), ("level_out", ctypes.c_uint32),
+                ("n_babies", ctypes.c_uint32), ("n_giants", ctypes.c_uint32), ("n_keyswitch", ctypes.c_uint32)]
 
 
 class HearError(RuntimeError):
@@ -114,6 +134,16 @@ def _load():
         "hear_server_poll": (st, [_vp, ctypes.c_uint64, _u64p, ctypes.c_size_t, _szp, ctypes.POINTER(ctypes.c_int)]),
         "hear_server_stats": (st, [_vp, ctypes.POINTER(hear_server_counters)]),
         "hear_server_destroy": (None, [_vp]),
+        "hear_cnn_create": (st, [_vp, ctypes.POINTER(hear_cnn_input), ctypes.POINTER(hear_cnn_layer),
+                                 ctypes.c_size_t, ctypes.POINTER(_vp)]),
+        "hear_cnn_destroy": (None, [_vp]),
+        "hear_cnn_rotations": (st, [_vp, _i32p, ctypes.c_size_t, _szp]),
+        "hear_cnn_ops": (st, [_vp, ctypes.POINTER(hear_cnn_op_info), ctypes.c_size_t, _szp]),
+        "hear_cnn_output_slots": (st, [_vp, _u32p, ctypes.c_size_t, _szp]),
+        "hear_cnn_encrypt": (st, [_vp, _vp, _vp, _dp, ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(_vp),
+                                  _vp]),
+        "hear_cnn_evaluate": (st, [_vp, _vp, ctypes.c_size_t, ctypes.c_size_t, ctypes.POINTER(_vp),
+                                   ctypes.c_size_t, ctypes.POINTER(_vp), _vp]),
         "hear_rescale_noalloc": (st, [_vp, _u64p, ctypes.c_uint32, ctypes.c_uint32, _u64p, _vp]),
         "hear_profile_begin": (st, [_vp]),
         "hear_profile_end": (st, [_vp, ctypes.POINTER(hear_profile_entry), ctypes.c_size_t, _szp]),
@@ -375,6 +405,104 @@ def hear_evaluate_host(m, evk, in_words, n_ct, scale, out=None, stream=None):
     _check(lib.hear_evaluate_host(m, evk, _p(w, _u64p), int(n_ct), float(scale), _p(out, _u64p), out.size,
                                   ctypes.byref(n), ctypes.byref(lv), ctypes.byref(sc), _stream(stream)))
     return out, lv.value, sc.value
+
+
+# ---------------------------------------------------------------- skeleton CNN
+_STRATEGIES = {"hybrid": HEAR_STRATEGY_HYBRID, "full": HEAR_STRATEGY_FULL, "baby": HEAR_STRATEGY_BABY,
+               "giant": HEAR_STRATEGY_GIANT}
+
+
+def _strategy(s):
+    """"full" | "baby" | "giant" | ("hybrid", n1) | None (hybrid, default n1) -> (code, n1)"""
+    if s is None:
+        return HEAR_STRATEGY_HYBRID, 0
+    if isinstance(s, str):
+        return _STRATEGIES[s], 0
+    return _STRATEGIES[s[0]], int(s[1])
+
+
+def hear_cnn_create(ctx, spec, strategies=None):
+    """spec: collapsed network dict {"conv_dims", "c_in", "h", "w", ["pitch", "stride"],
+    "layers": [("conv", W[c_out][c_in][fh][fw], fast) | ("quad", a, b, c) | ("pool",) |
+    ("gap",) | ("fc", W, bias)]}; strategies: one per conv / fc layer (see _strategy)"""
+    inp = hear_cnn_input(int(spec["conv_dims"]), int(spec["c_in"]), int(spec["h"]), int(spec["w"]),
+                         int(spec.get("pitch", 0)), int(spec.get("stride", 1)))
+    layers = spec["layers"]
+    descs = (hear_cnn_layer * len(layers))()
+    keep = []
+    si = 0
+    for i, layer in enumerate(layers):
+        d = descs[i]
+        kind = layer[0]
+        if kind == "conv":
+            W = _arr(layer[1], np.float64)
+            keep.append(W)
+            d.kind, d.c_out, d.f_h, d.f_w, d.w = HEAR_CNN_CONV, W.shape[0], W.shape[2], W.shape[3], _p(W, _dp)
+            d.fast = 1 if layer[2] else 0
+            d.strategy, d.n1 = _strategy(None if strategies is None else strategies[si])
+            si += 1
+        elif kind == "quad":
+            a, b, c = (_arr(v, np.float64) for v in layer[1:4])
+            keep += [a, b, c]
+            d.kind, d.a, d.b, d.c = HEAR_CNN_QUAD, _p(a, _dp), _p(b, _dp), _p(c, _dp)
+        elif kind == "pool":
+            d.kind = HEAR_CNN_POOL
+        elif kind == "gap":
+            d.kind = HEAR_CNN_GAP
+        elif kind == "fc":
+            W = _arr(layer[1], np.float64)
+            keep.append(W)
+            d.kind, d.c_out, d.w = HEAR_CNN_FC, W.shape[0], _p(W, _dp)
+            if len(layer) > 2 and layer[2] is not None:
+                bias = _arr(layer[2], np.float64)
+                keep.append(bias)
+                d.bias = _p(bias, _dp)
+            d.strategy, d.n1 = _strategy(None if strategies is None else strategies[si])
+            si += 1
+        else:
+            raise ValueError(kind)
+    h = _vp()
+    _check(lib.hear_cnn_create(ctx, ctypes.byref(inp), descs, len(layers), ctypes.byref(h)))
+    return h.value
+
+
+def hear_cnn_destroy(m):
+    lib.hear_cnn_destroy(m)
+
+
+def hear_cnn_rotations(m):
+    return [int(x) for x in _vec_out(lib.hear_cnn_rotations, m, np.int32, _i32p)]
+
+
+def hear_cnn_ops(m):
+    n = ctypes.c_size_t(0)
+    lib.hear_cnn_ops(m, None, 0, ctypes.byref(n))
+    arr = (hear_cnn_op_info * n.value)()
+    _check(lib.hear_cnn_ops(m, arr, n.value, ctypes.byref(n)))
+    return [{f: getattr(a, f) for f, _ in hear_cnn_op_info._fields_} for a in arr]
+
+
+def hear_cnn_output_slots(m):
+    return [int(x) for x in _vec_out(lib.hear_cnn_output_slots, m, np.uint32, _u32p)]
+
+
+def hear_cnn_encrypt(ctx, pk, m, x, seed, ct_id, stream=None):
+    """x: float64[c_in][h][w] -> the input ciphertexts of one sample"""
+    xx = _arr(x, np.float64).reshape(-1)
+    n_in = hear_cnn_ops(m)[0]["n_in"]
+    outs = (_vp * n_in)()
+    _check(lib.hear_cnn_encrypt(ctx, pk, m, _p(xx, _dp), int(seed), int(ct_id), outs, _stream(stream)))
+    return [o for o in outs]
+
+
+def hear_cnn_evaluate(m, evk, op0, op1, cts, n_samples, stream=None):
+    """cts: n_samples * n_in handles (sample-major) -> n_samples * n_out handles"""
+    ops = hear_cnn_ops(m)
+    n_out = ops[op1 - 1]["n_out"]
+    ins = (_vp * len(cts))(*cts)
+    outs = (_vp * (n_out * n_samples))()
+    _check(lib.hear_cnn_evaluate(m, evk, int(op0), int(op1), ins, int(n_samples), outs, _stream(stream)))
+    return [o for o in outs]
 
 
 # ---------------------------------------------------------------- serving
