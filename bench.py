@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--clips", type=int, default=None, help="clips in the batch (default: the workload's)")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--rates", default="500,2000,8000", help="request rates (req/s) of the served sweep")
+    ap.add_argument("--no-cnn", action="store_true", help="skip the CNN sections (Table 1 layers, 1D-CNN-64)")
+    ap.add_argument("--conv-rows", default="all", help="Table 1 rows to time: all | comma-separated indices")
     return ap.parse_args()
 
 
@@ -388,6 +390,117 @@ def run_served(H, S, rates, seconds=2.0, max_batch=32, n_slots=2, seed=601):
     return out
 
 
+# ------------------------------------------------------------------ skeleton CNN sections
+# The paper's homomorphic convolution microbenchmark (Table 1; Xeon Platinum 8268, 16
+# threads, SEAL 3.4, mean of 608 test samples): ordinary convolution ms, fast convolution
+# pre / conv / post / total ms, speedup.  Context only: a different machine and library.
+PAPER_TABLE1_MS = [
+    (409, 65, 283, 42, 390, 1.1), (422, 49, 156, 37, 242, 1.7),
+    (794, 68, 560, 47, 674, 1.2), (1416, 47, 408, 59, 514, 2.8),
+    (985, 70, 550, 74, 694, 1.4), (1145, 47, 288, 50, 385, 3.0),
+    (2173, 75, 856, 79, 1010, 2.2), (4251, 49, 507, 104, 660, 6.4),
+]
+
+
+def _time_range(H, m, evk, op0, op1, cts, n_samples, torch, stream, iters):
+    """device time of operations [op0, op1) on resident inputs (CUDA events on `stream`)"""
+    for o in H.hear_cnn_evaluate(m, evk, op0, op1, cts, n_samples, stream):
+        H.hear_ciphertext_destroy(o)
+    times = []
+    for _ in range(iters):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        outs = H.hear_cnn_evaluate(m, evk, op0, op1, cts, n_samples, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        for o in outs:
+            H.hear_ciphertext_destroy(o)
+    times.sort()
+    return times[len(times) // 2]
+
+
+def run_conv_table(H, torch, stream, device, rows, iters=5):
+    from paper_2104_09164_gb300.workloads import CONV_BENCH_PARAMS, TABLE1_LAYERS, conv_bench_layer
+    log_n, qb, pb = CONV_BENCH_PARAMS
+    ctx = H.hear_context_create(log_n, qb, pb, 40.0, 3.2, device)
+    out = []
+    for idx in rows:
+        row = {"network": TABLE1_LAYERS[idx][0], "layer": TABLE1_LAYERS[idx][1]}
+        for fast in (False, True):
+            spec, xs = conv_bench_layer(idx, fast)
+            t0 = time.perf_counter()
+            m = H.hear_cnn_create(ctx, spec)
+            build_s = time.perf_counter() - t0
+            ops = H.hear_cnn_ops(m)
+            sk, pk, evk = H.hear_keygen(ctx, 301, H.hear_cnn_rotations(m))
+            cts = [H.hear_encrypt(ctx, pk, xs[0][i], 2.0 ** 40, 401, i, stream) for i in range(xs.shape[1])]
+            if not fast:
+                ms = _time_range(H, m, evk, 0, 1, cts, 1, torch, stream, iters)
+                row.update({"n_in": ops[0]["n_in"], "n_out": ops[0]["n_out"], "ordinary_ms": ms,
+                            "ordinary_keyswitch": ops[0]["n_keyswitch"], "ordinary_build_s": build_s})
+            else:
+                # chain the stages once to get each stage's resident input
+                packed = H.hear_cnn_evaluate(m, evk, 0, 1, cts, 1, stream)
+                conv = H.hear_cnn_evaluate(m, evk, 1, 2, packed, 1, stream)
+                pre = _time_range(H, m, evk, 0, 1, cts, 1, torch, stream, iters)
+                mid = _time_range(H, m, evk, 1, 2, packed, 1, torch, stream, iters)
+                post = _time_range(H, m, evk, 2, 3, conv, 1, torch, stream, iters)
+                whole = _time_range(H, m, evk, 0, 3, cts, 1, torch, stream, iters)
+                row.update({"n_P": ops[0]["n_in"] // ops[0]["n_out"], "pre_ms": pre, "conv_ms": mid,
+                            "post_ms": post, "fast_total_ms": whole, "fast_build_s": build_s,
+                            "fast_keyswitch": sum(o["n_keyswitch"] for o in ops)})
+                for h in packed + conv:
+                    H.hear_ciphertext_destroy(h)
+            for h in cts:
+                H.hear_ciphertext_destroy(h)
+            H.hear_eval_keys_destroy(evk)
+            H.hear_public_key_destroy(pk)
+            H.hear_secret_key_destroy(sk)
+            H.hear_cnn_destroy(m)
+        row["speedup"] = row["ordinary_ms"] / row["fast_total_ms"]
+        p = PAPER_TABLE1_MS[idx]
+        row["paper_cpu_ms"] = {"ordinary": p[0], "pre": p[1], "conv": p[2], "post": p[3], "total": p[4],
+                               "speedup": p[5]}
+        out.append(row)
+    H.hear_context_destroy(ctx)
+    return out
+
+
+def run_cnn(H, torch, stream, device, batches=(1, 16), iters=5):
+    """the paper-shaped 1D-CNN-64 (2 x 32 x 15 inputs, N = 2^15): whole encrypted network"""
+    from paper_2104_09164_gb300.collapse import collapse_cnn
+    from paper_2104_09164_gb300.workloads import make_cnn
+    net = make_cnn("cnn1d64", n_samples=max(batches))
+    spec = collapse_cnn(net)
+    ctx = H.hear_context_create(net.log_n, net.q_bits, net.p_bits, net.log2_scale, net.sigma, device)
+    m = H.hear_cnn_create(ctx, spec)
+    ops = H.hear_cnn_ops(m)
+    sk, pk, evk = H.hear_keygen(ctx, 301, H.hear_cnn_rotations(m))
+    cts = [H.hear_cnn_encrypt(ctx, pk, m, clip, 401, s, stream)[0] for s, clip in enumerate(net.clips)]
+    res = {"workload": "1D-CNN-64 (conv 2->64->128->256, 3 taps, quadratic activations, average / global "
+                       "pooling, FC 256->2; fast convolution in conv2 / conv3), 2x32x15 synthetic skeleton "
+                       "clips, RNS-CKKS N=2^15, q=60+14x40 bits, p=60+60 bits",
+           "ops": len(ops), "keyswitch_per_sample": sum(o["n_keyswitch"] for o in ops), "batches": []}
+    for b in batches:
+        H.hear_profile_begin(ctx)
+        for o in H.hear_cnn_evaluate(m, evk, 0, len(ops), cts[:b], b, stream):
+            H.hear_ciphertext_destroy(o)
+        torch.cuda.synchronize()
+        st = H.hear_profile_end(ctx)
+        ms = _time_range(H, m, evk, 0, len(ops), cts[:b], b, torch, stream, iters)
+        res["batches"].append({"samples": b, "ms": ms, "inferences_s": b / (ms / 1e3),
+                               "stages_ms": {k: v[1] for k, v in sorted(st.items(), key=lambda kv: -kv[1][1])[:6]}})
+    for h in cts:
+        H.hear_ciphertext_destroy(h)
+    H.hear_eval_keys_destroy(evk)
+    H.hear_public_key_destroy(pk)
+    H.hear_secret_key_destroy(sk)
+    H.hear_cnn_destroy(m)
+    H.hear_context_destroy(ctx)
+    return res
+
+
 def main_gpu(a):
     import torch
     dist = Dist()
@@ -452,6 +565,14 @@ def main_gpu(a):
         SL.close()
     else:
         S.close()
+    if result is not None and not a.no_cnn and dist.world == 1:
+        rows = list(range(8)) if a.conv_rows == "all" else [int(x) for x in a.conv_rows.split(",")]
+        result["conv_table1"] = {
+            "note": "Table 1 layers at N=2^14 (q=60+7x40, p=60), inputs at the top level, one sample, "
+                    "synthetic weights, median device ms of 5 runs; paper_cpu_ms = the paper's Xeon/SEAL "
+                    "numbers (context, other hardware)",
+            "rows": run_conv_table(H, torch, stream, device, rows)}
+        result["cnn"] = run_cnn(H, torch, stream, device)
     if result is not None and not a.no_cpu_baseline and dist.world == 1:
         v, cores, desc = oracle_sample(w, H_steps_for(w))
         result["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
