@@ -361,6 +361,29 @@ hear_status hear_profile_end(hear_context *ctx, hear_profile_entry *out, size_t 
 /* kernel launches issued by the library (all contexts) since it was loaded */
 uint64_t hear_launch_count(void);
 
+/* ---- NTT launch variants and their tuner ----
+ * The forward / inverse NTT has three launch forms with bit-identical results:
+ * HEAR_NTT_WIDE (two passes, 4096-word shared-memory tiles, 256 threads), HEAR_NTT_NARROW
+ * (two passes, 1024-word tiles, 64 threads: more CTAs for launches of few limbs) and
+ * HEAR_NTT_FUSED (one launch; a cluster of 8 CTAs per limb exchanges the intermediate
+ * through distributed shared memory, so each residue crosses HBM once).  hear_ntt_tune
+ * times all three for launches of 1, 2, 4, .. max_limbs limbs in both directions on the
+ * context's stream (each timing a replayed CUDA graph of back-to-back transforms) and keeps
+ * the fastest per power-of-two bucket, the one-launch form only if it is 15% faster (its
+ * larger code competes for the instruction cache inside whole evaluations; larger launches use the
+ * largest tuned bucket's choice).  hear_context_create runs it once (max_limbs 1024, a few
+ * tens of milliseconds) unless the environment sets HEAR_NTT_TUNE=0, which keeps a fixed
+ * rule (narrow below two wide CTAs per SM, wide above).  It must
+ * not run concurrently with other work on the context.  ms_out (optional) receives
+ * float[2][16][3] = [forward, inverse][bucket][variant] milliseconds per launch, choice_out
+ * (optional) uint8_t[2][16].  hear_ntt_set_variant forces one variant (-1 = back to the
+ * table); it exists for tests and measurements. */
+#define HEAR_NTT_WIDE 0
+#define HEAR_NTT_NARROW 1
+#define HEAR_NTT_FUSED 2
+hear_status hear_ntt_tune(hear_context *ctx, uint32_t max_limbs, int iters, uint8_t *choice_out, float *ms_out);
+hear_status hear_ntt_set_variant(hear_context *ctx, int variant);
+
 /* ---- debug: ring products through the NTT kernels (tests only) ---- */
 /* out = a * b in Z_q[X]/(X^N+1) for limb prime index `prime` (0..n_q+n_p-1), coefficient domain */
 hear_status hear_dbg_poly_mul(hear_context *ctx, uint32_t prime, const uint64_t *a, const uint64_t *b,

@@ -95,7 +95,13 @@ const char *hear_last_error(void) { return g_last_error.c_str(); }
 hear_status hear_context_create(const hear_params_desc *params, int cuda_device, hear_context **out) {
     if (!out || !params) return fail(HEAR_E_INVAL, "null argument");
     auto c = new hear_context();
-    hear_status s = guard(nullptr, [&] { build_context(c, params, cuda_device); });
+    hear_status s = guard(nullptr, [&] {
+        build_context(c, params, cuda_device);
+        // pick the NTT launch variant per launch size by timing them (HEAR_NTT_TUNE=0 keeps
+        // the fixed rule); every variant computes the same residues
+        const char *v = std::getenv("HEAR_NTT_TUNE");
+        if (!(v && *v == '0')) ntt_tune(c, 1024, 8, nullptr);
+    });
     if (s != HEAR_OK) {
         delete c;
         return s;
@@ -593,6 +599,20 @@ hear_status hear_dbg_ntt_roundtrip(hear_context *ctx, uint64_t *limbs, size_t n_
         HEAR_CHECK_CUDA(cudaMemcpyAsync(limbs, d.p, words * 8, cudaMemcpyDeviceToHost, st));
         HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
     });
+}
+
+hear_status hear_ntt_tune(hear_context *ctx, uint32_t max_limbs, int iters, uint8_t *choice_out, float *ms_out) {
+    if (!ctx || max_limbs == 0 || max_limbs > (1u << 15) || iters < 1) return fail(HEAR_E_INVAL, "bad argument");
+    return guard(ctx, [&] {
+        ntt_tune(ctx, max_limbs, iters, ms_out);
+        if (choice_out) std::memcpy(choice_out, ctx->ntt_choice, sizeof(ctx->ntt_choice));
+    });
+}
+
+hear_status hear_ntt_set_variant(hear_context *ctx, int variant) {
+    if (!ctx || variant < -1 || variant > 2) return fail(HEAR_E_INVAL, "bad argument");
+    ctx->ntt_force = variant;
+    return HEAR_OK;
 }
 
 hear_status hear_dbg_ntt_time(hear_context *ctx, size_t n_limb, int iters, float *ms_fwd, float *ms_inv) {

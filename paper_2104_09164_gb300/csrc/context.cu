@@ -144,6 +144,7 @@ void build_context(hear_context *c, const hear_params_desc *d, int device) {
                  "need 1 <= n_q, 1 <= n_p, n_q + n_p <= 48");
     HEAR_REQUIRE(d->sigma > 0 && d->sigma < 10, HEAR_E_INVAL, "sigma out of range");
     c->device = device;
+    std::memset(c->ntt_choice, kNttAuto, sizeof(c->ntt_choice));
     c->log_n = d->log_n;
     c->n = 1u << d->log_n;
     c->n_q = d->n_q;

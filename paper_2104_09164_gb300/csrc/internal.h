@@ -102,8 +102,20 @@ extern std::atomic<uint64_t> g_launches;
 }  // namespace hear
 
 // ------------------------------------------------------------------ handles
+// NTT launch variants (ntt.cu): two-pass wide tiles, two-pass narrow tiles, one-launch
+// cluster form; kNttAuto = the default rule
+enum : uint8_t { kNttWide = 0, kNttNarrow = 1, kNttFused = 2, kNttAuto = 255 };
+constexpr int kNttBuckets = 16;   // launches of 1, 2-3, 4-7, .. limbs (log2 buckets)
+inline uint32_t ntt_bucket(uint32_t n_limbs) {
+    uint32_t b = 0;
+    while ((2u << b) <= n_limbs && b + 1 < (uint32_t)kNttBuckets) b++;
+    return b;
+}
+
 struct hear_context {
     int device = 0;
+    int ntt_force = -1;                       // debug: force one NTT variant (-1 = table)
+    uint8_t ntt_choice[2][kNttBuckets];       // [forward, inverse][limb bucket] -> variant
     uint32_t log_n = 0, n = 0, n_q = 0, n_p = 0, L = 0, K = 0, alpha = 0;
     double default_scale = 0, sigma = 0;
     std::vector<uint64_t> primes;          // n_q + n_p
@@ -197,6 +209,8 @@ inline LimbMap map_qp(uint32_t level, uint32_t n_q, uint32_t K) {
 
 void ntt_forward(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, LimbMap map, cudaStream_t s);
 void ntt_inverse(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, LimbMap map, cudaStream_t s);
+// fill ctx->ntt_choice by timing the launch variants (ms_out: [2][kNttBuckets][3] or null)
+void ntt_tune(hear_context *ctx, uint32_t max_limbs, int iters, float *ms_out);
 
 // RAII bracket of one or more kernel launches for the profiler
 struct ProfScope {

@@ -14,8 +14,12 @@
 // at a time to 8 or 16 words (radix-2^3 / 2^4 units), with Harvey lazy butterflies
 // (values kept in [0, 4q) forward and [0, 2q) inverse) and Shoup products by the
 // precomputed twiddle companions.
+#include <cooperative_groups.h>
+#include <mutex>
 #include "internal.h"
 #include "modarith.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace hear {
 namespace {
@@ -61,7 +65,7 @@ template <int LOGR, bool NARROW> struct Tile {
 // corrections.  Forward values then grow by at most 2q per stage; inverse sums double per
 // stage, so the subtraction adds 2^done * q, done = inverse stages applied before this one
 // (DONE0 before this pass).
-template <int LOGR, int W, int LS0, bool FWD, bool PASSA, int TILE, bool RED, int DONE0>
+template <int LOGR, int W, int LS0, bool FWD, bool PASSA, int TILE, bool RED, int DONE0, bool TWS>
 __device__ __forceinline__ void stage_group(uint64_t *s, uint32_t s_off, uint32_t blk_base,
                                             const uint64_t *__restrict__ tw,
                                             const uint64_t *__restrict__ tws, uint64_t q) {
@@ -99,8 +103,8 @@ __device__ __forceinline__ void stage_group(uint64_t *s, uint32_t s_off, uint32_
                 const int pe = FWD ? (((p - 1) / half) * 2 * half + ((p - 1) % half)) : 0;
                 const int pm = p == 0 ? -1 : (FWD ? (pe >> (W - i)) : ((p - 1) >> i));
                 if (m != pm) {
-                    w = __ldg(tw + base + m);
-                    wsh = __ldg(tws + base + m);
+                    w = TWS ? tw[base + m] : __ldg(tw + base + m);
+                    wsh = TWS ? tws[base + m] : __ldg(tws + base + m);
                 }
                 uint64_t X = x[e], Y = x[e + half];
                 if (FWD) {
@@ -127,14 +131,62 @@ __device__ __forceinline__ void stage_group(uint64_t *s, uint32_t s_off, uint32_
     }
 }
 
+// PASSA: the pass-A twiddles (indices below 2^LOGR) sit in shared memory; pass B reads its
+// (per-block) twiddles through the read-only cache.
 template <int LOGR, bool FWD, bool PASSA, int TILE, bool RED, int DONE0>
 __device__ __forceinline__ void all_groups(uint64_t *s, uint32_t s_off, uint32_t blk_base,
                                            const uint64_t *tw, const uint64_t *tws, uint64_t q) {
     constexpr int W0 = Split<LOGR>::W0, W1 = Split<LOGR>::W1;
-    stage_group<LOGR, W0, FWD ? 0 : LOGR - 1, FWD, PASSA, TILE, RED, DONE0>(s, s_off, blk_base, tw, tws, q);
+    stage_group<LOGR, W0, FWD ? 0 : LOGR - 1, FWD, PASSA, TILE, RED, DONE0, PASSA>(s, s_off, blk_base, tw, tws, q);
     __syncthreads();
-    stage_group<LOGR, W1, FWD ? W0 : LOGR - 1 - W0, FWD, PASSA, TILE, RED, DONE0>(s, s_off, blk_base, tw, tws, q);
+    stage_group<LOGR, W1, FWD ? W0 : LOGR - 1 - W0, FWD, PASSA, TILE, RED, DONE0, PASSA>(s, s_off, blk_base, tw, tws,
+                                                                                         q);
     __syncthreads();
+}
+
+// Tile transfers in two phases -- all of a thread's global (or remote shared) loads issued
+// before its first shared store -- so each thread has TILE / THREADS requests in flight.
+// (in batches of 8 words, which keeps the register footprint of the wide tiles in budget)
+template <int TILE, int THREADS, class Src>
+__device__ __forceinline__ void gather_tile(uint64_t *s, Src src) {
+    constexpr int PER = TILE / THREADS;
+    constexpr int B = PER < 8 ? PER : 8;
+    static_assert(PER * THREADS == TILE && PER % B == 0, "tile must split evenly");
+#pragma unroll
+    for (int k0 = 0; k0 < PER; k0 += B) {
+        uint64_t v[B];
+#pragma unroll
+        for (int k = 0; k < B; k++) v[k] = src(threadIdx.x + (k0 + k) * THREADS);
+#pragma unroll
+        for (int k = 0; k < B; k++) s[swz(threadIdx.x + (k0 + k) * THREADS)] = v[k];
+    }
+}
+template <int TILE, int THREADS>
+__device__ __forceinline__ void load_rows(uint64_t *s, const uint64_t *g) {
+    constexpr int PER = TILE / 2 / THREADS;
+    constexpr int B = PER < 4 ? PER : 4;
+    static_assert(PER * THREADS * 2 == TILE && PER % B == 0, "tile must split evenly");
+#pragma unroll
+    for (int k0 = 0; k0 < PER; k0 += B) {
+        ulonglong2 v[B];
+#pragma unroll
+        for (int k = 0; k < B; k++) v[k] = reinterpret_cast<const ulonglong2 *>(g)[threadIdx.x + (k0 + k) * THREADS];
+#pragma unroll
+        for (int k = 0; k < B; k++) {
+            const int i = threadIdx.x + (k0 + k) * THREADS;
+            s[swz(2 * i)] = v[k].x;
+            s[swz(2 * i + 1)] = v[k].y;
+        }
+    }
+}
+// the 2^LOGR pass-A twiddles (and companions) of a prime into shared memory
+template <int LOGR, int THREADS>
+__device__ __forceinline__ void load_twiddles(uint64_t *stw, const uint64_t *tw, const uint64_t *tws) {
+    constexpr int R = 1 << LOGR;
+    for (int i = threadIdx.x; i < R; i += THREADS) {
+        stw[i] = __ldg(tw + i);
+        stw[R + i] = __ldg(tws + i);
+    }
 }
 
 // Pass A: strided columns, stages 0..LOGR-1 (forward) or LOGR-1..0 (inverse, + N^-1).
@@ -151,17 +203,18 @@ __global__ void __launch_bounds__(Tile<LOGR, NARROW>::THREADS, NARROW ? 8 : 3) n
     if (limb >= a.n_limbs || !a.map.resolve(limb, &pi)) return;
     const DevPrime P = a.primes[pi];
     uint64_t *g = a.data + a.map.offset(limb, a.n);
+    constexpr int THREADS = Tile<LOGR, NARROW>::THREADS;
+    __shared__ uint64_t stw[2 * R];
     const uint32_t cols = a.n >> LOGR;
     const uint32_t c0 = tile * C;
-    for (int i = threadIdx.x; i < TILE; i += blockDim.x) {
-        const int u = i / C, c = i % C;
-        s[swz(i)] = g[c0 + c + (size_t)u * cols];
-    }
+    load_twiddles<LOGR, THREADS>(stw, a.tw + (size_t)pi * a.n, a.tw_sh + (size_t)pi * a.n);
+    gather_tile<TILE, THREADS>(s, [&](int i) { return g[c0 + i % C + (size_t)(i / C) * cols]; });
     __syncthreads();
-    const uint64_t *tw = a.tw + (size_t)pi * a.n, *tws = a.tw_sh + (size_t)pi * a.n;
-    if (P.q < a.small_below) all_groups<LOGR, FWD, true, TILE, false, DONE0>(s, 0, 0, tw, tws, P.q);
-    else all_groups<LOGR, FWD, true, TILE, true, DONE0>(s, 0, 0, tw, tws, P.q);
-    for (int i = threadIdx.x; i < TILE; i += blockDim.x) {
+    if (P.q < a.small_below) all_groups<LOGR, FWD, true, TILE, false, DONE0>(s, 0, 0, stw, stw + R, P.q);
+    else all_groups<LOGR, FWD, true, TILE, true, DONE0>(s, 0, 0, stw, stw + R, P.q);
+#pragma unroll
+    for (int k = 0; k < TILE / THREADS; k++) {
+        const int i = threadIdx.x + k * THREADS;
         const int u = i / C, c = i % C;
         uint64_t v = s[swz(i)];
         if (!FWD) {
@@ -186,18 +239,17 @@ __global__ void __launch_bounds__(Tile<LOGR, NARROW>::THREADS, NARROW ? 8 : 3) n
     if (limb >= a.n_limbs || !a.map.resolve(limb, &pi)) return;
     const DevPrime P = a.primes[pi];
     uint64_t *g = a.data + a.map.offset(limb, a.n) + (size_t)tile * TILE;
-    for (int i = threadIdx.x; i < TILE / 2; i += blockDim.x) {
-        const ulonglong2 v = reinterpret_cast<const ulonglong2 *>(g)[i];
-        s[swz(2 * i)] = v.x;
-        s[swz(2 * i + 1)] = v.y;
-    }
+    constexpr int THREADS = Tile<LOGR, NARROW>::THREADS;
+    load_rows<TILE, THREADS>(s, g);
     __syncthreads();
     const uint64_t *tw = a.tw + (size_t)pi * a.n, *tws = a.tw_sh + (size_t)pi * a.n;
     const bool small = P.q < a.small_below;
     if (small) all_groups<LOGR, FWD, false, TILE, false, 0>(s, s_off, tile * S, tw, tws, P.q);
     else all_groups<LOGR, FWD, false, TILE, true, 0>(s, s_off, tile * S, tw, tws, P.q);
     const uint64_t q = P.q, two_q = 2 * q;
-    for (int i = threadIdx.x; i < TILE / 2; i += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < TILE / 2 / THREADS; k++) {
+        const int i = threadIdx.x + k * THREADS;
         ulonglong2 v;
         v.x = s[swz(2 * i)];
         v.y = s[swz(2 * i + 1)];
@@ -214,6 +266,113 @@ __global__ void __launch_bounds__(Tile<LOGR, NARROW>::THREADS, NARROW ? 8 : 3) n
     }
 }
 
+// ------------------------------------------------------------------ one-launch variant
+// The two passes fused in one kernel: a cluster of CL CTAs owns one limb.  Forward: CTA r
+// runs pass A on columns [r*CA, (r+1)*CA) of the 2^LA x 2^LB matrix, the cluster
+// synchronises, CTA r gathers rows [r*SB, (r+1)*SB) from the pass-A tiles of all CTAs of
+// the cluster (distributed shared memory), synchronises again (no CTA leaves while its tile
+// is read), runs pass B and writes its rows.  Inverse: the same in reverse order.  Each
+// residue is read from and written to HBM once; the intermediate never leaves the SMs.
+template <int LA, int LB, int CL> struct Fused {
+    static constexpr int N = 1 << (LA + LB);
+    static constexpr int TILE = N / CL;                // words per CTA
+    static constexpr int RA = 1 << LA, CA = TILE / RA;  // pass A: RA rows x CA columns
+    static constexpr int RB = 1 << LB, SB = TILE / RB;  // pass B: SB rows of RB words
+    static constexpr int THREADS = TILE / 16 < 32 ? 32 : (TILE / 16 > 256 ? 256 : TILE / 16);
+    static constexpr size_t SMEM = (2 * TILE + 2 * RA) * sizeof(uint64_t);
+    static_assert(CA >= 1 && SB >= 1, "cluster too large for this ring size");
+};
+
+template <int LA, int LB, bool FWD, int CL>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(Fused<LA, LB, CL>::THREADS, 512 / Fused<LA, LB, CL>::THREADS)
+ntt_fused(PassArgs a) {
+    using F = Fused<LA, LB, CL>;
+    constexpr int TILE = F::TILE, CA = F::CA, RA = F::RA, RB = F::RB, SB = F::SB, THREADS = F::THREADS;
+    extern __shared__ uint64_t smem[];
+    uint64_t *sA = smem, *sB = smem + TILE, *stw = smem + 2 * TILE;
+    cg::cluster_group cluster = cg::this_cluster();
+    const uint32_t r = cluster.block_rank();
+    const uint32_t limb = blockIdx.x / CL;
+    uint32_t pi;
+    // every CTA of a cluster has the same limb, so the whole cluster leaves together
+    if (limb >= a.n_limbs || !a.map.resolve(limb, &pi)) return;
+    const DevPrime P = a.primes[pi];
+    const uint64_t q = P.q, two_q = 2 * q;
+    const bool small = q < a.small_below;
+    uint64_t *g = a.data + a.map.offset(limb, a.n);
+    const uint64_t *tw = a.tw + (size_t)pi * a.n, *tws = a.tw_sh + (size_t)pi * a.n;
+    load_twiddles<LA, THREADS>(stw, tw, tws);
+    if (FWD) {
+        gather_tile<TILE, THREADS>(sA, [&](int i) { return g[r * CA + i % CA + (size_t)(i / CA) * RB]; });
+        __syncthreads();
+        if (small) all_groups<LA, true, true, TILE, false, 0>(sA, 0, 0, stw, stw + RA, q);
+        else all_groups<LA, true, true, TILE, true, 0>(sA, 0, 0, stw, stw + RA, q);
+        cluster.sync();
+        gather_tile<TILE, THREADS>(sB, [&](int i) {
+            const int sp = i / RB, x = i % RB;
+            const uint64_t *rem = cluster.map_shared_rank(sA, (unsigned)(x / CA));
+            return rem[swz((r * SB + sp) * CA + x % CA)];
+        });
+        cluster.sync();
+        if (small) all_groups<LB, true, false, TILE, false, 0>(sB, LA, r * SB, tw, tws, q);
+        else all_groups<LB, true, false, TILE, true, 0>(sB, LA, r * SB, tw, tws, q);
+        uint64_t *out = g + (size_t)r * TILE;
+#pragma unroll
+        for (int k = 0; k < TILE / 2 / THREADS; k++) {
+            const int i = threadIdx.x + k * THREADS;
+            ulonglong2 v;
+            v.x = sB[swz(2 * i)];
+            v.y = sB[swz(2 * i + 1)];
+            if (small) {
+                v.x = shoup(v.x, 1, P.one_sh, q);
+                v.y = shoup(v.y, 1, P.one_sh, q);
+            } else {
+                v.x = v.x >= two_q ? v.x - two_q : v.x;
+                v.x = v.x >= q ? v.x - q : v.x;
+                v.y = v.y >= two_q ? v.y - two_q : v.y;
+                v.y = v.y >= q ? v.y - q : v.y;
+            }
+            reinterpret_cast<ulonglong2 *>(out)[i] = v;
+        }
+    } else {
+        load_rows<TILE, THREADS>(sB, g + (size_t)r * TILE);
+        __syncthreads();
+        if (small) all_groups<LB, false, false, TILE, false, 0>(sB, LA, r * SB, tw, tws, q);
+        else all_groups<LB, false, false, TILE, true, 0>(sB, LA, r * SB, tw, tws, q);
+        cluster.sync();
+        gather_tile<TILE, THREADS>(sA, [&](int i) {
+            const int u = i / CA, c = i % CA;
+            const uint64_t *rem = cluster.map_shared_rank(sB, (unsigned)(u / SB));
+            return rem[swz((u % SB) * RB + r * CA + c)];
+        });
+        cluster.sync();
+        if (small) all_groups<LA, false, true, TILE, false, LB>(sA, 0, 0, stw, stw + RA, q);
+        else all_groups<LA, false, true, TILE, true, LB>(sA, 0, 0, stw, stw + RA, q);
+#pragma unroll
+        for (int k = 0; k < TILE / THREADS; k++) {
+            const int i = threadIdx.x + k * THREADS;
+            const int u = i / CA, c = i % CA;
+            uint64_t v = shoup_lazy(sA[swz(i)], P.n_inv, P.n_inv_sh, q);
+            g[r * CA + c + (size_t)u * RB] = v >= q ? v - q : v;
+        }
+    }
+}
+
+constexpr int kCluster = 8;
+
+template <int LA, int LB, bool FWD>
+void launch_fused(const PassArgs &a, cudaStream_t st) {
+    using F = Fused<LA, LB, kCluster>;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] {
+        attr_err = cudaFuncSetAttribute(ntt_fused<LA, LB, FWD, kCluster>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)F::SMEM);
+    });
+    HEAR_CHECK_CUDA(attr_err);
+    ntt_fused<LA, LB, FWD, kCluster><<<a.n_limbs * kCluster, F::THREADS, F::SMEM, st>>>(a);
+}
+
 // a launch whose wide tiles would not give every SM two CTAs runs the narrow variant
 constexpr uint32_t kNarrowBelow = 2 * 152;
 
@@ -227,15 +386,35 @@ void launch_inv_t(const PassArgs &a, cudaStream_t st) {
     ntt_pass_b<B, false, NARROW><<<a.n_limbs * (a.n / Tile<B, NARROW>::WORDS), Tile<B, NARROW>::THREADS, 0, st>>>(a, A);
     ntt_pass_a<A, false, NARROW, B><<<a.n_limbs * (a.n / Tile<A, NARROW>::WORDS), Tile<A, NARROW>::THREADS, 0, st>>>(a);
 }
-template <int A, int B>
-void launch_fwd(const PassArgs &a, cudaStream_t st) {
-    if (a.n_limbs * (a.n / Split<A>::TILE) < kNarrowBelow) launch_fwd_t<A, B, true>(a, st);
-    else launch_fwd_t<A, B, false>(a, st);
+// variant of a launch of n_limbs limbs: the context's table (filled by the tuner) or the
+// default rule (narrow two-pass below two wide CTAs per SM, wide two-pass above)
+uint32_t pick(const hear_context *ctx, bool fwd, uint32_t n_limbs, uint32_t wide_ctas) {
+    if (ctx->ntt_force >= 0) return (uint32_t)ctx->ntt_force;
+    const uint32_t b = ntt_bucket(n_limbs);
+    const uint8_t v = ctx->ntt_choice[fwd ? 0 : 1][b];
+    if (v != kNttAuto) return v;
+    return wide_ctas < kNarrowBelow ? kNttNarrow : kNttWide;
+}
+// pass-A tile of the wide variant for a ring size (the A of the splits below)
+constexpr uint32_t wide_tile_a(uint32_t log_n) { return log_n <= 12 ? Split<6>::TILE : log_n <= 14 ? Split<7>::TILE : Split<8>::TILE; }
+uint32_t launches_of(const hear_context *ctx, bool fwd, uint32_t n_limbs) {
+    return pick(ctx, fwd, n_limbs, n_limbs * (ctx->n / wide_tile_a(ctx->log_n))) == kNttFused ? 1 : 2;
 }
 template <int A, int B>
-void launch_inv(const PassArgs &a, cudaStream_t st) {
-    if (a.n_limbs * (a.n / Split<A>::TILE) < kNarrowBelow) launch_inv_t<A, B, true>(a, st);
-    else launch_inv_t<A, B, false>(a, st);
+void launch_fwd(const hear_context *ctx, const PassArgs &a, cudaStream_t st) {
+    switch (pick(ctx, true, a.n_limbs, a.n_limbs * (a.n / Split<A>::TILE))) {
+    case kNttFused: launch_fused<A, B, true>(a, st); break;
+    case kNttNarrow: launch_fwd_t<A, B, true>(a, st); break;
+    default: launch_fwd_t<A, B, false>(a, st);
+    }
+}
+template <int A, int B>
+void launch_inv(const hear_context *ctx, const PassArgs &a, cudaStream_t st) {
+    switch (pick(ctx, false, a.n_limbs, a.n_limbs * (a.n / Split<A>::TILE))) {
+    case kNttFused: launch_fused<A, B, false>(a, st); break;
+    case kNttNarrow: launch_inv_t<A, B, true>(a, st); break;
+    default: launch_inv_t<A, B, false>(a, st);
+    }
 }
 
 PassArgs make_args(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, LimbMap map, bool fwd) {
@@ -268,15 +447,15 @@ double ntt_bytes(const hear_context *ctx, uint32_t n_limbs, const LimbMap &map) 
 
 void ntt_forward(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, LimbMap map, cudaStream_t s) {
     if (n_limbs == 0) return;
-    ProfScope ps(ctx, "ntt_fwd", s, ntt_bytes(ctx, n_limbs, map), 2);
+    ProfScope ps(ctx, "ntt_fwd", s, ntt_bytes(ctx, n_limbs, map), launches_of(ctx, true, n_limbs));
     PassArgs a = make_args(ctx, data, n_limbs, map, true);
     switch (ctx->log_n) {
-    case 11: launch_fwd<6, 5>(a, s); break;
-    case 12: launch_fwd<6, 6>(a, s); break;
-    case 13: launch_fwd<7, 6>(a, s); break;
-    case 14: launch_fwd<7, 7>(a, s); break;
-    case 15: launch_fwd<8, 7>(a, s); break;
-    case 16: launch_fwd<8, 8>(a, s); break;
+    case 11: launch_fwd<6, 5>(ctx, a, s); break;
+    case 12: launch_fwd<6, 6>(ctx, a, s); break;
+    case 13: launch_fwd<7, 6>(ctx, a, s); break;
+    case 14: launch_fwd<7, 7>(ctx, a, s); break;
+    case 15: launch_fwd<8, 7>(ctx, a, s); break;
+    case 16: launch_fwd<8, 8>(ctx, a, s); break;
     default: throw Error(HEAR_E_UNSUPPORTED, "log_n outside [11, 16]");
     }
     HEAR_CHECK_CUDA(cudaGetLastError());
@@ -284,18 +463,101 @@ void ntt_forward(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, Limb
 
 void ntt_inverse(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, LimbMap map, cudaStream_t s) {
     if (n_limbs == 0) return;
-    ProfScope ps(ctx, "ntt_inv", s, ntt_bytes(ctx, n_limbs, map), 2);
+    ProfScope ps(ctx, "ntt_inv", s, ntt_bytes(ctx, n_limbs, map), launches_of(ctx, false, n_limbs));
     PassArgs a = make_args(ctx, data, n_limbs, map, false);
     switch (ctx->log_n) {
-    case 11: launch_inv<6, 5>(a, s); break;
-    case 12: launch_inv<6, 6>(a, s); break;
-    case 13: launch_inv<7, 6>(a, s); break;
-    case 14: launch_inv<7, 7>(a, s); break;
-    case 15: launch_inv<8, 7>(a, s); break;
-    case 16: launch_inv<8, 8>(a, s); break;
+    case 11: launch_inv<6, 5>(ctx, a, s); break;
+    case 12: launch_inv<6, 6>(ctx, a, s); break;
+    case 13: launch_inv<7, 6>(ctx, a, s); break;
+    case 14: launch_inv<7, 7>(ctx, a, s); break;
+    case 15: launch_inv<8, 7>(ctx, a, s); break;
+    case 16: launch_inv<8, 8>(ctx, a, s); break;
     default: throw Error(HEAR_E_UNSUPPORTED, "log_n outside [11, 16]");
     }
     HEAR_CHECK_CUDA(cudaGetLastError());
+}
+
+constexpr float kFusedMargin = 1.15f;
+
+// Time every launch variant for launches of 1, 2, 4, .. max_limbs limbs (both directions)
+// and record the fastest per bucket.  Runs on the context's stream; the caller keeps other
+// work off the context meanwhile.
+void ntt_tune(hear_context *ctx, uint32_t max_limbs, int iters, float *ms_out) {
+    HEAR_REQUIRE(max_limbs >= 1 && iters >= 1, HEAR_E_INVAL, "bad tuning range");
+    cudaStream_t st = ctx->stream;
+    const size_t words = (size_t)max_limbs * ctx->n;
+    DevBuf d(words * 8, st);
+    HEAR_CHECK_CUDA(cudaMemsetAsync(d.p, 0, words * 8, st));
+    LimbMap m;
+    m.per_group = ctx->nqp();
+    m.q_count = ctx->n_q;
+    m.n_q = ctx->n_q;
+    cudaEvent_t e0, e1;
+    HEAR_CHECK_CUDA(cudaEventCreate(&e0));
+    HEAR_CHECK_CUDA(cudaEventCreate(&e1));
+    const int saved = ctx->ntt_force;
+    try {
+        for (int dir = 0; dir < 2; dir++)
+            for (uint32_t b = 0; b < (uint32_t)kNttBuckets && (1u << b) <= max_limbs; b++) {
+                const uint32_t nl = 1u << b;
+                float best = 0;
+                uint8_t best_v = kNttAuto;
+                for (uint8_t v = 0; v < 3; v++) {
+                    ctx->ntt_force = v;
+                    // timed as a replayed CUDA graph of `iters` back-to-back transforms, the
+                    // way whole evaluations run
+                    cudaGraph_t graph = nullptr;
+                    cudaGraphExec_t exec = nullptr;
+                    HEAR_CHECK_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+                    try {
+                        for (int i = 0; i < iters; i++) {
+                            if (dir == 0) ntt_forward(ctx, d.u64(), nl, m, st);
+                            else ntt_inverse(ctx, d.u64(), nl, m, st);
+                        }
+                    } catch (...) {
+                        cudaStreamEndCapture(st, &graph);
+                        if (graph) cudaGraphDestroy(graph);
+                        throw;
+                    }
+                    HEAR_CHECK_CUDA(cudaStreamEndCapture(st, &graph));
+                    cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+                    cudaGraphDestroy(graph);
+                    HEAR_CHECK_CUDA(ie);
+                    float ms = 0;
+                    cudaError_t le = cudaGraphLaunch(exec, st);
+                    if (le == cudaSuccess) le = cudaEventRecord(e0, st);
+                    if (le == cudaSuccess) le = cudaGraphLaunch(exec, st);
+                    if (le == cudaSuccess) le = cudaEventRecord(e1, st);
+                    if (le == cudaSuccess) le = cudaEventSynchronize(e1);
+                    if (le == cudaSuccess) le = cudaEventElapsedTime(&ms, e0, e1);
+                    cudaGraphExecDestroy(exec);
+                    HEAR_CHECK_CUDA(le);
+                    ms /= iters;
+                    if (ms_out) ms_out[((size_t)dir * kNttBuckets + b) * 3 + v] = ms;
+                    // the one-launch form carries both passes' code: inside a whole
+                    // evaluation it competes for the instruction cache with the other
+                    // kernels, so it must win its isolated timing by a clear margin
+                    const float eff = v == kNttFused ? ms * kFusedMargin : ms;
+                    if (best_v == kNttAuto || eff < best) {
+                        best = eff;
+                        best_v = v;
+                    }
+                }
+                ctx->ntt_choice[dir][b] = best_v;
+            }
+    } catch (...) {
+        ctx->ntt_force = saved;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    ctx->ntt_force = saved;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // buckets above the tuned range keep the choice of the largest tuned bucket
+    for (int dir = 0; dir < 2; dir++)
+        for (uint32_t b = 1; b < (uint32_t)kNttBuckets; b++)
+            if ((1u << b) > max_limbs) ctx->ntt_choice[dir][b] = ctx->ntt_choice[dir][b - 1];
 }
 
 }  // namespace hear

@@ -148,6 +148,9 @@ def _load():
         "hear_profile_begin": (st, [_vp]),
         "hear_profile_end": (st, [_vp, ctypes.POINTER(hear_profile_entry), ctypes.c_size_t, _szp]),
         "hear_launch_count": (ctypes.c_uint64, []),
+        "hear_ntt_tune": (st, [_vp, ctypes.c_uint32, ctypes.c_int, ctypes.POINTER(ctypes.c_uint8),
+                               ctypes.POINTER(ctypes.c_float)]),
+        "hear_ntt_set_variant": (st, [_vp, ctypes.c_int]),
         "hear_dbg_poly_mul": (st, [_vp, ctypes.c_uint32, _u64p, _u64p, _u64p]),
         "hear_dbg_ntt_roundtrip": (st, [_vp, _u64p, ctypes.c_size_t]),
         "hear_dbg_ntt_time": (st, [_vp, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
@@ -567,6 +570,22 @@ def hear_launch_count():
 
 
 # ---------------------------------------------------------------- debug
+HEAR_NTT_WIDE, HEAR_NTT_NARROW, HEAR_NTT_FUSED = 0, 1, 2
+
+
+def hear_ntt_tune(ctx, max_limbs=512, iters=5):
+    """time the NTT launch variants; returns (choice uint8[2][16], ms float32[2][16][3])"""
+    choice = np.zeros((2, 16), dtype=np.uint8)
+    ms = np.zeros((2, 16, 3), dtype=np.float32)
+    _check(lib.hear_ntt_tune(ctx, int(max_limbs), int(iters), _p(choice, ctypes.POINTER(ctypes.c_uint8)),
+                             _p(ms, ctypes.POINTER(ctypes.c_float))))
+    return choice, ms
+
+
+def hear_ntt_set_variant(ctx, variant):
+    _check(lib.hear_ntt_set_variant(ctx, int(variant)))
+
+
 def hear_dbg_poly_mul(ctx, prime, a, b):
     a, b = _arr(a, np.uint64), _arr(b, np.uint64)
     out = np.empty_like(a)
