@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--rates", default="500,2000,8000", help="request rates (req/s) of the served sweep")
     ap.add_argument("--no-cnn", action="store_true", help="skip the CNN sections (Table 1 layers, 1D-CNN-64)")
+    ap.add_argument("--no-min-level", action="store_true", help="skip the minimal-start-level variant")
     ap.add_argument("--conv-rows", default="all", help="Table 1 rows to time: all | comma-separated indices")
     return ap.parse_args()
 
@@ -231,13 +232,19 @@ def oracle_sample(w, steps_keys, seconds_budget=25.0):
 
 # ------------------------------------------------------------------ GPU arm
 class Setup:
-    def __init__(self, H, w, stream, device):
+    def __init__(self, H, w, stream, device, level=None):
+        """level: evaluate from ciphertexts dropped to this level (None = the top level)"""
         self.H, self.w = H, w
         self.ctx = H.hear_context_create(w.log_n, w.q_bits, w.p_bits, w.log2_scale, w.sigma, device)
-        self.model = H.hear_model_create(self.ctx, w.layers, w.clip_dim)
+        self.model = H.hear_model_create(self.ctx, w.layers, w.clip_dim, level)
         self.steps = H.hear_model_rotations(self.model)
         self.sk, self.pk, self.evk = H.hear_keygen(self.ctx, 301, self.steps)
         self.cts = [H.hear_encrypt_clips(self.ctx, self.pk, w.ct_clips(i), 401, i, stream) for i in range(w.n_ct)]
+        if level is not None:
+            top = self.cts
+            self.cts = [H.hear_ciphertext_drop_level(c, level, stream) for c in top]
+            for c in top:
+                H.hear_ciphertext_destroy(c)
         self.clips_per_step = w.n_clips
 
     def step(self, stream):
@@ -565,6 +572,21 @@ def main_gpu(a):
         SL.close()
     else:
         S.close()
+    if result is not None and not a.no_min_level and a.workload == "small" and a.clips is None and dist.world == 1:
+        # minimal start level: inputs dropped to the depth of the network (3 of 7 levels for
+        # the small network, 5 of 14 for the large one); the same networks and parameters
+        ms = {}
+        for name, level, steps in (("small", 3, a.steps), ("large", 5, max(3, a.steps // 4))):
+            wl = make_workload(name)
+            SM = Setup(H, wl, stream, device, level)
+            tms, mlat, ml, mclk = run_gpu(SM, steps, 2, dist, torch, stream, device)
+            ms[name] = {"workload": describe(wl), "start_level": level,
+                        "value": steps * SM.clips_per_step / (tms / 1e3), "unit": UNIT,
+                        "ms_per_step": tms / steps, "p50_ms": mlat[len(mlat) // 2],
+                        "p99_ms": mlat[min(len(mlat) - 1, int(0.99 * len(mlat)))], "gpu_launches": ml,
+                        "clocks": mclk}
+            SM.close()
+        result["min_start_level"] = ms
     if result is not None and not a.no_cnn and dist.world == 1:
         rows = list(range(8)) if a.conv_rows == "all" else [int(x) for x in a.conv_rows.split(",")]
         result["conv_table1"] = {

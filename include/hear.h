@@ -142,6 +142,13 @@ hear_status hear_rotate_hoisted(const hear_eval_keys *evk, const hear_ciphertext
                                 size_t n_steps, hear_ciphertext **out, void *stream);
 /* divide by the last prime and drop it (lazy rescaling uses it once per sum) */
 hear_status hear_rescale(const hear_ciphertext *ct, hear_ciphertext **out, void *stream);
+/* the same ciphertext over Q_level (level <= its level): the residues of the primes above
+ * `level` are discarded, no division, the scale is unchanged.  Evaluating a network from
+ * the lowest level its depth needs (minimal start level) makes every later operation work
+ * on fewer limbs; the plaintexts of a model built for that level carry only those limbs
+ * (Methods, "Algorithmic and cryptographic optimizations", level-aware encoding). */
+hear_status hear_ciphertext_drop_level(const hear_ciphertext *ct, uint32_t level, hear_ciphertext **out,
+                                       void *stream);
 hear_status hear_add(const hear_ciphertext *a, const hear_ciphertext *b, hear_ciphertext **out, void *stream);
 /* MultPlain(ct, pt): multiply by the plaintext encoding of N/2 slot values at pt_scale
  * (level-aware: the plaintext carries only the limbs of ct's level) -- no rescale */
@@ -173,6 +180,12 @@ typedef struct hear_layer_desc {
  * (Methods, "Algorithmic and cryptographic optimizations"; "Non-convolutional layers"). */
 hear_status hear_model_create(hear_context *ctx, const hear_layer_desc *layers, size_t n_layers,
                               uint32_t clip_dim, hear_model **out);
+/* the same network for input ciphertexts at `level` (1 <= level <= L; the network's depth
+ * must fit): every plaintext is encoded with the limbs of the level where it is used */
+hear_status hear_model_create_at_level(hear_context *ctx, const hear_layer_desc *layers, size_t n_layers,
+                                       uint32_t clip_dim, uint32_t level, hear_model **out);
+/* input and output level of a model */
+hear_status hear_model_levels(const hear_model *m, uint32_t *level_in, uint32_t *level_out);
 void hear_model_destroy(hear_model *);
 /* rotation steps (slots) the model needs keys for */
 hear_status hear_model_rotations(const hear_model *m, int32_t *steps, size_t cap, size_t *n);
@@ -185,7 +198,7 @@ hear_status hear_evaluate(const hear_model *m, const hear_eval_keys *evk, hear_c
 hear_status hear_evaluate_layer(const hear_model *m, size_t layer, const hear_eval_keys *evk,
                                 hear_ciphertext *const *in, size_t n_ct, hear_ciphertext **out, void *stream);
 /* end-to-end from host buffers: n_ct input ciphertexts in the coefficient domain
- * (uint64[n_ct][2][n_q][N], top level, `scale`) -> the result ciphertexts in the
+ * (uint64[n_ct][2][l+1][N] at the model's input level l, `scale`) -> the result ciphertexts in the
  * coefficient domain (uint64[n_ct][2][level_out+1][N]); copies both ways are included */
 hear_status hear_evaluate_host(const hear_model *m, const hear_eval_keys *evk, const uint64_t *in_words,
                                size_t n_ct, double scale, uint64_t *out_words, size_t cap, size_t *n,
@@ -281,6 +294,7 @@ typedef struct hear_cnn_input {
     uint32_t h, w;        /* map size (1D: h = 1)                                       */
     uint32_t pitch;       /* row pitch in slots (0 = w)                                 */
     uint32_t stride;      /* puncture of the input (1 for an encrypted input tensor)    */
+    uint32_t level;       /* level of the input ciphertexts (0 = the top level)          */
 } hear_cnn_input;
 typedef struct hear_cnn_layer {
     uint32_t kind;

@@ -349,6 +349,21 @@ hear_status hear_rescale(const hear_ciphertext *ct, hear_ciphertext **out, void 
     });
 }
 
+hear_status hear_ciphertext_drop_level(const hear_ciphertext *ct, uint32_t level, hear_ciphertext **out,
+                                       void *stream) {
+    if (!ct || !out) return fail(HEAR_E_INVAL, "null argument");
+    if (level > ct->level) return fail(HEAR_E_LEVEL, "cannot raise the level of a ciphertext");
+    hear_context *c = ct->ctx;
+    return guard(c, [&] {
+        cudaStream_t st = stream_of(c, stream);
+        std::unique_ptr<hear_ciphertext> r(new_ct(c, level, ct->n_poly, ct->scale, st));
+        HEAR_CHECK_CUDA(cudaMemcpy2DAsync(r->d.p, (size_t)(level + 1) * c->n * 8, ct->d.p,
+                                          (size_t)(ct->level + 1) * c->n * 8, (size_t)(level + 1) * c->n * 8,
+                                          ct->n_poly, cudaMemcpyDeviceToDevice, st));
+        *out = r.release();
+    });
+}
+
 hear_status hear_add(const hear_ciphertext *a, const hear_ciphertext *b, hear_ciphertext **out, void *stream) {
     if (!a || !b || !out) return fail(HEAR_E_INVAL, "null argument");
     hear_context *c = a->ctx;
@@ -397,7 +412,20 @@ hear_status hear_multiply_relin(const hear_eval_keys *evk, const hear_ciphertext
 hear_status hear_model_create(hear_context *ctx, const hear_layer_desc *layers, size_t n_layers, uint32_t clip_dim,
                               hear_model **out) {
     if (!ctx || !layers || !out) return fail(HEAR_E_INVAL, "null argument");
-    return guard(ctx, [&] { *out = model_create(ctx, layers, n_layers, clip_dim); });
+    return guard(ctx, [&] { *out = model_create(ctx, layers, n_layers, clip_dim, ctx->L); });
+}
+
+hear_status hear_model_create_at_level(hear_context *ctx, const hear_layer_desc *layers, size_t n_layers,
+                                       uint32_t clip_dim, uint32_t level, hear_model **out) {
+    if (!ctx || !layers || !out) return fail(HEAR_E_INVAL, "null argument");
+    return guard(ctx, [&] { *out = model_create(ctx, layers, n_layers, clip_dim, level); });
+}
+
+hear_status hear_model_levels(const hear_model *m, uint32_t *level_in, uint32_t *level_out) {
+    if (!m || m->layers.empty()) return fail(HEAR_E_INVAL, "null model");
+    if (level_in) *level_in = m->layers.front().level_in;
+    if (level_out) *level_out = m->layers.back().level_out;
+    return HEAR_OK;
 }
 
 void hear_model_destroy(hear_model *m) {

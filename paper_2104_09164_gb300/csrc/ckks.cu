@@ -397,8 +397,10 @@ DevBuf eval_fc(const hear_model *m, const hear_model::Fc &fc, const hear_eval_ke
 
 }  // namespace
 
-hear_model *model_create(hear_context *c, const hear_layer_desc *layers, size_t n_layers, uint32_t clip_dim) {
+hear_model *model_create(hear_context *c, const hear_layer_desc *layers, size_t n_layers, uint32_t clip_dim,
+                         uint32_t start_level) {
     HEAR_REQUIRE(layers && n_layers > 0, HEAR_E_INVAL, "no layers");
+    HEAR_REQUIRE(start_level >= 1 && start_level <= c->L, HEAR_E_LEVEL, "start level outside [1, L]");
     const uint32_t slots = c->n / 2;
     HEAR_REQUIRE(clip_dim && (clip_dim & (clip_dim - 1)) == 0 && clip_dim <= slots, HEAR_E_INVAL,
                  "clip_dim must be a power of two <= N/2");
@@ -407,7 +409,7 @@ hear_model *model_create(hear_context *c, const hear_layer_desc *layers, size_t 
     m->clip_dim = clip_dim;
     m->k = slots / clip_dim;
     m->M = clip_dim;
-    uint32_t level = c->L, dim = clip_dim;
+    uint32_t level = start_level, dim = clip_dim;
     std::set<int32_t> rots;
     for (size_t li = 0; li < n_layers; li++) {
         const hear_layer_desc &d = layers[li];

@@ -82,7 +82,10 @@ void mul_relin(hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *a
 DevBuf encode_plain(hear_context *c, const double *z, double scale, uint32_t level, cudaStream_t st);
 
 // network
-hear_model *model_create(hear_context *c, const hear_layer_desc *layers, size_t n_layers, uint32_t clip_dim);
+// the network evaluated from input ciphertexts at start_level (every plaintext encoded at
+// the level where it is used)
+hear_model *model_create(hear_context *c, const hear_layer_desc *layers, size_t n_layers, uint32_t clip_dim,
+                         uint32_t start_level);
 // evaluate layers [l0, l1) on a batch x at the first layer's level; returns the output batch
 DevBuf evaluate_batch(const hear_model *m, const hear_eval_keys *evk, size_t l0, size_t l1, const uint64_t *x,
                       uint32_t n_ct, uint32_t *level_out, double scale_in, double *scale_out, cudaStream_t st);

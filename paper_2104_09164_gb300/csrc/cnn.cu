@@ -191,7 +191,8 @@ hear_cnn *cnn_create(hear_context *c, const hear_cnn_input *in, const hear_cnn_l
     m->in_h = g.h;
     m->in_w = g.w;
     m->in_pitch = g.pitch;
-    uint32_t level = c->L;
+    HEAR_REQUIRE(in->level <= c->L, HEAR_E_LEVEL, "input level above the top level");
+    uint32_t level = in->level ? in->level : c->L;
     std::set<int32_t> rots;
     auto push = [&](hear_cnn::Op &&op, uint32_t layer) {
         op.level_out = level;

@@ -60,7 +60,8 @@ class hear_server_counters(ctypes.Structure):
 
 class hear_cnn_input(ctypes.Structure):
     _fields_ = [("conv_dims", ctypes.c_uint32), ("c_in", ctypes.c_uint32), ("h", ctypes.c_uint32),
-                ("w", ctypes.c_uint32), ("pitch", ctypes.c_uint32), ("stride", ctypes.c_uint32)]
+                ("w", ctypes.c_uint32), ("pitch", ctypes.c_uint32), ("stride", ctypes.c_uint32),
+                ("level", ctypes.c_uint32)]
 
 
 class hear_cnn_layer(ctypes.Structure):
@@ -121,6 +122,10 @@ def _load():
         "hear_model_create": (st, [_vp, ctypes.POINTER(hear_layer_desc), ctypes.c_size_t, ctypes.c_uint32,
                                    ctypes.POINTER(_vp)]),
         "hear_model_destroy": (None, [_vp]),
+        "hear_model_create_at_level": (st, [_vp, ctypes.POINTER(hear_layer_desc), ctypes.c_size_t,
+                                            ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(_vp)]),
+        "hear_model_levels": (st, [_vp, _u32p, _u32p]),
+        "hear_ciphertext_drop_level": (st, [_vp, ctypes.c_uint32, ctypes.POINTER(_vp), _vp]),
         "hear_model_rotations": (st, [_vp, _i32p, ctypes.c_size_t, _szp]),
         "hear_model_output_positions": (st, [_vp, _u32p, ctypes.c_size_t, _szp]),
         "hear_evaluate": (st, [_vp, _vp, ctypes.POINTER(_vp), ctypes.c_size_t, ctypes.POINTER(_vp), _vp]),
@@ -347,8 +352,9 @@ def hear_multiply_relin(evk, a, b, stream=None):
 
 
 # ---------------------------------------------------------------- network
-def hear_model_create(ctx, layers, clip_dim):
-    """layers: sequence of ("fc", W) | ("square",) | ("fc_sq_fc", W1, W2) with float64 matrices"""
+def hear_model_create(ctx, layers, clip_dim, level=None):
+    """layers: sequence of ("fc", W) | ("square",) | ("fc_sq_fc", W1, W2) with float64 matrices;
+    level: input level (None = the top level; hear_model_create_at_level)"""
     descs = (hear_layer_desc * len(layers))()
     keep = []
     for i, layer in enumerate(layers):
@@ -367,7 +373,26 @@ def hear_model_create(ctx, layers, clip_dim):
         else:
             raise ValueError(layer[0])
     h = _vp()
-    _check(lib.hear_model_create(ctx, descs, len(layers), int(clip_dim), ctypes.byref(h)))
+    if level is None:
+        _check(lib.hear_model_create(ctx, descs, len(layers), int(clip_dim), ctypes.byref(h)))
+    else:
+        _check(lib.hear_model_create_at_level(ctx, descs, len(layers), int(clip_dim), int(level), ctypes.byref(h)))
+    return h.value
+
+
+def hear_model_create_at_level(ctx, layers, clip_dim, level):
+    return hear_model_create(ctx, layers, clip_dim, level)
+
+
+def hear_model_levels(m):
+    a, b = ctypes.c_uint32(), ctypes.c_uint32()
+    _check(lib.hear_model_levels(m, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def hear_ciphertext_drop_level(ct, level, stream=None):
+    h = _vp()
+    _check(lib.hear_ciphertext_drop_level(ct, int(level), ctypes.byref(h), _stream(stream)))
     return h.value
 
 
@@ -429,7 +454,7 @@ def hear_cnn_create(ctx, spec, strategies=None):
     "layers": [("conv", W[c_out][c_in][fh][fw], fast) | ("quad", a, b, c) | ("pool",) |
     ("gap",) | ("fc", W, bias)]}; strategies: one per conv / fc layer (see _strategy)"""
     inp = hear_cnn_input(int(spec["conv_dims"]), int(spec["c_in"]), int(spec["h"]), int(spec["w"]),
-                         int(spec.get("pitch", 0)), int(spec.get("stride", 1)))
+                         int(spec.get("pitch", 0)), int(spec.get("stride", 1)), int(spec.get("level", 0)))
     layers = spec["layers"]
     descs = (hear_cnn_layer * len(layers))()
     keep = []
