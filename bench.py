@@ -478,17 +478,29 @@ def run_cnn(H, torch, stream, device, batches=(1, 16), iters=5):
     """the paper-shaped 1D-CNN-64 (2 x 32 x 15 inputs, N = 2^15): whole encrypted network"""
     from paper_2104_09164_gb300.collapse import collapse_cnn
     from paper_2104_09164_gb300.workloads import make_cnn
+    from paper_2104_09164_gb300.autotune import tune_cnn
     net = make_cnn("cnn1d64", n_samples=max(batches))
     spec = collapse_cnn(net)
     ctx = H.hear_context_create(net.log_n, net.q_bits, net.p_bits, net.log2_scale, net.sigma, device)
-    m = H.hear_cnn_create(ctx, spec)
+    t0 = time.perf_counter()
+    strategies, tune_report = tune_cnn(H, ctx, spec, net.slots, len(net.q_bits) - 1, iters=3, stream=stream)
+    tune_s = time.perf_counter() - t0
+    # default strategies (hybrid, n1 = min(4, block shifts)) for comparison
+    md = H.hear_cnn_create(ctx, spec)
+    m = H.hear_cnn_create(ctx, spec, strategies)
     ops = H.hear_cnn_ops(m)
-    sk, pk, evk = H.hear_keygen(ctx, 301, H.hear_cnn_rotations(m))
+    steps = sorted(set(H.hear_cnn_rotations(m)) | set(H.hear_cnn_rotations(md)))
+    sk, pk, evk = H.hear_keygen(ctx, 301, steps)
     cts = [H.hear_cnn_encrypt(ctx, pk, m, clip, 401, s, stream)[0] for s, clip in enumerate(net.clips)]
+    default_ms = _time_range(H, md, evk, 0, len(ops), cts[:1], 1, torch, stream, iters)
+    H.hear_cnn_destroy(md)
     res = {"workload": "1D-CNN-64 (conv 2->64->128->256, 3 taps, quadratic activations, average / global "
                        "pooling, FC 256->2; fast convolution in conv2 / conv3), 2x32x15 synthetic skeleton "
                        "clips, RNS-CKKS N=2^15, q=60+14x40 bits, p=60+60 bits",
-           "ops": len(ops), "keyswitch_per_sample": sum(o["n_keyswitch"] for o in ops), "batches": []}
+           "ops": len(ops), "keyswitch_per_sample": sum(o["n_keyswitch"] for o in ops),
+           "strategies": {"tuned": [r["best"] for r in tune_report], "tune_s": tune_s, "layers": tune_report,
+                          "default_batch1_ms": default_ms},
+           "batches": []}
     for b in batches:
         H.hear_profile_begin(ctx)
         for o in H.hear_cnn_evaluate(m, evk, 0, len(ops), cts[:b], b, stream):

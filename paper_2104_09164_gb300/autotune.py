@@ -1,0 +1,133 @@
+"""Per-layer strategy autotuning of the encrypted skeleton CNN.
+
+Every convolution of Eq. (conv) can split its rotations r_k + dist*l into a hoisted baby
+step and a giant step applied to the summed products in several ways -- the full-step,
+giant-step and baby-step strategies of the paper (Methods, "Algorithmic and cryptographic
+optimizations") and the hybrid splits between them -- and which is fastest depends on the
+numbers of input and output ciphertexts.  ``tune_cnn`` times each candidate on the GPU for
+each convolutional layer at the geometry and level the layer has inside the network, on
+random inputs with throw-away keys, and returns the fastest per layer.  Every candidate
+computes the same convolution (bit-exact against the oracle with that strategy).
+
+Host logic only: all timing goes through the C ABI (``hear.py``).
+"""
+import time
+
+import numpy as np
+
+
+def conv_layer_specs(spec):
+    """[(index among the conv / FC layers, level drop before it, single-layer spec)] for every
+    convolution of a collapsed network: the map geometry, channel count and puncture at the
+    layer's input; the level drop counts the levels the network consumes before the layer."""
+    dims = spec["conv_dims"]
+    c, h, w = spec["c_in"], spec["h"], spec["w"]
+    pitch = spec.get("pitch") or w
+    stride = spec.get("stride", 1)
+    used = 0
+    out = []
+    si = 0
+    for layer in spec["layers"]:
+        kind = layer[0]
+        if kind == "conv":
+            single = {"conv_dims": dims, "c_in": c, "h": h, "w": w,
+                      "pitch": w if dims == 1 else pitch, "stride": stride,
+                      "layers": [("conv", layer[1], layer[2])]}
+            out.append((si, used, single))
+            si += 1
+            used += 2 if layer[2] else 1
+            c = layer[1].shape[0]
+        elif kind == "quad":
+            used += 2
+        elif kind == "pool":
+            stride *= 2
+            w //= 2
+            if dims == 2:
+                h //= 2
+        elif kind == "fc":
+            si += 1
+            used += 1
+    return out
+
+
+def candidates(lr):
+    """strategies for a convolution whose block shifts span lr ciphertext blocks"""
+    c = ["full", "baby", "giant"]
+    n1 = 2
+    while n1 < lr:
+        c.append(("hybrid", n1))
+        n1 *= 2
+    return c
+
+
+def _block_shifts(H, ctx, single, level):
+    """block shifts of the layer = number of giant steps of its baby-step split"""
+    m = H.hear_cnn_create(ctx, dict(single, level=level), ["baby"])
+    try:
+        diag = [o for o in H.hear_cnn_ops(m) if o["kind"] == H.HEAR_CNN_OP_DIAG][0]
+        return diag["n_giants"]
+    finally:
+        H.hear_cnn_destroy(m)
+
+
+def time_layer(H, ctx, single, level, strategy, slots, n_samples=1, iters=3, stream=None, seed=7):
+    """median device ms of the whole single-layer plan (pack / conv / phase sums) on random
+    input ciphertexts at `level`, throw-away keys"""
+    import torch
+    m = H.hear_cnn_create(ctx, dict(single, level=level), [strategy])
+    try:
+        ops = H.hear_cnn_ops(m)
+        sk, pk, evk = H.hear_keygen(ctx, 9001, H.hear_cnn_rotations(m))
+        n_in = ops[0]["n_in"]
+        rng = np.random.default_rng(seed)
+        st = stream if stream is not None else torch.cuda.current_stream()
+        cts = []
+        for k in range(n_samples * n_in):
+            top = H.hear_encrypt(ctx, pk, rng.uniform(-1.0, 1.0, slots), 2.0 ** 40, 9002, k, st)
+            cts.append(H.hear_ciphertext_drop_level(top, ops[0]["level_in"], st))
+            H.hear_ciphertext_destroy(top)
+        for o in H.hear_cnn_evaluate(m, evk, 0, len(ops), cts, n_samples, st):
+            H.hear_ciphertext_destroy(o)
+        times = []
+        for _ in range(iters):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            outs = H.hear_cnn_evaluate(m, evk, 0, len(ops), cts, n_samples, st)
+            e1.record(st)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            for o in outs:
+                H.hear_ciphertext_destroy(o)
+        for h in cts:
+            H.hear_ciphertext_destroy(h)
+        H.hear_eval_keys_destroy(evk)
+        H.hear_public_key_destroy(pk)
+        H.hear_secret_key_destroy(sk)
+        times.sort()
+        return times[len(times) // 2]
+    finally:
+        H.hear_cnn_destroy(m)
+
+
+def tune_cnn(H, ctx, spec, slots, top_level, n_samples=1, iters=3, stream=None):
+    """-> (strategies for hear_cnn_create, report) with the fastest candidate per conv layer
+    (FC layers keep the default); `top_level` = the level of the network's input"""
+    n_tunable = sum(1 for layer in spec["layers"] if layer[0] in ("conv", "fc"))
+    strategies = [None] * n_tunable
+    report = []
+    for si, used, single in conv_layer_specs(spec):
+        level = top_level - used
+        lr = _block_shifts(H, ctx, single, level)
+        t0 = time.perf_counter()
+        timed = [(time_layer(H, ctx, single, level, cand, slots, n_samples, iters, stream), cand)
+                 for cand in candidates(lr)]
+        timed.sort(key=lambda t: t[0])
+        strategies[si] = timed[0][1]
+        report.append({"layer": si, "level": level, "block_shifts": lr,
+                       "ms": {_name(c): t for t, c in timed}, "best": _name(timed[0][1]),
+                       "tune_s": time.perf_counter() - t0})
+    return strategies, report
+
+
+def _name(s):
+    return s if isinstance(s, str) else "%s(%d)" % s

@@ -140,3 +140,17 @@ def test_table1_layer_sampled(H, idx, fast):
     finally:
         H.hear_cnn_destroy(m)
         H.hear_context_destroy(ctx)
+
+
+def test_autotuned_strategies_bit_exact(H):
+    """the tuner's per-layer choice evaluates bit-exactly like the oracle with that choice"""
+    from paper_2104_09164_gb300.autotune import tune_cnn
+    net = make_cnn("cnn_toy", n_samples=2)
+    spec = collapse_cnn(net)
+    ctx = H.hear_context_create(net.log_n, net.q_bits, net.p_bits, net.log2_scale, net.sigma, 0)
+    try:
+        strategies, report = tune_cnn(H, ctx, spec, net.slots, len(net.q_bits) - 1, iters=2)
+    finally:
+        H.hear_context_destroy(ctx)
+    assert len(report) == 3 and all(r["best"] in r["ms"] for r in report)
+    _network(H, "cnn_toy", strategies, 2, [0])

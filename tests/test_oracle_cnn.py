@@ -199,3 +199,35 @@ def test_encrypted_toy_cnn_matches_fp64():
     dec = o.decrypt(keys, r[0])
     assert np.max(np.abs(dec[out] - cnn_forward(net, net.clips[0]))) < 2.0 ** -15
     assert np.max(np.abs(dec - OC.simulate(ops, [OC.pack_input(spec, net.clips[0], S)])[0])) < 2.0 ** -15
+
+
+def test_autotune_layer_geometry_matches_the_network_plan():
+    """the single-layer specs the tuner times have the layouts and level drops the layers
+    have inside the network (compared with the oracle's network plan)"""
+    from paper_2104_09164_gb300.autotune import candidates, conv_layer_specs
+    for name in ("cnn_toy", "cnn2d64"):
+        net = make_cnn(name, n_samples=1)
+        spec = collapse_cnn(net)
+        S = net.slots
+        ops, _ = OC.build_plan(spec, S)
+        depth_before = []
+        used = 0
+        for op in ops:
+            if op[0] in ("pack", "diag"):
+                depth_before.append(used)
+            used += {"diag": 1, "pack": 1, "quad": 2}.get(op[0], 0)
+        diags = [op for op in ops if op[0] == "diag"][:-1]      # the convolutions (last = FC)
+        singles = conv_layer_specs(spec)
+        assert len(singles) == len(diags)
+        k = 0
+        for (si, used_before, single), diag in zip(singles, diags):
+            sops, _ = OC.build_plan(single, S)
+            sdiag = [op for op in sops if op[0] == "diag"][0]
+            assert sdiag[1] == diag[1]
+            assert sorted(sdiag[2].keys()) == sorted(diag[2].keys())
+            for key in diag[2]:
+                assert np.allclose(sdiag[2][key], diag[2][key])
+            assert used_before == depth_before[k]
+            k += 2 if single["layers"][0][2] else 1
+    assert candidates(32) == ["full", "baby", "giant", ("hybrid", 2), ("hybrid", 4), ("hybrid", 8),
+                              ("hybrid", 16)]
