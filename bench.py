@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--rates", default="500,2000,8000", help="request rates (req/s) of the served sweep")
     ap.add_argument("--no-cnn", action="store_true", help="skip the CNN sections (Table 1 layers, 1D-CNN-64)")
     ap.add_argument("--no-min-level", action="store_true", help="skip the minimal-start-level variant")
+    ap.add_argument("--mix-rates", default="100,300,1000", help="request rates (req/s) of the mixed sweep")
     ap.add_argument("--conv-rows", default="all", help="Table 1 rows to time: all | comma-separated indices")
     return ap.parse_args()
 
@@ -324,77 +325,127 @@ def run_e2e(S, steps, warmup, torch, stream):
     return el, pin_in.nbytes, pin_out.nbytes
 
 
+class Served:
+    """one continuous-batching server over a Setup, with every batch-size graph captured"""
+
+    def __init__(self, H, S, max_batch, n_slots, budget):
+        self.H, self.S = H, S
+        w = S.w
+        self.k = min(w.clips_per_ct, w.slots // w.clip_dim)
+        self.words1 = H.hear_ciphertext_export(S.cts[0]).reshape(-1)
+        self.scale = 2.0 ** w.log2_scale
+        self.out_words = H.hear_evaluate_host(S.model, S.evk, self.words1, 1, self.scale)[0].size
+        self.srv = H.hear_server_create(S.model, S.evk, max_batch=max_batch, n_slots=n_slots,
+                                        hbm_budget_bytes=budget)
+        ids = []
+        for rep in range(2 * n_slots):
+            b = max_batch
+            while b >= 1:
+                ids.append((H.hear_server_submit(self.srv, np.tile(self.words1, b), b, b * self.k, self.scale), b))
+                b //= 2
+        done = set()
+        while len(done) < len(ids):
+            for rid, b in ids:
+                if rid not in done and H.hear_server_poll(self.srv, rid, b * self.out_words) is not None:
+                    done.add(rid)
+            time.sleep(0.0005)
+
+    def submit(self, n_clips):
+        n_ct = (n_clips + self.k - 1) // self.k
+        return self.H.hear_server_submit(self.srv, np.tile(self.words1, n_ct), n_ct, n_clips, self.scale), n_ct
+
+    def poll(self, rid, n_ct):
+        return self.H.hear_server_poll(self.srv, rid, n_ct * self.out_words) is not None
+
+    def close(self):
+        self.H.hear_server_destroy(self.srv)
+
+
+def poisson_sweep(servers, mix, rates, seconds, seed):
+    """Poisson requests of 1-8 clips (uniform) at each rate; each request goes to server i
+    with probability mix[i]; per-server and total throughput, client-side p50/p99 latency
+    (submit -> result read back)."""
+    H = servers[0].H
+    rng = np.random.default_rng(seed)
+    out = []
+    for lam in rates:
+        base = [H.hear_server_stats(sv.srv) for sv in servers]
+        t0 = time.perf_counter()
+        t_next = t0
+        pend = {}
+        lat = [[] for _ in servers]
+        clips = 0
+
+        def drain():
+            for key in list(pend):
+                si, rid, n_ct, ts = pend[key]
+                if servers[si].poll(rid, n_ct):
+                    lat[si].append((time.perf_counter() - ts) * 1e3)
+                    del pend[key]
+        while True:
+            now = time.perf_counter()
+            if now - t0 >= seconds:
+                break
+            while t_next <= now:
+                n_clips = int(rng.integers(1, 9))
+                si = int(rng.choice(len(servers), p=mix))
+                rid, n_ct = servers[si].submit(n_clips)
+                pend[(si, rid)] = (si, rid, n_ct, time.perf_counter())
+                clips += n_clips
+                t_next += rng.exponential(1.0 / lam)
+            drain()
+            time.sleep(0.0002)
+        while pend:
+            drain()
+            time.sleep(0.0002)
+        el = time.perf_counter() - t0
+        row = {"rate_req_s": lam, "offered_inferences_s": clips / seconds, "inferences_s": 0.0, "per_net": []}
+        for si, sv in enumerate(servers):
+            st = H.hear_server_stats(sv.srv)
+            l = sorted(lat[si])
+            v = (st["clips_done"] - base[si]["clips_done"]) / el
+            row["inferences_s"] += v
+            row["per_net"].append({"net": sv.S.w.name, "inferences_s": v,
+                                   "requests": st["requests_done"] - base[si]["requests_done"],
+                                   "batches": st["batches"] - base[si]["batches"],
+                                   "max_in_flight_ciphertexts": st["max_in_flight_ciphertexts"],
+                                   "p50_ms": l[len(l) // 2] if l else None,
+                                   "p99_ms": l[min(len(l) - 1, int(0.99 * len(l)))] if l else None})
+        if len(servers) == 1:
+            row.update({k: row["per_net"][0][k] for k in ("requests", "batches", "p50_ms", "p99_ms")})
+            del row["per_net"]
+        out.append(row)
+    return out
+
+
 def run_served(H, S, rates, seconds=2.0, max_batch=32, n_slots=2, seed=601):
     """Poisson request stream against the continuous-batching server: each request carries
     1-8 clips (uniform) of the small network (4 clips per ciphertext -> 1 or 2 ciphertexts);
     returns per-rate throughput and p50/p99 latency (submit -> result ready)."""
-    w = S.w
-    k = w.slots // w.clip_dim
-    words1 = H.hear_ciphertext_export(S.cts[0]).reshape(-1)
-    scale = 2.0 ** w.log2_scale
-    rng = np.random.default_rng(seed)
-    srv = H.hear_server_create(S.model, S.evk, max_batch=max_batch, n_slots=n_slots, hbm_budget_bytes=96 << 30)
-    out = []
+    sv = Served(H, S, max_batch, n_slots, 96 << 30)
     try:
-        out_words = None
-        # warm-up: every power-of-two batch size on every slot captures its graphs once
-        ids = []
-        for rep in range(2 * n_slots):
-            for b in (32, 16, 8, 4, 2, 1):
-                if b <= max_batch:
-                    ids.append((H.hear_server_submit(srv, np.tile(words1, b), b, b * k, scale), b))
-        res = {}
-        while len(res) < len(ids):
-            for rid, b in ids:
-                if rid not in res:
-                    if out_words is None:
-                        out_words = H.hear_evaluate_host(S.model, S.evk, words1, 1, scale)[0].size
-                    r = H.hear_server_poll(srv, rid, b * out_words)
-                    if r is not None:
-                        res[rid] = r
-            time.sleep(0.0005)
-        for lam in rates:
-            base = H.hear_server_stats(srv)
-            t0 = time.perf_counter()
-            t_next = t0
-            pend = {}
-            lat = []
-            clips = 0
-
-            def drain():
-                for rid in list(pend):
-                    n_ct, ts = pend[rid]
-                    if H.hear_server_poll(srv, rid, n_ct * out_words) is not None:
-                        lat.append((time.perf_counter() - ts) * 1e3)
-                        del pend[rid]
-            while True:
-                now = time.perf_counter()
-                if now - t0 >= seconds:
-                    break
-                while t_next <= now:
-                    n_clips = int(rng.integers(1, 9))
-                    n_ct = (n_clips + k - 1) // k
-                    rid = H.hear_server_submit(srv, np.tile(words1, n_ct), n_ct, n_clips, scale)
-                    pend[rid] = (n_ct, time.perf_counter())
-                    clips += n_clips
-                    t_next += rng.exponential(1.0 / lam)
-                drain()
-                time.sleep(0.0002)
-            while pend:
-                drain()
-                time.sleep(0.0002)
-            el = time.perf_counter() - t0
-            st = H.hear_server_stats(srv)
-            lat.sort()
-            out.append({"rate_req_s": lam, "offered_inferences_s": clips / seconds,
-                        "inferences_s": (st["clips_done"] - base["clips_done"]) / el,
-                        "requests": st["requests_done"] - base["requests_done"],
-                        "batches": st["batches"] - base["batches"],
-                        "p50_ms": lat[len(lat) // 2] if lat else None,
-                        "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))] if lat else None})
+        return poisson_sweep([sv], [1.0], rates, seconds, seed)
     finally:
-        H.hear_server_destroy(srv)
-    return out
+        sv.close()
+
+
+def run_served_mix(H, stream, device, rates, seconds=2.0, seed=602):
+    """70% small / 30% large requests from one Poisson stream, each network served by its
+    own continuous-batching server (own context, keys resident in HBM, HBM budget for the
+    ciphertexts in flight); both servers' batches share the GPU."""
+    from paper_2104_09164_gb300.workloads import make_workload
+    Ss = Setup(H, make_workload("small"), stream, device)
+    Sl = Setup(H, make_workload("large", 8), stream, device)
+    servers = []
+    try:
+        servers.append(Served(H, Ss, 32, 2, 48 << 30))
+        servers.append(Served(H, Sl, 8, 2, 96 << 30))
+        return poisson_sweep(servers, [0.7, 0.3], rates, seconds, seed)
+    finally:
+        for sv in servers:
+            sv.close()
+        Ss.close()
+        Sl.close()
 
 
 # ------------------------------------------------------------------ skeleton CNN sections
@@ -566,6 +617,13 @@ def main_gpu(a):
                                         "continuous batching (max 32 ciphertexts, 2 batches in flight)",
                             "note": "latency = client submit -> result read back (host), per rate",
                             "sweep": sweep}
+    if result is not None and not a.no_served and a.workload == "small" and a.clips is None and dist.world == 1:
+        result["served_mix"] = {
+            "workload": "70% small (N=2^14) / 30% large (N=2^15) requests of 1-8 clips from one Poisson "
+                        "stream; one continuous-batching server per network (max batch 32 / 8 "
+                        "ciphertexts, 2 batches in flight each), both on one GPU",
+            "note": "latency = client submit -> result read back (host), per rate and network",
+            "sweep": run_served_mix(H, stream, device, [float(x) for x in a.mix_rates.split(",")])}
     if not a.no_batched and a.workload == "small" and a.clips is None:
         S.close()
         wl = make_workload("large")
