@@ -176,7 +176,8 @@ typedef struct hear_layer_desc {
  * diagonals diag_i[p] = W[p mod d_out][(p+i) mod d_in], n1 = smallest power of two with
  * n1^2 >= D, n2 = ceil(D/n1); hoisted baby rotations rho^(i k), plaintexts pre-rotated by
  * rho^(-j n1 k) and encoded at the level of use with scale q_level, non-hoisted giant
- * rotations rho^(j n1 k), one rescale, then rotate-and-sum by d_out 2^t k
+ * rotations rho^(j n1 k), one rescale, then the sum of the d_in/d_out copies rho^(j d_out k)
+ * in rounds of up to 8 (rotsum_radix) copies whose rotations share one ModUp
  * (Methods, "Algorithmic and cryptographic optimizations"; "Non-convolutional layers"). */
 hear_status hear_model_create(hear_context *ctx, const hear_layer_desc *layers, size_t n_layers,
                               uint32_t clip_dim, hear_model **out);
@@ -184,6 +185,17 @@ hear_status hear_model_create(hear_context *ctx, const hear_layer_desc *layers, 
  * must fit): every plaintext is encoded with the limbs of the level where it is used */
 hear_status hear_model_create_at_level(hear_context *ctx, const hear_layer_desc *layers, size_t n_layers,
                                        uint32_t clip_dim, uint32_t level, hear_model **out);
+/* model options: level = input level (0 = the top level); rotsum_radix = copies folded
+ * per rotate-and-sum round (0 = the default 8; 2 is the plain log2-depth tree; r > 2 folds
+ * r copies with r - 1 rotations that share one ModUp (hoisting), cutting the sequential
+ * rounds to ceil(log_r) at the cost of more rotation keys; a power of two <= 64).
+ * hear_model_create and hear_model_create_at_level use the default. */
+typedef struct hear_model_opts {
+    uint32_t level;
+    uint32_t rotsum_radix;
+} hear_model_opts;
+hear_status hear_model_create_ex(hear_context *ctx, const hear_layer_desc *layers, size_t n_layers,
+                                 uint32_t clip_dim, const hear_model_opts *opts, hear_model **out);
 /* input and output level of a model */
 hear_status hear_model_levels(const hear_model *m, uint32_t *level_in, uint32_t *level_out);
 void hear_model_destroy(hear_model *);

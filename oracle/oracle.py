@@ -141,6 +141,11 @@ class Keys:
         self.rot = {}        # galois -> [dnum][2][n_q+n_p][N]
 
 
+# copies folded per rotate-and-sum round (radix - 1 rotations sharing one ModUp); 2 = the
+# plain log2-depth tree; 8 is the evaluation's default
+ROTSUM_RADIX = 8
+
+
 def galois_for_step(step: int, n: int) -> int:
     """rho^step (left rotation by step slots) <-> X -> X^(5^step mod 2N)"""
     return pow(5, step % (n // 2), 2 * n)
@@ -412,7 +417,7 @@ class Oracle:
         """pos-space vector of size M -> N/2 slots, slot p*k + c holds v[p]"""
         return np.repeat(np.asarray(v, dtype=np.float64), k)
 
-    def fc(self, ct: Ct, W, k, keys: Keys, pool=None):
+    def fc(self, ct: Ct, W, k, keys: Keys, pool=None, radix=ROTSUM_RADIX):
         """Encrypted FC layer, BSGS diagonal form with hoisted baby steps and one lazy
         rescale, followed by rotate-and-sum; output replicated with period d_out."""
         d_out, d_in = W.shape
@@ -444,45 +449,61 @@ class Oracle:
                 inner = self.rotate(inner, j * n1 * k, keys)
             acc = inner if acc is None else self.add(acc, inner)
         out = self.rescale(acc)
-        step = d_out
-        while step < d_in:
-            out = self.add(out, self.rotate(out, step * k, keys))
-            step *= 2
-        return out
+        return self.rotsum(out, d_out, d_in // d_out, k, keys, radix)
+
+    def rotsum(self, ct: Ct, step, count, k, keys: Keys, radix):
+        """sum of the count (a power of two) copies rho^(j*step*k)(ct), j < count, folded in
+        rounds of up to radix - 1 hoisted rotations: out <- out + sum_j rho^(j*s*k)(out),
+        s <- s*r (radix 2 is the plain rotate-and-sum tree)"""
+        while count > 1:
+            r = min(radix, count)
+            rots = self.rotate_hoisted(ct, [j * step * k for j in range(1, r)], keys)
+            for x in rots:
+                ct = self.add(ct, x)
+            step *= r
+            count //= r
+        return ct
 
     def square(self, ct: Ct, keys: Keys):
         return self.mul_relin_rescale(ct, ct, keys)
 
-    def fc_sq_fc(self, ct: Ct, W1, W2, k, keys: Keys, pool=None):
+    def fc_sq_fc(self, ct: Ct, W1, W2, k, keys: Keys, pool=None, radix=ROTSUM_RADIX):
         """Collapsed FC -> x^2 -> FC: out_c = sum_r W2[c,r] y_r^2 with y = W1 x, as the
         product of y and u = U x, U[(c, r), :] = W2[c, r] W1[r, :], both at one level,
         then rotate-and-sum over r.  Logit c lands at pos c * d1."""
         d1 = W1.shape[0]
         d2 = W2.shape[0]
         U = (W2[:, :, None] * W1[None, :, :]).reshape(d2 * d1, W1.shape[1])
-        y = self.fc(ct, W1, k, keys, pool)
-        u = self.fc(ct, U, k, keys, pool)
+        y = self.fc(ct, W1, k, keys, pool, radix)
+        u = self.fc(ct, U, k, keys, pool, radix)
         z = self.mul_relin_rescale(y, u, keys)
-        step = 1
-        while step < d1:
-            z = self.add(z, self.rotate(z, step * k, keys))
-            step *= 2
-        return z
+        return self.rotsum(z, 1, d1, k, keys, radix)
 
-    def evaluate(self, layers, ct: Ct, k, keys: Keys, pool=None):
+    def evaluate(self, layers, ct: Ct, k, keys: Keys, pool=None, radix=ROTSUM_RADIX):
         for layer in layers:
             if layer[0] == "fc":
-                ct = self.fc(ct, layer[1], k, keys, pool)
+                ct = self.fc(ct, layer[1], k, keys, pool, radix)
             elif layer[0] == "square":
                 ct = self.square(ct, keys)
             elif layer[0] == "fc_sq_fc":
-                ct = self.fc_sq_fc(ct, layer[1], layer[2], k, keys, pool)
+                ct = self.fc_sq_fc(ct, layer[1], layer[2], k, keys, pool, radix)
             else:
                 raise ValueError(layer[0])
         return ct
 
 
-def rotation_steps(layers, clip_dim, k):
+def rotsum_steps(step, count, radix):
+    """rotation amounts (pos units) of Oracle.rotsum"""
+    out = []
+    while count > 1:
+        r = min(radix, count)
+        out += [j * step for j in range(1, r)]
+        step *= r
+        count //= r
+    return out
+
+
+def rotation_steps(layers, clip_dim, k, radix=ROTSUM_RADIX):
     """pos-space rotation amounts (times k = slots) every key switch of the network needs"""
     steps = set()
 
@@ -492,10 +513,7 @@ def rotation_steps(layers, clip_dim, k):
             steps.add(b * k)
         for j in range(1, n2):
             steps.add(j * n1 * k)
-        s = d_out
-        while s < d_in:
-            steps.add(s * k)
-            s *= 2
+        steps.update(s * k for s in rotsum_steps(d_out, d_in // d_out, radix))
 
     for layer in layers:
         if layer[0] == "fc":
@@ -504,10 +522,7 @@ def rotation_steps(layers, clip_dim, k):
             W1, W2 = layer[1], layer[2]
             fc_steps(*W1.shape)
             fc_steps(W2.shape[0] * W1.shape[0], W1.shape[1])
-            s = 1
-            while s < W1.shape[0]:
-                steps.add(s * k)
-                s *= 2
+            steps.update(s * k for s in rotsum_steps(1, W1.shape[0], radix))
     return sorted(steps)
 
 

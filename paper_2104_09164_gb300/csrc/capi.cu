@@ -412,13 +412,21 @@ hear_status hear_multiply_relin(const hear_eval_keys *evk, const hear_ciphertext
 hear_status hear_model_create(hear_context *ctx, const hear_layer_desc *layers, size_t n_layers, uint32_t clip_dim,
                               hear_model **out) {
     if (!ctx || !layers || !out) return fail(HEAR_E_INVAL, "null argument");
-    return guard(ctx, [&] { *out = model_create(ctx, layers, n_layers, clip_dim, ctx->L); });
+    return guard(ctx, [&] { *out = model_create(ctx, layers, n_layers, clip_dim, ctx->L, kDefaultRotsumRadix); });
 }
 
 hear_status hear_model_create_at_level(hear_context *ctx, const hear_layer_desc *layers, size_t n_layers,
                                        uint32_t clip_dim, uint32_t level, hear_model **out) {
     if (!ctx || !layers || !out) return fail(HEAR_E_INVAL, "null argument");
-    return guard(ctx, [&] { *out = model_create(ctx, layers, n_layers, clip_dim, level); });
+    return guard(ctx, [&] { *out = model_create(ctx, layers, n_layers, clip_dim, level, kDefaultRotsumRadix); });
+}
+
+hear_status hear_model_create_ex(hear_context *ctx, const hear_layer_desc *layers, size_t n_layers, uint32_t clip_dim,
+                                const hear_model_opts *opts, hear_model **out) {
+    if (!ctx || !layers || !out) return fail(HEAR_E_INVAL, "null argument");
+    const uint32_t level = opts && opts->level ? opts->level : ctx->L;
+    const uint32_t radix = opts && opts->rotsum_radix ? opts->rotsum_radix : kDefaultRotsumRadix;
+    return guard(ctx, [&] { *out = model_create(ctx, layers, n_layers, clip_dim, level, radix); });
 }
 
 hear_status hear_model_levels(const hear_model *m, uint32_t *level_in, uint32_t *level_out) {

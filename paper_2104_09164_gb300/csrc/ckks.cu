@@ -274,8 +274,23 @@ void mul_relin(hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *a
 // ------------------------------------------------------------------ network
 namespace {
 
+// rounds of the sum of `count` (a power of two) copies rho^(j*step*k): each round folds r =
+// min(radix, remaining) copies with r - 1 rotations of one hoisted ModUp
+std::vector<std::vector<int32_t>> rotsum_rounds(uint32_t step, uint32_t count, uint32_t k, uint32_t radix) {
+    std::vector<std::vector<int32_t>> rounds;
+    while (count > 1) {
+        const uint32_t r = std::min(radix, count);
+        std::vector<int32_t> round;
+        for (uint32_t j = 1; j < r; j++) round.push_back((int32_t)(j * step * k));
+        rounds.push_back(round);
+        step *= r;
+        count /= r;
+    }
+    return rounds;
+}
+
 void build_fc(hear_context *c, hear_model::Fc &fc, const double *W, uint32_t d_out, uint32_t d_in, uint32_t level,
-              uint32_t k, uint32_t M) {
+              uint32_t k, uint32_t M, uint32_t radix) {
     HEAR_REQUIRE(d_out && d_in && (d_out & (d_out - 1)) == 0 && (d_in & (d_in - 1)) == 0 && d_in % d_out == 0 &&
                      M % d_in == 0,
                  HEAR_E_INVAL, "FC dimensions must be powers of two with d_out | d_in | clip_dim");
@@ -330,14 +345,14 @@ void build_fc(hear_context *c, hear_model::Fc &fc, const double *W, uint32_t d_o
         }
         HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
     }
-    fc.rotsum.clear();
-    for (uint32_t s = d_out; s < d_in; s *= 2) fc.rotsum.push_back((int32_t)(s * k));
+    fc.rotsum = rotsum_rounds(d_out, d_in / d_out, k, radix);
 }
 
 void fc_rotations(const hear_model::Fc &fc, uint32_t k, std::set<int32_t> &out) {
     for (uint32_t b = 1; b < fc.n1; b++) out.insert((int32_t)(b * k));
     for (uint32_t j = 1; j < fc.n2; j++) out.insert((int32_t)(j * fc.n1 * k));
-    for (int32_t s : fc.rotsum) out.insert(s);
+    for (auto &round : fc.rotsum)
+        for (int32_t s : round) out.insert(s);
 }
 
 const uint64_t *need_key(const hear_eval_keys *evk, uint32_t g) {
@@ -346,14 +361,21 @@ const uint64_t *need_key(const hear_eval_keys *evk, uint32_t g) {
     return k;
 }
 
-// rotate-and-sum x <- x + rho^s(x) for each step s
+// rotate-and-sum in rounds: x <- x + sum_s rho^s(x) over the steps of each round, the
+// rotations of a round sharing one ModUp of x (hoisting)
 void rotsum(hear_context *c, const hear_eval_keys *evk, uint32_t level, uint32_t n_ct, uint64_t *x,
-            const std::vector<int32_t> &steps, cudaStream_t st) {
-    const uint64_t ctw = 2ull * (level + 1) * c->n;
-    DevBuf r((size_t)n_ct * ctw * 8, st);
-    for (int32_t s : steps) {
-        uint32_t g = galois_of(c, s);
-        rotate_each(c, level, 1, n_ct, x, {Rot{need_key(evk, g), g}}, r.u64(), st);
+            const std::vector<std::vector<int32_t>> &rounds, cudaStream_t st) {
+    const uint64_t ctw = 2ull * (level + 1) * c->n, batch = (uint64_t)n_ct * ctw;
+    for (auto &round : rounds) {
+        std::vector<Rot> rots;
+        for (int32_t s : round) {
+            uint32_t g = galois_of(c, s);
+            rots.push_back(Rot{need_key(evk, g), g});
+        }
+        const uint32_t R = (uint32_t)rots.size();
+        DevBuf r((size_t)R * batch * 8, st);
+        rotate_hoisted(c, level, n_ct, x, rots, r.u64(), st);
+        if (R > 1) sum_ct(c, level, 2 * n_ct, r.u64(), batch, R, r.u64(), st);
         add_ct(c, level, 2 * n_ct, x, r.u64(), x, st);
     }
 }
@@ -398,7 +420,9 @@ DevBuf eval_fc(const hear_model *m, const hear_model::Fc &fc, const hear_eval_ke
 }  // namespace
 
 hear_model *model_create(hear_context *c, const hear_layer_desc *layers, size_t n_layers, uint32_t clip_dim,
-                         uint32_t start_level) {
+                         uint32_t start_level, uint32_t rotsum_radix) {
+    HEAR_REQUIRE(rotsum_radix >= 2 && (rotsum_radix & (rotsum_radix - 1)) == 0 && rotsum_radix <= 64, HEAR_E_INVAL,
+                 "rotsum radix must be a power of two in [2, 64]");
     HEAR_REQUIRE(layers && n_layers > 0, HEAR_E_INVAL, "no layers");
     HEAR_REQUIRE(start_level >= 1 && start_level <= c->L, HEAR_E_LEVEL, "start level outside [1, L]");
     const uint32_t slots = c->n / 2;
@@ -407,6 +431,7 @@ hear_model *model_create(hear_context *c, const hear_layer_desc *layers, size_t 
     auto m = std::make_unique<hear_model>();
     m->ctx = c;
     m->clip_dim = clip_dim;
+    m->rotsum_radix = rotsum_radix;
     m->k = slots / clip_dim;
     m->M = clip_dim;
     uint32_t level = start_level, dim = clip_dim;
@@ -419,7 +444,7 @@ hear_model *model_create(hear_context *c, const hear_layer_desc *layers, size_t 
         if (d.kind == HEAR_LAYER_FC) {
             HEAR_REQUIRE(d.w && d.d_in == dim, HEAR_E_INVAL, "FC input dimension mismatch");
             HEAR_REQUIRE(!d.bias, HEAR_E_UNSUPPORTED, "bias is not supported");
-            build_fc(c, L.fc, d.w, d.d_out, d.d_in, level, m->k, m->M);
+            build_fc(c, L.fc, d.w, d.d_out, d.d_in, level, m->k, m->M, rotsum_radix);
             fc_rotations(L.fc, m->k, rots);
             level -= 1;
             dim = d.d_out;
@@ -431,17 +456,18 @@ hear_model *model_create(hear_context *c, const hear_layer_desc *layers, size_t 
                          "FC_SQ_FC must be the last layer and match the input dimension");
             HEAR_REQUIRE(level >= 2, HEAR_E_LEVEL, "not enough levels for the network");
             const uint32_t d1 = d.d_out, d2 = d.d_out2;
-            build_fc(c, L.fc, d.w, d1, d.d_in, level, m->k, m->M);
+            build_fc(c, L.fc, d.w, d1, d.d_in, level, m->k, m->M, rotsum_radix);
             std::vector<double> U((size_t)d2 * d1 * d.d_in);
             for (uint32_t cc = 0; cc < d2; cc++)
                 for (uint32_t r = 0; r < d1; r++)
                     for (uint32_t col = 0; col < d.d_in; col++)
                         U[((size_t)cc * d1 + r) * d.d_in + col] = d.w2[(size_t)cc * d1 + r] * d.w[(size_t)r * d.d_in + col];
-            build_fc(c, L.fc2, U.data(), d2 * d1, d.d_in, level, m->k, m->M);
+            build_fc(c, L.fc2, U.data(), d2 * d1, d.d_in, level, m->k, m->M, rotsum_radix);
             fc_rotations(L.fc, m->k, rots);
             fc_rotations(L.fc2, m->k, rots);
-            for (uint32_t s = 1; s < d1; s *= 2) L.final_rotsum.push_back((int32_t)(s * m->k));
-            for (int32_t s : L.final_rotsum) rots.insert(s);
+            L.final_rotsum = rotsum_rounds(1, d1, m->k, rotsum_radix);
+            for (auto &round : L.final_rotsum)
+                for (int32_t s : round) rots.insert(s);
             level -= 2;
             for (uint32_t cc = 0; cc < d2; cc++) m->out_pos.push_back(cc * d1);
             dim = 0;

@@ -14,13 +14,13 @@ struct hear_model {
         uint32_t d_out = 0, d_in = 0, D = 0, n1 = 0, n2 = 0, level = 0;
         hear::DevBuf pts;                           // [n2*n1][level+1][N] Montgomery, zero = no diagonal
         hear::DevBuf bias;                          // plaintext at level-1 (Montgomery), or empty
-        std::vector<int32_t> rotsum;                // slot steps of rotate-and-sum
+        std::vector<std::vector<int32_t>> rotsum;   // rotate-and-sum rounds (slot steps, hoisted per round)
     };
     struct Layer {
         uint32_t kind = 0;
         uint32_t level_in = 0, level_out = 0;
         Fc fc, fc2;                                 // FC; FC_SQ_FC: fc = W1, fc2 = collapsed U
-        std::vector<int32_t> final_rotsum;          // FC_SQ_FC: sum over r
+        std::vector<std::vector<int32_t>> final_rotsum;   // FC_SQ_FC: sum over r (rounds)
     };
     // CUDA graph of one evaluation (layers [l0, l1) for n_ct ciphertexts with given keys and
     // input scale), replayed from a fixed input/output workspace
@@ -38,6 +38,7 @@ struct hear_model {
     };
     hear_context *ctx = nullptr;
     uint32_t clip_dim = 0, k = 0, M = 0;
+    uint32_t rotsum_radix = 8;                      // copies folded per rotate-and-sum round
     mutable std::mutex plan_mu;
     mutable std::vector<std::unique_ptr<Plan>> plans;
     std::vector<Layer> layers;
@@ -82,10 +83,13 @@ void mul_relin(hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *a
 DevBuf encode_plain(hear_context *c, const double *z, double scale, uint32_t level, cudaStream_t st);
 
 // network
+// copies folded per rotate-and-sum round by default (measured on the small network at batch
+// 1: 1.45 / 1.20 / 1.19 / 1.22 ms for radix 2 / 4 / 8 / 16)
+constexpr uint32_t kDefaultRotsumRadix = 8;
 // the network evaluated from input ciphertexts at start_level (every plaintext encoded at
 // the level where it is used)
 hear_model *model_create(hear_context *c, const hear_layer_desc *layers, size_t n_layers, uint32_t clip_dim,
-                         uint32_t start_level);
+                         uint32_t start_level, uint32_t rotsum_radix = kDefaultRotsumRadix);
 // evaluate layers [l0, l1) on a batch x at the first layer's level; returns the output batch
 DevBuf evaluate_batch(const hear_model *m, const hear_eval_keys *evk, size_t l0, size_t l1, const uint64_t *x,
                       uint32_t n_ct, uint32_t *level_out, double scale_in, double *scale_out, cudaStream_t st);

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libhear.so")
 HEAR_LAYER_FC = 1
 HEAR_LAYER_SQUARE = 2
 HEAR_LAYER_FC_SQ_FC = 3
+DEFAULT_ROTSUM_RADIX = 8
 HEAR_CNN_CONV, HEAR_CNN_QUAD, HEAR_CNN_POOL, HEAR_CNN_GAP, HEAR_CNN_FC = 1, 2, 3, 4, 5
 HEAR_STRATEGY_HYBRID, HEAR_STRATEGY_FULL, HEAR_STRATEGY_BABY, HEAR_STRATEGY_GIANT = 0, 1, 2, 3
 HEAR_CNN_OP_DIAG, HEAR_CNN_OP_PACK, HEAR_CNN_OP_ROTSUM, HEAR_CNN_OP_QUAD, HEAR_CNN_OP_BIAS = 1, 2, 3, 4, 5
@@ -40,6 +41,10 @@ class hear_params_desc(ctypes.Structure):
 class hear_layer_desc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_uint32), ("d_out", ctypes.c_uint32), ("d_in", ctypes.c_uint32),
                 ("w", _dp), ("bias", _dp), ("d_out2", ctypes.c_uint32), ("w2", _dp)]
+
+
+class hear_model_opts(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_uint32), ("rotsum_radix", ctypes.c_uint32)]
 
 
 class hear_profile_entry(ctypes.Structure):
@@ -125,6 +130,8 @@ def _load():
         "hear_model_create_at_level": (st, [_vp, ctypes.POINTER(hear_layer_desc), ctypes.c_size_t,
                                             ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(_vp)]),
         "hear_model_levels": (st, [_vp, _u32p, _u32p]),
+        "hear_model_create_ex": (st, [_vp, ctypes.POINTER(hear_layer_desc), ctypes.c_size_t, ctypes.c_uint32,
+                                      ctypes.POINTER(hear_model_opts), ctypes.POINTER(_vp)]),
         "hear_ciphertext_drop_level": (st, [_vp, ctypes.c_uint32, ctypes.POINTER(_vp), _vp]),
         "hear_model_rotations": (st, [_vp, _i32p, ctypes.c_size_t, _szp]),
         "hear_model_output_positions": (st, [_vp, _u32p, ctypes.c_size_t, _szp]),
@@ -352,9 +359,9 @@ def hear_multiply_relin(evk, a, b, stream=None):
 
 
 # ---------------------------------------------------------------- network
-def hear_model_create(ctx, layers, clip_dim, level=None):
+def hear_model_create(ctx, layers, clip_dim, level=None, rotsum_radix=None):
     """layers: sequence of ("fc", W) | ("square",) | ("fc_sq_fc", W1, W2) with float64 matrices;
-    level: input level (None = the top level; hear_model_create_at_level)"""
+    level: input level (None = the top level); rotsum_radix: see hear_model_opts"""
     descs = (hear_layer_desc * len(layers))()
     keep = []
     for i, layer in enumerate(layers):
@@ -373,11 +380,18 @@ def hear_model_create(ctx, layers, clip_dim, level=None):
         else:
             raise ValueError(layer[0])
     h = _vp()
-    if level is None:
+    if rotsum_radix is not None:
+        opts = hear_model_opts(int(level or 0), int(rotsum_radix))
+        _check(lib.hear_model_create_ex(ctx, descs, len(layers), int(clip_dim), ctypes.byref(opts), ctypes.byref(h)))
+    elif level is None:
         _check(lib.hear_model_create(ctx, descs, len(layers), int(clip_dim), ctypes.byref(h)))
     else:
         _check(lib.hear_model_create_at_level(ctx, descs, len(layers), int(clip_dim), int(level), ctypes.byref(h)))
     return h.value
+
+
+def hear_model_create_ex(ctx, layers, clip_dim, level=0, rotsum_radix=0):
+    return hear_model_create(ctx, layers, clip_dim, level or None, rotsum_radix or DEFAULT_ROTSUM_RADIX)
 
 
 def hear_model_create_at_level(ctx, layers, clip_dim, level):

@@ -544,3 +544,23 @@ def test_toy_network_within_bound():
     dec = o.decrypt(keys, out)
     logits = np.array([dec[p * k] for p in O.output_positions(w.layers)])
     assert np.max(np.abs(logits - w.fp64_forward(w.clips)[0])) <= 2.0 ** -15
+
+
+def test_rotsum_radix_folds_the_same_sum():
+    """the hoisted rotate-and-sum rounds of any radix decrypt to sum_j rho^(j*step*k)(z)"""
+    from oracle import oracle as O
+    o = O.Oracle(12, [50, 40, 40], [50], 3.2)
+    S = o.n // 2
+    k = 4
+    steps = set()
+    for radix in (2, 4, 16):
+        steps.update(s * k for s in O.rotsum_steps(8, 16, radix))
+    keys = o.keygen(7, [O.galois_for_step(s, o.n) for s in steps])
+    z = np.random.default_rng(3).uniform(-1, 1, S)
+    ct = o.encrypt(keys.pk, z, 11, 0, 2.0 ** 40)
+    want = sum(np.roll(z, -j * 8 * k) for j in range(16))
+    for radix in (2, 4, 16):
+        got = o.decrypt(keys, o.rotsum(ct, 8, 16, k, keys, radix))
+        assert np.max(np.abs(got - want)) < 2.0 ** -20, radix
+    assert O.rotsum_steps(8, 16, 4) == [8, 16, 24, 32, 64, 96]
+    assert O.rotsum_steps(1, 64, 16) == list(range(1, 16)) + [16, 32, 48]
