@@ -388,12 +388,13 @@ hear_status hear_profile_end(hear_context *ctx, hear_profile_entry *out, size_t 
 uint64_t hear_launch_count(void);
 
 /* ---- NTT launch variants and their tuner ----
- * The forward / inverse NTT has three launch forms with bit-identical results:
+ * The forward / inverse NTT has four launch forms with bit-identical results:
  * HEAR_NTT_WIDE (two passes, 4096-word shared-memory tiles, 256 threads), HEAR_NTT_NARROW
- * (two passes, 1024-word tiles, 64 threads: more CTAs for launches of few limbs) and
+ * (two passes, 1024-word tiles, 64 threads: more CTAs for launches of few limbs),
  * HEAR_NTT_FUSED (one launch; a cluster of 8 CTAs per limb exchanges the intermediate
- * through distributed shared memory, so each residue crosses HBM once).  hear_ntt_tune
- * times all three for launches of 1, 2, 4, .. max_limbs limbs in both directions on the
+ * through distributed shared memory, so each residue crosses HBM once) and HEAR_NTT_TINY
+ * (two passes, 1024-word tiles, 256 threads with radix-4 units: four times the threads of
+ * the narrow form for launches of few limbs).  hear_ntt_tune times all four for launches of 1, 2, 4, .. max_limbs limbs in both directions on the
  * context's stream (each timing a replayed CUDA graph of back-to-back transforms) and keeps
  * the fastest per power-of-two bucket, the one-launch form only if it is 15% faster (its
  * larger code competes for the instruction cache inside whole evaluations; larger launches use the
@@ -401,12 +402,13 @@ uint64_t hear_launch_count(void);
  * tens of milliseconds) unless the environment sets HEAR_NTT_TUNE=0, which keeps a fixed
  * rule (narrow below two wide CTAs per SM, wide above).  It must
  * not run concurrently with other work on the context.  ms_out (optional) receives
- * float[2][16][3] = [forward, inverse][bucket][variant] milliseconds per launch, choice_out
+ * float[2][16][4] = [forward, inverse][bucket][variant] milliseconds per launch, choice_out
  * (optional) uint8_t[2][16].  hear_ntt_set_variant forces one variant (-1 = back to the
  * table); it exists for tests and measurements. */
 #define HEAR_NTT_WIDE 0
 #define HEAR_NTT_NARROW 1
 #define HEAR_NTT_FUSED 2
+#define HEAR_NTT_TINY 3
 hear_status hear_ntt_tune(hear_context *ctx, uint32_t max_limbs, int iters, uint8_t *choice_out, float *ms_out);
 hear_status hear_ntt_set_variant(hear_context *ctx, int variant);
 

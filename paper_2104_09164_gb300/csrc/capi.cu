@@ -646,7 +646,7 @@ hear_status hear_ntt_tune(hear_context *ctx, uint32_t max_limbs, int iters, uint
 }
 
 hear_status hear_ntt_set_variant(hear_context *ctx, int variant) {
-    if (!ctx || variant < -1 || variant > 2) return fail(HEAR_E_INVAL, "bad argument");
+    if (!ctx || variant < -1 || variant >= kNttVariants) return fail(HEAR_E_INVAL, "bad argument");
     ctx->ntt_force = variant;
     return HEAR_OK;
 }

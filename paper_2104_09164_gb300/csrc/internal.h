@@ -103,8 +103,9 @@ extern std::atomic<uint64_t> g_launches;
 
 // ------------------------------------------------------------------ handles
 // NTT launch variants (ntt.cu): two-pass wide tiles, two-pass narrow tiles, one-launch
-// cluster form; kNttAuto = the default rule
-enum : uint8_t { kNttWide = 0, kNttNarrow = 1, kNttFused = 2, kNttAuto = 255 };
+// cluster form, two-pass tiny tiles (radix-4 units); kNttAuto = the default rule
+enum : uint8_t { kNttWide = 0, kNttNarrow = 1, kNttFused = 2, kNttTiny = 3, kNttAuto = 255 };
+constexpr int kNttVariants = 4;
 constexpr int kNttBuckets = 16;   // launches of 1, 2-3, 4-7, .. limbs (log2 buckets)
 inline uint32_t ntt_bucket(uint32_t n_limbs) {
     uint32_t b = 0;
@@ -210,6 +211,7 @@ inline LimbMap map_qp(uint32_t level, uint32_t n_q, uint32_t K) {
 void ntt_forward(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, LimbMap map, cudaStream_t s);
 void ntt_inverse(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, LimbMap map, cudaStream_t s);
 // fill ctx->ntt_choice by timing the launch variants (ms_out: [2][kNttBuckets][3] or null)
+// ms_out: [2][kNttBuckets][kNttVariants] or null
 void ntt_tune(hear_context *ctx, uint32_t max_limbs, int iters, float *ms_out);
 
 // RAII bracket of one or more kernel launches for the profiler

@@ -51,9 +51,14 @@ template <> struct Split<5> { static constexpr int W0 = 3, W1 = 2, TILE = 2048; 
 template <> struct Split<6> { static constexpr int W0 = 3, W1 = 3, TILE = 2048; };
 template <> struct Split<7> { static constexpr int W0 = 4, W1 = 3, TILE = 4096; };
 template <> struct Split<8> { static constexpr int W0 = 4, W1 = 4, TILE = 4096; };
-template <int LOGR, bool NARROW> struct Tile {
-    static constexpr int WORDS = NARROW ? Split<LOGR>::TILE / 4 : Split<LOGR>::TILE;
-    static constexpr int THREADS = NARROW ? kThreads / 4 : kThreads;
+// MODE 0 (wide): Split::TILE words, 256 threads, radix-8/16 units; MODE 1 (narrow): a
+// quarter of the tile and of the threads; MODE 2 (tiny): 1024 words, 256 threads, radix-4
+// units (four words per thread: four times the threads of the narrow tile for launches of
+// few limbs, at the price of more shared-memory rounds)
+template <int LOGR, int MODE> struct Tile {
+    static constexpr int WORDS = MODE == 0 ? Split<LOGR>::TILE : MODE == 1 ? Split<LOGR>::TILE / 4 : 1024;
+    static constexpr int THREADS = MODE == 1 ? kThreads / 4 : kThreads;
+    static constexpr int MIN_CTAS = MODE == 0 ? 3 : MODE == 1 ? 8 : 4;
 };
 
 // One group of W stages on a tile: forward stages LS0, LS0+1, ..; inverse LS0, LS0-1, ...
@@ -144,6 +149,25 @@ __device__ __forceinline__ void all_groups(uint64_t *s, uint32_t s_off, uint32_t
     __syncthreads();
 }
 
+// MODE 2: the stages in groups of two (radix-4 units), a last group of one if LOGR is odd
+template <int LOGR, bool FWD, bool PASSA, int TILE, bool RED, int DONE0, int DONE_STAGES = 0>
+__device__ __forceinline__ void tiny_groups(uint64_t *s, uint32_t s_off, uint32_t blk_base,
+                                            const uint64_t *tw, const uint64_t *tws, uint64_t q) {
+    if constexpr (DONE_STAGES < LOGR) {
+        constexpr int W = LOGR - DONE_STAGES >= 2 ? 2 : 1;
+        constexpr int LS0 = FWD ? DONE_STAGES : LOGR - 1 - DONE_STAGES;
+        stage_group<LOGR, W, LS0, FWD, PASSA, TILE, RED, DONE0, PASSA>(s, s_off, blk_base, tw, tws, q);
+        __syncthreads();
+        tiny_groups<LOGR, FWD, PASSA, TILE, RED, DONE0, DONE_STAGES + W>(s, s_off, blk_base, tw, tws, q);
+    }
+}
+template <int LOGR, bool FWD, bool PASSA, int TILE, bool RED, int DONE0, int MODE>
+__device__ __forceinline__ void pass_groups(uint64_t *s, uint32_t s_off, uint32_t blk_base,
+                                            const uint64_t *tw, const uint64_t *tws, uint64_t q) {
+    if constexpr (MODE == 2) tiny_groups<LOGR, FWD, PASSA, TILE, RED, DONE0>(s, s_off, blk_base, tw, tws, q);
+    else all_groups<LOGR, FWD, PASSA, TILE, RED, DONE0>(s, s_off, blk_base, tw, tws, q);
+}
+
 // Tile transfers in two phases -- all of a thread's global (or remote shared) loads issued
 // before its first shared store -- so each thread has TILE / THREADS requests in flight.
 // (in batches of 8 words, which keeps the register footprint of the wide tiles in budget)
@@ -190,9 +214,9 @@ __device__ __forceinline__ void load_twiddles(uint64_t *stw, const uint64_t *tw,
 }
 
 // Pass A: strided columns, stages 0..LOGR-1 (forward) or LOGR-1..0 (inverse, + N^-1).
-template <int LOGR, bool FWD, bool NARROW, int DONE0>
-__global__ void __launch_bounds__(Tile<LOGR, NARROW>::THREADS, NARROW ? 8 : 3) ntt_pass_a(PassArgs a) {
-    constexpr int TILE = Tile<LOGR, NARROW>::WORDS;
+template <int LOGR, bool FWD, int MODE, int DONE0>
+__global__ void __launch_bounds__(Tile<LOGR, MODE>::THREADS, Tile<LOGR, MODE>::MIN_CTAS) ntt_pass_a(PassArgs a) {
+    constexpr int TILE = Tile<LOGR, MODE>::WORDS;
     __shared__ uint64_t s[TILE];
     constexpr int R = 1 << LOGR;
     constexpr int C = TILE / R;
@@ -203,15 +227,15 @@ __global__ void __launch_bounds__(Tile<LOGR, NARROW>::THREADS, NARROW ? 8 : 3) n
     if (limb >= a.n_limbs || !a.map.resolve(limb, &pi)) return;
     const DevPrime P = a.primes[pi];
     uint64_t *g = a.data + a.map.offset(limb, a.n);
-    constexpr int THREADS = Tile<LOGR, NARROW>::THREADS;
+    constexpr int THREADS = Tile<LOGR, MODE>::THREADS;
     __shared__ uint64_t stw[2 * R];
     const uint32_t cols = a.n >> LOGR;
     const uint32_t c0 = tile * C;
     load_twiddles<LOGR, THREADS>(stw, a.tw + (size_t)pi * a.n, a.tw_sh + (size_t)pi * a.n);
     gather_tile<TILE, THREADS>(s, [&](int i) { return g[c0 + i % C + (size_t)(i / C) * cols]; });
     __syncthreads();
-    if (P.q < a.small_below) all_groups<LOGR, FWD, true, TILE, false, DONE0>(s, 0, 0, stw, stw + R, P.q);
-    else all_groups<LOGR, FWD, true, TILE, true, DONE0>(s, 0, 0, stw, stw + R, P.q);
+    if (P.q < a.small_below) pass_groups<LOGR, FWD, true, TILE, false, DONE0, MODE>(s, 0, 0, stw, stw + R, P.q);
+    else pass_groups<LOGR, FWD, true, TILE, true, DONE0, MODE>(s, 0, 0, stw, stw + R, P.q);
 #pragma unroll
     for (int k = 0; k < TILE / THREADS; k++) {
         const int i = threadIdx.x + k * THREADS;
@@ -226,9 +250,10 @@ __global__ void __launch_bounds__(Tile<LOGR, NARROW>::THREADS, NARROW ? 8 : 3) n
 }
 
 // Pass B: contiguous blocks of R words, stages s_off..s_off+LOGR-1.
-template <int LOGR, bool FWD, bool NARROW>
-__global__ void __launch_bounds__(Tile<LOGR, NARROW>::THREADS, NARROW ? 8 : 3) ntt_pass_b(PassArgs a, uint32_t s_off) {
-    constexpr int TILE = Tile<LOGR, NARROW>::WORDS;
+template <int LOGR, bool FWD, int MODE>
+__global__ void __launch_bounds__(Tile<LOGR, MODE>::THREADS, Tile<LOGR, MODE>::MIN_CTAS) ntt_pass_b(PassArgs a,
+                                                                                               uint32_t s_off) {
+    constexpr int TILE = Tile<LOGR, MODE>::WORDS;
     __shared__ uint64_t s[TILE];
     constexpr int R = 1 << LOGR;
     constexpr int S = TILE / R;
@@ -239,13 +264,13 @@ __global__ void __launch_bounds__(Tile<LOGR, NARROW>::THREADS, NARROW ? 8 : 3) n
     if (limb >= a.n_limbs || !a.map.resolve(limb, &pi)) return;
     const DevPrime P = a.primes[pi];
     uint64_t *g = a.data + a.map.offset(limb, a.n) + (size_t)tile * TILE;
-    constexpr int THREADS = Tile<LOGR, NARROW>::THREADS;
+    constexpr int THREADS = Tile<LOGR, MODE>::THREADS;
     load_rows<TILE, THREADS>(s, g);
     __syncthreads();
     const uint64_t *tw = a.tw + (size_t)pi * a.n, *tws = a.tw_sh + (size_t)pi * a.n;
     const bool small = P.q < a.small_below;
-    if (small) all_groups<LOGR, FWD, false, TILE, false, 0>(s, s_off, tile * S, tw, tws, P.q);
-    else all_groups<LOGR, FWD, false, TILE, true, 0>(s, s_off, tile * S, tw, tws, P.q);
+    if (small) pass_groups<LOGR, FWD, false, TILE, false, 0, MODE>(s, s_off, tile * S, tw, tws, P.q);
+    else pass_groups<LOGR, FWD, false, TILE, true, 0, MODE>(s, s_off, tile * S, tw, tws, P.q);
     const uint64_t q = P.q, two_q = 2 * q;
 #pragma unroll
     for (int k = 0; k < TILE / 2 / THREADS; k++) {
@@ -376,15 +401,15 @@ void launch_fused(const PassArgs &a, cudaStream_t st) {
 // a launch whose wide tiles would not give every SM two CTAs runs the narrow variant
 constexpr uint32_t kNarrowBelow = 2 * 152;
 
-template <int A, int B, bool NARROW>
+template <int A, int B, int MODE>
 void launch_fwd_t(const PassArgs &a, cudaStream_t st) {
-    ntt_pass_a<A, true, NARROW, 0><<<a.n_limbs * (a.n / Tile<A, NARROW>::WORDS), Tile<A, NARROW>::THREADS, 0, st>>>(a);
-    ntt_pass_b<B, true, NARROW><<<a.n_limbs * (a.n / Tile<B, NARROW>::WORDS), Tile<B, NARROW>::THREADS, 0, st>>>(a, A);
+    ntt_pass_a<A, true, MODE, 0><<<a.n_limbs * (a.n / Tile<A, MODE>::WORDS), Tile<A, MODE>::THREADS, 0, st>>>(a);
+    ntt_pass_b<B, true, MODE><<<a.n_limbs * (a.n / Tile<B, MODE>::WORDS), Tile<B, MODE>::THREADS, 0, st>>>(a, A);
 }
-template <int A, int B, bool NARROW>
+template <int A, int B, int MODE>
 void launch_inv_t(const PassArgs &a, cudaStream_t st) {
-    ntt_pass_b<B, false, NARROW><<<a.n_limbs * (a.n / Tile<B, NARROW>::WORDS), Tile<B, NARROW>::THREADS, 0, st>>>(a, A);
-    ntt_pass_a<A, false, NARROW, B><<<a.n_limbs * (a.n / Tile<A, NARROW>::WORDS), Tile<A, NARROW>::THREADS, 0, st>>>(a);
+    ntt_pass_b<B, false, MODE><<<a.n_limbs * (a.n / Tile<B, MODE>::WORDS), Tile<B, MODE>::THREADS, 0, st>>>(a, A);
+    ntt_pass_a<A, false, MODE, B><<<a.n_limbs * (a.n / Tile<A, MODE>::WORDS), Tile<A, MODE>::THREADS, 0, st>>>(a);
 }
 // variant of a launch of n_limbs limbs: the context's table (filled by the tuner) or the
 // default rule (narrow two-pass below two wide CTAs per SM, wide two-pass above)
@@ -404,16 +429,18 @@ template <int A, int B>
 void launch_fwd(const hear_context *ctx, const PassArgs &a, cudaStream_t st) {
     switch (pick(ctx, true, a.n_limbs, a.n_limbs * (a.n / Split<A>::TILE))) {
     case kNttFused: launch_fused<A, B, true>(a, st); break;
-    case kNttNarrow: launch_fwd_t<A, B, true>(a, st); break;
-    default: launch_fwd_t<A, B, false>(a, st);
+    case kNttNarrow: launch_fwd_t<A, B, 1>(a, st); break;
+    case kNttTiny: launch_fwd_t<A, B, 2>(a, st); break;
+    default: launch_fwd_t<A, B, 0>(a, st);
     }
 }
 template <int A, int B>
 void launch_inv(const hear_context *ctx, const PassArgs &a, cudaStream_t st) {
     switch (pick(ctx, false, a.n_limbs, a.n_limbs * (a.n / Split<A>::TILE))) {
     case kNttFused: launch_fused<A, B, false>(a, st); break;
-    case kNttNarrow: launch_inv_t<A, B, true>(a, st); break;
-    default: launch_inv_t<A, B, false>(a, st);
+    case kNttNarrow: launch_inv_t<A, B, 1>(a, st); break;
+    case kNttTiny: launch_inv_t<A, B, 2>(a, st); break;
+    default: launch_inv_t<A, B, 0>(a, st);
     }
 }
 
@@ -502,7 +529,7 @@ void ntt_tune(hear_context *ctx, uint32_t max_limbs, int iters, float *ms_out) {
                 const uint32_t nl = 1u << b;
                 float best = 0;
                 uint8_t best_v = kNttAuto;
-                for (uint8_t v = 0; v < 3; v++) {
+                for (uint8_t v = 0; v < kNttVariants; v++) {
                     ctx->ntt_force = v;
                     // timed as a replayed CUDA graph of `iters` back-to-back transforms, the
                     // way whole evaluations run
@@ -533,7 +560,7 @@ void ntt_tune(hear_context *ctx, uint32_t max_limbs, int iters, float *ms_out) {
                     cudaGraphExecDestroy(exec);
                     HEAR_CHECK_CUDA(le);
                     ms /= iters;
-                    if (ms_out) ms_out[((size_t)dir * kNttBuckets + b) * 3 + v] = ms;
+                    if (ms_out) ms_out[((size_t)dir * kNttBuckets + b) * kNttVariants + v] = ms;
                     // the one-launch form carries both passes' code: inside a whole
                     // evaluation it competes for the instruction cache with the other
                     // kernels, so it must win its isolated timing by a clear margin

@@ -609,13 +609,13 @@ def hear_launch_count():
 
 
 # ---------------------------------------------------------------- debug
-HEAR_NTT_WIDE, HEAR_NTT_NARROW, HEAR_NTT_FUSED = 0, 1, 2
+HEAR_NTT_WIDE, HEAR_NTT_NARROW, HEAR_NTT_FUSED, HEAR_NTT_TINY = 0, 1, 2, 3
 
 
 def hear_ntt_tune(ctx, max_limbs=512, iters=5):
-    """time the NTT launch variants; returns (choice uint8[2][16], ms float32[2][16][3])"""
+    """time the NTT launch variants; returns (choice uint8[2][16], ms float32[2][16][4])"""
     choice = np.zeros((2, 16), dtype=np.uint8)
-    ms = np.zeros((2, 16, 3), dtype=np.float32)
+    ms = np.zeros((2, 16, 4), dtype=np.float32)
     _check(lib.hear_ntt_tune(ctx, int(max_limbs), int(iters), _p(choice, ctypes.POINTER(ctypes.c_uint8)),
                              _p(ms, ctypes.POINTER(ctypes.c_float))))
     return choice, ms

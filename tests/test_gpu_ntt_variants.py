@@ -35,24 +35,24 @@ def test_variants_compute_the_same_transform(H, log_n, qb, pb):
             A, B = o.ntt_fwd(a[None], [pi]), o.ntt_fwd(b[None], [pi])
             C = np.array([int(x) * int(y) % q for x, y in zip(A[0], B[0])], dtype=np.uint64)
             want = o.ntt_inv(C[None], [pi])[0]
-            for v in (H.HEAR_NTT_WIDE, H.HEAR_NTT_NARROW, H.HEAR_NTT_FUSED):
+            for v in (H.HEAR_NTT_WIDE, H.HEAR_NTT_NARROW, H.HEAR_NTT_FUSED, H.HEAR_NTT_TINY):
                 H.hear_ntt_set_variant(ctx, v)
                 assert np.array_equal(H.hear_dbg_poly_mul(ctx, pi, a, b), want), (pi, v)
         for n_limbs in (1, 7, 300):
             limbs = np.stack([rng.integers(0, o.primes[i % len(o.primes)], n, dtype=np.uint64)
                               for i in range(n_limbs)])
-            for v in (H.HEAR_NTT_WIDE, H.HEAR_NTT_NARROW, H.HEAR_NTT_FUSED):
+            for v in (H.HEAR_NTT_WIDE, H.HEAR_NTT_NARROW, H.HEAR_NTT_FUSED, H.HEAR_NTT_TINY):
                 H.hear_ntt_set_variant(ctx, v)
                 assert np.array_equal(H.hear_dbg_ntt_roundtrip(ctx, limbs), limbs), (n_limbs, v)
         H.hear_ntt_set_variant(ctx, -1)
         choice, ms = H.hear_ntt_tune(ctx, 64, 2)
-        assert set(np.unique(choice)) <= {0, 1, 2}
+        assert set(np.unique(choice)) <= {0, 1, 2, 3}
         assert np.all(ms[:, :7, :] > 0)
     finally:
         H.hear_context_destroy(ctx)
 
 
-@pytest.mark.parametrize("variant", ["wide", "narrow", "fused", "tuned"])
+@pytest.mark.parametrize("variant", ["wide", "narrow", "fused", "tiny", "tuned"])
 def test_small_network_bit_exact_under_each_variant(H, variant):
     w = make_workload("small")
     ctx = H.hear_context_create(w.log_n, w.q_bits, w.p_bits, w.log2_scale, w.sigma, 0)
@@ -60,7 +60,7 @@ def test_small_network_bit_exact_under_each_variant(H, variant):
         if variant == "tuned":
             H.hear_ntt_tune(ctx, 128, 2)
         else:
-            H.hear_ntt_set_variant(ctx, {"wide": 0, "narrow": 1, "fused": 2}[variant])
+            H.hear_ntt_set_variant(ctx, {"wide": 0, "narrow": 1, "fused": 2, "tiny": 3}[variant])
         model = H.hear_model_create(ctx, w.layers, w.clip_dim)
         steps = H.hear_model_rotations(model)
         sk, pk, evk = H.hear_keygen(ctx, 301, steps)
