@@ -771,6 +771,30 @@ hear_status hear_cnn_evaluate(const hear_cnn *m, const hear_eval_keys *evk, size
     return guard(c, [&] {
         cudaStream_t st = stream_of(c, stream);
         const uint64_t ctw = 2ull * (first.level_in + 1) * c->n;
+        const uint64_t ctw_o = 2ull * (last.level_out + 1) * c->n;
+        if (use_graphs(c)) {
+            std::lock_guard<std::mutex> g(m->plan_mu);
+            hear_cnn::Plan *p = cnn_graph_plan(m, evk, op0, op1, C, in[0]->scale, st);
+            HEAR_CHECK_CUDA(cudaStreamWaitEvent(st, p->done, 0));
+            for (uint32_t s = 0; s < C; s++)
+                for (uint32_t i = 0; i < n_in; i++)
+                    HEAR_CHECK_CUDA(cudaMemcpyAsync(p->X.u64() + ((uint64_t)i * C + s) * ctw,
+                                                    in[(size_t)s * n_in + i]->d.p, ctw * 8,
+                                                    cudaMemcpyDeviceToDevice, st));
+            HEAR_CHECK_CUDA(cudaGraphLaunch(p->exec, st));
+            g_launches += p->launches;
+            std::vector<std::unique_ptr<hear_ciphertext>> res(n_out * (size_t)C);
+            for (uint32_t s = 0; s < C; s++)
+                for (uint32_t j = 0; j < n_out; j++) {
+                    auto &h = res[(size_t)s * n_out + j];
+                    h.reset(new_ct(c, last.level_out, 2, p->scale_out, st));
+                    HEAR_CHECK_CUDA(cudaMemcpyAsync(h->d.p, p->Y.u64() + ((uint64_t)j * C + s) * ctw_o, ctw_o * 8,
+                                                    cudaMemcpyDeviceToDevice, st));
+                }
+            HEAR_CHECK_CUDA(cudaEventRecord(p->done, st));
+            for (size_t k = 0; k < res.size(); k++) out[k] = res[k].release();
+            return;
+        }
         DevBuf x((size_t)n_in * C * ctw * 8, st);
         for (uint32_t s = 0; s < C; s++)
             for (uint32_t i = 0; i < n_in; i++)
@@ -778,7 +802,6 @@ hear_status hear_cnn_evaluate(const hear_cnn *m, const hear_eval_keys *evk, size
                                                 ctw * 8, cudaMemcpyDeviceToDevice, st));
         double so = 0;
         DevBuf y = cnn_evaluate(m, evk, op0, op1, x.u64(), C, in[0]->scale, &so, st);
-        const uint64_t ctw_o = 2ull * (last.level_out + 1) * c->n;
         std::vector<std::unique_ptr<hear_ciphertext>> res(n_out * (size_t)C);
         for (uint32_t s = 0; s < C; s++)
             for (uint32_t j = 0; j < n_out; j++) {

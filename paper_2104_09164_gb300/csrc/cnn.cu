@@ -561,6 +561,56 @@ DevBuf cnn_evaluate(const hear_cnn *m, const hear_eval_keys *evk, size_t op0, si
     return cur;
 }
 
+hear_cnn::Plan *cnn_graph_plan(const hear_cnn *m, const hear_eval_keys *evk, size_t op0, size_t op1, uint32_t C,
+                               double scale_in, cudaStream_t st) {
+    for (auto &p : m->plans)
+        if (p->evk_serial == evk->serial && p->op0 == op0 && p->op1 == op1 && p->C == C && p->scale_in == scale_in)
+            return p.get();
+    hear_context *c = m->ctx;
+    auto plan = std::make_unique<hear_cnn::Plan>();
+    plan->evk_serial = evk->serial;
+    plan->op0 = op0;
+    plan->op1 = op1;
+    plan->C = C;
+    plan->scale_in = scale_in;
+    const hear_cnn::Op &first = m->ops[op0], &last = m->ops[op1 - 1];
+    const uint64_t in_words = (uint64_t)first.n_in * C * 2 * (first.level_in + 1) * c->n;
+    const uint64_t out_words = (uint64_t)last.n_out * C * 2 * (last.level_out + 1) * c->n;
+    plan->X = DevBuf(in_words * 8, nullptr);
+    plan->Y = DevBuf(out_words * 8, nullptr);
+    HEAR_CHECK_CUDA(cudaMemsetAsync(plan->X.p, 0, in_words * 8, st));
+    {
+        double so;
+        DevBuf y = cnn_evaluate(m, evk, op0, op1, plan->X.u64(), C, scale_in, &so, st);
+    }
+    HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
+    cudaStream_t cs;
+    HEAR_CHECK_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    const uint64_t launches0 = g_launches.load();
+    cudaGraph_t graph = nullptr;
+    HEAR_CHECK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    try {
+        double so;
+        DevBuf y = cnn_evaluate(m, evk, op0, op1, plan->X.u64(), C, scale_in, &so, cs);
+        plan->scale_out = so;
+        HEAR_CHECK_CUDA(cudaMemcpyAsync(plan->Y.p, y.p, out_words * 8, cudaMemcpyDeviceToDevice, cs));
+    } catch (...) {
+        cudaStreamEndCapture(cs, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+        throw;
+    }
+    HEAR_CHECK_CUDA(cudaStreamEndCapture(cs, &graph));
+    plan->launches = g_launches.load() - launches0;
+    cudaError_t e = cudaGraphInstantiate(&plan->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    HEAR_CHECK_CUDA(e);
+    HEAR_CHECK_CUDA(cudaEventCreateWithFlags(&plan->done, cudaEventDisableTiming));
+    m->plans.push_back(std::move(plan));
+    return m->plans.back().get();
+}
+
 std::vector<double> cnn_pack_input(const hear_cnn *m, const double *x) {
     const uint32_t S = m->ctx->n / 2, dist = m->in_dist, cbar = S / dist;
     const uint32_t n_ct = m->in_kind == 1 ? 1 : m->in_c / cbar;
@@ -578,3 +628,8 @@ std::vector<double> cnn_pack_input(const hear_cnn *m, const double *x) {
 }
 
 }  // namespace hear
+
+hear_cnn::Plan::~Plan() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (done) cudaEventDestroy(done);
+}

@@ -29,6 +29,21 @@ struct hear_cnn {
         hear::DevBuf A;
         std::vector<double> B, C, bias;            // [n_in][N/2] / [N/2]
     };
+    // CUDA graph of operations [op0, op1) on C samples with given keys and input scale,
+    // replayed from a fixed input / output workspace
+    struct Plan {
+        uint64_t evk_serial = 0;
+        size_t op0 = 0, op1 = 0;
+        uint32_t C = 0;
+        double scale_in = 0, scale_out = 0;
+        hear::DevBuf X, Y;
+        cudaGraphExec_t exec = nullptr;
+        cudaEvent_t done = nullptr;
+        uint64_t launches = 0;
+        ~Plan();
+    };
+    mutable std::mutex plan_mu;
+    mutable std::vector<std::unique_ptr<Plan>> plans;
     hear_context *ctx = nullptr;
     std::vector<Op> ops;
     std::vector<uint32_t> op_layer;                // layer each operation comes from
@@ -49,6 +64,11 @@ double cnn_scale_after(const hear_cnn *m, size_t op0, size_t op1, double scale);
 // run ops [op0, op1) on x [n_in(op0)][C][2][L1][N]; returns [n_out(op1-1)][C][2][L1'][N]
 DevBuf cnn_evaluate(const hear_cnn *m, const hear_eval_keys *evk, size_t op0, size_t op1, const uint64_t *x,
                     uint32_t C, double scale_in, double *scale_out, cudaStream_t st);
+// graph plan for (evk, op0, op1, C, scale_in): one direct warm-up run (builds every table the
+// capture needs), then stream capture; the caller fills plan->X, launches plan->exec and
+// reads plan->Y.  Caller holds m->plan_mu.
+hear_cnn::Plan *cnn_graph_plan(const hear_cnn *m, const hear_eval_keys *evk, size_t op0, size_t op1, uint32_t C,
+                               double scale_in, cudaStream_t st);
 // slot vector of the input ciphertext(s) of one sample: [n_in][N/2]
 std::vector<double> cnn_pack_input(const hear_cnn *m, const double *x);
 
