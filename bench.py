@@ -611,6 +611,9 @@ def main_gpu(a):
             "stages_ms_per_step": {k: v[1] / psteps for k, v in sorted(stages.items(), key=lambda kv: -kv[1][1])},
             "clocks": clocks, "gpu_launches": launches,
         }
+        # the NTT launch-variant table this run used (pin it with HEAR_NTT_TABLE to profile
+        # the same kernels)
+        result["config"]["ntt_table"] = H.hear_ntt_get_table(S.ctx)
     if result is not None and not a.no_served and a.workload == "small" and a.clips is None and dist.world == 1:
         sweep = run_served(H, S, [float(x) for x in a.rates.split(",")])
         result["served"] = {"workload": "small network, Poisson arrivals, 1-8 clips per request, "

@@ -411,6 +411,12 @@ uint64_t hear_launch_count(void);
 #define HEAR_NTT_TINY 3
 hear_status hear_ntt_tune(hear_context *ctx, uint32_t max_limbs, int iters, uint8_t *choice_out, float *ms_out);
 hear_status hear_ntt_set_variant(hear_context *ctx, int variant);
+/* the variant table uint8_t[2][16] ([forward, inverse][bucket]); setting it pins the choice
+ * (e.g. to profile a run with the table another run tuned).  The environment variable
+ * HEAR_NTT_TABLE (32 digits, forward buckets then inverse) pins it at context creation
+ * instead of tuning. */
+hear_status hear_ntt_get_table(const hear_context *ctx, uint8_t *table);
+hear_status hear_ntt_set_table(hear_context *ctx, const uint8_t *table);
 
 /* ---- debug: ring products through the NTT kernels (tests only) ---- */
 /* out = a * b in Z_q[X]/(X^N+1) for limb prime index `prime` (0..n_q+n_p-1), coefficient domain */

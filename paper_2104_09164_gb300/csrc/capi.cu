@@ -99,8 +99,18 @@ hear_status hear_context_create(const hear_params_desc *params, int cuda_device,
         build_context(c, params, cuda_device);
         // pick the NTT launch variant per launch size by timing them (HEAR_NTT_TUNE=0 keeps
         // the fixed rule); every variant computes the same residues
+        const char *t = std::getenv("HEAR_NTT_TABLE");
         const char *v = std::getenv("HEAR_NTT_TUNE");
-        if (!(v && *v == '0')) ntt_tune(c, 1024, 8, nullptr);
+        if (t && *t) {
+            // a pinned table: 32 digits, forward buckets then inverse buckets
+            HEAR_REQUIRE(std::strlen(t) == 2 * (size_t)kNttBuckets, HEAR_E_INVAL, "HEAR_NTT_TABLE needs 32 digits");
+            for (int i = 0; i < 2 * kNttBuckets; i++) {
+                HEAR_REQUIRE(t[i] >= '0' && t[i] < '0' + kNttVariants, HEAR_E_INVAL, "bad HEAR_NTT_TABLE digit");
+                c->ntt_choice[i / kNttBuckets][i % kNttBuckets] = (uint8_t)(t[i] - '0');
+            }
+        } else if (!(v && *v == '0')) {
+            ntt_tune(c, 1024, 8, nullptr);
+        }
     });
     if (s != HEAR_OK) {
         delete c;
@@ -643,6 +653,20 @@ hear_status hear_ntt_tune(hear_context *ctx, uint32_t max_limbs, int iters, uint
         ntt_tune(ctx, max_limbs, iters, ms_out);
         if (choice_out) std::memcpy(choice_out, ctx->ntt_choice, sizeof(ctx->ntt_choice));
     });
+}
+
+hear_status hear_ntt_get_table(const hear_context *ctx, uint8_t *table) {
+    if (!ctx || !table) return fail(HEAR_E_INVAL, "null argument");
+    std::memcpy(table, ctx->ntt_choice, sizeof(ctx->ntt_choice));
+    return HEAR_OK;
+}
+
+hear_status hear_ntt_set_table(hear_context *ctx, const uint8_t *table) {
+    if (!ctx || !table) return fail(HEAR_E_INVAL, "null argument");
+    for (int i = 0; i < 2 * kNttBuckets; i++)
+        if (table[i] >= kNttVariants) return fail(HEAR_E_INVAL, "bad variant in table");
+    std::memcpy(ctx->ntt_choice, table, sizeof(ctx->ntt_choice));
+    return HEAR_OK;
 }
 
 hear_status hear_ntt_set_variant(hear_context *ctx, int variant) {

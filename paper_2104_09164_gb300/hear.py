@@ -163,6 +163,8 @@ def _load():
         "hear_ntt_tune": (st, [_vp, ctypes.c_uint32, ctypes.c_int, ctypes.POINTER(ctypes.c_uint8),
                                ctypes.POINTER(ctypes.c_float)]),
         "hear_ntt_set_variant": (st, [_vp, ctypes.c_int]),
+        "hear_ntt_get_table": (st, [_vp, ctypes.POINTER(ctypes.c_uint8)]),
+        "hear_ntt_set_table": (st, [_vp, ctypes.POINTER(ctypes.c_uint8)]),
         "hear_dbg_poly_mul": (st, [_vp, ctypes.c_uint32, _u64p, _u64p, _u64p]),
         "hear_dbg_ntt_roundtrip": (st, [_vp, _u64p, ctypes.c_size_t]),
         "hear_dbg_ntt_time": (st, [_vp, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
@@ -619,6 +621,18 @@ def hear_ntt_tune(ctx, max_limbs=512, iters=5):
     _check(lib.hear_ntt_tune(ctx, int(max_limbs), int(iters), _p(choice, ctypes.POINTER(ctypes.c_uint8)),
                              _p(ms, ctypes.POINTER(ctypes.c_float))))
     return choice, ms
+
+
+def hear_ntt_get_table(ctx):
+    """-> the variant table as a 32-character string (forward buckets, then inverse)"""
+    t = np.zeros(32, dtype=np.uint8)
+    _check(lib.hear_ntt_get_table(ctx, _p(t, ctypes.POINTER(ctypes.c_uint8))))
+    return "".join(str(int(x)) for x in t)
+
+
+def hear_ntt_set_table(ctx, table):
+    t = np.array([int(ch) for ch in table], dtype=np.uint8)
+    _check(lib.hear_ntt_set_table(ctx, _p(t, ctypes.POINTER(ctypes.c_uint8))))
 
 
 def hear_ntt_set_variant(ctx, variant):
