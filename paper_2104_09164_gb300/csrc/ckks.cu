@@ -375,8 +375,7 @@ void rotsum(hear_context *c, const hear_eval_keys *evk, uint32_t level, uint32_t
         const uint32_t R = (uint32_t)rots.size();
         DevBuf r((size_t)R * batch * 8, st);
         rotate_hoisted(c, level, n_ct, x, rots, r.u64(), st);
-        if (R > 1) sum_ct(c, level, 2 * n_ct, r.u64(), batch, R, r.u64(), st);
-        add_ct(c, level, 2 * n_ct, x, r.u64(), x, st);
+        sum_add_ct(c, level, 2 * n_ct, r.u64(), batch, R, x, x, st);
     }
 }
 
@@ -407,8 +406,7 @@ DevBuf eval_fc(const hear_model *m, const hear_model::Fc &fc, const hear_eval_ke
         }
         DevBuf R((size_t)(n2 - 1) * batch * 8, st);
         rotate_each(c, level, n2 - 1, n_ct, G.u64() + batch, gr, R.u64(), st);
-        sum_ct(c, level, 2 * n_ct, R.u64(), batch, n2 - 1, R.u64(), st);
-        add_ct(c, level, 2 * n_ct, G.u64(), R.u64(), G.u64(), st);
+        sum_add_ct(c, level, 2 * n_ct, R.u64(), batch, n2 - 1, G.u64(), G.u64(), st);
     }
     // one rescale (lazy rescaling), then rotate-and-sum over the d_in / d_out blocks
     DevBuf Y((size_t)n_ct * 2 * level * n * 8, st), tmp((size_t)n_ct * 2 * level * n * 8, st);

@@ -484,8 +484,7 @@ DevBuf cnn_evaluate(const hear_cnn *m, const hear_eval_keys *evk, size_t op0, si
                 DevBuf R((size_t)(ng - 1) * batch_out * 8, st);
                 rotate_each(c, level, (ng - 1) * op.n_out, C, G.u64() + batch_out, rots_for(c, evk, gsteps), R.u64(),
                             st);
-                if (ng > 2) sum_ct(c, level, 2 * op.n_out * C, R.u64(), batch_out, ng - 1, R.u64(), st);
-                add_ct(c, level, 2 * op.n_out * C, G.u64(), R.u64(), G.u64(), st);
+                sum_add_ct(c, level, 2 * op.n_out * C, R.u64(), batch_out, ng - 1, G.u64(), G.u64(), st);
             }
             next = DevBuf((size_t)op.n_out * C * 2 * level * n * 8, st);
             DevBuf tmp((size_t)op.n_out * C * 2 * level * n * 8, st);
@@ -511,8 +510,7 @@ DevBuf cnn_evaluate(const hear_cnn *m, const hear_eval_keys *evk, size_t op0, si
                     continue;
                 }
                 rotate_each(c, level - 1, n_p - 1, C, yt + C * ctw1, rots_for(c, evk, back), R.u64(), st);
-                if (n_p > 2) sum_ct(c, level - 1, 2 * C, R.u64(), C * ctw1, n_p - 1, R.u64(), st);
-                add_ct(c, level - 1, 2 * C, yt, R.u64(), ot, st);
+                sum_add_ct(c, level - 1, 2 * C, R.u64(), C * ctw1, n_p - 1, yt, ot, st);
             }
             const double ql = (double)c->primes[level];
             scale = scale * ql / ql;

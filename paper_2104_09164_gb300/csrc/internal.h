@@ -210,6 +210,10 @@ inline LimbMap map_qp(uint32_t level, uint32_t n_q, uint32_t K) {
 
 void ntt_forward(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, LimbMap map, cudaStream_t s);
 void ntt_inverse(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, LimbMap map, cudaStream_t s);
+// inverse NTT from src (limb b of group g at src + g * src_gstride + b' * N) into data (the
+// layout of `map`, contiguous groups); src is left unchanged
+void ntt_inverse_from(const hear_context *ctx, const uint64_t *src, uint64_t src_gstride, uint64_t *data,
+                      uint32_t n_limbs, LimbMap map, cudaStream_t s);
 // fill ctx->ntt_choice by timing the launch variants (ms_out: [2][kNttBuckets][3] or null)
 // ms_out: [2][kNttBuckets][kNttVariants] or null
 void ntt_tune(hear_context *ctx, uint32_t max_limbs, int iters, float *ms_out);

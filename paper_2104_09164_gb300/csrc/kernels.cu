@@ -179,12 +179,13 @@ __global__ void k_add(const uint64_t *a, const uint64_t *b, uint64_t *out, uint3
 }
 
 // out = a_0 + a_1 + ... + a_{cnt-1} (batches at stride `stride` words); y = limb, z = polynomial
-__global__ void k_sum(const uint64_t *a, uint64_t stride, uint32_t cnt, uint64_t *out, uint32_t L1,
-                      const DevPrime *P, uint32_t n) {
+// (base = null) or out = base + a_0 + ... + a_{cnt-1}
+__global__ void k_sum(const uint64_t *a, uint64_t stride, uint32_t cnt, const uint64_t *base, uint64_t *out,
+                      uint32_t L1, const DevPrime *P, uint32_t n) {
     uint64_t i = ((uint64_t)blockIdx.z * L1 + blockIdx.y) * n + COEF();
     const uint64_t q = P[blockIdx.y].q;
-    uint64_t s = a[i];
-    for (uint32_t j = 1; j < cnt; j++) s = add_mod(s, a[j * stride + i], q);
+    uint64_t s = base ? base[i] : 0;
+    for (uint32_t j = 0; j < cnt; j++) s = add_mod(s, a[j * stride + i], q);
     out[i] = s;
 }
 
@@ -575,8 +576,15 @@ void sum_ct(const hear_context *c, uint32_t level, uint32_t n_polys_total, const
             uint32_t cnt, uint64_t *out, cudaStream_t st) {
     check_yz(level + 1, n_polys_total);
     LAUNCH3(k_sum, grid3(c->n, level + 1, n_polys_total), kBlock, st,
-            8.0 * (cnt + 1) * n_polys_total * (level + 1) * c->n, a, stride, cnt, out, level + 1, c->dev_primes(),
-            c->n);
+            8.0 * (cnt + 1) * n_polys_total * (level + 1) * c->n, a, stride, cnt, (const uint64_t *)nullptr, out,
+            level + 1, c->dev_primes(), c->n);
+}
+void sum_add_ct(const hear_context *c, uint32_t level, uint32_t n_polys_total, const uint64_t *a, uint64_t stride,
+                uint32_t cnt, const uint64_t *base, uint64_t *out, cudaStream_t st) {
+    check_yz(level + 1, n_polys_total);
+    LAUNCH3(k_sum, grid3(c->n, level + 1, n_polys_total), kBlock, st,
+            8.0 * (cnt + 2) * n_polys_total * (level + 1) * c->n, a, stride, cnt, base, out, level + 1,
+            c->dev_primes(), c->n);
 }
 void tensor_ct(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *a, const uint64_t *b,
                uint64_t *out3, cudaStream_t st) {
@@ -627,10 +635,8 @@ void modup(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t 
     const uint32_t L1 = level + 1, W = L1 + c->K, dnum = c->dnum(level);
     const LevelConsts &lc = *c->levels[level];
     HEAR_REQUIRE(c->alpha <= 4, HEAR_E_UNSUPPORTED, "at most 4 special primes");
-    // coefficient-domain copy of the digit limbs
-    HEAR_CHECK_CUDA(cudaMemcpy2DAsync(tmp, (size_t)L1 * c->n * 8, c1, c1_stride * 8, (size_t)L1 * c->n * 8, n_ct,
-                                      cudaMemcpyDeviceToDevice, st));
-    ntt_inverse(c, tmp, n_ct * L1, map_q(level, c->n_q), st);
+    // coefficient-domain copy of the digit limbs (the inverse NTT reads c1 in place of a copy)
+    ntt_inverse_from(c, c1, c1_stride, tmp, n_ct * L1, map_q(level, c->n_q), st);
     check_yz(dnum, n_ct);
     LAUNCH3(k_modup_conv, grid3(c->n, dnum, n_ct), kBlock, st, 8.0 * n_ct * ((double)L1 + (double)dnum * W) * c->n,
             c1, c1_stride, tmp, ext, L1, W, dnum, c->alpha, c->n_q, lc.d.u64() + lc.off_qhat_inv,

@@ -77,6 +77,9 @@ void moddown(const hear_context *c, uint32_t level, uint32_t n_ct, uint64_t *acc
 // out = sum of cnt batches a + j*stride (n_polys_total polynomials at level)
 void sum_ct(const hear_context *c, uint32_t level, uint32_t n_polys_total, const uint64_t *a, uint64_t stride,
             uint32_t cnt, uint64_t *out, cudaStream_t st);
+// out = base + sum of cnt batches a + j*stride (out may alias base)
+void sum_add_ct(const hear_context *c, uint32_t level, uint32_t n_polys_total, const uint64_t *a, uint64_t stride,
+                uint32_t cnt, const uint64_t *base, uint64_t *out, cudaStream_t st);
 // out = a (.) b_mont over n_limbs limbs (Montgomery product: a * b)
 void pointwise_mont(const hear_context *c, uint32_t n_limbs, LimbMap m, const uint64_t *a, const uint64_t *b_mont,
                     uint64_t *out, cudaStream_t st);

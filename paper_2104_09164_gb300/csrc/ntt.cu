@@ -29,6 +29,10 @@ constexpr int kThreads = 256;
 struct PassArgs {
     uint64_t small_below;    // primes below this skip the per-stage corrections
     uint64_t *data;
+    // inverse only: the first pass reads limb b from src + (b / per_group) * src_gstride +
+    // (b % per_group) * N instead of from data (out-of-place start), null = in place
+    const uint64_t *src;
+    uint64_t src_gstride;
     uint32_t n_limbs;
     uint32_t log_n;
     LimbMap map;
@@ -265,7 +269,11 @@ __global__ void __launch_bounds__(Tile<LOGR, MODE>::THREADS, Tile<LOGR, MODE>::M
     const DevPrime P = a.primes[pi];
     uint64_t *g = a.data + a.map.offset(limb, a.n) + (size_t)tile * TILE;
     constexpr int THREADS = Tile<LOGR, MODE>::THREADS;
-    load_rows<TILE, THREADS>(s, g);
+    const uint64_t *gin = g;
+    if (!FWD && a.src)
+        gin = a.src + (uint64_t)(limb / a.map.per_group) * a.src_gstride + (uint64_t)(limb % a.map.per_group) * a.n +
+              (size_t)tile * TILE;
+    load_rows<TILE, THREADS>(s, gin);
     __syncthreads();
     const uint64_t *tw = a.tw + (size_t)pi * a.n, *tws = a.tw_sh + (size_t)pi * a.n;
     const bool small = P.q < a.small_below;
@@ -360,7 +368,10 @@ ntt_fused(PassArgs a) {
             reinterpret_cast<ulonglong2 *>(out)[i] = v;
         }
     } else {
-        load_rows<TILE, THREADS>(sB, g + (size_t)r * TILE);
+        const uint64_t *gin = a.src ? a.src + (uint64_t)(limb / a.map.per_group) * a.src_gstride +
+                                          (uint64_t)(limb % a.map.per_group) * a.n
+                                    : g;
+        load_rows<TILE, THREADS>(sB, gin + (size_t)r * TILE);
         __syncthreads();
         if (small) all_groups<LB, false, false, TILE, false, 0>(sB, LA, r * SB, tw, tws, q);
         else all_groups<LB, false, false, TILE, true, 0>(sB, LA, r * SB, tw, tws, q);
@@ -459,6 +470,8 @@ PassArgs make_args(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, Li
     // forward: values stay below (1 + 2 logN) q < 2^64 for q < 2^58; inverse: below
     // 2^(logN+1) q < 2^64 for q < 2^(63 - logN)
     a.small_below = fwd ? (1ull << 58) : (1ull << (63 - ctx->log_n));
+    a.src = nullptr;
+    a.src_gstride = 0;
     return a;
 }
 
@@ -489,9 +502,17 @@ void ntt_forward(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, Limb
 }
 
 void ntt_inverse(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, LimbMap map, cudaStream_t s) {
+    ntt_inverse_from(ctx, nullptr, 0, data, n_limbs, map, s);
+}
+
+void ntt_inverse_from(const hear_context *ctx, const uint64_t *src, uint64_t src_gstride, uint64_t *data,
+                      uint32_t n_limbs, LimbMap map, cudaStream_t s) {
     if (n_limbs == 0) return;
+    HEAR_REQUIRE(!src || map.group_stride == 0, HEAR_E_INVAL, "out-of-place NTT needs contiguous groups");
     ProfScope ps(ctx, "ntt_inv", s, ntt_bytes(ctx, n_limbs, map), launches_of(ctx, false, n_limbs));
     PassArgs a = make_args(ctx, data, n_limbs, map, false);
+    a.src = src;
+    a.src_gstride = src_gstride;
     switch (ctx->log_n) {
     case 11: launch_inv<6, 5>(ctx, a, s); break;
     case 12: launch_inv<6, 6>(ctx, a, s); break;

@@ -106,3 +106,53 @@ def test_admission_respects_the_hbm_budget(setup):
         assert e.value.code == -2
     finally:
         H.hear_server_destroy(srv)
+
+
+def test_two_networks_served_together_equal_alone():
+    """small (N = 2^14) and large (N = 2^15) requests interleaved from one submitter into two
+    servers running at once on one GPU: every result equals its request evaluated alone"""
+    from paper_2104_09164_gb300 import hear as H
+    rng = np.random.default_rng(91)
+    nets = []
+    for name, n_clips in (("small", None), ("large", 8)):
+        w = make_workload(name, n_clips)
+        ctx = H.hear_context_create(w.log_n, w.q_bits, w.p_bits, w.log2_scale, w.sigma, 0)
+        model = H.hear_model_create(ctx, w.layers, w.clip_dim)
+        sk, pk, evk = H.hear_keygen(ctx, 301, H.hear_model_rotations(model))
+        k = w.slots // w.clip_dim
+        reqs = []
+        for i, n_ct in enumerate([1, 2, 1, 3] if name == "small" else [1, 1, 2]):
+            words = []
+            for j in range(n_ct):
+                x = rng.uniform(-1, 1, (k, w.clip_dim))
+                ct = H.hear_encrypt_clips(ctx, pk, x, 700 + i, j)
+                words.append(H.hear_ciphertext_export(ct).reshape(-1))
+                H.hear_ciphertext_destroy(ct)
+            reqs.append((n_ct, np.concatenate(words)))
+        scale = 2.0 ** w.log2_scale
+        alone = [H.hear_evaluate_host(model, evk, words, n_ct, scale)[0] for n_ct, words in reqs]
+        srv = H.hear_server_create(model, evk, max_batch=4, n_slots=2, hbm_budget_bytes=32 << 30)
+        nets.append(dict(H=H, ctx=ctx, model=model, keys=(sk, pk, evk), reqs=reqs, alone=alone, srv=srv,
+                         scale=scale, out_words=alone[0].size // reqs[0][0]))
+    try:
+        order = [(0, i) for i in range(len(nets[0]["reqs"]))] + [(1, i) for i in range(len(nets[1]["reqs"]))]
+        rng.shuffle(order)
+        ids = {}
+        for ni, i in order:
+            n = nets[ni]
+            n_ct, words = n["reqs"][i]
+            ids[(ni, i)] = H.hear_server_submit(n["srv"], words, n_ct, n_ct, n["scale"])
+        for ni, n in enumerate(nets):
+            mine = [(ids[(ni, i)], n["reqs"][i][0]) for i in range(len(n["reqs"]))]
+            res = _wait(H, n["srv"], mine, n["out_words"])
+            for i, (rid, _) in enumerate(mine):
+                assert np.array_equal(res[rid], n["alone"][i]), (ni, i)
+    finally:
+        for n in nets:
+            H.hear_server_destroy(n["srv"])
+            H.hear_model_destroy(n["model"])
+            sk, pk, evk = n["keys"]
+            H.hear_eval_keys_destroy(evk)
+            H.hear_public_key_destroy(pk)
+            H.hear_secret_key_destroy(sk)
+            H.hear_context_destroy(n["ctx"])
