@@ -215,13 +215,37 @@ __global__ void k_automorphism(const uint64_t *in, uint64_t *out, uint32_t n_lim
 }
 
 // lazily accumulate x*y into acc keeping acc.hi < q (so the final Montgomery reduce is valid)
+__device__ __forceinline__ void mac_raw(u128 &acc, uint64_t x, uint64_t y);
 __device__ __forceinline__ void mac_lazy(u128 &acc, uint64_t x, uint64_t y, uint64_t q) {
-    add_to(acc, mul_wide(x, y));
+    mac_raw(acc, x, y);
     if (acc.hi >= q) acc.hi -= q;
 }
 // accumulate without the check: up to 8 products of residues below q < 2^61 keep acc.hi
 // below q + 8 q^2 / 2^64 < 2q; fold() then restores acc.hi < q
-__device__ __forceinline__ void mac_raw(u128 &acc, uint64_t x, uint64_t y) { add_to(acc, mul_wide(x, y)); }
+// acc += x * y as one carry chain over 32-bit halves (x = x1 2^32 + x0, y likewise): the
+// partial products x0 y0 and x1 y1 land on words 0-1 and 2-3, x0 y1 and x1 y0 on words 1-2,
+// each chain propagating its carry to word 3 -- ten multiply-adds for the 128-bit sum
+__device__ __forceinline__ void mac_raw(u128 &acc, uint64_t x, uint64_t y) {
+    uint32_t a0, a1, a2, a3, x0, x1, y0, y1;
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(a0), "=r"(a1) : "l"(acc.lo));
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(a2), "=r"(a3) : "l"(acc.hi));
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(x0), "=r"(x1) : "l"(x));
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(y0), "=r"(y1) : "l"(y));
+    asm("mad.lo.cc.u32 %0, %4, %6, %0;\n\t"
+        "madc.hi.cc.u32 %1, %4, %6, %1;\n\t"
+        "madc.lo.cc.u32 %2, %5, %7, %2;\n\t"
+        "madc.hi.u32 %3, %5, %7, %3;\n\t"
+        "mad.lo.cc.u32 %1, %4, %7, %1;\n\t"
+        "madc.hi.cc.u32 %2, %4, %7, %2;\n\t"
+        "addc.u32 %3, %3, 0;\n\t"
+        "mad.lo.cc.u32 %1, %5, %6, %1;\n\t"
+        "madc.hi.cc.u32 %2, %5, %6, %2;\n\t"
+        "addc.u32 %3, %3, 0;"
+        : "+r"(a0), "+r"(a1), "+r"(a2), "+r"(a3)
+        : "r"(x0), "r"(x1), "r"(y0), "r"(y1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(acc.lo) : "r"(a0), "r"(a1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(acc.hi) : "r"(a2), "r"(a3));
+}
 __device__ __forceinline__ void fold(u128 &acc, uint64_t q) {
     if (acc.hi >= q) acc.hi -= q;
 }
