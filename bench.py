@@ -640,7 +640,11 @@ def main_gpu(a):
                                  "unit": UNIT, "ms_per_step": tms / bsteps, "steps": bsteps,
                                  "p50_ms": blat[len(blat) // 2], "gpu_launches": bl, "clocks": bclk,
                                  "stages_ms_per_step": {k: v[1] / bps for k, v in
-                                                        sorted(bst.items(), key=lambda kv: -kv[1][1])[:8]}}
+                                                        sorted(bst.items(), key=lambda kv: -kv[1][1])[:8]},
+                                 # algorithmic bytes / stage time (HBM roofline of each stage)
+                                 "stages_algorithmic_gbs": {k: v[2] / (v[1] / 1e3) / 1e9 for k, v in
+                                                            sorted(bst.items(), key=lambda kv: -kv[1][1])[:8]
+                                                            if v[1] > 0}}
             result["batched"]["vs_plain"] = result["batched"]["value"] / result["value"]
         SL.close()
     else:
