@@ -649,6 +649,22 @@ def main_gpu(a):
         SL.close()
     else:
         S.close()
+    if result is not None and not a.no_batched and a.workload == "small" and a.clips is None and dist.world == 1:
+        # the same small network batched: clips packed 4 per ciphertext, many ciphertexts per
+        # launch (one CUDA-graph replay per step), against the plain one-clip-per-launch path
+        rows = []
+        for n_clips in (128, 512):
+            wb = make_workload("small", n_clips)
+            SB = Setup(H, wb, stream, device)
+            bsteps = 5
+            tms, blat, bl, bclk = run_gpu(SB, bsteps, 2, dist, torch, stream, device)
+            v = bsteps * SB.clips_per_step / (tms / 1e3)
+            rows.append({"clips": n_clips, "ciphertexts": wb.n_ct, "value": v, "unit": UNIT,
+                         "ms_per_step": tms / bsteps, "p50_ms": blat[len(blat) // 2], "gpu_launches": bl,
+                         "clocks": bclk, "vs_plain": v / result["value"]})
+            SB.close()
+        result["batched_small"] = {"workload": "small network (as the plain path), batches of 128 / 512 clips "
+                                               "in 32 / 128 ciphertexts per launch", "rows": rows}
     if result is not None and not a.no_min_level and a.workload == "small" and a.clips is None and dist.world == 1:
         # minimal start level: inputs dropped to the depth of the network (3 of 7 levels for
         # the small network, 5 of 14 for the large one); the same networks and parameters
