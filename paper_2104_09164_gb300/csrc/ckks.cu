@@ -241,7 +241,7 @@ void rotate_hoisted(hear_context *c, uint32_t level, uint32_t n_ct, const uint64
         acc((size_t)R * n_ct * 2 * W * n * 8, st);
     modup(c, level, n_ct, x + plane, ctw, ext.u64(), tmp.u64(), st);
     JobTable jobs = make_jobs(c, rots, st);
-    ks_inner(c, level, R, n_ct, ext.u64(), false, jobs.keys(), jobs.ginv(), acc.u64(), st);
+    ks_inner(c, level, R, n_ct, ext.u64(), false, jobs.keys(), jobs.ginv(), acc.u64(), x + plane, ctw, st);
     moddown(c, level, R * n_ct, acc.u64(), out, x, ctw, 1u, true, jobs.gal(), n_ct, tmp.u64(), st);
 }
 
@@ -253,7 +253,7 @@ void rotate_each(hear_context *c, uint32_t level, uint32_t R, uint32_t C, const 
         acc((size_t)n_ct * 2 * W * n * 8, st);
     modup(c, level, n_ct, x + plane, ctw, ext.u64(), tmp.u64(), st);
     JobTable jobs = make_jobs(c, rots, st);
-    ks_inner(c, level, R, C, ext.u64(), true, jobs.keys(), jobs.ginv(), acc.u64(), st);
+    ks_inner(c, level, R, C, ext.u64(), true, jobs.keys(), jobs.ginv(), acc.u64(), x + plane, ctw, st);
     moddown(c, level, n_ct, acc.u64(), out, x, ctw, 1u, false, jobs.gal(), C, tmp.u64(), st);
 }
 
@@ -267,7 +267,8 @@ void mul_relin(hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *a
         acc((size_t)n_ct * 2 * W * n * 8, st);
     modup(c, level, n_ct, d3.u64() + 2 * plane, 3 * plane, ext.u64(), tmp.u64(), st);
     JobTable jobs = make_jobs(c, {Rot{relin_key, 1u}}, st);
-    ks_inner(c, level, 1, n_ct, ext.u64(), false, jobs.keys(), jobs.ginv(), acc.u64(), st);
+    ks_inner(c, level, 1, n_ct, ext.u64(), false, jobs.keys(), jobs.ginv(), acc.u64(), d3.u64() + 2 * plane,
+             3 * plane, st);
     moddown(c, level, n_ct, acc.u64(), out, d3.u64(), 3 * plane, 3u, false, nullptr, 1, tmp.u64(), st);
 }
 

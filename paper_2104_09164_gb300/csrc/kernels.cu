@@ -366,10 +366,13 @@ __global__ void k_modup_conv(const uint64_t *c1, uint64_t c1_stride, const uint6
 // sum_j sigma_{g_r}(ext_j) (.) key_j (the automorphism applied to the extended digits).
 // The 2*dnum key words of a coefficient are loaded once and reused for all C ciphertexts.
 // y = limb t of Q_l u P.
-template <int MAXD>
+// OWN (one-limb digits): digit j's own limb t = j is read from own + ct * own_stride (the
+// input's c1 in the NTT domain) instead of ext.
+template <int MAXD, bool OWN>
 __global__ void __launch_bounds__(256, 3) k_ks_inner(const uint64_t *ext, int ext_per_job, const uint64_t *const *keys, const uint32_t *ginv,
                            uint64_t *out, uint32_t C, uint32_t L1, uint32_t W, uint32_t dnum, uint32_t n_q,
-                           uint32_t nqp, uint32_t log_n, const DevPrime *P) {
+                           uint32_t nqp, uint32_t log_n, const DevPrime *P, const uint64_t *own,
+                           uint64_t own_stride) {
     // grid y = job (varies before the limb, so the jobs of one limb run together and
     // share that limb's digit slice in L2), z = limb t of Q_l u P
     const uint32_t n = 1u << log_n, k = COEF(), r = blockIdx.y, t = blockIdx.z;
@@ -389,11 +392,13 @@ __global__ void __launch_bounds__(256, 3) k_ks_inner(const uint64_t *ext, int ex
     const uint32_t kk = g == 1 ? k : auto_index(k, g, log_n);
     const uint64_t ext_ct = (uint64_t)dnum * W * n, out_ct = 2ull * W * n;
     for (uint32_t c = 0; c < C; c++) {
-        const uint64_t *e = ext + (ext_per_job ? (uint64_t)r * C + c : c) * ext_ct + (uint64_t)t * n + k;
+        const uint64_t cti = ext_per_job ? (uint64_t)r * C + c : c;
+        const uint64_t *e = ext + cti * ext_ct + (uint64_t)t * n + k;
         uint64_t xs[MAXD];
 #pragma unroll
         for (int j = 0; j < MAXD; j++)      // all digit loads issued before the products
-            if (j < (int)dnum) xs[j] = e[(uint64_t)j * W * n];
+            if (j < (int)dnum) xs[j] = (OWN && j == (int)t) ? own[cti * own_stride + (uint64_t)t * n + k]
+                                                            : e[(uint64_t)j * W * n];
         u128 a0{0, 0}, a1{0, 0};
 #pragma unroll
         for (int j = 0; j < MAXD; j++) {
@@ -661,33 +666,50 @@ void modup(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t 
     HEAR_REQUIRE(c->alpha <= 4, HEAR_E_UNSUPPORTED, "at most 4 special primes");
     // coefficient-domain copy of the digit limbs (the inverse NTT reads c1 in place of a copy)
     ntt_inverse_from(c, c1, c1_stride, tmp, n_ct * L1, map_q(level, c->n_q), st);
+    LimbMap m = map_qp(level, c->n_q, c->K);
+    m.skip_dnum = dnum;
+    m.alpha = c->alpha;
+    if (c->alpha == 1) {
+        // one-limb digits: the extension of digit j to limb t is [a_j]_t, folded into the
+        // forward transform's load; the digit's own limb stays in c1 (ks_inner reads it there)
+        ntt_forward_pro(c, ext, n_ct * dnum * W, m, tmp, c->n, st);
+        return;
+    }
     check_yz(dnum, n_ct);
     LAUNCH3(k_modup_conv, grid3(c->n, dnum, n_ct), kBlock, st, 8.0 * n_ct * ((double)L1 + (double)dnum * W) * c->n,
             c1, c1_stride, tmp, ext, L1, W, dnum, c->alpha, c->n_q, lc.d.u64() + lc.off_qhat_inv,
             lc.d.u64() + lc.off_qhat_mod, c->dev_primes(), c->n);
-    LimbMap m = map_qp(level, c->n_q, c->K);
-    m.skip_dnum = dnum;
-    m.alpha = c->alpha;
     ntt_forward(c, ext, n_ct * dnum * W, m, st);
 }
 
 void ks_inner(const hear_context *c, uint32_t level, uint32_t R, uint32_t C, const uint64_t *ext, bool ext_per_job,
-              const uint64_t *const *d_keys, const uint32_t *d_ginv, uint64_t *out, cudaStream_t st) {
+              const uint64_t *const *d_keys, const uint32_t *d_ginv, uint64_t *out, const uint64_t *c1,
+              uint64_t c1_stride, cudaStream_t st) {
+    const uint64_t *own = c->alpha == 1 ? c1 : nullptr;
     const uint32_t L1 = level + 1, W = L1 + c->K, dnum = c->dnum(level);
     check_yz(R, W);
     const double dn = dnum, wn = (double)W * c->n * 8.0;
     // algorithmic: each key once, each extended digit once (per job if not shared), each output once
     const double bytes = R * 2.0 * dn * wn + (ext_per_job ? (double)R * C : (double)C) * dn * wn + R * C * 2.0 * wn;
     const dim3 grid = grid3(c->n, R, W);
-    if (dnum <= 8)
-        LAUNCH3(k_ks_inner<8>, grid, kBlock, st, bytes, ext, (int)ext_per_job, d_keys, d_ginv, out, C, L1, W, dnum,
-                c->n_q, c->nqp(), c->log_n, c->dev_primes());
-    else if (dnum <= 16)
-        LAUNCH3(k_ks_inner<16>, grid, kBlock, st, bytes, ext, (int)ext_per_job, d_keys, d_ginv, out, C, L1, W, dnum,
-                c->n_q, c->nqp(), c->log_n, c->dev_primes());
-    else
-        LAUNCH3(k_ks_inner<48>, grid, kBlock, st, bytes, ext, (int)ext_per_job, d_keys, d_ginv, out, C, L1, W, dnum,
-                c->n_q, c->nqp(), c->log_n, c->dev_primes());
+#define KS_LAUNCH(NAME, D, O)                                                                                    \
+    do {                                                                                                          \
+        ProfScope ps__(c, NAME, st, bytes);                                                                       \
+        k_ks_inner<D, O><<<grid, kBlock, 0, st>>>(ext, (int)ext_per_job, d_keys, d_ginv, out, C, L1, W, dnum,     \
+                                                  c->n_q, c->nqp(), c->log_n, c->dev_primes(), own, c1_stride);   \
+        HEAR_CHECK_CUDA(cudaGetLastError());                                                                      \
+    } while (0)
+    if (dnum <= 8) {
+        if (own) KS_LAUNCH("k_ks_inner<8>", 8, true);
+        else KS_LAUNCH("k_ks_inner<8>", 8, false);
+    } else if (dnum <= 16) {
+        if (own) KS_LAUNCH("k_ks_inner<16>", 16, true);
+        else KS_LAUNCH("k_ks_inner<16>", 16, false);
+    } else {
+        if (own) KS_LAUNCH("k_ks_inner<48>", 48, true);
+        else KS_LAUNCH("k_ks_inner<48>", 48, false);
+    }
+#undef KS_LAUNCH
 }
 
 void moddown(const hear_context *c, uint32_t level, uint32_t n_ct, uint64_t *acc, uint64_t *out,
@@ -702,12 +724,19 @@ void moddown(const hear_context *c, uint32_t level, uint32_t n_ct, uint64_t *acc
     pm.n_q = c->n_q;
     pm.group_stride = (uint64_t)W * c->n;
     ntt_inverse(c, acc + (uint64_t)L1 * c->n, groups * c->K, pm, st);
+    if (c->K == 1) {
+        // one special prime: the conversion P -> q_t is [x_P]_t, folded into the load of the
+        // forward transform
+        ntt_forward_pro(c, tmp, groups * L1, map_q(level, c->n_q), acc + (uint64_t)L1 * c->n, (uint64_t)W * c->n,
+                        st);
+    } else {
     uint32_t ny, nz;
     split_yz(groups, ny, nz);
     LAUNCH3(k_moddown_conv, grid3(c->n, ny, nz), kBlock, st, 8.0 * groups * ((double)c->K + L1) * c->n, acc, tmp,
             groups, L1, W, c->K, c->n_q, lc.d.u64() + lc.off_phat_inv, lc.d.u64() + lc.off_phat_mod, c->dev_primes(),
             c->n);
     ntt_forward(c, tmp, groups * L1, map_q(level, c->n_q), st);
+    }
     check_yz(L1, groups);
     LAUNCH3(k_moddown_combine, grid3(c->n, L1, groups), kBlock, st,
             8.0 * groups * L1 * c->n * (3.0 + (addend ? 1.0 : 0.0)), acc, tmp, out, addend, add_stride, add_mask,

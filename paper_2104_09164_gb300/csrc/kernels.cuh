@@ -65,8 +65,11 @@ void modup(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t 
 // Key inner product, R jobs of C ciphertexts: out[r*C + c] ([2][W][N]) =
 //   sum_j sigma_{g_r}(ext_j) (.) key_r[j],  ext = ext[c] (shared) or ext[r*C + c] (per job).
 // d_keys[r]: switching key stored sigma_{g_r}^{-1}-permuted; d_ginv[r] = g_r^{-1} mod 2N.
+// c1 / c1_stride: the polynomials modup() extended (with one-limb digits modup leaves each
+// digit's own limb there instead of copying it into ext)
 void ks_inner(const hear_context *c, uint32_t level, uint32_t R, uint32_t C, const uint64_t *ext, bool ext_per_job,
-              const uint64_t *const *d_keys, const uint32_t *d_ginv, uint64_t *out, cudaStream_t st);
+              const uint64_t *const *d_keys, const uint32_t *d_ginv, uint64_t *out, const uint64_t *c1,
+              uint64_t c1_stride, cudaStream_t st);
 // ModDown of acc [n_ct][2][W][N] (destroys its P limbs) into out [n_ct][2][l+1][N], adding an
 // addend ciphertext (ciphertext index c, or c mod cts_per_job if add_shared, at addend +
 // index*add_stride, polys [2][l+1][N]; poly p only if add_mask bit p) gathered through

@@ -33,6 +33,11 @@ struct PassArgs {
     // (b % per_group) * N instead of from data (out-of-place start), null = in place
     const uint64_t *src;
     uint64_t src_gstride;
+    // forward only: the first pass reads limb b's values from pro + (b / per_group) *
+    // pro_gstride (coefficient domain, any residue below 2^64) reduced mod the limb's
+    // prime -- a basis extension by one source limb folded into the transform's load
+    const uint64_t *pro;
+    uint64_t pro_gstride;
     uint32_t n_limbs;
     uint32_t log_n;
     LimbMap map;
@@ -236,7 +241,14 @@ __global__ void __launch_bounds__(Tile<LOGR, MODE>::THREADS, Tile<LOGR, MODE>::M
     const uint32_t cols = a.n >> LOGR;
     const uint32_t c0 = tile * C;
     load_twiddles<LOGR, THREADS>(stw, a.tw + (size_t)pi * a.n, a.tw_sh + (size_t)pi * a.n);
-    gather_tile<TILE, THREADS>(s, [&](int i) { return g[c0 + i % C + (size_t)(i / C) * cols]; });
+    if (FWD && a.pro) {
+        const uint64_t *pg = a.pro + (uint64_t)(limb / a.map.per_group) * a.pro_gstride;
+        gather_tile<TILE, THREADS>(s, [&](int i) {
+            return shoup(pg[c0 + i % C + (size_t)(i / C) * cols], 1, P.one_sh, P.q);
+        });
+    } else {
+        gather_tile<TILE, THREADS>(s, [&](int i) { return g[c0 + i % C + (size_t)(i / C) * cols]; });
+    }
     __syncthreads();
     if (P.q < a.small_below) pass_groups<LOGR, FWD, true, TILE, false, DONE0, MODE>(s, 0, 0, stw, stw + R, P.q);
     else pass_groups<LOGR, FWD, true, TILE, true, DONE0, MODE>(s, 0, 0, stw, stw + R, P.q);
@@ -336,7 +348,14 @@ ntt_fused(PassArgs a) {
     const uint64_t *tw = a.tw + (size_t)pi * a.n, *tws = a.tw_sh + (size_t)pi * a.n;
     load_twiddles<LA, THREADS>(stw, tw, tws);
     if (FWD) {
-        gather_tile<TILE, THREADS>(sA, [&](int i) { return g[r * CA + i % CA + (size_t)(i / CA) * RB]; });
+        if (a.pro) {
+            const uint64_t *pg = a.pro + (uint64_t)(limb / a.map.per_group) * a.pro_gstride;
+            gather_tile<TILE, THREADS>(sA, [&](int i) {
+                return shoup(pg[r * CA + i % CA + (size_t)(i / CA) * RB], 1, P.one_sh, q);
+            });
+        } else {
+            gather_tile<TILE, THREADS>(sA, [&](int i) { return g[r * CA + i % CA + (size_t)(i / CA) * RB]; });
+        }
         __syncthreads();
         if (small) all_groups<LA, true, true, TILE, false, 0>(sA, 0, 0, stw, stw + RA, q);
         else all_groups<LA, true, true, TILE, true, 0>(sA, 0, 0, stw, stw + RA, q);
@@ -472,6 +491,8 @@ PassArgs make_args(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, Li
     a.small_below = fwd ? (1ull << 58) : (1ull << (63 - ctx->log_n));
     a.src = nullptr;
     a.src_gstride = 0;
+    a.pro = nullptr;
+    a.pro_gstride = 0;
     return a;
 }
 
@@ -486,9 +507,16 @@ double ntt_bytes(const hear_context *ctx, uint32_t n_limbs, const LimbMap &map) 
 }
 
 void ntt_forward(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, LimbMap map, cudaStream_t s) {
+    ntt_forward_pro(ctx, data, n_limbs, map, nullptr, 0, s);
+}
+
+void ntt_forward_pro(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, LimbMap map, const uint64_t *pro,
+                     uint64_t pro_gstride, cudaStream_t s) {
     if (n_limbs == 0) return;
     ProfScope ps(ctx, "ntt_fwd", s, ntt_bytes(ctx, n_limbs, map), launches_of(ctx, true, n_limbs));
     PassArgs a = make_args(ctx, data, n_limbs, map, true);
+    a.pro = pro;
+    a.pro_gstride = pro_gstride;
     switch (ctx->log_n) {
     case 11: launch_fwd<6, 5>(ctx, a, s); break;
     case 12: launch_fwd<6, 6>(ctx, a, s); break;
