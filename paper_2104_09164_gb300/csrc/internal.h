@@ -211,10 +211,10 @@ inline LimbMap map_qp(uint32_t level, uint32_t n_q, uint32_t K) {
 void ntt_forward(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, LimbMap map, cudaStream_t s);
 void ntt_inverse(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, LimbMap map, cudaStream_t s);
 // forward NTT whose input limb b (group g = b / per_group) is read from pro + g * pro_gstride
-// (coefficient domain) and reduced mod limb b's prime (an extension by one source limb);
-// pro = null: ntt_forward
+// (coefficient domain) and reduced mod limb b's prime (an extension by one source limb),
+// centred mod pro_center first when that is nonzero; pro = null: ntt_forward
 void ntt_forward_pro(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, LimbMap map, const uint64_t *pro,
-                     uint64_t pro_gstride, cudaStream_t s);
+                     uint64_t pro_gstride, cudaStream_t s, uint64_t pro_center = 0);
 // inverse NTT from src (limb b of group g at src + g * src_gstride + b' * N) into data (the
 // layout of `map`, contiguous groups); src is left unchanged
 void ntt_inverse_from(const hear_context *ctx, const uint64_t *src, uint64_t src_gstride, uint64_t *data,

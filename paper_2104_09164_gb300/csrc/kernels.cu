@@ -469,24 +469,6 @@ __global__ void k_moddown_combine(const uint64_t *acc, const uint64_t *tmp, uint
     out[i] = v;
 }
 
-// w_i = [c_l]_centred mod q_i for every i < l, from the coefficient-domain last limb;
-// one thread per (polynomial = y + z*gridDim.y, coefficient)
-__global__ void k_rescale_lift(const uint64_t *in, uint64_t *tmp, uint32_t n_polys, uint32_t L1, const DevPrime *P,
-                               uint32_t n) {
-    const uint32_t g = limb_yz(), k = COEF();
-    if (g >= n_polys) return;
-    const uint32_t l = L1 - 1;
-    const uint64_t ql = P[l].q, half = (ql - 1) / 2;
-    const uint64_t v = in[((uint64_t)g * L1 + l) * n + k];
-    const bool neg = v > half;
-    const uint64_t mag = neg ? ql - v : v;
-    for (uint32_t t = 0; t < l; t++) {
-        const DevPrime p = P[t];
-        const uint64_t r = reduce64(mag, p);
-        tmp[((uint64_t)g * l + t) * n + k] = neg ? neg_mod(r, p.q) : r;
-    }
-}
-
 // y = limb t < l, z = polynomial
 __global__ void k_rescale_combine(const uint64_t *in, const uint64_t *tmp, uint64_t *out, uint32_t L1,
                                   const uint64_t *ql_inv, const DevPrime *P, uint32_t n) {
@@ -754,11 +736,10 @@ void rescale(const hear_context *c, uint32_t level, uint32_t n_polys, uint64_t *
     lm.n_q = c->n_q;
     lm.group_stride = (uint64_t)L1 * c->n;
     ntt_inverse(c, in + (uint64_t)level * c->n, n_polys, lm, st);
-    uint32_t ny, nz;
-    split_yz(n_polys, ny, nz);
-    LAUNCH3(k_rescale_lift, grid3(c->n, ny, nz), kBlock, st, 8.0 * n_polys * (1.0 + level) * c->n, in, tmp, n_polys,
-            L1, c->dev_primes(), c->n);
-    ntt_forward(c, tmp, n_polys * level, map_q(level - 1, c->n_q), st);
+    // the centred lift of the last limb to the other limbs, folded into the forward
+    // transform's load
+    ntt_forward_pro(c, tmp, n_polys * level, map_q(level - 1, c->n_q), in + (uint64_t)level * c->n,
+                    (uint64_t)L1 * c->n, st, c->primes[level]);
     check_yz(level, n_polys);
     LAUNCH3(k_rescale_combine, grid3(c->n, level, n_polys), kBlock, st, 24.0 * n_polys * level * c->n, in, tmp, out,
             L1, lc.d.u64() + lc.off_ql_inv, c->dev_primes(), c->n);

@@ -38,6 +38,7 @@ struct PassArgs {
     // prime -- a basis extension by one source limb folded into the transform's load
     const uint64_t *pro;
     uint64_t pro_gstride;
+    uint64_t pro_center;     // nonzero: the source residues are centred mod this prime first
     uint32_t n_limbs;
     uint32_t log_n;
     LimbMap map;
@@ -177,6 +178,15 @@ __device__ __forceinline__ void pass_groups(uint64_t *s, uint32_t s_off, uint32_
     else all_groups<LOGR, FWD, PASSA, TILE, RED, DONE0>(s, s_off, blk_base, tw, tws, q);
 }
 
+// the prologue value of a forward transform: v (a residue of the source limb) reduced mod q,
+// after centring it into (-qc/2, qc/2] when qc is nonzero
+__device__ __forceinline__ uint64_t pro_value(uint64_t v, uint64_t qc, const DevPrime &P) {
+    if (!qc) return shoup(v, 1, P.one_sh, P.q);
+    const bool neg = v > (qc - 1) / 2;
+    const uint64_t r = shoup(neg ? qc - v : v, 1, P.one_sh, P.q);
+    return neg ? neg_mod(r, P.q) : r;
+}
+
 // Tile transfers in two phases -- all of a thread's global (or remote shared) loads issued
 // before its first shared store -- so each thread has TILE / THREADS requests in flight.
 // (in batches of 8 words, which keeps the register footprint of the wide tiles in budget)
@@ -243,9 +253,8 @@ __global__ void __launch_bounds__(Tile<LOGR, MODE>::THREADS, Tile<LOGR, MODE>::M
     load_twiddles<LOGR, THREADS>(stw, a.tw + (size_t)pi * a.n, a.tw_sh + (size_t)pi * a.n);
     if (FWD && a.pro) {
         const uint64_t *pg = a.pro + (uint64_t)(limb / a.map.per_group) * a.pro_gstride;
-        gather_tile<TILE, THREADS>(s, [&](int i) {
-            return shoup(pg[c0 + i % C + (size_t)(i / C) * cols], 1, P.one_sh, P.q);
-        });
+        const uint64_t qc = a.pro_center;
+        gather_tile<TILE, THREADS>(s, [&](int i) { return pro_value(pg[c0 + i % C + (size_t)(i / C) * cols], qc, P); });
     } else {
         gather_tile<TILE, THREADS>(s, [&](int i) { return g[c0 + i % C + (size_t)(i / C) * cols]; });
     }
@@ -350,9 +359,8 @@ ntt_fused(PassArgs a) {
     if (FWD) {
         if (a.pro) {
             const uint64_t *pg = a.pro + (uint64_t)(limb / a.map.per_group) * a.pro_gstride;
-            gather_tile<TILE, THREADS>(sA, [&](int i) {
-                return shoup(pg[r * CA + i % CA + (size_t)(i / CA) * RB], 1, P.one_sh, q);
-            });
+            const uint64_t qc = a.pro_center;
+            gather_tile<TILE, THREADS>(sA, [&](int i) { return pro_value(pg[r * CA + i % CA + (size_t)(i / CA) * RB], qc, P); });
         } else {
             gather_tile<TILE, THREADS>(sA, [&](int i) { return g[r * CA + i % CA + (size_t)(i / CA) * RB]; });
         }
@@ -493,6 +501,7 @@ PassArgs make_args(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, Li
     a.src_gstride = 0;
     a.pro = nullptr;
     a.pro_gstride = 0;
+    a.pro_center = 0;
     return a;
 }
 
@@ -511,12 +520,13 @@ void ntt_forward(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, Limb
 }
 
 void ntt_forward_pro(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, LimbMap map, const uint64_t *pro,
-                     uint64_t pro_gstride, cudaStream_t s) {
+                     uint64_t pro_gstride, cudaStream_t s, uint64_t pro_center) {
     if (n_limbs == 0) return;
     ProfScope ps(ctx, "ntt_fwd", s, ntt_bytes(ctx, n_limbs, map), launches_of(ctx, true, n_limbs));
     PassArgs a = make_args(ctx, data, n_limbs, map, true);
     a.pro = pro;
     a.pro_gstride = pro_gstride;
+    a.pro_center = pro_center;
     switch (ctx->log_n) {
     case 11: launch_fwd<6, 5>(ctx, a, s); break;
     case 12: launch_fwd<6, 6>(ctx, a, s); break;
