@@ -257,17 +257,30 @@ __device__ __forceinline__ void fold(u128 &acc, uint64_t q) {
 // all CTAs of one (limb, tile) run back to back, so the plaintext tile they share comes
 // from HBM once and from L2 (and, within a CTA, L1) afterwards.  Each thread walks the
 // giant steps in chunks of four accumulators; its baby words stay in L1/L2 across chunks.
+// With few ciphertexts (2C <= 4 polynomials, one CTA column) the warps beyond 2C would idle:
+// jw = 8 / 2C warps then share each polynomial, warp w taking polynomial w mod 2C and the
+// giant-step chunks (4 outputs each) jpart, jpart + jw, .. with jpart = w / 2C.
 __global__ void __launch_bounds__(256, 4) k_lincomb(uint32_t L1, uint32_t C, uint32_t n1, uint32_t n2,
                                                  const uint64_t *__restrict__ baby, const uint64_t *__restrict__ pt,
-                                                 uint64_t *__restrict__ out, const DevPrime *P, uint32_t n) {
-    const uint32_t cp = blockIdx.x * 8 + (threadIdx.x >> 5);   // c * 2 + poly
-    if (cp >= 2 * C) return;
+                                                 uint64_t *__restrict__ out, const DevPrime *P, uint32_t n,
+                                                 uint32_t jw) {
+    const uint32_t w = threadIdx.x >> 5;
+    uint32_t cp, jpart;                                           // cp = c * 2 + poly
+    if (jw > 1) {
+        cp = w % (2 * C);
+        jpart = w / (2 * C);
+        if (jpart >= jw) return;
+    } else {
+        cp = blockIdx.x * 8 + w;
+        jpart = 0;
+        if (cp >= 2 * C) return;
+    }
     const uint32_t t = blockIdx.z, k = blockIdx.y * 32 + (threadIdx.x & 31);
     const uint64_t plane = (uint64_t)L1 * n, r = (uint64_t)t * n + k;
     const uint64_t q = P[t].q, qinv = P[t].qinv;
     const uint64_t bstride = 2ull * C * plane;                    // between baby steps / giant outputs
     const uint64_t *bp = baby + (uint64_t)cp * plane + r;
-    for (uint32_t j0 = 0; j0 < n2; j0 += 4) {
+    for (uint32_t j0 = 4 * jpart; j0 < n2; j0 += 4 * jw) {
         u128 acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
         const uint64_t *pp = pt + ((uint64_t)j0 * n1) * plane + r;
         const uint32_t jn = min(4u, n2 - j0);
@@ -616,7 +629,8 @@ void lincomb(const hear_context *c, uint32_t level, uint32_t n_ct, uint32_t n1, 
     HEAR_REQUIRE(grid.x < (1u << 31) && L1 <= 65535, HEAR_E_UNSUPPORTED, "launch too large");
     // algorithmic: every baby ciphertext, every plaintext and every output once
     const double bytes = 8.0 * L1 * c->n * (2.0 * n_ct * n1 + (double)n1 * n2 + 2.0 * n_ct * n2);
-    LAUNCH3(k_lincomb, grid, 256, st, bytes, L1, n_ct, n1, n2, baby, pt, out, c->dev_primes(), c->n);
+    const uint32_t jw = 2 * n_ct <= 4 ? 8 / (2 * n_ct) : 1;
+    LAUNCH3(k_lincomb, grid, 256, st, bytes, L1, n_ct, n1, n2, baby, pt, out, c->dev_primes(), c->n, jw);
 }
 void mulplain(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *ct, const uint64_t *pt,
               uint64_t *out, cudaStream_t st) {
