@@ -432,6 +432,58 @@ __global__ void __launch_bounds__(256, 3) k_ks_inner(const uint64_t *ext, int ex
     }
 }
 
+// The key inner product for one ciphertext whose extended digits all jobs share (hoisted
+// rotations of a single input): a thread loads the digits of its coefficient once and runs RJ
+// jobs (keys) on them; grid y = group of RJ jobs, z = limb.  Same sums as k_ks_inner.
+template <int MAXD, bool OWN, int RJ>
+__global__ void __launch_bounds__(256, 3) k_ks_inner_rj(const uint64_t *ext, const uint64_t *const *keys,
+                                                        const uint32_t *ginv, uint64_t *out, uint32_t R, uint32_t L1,
+                                                        uint32_t W, uint32_t dnum, uint32_t n_q, uint32_t nqp,
+                                                        uint32_t log_n, const DevPrime *P, const uint64_t *own) {
+    const uint32_t n = 1u << log_n, k = COEF(), r0 = blockIdx.y * RJ, t = blockIdx.z;
+    const uint32_t pt = t < L1 ? t : n_q + (t - L1);
+    const uint64_t q = P[pt].q, qinv = P[pt].qinv;
+    const uint64_t key_plane = (uint64_t)nqp * n, out_ct = 2ull * W * n;
+    uint64_t xs[MAXD];
+    const uint64_t *e = ext + (uint64_t)t * n + k;
+#pragma unroll
+    for (int j = 0; j < MAXD; j++)
+        if (j < (int)dnum) xs[j] = (OWN && j == (int)t) ? own[(uint64_t)t * n + k] : e[(uint64_t)j * W * n];
+#pragma unroll 1
+    for (int rr = 0; rr < RJ; rr++) {
+        const uint32_t r = r0 + rr;
+        if (r >= R) break;
+        const uint64_t *key = keys[r] + (uint64_t)pt * n + k;
+        uint64_t k0[MAXD], k1[MAXD];
+#pragma unroll
+        for (int j = 0; j < MAXD; j++) {
+            if (j < (int)dnum) {
+                k0[j] = __ldg(key + (uint64_t)j * 2 * key_plane);
+                k1[j] = __ldg(key + (uint64_t)j * 2 * key_plane + key_plane);
+            }
+        }
+        u128 a0{0, 0}, a1{0, 0};
+#pragma unroll
+        for (int j = 0; j < MAXD; j++) {
+            if (j < (int)dnum) {
+                mac_raw(a0, xs[j], k0[j]);
+                mac_raw(a1, xs[j], k1[j]);
+                if ((j & 7) == 7) {
+                    fold(a0, q);
+                    fold(a1, q);
+                }
+            }
+        }
+        fold(a0, q);
+        fold(a1, q);
+        const uint32_t g = ginv[r];
+        const uint32_t kk = g == 1 ? k : auto_index(k, g, log_n);
+        uint64_t *o = out + (uint64_t)r * out_ct + (uint64_t)t * n + kk;
+        o[0] = mont_reduce(a0, q, qinv);
+        o[(uint64_t)W * n] = mont_reduce(a1, q, qinv);
+    }
+}
+
 // ModDown conversion, one thread per (group = y + z*gridDim.y, coefficient):
 // y_k = [x_{p_k} * phat_inv_k]_{p_k} once, conv_i = sum_k y_k * [P/p_k]_{q_i} mod q_i for
 // every i < L1 (x_P in the coefficient domain).
@@ -695,6 +747,19 @@ void ks_inner(const hear_context *c, uint32_t level, uint32_t R, uint32_t C, con
                                                   c->n_q, c->nqp(), c->log_n, c->dev_primes(), own, c1_stride);   \
         HEAR_CHECK_CUDA(cudaGetLastError());                                                                      \
     } while (0)
+    if (C == 1 && !ext_per_job && R >= 2 && dnum <= 8) {
+        constexpr int RJ = 4;
+        const dim3 g4(c->n / kBlock, (R + RJ - 1) / RJ, W);
+        ProfScope ps__(c, "k_ks_inner<8>", st, bytes);
+        if (own)
+            k_ks_inner_rj<8, true, RJ><<<g4, kBlock, 0, st>>>(ext, d_keys, d_ginv, out, R, L1, W, dnum, c->n_q,
+                                                              c->nqp(), c->log_n, c->dev_primes(), own);
+        else
+            k_ks_inner_rj<8, false, RJ><<<g4, kBlock, 0, st>>>(ext, d_keys, d_ginv, out, R, L1, W, dnum, c->n_q,
+                                                               c->nqp(), c->log_n, c->dev_primes(), own);
+        HEAR_CHECK_CUDA(cudaGetLastError());
+        return;
+    }
     if (dnum <= 8) {
         if (own) KS_LAUNCH("k_ks_inner<8>", 8, true);
         else KS_LAUNCH("k_ks_inner<8>", 8, false);
