@@ -154,3 +154,37 @@ def test_autotuned_strategies_bit_exact(H):
         H.hear_context_destroy(ctx)
     assert len(report) == 3 and all(r["best"] in r["ms"] for r in report)
     _network(H, "cnn_toy", strategies, 2, [0])
+
+
+def test_cnn_rejects_bad_inputs(H):
+    """errors come back as status codes: a fast convolution on a dense input, channel counts
+    that do not fill the blocks, missing rotation keys, inputs at the wrong level"""
+    net = make_cnn("cnn_toy", n_samples=1)
+    spec = collapse_cnn(net)
+    ctx = H.hear_context_create(net.log_n, net.q_bits, net.p_bits, net.log2_scale, net.sigma, 0)
+    try:
+        bad = dict(spec, layers=[("conv", spec["layers"][0][1], True)] + spec["layers"][1:])
+        with pytest.raises(H.HearError) as e:
+            H.hear_cnn_create(ctx, bad)
+        assert e.value.code == -1
+        W = spec["layers"][0][1]
+        with pytest.raises(H.HearError):
+            H.hear_cnn_create(ctx, dict(spec, layers=[("conv", W[:6], False)]))
+        m = H.hear_cnn_create(ctx, spec)
+        sk, pk, evk = H.hear_keygen(ctx, 301, H.hear_cnn_rotations(m)[:3])
+        ct = H.hear_cnn_encrypt(ctx, pk, m, net.clips[0], 401, 0)
+        with pytest.raises(H.HearError) as e:
+            H.hear_cnn_evaluate(m, evk, 0, len(H.hear_cnn_ops(m)), ct, 1)
+        assert e.value.code == -6
+        low = H.hear_ciphertext_drop_level(ct[0], 3)
+        with pytest.raises(H.HearError) as e:
+            H.hear_cnn_evaluate(m, evk, 0, 1, [low], 1)
+        assert e.value.code == -4
+        for h in ct + [low]:
+            H.hear_ciphertext_destroy(h)
+        H.hear_eval_keys_destroy(evk)
+        H.hear_public_key_destroy(pk)
+        H.hear_secret_key_destroy(sk)
+        H.hear_cnn_destroy(m)
+    finally:
+        H.hear_context_destroy(ctx)
