@@ -984,6 +984,73 @@ int or_ks_inner(const or_ctx *c, uint32_t level, const uint64_t *ext, const uint
     return 0;
 }
 
+/* Arithmetic over Q_l u P (limb t < l+1: q_t, else the special prime p_(t-l-1)), used by
+ * the hoisted-ModDown evaluation of baby-step rotations. */
+/* out[p] = a[p] (.) b for n_poly polynomials a [n_poly][W][N] and one b [W][N] */
+int or_mul_ext(const or_ctx *c, uint32_t level, uint32_t n_poly, const uint64_t *a, const uint64_t *b,
+               uint64_t *out)
+{
+    size_t n = c->n;
+    uint32_t W = level + 1 + c->n_p;
+    for (uint32_t p = 0; p < n_poly; p++)
+        for (uint32_t t = 0; t < W; t++) {
+            const om_mod *m = &c->pr[qp_prime(c, level, t)].m;
+            size_t o = ((size_t)p * W + t) * n;
+            for (size_t k = 0; k < n; k++) out[o + k] = om_mul(a[o + k], b[(size_t)t * n + k], m);
+        }
+    return 0;
+}
+
+int or_add_ext(const or_ctx *c, uint32_t level, uint32_t n_poly, const uint64_t *a, const uint64_t *b,
+               uint64_t *out)
+{
+    size_t n = c->n;
+    uint32_t W = level + 1 + c->n_p;
+    for (uint32_t p = 0; p < n_poly; p++)
+        for (uint32_t t = 0; t < W; t++) {
+            uint64_t q = c->pr[qp_prime(c, level, t)].m.q;
+            size_t o = ((size_t)p * W + t) * n;
+            for (size_t k = 0; k < n; k++) out[o + k] = om_add(a[o + k], b[o + k], q);
+        }
+    return 0;
+}
+
+/* P * x lifted to Q_l u P: limb t < l+1 is [P]_{q_t} x_t, the special-prime limbs are 0
+ * (n_poly polynomials x [n_poly][l+1][N] -> out [n_poly][W][N]) */
+int or_scale_p_ext(const or_ctx *c, uint32_t level, uint32_t n_poly, const uint64_t *x, uint64_t *out)
+{
+    size_t n = c->n;
+    uint32_t L1 = level + 1, W = L1 + c->n_p;
+    for (uint32_t p = 0; p < n_poly; p++)
+        for (uint32_t t = 0; t < W; t++) {
+            size_t o = ((size_t)p * W + t) * n;
+            if (t >= L1) {
+                memset(out + o, 0, n * 8);
+                continue;
+            }
+            const om_mod *m = &c->pr[t].m;
+            uint64_t Pm = 1;
+            for (uint32_t k = 0; k < c->n_p; k++) Pm = om_mul(Pm, c->pr[c->n_q + k].m.q % m->q, m);
+            const uint64_t *xi = x + ((size_t)p * L1 + t) * n;
+            for (size_t k = 0; k < n; k++) out[o + k] = om_mul(xi[k], Pm, m);
+        }
+    return 0;
+}
+
+/* plaintext of integer coefficients m over Q_l u P, NTT domain */
+int or_encode_pt_ext(const or_ctx *c, uint32_t level, const int64_t *m, uint64_t *pt)
+{
+    uint32_t W = level + 1 + c->n_p;
+    uint32_t pr[OR_MAXP] = {0};
+    for (uint32_t t = 0; t < W; t++) {
+        pr[t] = qp_prime(c, level, t);
+        uint64_t q = c->pr[pr[t]].m.q;
+        for (size_t k = 0; k < c->n; k++) pt[(size_t)t * c->n + k] = signed_mod(m[k], q);
+    }
+    or_ntt_fwd(c, pr, W, pt);
+    return 0;
+}
+
 /* ModDown: out_i = (x_i - Conv_{P->q_i}(x_P)) * P^-1 mod q_i, with the fast basis
  * conversion Conv_{P->q}(x) = sum_k [x_k * (P/p_k)^-1]_{p_k} * (P/p_k) mod q (x_k in [0,p_k),
  * no correction term). */

@@ -110,6 +110,14 @@ int or_modup(const or_ctx *, uint32_t level, const uint64_t *d, uint64_t *ext);
  * out: [2][l+1+K][N] */
 int or_ks_inner(const or_ctx *, uint32_t level, const uint64_t *ext, const uint64_t *swk,
                 uint32_t galois, uint64_t *out);
+/* Q_l u P arithmetic for hoisted ModDown: products with one plaintext, sums, P * x lift,
+ * plaintext encoding (NTT domain); polynomials [n_poly][l+1+K][N] */
+int or_mul_ext(const or_ctx *, uint32_t level, uint32_t n_poly, const uint64_t *a, const uint64_t *b,
+               uint64_t *out);
+int or_add_ext(const or_ctx *, uint32_t level, uint32_t n_poly, const uint64_t *a, const uint64_t *b,
+               uint64_t *out);
+int or_scale_p_ext(const or_ctx *, uint32_t level, uint32_t n_poly, const uint64_t *x, uint64_t *out);
+int or_encode_pt_ext(const or_ctx *, uint32_t level, const int64_t *m, uint64_t *pt);
 /* ModDown: x [l+1+K][N] over Q_l u P -> out [l+1][N] */
 int or_moddown(const or_ctx *, uint32_t level, const uint64_t *x, uint64_t *out);
 /* Rescale by q_l: [n_poly][l+1][N] -> [n_poly][l][N] */

@@ -83,6 +83,10 @@ def lib():
             "or_from_coeff": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32,
                                              _u64p, _u64p]),
             "or_encode_pt": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, _i64p, _u64p]),
+            "or_mul_ext": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, _u64p, _u64p, _u64p]),
+            "or_add_ext": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, _u64p, _u64p, _u64p]),
+            "or_scale_p_ext": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, _u64p, _u64p]),
+            "or_encode_pt_ext": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, _i64p, _u64p]),
             "or_add": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32,
                                       _u64p, _u64p, _u64p]),
             "or_mulplain": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, _u64p, _u64p, _u64p]),
@@ -389,6 +393,50 @@ class Oracle:
             outs.append(Ct(out, ct.level, ct.scale))
         return outs
 
+    # ---------------- hoisted ModDown (baby steps kept over Q_l u P) ----------------
+    def encode_pt_ext(self, z, scale, level):
+        m, ties = self.encode(z, scale)
+        if ties:
+            raise RuntimeError("encoding hit %d near-ties" % ties)
+        W = level + 1 + self.n_p
+        pt = np.empty((W, self.n), dtype=np.uint64)
+        _chk(lib().or_encode_pt_ext(self.h, level, P(m, _i64p), P(pt)), "encode_pt_ext")
+        return pt
+
+    def mul_ext(self, level, a, pt):
+        a = np.ascontiguousarray(a, dtype=np.uint64)
+        out = np.empty_like(a)
+        _chk(lib().or_mul_ext(self.h, level, a.shape[0], P(a), P(np.ascontiguousarray(pt)), P(out)), "mul_ext")
+        return out
+
+    def add_ext(self, level, a, b):
+        out = np.empty_like(a)
+        _chk(lib().or_add_ext(self.h, level, a.shape[0], P(np.ascontiguousarray(a)), P(np.ascontiguousarray(b)),
+                              P(out)), "add_ext")
+        return out
+
+    def scale_p_ext(self, ct: Ct):
+        W = ct.level + 1 + self.n_p
+        out = np.empty((ct.n_poly, W, self.n), dtype=np.uint64)
+        _chk(lib().or_scale_p_ext(self.h, ct.level, ct.n_poly, P(np.ascontiguousarray(ct.data)), P(out)),
+             "scale_p_ext")
+        return out
+
+    def rotate_hoisted_ext(self, ct: Ct, steps, keys: Keys):
+        """rho^step(ct) before ModDown, over Q_l u P: (P sigma_g(c0) + u0, u1) with (u0, u1)
+        the key inner product of the hoisted ModUp of c1 (one ModUp for all steps)"""
+        ext = self.modup(ct.level, ct.data[1])
+        outs = []
+        for st in steps:
+            g = galois_for_step(st, self.n)
+            inner = self.ks_inner(ct.level, ext, keys.rot[g], g)
+            c0g = self.automorphism(ct.level, 1, ct.data[:1], g)
+            pc0 = self.scale_p_ext(Ct(c0g, ct.level, 1))
+            out = inner.copy()
+            out[:1] = self.add_ext(ct.level, inner[:1], pc0)
+            outs.append(out)
+        return outs
+
     def rotate(self, ct: Ct, step, keys: Keys):
         return self.rotate_hoisted(ct, [step], keys)[0]
 
@@ -417,21 +465,33 @@ class Oracle:
         """pos-space vector of size M -> N/2 slots, slot p*k + c holds v[p]"""
         return np.repeat(np.asarray(v, dtype=np.float64), k)
 
-    def fc(self, ct: Ct, W, k, keys: Keys, pool=None, radix=ROTSUM_RADIX):
+    def fc(self, ct: Ct, W, k, keys: Keys, pool=None, radix=ROTSUM_RADIX, n1=None, dh=False):
         """Encrypted FC layer, BSGS diagonal form with hoisted baby steps and one lazy
-        rescale, followed by rotate-and-sum; output replicated with period d_out."""
+        rescale, followed by rotate-and-sum; output replicated with period d_out.
+        n1: baby steps (default bsgs_split); dh: hoisted ModDown -- the baby rotations stay
+        over Q_l u P (P-scaled identity as baby 0), the inner sums are formed there with
+        plaintexts over Q_l u P and each giant-step sum is ModDowned once."""
         d_out, d_in = W.shape
         M = (self.n // 2) // k
         assert d_in <= M and M % d_in == 0 and d_in % d_out == 0
         D = d_out
-        n1, n2 = bsgs_split(D)
+        if n1 is None:
+            n1, n2 = bsgs_split(D)
+        else:
+            n1 = min(n1, D)
+            n2 = (D + n1 - 1) // n1
         level = ct.level
         ql = float(self.q[level])
-        babies = [ct] + (self.rotate_hoisted(ct, [b * k for b in range(1, n1)], keys) if n1 > 1 else [])
+        steps = [b * k for b in range(1, n1)]
+        if dh:
+            babies = [self.scale_p_ext(ct)] + (self.rotate_hoisted_ext(ct, steps, keys) if n1 > 1 else [])
+        else:
+            babies = [ct] + (self.rotate_hoisted(ct, steps, keys) if n1 > 1 else [])
+        enc = self.encode_pt_ext if dh else self.encode_pt
 
         def pt_for(j, b):
             v = np.roll(self.diag_vector(W, j * n1 + b, M), j * n1)   # rho^(-j n1)
-            return self.encode_pt(self.expand(v, k), ql, level)
+            return enc(self.expand(v, k), ql, level)
 
         jobs = [(j, b) for j in range(n2) for b in range(n1) if j * n1 + b < D]
         if pool is None:
@@ -443,8 +503,15 @@ class Oracle:
             for b in range(n1):
                 if j * n1 + b >= D:
                     break
-                prod = self.mulplain(babies[b], pts[(j, b)], ql)
-                inner = prod if inner is None else self.add(inner, prod)
+                if dh:
+                    prod = self.mul_ext(level, babies[b], pts[(j, b)])
+                    inner = prod if inner is None else self.add_ext(level, inner, prod)
+                else:
+                    prod = self.mulplain(babies[b], pts[(j, b)], ql)
+                    inner = prod if inner is None else self.add(inner, prod)
+            if dh:
+                data = np.stack([self.moddown(level, inner[p]) for p in range(2)])
+                inner = Ct(data, level, ct.scale * ql)
             if j > 0:
                 inner = self.rotate(inner, j * n1 * k, keys)
             acc = inner if acc is None else self.add(acc, inner)
@@ -479,10 +546,10 @@ class Oracle:
         z = self.mul_relin_rescale(y, u, keys)
         return self.rotsum(z, 1, d1, k, keys, radix)
 
-    def evaluate(self, layers, ct: Ct, k, keys: Keys, pool=None, radix=ROTSUM_RADIX):
+    def evaluate(self, layers, ct: Ct, k, keys: Keys, pool=None, radix=ROTSUM_RADIX, n1=None, dh=False):
         for layer in layers:
             if layer[0] == "fc":
-                ct = self.fc(ct, layer[1], k, keys, pool, radix)
+                ct = self.fc(ct, layer[1], k, keys, pool, radix, n1, dh)
             elif layer[0] == "square":
                 ct = self.square(ct, keys)
             elif layer[0] == "fc_sq_fc":
@@ -503,12 +570,16 @@ def rotsum_steps(step, count, radix):
     return out
 
 
-def rotation_steps(layers, clip_dim, k, radix=ROTSUM_RADIX):
+def rotation_steps(layers, clip_dim, k, radix=ROTSUM_RADIX, n1_opt=None):
     """pos-space rotation amounts (times k = slots) every key switch of the network needs"""
     steps = set()
 
     def fc_steps(d_out, d_in):
-        n1, n2 = bsgs_split(d_out)
+        if n1_opt is None:
+            n1, n2 = bsgs_split(d_out)
+        else:
+            n1 = min(n1_opt, d_out)
+            n2 = (d_out + n1 - 1) // n1
         for b in range(1, n1):
             steps.add(b * k)
         for j in range(1, n2):

@@ -564,3 +564,35 @@ def test_rotsum_radix_folds_the_same_sum():
         assert np.max(np.abs(got - want)) < 2.0 ** -20, radix
     assert O.rotsum_steps(8, 16, 4) == [8, 16, 24, 32, 64, 96]
     assert O.rotsum_steps(1, 64, 16) == list(range(1, 16)) + [16, 32, 48]
+
+
+def test_hoisted_moddown_fc_matches_plain_product():
+    """the FC with baby steps kept over Q_l u P and one ModDown per giant-step sum decrypts
+    to W x (and agrees with the per-rotation ModDown form), for several baby-step counts;
+    the P-lift of the identity and the extended products are exact identities"""
+    from oracle import oracle as O
+    o = O.Oracle(12, [50, 40, 40], [50], 3.2)
+    S = o.n // 2
+    rng = np.random.default_rng(8)
+    k = 16
+    M = S // k
+    W = rng.normal(0, 0.1, size=(16, M))
+    steps = set()
+    for n1 in (2, 4, 16):
+        steps.update(O.rotation_steps([("fc", W)], M, k, 2, n1))
+    keys = o.keygen(9, [O.galois_for_step(s, o.n) for s in steps])
+    x = rng.uniform(-1, 1, M)
+    ct = o.encrypt(keys.pk, np.repeat(x, k), 12, 0, 2.0 ** 40)
+    want = np.repeat(W @ x, 1)
+    for n1 in (2, 4, 16):
+        r_dh = o.fc(ct, W, k, keys, radix=2, n1=n1, dh=True)
+        r_std = o.fc(ct, W, k, keys, radix=2, n1=n1, dh=False)
+        got_dh = o.decrypt(keys, r_dh)[::k][:16]
+        got_std = o.decrypt(keys, r_std)[::k][:16]
+        assert np.max(np.abs(got_dh - want)) < 2.0 ** -20, n1
+        assert np.max(np.abs(got_dh - got_std)) < 2.0 ** -20, n1
+        assert r_dh.level == r_std.level and r_dh.scale == r_std.scale
+    # ModDown(P x lifted) = x exactly
+    lifted = o.scale_p_ext(ct)
+    back = np.stack([o.moddown(ct.level, lifted[p]) for p in range(2)])
+    assert np.array_equal(back, ct.data)
