@@ -233,11 +233,13 @@ def oracle_sample(w, steps_keys, seconds_budget=25.0):
 
 # ------------------------------------------------------------------ GPU arm
 class Setup:
-    def __init__(self, H, w, stream, device, level=None):
-        """level: evaluate from ciphertexts dropped to this level (None = the top level)"""
+    def __init__(self, H, w, stream, device, level=None, fc_n1=None, hoist_moddown=False):
+        """level: evaluate from ciphertexts dropped to this level (None = the top level);
+        fc_n1 / hoist_moddown: the FC evaluation form (hear_model_opts)"""
         self.H, self.w = H, w
         self.ctx = H.hear_context_create(w.log_n, w.q_bits, w.p_bits, w.log2_scale, w.sigma, device)
-        self.model = H.hear_model_create(self.ctx, w.layers, w.clip_dim, level)
+        self.model = H.hear_model_create(self.ctx, w.layers, w.clip_dim, level, fc_n1=fc_n1,
+                                         hoist_moddown=hoist_moddown)
         self.steps = H.hear_model_rotations(self.model)
         self.sk, self.pk, self.evk = H.hear_keygen(self.ctx, 301, self.steps)
         self.cts = [H.hear_encrypt_clips(self.ctx, self.pk, w.ct_clips(i), 401, i, stream) for i in range(w.n_ct)]
@@ -653,18 +655,22 @@ def main_gpu(a):
         # the same small network batched: clips packed 4 per ciphertext, many ciphertexts per
         # launch (one CUDA-graph replay per step), against the plain one-clip-per-launch path
         rows = []
-        for n_clips in (128, 512):
+        # the same model as the plain path, then a throughput form of it: FC baby steps 32
+        # with hoisted ModDown (fewer ModUps of giant steps, one ModDown per giant sum)
+        for n_clips, fc_n1, dh in ((128, None, False), (512, None, False), (512, 32, True)):
             wb = make_workload("small", n_clips)
-            SB = Setup(H, wb, stream, device)
+            SB = Setup(H, wb, stream, device, fc_n1=fc_n1, hoist_moddown=dh)
             bsteps = 5
             tms, blat, bl, bclk = run_gpu(SB, bsteps, 2, dist, torch, stream, device)
             v = bsteps * SB.clips_per_step / (tms / 1e3)
-            rows.append({"clips": n_clips, "ciphertexts": wb.n_ct, "value": v, "unit": UNIT,
+            rows.append({"clips": n_clips, "ciphertexts": wb.n_ct, "fc_n1": fc_n1, "hoist_moddown": dh,
+                         "value": v, "unit": UNIT,
                          "ms_per_step": tms / bsteps, "p50_ms": blat[len(blat) // 2], "gpu_launches": bl,
                          "clocks": bclk, "vs_plain": v / result["value"]})
             SB.close()
         result["batched_small"] = {"workload": "small network (as the plain path), batches of 128 / 512 clips "
-                                               "in 32 / 128 ciphertexts per launch", "rows": rows}
+                                               "in 32 / 128 ciphertexts per launch; last row: FC with 32 baby "
+                                               "steps and hoisted ModDown", "rows": rows}
     if result is not None and not a.no_min_level and a.workload == "small" and a.clips is None and dist.world == 1:
         # minimal start level: inputs dropped to the depth of the network (3 of 7 levels for
         # the small network, 5 of 14 for the large one); the same networks and parameters

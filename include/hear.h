@@ -193,6 +193,10 @@ hear_status hear_model_create_at_level(hear_context *ctx, const hear_layer_desc 
 typedef struct hear_model_opts {
     uint32_t level;
     uint32_t rotsum_radix;
+    uint32_t fc_n1;          /* FC baby steps (power of two; 0 = smallest n1 with n1^2 >= d_out) */
+    uint32_t hoist_moddown;  /* 1: FC baby rotations kept over Q_l u P (baby 0 = P x), inner sums
+                              * with plaintexts over Q_l u P, one ModDown per giant-step sum --
+                              * n2 instead of n1 ModDowns per ciphertext (FC layers only) */
 } hear_model_opts;
 hear_status hear_model_create_ex(hear_context *ctx, const hear_layer_desc *layers, size_t n_layers,
                                  uint32_t clip_dim, const hear_model_opts *opts, hear_model **out);

@@ -436,7 +436,10 @@ hear_status hear_model_create_ex(hear_context *ctx, const hear_layer_desc *layer
     if (!ctx || !layers || !out) return fail(HEAR_E_INVAL, "null argument");
     const uint32_t level = opts && opts->level ? opts->level : ctx->L;
     const uint32_t radix = opts && opts->rotsum_radix ? opts->rotsum_radix : kDefaultRotsumRadix;
-    return guard(ctx, [&] { *out = model_create(ctx, layers, n_layers, clip_dim, level, radix); });
+    const uint32_t n1 = opts ? opts->fc_n1 : 0;
+    const bool dh = opts && opts->hoist_moddown;
+    if (n1 && (n1 & (n1 - 1))) return fail(HEAR_E_INVAL, "fc_n1 must be a power of two");
+    return guard(ctx, [&] { *out = model_create(ctx, layers, n_layers, clip_dim, level, radix, n1, dh); });
 }
 
 hear_status hear_model_levels(const hear_model *m, uint32_t *level_in, uint32_t *level_out) {

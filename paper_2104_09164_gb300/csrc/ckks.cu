@@ -245,6 +245,17 @@ void rotate_hoisted(hear_context *c, uint32_t level, uint32_t n_ct, const uint64
     moddown(c, level, R * n_ct, acc.u64(), out, x, ctw, 1u, true, jobs.gal(), n_ct, tmp.u64(), st);
 }
 
+void rotate_hoisted_ext(hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *x, const std::vector<Rot> &rots,
+                        uint64_t *out_ext, const uint64_t *pmod, cudaStream_t st) {
+    if (rots.empty()) return;
+    const uint32_t n = c->n, L1 = level + 1, W = L1 + c->K, dnum = c->dnum(level), R = (uint32_t)rots.size();
+    const uint64_t plane = (uint64_t)L1 * n, ctw = 2 * plane;
+    DevBuf ext((size_t)n_ct * dnum * W * n * 8, st), tmp((size_t)n_ct * plane * 8, st);
+    modup(c, level, n_ct, x + plane, ctw, ext.u64(), tmp.u64(), st);
+    JobTable jobs = make_jobs(c, rots, st);
+    ks_inner(c, level, R, n_ct, ext.u64(), false, jobs.keys(), jobs.ginv(), out_ext, x + plane, ctw, st, pmod);
+}
+
 void rotate_each(hear_context *c, uint32_t level, uint32_t R, uint32_t C, const uint64_t *x,
                  const std::vector<Rot> &rots, uint64_t *out, cudaStream_t st) {
     const uint32_t n = c->n, L1 = level + 1, W = L1 + c->K, dnum = c->dnum(level), n_ct = R * C;
@@ -291,7 +302,7 @@ std::vector<std::vector<int32_t>> rotsum_rounds(uint32_t step, uint32_t count, u
 }
 
 void build_fc(hear_context *c, hear_model::Fc &fc, const double *W, uint32_t d_out, uint32_t d_in, uint32_t level,
-              uint32_t k, uint32_t M, uint32_t radix) {
+              uint32_t k, uint32_t M, uint32_t radix, uint32_t n1_opt = 0, bool dh = false) {
     HEAR_REQUIRE(d_out && d_in && (d_out & (d_out - 1)) == 0 && (d_in & (d_in - 1)) == 0 && d_in % d_out == 0 &&
                      M % d_in == 0,
                  HEAR_E_INVAL, "FC dimensions must be powers of two with d_out | d_in | clip_dim");
@@ -303,10 +314,25 @@ void build_fc(hear_context *c, hear_model::Fc &fc, const double *W, uint32_t d_o
     fc.level = level;
     uint32_t n1 = 1;
     while (n1 * n1 < fc.D) n1 *= 2;
+    if (n1_opt) n1 = n1_opt;
     n1 = std::min(n1, fc.D);
     fc.n1 = n1;
     fc.n2 = (fc.D + n1 - 1) / n1;
-    const uint32_t n = c->n, slots = n / 2, L1 = level + 1;
+    fc.dh = dh;
+    const uint32_t n = c->n, slots = n / 2, L1 = level + (dh ? 1 + c->K : 1);
+    const LimbMap pmap = dh ? map_qp(level, c->n_q, c->K) : map_q(level, c->n_q);
+    if (dh) {
+        std::vector<uint64_t> pm;
+        for (uint32_t t = 0; t <= level; t++) {
+            const uint64_t q = c->primes[t];
+            uint64_t v = 1;
+            for (uint32_t kk = 0; kk < c->K; kk++) v = hm::mulmod(v, c->primes[c->n_q + kk] % q, q);
+            pm.push_back(v);
+            pm.push_back(hm::shoup_companion(v, q));
+        }
+        fc.pmod = DevBuf(pm.size() * 8, nullptr);
+        HEAR_CHECK_CUDA(cudaMemcpy(fc.pmod.p, pm.data(), pm.size() * 8, cudaMemcpyHostToDevice));
+    }
     const double ql = (double)c->primes[level];
     // diagonal plaintexts, pre-rotated by rho^(-j n1) (baby-step strategy re-association)
     std::vector<std::pair<uint32_t, uint32_t>> jobs;
@@ -340,9 +366,9 @@ void build_fc(hear_context *c, hear_model::Fc &fc, const double *W, uint32_t d_o
         for (size_t q = 0; q < cnt; q++) {
             uint32_t j = jobs[s0 + q].first, b = jobs[s0 + q].second;
             uint64_t *pt = fc.pts.u64() + ((size_t)j * n1 + b) * plane;
-            i64_to_limbs(c, (const int64_t *)dm.p + q * n, pt, L1, map_q(level, c->n_q), st);
-            ntt_forward(c, pt, L1, map_q(level, c->n_q), st);
-            to_mont(c, pt, L1, map_q(level, c->n_q), st);
+            i64_to_limbs(c, (const int64_t *)dm.p + q * n, pt, L1, pmap, st);
+            ntt_forward(c, pt, L1, pmap, st);
+            to_mont(c, pt, L1, pmap, st);
         }
         HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
     }
@@ -385,19 +411,33 @@ DevBuf eval_fc(const hear_model *m, const hear_model::Fc &fc, const hear_eval_ke
     hear_context *c = m->ctx;
     const uint32_t level = fc.level, n = c->n, L1 = level + 1, n1 = fc.n1, n2 = fc.n2, k = m->k;
     const uint64_t ctw = 2ull * L1 * n, batch = (uint64_t)n_ct * ctw;
-    // baby steps rho^(b k)(x), b < n1, hoisted; slot 0 holds x itself so that the inner
-    // sums read one contiguous [n1][n_ct] batch
-    DevBuf babies((size_t)n1 * batch * 8, st);
-    HEAR_CHECK_CUDA(cudaMemcpyAsync(babies.p, x, batch * 8, cudaMemcpyDeviceToDevice, st));
     std::vector<Rot> rots;
     for (uint32_t b = 1; b < n1; b++) {
         uint32_t g = galois_of(c, (int64_t)b * k);
         rots.push_back(Rot{need_key(evk, g), g});
     }
-    rotate_hoisted(c, level, n_ct, x, rots, babies.u64() + batch, st);
-    // giant-step inner sums sum_b pt_{j,b} (.) baby_b (lazy: no rescale yet)
     DevBuf G((size_t)n2 * batch * 8, st);
-    lincomb(c, level, n_ct, n1, n2, babies.u64(), fc.pts.u64(), G.u64(), st);
+    if (fc.dh) {
+        // hoisted ModDown: the babies stay over Q_l u P (slot 0 = P x), the inner sums are
+        // formed there with plaintexts over Q_l u P, and each giant-step sum is ModDowned
+        // once (ModDown(P a + b) = a + ModDown(b))
+        const uint32_t W = L1 + c->K;
+        const uint64_t batch_e = (uint64_t)n_ct * 2 * W * n;
+        DevBuf babies((size_t)n1 * batch_e * 8, st);
+        scale_p_ext(c, level, 2 * n_ct, x, babies.u64(), fc.pmod.u64(), st);
+        rotate_hoisted_ext(c, level, n_ct, x, rots, babies.u64() + batch_e, fc.pmod.u64(), st);
+        DevBuf Ge((size_t)n2 * batch_e * 8, st), tmp((size_t)n2 * batch * 8, st);
+        lincomb_ext(c, level, n_ct, n1, n2, babies.u64(), fc.pts.u64(), Ge.u64(), st);
+        moddown(c, level, n2 * n_ct, Ge.u64(), G.u64(), nullptr, 0, 0u, false, nullptr, 1, tmp.u64(), st);
+    } else {
+        // baby steps rho^(b k)(x), b < n1, hoisted; slot 0 holds x itself so that the inner
+        // sums read one contiguous [n1][n_ct] batch
+        DevBuf babies((size_t)n1 * batch * 8, st);
+        HEAR_CHECK_CUDA(cudaMemcpyAsync(babies.p, x, batch * 8, cudaMemcpyDeviceToDevice, st));
+        rotate_hoisted(c, level, n_ct, x, rots, babies.u64() + batch, st);
+        // giant-step inner sums sum_b pt_{j,b} (.) baby_b (lazy: no rescale yet)
+        lincomb(c, level, n_ct, n1, n2, babies.u64(), fc.pts.u64(), G.u64(), st);
+    }
     // giant rotations rho^(j n1 k), j >= 1, of the un-rescaled sums, then accumulate
     if (n2 > 1) {
         std::vector<Rot> gr;
@@ -419,7 +459,7 @@ DevBuf eval_fc(const hear_model *m, const hear_model::Fc &fc, const hear_eval_ke
 }  // namespace
 
 hear_model *model_create(hear_context *c, const hear_layer_desc *layers, size_t n_layers, uint32_t clip_dim,
-                         uint32_t start_level, uint32_t rotsum_radix) {
+                         uint32_t start_level, uint32_t rotsum_radix, uint32_t fc_n1, bool hoist_moddown) {
     HEAR_REQUIRE(rotsum_radix >= 2 && (rotsum_radix & (rotsum_radix - 1)) == 0 && rotsum_radix <= 64, HEAR_E_INVAL,
                  "rotsum radix must be a power of two in [2, 64]");
     HEAR_REQUIRE(layers && n_layers > 0, HEAR_E_INVAL, "no layers");
@@ -431,6 +471,8 @@ hear_model *model_create(hear_context *c, const hear_layer_desc *layers, size_t 
     m->ctx = c;
     m->clip_dim = clip_dim;
     m->rotsum_radix = rotsum_radix;
+    m->fc_n1 = fc_n1;
+    m->hoist_moddown = hoist_moddown;
     m->k = slots / clip_dim;
     m->M = clip_dim;
     uint32_t level = start_level, dim = clip_dim;
@@ -443,7 +485,7 @@ hear_model *model_create(hear_context *c, const hear_layer_desc *layers, size_t 
         if (d.kind == HEAR_LAYER_FC) {
             HEAR_REQUIRE(d.w && d.d_in == dim, HEAR_E_INVAL, "FC input dimension mismatch");
             HEAR_REQUIRE(!d.bias, HEAR_E_UNSUPPORTED, "bias is not supported");
-            build_fc(c, L.fc, d.w, d.d_out, d.d_in, level, m->k, m->M, rotsum_radix);
+            build_fc(c, L.fc, d.w, d.d_out, d.d_in, level, m->k, m->M, rotsum_radix, fc_n1, hoist_moddown);
             fc_rotations(L.fc, m->k, rots);
             level -= 1;
             dim = d.d_out;

@@ -12,7 +12,9 @@
 struct hear_model {
     struct Fc {
         uint32_t d_out = 0, d_in = 0, D = 0, n1 = 0, n2 = 0, level = 0;
-        hear::DevBuf pts;                           // [n2*n1][level+1][N] Montgomery, zero = no diagonal
+        bool dh = false;                            // hoisted ModDown: babies and inner sums over Q_l u P
+        hear::DevBuf pts;                           // [n2*n1][level+1 (+K if dh)][N] Montgomery, zero = no diagonal
+        hear::DevBuf pmod;                          // dh: ([P]_{q_t}, Shoup) for t <= level
         hear::DevBuf bias;                          // plaintext at level-1 (Montgomery), or empty
         std::vector<std::vector<int32_t>> rotsum;   // rotate-and-sum rounds (slot steps, hoisted per round)
     };
@@ -39,6 +41,8 @@ struct hear_model {
     hear_context *ctx = nullptr;
     uint32_t clip_dim = 0, k = 0, M = 0;
     uint32_t rotsum_radix = 8;                      // copies folded per rotate-and-sum round
+    uint32_t fc_n1 = 0;                             // FC baby steps (0 = smallest power of two with n1^2 >= D)
+    bool hoist_moddown = false;                     // FC babies kept over Q_l u P, one ModDown per giant sum
     mutable std::mutex plan_mu;
     mutable std::vector<std::unique_ptr<Plan>> plans;
     std::vector<Layer> layers;
@@ -72,6 +76,10 @@ struct Rot {
 // x[c] (hoisting); out is contiguous [R][n_ct][2][level+1][N]
 void rotate_hoisted(hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *x,
                     const std::vector<Rot> &rots, uint64_t *out, cudaStream_t st);
+// the hoisted rotations before ModDown: out_ext [R][n_ct][2][W][N] over Q_l u P holds
+// (P sigma_r(c0) + u0, u1); pmod = ([P]_{q_t}, Shoup) pairs
+void rotate_hoisted_ext(hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *x, const std::vector<Rot> &rots,
+                        uint64_t *out_ext, const uint64_t *pmod, cudaStream_t st);
 // out[r*C + c] = rho_r(x[r*C + c]): job r rotates its C ciphertexts with rots[r]
 void rotate_each(hear_context *c, uint32_t level, uint32_t R, uint32_t C, const uint64_t *x,
                  const std::vector<Rot> &rots, uint64_t *out, cudaStream_t st);
@@ -89,7 +97,8 @@ constexpr uint32_t kDefaultRotsumRadix = 8;
 // the network evaluated from input ciphertexts at start_level (every plaintext encoded at
 // the level where it is used)
 hear_model *model_create(hear_context *c, const hear_layer_desc *layers, size_t n_layers, uint32_t clip_dim,
-                         uint32_t start_level, uint32_t rotsum_radix = kDefaultRotsumRadix);
+                         uint32_t start_level, uint32_t rotsum_radix = kDefaultRotsumRadix, uint32_t fc_n1 = 0,
+                         bool hoist_moddown = false);
 // evaluate layers [l0, l1) on a batch x at the first layer's level; returns the output batch
 DevBuf evaluate_batch(const hear_model *m, const hear_eval_keys *evk, size_t l0, size_t l1, const uint64_t *x,
                       uint32_t n_ct, uint32_t *level_out, double scale_in, double *scale_out, cudaStream_t st);

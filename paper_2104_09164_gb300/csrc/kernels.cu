@@ -260,10 +260,11 @@ __device__ __forceinline__ void fold(u128 &acc, uint64_t q) {
 // With few ciphertexts (2C <= 4 polynomials, one CTA column) the warps beyond 2C would idle:
 // jw = 8 / 2C warps then share each polynomial, warp w taking polynomial w mod 2C and the
 // giant-step chunks (4 outputs each) jpart, jpart + jw, .. with jpart = w / 2C.
+// Limbs t >= lq are over the special primes (inner sums over Q_l u P): prime n_q + t - lq.
 __global__ void __launch_bounds__(256, 4) k_lincomb(uint32_t L1, uint32_t C, uint32_t n1, uint32_t n2,
                                                  const uint64_t *__restrict__ baby, const uint64_t *__restrict__ pt,
                                                  uint64_t *__restrict__ out, const DevPrime *P, uint32_t n,
-                                                 uint32_t jw) {
+                                                 uint32_t jw, uint32_t lq, uint32_t n_q) {
     const uint32_t w = threadIdx.x >> 5;
     uint32_t cp, jpart;                                           // cp = c * 2 + poly
     if (jw > 1) {
@@ -277,7 +278,8 @@ __global__ void __launch_bounds__(256, 4) k_lincomb(uint32_t L1, uint32_t C, uin
     }
     const uint32_t t = blockIdx.z, k = blockIdx.y * 32 + (threadIdx.x & 31);
     const uint64_t plane = (uint64_t)L1 * n, r = (uint64_t)t * n + k;
-    const uint64_t q = P[t].q, qinv = P[t].qinv;
+    const uint32_t pi = t < lq ? t : n_q + (t - lq);
+    const uint64_t q = P[pi].q, qinv = P[pi].qinv;
     const uint64_t bstride = 2ull * C * plane;                    // between baby steps / giant outputs
     const uint64_t *bp = baby + (uint64_t)cp * plane + r;
     for (uint32_t j0 = 4 * jpart; j0 < n2; j0 += 4 * jw) {
@@ -385,7 +387,7 @@ template <int MAXD, bool OWN>
 __global__ void __launch_bounds__(256, 3) k_ks_inner(const uint64_t *ext, int ext_per_job, const uint64_t *const *keys, const uint32_t *ginv,
                            uint64_t *out, uint32_t C, uint32_t L1, uint32_t W, uint32_t dnum, uint32_t n_q,
                            uint32_t nqp, uint32_t log_n, const DevPrime *P, const uint64_t *own,
-                           uint64_t own_stride) {
+                           uint64_t own_stride, const uint64_t *pc0, const uint64_t *pmod) {
     // grid y = job (varies before the limb, so the jobs of one limb run together and
     // share that limb's digit slice in L2), z = limb t of Q_l u P
     const uint32_t n = 1u << log_n, k = COEF(), r = blockIdx.y, t = blockIdx.z;
@@ -427,7 +429,11 @@ __global__ void __launch_bounds__(256, 3) k_ks_inner(const uint64_t *ext, int ex
         fold(a0, q);
         fold(a1, q);
         uint64_t *o = out + ((uint64_t)r * C + c) * out_ct + (uint64_t)t * n + kk;
-        o[0] = mont_reduce(a0, q, qinv);
+        uint64_t v0 = mont_reduce(a0, q, qinv);
+        // pc0 (outputs kept over Q_l u P): + P sigma_g(c0) = P c0[k] at position kk
+        if (pc0 && t < L1) v0 = add_mod(v0, shoup(pc0[cti * own_stride + (uint64_t)t * n + k], pmod[2 * t],
+                                                  pmod[2 * t + 1], q), q);
+        o[0] = v0;
         o[(uint64_t)W * n] = mont_reduce(a1, q, qinv);
     }
 }
@@ -439,7 +445,8 @@ template <int MAXD, bool OWN, int RJ>
 __global__ void __launch_bounds__(256, 3) k_ks_inner_rj(const uint64_t *ext, const uint64_t *const *keys,
                                                         const uint32_t *ginv, uint64_t *out, uint32_t R, uint32_t L1,
                                                         uint32_t W, uint32_t dnum, uint32_t n_q, uint32_t nqp,
-                                                        uint32_t log_n, const DevPrime *P, const uint64_t *own) {
+                                                        uint32_t log_n, const DevPrime *P, const uint64_t *own,
+                                                        const uint64_t *pc0, const uint64_t *pmod) {
     const uint32_t n = 1u << log_n, k = COEF(), r0 = blockIdx.y * RJ, t = blockIdx.z;
     const uint32_t pt = t < L1 ? t : n_q + (t - L1);
     const uint64_t q = P[pt].q, qinv = P[pt].qinv;
@@ -479,11 +486,22 @@ __global__ void __launch_bounds__(256, 3) k_ks_inner_rj(const uint64_t *ext, con
         const uint32_t g = ginv[r];
         const uint32_t kk = g == 1 ? k : auto_index(k, g, log_n);
         uint64_t *o = out + (uint64_t)r * out_ct + (uint64_t)t * n + kk;
-        o[0] = mont_reduce(a0, q, qinv);
+        uint64_t v0 = mont_reduce(a0, q, qinv);
+        if (pc0 && t < L1) v0 = add_mod(v0, shoup(pc0[(uint64_t)t * n + k], pmod[2 * t], pmod[2 * t + 1], q), q);
+        o[0] = v0;
         o[(uint64_t)W * n] = mont_reduce(a1, q, qinv);
     }
 }
 
+// P x over Q_l u P: limb t < L1 is [P]_{q_t} x_t (pmod = (value, Shoup) pairs), the special
+// limbs are zero.  y = limb t of W, z = polynomial.
+__global__ void k_scale_p_ext(const uint64_t *x, uint64_t *out, uint32_t L1, uint32_t W, const uint64_t *pmod,
+                              const DevPrime *P, uint32_t n) {
+    const uint32_t t = blockIdx.y, g = blockIdx.z, k = COEF();
+    uint64_t v = 0;
+    if (t < L1) v = shoup(x[((uint64_t)g * L1 + t) * n + k], pmod[2 * t], pmod[2 * t + 1], P[t].q);
+    out[((uint64_t)g * W + t) * n + k] = v;
+}
 // ModDown conversion, one thread per (group = y + z*gridDim.y, coefficient):
 // y_k = [x_{p_k} * phat_inv_k]_{p_k} once, conv_i = sum_k y_k * [P/p_k]_{q_i} mod q_i for
 // every i < L1 (x_P in the coefficient domain).
@@ -682,7 +700,18 @@ void lincomb(const hear_context *c, uint32_t level, uint32_t n_ct, uint32_t n1, 
     // algorithmic: every baby ciphertext, every plaintext and every output once
     const double bytes = 8.0 * L1 * c->n * (2.0 * n_ct * n1 + (double)n1 * n2 + 2.0 * n_ct * n2);
     const uint32_t jw = 2 * n_ct <= 4 ? 8 / (2 * n_ct) : 1;
-    LAUNCH3(k_lincomb, grid, 256, st, bytes, L1, n_ct, n1, n2, baby, pt, out, c->dev_primes(), c->n, jw);
+    LAUNCH3(k_lincomb, grid, 256, st, bytes, L1, n_ct, n1, n2, baby, pt, out, c->dev_primes(), c->n, jw, L1,
+            c->n_q);
+}
+void lincomb_ext(const hear_context *c, uint32_t level, uint32_t n_ct, uint32_t n1, uint32_t n2, const uint64_t *baby,
+                 const uint64_t *pt, uint64_t *out, cudaStream_t st) {
+    const uint32_t L1 = level + 1, W = L1 + c->K;
+    dim3 grid((2 * n_ct + 7) / 8, c->n / 32, W);
+    HEAR_REQUIRE(grid.x < (1u << 31), HEAR_E_UNSUPPORTED, "launch too large");
+    const double bytes = 8.0 * W * c->n * (2.0 * n_ct * n1 + (double)n1 * n2 + 2.0 * n_ct * n2);
+    const uint32_t jw = 2 * n_ct <= 4 ? 8 / (2 * n_ct) : 1;
+    LAUNCH3(k_lincomb, grid, 256, st, bytes, W, n_ct, n1, n2, baby, pt, out, c->dev_primes(), c->n, jw, L1,
+            c->n_q);
 }
 void mulplain(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *ct, const uint64_t *pt,
               uint64_t *out, cudaStream_t st) {
@@ -732,8 +761,10 @@ void modup(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t 
 
 void ks_inner(const hear_context *c, uint32_t level, uint32_t R, uint32_t C, const uint64_t *ext, bool ext_per_job,
               const uint64_t *const *d_keys, const uint32_t *d_ginv, uint64_t *out, const uint64_t *c1,
-              uint64_t c1_stride, cudaStream_t st) {
+              uint64_t c1_stride, cudaStream_t st, const uint64_t *pmod) {
     const uint64_t *own = c->alpha == 1 ? c1 : nullptr;
+    // with pmod: the outputs stay over Q_l u P and receive P sigma_g(c0), c0 = c1 - one plane
+    const uint64_t *pc0 = pmod ? c1 - (uint64_t)(level + 1) * c->n : nullptr;
     const uint32_t L1 = level + 1, W = L1 + c->K, dnum = c->dnum(level);
     check_yz(R, W);
     const double dn = dnum, wn = (double)W * c->n * 8.0;
@@ -744,7 +775,8 @@ void ks_inner(const hear_context *c, uint32_t level, uint32_t R, uint32_t C, con
     do {                                                                                                          \
         ProfScope ps__(c, NAME, st, bytes);                                                                       \
         k_ks_inner<D, O><<<grid, kBlock, 0, st>>>(ext, (int)ext_per_job, d_keys, d_ginv, out, C, L1, W, dnum,     \
-                                                  c->n_q, c->nqp(), c->log_n, c->dev_primes(), own, c1_stride);   \
+                                                  c->n_q, c->nqp(), c->log_n, c->dev_primes(), own, c1_stride,    \
+                                                  pc0, pmod);                                                     \
         HEAR_CHECK_CUDA(cudaGetLastError());                                                                      \
     } while (0)
     if (C == 1 && !ext_per_job && R >= 2 && dnum <= 8) {
@@ -753,10 +785,10 @@ void ks_inner(const hear_context *c, uint32_t level, uint32_t R, uint32_t C, con
         ProfScope ps__(c, "k_ks_inner<8>", st, bytes);
         if (own)
             k_ks_inner_rj<8, true, RJ><<<g4, kBlock, 0, st>>>(ext, d_keys, d_ginv, out, R, L1, W, dnum, c->n_q,
-                                                              c->nqp(), c->log_n, c->dev_primes(), own);
+                                                              c->nqp(), c->log_n, c->dev_primes(), own, pc0, pmod);
         else
             k_ks_inner_rj<8, false, RJ><<<g4, kBlock, 0, st>>>(ext, d_keys, d_ginv, out, R, L1, W, dnum, c->n_q,
-                                                               c->nqp(), c->log_n, c->dev_primes(), own);
+                                                               c->nqp(), c->log_n, c->dev_primes(), own, pc0, pmod);
         HEAR_CHECK_CUDA(cudaGetLastError());
         return;
     }
@@ -773,6 +805,13 @@ void ks_inner(const hear_context *c, uint32_t level, uint32_t R, uint32_t C, con
 #undef KS_LAUNCH
 }
 
+void scale_p_ext(const hear_context *c, uint32_t level, uint32_t n_polys, const uint64_t *x, uint64_t *out,
+                 const uint64_t *pmod, cudaStream_t st) {
+    const uint32_t L1 = level + 1, W = L1 + c->K;
+    check_yz(W, n_polys);
+    LAUNCH3(k_scale_p_ext, grid3(c->n, W, n_polys), kBlock, st, 8.0 * n_polys * ((double)L1 + W) * c->n, x, out, L1,
+            W, pmod, c->dev_primes(), c->n);
+}
 void moddown(const hear_context *c, uint32_t level, uint32_t n_ct, uint64_t *acc, uint64_t *out,
              const uint64_t *addend, uint64_t add_stride, uint32_t add_mask, bool add_shared, const uint32_t *d_gal,
              uint32_t cts_per_job, uint64_t *tmp, cudaStream_t st) {

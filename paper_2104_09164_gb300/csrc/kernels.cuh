@@ -48,6 +48,13 @@ void automorphism(const hear_context *c, uint32_t level, uint32_t n_polys_total,
 // diagonals), out [n2][n_ct][2][level+1][N]
 void lincomb(const hear_context *c, uint32_t level, uint32_t n_ct, uint32_t n1, uint32_t n2, const uint64_t *baby,
              const uint64_t *pt, uint64_t *out, cudaStream_t st);
+// the same over Q_l u P: baby [n1][n_ct][2][W][N], pt [n2*n1][W][N], out [n2][n_ct][2][W][N]
+void lincomb_ext(const hear_context *c, uint32_t level, uint32_t n_ct, uint32_t n1, uint32_t n2, const uint64_t *baby,
+                 const uint64_t *pt, uint64_t *out, cudaStream_t st);
+// P x over Q_l u P for n_polys polynomials x [.][l+1][N] -> out [.][W][N]; pmod = ([P]_{q_t},
+// Shoup) pairs for t <= l
+void scale_p_ext(const hear_context *c, uint32_t level, uint32_t n_polys, const uint64_t *x, uint64_t *out,
+                 const uint64_t *pmod, cudaStream_t st);
 // out (batch [n_ct][2][level+1][N]) = ct (batch) (.) pt   (pt Montgomery, no accumulation)
 void mulplain(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *ct, const uint64_t *pt,
               uint64_t *out, cudaStream_t st);
@@ -67,9 +74,11 @@ void modup(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t 
 // d_keys[r]: switching key stored sigma_{g_r}^{-1}-permuted; d_ginv[r] = g_r^{-1} mod 2N.
 // c1 / c1_stride: the polynomials modup() extended (with one-limb digits modup leaves each
 // digit's own limb there instead of copying it into ext)
+// pmod (optional, ([P]_{q_t}, Shoup) pairs): the outputs are the rotations before ModDown,
+// (P sigma_g(c0) + u0, u1) over Q_l u P, with c0 the plane before c1 (shared digits only)
 void ks_inner(const hear_context *c, uint32_t level, uint32_t R, uint32_t C, const uint64_t *ext, bool ext_per_job,
               const uint64_t *const *d_keys, const uint32_t *d_ginv, uint64_t *out, const uint64_t *c1,
-              uint64_t c1_stride, cudaStream_t st);
+              uint64_t c1_stride, cudaStream_t st, const uint64_t *pmod = nullptr);
 // ModDown of acc [n_ct][2][W][N] (destroys its P limbs) into out [n_ct][2][l+1][N], adding an
 // addend ciphertext (ciphertext index c, or c mod cts_per_job if add_shared, at addend +
 // index*add_stride, polys [2][l+1][N]; poly p only if add_mask bit p) gathered through

@@ -44,7 +44,8 @@ class hear_layer_desc(ctypes.Structure):
 
 
 class hear_model_opts(ctypes.Structure):
-    _fields_ = [("level", ctypes.c_uint32), ("rotsum_radix", ctypes.c_uint32)]
+    _fields_ = [("level", ctypes.c_uint32), ("rotsum_radix", ctypes.c_uint32), ("fc_n1", ctypes.c_uint32),
+                ("hoist_moddown", ctypes.c_uint32)]
 
 
 class hear_profile_entry(ctypes.Structure):
@@ -361,9 +362,10 @@ def hear_multiply_relin(evk, a, b, stream=None):
 
 
 # ---------------------------------------------------------------- network
-def hear_model_create(ctx, layers, clip_dim, level=None, rotsum_radix=None):
+def hear_model_create(ctx, layers, clip_dim, level=None, rotsum_radix=None, fc_n1=None, hoist_moddown=False):
     """layers: sequence of ("fc", W) | ("square",) | ("fc_sq_fc", W1, W2) with float64 matrices;
-    level: input level (None = the top level); rotsum_radix: see hear_model_opts"""
+    level: input level (None = the top level); rotsum_radix, fc_n1, hoist_moddown: see
+    hear_model_opts"""
     descs = (hear_layer_desc * len(layers))()
     keep = []
     for i, layer in enumerate(layers):
@@ -382,8 +384,8 @@ def hear_model_create(ctx, layers, clip_dim, level=None, rotsum_radix=None):
         else:
             raise ValueError(layer[0])
     h = _vp()
-    if rotsum_radix is not None:
-        opts = hear_model_opts(int(level or 0), int(rotsum_radix))
+    if rotsum_radix is not None or fc_n1 is not None or hoist_moddown:
+        opts = hear_model_opts(int(level or 0), int(rotsum_radix or 0), int(fc_n1 or 0), int(bool(hoist_moddown)))
         _check(lib.hear_model_create_ex(ctx, descs, len(layers), int(clip_dim), ctypes.byref(opts), ctypes.byref(h)))
     elif level is None:
         _check(lib.hear_model_create(ctx, descs, len(layers), int(clip_dim), ctypes.byref(h)))
