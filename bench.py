@@ -616,6 +616,8 @@ def main_gpu(a):
         # the NTT launch-variant table this run used (pin it with HEAR_NTT_TABLE to profile
         # the same kernels)
         result["config"]["ntt_table"] = H.hear_ntt_get_table(S.ctx)
+        # kernels captured with programmatic dependent launch so far (HEAR_PDL=0: none)
+        result["config"]["pdl_launches_captured"] = H.hear_pdl_launch_count()
     if result is not None and not a.no_served and a.workload == "small" and a.clips is None and dist.world == 1:
         sweep = run_served(H, S, [float(x) for x in a.rates.split(",")])
         result["served"] = {"workload": "small network, Poisson arrivals, 1-8 clips per request, "

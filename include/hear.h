@@ -390,6 +390,11 @@ hear_status hear_profile_begin(hear_context *ctx);
 hear_status hear_profile_end(hear_context *ctx, hear_profile_entry *out, size_t cap, size_t *n);
 /* kernel launches issued by the library (all contexts) since it was loaded */
 uint64_t hear_launch_count(void);
+/* kernel launches captured into CUDA graphs with programmatic dependent launch (the
+ * kernel may be scheduled while the one before it drains and waits on it on the device:
+ * every capture whose pending dependencies are all kernel nodes; HEAR_PDL=0 in the
+ * environment turns it off) since the library was loaded */
+uint64_t hear_pdl_launch_count(void);
 
 /* ---- NTT launch variants and their tuner ----
  * The forward / inverse NTT has four launch forms with bit-identical results:

@@ -607,6 +607,7 @@ hear_status hear_profile_end(hear_context *ctx, hear_profile_entry *out, size_t 
 }
 
 uint64_t hear_launch_count(void) { return hear::g_launches.load(); }
+uint64_t hear_pdl_launch_count(void) { return hear::g_pdl_launches.load(); }
 
 hear_status hear_dbg_poly_mul(hear_context *ctx, uint32_t prime, const uint64_t *a, const uint64_t *b, uint64_t *out) {
     if (!ctx || !a || !b || !out) return fail(HEAR_E_INVAL, "null argument");

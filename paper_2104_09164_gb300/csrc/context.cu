@@ -8,8 +8,10 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <cstdlib>
 #include "internal.h"
 #include "hostmath.h"
+#include "launch.cuh"
 
 namespace hear {
 
@@ -43,6 +45,33 @@ DevBuf &DevBuf::operator=(DevBuf &&o) noexcept {
 }
 
 std::atomic<uint64_t> g_launches{0};
+std::atomic<uint64_t> g_pdl_launches{0};
+
+bool pdl_allowed(cudaStream_t st) {
+    static const bool enabled = [] {
+        const char *e = std::getenv("HEAR_PDL");
+        return !(e && e[0] == '0');
+    }();
+    if (!enabled) return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *edges = nullptr;
+    size_t nd = 0;
+    if (cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, &edges, &nd) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (cs != cudaStreamCaptureStatusActive || nd == 0) return false;
+    for (size_t i = 0; i < nd; i++) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(deps[i], &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) {
+            cudaGetLastError();
+            return false;
+        }
+    }
+    g_pdl_launches++;
+    return true;
+}
 
 cudaEvent_t Profiler::get() {
     if (!spare.empty()) {

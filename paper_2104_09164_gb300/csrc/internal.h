@@ -98,6 +98,7 @@ struct Profiler {
 
 // total kernel launches issued by the library since it was loaded
 extern std::atomic<uint64_t> g_launches;
+extern std::atomic<uint64_t> g_pdl_launches;
 
 }  // namespace hear
 

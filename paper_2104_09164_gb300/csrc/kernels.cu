@@ -6,6 +6,7 @@
 // of ntt.cu: index i holds the evaluation at psi^(2 brv(i) + 1).
 #include "kernels.cuh"
 #include "modarith.cuh"
+#include "launch.cuh"
 
 namespace hear {
 namespace {
@@ -29,6 +30,7 @@ __device__ __forceinline__ uint32_t limb_yz() { return blockIdx.y + blockIdx.z *
 
 // ------------------------------------------------------------------ representation
 __global__ void k_to_mont(uint64_t *d, uint32_t n_limbs, LimbMap m, const DevPrime *P, uint32_t n, int dir) {
+    pdl_enter();
     uint32_t b = limb_yz(), pi;
     if (b >= n_limbs || !m.resolve(b, &pi)) return;
     const DevPrime p = P[pi];
@@ -38,6 +40,7 @@ __global__ void k_to_mont(uint64_t *d, uint32_t n_limbs, LimbMap m, const DevPri
 
 __global__ void k_pointwise_mont(const uint64_t *a, const uint64_t *b, uint64_t *out, uint32_t n_limbs, LimbMap m,
                                  const DevPrime *P, uint32_t n) {
+    pdl_enter();
     uint32_t bb = limb_yz(), pi;
     if (bb >= n_limbs || !m.resolve(bb, &pi)) return;
     const DevPrime p = P[pi];
@@ -47,6 +50,7 @@ __global__ void k_pointwise_mont(const uint64_t *a, const uint64_t *b, uint64_t 
 
 __global__ void k_small_to_limbs(const int8_t *e, uint64_t *out, uint32_t n_limbs, LimbMap m, const DevPrime *P,
                                  uint32_t n) {
+    pdl_enter();
     uint32_t b = limb_yz(), pi, k = COEF();
     if (b >= n_limbs || !m.resolve(b, &pi)) return;
     int v = e[k];
@@ -57,6 +61,7 @@ __global__ void k_small_to_limbs(const int8_t *e, uint64_t *out, uint32_t n_limb
 // group g of the limb map reads v + g * v_stride (v_stride 0: one vector for every limb)
 __global__ void k_i64_to_limbs(const int64_t *v, uint64_t *out, uint32_t n_limbs, LimbMap m, const DevPrime *P,
                                uint32_t n, uint64_t v_stride) {
+    pdl_enter();
     uint32_t b = limb_yz(), pi, k = COEF();
     if (b >= n_limbs || !m.resolve(b, &pi)) return;
     const DevPrime p = P[pi];
@@ -101,6 +106,7 @@ __device__ void chacha_words(uint64_t seed, uint32_t purpose, uint64_t index, ui
 
 __global__ void k_sample_small(uint64_t seed, uint32_t purpose, uint64_t index, uint32_t n, int kind,
                                const uint64_t *cdt, uint32_t cdt_n, int8_t *out) {
+    pdl_enter();
     uint32_t blk = blockIdx.x * blockDim.x + threadIdx.x;
     if (blk >= n / 8) return;
     uint64_t w[8];
@@ -124,6 +130,7 @@ __global__ void k_sample_small(uint64_t seed, uint32_t purpose, uint64_t index, 
 // index_base | prime(b); one thread per ChaCha20 block (four coefficients)
 __global__ void k_sample_uniform(uint64_t seed, uint32_t purpose, uint64_t index_base, uint64_t *out,
                                  uint32_t n_limbs, LimbMap m, const DevPrime *P, uint32_t n) {
+    pdl_enter();
     uint32_t b = limb_yz(), pi, blk = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n_limbs || blk >= n / 4 || !m.resolve(b, &pi)) return;
     const DevPrime p = P[pi];
@@ -138,6 +145,7 @@ __global__ void k_sample_uniform(uint64_t seed, uint32_t purpose, uint64_t index
 // y = limb (prime index == limb index in these layouts)
 __global__ void k_pk_combine(const uint64_t *a, const uint64_t *s_mont, const uint64_t *e, uint64_t *b,
                              const DevPrime *P, uint32_t n) {
+    pdl_enter();
     const DevPrime p = P[blockIdx.y];
     uint64_t i = (uint64_t)blockIdx.y * n + COEF();
     b[i] = sub_mod(e[i], mont_mul(a[i], s_mont[i], p.q, p.qinv), p.q);
@@ -146,6 +154,7 @@ __global__ void k_pk_combine(const uint64_t *a, const uint64_t *s_mont, const ui
 __global__ void k_swk_combine(const uint64_t *a, const uint64_t *s_mont, const uint64_t *e, const uint64_t *sp_mont,
                               const uint64_t *p_mod, uint32_t lo, uint32_t hi, const DevPrime *P, uint32_t n,
                               uint64_t *b) {
+    pdl_enter();
     const uint32_t t = blockIdx.y;
     const DevPrime p = P[t];
     uint64_t i = (uint64_t)t * n + COEF();
@@ -157,6 +166,7 @@ __global__ void k_swk_combine(const uint64_t *a, const uint64_t *s_mont, const u
 __global__ void k_encrypt_combine(const uint64_t *v, const uint64_t *e0, const uint64_t *e1, const uint64_t *m,
                                   const uint64_t *pk_mont, uint64_t *ct, uint64_t limbs, const DevPrime *P,
                                   uint32_t n) {
+    pdl_enter();
     const DevPrime p = P[blockIdx.y];
     uint64_t i = (uint64_t)blockIdx.y * n + COEF();
     ct[i] = add_mod(add_mod(mont_mul(v[i], pk_mont[i], p.q, p.qinv), e0[i], p.q), m[i], p.q);
@@ -165,6 +175,7 @@ __global__ void k_encrypt_combine(const uint64_t *v, const uint64_t *e0, const u
 
 __global__ void k_decrypt_combine(const uint64_t *ct, const uint64_t *s_mont, uint64_t *out, uint64_t limbs,
                                   const DevPrime *P, uint32_t n) {
+    pdl_enter();
     const DevPrime p = P[blockIdx.y];
     uint64_t i = (uint64_t)blockIdx.y * n + COEF();
     out[i] = add_mod(ct[i], mont_mul(ct[limbs + i], s_mont[i], p.q, p.qinv), p.q);
@@ -174,6 +185,7 @@ __global__ void k_decrypt_combine(const uint64_t *ct, const uint64_t *s_mont, ui
 // y = limb t, z = polynomial
 __global__ void k_add(const uint64_t *a, const uint64_t *b, uint64_t *out, uint32_t L1, const DevPrime *P,
                       uint32_t n) {
+    pdl_enter();
     uint64_t i = ((uint64_t)blockIdx.z * L1 + blockIdx.y) * n + COEF();
     out[i] = add_mod(a[i], b[i], P[blockIdx.y].q);
 }
@@ -182,6 +194,7 @@ __global__ void k_add(const uint64_t *a, const uint64_t *b, uint64_t *out, uint3
 // (base = null) or out = base + a_0 + ... + a_{cnt-1}
 __global__ void k_sum(const uint64_t *a, uint64_t stride, uint32_t cnt, const uint64_t *base, uint64_t *out,
                       uint32_t L1, const DevPrime *P, uint32_t n) {
+    pdl_enter();
     uint64_t i = ((uint64_t)blockIdx.z * L1 + blockIdx.y) * n + COEF();
     const uint64_t q = P[blockIdx.y].q;
     uint64_t s = base ? base[i] : 0;
@@ -192,6 +205,7 @@ __global__ void k_sum(const uint64_t *a, uint64_t stride, uint32_t cnt, const ui
 // y = limb t, z = ciphertext
 __global__ void k_tensor(const uint64_t *a, const uint64_t *b, uint64_t *out, uint32_t L1, const DevPrime *P,
                          uint32_t n) {
+    pdl_enter();
     const uint64_t plane = (uint64_t)L1 * n, c = blockIdx.z;
     const uint64_t r = (uint64_t)blockIdx.y * n + COEF();
     const DevPrime p = P[blockIdx.y];
@@ -208,6 +222,7 @@ __global__ void k_tensor(const uint64_t *a, const uint64_t *b, uint64_t *out, ui
 // y + z * gridDim.y = limb of the whole batch
 __global__ void k_automorphism(const uint64_t *in, uint64_t *out, uint32_t n_limbs, uint32_t galois,
                                uint32_t log_n) {
+    pdl_enter();
     uint32_t b = limb_yz(), k = COEF();
     if (b >= n_limbs) return;
     const uint64_t base = (uint64_t)b << log_n;
@@ -265,6 +280,7 @@ __global__ void __launch_bounds__(256, 4) k_lincomb(uint32_t L1, uint32_t C, uin
                                                  const uint64_t *__restrict__ baby, const uint64_t *__restrict__ pt,
                                                  uint64_t *__restrict__ out, const DevPrime *P, uint32_t n,
                                                  uint32_t jw, uint32_t lq, uint32_t n_q) {
+    pdl_enter();
     const uint32_t w = threadIdx.x >> 5;
     uint32_t cp, jpart;                                           // cp = c * 2 + poly
     if (jw > 1) {
@@ -323,6 +339,7 @@ __global__ void __launch_bounds__(256, 4) k_lincomb(uint32_t L1, uint32_t C, uin
 // y = poly*L1 + limb, z = ciphertext; ciphertext z meets plaintext z / cts_per_pt
 __global__ void k_mulplain(const uint64_t *ct, const uint64_t *pt, uint64_t *out, uint32_t L1, const DevPrime *P,
                            uint32_t n, uint32_t cts_per_pt) {
+    pdl_enter();
     const uint32_t t = blockIdx.y % L1;
     const DevPrime p = P[t];
     const uint64_t i = ((uint64_t)blockIdx.z * 2 * L1 + blockIdx.y) * n + COEF();
@@ -333,6 +350,7 @@ __global__ void k_mulplain(const uint64_t *ct, const uint64_t *pt, uint64_t *out
 // c0 of ciphertext z += plaintext z / cts_per_pt (normal NTT form); y = limb
 __global__ void k_add_plain(uint64_t *ct, const uint64_t *pt, uint32_t L1, const DevPrime *P, uint32_t n,
                             uint32_t cts_per_pt) {
+    pdl_enter();
     const uint32_t t = blockIdx.y;
     const uint64_t i = ((uint64_t)blockIdx.z * 2 * L1 + t) * n + COEF();
     const uint64_t *pz = pt + (uint64_t)(blockIdx.z / cts_per_pt) * L1 * n;
@@ -347,6 +365,7 @@ __global__ void k_add_plain(uint64_t *ct, const uint64_t *pt, uint32_t L1, const
 __global__ void k_modup_conv(const uint64_t *c1, uint64_t c1_stride, const uint64_t *y, uint64_t *ext,
                              uint32_t L1, uint32_t W, uint32_t dnum, uint32_t alpha, uint32_t n_q,
                              const uint64_t *qhat_inv, const uint64_t *qhat_mod, const DevPrime *P, uint32_t n) {
+    pdl_enter();
     const uint32_t k = COEF(), j = blockIdx.y, c = blockIdx.z;
     const uint32_t lo = j * alpha, hi = min(lo + alpha, L1);
     uint64_t *e = ext + ((uint64_t)c * dnum + j) * W * n + k;
@@ -388,6 +407,7 @@ __global__ void __launch_bounds__(256, 3) k_ks_inner(const uint64_t *ext, int ex
                            uint64_t *out, uint32_t C, uint32_t L1, uint32_t W, uint32_t dnum, uint32_t n_q,
                            uint32_t nqp, uint32_t log_n, const DevPrime *P, const uint64_t *own,
                            uint64_t own_stride, const uint64_t *pc0, const uint64_t *pmod) {
+    pdl_enter();
     // grid y = job (varies before the limb, so the jobs of one limb run together and
     // share that limb's digit slice in L2), z = limb t of Q_l u P
     const uint32_t n = 1u << log_n, k = COEF(), r = blockIdx.y, t = blockIdx.z;
@@ -447,6 +467,7 @@ __global__ void __launch_bounds__(256, 3) k_ks_inner_rj(const uint64_t *ext, con
                                                         uint32_t W, uint32_t dnum, uint32_t n_q, uint32_t nqp,
                                                         uint32_t log_n, const DevPrime *P, const uint64_t *own,
                                                         const uint64_t *pc0, const uint64_t *pmod) {
+    pdl_enter();
     const uint32_t n = 1u << log_n, k = COEF(), r0 = blockIdx.y * RJ, t = blockIdx.z;
     const uint32_t pt = t < L1 ? t : n_q + (t - L1);
     const uint64_t q = P[pt].q, qinv = P[pt].qinv;
@@ -497,6 +518,7 @@ __global__ void __launch_bounds__(256, 3) k_ks_inner_rj(const uint64_t *ext, con
 // limbs are zero.  y = limb t of W, z = polynomial.
 __global__ void k_scale_p_ext(const uint64_t *x, uint64_t *out, uint32_t L1, uint32_t W, const uint64_t *pmod,
                               const DevPrime *P, uint32_t n) {
+    pdl_enter();
     const uint32_t t = blockIdx.y, g = blockIdx.z, k = COEF();
     uint64_t v = 0;
     if (t < L1) v = shoup(x[((uint64_t)g * L1 + t) * n + k], pmod[2 * t], pmod[2 * t + 1], P[t].q);
@@ -508,6 +530,7 @@ __global__ void k_scale_p_ext(const uint64_t *x, uint64_t *out, uint32_t L1, uin
 __global__ void k_moddown_conv(const uint64_t *acc, uint64_t *tmp, uint32_t n_groups, uint32_t L1, uint32_t W,
                                uint32_t K, uint32_t n_q, const uint64_t *phat_inv, const uint64_t *phat_mod,
                                const DevPrime *P, uint32_t n) {
+    pdl_enter();
     const uint32_t g = limb_yz(), k = COEF();
     if (g >= n_groups) return;
     uint64_t ys[4] = {0, 0, 0, 0};
@@ -537,6 +560,7 @@ __global__ void k_moddown_combine(const uint64_t *acc, const uint64_t *tmp, uint
                                   uint64_t add_stride, uint32_t add_mask, uint32_t add_shared, const uint32_t *gal,
                                   uint32_t cts_per_job, uint32_t L1, uint32_t W, const uint64_t *p_inv,
                                   const DevPrime *P, uint32_t log_n) {
+    pdl_enter();
     const uint32_t n = 1u << log_n, k = COEF(), t = blockIdx.y, g = blockIdx.z;
     const DevPrime p = P[t];
     const uint64_t i = ((uint64_t)g * L1 + t) * n + k;
@@ -555,6 +579,7 @@ __global__ void k_moddown_combine(const uint64_t *acc, const uint64_t *tmp, uint
 // y = limb t < l, z = polynomial
 __global__ void k_rescale_combine(const uint64_t *in, const uint64_t *tmp, uint64_t *out, uint32_t L1,
                                   const uint64_t *ql_inv, const DevPrime *P, uint32_t n) {
+    pdl_enter();
     const uint32_t l = L1 - 1, k = COEF(), t = blockIdx.y, g = blockIdx.z;
     const DevPrime p = P[t];
     const uint64_t i = ((uint64_t)g * l + t) * n + k;
@@ -582,8 +607,7 @@ void check_yz(uint32_t y, uint32_t z) {
 #define LAUNCH3(kernel, grid, block, st, bytes, ...)                                      \
     do {                                                                                  \
         ProfScope ps__(c, #kernel, st, (double)(bytes));                                   \
-        kernel<<<grid, block, 0, st>>>(__VA_ARGS__);                                       \
-        HEAR_CHECK_CUDA(cudaGetLastError());                                               \
+        launch(kernel, grid, block, 0, st, __VA_ARGS__);                                   \
     } while (0)
 
 void to_mont(const hear_context *c, uint64_t *d, uint32_t n_limbs, LimbMap m, cudaStream_t s) {
@@ -774,20 +798,18 @@ void ks_inner(const hear_context *c, uint32_t level, uint32_t R, uint32_t C, con
 #define KS_LAUNCH(NAME, D, O)                                                                                    \
     do {                                                                                                          \
         ProfScope ps__(c, NAME, st, bytes);                                                                       \
-        k_ks_inner<D, O><<<grid, kBlock, 0, st>>>(ext, (int)ext_per_job, d_keys, d_ginv, out, C, L1, W, dnum,     \
-                                                  c->n_q, c->nqp(), c->log_n, c->dev_primes(), own, c1_stride,    \
-                                                  pc0, pmod);                                                     \
-        HEAR_CHECK_CUDA(cudaGetLastError());                                                                      \
+        launch(k_ks_inner<D, O>, grid, kBlock, 0, st, ext, (int)ext_per_job, d_keys, d_ginv, out, C, L1, W, dnum, \
+               c->n_q, c->nqp(), c->log_n, c->dev_primes(), own, c1_stride, pc0, pmod);                           \
     } while (0)
     if (C == 1 && !ext_per_job && R >= 2 && dnum <= 8) {
         constexpr int RJ = 4;
         const dim3 g4(c->n / kBlock, (R + RJ - 1) / RJ, W);
         ProfScope ps__(c, "k_ks_inner<8>", st, bytes);
         if (own)
-            k_ks_inner_rj<8, true, RJ><<<g4, kBlock, 0, st>>>(ext, d_keys, d_ginv, out, R, L1, W, dnum, c->n_q,
+            launch(k_ks_inner_rj<8, true, RJ>, g4, kBlock, 0, st, ext, d_keys, d_ginv, out, R, L1, W, dnum, c->n_q,
                                                               c->nqp(), c->log_n, c->dev_primes(), own, pc0, pmod);
         else
-            k_ks_inner_rj<8, false, RJ><<<g4, kBlock, 0, st>>>(ext, d_keys, d_ginv, out, R, L1, W, dnum, c->n_q,
+            launch(k_ks_inner_rj<8, false, RJ>, g4, kBlock, 0, st, ext, d_keys, d_ginv, out, R, L1, W, dnum, c->n_q,
                                                                c->nqp(), c->log_n, c->dev_primes(), own, pc0, pmod);
         HEAR_CHECK_CUDA(cudaGetLastError());
         return;

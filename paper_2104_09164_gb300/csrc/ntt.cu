@@ -18,6 +18,7 @@
 #include <mutex>
 #include "internal.h"
 #include "modarith.cuh"
+#include "launch.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -235,6 +236,7 @@ __device__ __forceinline__ void load_twiddles(uint64_t *stw, const uint64_t *tw,
 // Pass A: strided columns, stages 0..LOGR-1 (forward) or LOGR-1..0 (inverse, + N^-1).
 template <int LOGR, bool FWD, int MODE, int DONE0>
 __global__ void __launch_bounds__(Tile<LOGR, MODE>::THREADS, Tile<LOGR, MODE>::MIN_CTAS) ntt_pass_a(PassArgs a) {
+    pdl_enter();
     constexpr int TILE = Tile<LOGR, MODE>::WORDS;
     __shared__ uint64_t s[TILE];
     constexpr int R = 1 << LOGR;
@@ -278,6 +280,7 @@ __global__ void __launch_bounds__(Tile<LOGR, MODE>::THREADS, Tile<LOGR, MODE>::M
 template <int LOGR, bool FWD, int MODE>
 __global__ void __launch_bounds__(Tile<LOGR, MODE>::THREADS, Tile<LOGR, MODE>::MIN_CTAS) ntt_pass_b(PassArgs a,
                                                                                                uint32_t s_off) {
+    pdl_enter();
     constexpr int TILE = Tile<LOGR, MODE>::WORDS;
     __shared__ uint64_t s[TILE];
     constexpr int R = 1 << LOGR;
@@ -340,6 +343,7 @@ template <int LA, int LB, int CL> struct Fused {
 template <int LA, int LB, bool FWD, int CL>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(Fused<LA, LB, CL>::THREADS, 512 / Fused<LA, LB, CL>::THREADS)
 ntt_fused(PassArgs a) {
+    pdl_enter();
     using F = Fused<LA, LB, CL>;
     constexpr int TILE = F::TILE, CA = F::CA, RA = F::RA, RB = F::RB, SB = F::SB, THREADS = F::THREADS;
     extern __shared__ uint64_t smem[];
@@ -433,7 +437,7 @@ void launch_fused(const PassArgs &a, cudaStream_t st) {
                                         (int)F::SMEM);
     });
     HEAR_CHECK_CUDA(attr_err);
-    ntt_fused<LA, LB, FWD, kCluster><<<a.n_limbs * kCluster, F::THREADS, F::SMEM, st>>>(a);
+    launch(ntt_fused<LA, LB, FWD, kCluster>, a.n_limbs * kCluster, F::THREADS, F::SMEM, st, a);
 }
 
 // a launch whose wide tiles would not give every SM two CTAs runs the narrow variant
@@ -441,13 +445,15 @@ constexpr uint32_t kNarrowBelow = 2 * 152;
 
 template <int A, int B, int MODE>
 void launch_fwd_t(const PassArgs &a, cudaStream_t st) {
-    ntt_pass_a<A, true, MODE, 0><<<a.n_limbs * (a.n / Tile<A, MODE>::WORDS), Tile<A, MODE>::THREADS, 0, st>>>(a);
-    ntt_pass_b<B, true, MODE><<<a.n_limbs * (a.n / Tile<B, MODE>::WORDS), Tile<B, MODE>::THREADS, 0, st>>>(a, A);
+    launch(ntt_pass_a<A, true, MODE, 0>, a.n_limbs * (a.n / Tile<A, MODE>::WORDS), Tile<A, MODE>::THREADS, 0, st, a);
+    launch(ntt_pass_b<B, true, MODE>, a.n_limbs * (a.n / Tile<B, MODE>::WORDS), Tile<B, MODE>::THREADS, 0, st, a,
+           (uint32_t)A);
 }
 template <int A, int B, int MODE>
 void launch_inv_t(const PassArgs &a, cudaStream_t st) {
-    ntt_pass_b<B, false, MODE><<<a.n_limbs * (a.n / Tile<B, MODE>::WORDS), Tile<B, MODE>::THREADS, 0, st>>>(a, A);
-    ntt_pass_a<A, false, MODE, B><<<a.n_limbs * (a.n / Tile<A, MODE>::WORDS), Tile<A, MODE>::THREADS, 0, st>>>(a);
+    launch(ntt_pass_b<B, false, MODE>, a.n_limbs * (a.n / Tile<B, MODE>::WORDS), Tile<B, MODE>::THREADS, 0, st, a,
+           (uint32_t)A);
+    launch(ntt_pass_a<A, false, MODE, B>, a.n_limbs * (a.n / Tile<A, MODE>::WORDS), Tile<A, MODE>::THREADS, 0, st, a);
 }
 // variant of a launch of n_limbs limbs: the context's table (filled by the tuner) or the
 // default rule (narrow two-pass below two wide CTAs per SM, wide two-pass above)

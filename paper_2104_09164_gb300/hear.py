@@ -161,6 +161,7 @@ def _load():
         "hear_profile_begin": (st, [_vp]),
         "hear_profile_end": (st, [_vp, ctypes.POINTER(hear_profile_entry), ctypes.c_size_t, _szp]),
         "hear_launch_count": (ctypes.c_uint64, []),
+        "hear_pdl_launch_count": (ctypes.c_uint64, []),
         "hear_ntt_tune": (st, [_vp, ctypes.c_uint32, ctypes.c_int, ctypes.POINTER(ctypes.c_uint8),
                                ctypes.POINTER(ctypes.c_float)]),
         "hear_ntt_set_variant": (st, [_vp, ctypes.c_int]),
@@ -610,6 +611,10 @@ def hear_profile_end(ctx):
 
 def hear_launch_count():
     return int(lib.hear_launch_count())
+
+
+def hear_pdl_launch_count():
+    return int(lib.hear_pdl_launch_count())
 
 
 # ---------------------------------------------------------------- debug
