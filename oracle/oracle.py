@@ -16,7 +16,12 @@ ctypes) and the composition below follows the paper step by step:
   level at which it is used;
 * FC layer (Methods, "Non-convolutional layers"), polynomial activation x^2, and the
   collapse of adjacent layers into one polynomial evaluation (same paragraph);
-* data encryption with interlaced copies (Methods, "Data encryption").
+* data encryption with interlaced copies (Methods, "Data encryption");
+* slot-batched evaluation of the same FC / x^2 networks (one clip per slot, one
+  ciphertext per feature): the FC layer of Methods "Non-convolutional layers" becomes a
+  sum of ciphertexts times plaintext scalars, each scalar the encoding of a constant slot
+  vector (the canonical embedding maps a constant polynomial c to c in every slot), with
+  one lazy rescale per output and no rotation.
 
 Ciphertexts here are numpy uint64 arrays [n_poly][level+1][N] in the oracle's own NTT
 domain; ``to_coeff`` gives the coefficient domain used for every comparison.
@@ -24,6 +29,7 @@ domain; ``to_coeff`` gives the coefficient domain used for every comparison.
 import ctypes
 import math
 import os
+from fractions import Fraction
 from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
@@ -557,6 +563,95 @@ class Oracle:
             else:
                 raise ValueError(layer[0])
         return ct
+
+    # ---------------- slot-batched evaluation (one clip per slot) ----------------
+    def scalar_residues(self, w, level):
+        """The plaintext scalar for weight w at scale q_level: the constant slot vector w
+        encodes to the constant polynomial round(w q_level), rounded exactly with ties away
+        from zero like the encoder, i.e. one residue per limb t <= level.
+        w: float array of any shape -> uint64 [..., level+1]."""
+        w = np.asarray(w, dtype=np.float64)
+        ql = self.q[level]
+        c = []
+        for v in w.ravel():
+            f = Fraction(float(v)) * ql
+            mag = (2 * abs(f.numerator) + f.denominator) // (2 * f.denominator)
+            c.append(-mag if f.numerator < 0 else mag)
+        out = np.empty((len(c), level + 1), dtype=np.uint64)
+        for t in range(level + 1):
+            qt = self.q[t]
+            out[:, t] = [x % qt for x in c]
+        return out.reshape(w.shape + (level + 1,))
+
+    def mul_scalar(self, ct: Ct, res, pt_scale):
+        """ct times the constant polynomial with residues res[t]: in the NTT domain every
+        evaluation of limb t is multiplied by res[t]"""
+        pt = np.repeat(np.asarray(res, dtype=np.uint64)[:ct.level + 1, None], self.n, axis=1)
+        return self.mulplain(ct, pt, pt_scale)
+
+    def encrypt_simd(self, pk, X, seed, scale):
+        """Clips X [n_clips][d] (n_clips <= N/2) -> d ciphertexts; ciphertext i encrypts
+        the slot vector (X[0][i], .., X[n_clips-1][i], 0, ..) with randomness stream i"""
+        X = np.asarray(X, dtype=np.float64)
+        assert X.shape[0] <= self.n // 2
+        out = []
+        for i in range(X.shape[1]):
+            z = np.zeros(self.n // 2)
+            z[:X.shape[0]] = X[:, i]
+            out.append(self.encrypt(pk, z, seed, i, scale))
+        return out
+
+    def fc_simd(self, cts, W):
+        """FC layer with one clip per slot: y_o = rescale(sum_i [W[o,i]]_{q_l} x_i), the
+        scalars at scale q_l (lazy rescaling: the products are summed, then rescaled once)"""
+        W = np.asarray(W, dtype=np.float64)
+        d_out, d_in = W.shape
+        assert len(cts) == d_in
+        level = cts[0].level
+        R = self.scalar_residues(W, level)
+        ql = float(self.q[level])
+        out = []
+        for o in range(d_out):
+            acc = self.mul_scalar(cts[0], R[o, 0], ql)
+            for i in range(1, d_in):
+                acc = self.add(acc, self.mul_scalar(cts[i], R[o, i], ql))
+            out.append(self.rescale(acc))
+        return out
+
+    def fc_sq_fc_simd(self, cts, W1, W2, keys: Keys):
+        """Collapsed FC -> x^2 -> FC with one clip per slot: out_c = sum_r W2[c,r] y_r^2,
+        y = W1 x, as sum_r y_r * u_(c,r) with u_(c,r) = U[(c,r)] x, U[(c,r), :] =
+        W2[c, r] W1[r, :] (both FC outputs one level down), the degree-2 products summed
+        over r before one relinearisation and one rescale per output"""
+        W1 = np.asarray(W1, dtype=np.float64)
+        W2 = np.asarray(W2, dtype=np.float64)
+        d1, d2 = W1.shape[0], W2.shape[0]
+        U = (W2[:, :, None] * W1[None, :, :]).reshape(d2 * d1, W1.shape[1])
+        y = self.fc_simd(cts, W1)
+        u = self.fc_simd(cts, U)
+        out = []
+        for c in range(d2):
+            t = self.tensor(y[0], u[c * d1])
+            for r in range(1, d1):
+                t = self.add(t, self.tensor(y[r], u[c * d1 + r]))
+            out.append(self.rescale(self.relinearize(t, keys)))
+        return out
+
+    def evaluate_simd(self, layers, cts, keys: Keys):
+        for layer in layers:
+            if layer[0] == "fc":
+                cts = self.fc_simd(cts, layer[1])
+            elif layer[0] == "square":
+                cts = [self.square(c, keys) for c in cts]
+            elif layer[0] == "fc_sq_fc":
+                cts = self.fc_sq_fc_simd(cts, layer[1], layer[2], keys)
+            else:
+                raise ValueError(layer[0])
+        return cts
+
+    def decrypt_simd(self, keys, cts, n_clips):
+        """-> [n_clips][len(cts)]: slot c of ciphertext o is output o of clip c"""
+        return np.stack([self.decrypt(keys, ct)[:n_clips] for ct in cts], axis=1)
 
 
 def rotsum_steps(step, count, radix):

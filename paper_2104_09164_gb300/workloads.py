@@ -7,7 +7,7 @@ The paper evaluates skeleton CNNs on a private test set (608 clips of 2x32x15
 min-max-normalised joint coordinates, Methods "Data preprocessing"); that data and the
 trained weights are not available, so these synthetic inputs stand in for them:
 
-* ``toy``   -- N = 2^12, q = 50 + 40 + 40 bits, one 50-bit special prime; one 64-dim
+* ``toy``   -- N = 2^12, q = 50 + 40 + 40 bits, one 50-bit special prime; 64-dim (one by default)
   input uniform in [-1, 1]; FC 64->16 -> x^2 -> FC 16->2 with N(0, 0.1^2) weights.
 * ``small`` -- N = 2^14, q = 60 + 7x40 bits, one 60-bit special prime; one clip of
   16 frames x 128 features ~ N(0,1) clipped to [-1, 1]; FC 2048->128 -> x^2 -> FC 128->2.
@@ -103,7 +103,8 @@ def make_workload(name: str, n_clips: int = None) -> Workload:
         # the activation and the second FC are collapsed into one quadratic form.
         w.layers = [("fc_sq_fc", W1, W2)]
         ri = np.random.default_rng(SEED_INPUTS)
-        w.clips = ri.uniform(-1.0, 1.0, size=(1, 64))
+        w.n_clips = 1 if n_clips is None else n_clips
+        w.clips = ri.uniform(-1.0, 1.0, size=(w.n_clips, 64))
         return w
     if name == "small":
         w = Workload("small", 14, [60] + [40] * 7, [60], 40.0, 3.2, clip_dim=2048,
