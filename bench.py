@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-min-level", action="store_true", help="skip the minimal-start-level variant")
     ap.add_argument("--mix-rates", default="100,300,1000", help="request rates (req/s) of the mixed sweep")
     ap.add_argument("--conv-rows", default="all", help="Table 1 rows to time: all | comma-separated indices")
+    ap.add_argument("--no-simd", action="store_true", help="skip the slot-batched (one clip per slot) rows")
+    ap.add_argument("--simd-rows", default="all",
+                    help="slot-batched rows: all | comma-separated indices into small@top, small@level3, large@top")
     return ap.parse_args()
 
 
@@ -158,6 +161,12 @@ def peaks():
 # the correction, add and subtract of 64-bit words: 10).
 ALU_PEAK_TOPS = 152 * 4 * 32 * 2.070e9 / 1e12
 OPS_PER_BUTTERFLY = 30
+# Multiply-pipe roofline of the slot-batched matrix product: a mad.wide.u32 (32 x 32 -> 64
+# bits plus a 64-bit addend) occupies the integer multiply (FMA-heavy) pipe for 4 cycles per
+# warp instruction (ncu on a throughput kernel of such multiply-adds: 0.19 warp instructions
+# per sub-partition cycle at 76 % heavy-pipe cycles), i.e. 8 lanes per cycle per sub-partition:
+# 152 SMs x 4 x 8 lanes x 2.07 GHz.
+MAD_WIDE_PEAK_TOPS = 152 * 4 * 8 * 2.070e9 / 1e12
 
 
 def ntt_source_hash():
@@ -480,6 +489,117 @@ def _time_range(H, m, evk, op0, op1, cts, n_samples, torch, stream, iters):
     return times[len(times) // 2]
 
 
+def simd_mad_lanes(primes, layers, level, n):
+    """algorithmic mad.wide.u32 lane operations of the slot-batched matrix products: per FC
+    row, input and residue, 3 for a two-piece limb (q < 2^42, Karatsuba) and 6 for a
+    three-piece one"""
+    total = 0.0
+    for layer in layers:
+        if layer[0] == "square":
+            level -= 1
+            continue
+        if layer[0] == "fc":
+            M, K = layer[1].shape
+            used = 1
+        else:
+            M, K = 2 * layer[1].shape[0] * layer[2].shape[0], layer[1].shape[1]
+            used = 2
+        cost = sum(3 if primes[t] < (1 << 42) else 6 for t in range(level + 1))
+        total += float(M) * K * 2 * n * cost
+        level -= used
+    return total
+
+
+SIMD_ROWS = (("small", 8192, 0), ("small", 8192, 3), ("large", 16384, 0))
+
+
+def run_simd(H, torch, stream, device, plain_value, rows=SIMD_ROWS, steps=3, warmup=1):
+    """slot-batched evaluation: one clip per slot, one ciphertext per feature; one step = the
+    whole network over a full batch of clips resident in HBM (FC layers as scalar matrix
+    products on the integer multiply-add pipe, no rotations)"""
+    from paper_2104_09164_gb300.workloads import make_workload
+    out = []
+    for name, n_clips, level in rows:
+        w = make_workload(name, n_clips)
+        ctx = H.hear_context_create(w.log_n, w.q_bits, w.p_bits, w.log2_scale, w.sigma, device)
+        m = H.hear_simd_model_create(ctx, w.layers, level)
+        d_in, d_out, lin, lout = H.hear_simd_model_info(m)
+        sk, pk, evk = H.hear_keygen(ctx, 301, [])
+        t0 = time.perf_counter()
+        b = H.hear_simd_encrypt(ctx, pk, w.clips, 401, level, stream=stream)
+        torch.cuda.synchronize()
+        enc_s = time.perf_counter() - t0
+        for _ in range(warmup):
+            H.hear_simd_batch_destroy(H.hear_simd_evaluate(m, evk, b, stream))
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        launches0 = H.hear_launch_count()
+        with ClockSampler(device) as clk:
+            ta, tb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ta.record(stream)
+            for i in range(steps):
+                ev[i][0].record(stream)
+                y = H.hear_simd_evaluate(m, evk, b, stream)
+                ev[i][1].record(stream)
+                H.hear_simd_batch_destroy(y)
+            tb.record(stream)
+            torch.cuda.synchronize()
+        launches = H.hear_launch_count() - launches0
+        total_ms = ta.elapsed_time(tb)
+        lat = sorted(x.elapsed_time(y) for x, y in ev)
+        H.hear_profile_begin(ctx)
+        y = H.hear_simd_evaluate(m, evk, b, stream)
+        torch.cuda.synchronize()
+        prof = H.hear_profile_end(ctx)
+        logits = H.hear_simd_decrypt(ctx, sk, y, n_clips)
+        err = float(np.max(np.abs(logits - w.fp64_forward(w.clips))))
+        H.hear_simd_batch_destroy(y)
+        gemm_ms = prof.get("k_simd_fc", (0, 0.0, 0.0))[1]
+        lanes = simd_mad_lanes(H.hear_context_primes(ctx), w.layers, lin, 1 << w.log_n)
+        probe = H.hear_dbg_imad_peak(ctx, 0) / 1e12
+        peak = MAD_WIDE_PEAK_TOPS
+        achieved = lanes / (gemm_ms / 1e3) / 1e12 if gemm_ms else None
+        # end to end: coefficient-domain inputs from pinned host memory, result read back
+        words = H.hear_simd_batch_export(b).reshape(-1)
+        pin_in = torch.empty(words.size, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+        pin_in[:] = words
+        del words
+        scale = H.hear_simd_batch_info(b)[2]
+        o0 = H.hear_simd_evaluate_host(m, evk, pin_in, scale, None, stream)[0]
+        pin_out = torch.empty(o0.size, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+        torch.cuda.synchronize()
+        e2e_steps = 2
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            H.hear_simd_evaluate_host(m, evk, pin_in, scale, pin_out, stream)
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        v = steps * n_clips / (total_ms / 1e3)
+        out.append({"workload": describe(w).split(",")[0] + ", FC/x^2 network of the plain path, %d clips one per "
+                                "slot, %d input ciphertexts (one per feature), input level %d" % (n_clips, d_in, lin),
+                    "value": v, "unit": UNIT, "ms_per_step": total_ms / steps, "steps": steps,
+                    "p50_ms": lat[len(lat) // 2], "gpu_launches": launches, "clocks": clk.summary(),
+                    "vs_plain": v / plain_value if plain_value else None,
+                    "max_abs_err_vs_fp64": err, "encrypt_s": enc_s,
+                    "e2e": {"value": n_clips / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(pin_in.nbytes),
+                            "d2h_bytes_per_step": int(pin_out.nbytes)},
+                    "roofline": {"bound": "alu", "kernel": "k_simd_fc (scalar matrix product, mad.wide.u32)",
+                                 "achieved": achieved, "peak": peak, "unit": "T mad.wide.u32 lane-ops/s",
+                                 "frac": achieved / peak if achieved else None, "traffic": None,
+                                 "peak_kind": "derived: 152 SMs x 32 lanes/clk x 2.07 GHz (mad.wide.u32 holds "
+                                              "the multiply pipe 4 cycles per warp instruction)",
+                                 "probe_tops": probe},
+                    "stages_ms_per_step": {k: v_[1] for k, v_ in sorted(prof.items(), key=lambda kv: -kv[1][1])[:6]}})
+        del pin_in, pin_out
+        H.hear_simd_batch_destroy(b)
+        H.hear_simd_model_destroy(m)
+        H.hear_eval_keys_destroy(evk)
+        H.hear_public_key_destroy(pk)
+        H.hear_secret_key_destroy(sk)
+        H.hear_context_destroy(ctx)
+    return out
+
+
 def run_conv_table(H, torch, stream, device, rows, iters=5):
     from paper_2104_09164_gb300.workloads import CONV_BENCH_PARAMS, TABLE1_LAYERS, conv_bench_layer
     log_n, qb, pb = CONV_BENCH_PARAMS
@@ -688,6 +808,14 @@ def main_gpu(a):
                         "clocks": mclk}
             SM.close()
         result["min_start_level"] = ms
+    if result is not None and not a.no_simd and a.workload == "small" and a.clips is None and dist.world == 1:
+        result["batched_simd"] = {
+            "note": "slot-batched form: the batch's clips one per slot, FC layers as plaintext-scalar "
+                    "matrix products over the per-feature ciphertexts (no rotations); same parameters, "
+                    "networks and accuracy bound; value = clips / step time",
+            "rows": run_simd(H, torch, stream, device, result["value"],
+                             SIMD_ROWS if a.simd_rows == "all" else
+                             [SIMD_ROWS[int(i)] for i in a.simd_rows.split(",")])}
     if result is not None and not a.no_cnn and dist.world == 1:
         rows = list(range(8)) if a.conv_rows == "all" else [int(x) for x in a.conv_rows.split(",")]
         result["conv_table1"] = {

@@ -61,6 +61,8 @@ typedef struct hear_eval_keys hear_eval_keys;
 typedef struct hear_ciphertext hear_ciphertext;
 typedef struct hear_model hear_model;
 typedef struct hear_cnn hear_cnn;
+typedef struct hear_simd_model hear_simd_model;
+typedef struct hear_simd_batch hear_simd_batch;
 
 /* Encryption parameters.  The ciphertext modulus is Q = q_0 * ... * q_{n_q-1} (top level
  * L = n_q - 1); the n_p special primes p_0..p_{K-1} are used by key switching only.
@@ -354,6 +356,47 @@ hear_status hear_cnn_encrypt(hear_context *ctx, const hear_public_key *pk, const
 hear_status hear_cnn_evaluate(const hear_cnn *m, const hear_eval_keys *evk, size_t op0, size_t op1,
                               hear_ciphertext *const *in, size_t n_samples, hear_ciphertext **out, void *stream);
 
+/* ---- slot-batched evaluation (one clip per slot) ----
+ * A throughput form of the FC / x^2 networks of hear_model_create for batches of up to N/2
+ * clips: slot c of every ciphertext belongs to clip c and ciphertext i of a batch holds
+ * feature i of every clip.  An FC layer y = W x is then y_o = rescale(sum_i [w_oi] x_i) with
+ * plaintext scalars [w] = round(w q_l) (exact, ties away from zero: the encoding of the
+ * constant slot vector w at scale q_l; Methods, "Non-convolutional layers") and no rotation;
+ * x^2 is a ciphertext product with relinearisation and rescale; FC_SQ_FC sums the degree-2
+ * products y_r u_(c,r) (u = (W2[c,r] W1[r]) x) before one relinearisation and rescale per
+ * output.  Only the relinearisation key is needed.  A batch is one contiguous device array
+ * [n_ct][2][level+1][N] (NTT domain).  Layers: FC (d_in <= 2^19, no bias), SQUARE,
+ * FC_SQ_FC; d_in of the first layer = the batch's ciphertext count. */
+hear_status hear_simd_model_create(hear_context *ctx, const hear_layer_desc *layers, size_t n_layers,
+                                   uint32_t level, hear_simd_model **out);   /* level 0 = the top level */
+hear_status hear_simd_model_info(const hear_simd_model *m, uint32_t *d_in, uint32_t *d_out, uint32_t *level_in,
+                                 uint32_t *level_out);
+void hear_simd_model_destroy(hear_simd_model *m);
+/* x: n_clips x n_features row-major (1 <= n_clips <= N/2); ciphertext i encrypts the slot
+ * vector (x[0][i], .., x[n_clips-1][i], 0, ..) at `scale` (0 = the context's default) with
+ * randomness stream i of `seed`, then keeps the limbs of `level` (0 = the top level) */
+hear_status hear_simd_encrypt(hear_context *ctx, const hear_public_key *pk, const double *x, size_t n_clips,
+                              size_t n_features, double scale, uint64_t seed, uint32_t level,
+                              hear_simd_batch **out, void *stream);
+hear_status hear_simd_batch_info(const hear_simd_batch *b, uint32_t *n_ct, uint32_t *level, double *scale);
+/* coefficient domain uint64[n_ct][2][level+1][N] */
+hear_status hear_simd_batch_export(const hear_simd_batch *b, uint64_t *out, size_t cap, size_t *n);
+hear_status hear_simd_batch_import(hear_context *ctx, const uint64_t *words, size_t n_ct, uint32_t level,
+                                   double scale, hear_simd_batch **out, void *stream);
+void hear_simd_batch_destroy(hear_simd_batch *b);
+/* in: d_in ciphertexts at the model's input level -> out: d_out ciphertexts */
+hear_status hear_simd_evaluate(const hear_simd_model *m, const hear_eval_keys *evk, const hear_simd_batch *in,
+                               hear_simd_batch **out, void *stream);
+/* end to end from host buffers: in = uint64[d_in][2][l+1][N] coefficient domain at the
+ * model's input level l and `scale` -> out = uint64[d_out][2][level_out+1][N]; both copies
+ * are included */
+hear_status hear_simd_evaluate_host(const hear_simd_model *m, const hear_eval_keys *evk, const uint64_t *in_words,
+                                    double scale, uint64_t *out_words, size_t cap, size_t *n, uint32_t *level_out,
+                                    double *scale_out, void *stream);
+/* out: n_clips x n_ct row-major, out[c][o] = slot c of ciphertext o */
+hear_status hear_simd_decrypt(hear_context *ctx, const hear_secret_key *sk, const hear_simd_batch *b,
+                              size_t n_clips, double *out, size_t cap, size_t *n);
+
 /* ---- rescale for callers that cannot allocate device memory ----
  * The paper has no counterpart: this entry point exists for callers that cannot call
  * cudaMalloc -- a process whose device-memory quota is already held by another
@@ -429,6 +472,12 @@ hear_status hear_ntt_set_table(hear_context *ctx, const uint8_t *table);
 
 /* ---- debug: ring products through the NTT kernels (tests only) ---- */
 /* out = a * b in Z_q[X]/(X^N+1) for limb prime index `prime` (0..n_q+n_p-1), coefficient domain */
+/* lane operations per second of an integer multiply-add form (kind 0: mad.wide.u32 --
+ * 32 x 32 -> 64 bits plus a 64-bit addend, the step of the slot-batched matrix product;
+ * kind 1: mad.lo.u32), from a throughput kernel of 8 independent chains per thread on every
+ * SM (iters multiply-adds per chain, iters in [1, 2^20]); the roofline denominator of the
+ * integer-multiply-bound kernels */
+hear_status hear_dbg_imad_peak(hear_context *ctx, int kind, uint32_t iters, double *lane_ops_per_s);
 hear_status hear_dbg_poly_mul(hear_context *ctx, uint32_t prime, const uint64_t *a, const uint64_t *b,
                               uint64_t *out);
 /* forward+inverse NTT round trip of n_limb limbs (prime i % (n_q+n_p)) in place */

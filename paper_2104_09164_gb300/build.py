@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhear.so")
-SOURCES = ["context.cu", "ntt.cu", "kernels.cu", "ckks.cu", "capi.cu", "server.cu", "noalloc.cu", "cnn.cu", "encode.cpp"]
+SOURCES = ["context.cu", "ntt.cu", "kernels.cu", "ckks.cu", "capi.cu", "server.cu", "noalloc.cu", "cnn.cu", "simd.cu", "encode.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -843,3 +843,201 @@ hear_status hear_cnn_evaluate(const hear_cnn *m, const hear_eval_keys *evk, size
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ slot-batched evaluation
+#include "simd.h"
+#include "encode.h"
+
+namespace {
+hear_simd_batch *new_batch(hear_context *c, uint32_t n_ct, uint32_t level, double scale, cudaStream_t st) {
+    auto b = std::make_unique<hear_simd_batch>();
+    b->ctx = c;
+    b->n_ct = n_ct;
+    b->level = level;
+    b->scale = scale;
+    b->d = DevBuf((size_t)n_ct * 2 * (level + 1) * c->n * 8, st);
+    return b.release();
+}
+void check_reduced(const hear_context *c, const uint64_t *words, size_t n_polys, uint32_t level) {
+    for (size_t i = 0; i < n_polys * (level + 1); i++) {
+        const uint64_t q = c->primes[i % (level + 1)];
+        const uint64_t *w = words + i * c->n;
+        for (uint32_t k = 0; k < c->n; k++) HEAR_REQUIRE(w[k] < q, HEAR_E_FORMAT, "residue not reduced");
+    }
+}
+}  // namespace
+
+extern "C" {
+
+hear_status hear_simd_model_create(hear_context *ctx, const hear_layer_desc *layers, size_t n_layers,
+                                   uint32_t level, hear_simd_model **out) {
+    if (!ctx || !layers || !out) return fail(HEAR_E_INVAL, "null argument");
+    return guard(ctx, [&] { *out = simd_model_create(ctx, layers, n_layers, level ? level : ctx->L); });
+}
+
+hear_status hear_simd_model_info(const hear_simd_model *m, uint32_t *d_in, uint32_t *d_out, uint32_t *level_in,
+                                 uint32_t *level_out) {
+    if (!m) return fail(HEAR_E_INVAL, "null model");
+    if (d_in) *d_in = m->d_in;
+    if (d_out) *d_out = m->d_out;
+    if (level_in) *level_in = m->level_in;
+    if (level_out) *level_out = m->level_out;
+    return HEAR_OK;
+}
+
+void hear_simd_model_destroy(hear_simd_model *m) {
+    if (m) cudaSetDevice(m->ctx->device);
+    delete m;
+}
+
+hear_status hear_simd_encrypt(hear_context *ctx, const hear_public_key *pk, const double *x, size_t n_clips,
+                              size_t n_features, double scale, uint64_t seed, uint32_t level, hear_simd_batch **out,
+                              void *stream) {
+    if (!ctx || !pk || !x || !out) return fail(HEAR_E_INVAL, "null argument");
+    if (pk->ctx != ctx) return fail(HEAR_E_STATE, "key from another context");
+    const size_t slots = ctx->n / 2;
+    if (n_clips < 1 || n_clips > slots) return fail(HEAR_E_INVAL, "n_clips must be in [1, N/2]");
+    if (n_features < 1 || n_features > (1u << 19)) return fail(HEAR_E_INVAL, "n_features must be in [1, 2^19]");
+    const uint32_t lv = level ? level : ctx->L;
+    if (lv > ctx->L) return fail(HEAR_E_LEVEL, "level above the top level");
+    return guard(ctx, [&] {
+        cudaStream_t st = stream_of(ctx, stream);
+        const double sc = scale > 0 ? scale : ctx->default_scale;
+        std::unique_ptr<hear_simd_batch> b(new_batch(ctx, (uint32_t)n_features, lv, sc, st));
+        const uint64_t n = ctx->n, ctw = 2ull * (lv + 1) * n;
+        // encode blocks of features on the host cores, then encrypt them one by one
+        constexpr size_t kBlock = 64;
+        std::vector<double> z(kBlock * slots), scales(kBlock, sc);
+        std::vector<int64_t> m(kBlock * n);
+        auto enc = encoder(ctx);
+        for (size_t i0 = 0; i0 < n_features; i0 += kBlock) {
+            const size_t cnt = std::min(kBlock, n_features - i0);
+            std::fill(z.begin(), z.end(), 0.0);
+            for (size_t f = 0; f < cnt; f++)
+                for (size_t c = 0; c < n_clips; c++) z[f * slots + c] = x[c * n_features + i0 + f];
+            encode_many(*enc, z.data(), cnt, scales.data(), m.data());
+            for (size_t f = 0; f < cnt; f++) {
+                const size_t i = i0 + f;
+                std::unique_ptr<hear_ciphertext> ct(encrypt_encoded(ctx, pk, m.data() + f * n, sc, seed, i, st));
+                // keep the limbs of the batch's level (no division: the scale is unchanged)
+                HEAR_CHECK_CUDA(cudaMemcpy2DAsync(b->d.u64() + i * ctw, (size_t)(lv + 1) * n * 8, ct->d.p,
+                                                  (size_t)(ct->level + 1) * n * 8, (size_t)(lv + 1) * n * 8, 2,
+                                                  cudaMemcpyDeviceToDevice, st));
+            }
+        }
+        *out = b.release();
+    });
+}
+
+hear_status hear_simd_batch_info(const hear_simd_batch *b, uint32_t *n_ct, uint32_t *level, double *scale) {
+    if (!b) return fail(HEAR_E_INVAL, "null batch");
+    if (n_ct) *n_ct = b->n_ct;
+    if (level) *level = b->level;
+    if (scale) *scale = b->scale;
+    return HEAR_OK;
+}
+
+hear_status hear_simd_batch_export(const hear_simd_batch *b, uint64_t *out, size_t cap, size_t *n) {
+    if (!b) return fail(HEAR_E_INVAL, "null batch");
+    hear_context *c = b->ctx;
+    const size_t words = (size_t)b->n_ct * 2 * (b->level + 1) * c->n;
+    if (n) *n = words;
+    if (!out || cap < words) return fail(HEAR_E_INVAL, "output capacity too small");
+    return guard(c, [&] {
+        cudaStream_t st = c->stream;
+        DevBuf t(words * 8, st);
+        HEAR_CHECK_CUDA(cudaMemcpyAsync(t.p, b->d.p, words * 8, cudaMemcpyDeviceToDevice, st));
+        ntt_inverse(c, t.u64(), b->n_ct * 2 * (b->level + 1), map_q(b->level, c->n_q), st);
+        HEAR_CHECK_CUDA(cudaMemcpyAsync(out, t.p, words * 8, cudaMemcpyDeviceToHost, st));
+        HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+hear_status hear_simd_batch_import(hear_context *ctx, const uint64_t *words, size_t n_ct, uint32_t level,
+                                   double scale, hear_simd_batch **out, void *stream) {
+    if (!ctx || !words || !out || n_ct == 0) return fail(HEAR_E_INVAL, "null argument");
+    if (level > ctx->L) return fail(HEAR_E_FORMAT, "bad level");
+    return guard(ctx, [&] {
+        check_reduced(ctx, words, 2 * n_ct, level);
+        cudaStream_t st = stream_of(ctx, stream);
+        std::unique_ptr<hear_simd_batch> b(new_batch(ctx, (uint32_t)n_ct, level, scale, st));
+        to_device_ntt(ctx, words, level, (uint32_t)(2 * n_ct), b->d.u64(), st);
+        *out = b.release();
+    });
+}
+
+void hear_simd_batch_destroy(hear_simd_batch *b) {
+    if (b) cudaSetDevice(b->ctx->device);
+    delete b;
+}
+
+hear_status hear_simd_evaluate(const hear_simd_model *m, const hear_eval_keys *evk, const hear_simd_batch *in,
+                               hear_simd_batch **out, void *stream) {
+    if (!m || !evk || !in || !out) return fail(HEAR_E_INVAL, "null argument");
+    hear_context *c = m->ctx;
+    if (evk->ctx != c || in->ctx != c) return fail(HEAR_E_STATE, "keys or batch from another context");
+    if (in->n_ct != m->d_in) return fail(HEAR_E_INVAL, "batch size differs from the model's input dimension");
+    if (in->level != m->level_in) return fail(HEAR_E_LEVEL, "batch not at the model's input level");
+    return guard(c, [&] {
+        cudaStream_t st = stream_of(c, stream);
+        double so;
+        DevBuf y = simd_evaluate(m, evk, in->d.u64(), in->scale, &so, st);
+        auto b = std::make_unique<hear_simd_batch>();
+        b->ctx = c;
+        b->n_ct = m->d_out;
+        b->level = m->level_out;
+        b->scale = so;
+        b->d = std::move(y);
+        *out = b.release();
+    });
+}
+
+hear_status hear_simd_evaluate_host(const hear_simd_model *m, const hear_eval_keys *evk, const uint64_t *in_words,
+                                    double scale, uint64_t *out_words, size_t cap, size_t *n, uint32_t *level_out,
+                                    double *scale_out, void *stream) {
+    if (!m || !evk || !in_words) return fail(HEAR_E_INVAL, "null argument");
+    hear_context *c = m->ctx;
+    if (evk->ctx != c) return fail(HEAR_E_STATE, "keys from another context");
+    const size_t out_n = (size_t)m->d_out * 2 * (m->level_out + 1) * c->n;
+    if (n) *n = out_n;
+    if (!out_words || cap < out_n) return fail(HEAR_E_INVAL, "output capacity too small");
+    return guard(c, [&] {
+        cudaStream_t st = stream_of(c, stream);
+        DevBuf X((size_t)m->d_in * 2 * (m->level_in + 1) * c->n * 8, st);
+        to_device_ntt(c, in_words, m->level_in, 2 * m->d_in, X.u64(), st);
+        double so;
+        DevBuf Y = simd_evaluate(m, evk, X.u64(), scale, &so, st);
+        ntt_inverse(c, Y.u64(), 2 * m->d_out * (m->level_out + 1), map_q(m->level_out, c->n_q), st);
+        HEAR_CHECK_CUDA(cudaMemcpyAsync(out_words, Y.p, out_n * 8, cudaMemcpyDeviceToHost, st));
+        HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
+        if (level_out) *level_out = m->level_out;
+        if (scale_out) *scale_out = so;
+    });
+}
+
+hear_status hear_dbg_imad_peak(hear_context *ctx, int kind, uint32_t iters, double *lane_ops_per_s) {
+    if (!ctx || !lane_ops_per_s) return fail(HEAR_E_INVAL, "null argument");
+    return guard(ctx, [&] { *lane_ops_per_s = imad_peak(ctx, kind, iters); });
+}
+
+hear_status hear_simd_decrypt(hear_context *ctx, const hear_secret_key *sk, const hear_simd_batch *b,
+                              size_t n_clips, double *out, size_t cap, size_t *n) {
+    if (!ctx || !sk || !b) return fail(HEAR_E_INVAL, "null argument");
+    if (b->ctx != ctx) return fail(HEAR_E_STATE, "batch from another context");
+    if (n_clips < 1 || n_clips > ctx->n / 2) return fail(HEAR_E_INVAL, "n_clips must be in [1, N/2]");
+    if (n) *n = n_clips * b->n_ct;
+    if (!out || cap < n_clips * b->n_ct) return fail(HEAR_E_INVAL, "output capacity too small");
+    return guard(ctx, [&] {
+        cudaStream_t st = ctx->stream;
+        const uint64_t ctw = 2ull * (b->level + 1) * ctx->n;
+        std::vector<double> slots(ctx->n / 2);
+        for (uint32_t o = 0; o < b->n_ct; o++) {
+            std::unique_ptr<hear_ciphertext> ct(new_ct(ctx, b->level, 2, b->scale, st));
+            HEAR_CHECK_CUDA(cudaMemcpyAsync(ct->d.p, b->d.u64() + o * ctw, ctw * 8, cudaMemcpyDeviceToDevice, st));
+            decrypt_slots(ctx, sk, ct.get(), slots.data());
+            for (size_t c = 0; c < n_clips; c++) out[c * b->n_ct + o] = slots[c];
+        }
+    });
+}
+
+}  // extern "C"

@@ -143,11 +143,16 @@ void keygen(hear_context *c, uint64_t seed, const int32_t *steps, size_t n_steps
 // ------------------------------------------------------------------ encryption
 hear_ciphertext *encrypt_slots(hear_context *c, const hear_public_key *pk, const double *z, double scale,
                                uint64_t seed, uint64_t ct_id, cudaStream_t st) {
+    std::vector<int64_t> m(c->n);
+    encode_dd(*encoder(c), z, scale, m.data());
+    return encrypt_encoded(c, pk, m.data(), scale, seed, ct_id, st);
+}
+
+hear_ciphertext *encrypt_encoded(hear_context *c, const hear_public_key *pk, const int64_t *m, double scale,
+                                 uint64_t seed, uint64_t ct_id, cudaStream_t st) {
     const uint32_t n = c->n, nq = c->n_q;
     const LimbMap mq = map_q(c->L, nq);
-    std::vector<int64_t> m(n);
-    encode_dd(*encoder(c), z, scale, m.data());
-    DevBuf dm = upload(m.data(), n * 8, st);
+    DevBuf dm = upload(m, n * 8, st);
     const size_t limbs = (size_t)nq * n;
     DevBuf buf(4 * limbs * 8, st), e8(n, st);
     uint64_t *mn = buf.u64(), *vn = mn + limbs, *e0 = vn + limbs, *e1 = e0 + limbs;
@@ -270,17 +275,23 @@ void rotate_each(hear_context *c, uint32_t level, uint32_t R, uint32_t C, const 
 
 void mul_relin(hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *a, const uint64_t *b,
                const uint64_t *relin_key, uint64_t *out, cudaStream_t st) {
-    const uint32_t n = c->n, L1 = level + 1, W = L1 + c->K, dnum = c->dnum(level);
-    const uint64_t plane = (uint64_t)L1 * n;
+    const uint64_t plane = (uint64_t)(level + 1) * c->n;
     DevBuf d3((size_t)n_ct * 3 * plane * 8, st);
     tensor_ct(c, level, n_ct, a, b, d3.u64(), st);
+    relin3(c, level, n_ct, d3.u64(), relin_key, out, st);
+}
+
+void relin3(hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *d3, const uint64_t *relin_key,
+            uint64_t *out, cudaStream_t st) {
+    const uint32_t n = c->n, L1 = level + 1, W = L1 + c->K, dnum = c->dnum(level);
+    const uint64_t plane = (uint64_t)L1 * n;
     DevBuf ext((size_t)n_ct * dnum * W * n * 8, st), tmp((size_t)n_ct * 2 * plane * 8, st),
         acc((size_t)n_ct * 2 * W * n * 8, st);
-    modup(c, level, n_ct, d3.u64() + 2 * plane, 3 * plane, ext.u64(), tmp.u64(), st);
+    modup(c, level, n_ct, d3 + 2 * plane, 3 * plane, ext.u64(), tmp.u64(), st);
     JobTable jobs = make_jobs(c, {Rot{relin_key, 1u}}, st);
-    ks_inner(c, level, 1, n_ct, ext.u64(), false, jobs.keys(), jobs.ginv(), acc.u64(), d3.u64() + 2 * plane,
-             3 * plane, st);
-    moddown(c, level, n_ct, acc.u64(), out, d3.u64(), 3 * plane, 3u, false, nullptr, 1, tmp.u64(), st);
+    ks_inner(c, level, 1, n_ct, ext.u64(), false, jobs.keys(), jobs.ginv(), acc.u64(), d3 + 2 * plane, 3 * plane,
+             st);
+    moddown(c, level, n_ct, acc.u64(), out, d3, 3 * plane, 3u, false, nullptr, 1, tmp.u64(), st);
 }
 
 // ------------------------------------------------------------------ network

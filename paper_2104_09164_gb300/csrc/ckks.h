@@ -65,6 +65,9 @@ void keygen(hear_context *c, uint64_t seed, const int32_t *steps, size_t n_steps
             hear_public_key **pk, hear_eval_keys **evk);
 hear_ciphertext *encrypt_slots(hear_context *c, const hear_public_key *pk, const double *z, double scale,
                                uint64_t seed, uint64_t ct_id, cudaStream_t st);
+// the same from an encoded message m (N integer coefficients)
+hear_ciphertext *encrypt_encoded(hear_context *c, const hear_public_key *pk, const int64_t *m, double scale,
+                                 uint64_t seed, uint64_t ct_id, cudaStream_t st);
 void decrypt_slots(hear_context *c, const hear_secret_key *sk, const hear_ciphertext *ct, double *out);
 
 // batched primitives on contiguous batches [n_ct][n_poly][level+1][N]
@@ -86,6 +89,9 @@ void rotate_each(hear_context *c, uint32_t level, uint32_t R, uint32_t C, const 
 // tensor + relinearise (no rescale): out [n_ct][2][level+1][N]
 void mul_relin(hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *a, const uint64_t *b,
                const uint64_t *relin_key, uint64_t *out, cudaStream_t st);
+// relinearise degree-2 ciphertexts d3 [n_ct][3][level+1][N] -> out [n_ct][2][level+1][N]
+void relin3(hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *d3, const uint64_t *relin_key,
+            uint64_t *out, cudaStream_t st);
 
 // encoded plaintext helpers
 DevBuf encode_plain(hear_context *c, const double *z, double scale, uint32_t level, cudaStream_t st);

@@ -1,0 +1,477 @@
+// simd.cu -- slot-batched evaluation of the FC / x^2 networks on sm_103a.
+//
+// One clip per slot and one ciphertext per feature: an FC layer y_o = sum_i [w_oi] x_i
+// multiplies the d_in input ciphertexts by plaintext scalars (the constant polynomial
+// round(w q_l), i.e. the encoding of the constant slot vector w at scale q_l; Methods,
+// "Non-convolutional layers", with every slot a different clip) and needs no rotation.  Per
+// limb t this is a product of an M x K matrix of residues with a K x 2N matrix of residues,
+// done here as a modular matrix product on the integer pipes (the exact arithmetic rules the
+// tensor cores out).  Each residue a < 2^63 is cut into 21-bit pieces so that every
+// partial product is one 32 x 32 -> 64-bit multiply-add and K <= 2^19 of them sum without
+// overflow in 64 bits.  With a0 b1 + a1 b0 = (a0 + a1)(b0 + b1) - a0 b0 - a1 b1 a product of
+// two-piece residues (primes below 2^42) takes three multiply-adds and one of three-piece
+// residues six; the 64-bit partial sums are reduced mod q_t once per output.
+#include <cmath>
+#include <mutex>
+#include "simd.h"
+#include "modarith.cuh"
+#include "launch.cuh"
+
+namespace hear {
+namespace {
+
+constexpr int kGemmThreads = 256;
+constexpr int kTX = 64;                  // columns (residues of one limb) per CTA
+constexpr uint32_t kPieceBits = 21;
+constexpr uint32_t kPieceMask = (1u << kPieceBits) - 1;
+constexpr uint32_t kMaxK = 1u << 19;     // K * 2^44 < 2^63
+constexpr uint32_t kMpadUnit = 64;
+
+// PL planes of pieces (two-piece: a0, a1, a0 + a1; three-piece: a0, a1, a2, a0 + a1,
+// a0 + a2, a1 + a2), a CTA tile of TM rows x kTX columns, RM rows x 4 columns per thread
+// (16 x 16 threads), KC inner indices per shared-memory round
+template <int NP> struct Gemm;
+template <> struct Gemm<2> { static constexpr int PL = 3, TM = 64, RM = 4, KC = 32; };
+template <> struct Gemm<3> { static constexpr int PL = 6, TM = 16, RM = 1, KC = 16; };
+
+struct LimbSet {
+    uint32_t n;
+    uint8_t t[kMaxPrimes];
+};
+
+// 2^21, 2^42, 2^63, 2^84 mod q_t and their Shoup companions
+struct PieceConsts {
+    uint64_t c[4], c_sh[4];
+};
+
+template <int NP>
+__device__ __forceinline__ void split_pieces(uint64_t v, uint32_t *p) {
+    const uint32_t b0 = (uint32_t)v & kPieceMask, b1 = (uint32_t)(v >> kPieceBits) & kPieceMask;
+    if constexpr (NP == 2) {
+        p[0] = b0;
+        p[1] = b1;
+        p[2] = b0 + b1;
+    } else {
+        const uint32_t b2 = (uint32_t)(v >> (2 * kPieceBits));
+        p[0] = b0;
+        p[1] = b1;
+        p[2] = b2;
+        p[3] = b0 + b1;
+        p[4] = b0 + b2;
+        p[5] = b1 + b2;
+    }
+}
+
+// y[m][poly][t][j] = sum_k A_t[m][k] x[k][poly][t][j] mod q_t for the limbs of `limbs`
+// (blockIdx.y), rows m0 = blockIdx.z * TM .., columns (poly, j) = blockIdx.x * kTX ..
+template <int NP>
+__global__ void __launch_bounds__(kGemmThreads, 2)
+k_simd_fc(const uint64_t *__restrict__ x, uint64_t *__restrict__ y, const uint32_t *__restrict__ a,
+          const uint64_t *__restrict__ a_off, const PieceConsts *__restrict__ pc, LimbSet limbs, uint32_t M,
+          uint32_t Mpad, uint32_t K, uint32_t L1, uint32_t n, const DevPrime *__restrict__ P) {
+    pdl_enter();
+    using G = Gemm<NP>;
+    constexpr int PL = G::PL, TM = G::TM, RM = G::RM, KC = G::KC;
+    __shared__ __align__(16) uint32_t sa[PL][KC][TM];
+    __shared__ __align__(16) uint32_t sb[PL][KC][kTX];
+    const uint32_t t = limbs.t[blockIdx.y];
+    const uint32_t m0 = blockIdx.z * TM;
+    const uint32_t col0 = blockIdx.x * kTX;
+    const uint32_t poly = col0 / n, j0 = col0 % n;
+    const uint32_t tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const uint64_t xrow = 2ull * L1 * n;                                // words per input ciphertext
+    const uint64_t *xb = x + ((uint64_t)poly * L1 + t) * n + j0;      // inner index k at xb + k * xrow
+    const uint32_t *ab = a + a_off[t] + m0;                            // plane p, index k: + (p K + k) Mpad
+
+    uint64_t acc[RM][4][PL];
+#pragma unroll
+    for (int r = 0; r < RM; r++)
+#pragma unroll
+        for (int c = 0; c < 4; c++)
+#pragma unroll
+            for (int p = 0; p < PL; p++) acc[r][c][p] = 0;
+
+    constexpr int WPT = KC * kTX / kGemmThreads;   // residues of x per thread per round
+    constexpr int TPR = kTX / WPT;                 // threads per inner index
+    static_assert(WPT % 2 == 0 && TPR * WPT == kTX, "x tile split");
+    constexpr int A4 = PL * KC * TM / 4;           // uint4 of pieces per round
+    for (uint32_t k0 = 0; k0 < K; k0 += KC) {
+        {   // x: KC inner indices x 64 residues, cut into pieces
+            const uint32_t r = threadIdx.x / TPR, c = (threadIdx.x % TPR) * WPT;
+            uint64_t v[WPT];
+            if (k0 + r < K) {
+                const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(xb + (uint64_t)(k0 + r) * xrow + c);
+#pragma unroll
+                for (int w = 0; w < WPT / 2; w++) {
+                    const ulonglong2 u = src[w];
+                    v[2 * w] = u.x;
+                    v[2 * w + 1] = u.y;
+                }
+            } else {
+#pragma unroll
+                for (int w = 0; w < WPT; w++) v[w] = 0;
+            }
+#pragma unroll
+            for (int w = 0; w < WPT; w++) {
+                uint32_t pcs[PL];
+                split_pieces<NP>(v[w], pcs);
+#pragma unroll
+                for (int p = 0; p < PL; p++) sb[p][r][c + w] = pcs[p];
+            }
+        }
+        // the scalars' pieces (zero past K)
+        for (int i = threadIdx.x; i < A4; i += kGemmThreads) {
+            const int p = i / (KC * TM / 4), rem = i % (KC * TM / 4);
+            const int r = rem / (TM / 4), c4 = rem % (TM / 4);
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (k0 + r < K) val = *reinterpret_cast<const uint4 *>(ab + ((uint64_t)p * K + k0 + r) * Mpad + c4 * 4);
+            *reinterpret_cast<uint4 *>(&sa[p][r][c4 * 4]) = val;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < KC; kk++) {
+            uint32_t av[PL][RM], bv[PL][4];
+#pragma unroll
+            for (int p = 0; p < PL; p++) {
+                const uint4 b4 = *reinterpret_cast<const uint4 *>(&sb[p][kk][tx * 4]);
+                bv[p][0] = b4.x;
+                bv[p][1] = b4.y;
+                bv[p][2] = b4.z;
+                bv[p][3] = b4.w;
+                if constexpr (RM == 4) {
+                    const uint4 a4 = *reinterpret_cast<const uint4 *>(&sa[p][kk][ty * 4]);
+                    av[p][0] = a4.x;
+                    av[p][1] = a4.y;
+                    av[p][2] = a4.z;
+                    av[p][3] = a4.w;
+                } else {
+                    av[p][0] = sa[p][kk][ty];
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < RM; r++)
+#pragma unroll
+                for (int c = 0; c < 4; c++)
+#pragma unroll
+                    for (int p = 0; p < PL; p++) acc[r][c][p] += (uint64_t)av[p][r] * bv[p][c];
+        }
+        __syncthreads();
+    }
+
+    const DevPrime pr = P[t];
+    const PieceConsts k = pc[t];
+    const uint64_t q = pr.q;
+#pragma unroll
+    for (int r = 0; r < RM; r++) {
+        const uint32_t m = m0 + ty * RM + r;
+        if (m >= M) continue;
+        uint64_t o[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            const uint64_t *s = acc[r][c];
+            uint64_t v;
+            if constexpr (NP == 2) {   // s00 + (sm - s00 - s11) 2^21 + s11 2^42
+                const uint64_t cross = s[2] - s[0] - s[1];
+                v = add_mod(shoup(s[0], 1, pr.one_sh, q), shoup(cross, k.c[0], k.c_sh[0], q), q);
+                v = add_mod(v, shoup(s[1], k.c[1], k.c_sh[1], q), q);
+            } else {         // s00 + c01 2^21 + (c02 + s11) 2^42 + c12 2^63 + s22 2^84
+                const uint64_t c01 = s[3] - s[0] - s[1], c02 = s[4] - s[0] - s[2], c12 = s[5] - s[1] - s[2];
+                v = add_mod(shoup(s[0], 1, pr.one_sh, q), shoup(c01, k.c[0], k.c_sh[0], q), q);
+                v = add_mod(v, shoup(c02 + s[1], k.c[1], k.c_sh[1], q), q);
+                v = add_mod(v, shoup(c12, k.c[2], k.c_sh[2], q), q);
+                v = add_mod(v, shoup(s[2], k.c[3], k.c_sh[3], q), q);
+            }
+            o[c] = v;
+        }
+        ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(y + (((uint64_t)m * 2 + poly) * L1 + t) * n + j0 + tx * 4);
+        dst[0] = make_ulonglong2(o[0], o[1]);
+        dst[1] = make_ulonglong2(o[2], o[3]);
+    }
+}
+
+// Throughput of the integer multiply-add forms on this GPU: every thread runs 8 independent
+// chains of `iters` multiply-adds (kind 0: mad.wide.u32, 32 x 32 -> 64 bits plus a 64-bit
+// addend, the GEMM's step; kind 1: mad.lo.u32).  Each step multiplies a word of the next
+// chain's accumulator, so no product is loop-invariant and no operand overlaps its own
+// destination; one word per thread keeps the chains live.
+template <int KIND>
+__global__ void __launch_bounds__(256) k_imad_peak(uint32_t seed, uint32_t iters, uint64_t *out) {
+    pdl_enter();
+    uint64_t acc[8];
+    uint32_t acc32[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        acc[i] = seed + threadIdx.x * 8 + i;
+        acc32[i] = (uint32_t)acc[i];
+    }
+    const uint32_t b = (seed ^ (blockIdx.x * 2654435761u)) | 1u;
+    for (uint32_t it = 0; it < iters; it++) {
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            if constexpr (KIND == 0)
+                asm volatile("mad.wide.u32 %0, %1, %2, %0;"
+                             : "+l"(acc[i])
+                             : "r"((uint32_t)(acc[(i + 1) & 7] >> 32)), "r"(b));
+            else
+                asm volatile("mad.lo.u32 %0, %1, %2, %0;" : "+r"(acc32[i]) : "r"(acc32[(i + 1) & 7]), "r"(b));
+        }
+    }
+    uint64_t x = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) x ^= acc[i] ^ acc32[i];
+    out[(uint64_t)blockIdx.x * blockDim.x + threadIdx.x] = x;
+}
+
+uint64_t pow2_mod(uint32_t e, uint64_t q) {
+    unsigned __int128 r = 1;
+    for (uint32_t i = 0; i < e; i++) r = (r * 2) % q;
+    return (uint64_t)r;
+}
+uint64_t shoup_companion(uint64_t w, uint64_t q) { return (uint64_t)(((unsigned __int128)w << 64) / q); }
+
+uint32_t pieces_of(uint64_t q) { return q < (1ull << 42) ? 2 : 3; }
+
+// the scalars of an M x K weight matrix (row-major, rows beyond M zero) at scale q_level,
+// cut into pieces per limb t <= level
+void build_matrix(hear_context *c, hear_simd_model::Layer &L, const std::vector<double> &W, uint32_t level,
+                  cudaStream_t st) {
+    const uint32_t L1 = level + 1, M = L.M, K = L.K;
+    L.Mpad = (M + kMpadUnit - 1) / kMpadUnit * kMpadUnit;
+    const uint64_t ql = c->primes[level];
+    std::vector<int64_t> sc((size_t)M * K);
+    for (size_t i = 0; i < sc.size(); i++) sc[i] = round_scalar(W[i], ql);
+    std::vector<uint64_t> off(L1);
+    uint64_t total = 0;
+    for (uint32_t t = 0; t < L1; t++) {
+        off[t] = total;
+        const uint32_t np = pieces_of(c->primes[t]);
+        total += (uint64_t)(np == 2 ? 3 : 6) * K * L.Mpad;
+        (np == 2 ? L.limbs2 : L.limbs3).push_back((uint8_t)t);
+    }
+    std::vector<uint32_t> A(total, 0u);
+    std::vector<PieceConsts> pcs(L1);
+    for (uint32_t t = 0; t < L1; t++) {
+        const uint64_t q = c->primes[t];
+        const uint32_t np = pieces_of(q), planes = np == 2 ? 3 : 6;
+        uint32_t *base = A.data() + off[t];
+        for (uint32_t m = 0; m < M; m++)
+            for (uint32_t k = 0; k < K; k++) {
+                const int64_t s = sc[(size_t)m * K + k];
+                const uint64_t r = s >= 0 ? (uint64_t)s % q : (q - (uint64_t)(-(s + 1)) % q - 1) % q;
+                const uint32_t a0 = (uint32_t)r & kPieceMask, a1 = (uint32_t)(r >> kPieceBits) & kPieceMask,
+                               a2 = (uint32_t)(r >> (2 * kPieceBits));
+                const uint32_t pv[6] = {a0, a1, np == 2 ? a0 + a1 : a2, a0 + a1, a0 + a2, a1 + a2};
+                for (uint32_t p = 0; p < planes; p++) base[((uint64_t)p * K + k) * L.Mpad + m] = pv[p];
+            }
+        for (int e = 0; e < 4; e++) {
+            pcs[t].c[e] = pow2_mod(kPieceBits * (e + 1), q);
+            pcs[t].c_sh[e] = shoup_companion(pcs[t].c[e], q);
+        }
+    }
+    L.a = DevBuf(total * 4, st);
+    L.a_off = DevBuf(L1 * 8, st);
+    L.consts = DevBuf(L1 * sizeof(PieceConsts), st);
+    HEAR_CHECK_CUDA(cudaMemcpyAsync(L.a.p, A.data(), total * 4, cudaMemcpyHostToDevice, st));
+    HEAR_CHECK_CUDA(cudaMemcpyAsync(L.a_off.p, off.data(), L1 * 8, cudaMemcpyHostToDevice, st));
+    HEAR_CHECK_CUDA(cudaMemcpyAsync(L.consts.p, pcs.data(), L1 * sizeof(PieceConsts), cudaMemcpyHostToDevice, st));
+    HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
+}
+
+// Y [Mpad... only M rows written][2][l+1][N] = scalars (.) X [K][2][l+1][N]
+void gemm(const hear_context *c, const hear_simd_model::Layer &L, uint32_t level, const uint64_t *x, uint64_t *y,
+          cudaStream_t st) {
+    const uint32_t L1 = level + 1, n = c->n;
+    const double bytes = 8.0 * (double)n * 2 * L1 * (L.K + L.M);
+    ProfScope ps(c, "k_simd_fc", st, bytes, (L.limbs2.empty() ? 0 : 1) + (L.limbs3.empty() ? 0 : 1));
+    const uint32_t gx = 2 * n / kTX;
+    HEAR_REQUIRE(gx <= 0x7fffffffu, HEAR_E_UNSUPPORTED, "ring too large");
+    const uint64_t *aoff = static_cast<const uint64_t *>(L.a_off.p);
+    const PieceConsts *pc = static_cast<const PieceConsts *>(L.consts.p);
+    if (!L.limbs2.empty()) {
+        LimbSet s{};
+        s.n = (uint32_t)L.limbs2.size();
+        for (uint32_t i = 0; i < s.n; i++) s.t[i] = L.limbs2[i];
+        launch(k_simd_fc<2>, dim3(gx, s.n, L.Mpad / Gemm<2>::TM), kGemmThreads, 0, st, x, y,
+               static_cast<const uint32_t *>(L.a.p), aoff, pc, s, L.M, L.Mpad, L.K, L1, n, c->dev_primes());
+    }
+    if (!L.limbs3.empty()) {
+        LimbSet s{};
+        s.n = (uint32_t)L.limbs3.size();
+        for (uint32_t i = 0; i < s.n; i++) s.t[i] = L.limbs3[i];
+        launch(k_simd_fc<3>, dim3(gx, s.n, L.Mpad / Gemm<3>::TM), kGemmThreads, 0, st, x, y,
+               static_cast<const uint32_t *>(L.a.p), aoff, pc, s, L.M, L.Mpad, L.K, L1, n, c->dev_primes());
+    }
+}
+
+}  // namespace
+
+double imad_peak(hear_context *c, int kind, uint32_t iters) {
+    HEAR_REQUIRE(kind == 0 || kind == 1, HEAR_E_INVAL, "kind must be 0 (mad.wide.u32) or 1 (mad.lo.u32)");
+    HEAR_REQUIRE(iters >= 1 && iters <= (1u << 20), HEAR_E_INVAL, "iters must be in [1, 2^20]");
+    int sms = 0;
+    HEAR_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    const uint32_t blocks = (uint32_t)sms * 8, threads = 256;
+    cudaStream_t st = c->stream;
+    DevBuf out((size_t)blocks * threads * 8, st);
+    auto run = [&](uint32_t it) {
+        if (kind == 0) launch(k_imad_peak<0>, blocks, threads, 0, st, 12345u, it, out.u64());
+        else launch(k_imad_peak<1>, blocks, threads, 0, st, 12345u, it, out.u64());
+    };
+    run(iters);   // warm-up
+    cudaEvent_t e0, e1;
+    HEAR_CHECK_CUDA(cudaEventCreate(&e0));
+    HEAR_CHECK_CUDA(cudaEventCreate(&e1));
+    HEAR_CHECK_CUDA(cudaEventRecord(e0, st));
+    run(iters);
+    HEAR_CHECK_CUDA(cudaEventRecord(e1, st));
+    HEAR_CHECK_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return (double)blocks * threads * 8.0 * iters / (ms / 1e3);
+}
+
+int64_t round_scalar(double w, uint64_t q) {
+    HEAR_REQUIRE(std::isfinite(w), HEAR_E_INVAL, "weight is not finite");
+    if (w == 0.0) return 0;
+    int e = 0;
+    const double fr = std::frexp(std::fabs(w), &e);            // |w| = fr 2^e, fr in [1/2, 1)
+    const uint64_t mant = (uint64_t)std::ldexp(fr, 53);        // |w| = mant 2^(e - 53), exact
+    const int sh = e - 53;
+    const unsigned __int128 pq = (unsigned __int128)mant * q;  // < 2^114
+    unsigned __int128 r;
+    HEAR_REQUIRE(sh < 0, HEAR_E_INVAL, "weight too large for the scale");   // |w| >= 2^53
+    if (-sh > 115) {
+        r = 0;                                                  // |w q| < 1/4
+    } else {
+        r = (pq + ((unsigned __int128)1 << (-sh - 1))) >> (-sh);   // half away from zero
+    }
+    HEAR_REQUIRE((r >> 62) == 0, HEAR_E_INVAL, "weight too large for the scale");
+    return w < 0 ? -(int64_t)r : (int64_t)r;
+}
+
+hear_simd_model *simd_model_create(hear_context *c, const hear_layer_desc *layers, size_t n_layers,
+                                   uint32_t level) {
+    HEAR_REQUIRE(layers && n_layers > 0, HEAR_E_INVAL, "no layers");
+    HEAR_REQUIRE(level >= 1 && level <= c->L, HEAR_E_LEVEL, "start level outside [1, L]");
+    auto m = std::make_unique<hear_simd_model>();
+    m->ctx = c;
+    m->level_in = level;
+    cudaStream_t st = c->stream;
+    uint32_t dim = 0;
+    for (size_t li = 0; li < n_layers; li++) {
+        const hear_layer_desc &d = layers[li];
+        hear_simd_model::Layer L;
+        L.kind = d.kind;
+        L.level_in = level;
+        if (li == 0) {
+            HEAR_REQUIRE(d.kind != HEAR_LAYER_SQUARE, HEAR_E_INVAL, "the first layer must be linear");
+            dim = d.d_in;
+            m->d_in = dim;
+        }
+        L.n_in = dim;
+        if (d.kind == HEAR_LAYER_FC || d.kind == HEAR_LAYER_FC_SQ_FC) {
+            HEAR_REQUIRE(d.w && d.d_in == dim && d.d_out >= 1, HEAR_E_INVAL, "FC input dimension mismatch");
+            HEAR_REQUIRE(!d.bias, HEAR_E_UNSUPPORTED, "bias is not supported");
+            HEAR_REQUIRE(d.d_in >= 1 && d.d_in <= kMaxK, HEAR_E_UNSUPPORTED, "FC input dimension above 2^19");
+        }
+        if (d.kind == HEAR_LAYER_FC) {
+            HEAR_REQUIRE(level >= 1, HEAR_E_LEVEL, "not enough levels for the network");
+            L.M = d.d_out;
+            L.K = d.d_in;
+            std::vector<double> W(d.w, d.w + (size_t)d.d_out * d.d_in);
+            build_matrix(c, L, W, level, st);
+            level -= 1;
+            dim = d.d_out;
+        } else if (d.kind == HEAR_LAYER_SQUARE) {
+            HEAR_REQUIRE(level >= 1, HEAR_E_LEVEL, "not enough levels for the network");
+            level -= 1;
+        } else if (d.kind == HEAR_LAYER_FC_SQ_FC) {
+            HEAR_REQUIRE(d.w2 && d.d_out2 >= 1, HEAR_E_INVAL, "FC_SQ_FC needs its second matrix");
+            HEAR_REQUIRE(level >= 2, HEAR_E_LEVEL, "not enough levels for the network");
+            const uint32_t d1 = d.d_out, d2 = d.d_out2, K = d.d_in;
+            L.d1 = d1;
+            L.d2 = d2;
+            L.M = 2 * d1 * d2;
+            L.K = K;
+            std::vector<double> W((size_t)L.M * K);
+            for (uint32_t r = 0; r < d1; r++)
+                for (uint32_t cc = 0; cc < d2; cc++)
+                    for (uint32_t i = 0; i < K; i++) {
+                        const double w1 = d.w[(size_t)r * K + i];
+                        W[((size_t)r * d2 + cc) * K + i] = w1;
+                        W[((size_t)d1 * d2 + r * d2 + cc) * K + i] = d.w2[(size_t)cc * d1 + r] * w1;
+                    }
+            build_matrix(c, L, W, level, st);
+            level -= 2;
+            dim = d2;
+        } else {
+            throw Error(HEAR_E_INVAL, "unknown layer kind");
+        }
+        L.n_out = dim;
+        L.level_out = level;
+        m->layers.push_back(std::move(L));
+    }
+    m->d_out = dim;
+    m->level_out = level;
+    return m.release();
+}
+
+DevBuf simd_evaluate(const hear_simd_model *m, const hear_eval_keys *evk, const uint64_t *x, double scale_in,
+                     double *scale_out, cudaStream_t st) {
+    hear_context *c = m->ctx;
+    const uint32_t n = c->n;
+    DevBuf cur;
+    const uint64_t *xin = x;
+    double scale = scale_in;
+    for (const hear_simd_model::Layer &L : m->layers) {
+        const uint32_t level = L.level_in;
+        const uint64_t plane = (uint64_t)(level + 1) * n, plane1 = (uint64_t)level * n;
+        DevBuf next;
+        if (L.kind == HEAR_LAYER_FC) {
+            DevBuf Y((size_t)L.M * 2 * plane * 8, st), tmp((size_t)L.M * 2 * plane1 * 8, st);
+            gemm(c, L, level, xin, Y.u64(), st);
+            next = DevBuf((size_t)L.M * 2 * plane1 * 8, st);
+            rescale(c, level, 2 * L.M, Y.u64(), next.u64(), tmp.u64(), st);
+            const double ql = (double)c->primes[level];
+            scale = scale * ql / ql;
+        } else if (L.kind == HEAR_LAYER_SQUARE) {
+            const uint64_t *rk = evk->key(1);
+            HEAR_REQUIRE(rk, HEAR_E_NOKEY, "missing relinearisation key");
+            DevBuf prod((size_t)L.n_in * 2 * plane * 8, st), tmp((size_t)L.n_in * 2 * plane1 * 8, st);
+            mul_relin(c, level, L.n_in, xin, xin, rk, prod.u64(), st);
+            next = DevBuf((size_t)L.n_in * 2 * plane1 * 8, st);
+            rescale(c, level, 2 * L.n_in, prod.u64(), next.u64(), tmp.u64(), st);
+            scale = scale * scale / (double)c->primes[level];
+        } else {
+            // y_r and u_(c,r) one level down, then sum_r y_r u_(c,r) as degree-2
+            // ciphertexts, one relinearisation and one rescale per output
+            const uint64_t *rk = evk->key(1);
+            HEAR_REQUIRE(rk, HEAR_E_NOKEY, "missing relinearisation key");
+            const uint32_t P2 = L.d1 * L.d2, lv = level - 1;
+            const uint64_t p1 = plane1, p2 = (uint64_t)lv * n;
+            DevBuf Y((size_t)L.M * 2 * plane * 8, st), Z((size_t)L.M * 2 * p1 * 8, st),
+                tmp((size_t)L.M * 2 * p1 * 8, st);
+            gemm(c, L, level, xin, Y.u64(), st);
+            rescale(c, level, 2 * L.M, Y.u64(), Z.u64(), tmp.u64(), st);
+            const double ql = (double)c->primes[level];
+            const double s1 = scale * ql / ql;
+            DevBuf T((size_t)P2 * 3 * p1 * 8, st), S((size_t)L.d2 * 3 * p1 * 8, st);
+            tensor_ct(c, lv, P2, Z.u64(), Z.u64() + (uint64_t)P2 * 2 * p1, T.u64(), st);
+            // T is ordered (r, c): sum over r = stride d2 degree-2 ciphertexts
+            sum_ct(c, lv, 3 * L.d2, T.u64(), (uint64_t)L.d2 * 3 * p1, L.d1, S.u64(), st);
+            DevBuf R((size_t)L.d2 * 2 * p1 * 8, st), tmp2((size_t)L.d2 * 2 * p2 * 8, st);
+            relin3(c, lv, L.d2, S.u64(), rk, R.u64(), st);
+            next = DevBuf((size_t)L.d2 * 2 * p2 * 8, st);
+            rescale(c, lv, 2 * L.d2, R.u64(), next.u64(), tmp2.u64(), st);
+            scale = s1 * s1 / (double)c->primes[lv];
+        }
+        cur = std::move(next);
+        xin = cur.u64();
+    }
+    *scale_out = scale;
+    return cur;
+}
+
+}  // namespace hear

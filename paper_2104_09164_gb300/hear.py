@@ -157,6 +157,21 @@ def _load():
                                   _vp]),
         "hear_cnn_evaluate": (st, [_vp, _vp, ctypes.c_size_t, ctypes.c_size_t, ctypes.POINTER(_vp),
                                    ctypes.c_size_t, ctypes.POINTER(_vp), _vp]),
+        "hear_simd_model_create": (st, [_vp, ctypes.POINTER(hear_layer_desc), ctypes.c_size_t, ctypes.c_uint32,
+                                        ctypes.POINTER(_vp)]),
+        "hear_simd_model_info": (st, [_vp, _u32p, _u32p, _u32p, _u32p]),
+        "hear_simd_model_destroy": (None, [_vp]),
+        "hear_simd_encrypt": (st, [_vp, _vp, _dp, ctypes.c_size_t, ctypes.c_size_t, ctypes.c_double,
+                                   ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(_vp), _vp]),
+        "hear_simd_batch_info": (st, [_vp, _u32p, _u32p, _dp]),
+        "hear_simd_batch_export": (st, [_vp, _u64p, ctypes.c_size_t, _szp]),
+        "hear_simd_batch_import": (st, [_vp, _u64p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_double,
+                                        ctypes.POINTER(_vp), _vp]),
+        "hear_simd_batch_destroy": (None, [_vp]),
+        "hear_simd_evaluate": (st, [_vp, _vp, _vp, ctypes.POINTER(_vp), _vp]),
+        "hear_simd_evaluate_host": (st, [_vp, _vp, _u64p, ctypes.c_double, _u64p, ctypes.c_size_t, _szp, _u32p,
+                                         _dp, _vp]),
+        "hear_simd_decrypt": (st, [_vp, _vp, _vp, ctypes.c_size_t, _dp, ctypes.c_size_t, _szp]),
         "hear_rescale_noalloc": (st, [_vp, _u64p, ctypes.c_uint32, ctypes.c_uint32, _u64p, _vp]),
         "hear_profile_begin": (st, [_vp]),
         "hear_profile_end": (st, [_vp, ctypes.POINTER(hear_profile_entry), ctypes.c_size_t, _szp]),
@@ -167,6 +182,7 @@ def _load():
         "hear_ntt_set_variant": (st, [_vp, ctypes.c_int]),
         "hear_ntt_get_table": (st, [_vp, ctypes.POINTER(ctypes.c_uint8)]),
         "hear_ntt_set_table": (st, [_vp, ctypes.POINTER(ctypes.c_uint8)]),
+        "hear_dbg_imad_peak": (st, [_vp, ctypes.c_int, ctypes.c_uint32, _dp]),
         "hear_dbg_poly_mul": (st, [_vp, ctypes.c_uint32, _u64p, _u64p, _u64p]),
         "hear_dbg_ntt_roundtrip": (st, [_vp, _u64p, ctypes.c_size_t]),
         "hear_dbg_ntt_time": (st, [_vp, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
@@ -363,10 +379,8 @@ def hear_multiply_relin(evk, a, b, stream=None):
 
 
 # ---------------------------------------------------------------- network
-def hear_model_create(ctx, layers, clip_dim, level=None, rotsum_radix=None, fc_n1=None, hoist_moddown=False):
-    """layers: sequence of ("fc", W) | ("square",) | ("fc_sq_fc", W1, W2) with float64 matrices;
-    level: input level (None = the top level); rotsum_radix, fc_n1, hoist_moddown: see
-    hear_model_opts"""
+def _layer_descs(layers):
+    """-> (hear_layer_desc array, the arrays it points into)"""
     descs = (hear_layer_desc * len(layers))()
     keep = []
     for i, layer in enumerate(layers):
@@ -384,6 +398,14 @@ def hear_model_create(ctx, layers, clip_dim, level=None, rotsum_radix=None, fc_n
             d.d_out2, d.w2 = W2.shape[0], _p(W2, _dp)
         else:
             raise ValueError(layer[0])
+    return descs, keep
+
+
+def hear_model_create(ctx, layers, clip_dim, level=None, rotsum_radix=None, fc_n1=None, hoist_moddown=False):
+    """layers: sequence of ("fc", W) | ("square",) | ("fc_sq_fc", W1, W2) with float64 matrices;
+    level: input level (None = the top level); rotsum_radix, fc_n1, hoist_moddown: see
+    hear_model_opts"""
+    descs, keep = _layer_descs(layers)
     h = _vp()
     if rotsum_radix is not None or fc_n1 is not None or hoist_moddown:
         opts = hear_model_opts(int(level or 0), int(rotsum_radix or 0), int(fc_n1 or 0), int(bool(hoist_moddown)))
@@ -452,6 +474,86 @@ def hear_evaluate_host(m, evk, in_words, n_ct, scale, out=None, stream=None):
     _check(lib.hear_evaluate_host(m, evk, _p(w, _u64p), int(n_ct), float(scale), _p(out, _u64p), out.size,
                                   ctypes.byref(n), ctypes.byref(lv), ctypes.byref(sc), _stream(stream)))
     return out, lv.value, sc.value
+
+
+# ---------------------------------------------------------------- slot-batched evaluation
+def hear_simd_model_create(ctx, layers, level=0):
+    """layers as for hear_model_create; level 0 = the top level"""
+    descs, keep = _layer_descs(layers)
+    h = _vp()
+    _check(lib.hear_simd_model_create(ctx, descs, len(layers), int(level), ctypes.byref(h)))
+    return h.value
+
+
+def hear_simd_model_info(m):
+    """-> (d_in, d_out, level_in, level_out)"""
+    v = [ctypes.c_uint32() for _ in range(4)]
+    _check(lib.hear_simd_model_info(m, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def hear_simd_model_destroy(m):
+    lib.hear_simd_model_destroy(m)
+
+
+def hear_simd_encrypt(ctx, pk, x, seed, level=0, scale=0.0, stream=None):
+    """x: [n_clips][n_features] -> batch of n_features ciphertexts, clip c in slot c"""
+    a = _arr(np.atleast_2d(x), np.float64)
+    h = _vp()
+    _check(lib.hear_simd_encrypt(ctx, pk, _p(a, _dp), a.shape[0], a.shape[1], float(scale), int(seed), int(level),
+                                 ctypes.byref(h), _stream(stream)))
+    return h.value
+
+
+def hear_simd_batch_info(b):
+    """-> (n_ct, level, scale)"""
+    n, lv, sc = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_double()
+    _check(lib.hear_simd_batch_info(b, ctypes.byref(n), ctypes.byref(lv), ctypes.byref(sc)))
+    return n.value, lv.value, sc.value
+
+
+def hear_simd_batch_export(b):
+    n_ct, lv, _ = hear_simd_batch_info(b)
+    return _vec_out(lib.hear_simd_batch_export, b, np.uint64, _u64p).reshape(n_ct, 2, lv + 1, -1)
+
+
+def hear_simd_batch_import(ctx, words, n_ct, level, scale, stream=None):
+    w = _arr(words, np.uint64).reshape(-1)
+    h = _vp()
+    _check(lib.hear_simd_batch_import(ctx, _p(w, _u64p), int(n_ct), int(level), float(scale), ctypes.byref(h),
+                                      _stream(stream)))
+    return h.value
+
+
+def hear_simd_batch_destroy(b):
+    lib.hear_simd_batch_destroy(b)
+
+
+def hear_simd_evaluate(m, evk, batch, stream=None):
+    h = _vp()
+    _check(lib.hear_simd_evaluate(m, evk, batch, ctypes.byref(h), _stream(stream)))
+    return h.value
+
+
+def hear_simd_evaluate_host(m, evk, in_words, scale, out=None, stream=None):
+    w = _arr(in_words, np.uint64).reshape(-1)
+    n = ctypes.c_size_t(0)
+    lv, sc = ctypes.c_uint32(), ctypes.c_double()
+    if out is None:
+        lib.hear_simd_evaluate_host(m, evk, _p(w, _u64p), float(scale), None, 0, ctypes.byref(n), None, None, None)
+        out = np.empty(n.value, dtype=np.uint64)
+    _check(lib.hear_simd_evaluate_host(m, evk, _p(w, _u64p), float(scale), _p(out, _u64p), out.size,
+                                       ctypes.byref(n), ctypes.byref(lv), ctypes.byref(sc), _stream(stream)))
+    return out, lv.value, sc.value
+
+
+def hear_simd_decrypt(ctx, sk, batch, n_clips):
+    """-> [n_clips][n_ct]"""
+    n_ct = hear_simd_batch_info(batch)[0]
+    out = np.empty(int(n_clips) * n_ct, dtype=np.float64)
+    n = ctypes.c_size_t(0)
+    _check(lib.hear_simd_decrypt(ctx, sk, batch, int(n_clips), _p(out, _dp), out.size, ctypes.byref(n)))
+    return out.reshape(int(n_clips), n_ct)
 
 
 # ---------------------------------------------------------------- skeleton CNN
@@ -618,6 +720,13 @@ def hear_pdl_launch_count():
 
 
 # ---------------------------------------------------------------- debug
+def hear_dbg_imad_peak(ctx, kind=0, iters=4096):
+    """lane operations per second of mad.wide.u32 (kind 0) or mad.lo.u32 (kind 1)"""
+    v = ctypes.c_double()
+    _check(lib.hear_dbg_imad_peak(ctx, int(kind), int(iters), ctypes.byref(v)))
+    return v.value
+
+
 HEAR_NTT_WIDE, HEAR_NTT_NARROW, HEAR_NTT_FUSED, HEAR_NTT_TINY = 0, 1, 2, 3
 
 
