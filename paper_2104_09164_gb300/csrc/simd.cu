@@ -21,18 +21,18 @@ namespace hear {
 namespace {
 
 constexpr int kGemmThreads = 256;
-constexpr int kTX = 64;                  // columns (residues of one limb) per CTA
 constexpr uint32_t kPieceBits = 21;
 constexpr uint32_t kPieceMask = (1u << kPieceBits) - 1;
 constexpr uint32_t kMaxK = 1u << 19;     // K * 2^44 < 2^63
 constexpr uint32_t kMpadUnit = 64;
 
 // PL planes of pieces (two-piece: a0, a1, a0 + a1; three-piece: a0, a1, a2, a0 + a1,
-// a0 + a2, a1 + a2), a CTA tile of TM rows x kTX columns, RM rows x 4 columns per thread
-// (16 x 16 threads), KC inner indices per shared-memory round
+// a0 + a2, a1 + a2), a CTA tile of TM rows x TX columns (residues of one limb), RM rows x CM
+// columns per thread (16 x 16 threads), KC inner indices per shared-memory round, MINB
+// resident CTAs per SM
 template <int NP> struct Gemm;
-template <> struct Gemm<2> { static constexpr int PL = 3, TM = 64, RM = 4, KC = 32; };
-template <> struct Gemm<3> { static constexpr int PL = 6, TM = 16, RM = 1, KC = 16; };
+template <> struct Gemm<2> { static constexpr int PL = 3, TM = 64, TX = 64, RM = 4, CM = 4, KC = 32, MINB = 2; };
+template <> struct Gemm<3> { static constexpr int PL = 6, TM = 32, TX = 32, RM = 2, CM = 2, KC = 16, MINB = 2; };
 
 struct LimbSet {
     uint32_t n;
@@ -43,6 +43,24 @@ struct LimbSet {
 struct PieceConsts {
     uint64_t c[4], c_sh[4];
 };
+
+// V consecutive words of shared memory (V = 1, 2 or 4; 4V-byte aligned) into registers
+template <int V>
+__device__ __forceinline__ void load_vec(const uint32_t *s, uint32_t *r) {
+    if constexpr (V == 4) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(s);
+        r[0] = v.x;
+        r[1] = v.y;
+        r[2] = v.z;
+        r[3] = v.w;
+    } else if constexpr (V == 2) {
+        const uint2 v = *reinterpret_cast<const uint2 *>(s);
+        r[0] = v.x;
+        r[1] = v.y;
+    } else {
+        r[0] = s[0];
+    }
+}
 
 template <int NP>
 __device__ __forceinline__ void split_pieces(uint64_t v, uint32_t *p) {
@@ -63,40 +81,41 @@ __device__ __forceinline__ void split_pieces(uint64_t v, uint32_t *p) {
 }
 
 // y[m][poly][t][j] = sum_k A_t[m][k] x[k][poly][t][j] mod q_t for the limbs of `limbs`
-// (blockIdx.y), rows m0 = blockIdx.z * TM .., columns (poly, j) = blockIdx.x * kTX ..
+// (blockIdx.y), rows m0 = blockIdx.z * TM .., columns (poly, j) = blockIdx.x * TX ..
 template <int NP>
-__global__ void __launch_bounds__(kGemmThreads, 2)
+__global__ void __launch_bounds__(kGemmThreads, Gemm<NP>::MINB)
 k_simd_fc(const uint64_t *__restrict__ x, uint64_t *__restrict__ y, const uint32_t *__restrict__ a,
           const uint64_t *__restrict__ a_off, const PieceConsts *__restrict__ pc, LimbSet limbs, uint32_t M,
           uint32_t Mpad, uint32_t K, uint32_t L1, uint32_t n, const DevPrime *__restrict__ P) {
     pdl_enter();
     using G = Gemm<NP>;
-    constexpr int PL = G::PL, TM = G::TM, RM = G::RM, KC = G::KC;
+    constexpr int PL = G::PL, TM = G::TM, TX = G::TX, RM = G::RM, CM = G::CM, KC = G::KC;
+    static_assert(TM == 16 * RM && TX == 16 * CM, "16 x 16 threads");
     __shared__ __align__(16) uint32_t sa[PL][KC][TM];
-    __shared__ __align__(16) uint32_t sb[PL][KC][kTX];
+    __shared__ __align__(16) uint32_t sb[PL][KC][TX];
     const uint32_t t = limbs.t[blockIdx.y];
     const uint32_t m0 = blockIdx.z * TM;
-    const uint32_t col0 = blockIdx.x * kTX;
+    const uint32_t col0 = blockIdx.x * TX;
     const uint32_t poly = col0 / n, j0 = col0 % n;
     const uint32_t tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const uint64_t xrow = 2ull * L1 * n;                                // words per input ciphertext
     const uint64_t *xb = x + ((uint64_t)poly * L1 + t) * n + j0;      // inner index k at xb + k * xrow
     const uint32_t *ab = a + a_off[t] + m0;                            // plane p, index k: + (p K + k) Mpad
 
-    uint64_t acc[RM][4][PL];
+    uint64_t acc[RM][CM][PL];
 #pragma unroll
     for (int r = 0; r < RM; r++)
 #pragma unroll
-        for (int c = 0; c < 4; c++)
+        for (int c = 0; c < CM; c++)
 #pragma unroll
             for (int p = 0; p < PL; p++) acc[r][c][p] = 0;
 
-    constexpr int WPT = KC * kTX / kGemmThreads;   // residues of x per thread per round
-    constexpr int TPR = kTX / WPT;                 // threads per inner index
-    static_assert(WPT % 2 == 0 && TPR * WPT == kTX, "x tile split");
+    constexpr int WPT = KC * TX / kGemmThreads;    // residues of x per thread per round
+    constexpr int TPR = TX / WPT;                  // threads per inner index
+    static_assert(WPT % 2 == 0 && TPR * WPT == TX, "x tile split");
     constexpr int A4 = PL * KC * TM / 4;           // uint4 of pieces per round
     for (uint32_t k0 = 0; k0 < K; k0 += KC) {
-        {   // x: KC inner indices x 64 residues, cut into pieces
+        {   // x: KC inner indices x TX residues, cut into pieces
             const uint32_t r = threadIdx.x / TPR, c = (threadIdx.x % TPR) * WPT;
             uint64_t v[WPT];
             if (k0 + r < K) {
@@ -128,30 +147,18 @@ k_simd_fc(const uint64_t *__restrict__ x, uint64_t *__restrict__ y, const uint32
             *reinterpret_cast<uint4 *>(&sa[p][r][c4 * 4]) = val;
         }
         __syncthreads();
-#pragma unroll 4
+#pragma unroll
         for (int kk = 0; kk < KC; kk++) {
-            uint32_t av[PL][RM], bv[PL][4];
+            uint32_t av[PL][RM], bv[PL][CM];
 #pragma unroll
             for (int p = 0; p < PL; p++) {
-                const uint4 b4 = *reinterpret_cast<const uint4 *>(&sb[p][kk][tx * 4]);
-                bv[p][0] = b4.x;
-                bv[p][1] = b4.y;
-                bv[p][2] = b4.z;
-                bv[p][3] = b4.w;
-                if constexpr (RM == 4) {
-                    const uint4 a4 = *reinterpret_cast<const uint4 *>(&sa[p][kk][ty * 4]);
-                    av[p][0] = a4.x;
-                    av[p][1] = a4.y;
-                    av[p][2] = a4.z;
-                    av[p][3] = a4.w;
-                } else {
-                    av[p][0] = sa[p][kk][ty];
-                }
+                load_vec<CM>(&sb[p][kk][tx * CM], bv[p]);
+                load_vec<RM>(&sa[p][kk][ty * RM], av[p]);
             }
 #pragma unroll
             for (int r = 0; r < RM; r++)
 #pragma unroll
-                for (int c = 0; c < 4; c++)
+                for (int c = 0; c < CM; c++)
 #pragma unroll
                     for (int p = 0; p < PL; p++) acc[r][c][p] += (uint64_t)av[p][r] * bv[p][c];
         }
@@ -165,9 +172,9 @@ k_simd_fc(const uint64_t *__restrict__ x, uint64_t *__restrict__ y, const uint32
     for (int r = 0; r < RM; r++) {
         const uint32_t m = m0 + ty * RM + r;
         if (m >= M) continue;
-        uint64_t o[4];
+        uint64_t o[CM];
 #pragma unroll
-        for (int c = 0; c < 4; c++) {
+        for (int c = 0; c < CM; c++) {
             const uint64_t *s = acc[r][c];
             uint64_t v;
             if constexpr (NP == 2) {   // s00 + (sm - s00 - s11) 2^21 + s11 2^42
@@ -183,9 +190,9 @@ k_simd_fc(const uint64_t *__restrict__ x, uint64_t *__restrict__ y, const uint32
             }
             o[c] = v;
         }
-        ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(y + (((uint64_t)m * 2 + poly) * L1 + t) * n + j0 + tx * 4);
-        dst[0] = make_ulonglong2(o[0], o[1]);
-        dst[1] = make_ulonglong2(o[2], o[3]);
+        ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(y + (((uint64_t)m * 2 + poly) * L1 + t) * n + j0 + tx * CM);
+#pragma unroll
+        for (int c = 0; c < CM; c += 2) dst[c / 2] = make_ulonglong2(o[c], o[c + 1]);
     }
 }
 
@@ -283,22 +290,21 @@ void gemm(const hear_context *c, const hear_simd_model::Layer &L, uint32_t level
     const uint32_t L1 = level + 1, n = c->n;
     const double bytes = 8.0 * (double)n * 2 * L1 * (L.K + L.M);
     ProfScope ps(c, "k_simd_fc", st, bytes, (L.limbs2.empty() ? 0 : 1) + (L.limbs3.empty() ? 0 : 1));
-    const uint32_t gx = 2 * n / kTX;
-    HEAR_REQUIRE(gx <= 0x7fffffffu, HEAR_E_UNSUPPORTED, "ring too large");
+
     const uint64_t *aoff = static_cast<const uint64_t *>(L.a_off.p);
     const PieceConsts *pc = static_cast<const PieceConsts *>(L.consts.p);
     if (!L.limbs2.empty()) {
         LimbSet s{};
         s.n = (uint32_t)L.limbs2.size();
         for (uint32_t i = 0; i < s.n; i++) s.t[i] = L.limbs2[i];
-        launch(k_simd_fc<2>, dim3(gx, s.n, L.Mpad / Gemm<2>::TM), kGemmThreads, 0, st, x, y,
+        launch(k_simd_fc<2>, dim3(2 * n / Gemm<2>::TX, s.n, L.Mpad / Gemm<2>::TM), kGemmThreads, 0, st, x, y,
                static_cast<const uint32_t *>(L.a.p), aoff, pc, s, L.M, L.Mpad, L.K, L1, n, c->dev_primes());
     }
     if (!L.limbs3.empty()) {
         LimbSet s{};
         s.n = (uint32_t)L.limbs3.size();
         for (uint32_t i = 0; i < s.n; i++) s.t[i] = L.limbs3[i];
-        launch(k_simd_fc<3>, dim3(gx, s.n, L.Mpad / Gemm<3>::TM), kGemmThreads, 0, st, x, y,
+        launch(k_simd_fc<3>, dim3(2 * n / Gemm<3>::TX, s.n, L.Mpad / Gemm<3>::TM), kGemmThreads, 0, st, x, y,
                static_cast<const uint32_t *>(L.a.p), aoff, pc, s, L.M, L.Mpad, L.K, L1, n, c->dev_primes());
     }
 }
