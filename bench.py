@@ -490,9 +490,10 @@ def _time_range(H, m, evk, op0, op1, cts, n_samples, torch, stream, iters):
 
 
 def simd_mad_lanes(primes, layers, level, n):
-    """algorithmic mad.wide.u32 lane operations of the slot-batched matrix products: per FC
-    row, input and residue, 3 for a two-piece limb (q < 2^42, Karatsuba) and 6 for a
-    three-piece one"""
+    """algorithmic multiply-pipe work of the slot-batched matrix products in mad.wide.u32
+    lane operations: per FC row, input and residue the three Karatsuba partial products of two
+    pieces (one mad.wide.u32 each below 2^42; a multiply-low / multiply-high pair, the same
+    pipe time, for the 60-bit primes)"""
     total = 0.0
     for layer in layers:
         if layer[0] == "square":
@@ -504,7 +505,7 @@ def simd_mad_lanes(primes, layers, level, n):
         else:
             M, K = 2 * layer[1].shape[0] * layer[2].shape[0], layer[1].shape[1]
             used = 2
-        cost = sum(3 if primes[t] < (1 << 42) else 6 for t in range(level + 1))
+        cost = 3 * (level + 1)
         total += float(M) * K * 2 * n * cost
         level -= used
     return total

@@ -5,12 +5,15 @@
 // round(w q_l), i.e. the encoding of the constant slot vector w at scale q_l; Methods,
 // "Non-convolutional layers", with every slot a different clip) and needs no rotation.  Per
 // limb t this is a product of an M x K matrix of residues with a K x 2N matrix of residues,
-// done here as a modular matrix product on the integer pipes (the exact arithmetic rules the
-// tensor cores out).  Each residue a < 2^63 is cut into 21-bit pieces so that every
-// partial product is one 32 x 32 -> 64-bit multiply-add and K <= 2^19 of them sum without
-// overflow in 64 bits.  With a0 b1 + a1 b0 = (a0 + a1)(b0 + b1) - a0 b0 - a1 b1 a product of
-// two-piece residues (primes below 2^42) takes three multiply-adds and one of three-piece
-// residues six; the 64-bit partial sums are reduced mod q_t once per output.
+// done here as a modular matrix product on the integer multiply-add pipe (the exact
+// arithmetic rules the tensor cores out).  Each residue is cut into two pieces and the three
+// partial products of Karatsuba's identity a0 b1 + a1 b0 = (a0 + a1)(b0 + b1) - a0 b0 - a1 b1
+// are summed over K and reduced mod q_t once per output:
+//  * primes below 2^42: 21-bit pieces, every partial product one 32 x 32 -> 64-bit
+//    multiply-add (mad.wide.u32) into a 64-bit sum (K <= 2^19 products of < 2^44);
+//  * primes below 2^62: 31-bit pieces, every partial product a multiply-low / multiply-high
+//    pair added into a 96-bit sum by one carry chain.
+// Both forms hold the multiply pipe the same number of cycles per partial product.
 #include <cmath>
 #include <mutex>
 #include "simd.h"
@@ -21,30 +24,33 @@ namespace hear {
 namespace {
 
 constexpr int kGemmThreads = 256;
-constexpr uint32_t kPieceBits = 21;
-constexpr uint32_t kPieceMask = (1u << kPieceBits) - 1;
 constexpr uint32_t kMaxK = 1u << 19;     // K * 2^44 < 2^63
 constexpr uint32_t kMpadUnit = 64;
 
-// PL planes of pieces (two-piece: a0, a1, a0 + a1; three-piece: a0, a1, a2, a0 + a1,
-// a0 + a2, a1 + a2), a CTA tile of TM rows x TX columns (residues of one limb), RM rows x CM
-// columns per thread (16 x 16 threads), KC inner indices per shared-memory round, MINB
-// resident CTAs per SM
-template <int NP> struct Gemm;
-template <> struct Gemm<2> { static constexpr int PL = 3, TM = 64, TX = 64, RM = 4, CM = 4, KC = 32, MINB = 2; };
-template <> struct Gemm<3> { static constexpr int PL = 6, TM = 32, TX = 32, RM = 2, CM = 2, KC = 16, MINB = 2; };
+// KIND 0: 21-bit pieces (q < 2^42), 64-bit sums; KIND 1: 31-bit pieces (q < 2^62), 96-bit
+// sums.  Planes of pieces: a0, a1, a0 + a1.  A CTA tile of TM rows x TX columns (residues of
+// one limb), RM rows x CM columns per thread (16 x 16 threads), KC inner indices per
+// shared-memory round, MINB resident CTAs per SM.
+template <int KIND> struct Gemm;
+template <> struct Gemm<0> {
+    static constexpr int BITS = 21, TM = 64, TX = 64, RM = 4, CM = 4, KC = 32, MINB = 2;
+};
+template <> struct Gemm<1> {
+    static constexpr int BITS = 31, TM = 32, TX = 32, RM = 2, CM = 2, KC = 32, MINB = 2;
+};
+constexpr int kPlanes = 3;
 
 struct LimbSet {
     uint32_t n;
     uint8_t t[kMaxPrimes];
 };
 
-// 2^21, 2^42, 2^63, 2^84 mod q_t and their Shoup companions
+// per limb: c[0] = 2^BITS, c[1] = 2^(2 BITS), c[2] = 2^64 mod q_t and their Shoup companions
 struct PieceConsts {
     uint64_t c[4], c_sh[4];
 };
 
-// V consecutive words of shared memory (V = 1, 2 or 4; 4V-byte aligned) into registers
+// V consecutive words of shared memory (V = 2 or 4; 4V-byte aligned) into registers
 template <int V>
 __device__ __forceinline__ void load_vec(const uint32_t *s, uint32_t *r) {
     if constexpr (V == 4) {
@@ -53,43 +59,48 @@ __device__ __forceinline__ void load_vec(const uint32_t *s, uint32_t *r) {
         r[1] = v.y;
         r[2] = v.z;
         r[3] = v.w;
-    } else if constexpr (V == 2) {
+    } else {
         const uint2 v = *reinterpret_cast<const uint2 *>(s);
         r[0] = v.x;
         r[1] = v.y;
-    } else {
-        r[0] = s[0];
     }
 }
 
-template <int NP>
+template <int KIND>
 __device__ __forceinline__ void split_pieces(uint64_t v, uint32_t *p) {
-    const uint32_t b0 = (uint32_t)v & kPieceMask, b1 = (uint32_t)(v >> kPieceBits) & kPieceMask;
-    if constexpr (NP == 2) {
-        p[0] = b0;
-        p[1] = b1;
-        p[2] = b0 + b1;
-    } else {
-        const uint32_t b2 = (uint32_t)(v >> (2 * kPieceBits));
-        p[0] = b0;
-        p[1] = b1;
-        p[2] = b2;
-        p[3] = b0 + b1;
-        p[4] = b0 + b2;
-        p[5] = b1 + b2;
-    }
+    constexpr int B = Gemm<KIND>::BITS;
+    const uint32_t b0 = (uint32_t)v & ((1u << B) - 1), b1 = (uint32_t)(v >> B);
+    p[0] = b0;
+    p[1] = b1;
+    p[2] = b0 + b1;
+}
+
+// (x2 x1 x0) += a * b: one carry chain of a multiply-low, a multiply-high and a carry add
+__device__ __forceinline__ void mac96(uint32_t a, uint32_t b, uint32_t &x0, uint32_t &x1, uint32_t &x2) {
+    asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
+        "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
+        "addc.u32 %2, %2, 0;"
+        : "+r"(x0), "+r"(x1), "+r"(x2)
+        : "r"(a), "r"(b));
+}
+
+// a 96-bit sum (x2 x1 x0) mod q
+__device__ __forceinline__ uint64_t reduce96(uint32_t x0, uint32_t x1, uint32_t x2, const DevPrime &pr,
+                                             const PieceConsts &k) {
+    const uint64_t lo = ((uint64_t)x1 << 32) | x0;
+    return add_mod(shoup(lo, 1, pr.one_sh, pr.q), shoup(x2, k.c[2], k.c_sh[2], pr.q), pr.q);
 }
 
 // y[m][poly][t][j] = sum_k A_t[m][k] x[k][poly][t][j] mod q_t for the limbs of `limbs`
 // (blockIdx.y), rows m0 = blockIdx.z * TM .., columns (poly, j) = blockIdx.x * TX ..
-template <int NP>
-__global__ void __launch_bounds__(kGemmThreads, Gemm<NP>::MINB)
+template <int KIND>
+__global__ void __launch_bounds__(kGemmThreads, Gemm<KIND>::MINB)
 k_simd_fc(const uint64_t *__restrict__ x, uint64_t *__restrict__ y, const uint32_t *__restrict__ a,
           const uint64_t *__restrict__ a_off, const PieceConsts *__restrict__ pc, LimbSet limbs, uint32_t M,
           uint32_t Mpad, uint32_t K, uint32_t L1, uint32_t n, const DevPrime *__restrict__ P) {
     pdl_enter();
-    using G = Gemm<NP>;
-    constexpr int PL = G::PL, TM = G::TM, TX = G::TX, RM = G::RM, CM = G::CM, KC = G::KC;
+    using G = Gemm<KIND>;
+    constexpr int PL = kPlanes, TM = G::TM, TX = G::TX, RM = G::RM, CM = G::CM, KC = G::KC;
     static_assert(TM == 16 * RM && TX == 16 * CM, "16 x 16 threads");
     __shared__ __align__(16) uint32_t sa[PL][KC][TM];
     __shared__ __align__(16) uint32_t sb[PL][KC][TX];
@@ -102,13 +113,18 @@ k_simd_fc(const uint64_t *__restrict__ x, uint64_t *__restrict__ y, const uint32
     const uint64_t *xb = x + ((uint64_t)poly * L1 + t) * n + j0;      // inner index k at xb + k * xrow
     const uint32_t *ab = a + a_off[t] + m0;                            // plane p, index k: + (p K + k) Mpad
 
-    uint64_t acc[RM][CM][PL];
+    // KIND 0: 64-bit sums s00, s11, sm; KIND 1: three 96-bit sums as 32-bit words
+    uint64_t acc[RM][CM][KIND == 0 ? PL : 1];
+    uint32_t acw[RM][CM][KIND == 1 ? 3 * PL : 1];
 #pragma unroll
     for (int r = 0; r < RM; r++)
 #pragma unroll
-        for (int c = 0; c < CM; c++)
+        for (int c = 0; c < CM; c++) {
 #pragma unroll
-            for (int p = 0; p < PL; p++) acc[r][c][p] = 0;
+            for (int p = 0; p < (KIND == 0 ? PL : 1); p++) acc[r][c][p] = 0;
+#pragma unroll
+            for (int p = 0; p < (KIND == 1 ? 3 * PL : 1); p++) acw[r][c][p] = 0;
+        }
 
     constexpr int WPT = KC * TX / kGemmThreads;    // residues of x per thread per round
     constexpr int TPR = TX / WPT;                  // threads per inner index
@@ -117,8 +133,7 @@ k_simd_fc(const uint64_t *__restrict__ x, uint64_t *__restrict__ y, const uint32
     for (uint32_t k0 = 0; k0 < K; k0 += KC) {
         {   // x: KC inner indices x TX residues, cut into pieces
             const uint32_t r = threadIdx.x / TPR, c = (threadIdx.x % TPR) * WPT;
-            uint64_t v[WPT];
-            if (k0 + r < K) {
+            uint64_t v[WPT];            if (k0 + r < K) {
                 const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(xb + (uint64_t)(k0 + r) * xrow + c);
 #pragma unroll
                 for (int w = 0; w < WPT / 2; w++) {
@@ -133,7 +148,7 @@ k_simd_fc(const uint64_t *__restrict__ x, uint64_t *__restrict__ y, const uint32
 #pragma unroll
             for (int w = 0; w < WPT; w++) {
                 uint32_t pcs[PL];
-                split_pieces<NP>(v[w], pcs);
+                split_pieces<KIND>(v[w], pcs);
 #pragma unroll
                 for (int p = 0; p < PL; p++) sb[p][r][c + w] = pcs[p];
             }
@@ -160,7 +175,12 @@ k_simd_fc(const uint64_t *__restrict__ x, uint64_t *__restrict__ y, const uint32
 #pragma unroll
                 for (int c = 0; c < CM; c++)
 #pragma unroll
-                    for (int p = 0; p < PL; p++) acc[r][c][p] += (uint64_t)av[p][r] * bv[p][c];
+                    for (int p = 0; p < PL; p++) {
+                        if constexpr (KIND == 0)
+                            acc[r][c][p] += (uint64_t)av[p][r] * bv[p][c];
+                        else
+                            mac96(av[p][r], bv[p][c], acw[r][c][3 * p], acw[r][c][3 * p + 1], acw[r][c][3 * p + 2]);
+                    }
         }
         __syncthreads();
     }
@@ -175,18 +195,28 @@ k_simd_fc(const uint64_t *__restrict__ x, uint64_t *__restrict__ y, const uint32
         uint64_t o[CM];
 #pragma unroll
         for (int c = 0; c < CM; c++) {
-            const uint64_t *s = acc[r][c];
             uint64_t v;
-            if constexpr (NP == 2) {   // s00 + (sm - s00 - s11) 2^21 + s11 2^42
+            if constexpr (KIND == 0) {   // s00 + (sm - s00 - s11) 2^21 + s11 2^42
+                const uint64_t *s = acc[r][c];
                 const uint64_t cross = s[2] - s[0] - s[1];
                 v = add_mod(shoup(s[0], 1, pr.one_sh, q), shoup(cross, k.c[0], k.c_sh[0], q), q);
                 v = add_mod(v, shoup(s[1], k.c[1], k.c_sh[1], q), q);
-            } else {         // s00 + c01 2^21 + (c02 + s11) 2^42 + c12 2^63 + s22 2^84
-                const uint64_t c01 = s[3] - s[0] - s[1], c02 = s[4] - s[0] - s[2], c12 = s[5] - s[1] - s[2];
-                v = add_mod(shoup(s[0], 1, pr.one_sh, q), shoup(c01, k.c[0], k.c_sh[0], q), q);
-                v = add_mod(v, shoup(c02 + s[1], k.c[1], k.c_sh[1], q), q);
-                v = add_mod(v, shoup(c12, k.c[2], k.c_sh[2], q), q);
-                v = add_mod(v, shoup(s[2], k.c[3], k.c_sh[3], q), q);
+            } else {                     // the same with 96-bit sums and 2^31, 2^62
+                const uint32_t *w = acw[r][c];
+                uint32_t c0, c1, c2;     // cross = sm - s00 - s11 (never negative)
+                asm("sub.cc.u32 %0, %3, %6;\n\t"
+                    "subc.cc.u32 %1, %4, %7;\n\t"
+                    "subc.u32 %2, %5, %8;"
+                    : "=r"(c0), "=r"(c1), "=r"(c2)
+                    : "r"(w[6]), "r"(w[7]), "r"(w[8]), "r"(w[0]), "r"(w[1]), "r"(w[2]));
+                asm("sub.cc.u32 %0, %0, %3;\n\t"
+                    "subc.cc.u32 %1, %1, %4;\n\t"
+                    "subc.u32 %2, %2, %5;"
+                    : "+r"(c0), "+r"(c1), "+r"(c2)
+                    : "r"(w[3]), "r"(w[4]), "r"(w[5]));
+                v = add_mod(reduce96(w[0], w[1], w[2], pr, k),
+                            shoup(reduce96(c0, c1, c2, pr, k), k.c[0], k.c_sh[0], q), q);
+                v = add_mod(v, shoup(reduce96(w[3], w[4], w[5], pr, k), k.c[1], k.c_sh[1], q), q);
             }
             o[c] = v;
         }
@@ -236,10 +266,14 @@ uint64_t pow2_mod(uint32_t e, uint64_t q) {
 }
 uint64_t shoup_companion(uint64_t w, uint64_t q) { return (uint64_t)(((unsigned __int128)w << 64) / q); }
 
-uint32_t pieces_of(uint64_t q) { return q < (1ull << 42) ? 2 : 3; }
+// residue kind of a prime: 0 = 21-bit pieces (q < 2^42), 1 = 31-bit pieces (q < 2^62)
+int kind_of(uint64_t q) {
+    HEAR_REQUIRE(q < (1ull << 62), HEAR_E_UNSUPPORTED, "prime above 2^62");
+    return q < (1ull << 42) ? 0 : 1;
+}
 
 // the scalars of an M x K weight matrix (row-major, rows beyond M zero) at scale q_level,
-// cut into pieces per limb t <= level
+// cut into pieces per limb t <= level: planes a0, a1, a0 + a1, each [K][Mpad]
 void build_matrix(hear_context *c, hear_simd_model::Layer &L, const std::vector<double> &W, uint32_t level,
                   cudaStream_t st) {
     const uint32_t L1 = level + 1, M = L.M, K = L.K;
@@ -247,66 +281,61 @@ void build_matrix(hear_context *c, hear_simd_model::Layer &L, const std::vector<
     const uint64_t ql = c->primes[level];
     std::vector<int64_t> sc((size_t)M * K);
     for (size_t i = 0; i < sc.size(); i++) sc[i] = round_scalar(W[i], ql);
+    const uint64_t per_limb = (uint64_t)kPlanes * K * L.Mpad;
     std::vector<uint64_t> off(L1);
-    uint64_t total = 0;
     for (uint32_t t = 0; t < L1; t++) {
-        off[t] = total;
-        const uint32_t np = pieces_of(c->primes[t]);
-        total += (uint64_t)(np == 2 ? 3 : 6) * K * L.Mpad;
-        (np == 2 ? L.limbs2 : L.limbs3).push_back((uint8_t)t);
+        off[t] = t * per_limb;
+        (kind_of(c->primes[t]) == 0 ? L.limbs_narrow : L.limbs_wide).push_back((uint8_t)t);
     }
-    std::vector<uint32_t> A(total, 0u);
+    std::vector<uint32_t> A(L1 * per_limb, 0u);
     std::vector<PieceConsts> pcs(L1);
     for (uint32_t t = 0; t < L1; t++) {
         const uint64_t q = c->primes[t];
-        const uint32_t np = pieces_of(q), planes = np == 2 ? 3 : 6;
+        const uint32_t bits = kind_of(q) == 0 ? Gemm<0>::BITS : Gemm<1>::BITS;
         uint32_t *base = A.data() + off[t];
         for (uint32_t m = 0; m < M; m++)
             for (uint32_t k = 0; k < K; k++) {
                 const int64_t s = sc[(size_t)m * K + k];
                 const uint64_t r = s >= 0 ? (uint64_t)s % q : (q - (uint64_t)(-(s + 1)) % q - 1) % q;
-                const uint32_t a0 = (uint32_t)r & kPieceMask, a1 = (uint32_t)(r >> kPieceBits) & kPieceMask,
-                               a2 = (uint32_t)(r >> (2 * kPieceBits));
-                const uint32_t pv[6] = {a0, a1, np == 2 ? a0 + a1 : a2, a0 + a1, a0 + a2, a1 + a2};
-                for (uint32_t p = 0; p < planes; p++) base[((uint64_t)p * K + k) * L.Mpad + m] = pv[p];
+                const uint32_t a0 = (uint32_t)(r & ((1ull << bits) - 1)), a1 = (uint32_t)(r >> bits);
+                const uint32_t pv[kPlanes] = {a0, a1, a0 + a1};
+                for (int p = 0; p < kPlanes; p++) base[((uint64_t)p * K + k) * L.Mpad + m] = pv[p];
             }
-        for (int e = 0; e < 4; e++) {
-            pcs[t].c[e] = pow2_mod(kPieceBits * (e + 1), q);
-            pcs[t].c_sh[e] = shoup_companion(pcs[t].c[e], q);
+        const uint32_t e[4] = {bits, 2 * bits, 64, 0};
+        for (int i = 0; i < 4; i++) {
+            pcs[t].c[i] = pow2_mod(e[i], q);
+            pcs[t].c_sh[i] = shoup_companion(pcs[t].c[i], q);
         }
     }
-    L.a = DevBuf(total * 4, st);
+    L.a = DevBuf(A.size() * 4, st);
     L.a_off = DevBuf(L1 * 8, st);
     L.consts = DevBuf(L1 * sizeof(PieceConsts), st);
-    HEAR_CHECK_CUDA(cudaMemcpyAsync(L.a.p, A.data(), total * 4, cudaMemcpyHostToDevice, st));
+    HEAR_CHECK_CUDA(cudaMemcpyAsync(L.a.p, A.data(), A.size() * 4, cudaMemcpyHostToDevice, st));
     HEAR_CHECK_CUDA(cudaMemcpyAsync(L.a_off.p, off.data(), L1 * 8, cudaMemcpyHostToDevice, st));
     HEAR_CHECK_CUDA(cudaMemcpyAsync(L.consts.p, pcs.data(), L1 * sizeof(PieceConsts), cudaMemcpyHostToDevice, st));
     HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
 }
 
-// Y [Mpad... only M rows written][2][l+1][N] = scalars (.) X [K][2][l+1][N]
+template <int KIND>
+void launch_gemm(const hear_context *c, const hear_simd_model::Layer &L, const std::vector<uint8_t> &limbs,
+                 uint32_t L1, const uint64_t *x, uint64_t *y, cudaStream_t st) {
+    if (limbs.empty()) return;
+    LimbSet s{};
+    s.n = (uint32_t)limbs.size();
+    for (uint32_t i = 0; i < s.n; i++) s.t[i] = limbs[i];
+    launch(k_simd_fc<KIND>, dim3(2 * c->n / Gemm<KIND>::TX, s.n, L.Mpad / Gemm<KIND>::TM), kGemmThreads, 0, st, x,
+           y, static_cast<const uint32_t *>(L.a.p), static_cast<const uint64_t *>(L.a_off.p),
+           static_cast<const PieceConsts *>(L.consts.p), s, L.M, L.Mpad, L.K, L1, c->n, c->dev_primes());
+}
+
+// Y [M][2][l+1][N] = scalars (.) X [K][2][l+1][N]
 void gemm(const hear_context *c, const hear_simd_model::Layer &L, uint32_t level, const uint64_t *x, uint64_t *y,
           cudaStream_t st) {
-    const uint32_t L1 = level + 1, n = c->n;
-    const double bytes = 8.0 * (double)n * 2 * L1 * (L.K + L.M);
-    ProfScope ps(c, "k_simd_fc", st, bytes, (L.limbs2.empty() ? 0 : 1) + (L.limbs3.empty() ? 0 : 1));
-
-    const uint64_t *aoff = static_cast<const uint64_t *>(L.a_off.p);
-    const PieceConsts *pc = static_cast<const PieceConsts *>(L.consts.p);
-    if (!L.limbs2.empty()) {
-        LimbSet s{};
-        s.n = (uint32_t)L.limbs2.size();
-        for (uint32_t i = 0; i < s.n; i++) s.t[i] = L.limbs2[i];
-        launch(k_simd_fc<2>, dim3(2 * n / Gemm<2>::TX, s.n, L.Mpad / Gemm<2>::TM), kGemmThreads, 0, st, x, y,
-               static_cast<const uint32_t *>(L.a.p), aoff, pc, s, L.M, L.Mpad, L.K, L1, n, c->dev_primes());
-    }
-    if (!L.limbs3.empty()) {
-        LimbSet s{};
-        s.n = (uint32_t)L.limbs3.size();
-        for (uint32_t i = 0; i < s.n; i++) s.t[i] = L.limbs3[i];
-        launch(k_simd_fc<3>, dim3(2 * n / Gemm<3>::TX, s.n, L.Mpad / Gemm<3>::TM), kGemmThreads, 0, st, x, y,
-               static_cast<const uint32_t *>(L.a.p), aoff, pc, s, L.M, L.Mpad, L.K, L1, n, c->dev_primes());
-    }
+    const uint32_t L1 = level + 1;
+    const double bytes = 8.0 * (double)c->n * 2 * L1 * (L.K + L.M);
+    ProfScope ps(c, "k_simd_fc", st, bytes, (L.limbs_narrow.empty() ? 0 : 1) + (L.limbs_wide.empty() ? 0 : 1));
+    launch_gemm<0>(c, L, L.limbs_narrow, L1, x, y, st);
+    launch_gemm<1>(c, L, L.limbs_wide, L1, x, y, st);
 }
 
 }  // namespace

@@ -13,10 +13,10 @@ struct hear_simd_model {
         // K input ciphertexts; FC_SQ_FC rows are (r, c) -> W1[r] for r*d2 + c, then
         // W2[c, r] W1[r] for d1*d2 + r*d2 + c
         uint32_t M = 0, Mpad = 0, K = 0, d1 = 0, d2 = 0;
-        hear::DevBuf a;                    // u32 pieces, limb t at a_off[t]: [planes][K][Mpad]
+        hear::DevBuf a;                    // u32 pieces, limb t at a_off[t]: [3 planes][K][Mpad]
         hear::DevBuf a_off;                // u64 [L1] offsets into a
         hear::DevBuf consts;               // per-limb reduction constants
-        std::vector<uint8_t> limbs2, limbs3;   // limbs with two- / three-piece residues
+        std::vector<uint8_t> limbs_narrow, limbs_wide;   // primes below 2^42 / below 2^62
     };
     hear_context *ctx = nullptr;
     uint32_t d_in = 0, d_out = 0, level_in = 0, level_out = 0;
