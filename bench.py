@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--mix-rates", default="100,300,1000", help="request rates (req/s) of the mixed sweep")
     ap.add_argument("--conv-rows", default="all", help="Table 1 rows to time: all | comma-separated indices")
     ap.add_argument("--no-simd", action="store_true", help="skip the slot-batched (one clip per slot) rows")
+    ap.add_argument("--no-fc-tune", action="store_true",
+                    help="evaluate every network in the default FC form instead of the tuned one")
     ap.add_argument("--simd-rows", default="all",
                     help="slot-batched rows: all | comma-separated indices into small@top, small@level3, large@top")
     return ap.parse_args()
@@ -242,11 +244,18 @@ def oracle_sample(w, steps_keys, seconds_budget=25.0):
 
 # ------------------------------------------------------------------ GPU arm
 class Setup:
-    def __init__(self, H, w, stream, device, level=None, fc_n1=None, hoist_moddown=False):
+    def __init__(self, H, w, stream, device, level=None, fc_n1=None, hoist_moddown=False, tune=False):
         """level: evaluate from ciphertexts dropped to this level (None = the top level);
-        fc_n1 / hoist_moddown: the FC evaluation form (hear_model_opts)"""
+        fc_n1 / hoist_moddown: the FC evaluation form (hear_model_opts); tune: pick the form by
+        timing the candidates at this batch size first (autotune.tune_fc)"""
         self.H, self.w = H, w
         self.ctx = H.hear_context_create(w.log_n, w.q_bits, w.p_bits, w.log2_scale, w.sigma, device)
+        report = None
+        if tune:
+            from paper_2104_09164_gb300.autotune import tune_fc
+            (fc_n1, hoist_moddown), report = tune_fc(H, self.ctx, w.layers, w.clip_dim, w.n_ct, w.slots, level,
+                                                     stream=stream)
+        self.fc_form = {"fc_n1": fc_n1, "hoist_moddown": hoist_moddown, "tuned": report}
         self.model = H.hear_model_create(self.ctx, w.layers, w.clip_dim, level, fc_n1=fc_n1,
                                          hoist_moddown=hoist_moddown)
         self.steps = H.hear_model_rotations(self.model)
@@ -705,7 +714,7 @@ def main_gpu(a):
     from paper_2104_09164_gb300.workloads import make_workload
     stream = torch.cuda.Stream(device=device)
     w = make_workload(a.workload, a.clips)
-    S = Setup(H, w, stream, device)
+    S = Setup(H, w, stream, device, tune=not a.no_fc_tune)
     total_ms, lat, launches, clocks = run_gpu(S, a.steps, a.warmup, dist, torch, stream, device)
     total_ms = dist.max(total_ms)
     value = dist.world * a.steps * S.clips_per_step / (total_ms / 1e3)
@@ -737,6 +746,8 @@ def main_gpu(a):
         # the NTT launch-variant table this run used (pin it with HEAR_NTT_TABLE to profile
         # the same kernels)
         result["config"]["ntt_table"] = H.hear_ntt_get_table(S.ctx)
+        # the FC evaluation form (baby steps, hoisted ModDown) and how it was chosen
+        result["config"]["fc_form"] = S.fc_form
         # kernels captured with programmatic dependent launch so far (HEAR_PDL=0: none)
         result["config"]["pdl_launches_captured"] = H.hear_pdl_launch_count()
     if result is not None and not a.no_served and a.workload == "small" and a.clips is None and dist.world == 1:
@@ -755,7 +766,7 @@ def main_gpu(a):
     if not a.no_batched and a.workload == "small" and a.clips is None:
         S.close()
         wl = make_workload("large")
-        SL = Setup(H, wl, stream, device)
+        SL = Setup(H, wl, stream, device, tune=not a.no_fc_tune)
         bsteps = max(3, a.steps // 4)
         tms, blat, bl, bclk = run_gpu(SL, bsteps, 2, dist, torch, stream, device)
         tms = dist.max(tms)
@@ -764,6 +775,7 @@ def main_gpu(a):
             result["batched"] = {"workload": describe(wl), "value": dist.world * bsteps * SL.clips_per_step / (tms / 1e3),
                                  "unit": UNIT, "ms_per_step": tms / bsteps, "steps": bsteps,
                                  "p50_ms": blat[len(blat) // 2], "gpu_launches": bl, "clocks": bclk,
+                                 "fc_form": SL.fc_form,
                                  "stages_ms_per_step": {k: v[1] / bps for k, v in
                                                         sorted(bst.items(), key=lambda kv: -kv[1][1])[:8]},
                                  # algorithmic bytes / stage time (HBM roofline of each stage)
@@ -778,22 +790,22 @@ def main_gpu(a):
         # the same small network batched: clips packed 4 per ciphertext, many ciphertexts per
         # launch (one CUDA-graph replay per step), against the plain one-clip-per-launch path
         rows = []
-        # the same model as the plain path, then a throughput form of it: FC baby steps 32
-        # with hoisted ModDown (fewer ModUps of giant steps, one ModDown per giant sum)
-        for n_clips, fc_n1, dh in ((128, None, False), (512, None, False), (512, 32, True)):
+        # the FC form tuned for each batch size, and the default form at 512 clips
+        for n_clips, tune in ((128, True), (512, True), (512, False)):
             wb = make_workload("small", n_clips)
-            SB = Setup(H, wb, stream, device, fc_n1=fc_n1, hoist_moddown=dh)
+            SB = Setup(H, wb, stream, device, tune=tune and not a.no_fc_tune)
             bsteps = 5
             tms, blat, bl, bclk = run_gpu(SB, bsteps, 2, dist, torch, stream, device)
             v = bsteps * SB.clips_per_step / (tms / 1e3)
-            rows.append({"clips": n_clips, "ciphertexts": wb.n_ct, "fc_n1": fc_n1, "hoist_moddown": dh,
+            rows.append({"clips": n_clips, "ciphertexts": wb.n_ct, "fc_n1": SB.fc_form["fc_n1"],
+                         "hoist_moddown": SB.fc_form["hoist_moddown"], "fc_tuned": SB.fc_form["tuned"] is not None,
                          "value": v, "unit": UNIT,
                          "ms_per_step": tms / bsteps, "p50_ms": blat[len(blat) // 2], "gpu_launches": bl,
                          "clocks": bclk, "vs_plain": v / result["value"]})
             SB.close()
         result["batched_small"] = {"workload": "small network (as the plain path), batches of 128 / 512 clips "
-                                               "in 32 / 128 ciphertexts per launch; last row: FC with 32 baby "
-                                               "steps and hoisted ModDown", "rows": rows}
+                                               "in 32 / 128 ciphertexts per launch, FC form tuned per batch "
+                                               "size; last row: the default FC form", "rows": rows}
     if result is not None and not a.no_min_level and a.workload == "small" and a.clips is None and dist.world == 1:
         # minimal start level: inputs dropped to the depth of the network (3 of 7 levels for
         # the small network, 5 of 14 for the large one); the same networks and parameters

@@ -1,4 +1,5 @@
-"""Per-layer strategy autotuning of the encrypted skeleton CNN.
+"""Strategy autotuning: the per-layer rotation split of the encrypted skeleton CNN and the FC
+evaluation form of the FC / x^2 networks.
 
 Every convolution of Eq. (conv) can split its rotations r_k + dist*l into a hoisted baby
 step and a giant step applied to the summed products in several ways -- the full-step,
@@ -131,3 +132,64 @@ def tune_cnn(H, ctx, spec, slots, top_level, n_samples=1, iters=3, stream=None):
 
 def _name(s):
     return s if isinstance(s, str) else "%s(%d)" % s
+
+
+# ---------------------------------------------------------------- FC evaluation form
+def fc_candidates(layers):
+    """(fc_n1, hoist_moddown) forms to try for a network of FC / x^2 layers: baby-step counts
+    d/2, d and 2d around d = the smallest power of two with d^2 >= D of the widest FC (D = its
+    output dimension; each layer clamps n1 to its own D), each with and without hoisted ModDown"""
+    D = max(layer[1].shape[0] for layer in layers if layer[0] == "fc")
+    d = 1
+    while d * d < D:
+        d *= 2
+    n1s = sorted({max(2, d // 2), d, min(2 * d, D)})
+    return [(n1, dh) for n1 in n1s for dh in (False, True)]
+
+
+def tune_fc(H, ctx, layers, clip_dim, n_ct, slots, level=None, steps=3, warmup=1, stream=None, seed=7):
+    """-> ((fc_n1, hoist_moddown), report): the fastest FC evaluation form (Methods,
+    "Algorithmic and cryptographic optimizations": the baby-step / giant-step split and where
+    the ModDown of the hoisted rotations happens) for whole-network evaluations of n_ct
+    ciphertexts, timed through the C ABI (CUDA-graph replay, CUDA events on `stream`) on random
+    inputs with throw-away keys.  Every form computes the same network; the oracle evaluates
+    each one bit-exactly."""
+    import torch
+    st = stream if stream is not None else torch.cuda.Stream()
+    rng = np.random.default_rng(seed)
+    report = []
+    for n1, dh in fc_candidates(layers):
+        t0 = time.perf_counter()
+        m = H.hear_model_create(ctx, layers, clip_dim, level, fc_n1=n1, hoist_moddown=dh)
+        try:
+            sk, pk, evk = H.hear_keygen(ctx, 9001, H.hear_model_rotations(m))
+            cts = []
+            for i in range(n_ct):
+                c = H.hear_encrypt(ctx, pk, rng.uniform(-1.0, 1.0, slots), 2.0 ** 40, 9002, i, st)
+                if level is not None:
+                    low = H.hear_ciphertext_drop_level(c, level, st)
+                    H.hear_ciphertext_destroy(c)
+                    c = low
+                cts.append(c)
+            for _ in range(warmup):
+                for o in H.hear_evaluate(m, evk, cts, st):
+                    H.hear_ciphertext_destroy(o)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(steps):
+                for o in H.hear_evaluate(m, evk, cts, st):
+                    H.hear_ciphertext_destroy(o)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            for c in cts:
+                H.hear_ciphertext_destroy(c)
+            H.hear_eval_keys_destroy(evk)
+            H.hear_public_key_destroy(pk)
+            H.hear_secret_key_destroy(sk)
+        finally:
+            H.hear_model_destroy(m)
+        report.append({"fc_n1": n1, "hoist_moddown": dh, "ms": ms, "tune_s": time.perf_counter() - t0})
+    best = min(report, key=lambda r: r["ms"])
+    return (best["fc_n1"], best["hoist_moddown"]), report

@@ -19,7 +19,8 @@ def H():
     return hear
 
 
-@pytest.mark.parametrize("name,n1,n_clips", [("small", 16, 8), ("small", 64, 8), ("large", None, 16)])
+@pytest.mark.parametrize("name,n1,n_clips", [("small", 16, 8), ("small", 64, 8), ("large", None, 16),
+                                             ("large", 64, 16)])
 def test_hoisted_moddown_bit_exact(H, name, n1, n_clips):
     w = make_workload(name, n_clips)
     ctx = H.hear_context_create(w.log_n, w.q_bits, w.p_bits, w.log2_scale, w.sigma, 0)
