@@ -449,13 +449,13 @@ def run_served(H, S, rates, seconds=2.0, max_batch=32, n_slots=2, seed=601):
         sv.close()
 
 
-def run_served_mix(H, stream, device, rates, seconds=2.0, seed=602):
+def run_served_mix(H, stream, device, rates, seconds=2.0, seed=602, tune=True):
     """70% small / 30% large requests from one Poisson stream, each network served by its
     own continuous-batching server (own context, keys resident in HBM, HBM budget for the
     ciphertexts in flight); both servers' batches share the GPU."""
     from paper_2104_09164_gb300.workloads import make_workload
-    Ss = Setup(H, make_workload("small"), stream, device)
-    Sl = Setup(H, make_workload("large", 8), stream, device)
+    Ss = Setup(H, make_workload("small"), stream, device, tune=tune)
+    Sl = Setup(H, make_workload("large", 8), stream, device, tune=tune)
     servers = []
     try:
         servers.append(Served(H, Ss, 32, 2, 48 << 30))
@@ -762,7 +762,8 @@ def main_gpu(a):
                         "stream; one continuous-batching server per network (max batch 32 / 8 "
                         "ciphertexts, 2 batches in flight each), both on one GPU",
             "note": "latency = client submit -> result read back (host), per rate and network",
-            "sweep": run_served_mix(H, stream, device, [float(x) for x in a.mix_rates.split(",")])}
+            "sweep": run_served_mix(H, stream, device, [float(x) for x in a.mix_rates.split(",")],
+                                    tune=not a.no_fc_tune)}
     if not a.no_batched and a.workload == "small" and a.clips is None:
         S.close()
         wl = make_workload("large")
@@ -812,9 +813,9 @@ def main_gpu(a):
         ms = {}
         for name, level, steps in (("small", 3, a.steps), ("large", 5, max(3, a.steps // 4))):
             wl = make_workload(name)
-            SM = Setup(H, wl, stream, device, level)
+            SM = Setup(H, wl, stream, device, level, tune=not a.no_fc_tune)
             tms, mlat, ml, mclk = run_gpu(SM, steps, 2, dist, torch, stream, device)
-            ms[name] = {"workload": describe(wl), "start_level": level,
+            ms[name] = {"workload": describe(wl), "start_level": level, "fc_form": SM.fc_form,
                         "value": steps * SM.clips_per_step / (tms / 1e3), "unit": UNIT,
                         "ms_per_step": tms / steps, "p50_ms": mlat[len(mlat) // 2],
                         "p99_ms": mlat[min(len(mlat) - 1, int(0.99 * len(mlat)))], "gpu_launches": ml,
