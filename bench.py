@@ -610,6 +610,55 @@ def run_simd(H, torch, stream, device, plain_value, rows=SIMD_ROWS, steps=3, war
     return out
 
 
+def run_ragged(H, torch, stream, device, tune=True, n_req=64, seed=603, steps=3):
+    """ragged mixed batch: n_req requests of U{1..32} clips, 70 % for the small network
+    (N = 2^14, 4 clips per ciphertext) and 30 % for the large one (N = 2^15, 8 per ciphertext),
+    both networks evaluated by ONE CUDA-graph launch (hear_multi) against the same two
+    evaluations launched one after the other"""
+    from paper_2104_09164_gb300.workloads import make_workload
+    rng = np.random.default_rng(seed)
+    clips = rng.integers(1, 33, n_req)
+    small = rng.random(n_req) < 0.7
+    n_s, n_l = int(clips[small].sum()), int(clips[~small].sum())
+    Ss = Setup(H, make_workload("small", n_s), stream, device, tune=tune)
+    Sl = Setup(H, make_workload("large", n_l), stream, device, tune=tune)
+    mu = H.hear_multi_create([Ss.model, Sl.model], [Ss.evk, Sl.evk], [len(Ss.cts), len(Sl.cts)],
+                             [2.0 ** 40, 2.0 ** 40])
+    try:
+        cts = Ss.cts + Sl.cts
+
+        def one():
+            for o in H.hear_multi_evaluate(mu, cts, stream):
+                H.hear_ciphertext_destroy(o)
+
+        def two():
+            for S in (Ss, Sl):
+                for o in H.hear_evaluate(S.model, S.evk, S.cts, stream):
+                    H.hear_ciphertext_destroy(o)
+
+        res = {}
+        for name, fn in (("one_launch", one), ("two_launches", two)):
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res[name] = e0.elapsed_time(e1) / steps
+        return {"workload": "%d requests of 1-32 clips: %d small-network clips (%d ciphertexts, N=2^14) and %d "
+                            "large-network clips (%d ciphertexts, N=2^15)" % (n_req, n_s, len(Ss.cts), n_l, len(Sl.cts)),
+                "value": (n_s + n_l) / (res["one_launch"] / 1e3), "unit": UNIT, "ms_per_step": res["one_launch"],
+                "two_launches_ms": res["two_launches"], "steps": steps,
+                "fc_form": {"small": {k: v for k, v in Ss.fc_form.items() if k != "tuned"},
+                            "large": {k: v for k, v in Sl.fc_form.items() if k != "tuned"}}}
+    finally:
+        H.hear_multi_destroy(mu)
+        Ss.close()
+        Sl.close()
+
+
 def run_conv_table(H, torch, stream, device, rows, iters=5):
     from paper_2104_09164_gb300.workloads import CONV_BENCH_PARAMS, TABLE1_LAYERS, conv_bench_layer
     log_n, qb, pb = CONV_BENCH_PARAMS
@@ -822,6 +871,8 @@ def main_gpu(a):
                         "clocks": mclk}
             SM.close()
         result["min_start_level"] = ms
+    if result is not None and not a.no_batched and a.workload == "small" and a.clips is None and dist.world == 1:
+        result["ragged_mix"] = run_ragged(H, torch, stream, device, tune=not a.no_fc_tune)
     if result is not None and not a.no_simd and a.workload == "small" and a.clips is None and dist.world == 1:
         result["batched_simd"] = {
             "note": "slot-batched form: the batch's clips one per slot, FC layers as plaintext-scalar "

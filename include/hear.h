@@ -61,6 +61,7 @@ typedef struct hear_eval_keys hear_eval_keys;
 typedef struct hear_ciphertext hear_ciphertext;
 typedef struct hear_model hear_model;
 typedef struct hear_cnn hear_cnn;
+typedef struct hear_multi hear_multi;
 typedef struct hear_simd_model hear_simd_model;
 typedef struct hear_simd_batch hear_simd_batch;
 
@@ -212,6 +213,18 @@ hear_status hear_model_output_positions(const hear_model *m, uint32_t *pos, size
 /* evaluate the whole network on n_ct ciphertexts (one batch; all at the top level) */
 hear_status hear_evaluate(const hear_model *m, const hear_eval_keys *evk, hear_ciphertext *const *in, size_t n_ct,
                           hear_ciphertext **out, void *stream);
+/* several networks -- own contexts, possibly different ring sizes (e.g. the small N = 2^14
+ * and the large N = 2^15 network), one device -- evaluated by ONE CUDA-graph launch whose
+ * branches run concurrently: job i evaluates models[i] with evks[i] on n_ct[i] ciphertexts at
+ * the model's input level and scales[i].  Creating it runs every job once and captures the
+ * graph; destroy it before any of its models or keys. */
+hear_status hear_multi_create(const hear_model *const *models, const hear_eval_keys *const *evks, size_t n_jobs,
+                              const uint32_t *n_ct, const double *scales, hear_multi **out);
+/* in: the jobs' input ciphertexts concatenated (job 0's n_ct[0] first); out (caller array of
+ * the same length): the result ciphertexts in the same order, as hear_evaluate gives them;
+ * stream null = the first job's context stream */
+hear_status hear_multi_evaluate(hear_multi *mu, hear_ciphertext *const *in, hear_ciphertext **out, void *stream);
+void hear_multi_destroy(hear_multi *mu);
 /* evaluate layer `layer` only (input at that layer's level) */
 hear_status hear_evaluate_layer(const hear_model *m, size_t layer, const hear_eval_keys *evk,
                                 hear_ciphertext *const *in, size_t n_ct, hear_ciphertext **out, void *stream);

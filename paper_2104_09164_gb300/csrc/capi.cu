@@ -519,6 +519,58 @@ hear_status hear_evaluate(const hear_model *m, const hear_eval_keys *evk, hear_c
     return evaluate_range(m, 0, m->layers.size(), evk, in, n_ct, out, stream);
 }
 
+hear_status hear_multi_create(const hear_model *const *models, const hear_eval_keys *const *evks, size_t n_jobs,
+                              const uint32_t *n_ct, const double *scales, hear_multi **out) {
+    if (!models || !evks || !n_ct || !scales || !out || n_jobs == 0) return fail(HEAR_E_INVAL, "null argument");
+    for (size_t i = 0; i < n_jobs; i++) {
+        if (!models[i] || !evks[i]) return fail(HEAR_E_INVAL, "null model or keys");
+        if (evks[i]->ctx != models[i]->ctx) return fail(HEAR_E_STATE, "keys from another context");
+        if (models[i]->ctx->device != models[0]->ctx->device) return fail(HEAR_E_INVAL, "jobs on different devices");
+        if (n_ct[i] == 0 || !(scales[i] > 0)) return fail(HEAR_E_INVAL, "empty job or bad scale");
+    }
+    hear_context *c = models[0]->ctx;
+    return guard(c, [&] { *out = multi_create(models, evks, n_jobs, n_ct, scales, c->stream); });
+}
+
+hear_status hear_multi_evaluate(hear_multi *mu, hear_ciphertext *const *in, hear_ciphertext **out, void *stream) {
+    if (!mu || !in || !out) return fail(HEAR_E_INVAL, "null argument");
+    size_t k = 0;
+    for (size_t j = 0; j < mu->models.size(); j++)
+        for (uint32_t i = 0; i < mu->n_ct[j]; i++, k++) {
+            const hear_ciphertext *ct = in[k];
+            if (!ct || ct->ctx != mu->models[j]->ctx) return fail(HEAR_E_STATE, "ciphertext from another context");
+            if (ct->level != mu->level_in[j] || ct->n_poly != 2) return fail(HEAR_E_LEVEL, "input not at the job's level");
+            if (ct->scale != mu->scale_in[j]) return fail(HEAR_E_SCALE, "input not at the job's scale");
+        }
+    hear_context *c0 = mu->models[0]->ctx;
+    return guard(c0, [&] {
+        cudaStream_t st = stream_of(c0, stream);
+        HEAR_CHECK_CUDA(cudaStreamWaitEvent(st, mu->done, 0));
+        size_t kk = 0;
+        for (size_t j = 0; j < mu->models.size(); j++) {
+            const uint64_t ctw = 2ull * (mu->level_in[j] + 1) * mu->models[j]->ctx->n;
+            for (uint32_t i = 0; i < mu->n_ct[j]; i++, kk++)
+                HEAR_CHECK_CUDA(cudaMemcpyAsync(mu->X[j].u64() + i * ctw, in[kk]->d.p, ctw * 8, cudaMemcpyDeviceToDevice, st));
+        }
+        HEAR_CHECK_CUDA(cudaGraphLaunch(mu->exec, st));
+        g_launches += mu->launches;
+        std::vector<std::unique_ptr<hear_ciphertext>> res;
+        for (size_t j = 0; j < mu->models.size(); j++) {
+            hear_context *c = mu->models[j]->ctx;
+            const uint64_t otw = 2ull * (mu->level_out[j] + 1) * c->n;
+            for (uint32_t i = 0; i < mu->n_ct[j]; i++) {
+                res.emplace_back(new_ct(c, mu->level_out[j], 2, mu->scale_out[j], st));
+                HEAR_CHECK_CUDA(cudaMemcpyAsync(res.back()->d.p, mu->Y[j].u64() + i * otw, otw * 8,
+                                                cudaMemcpyDeviceToDevice, st));
+            }
+        }
+        HEAR_CHECK_CUDA(cudaEventRecord(mu->done, st));
+        for (size_t i = 0; i < res.size(); i++) out[i] = res[i].release();
+    });
+}
+
+void hear_multi_destroy(hear_multi *mu) { delete mu; }
+
 hear_status hear_evaluate_layer(const hear_model *m, size_t layer, const hear_eval_keys *evk,
                                 hear_ciphertext *const *in, size_t n_ct, hear_ciphertext **out, void *stream) {
     if (!m || layer >= m->layers.size()) return fail(HEAR_E_INVAL, "bad layer index");

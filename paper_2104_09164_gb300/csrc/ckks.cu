@@ -637,7 +637,90 @@ hear_model::Plan *graph_plan(const hear_model *m, const hear_eval_keys *evk, siz
     return m->plans.back().get();
 }
 
+hear_multi *multi_create(const hear_model *const *models, const hear_eval_keys *const *evks, size_t n_jobs,
+                         const uint32_t *n_ct, const double *scales, cudaStream_t st) {
+    auto mu = std::make_unique<hear_multi>();
+    for (size_t i = 0; i < n_jobs; i++) {
+        const hear_model *m = models[i];
+        hear_context *c = m->ctx;
+        mu->models.push_back(m);
+        mu->evks.push_back(evks[i]);
+        mu->n_ct.push_back(n_ct[i]);
+        mu->scale_in.push_back(scales[i]);
+        mu->level_in.push_back(m->layers.front().level_in);
+        mu->level_out.push_back(m->layers.back().level_out);
+        const uint64_t in_words = (uint64_t)n_ct[i] * 2 * (mu->level_in[i] + 1) * c->n;
+        const uint64_t out_words = (uint64_t)n_ct[i] * 2 * (mu->level_out[i] + 1) * c->n;
+        mu->X.emplace_back(in_words * 8, nullptr);
+        mu->Y.emplace_back(out_words * 8, nullptr);
+        HEAR_CHECK_CUDA(cudaMemsetAsync(mu->X[i].p, 0, in_words * 8, st));
+        uint32_t lo;
+        double so;
+        DevBuf y = evaluate_batch(m, evks[i], 0, m->layers.size(), mu->X[i].u64(), n_ct[i], &lo, scales[i], &so, st);
+        mu->scale_out.push_back(so);
+    }
+    HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
+    std::vector<cudaStream_t> cs(n_jobs, nullptr);
+    std::vector<cudaEvent_t> ev(n_jobs, nullptr);
+    auto cleanup = [&] {
+        for (auto e : ev)
+            if (e) cudaEventDestroy(e);
+        for (auto s : cs)
+            if (s) cudaStreamDestroy(s);
+    };
+    cudaGraph_t graph = nullptr;
+    try {
+        for (size_t i = 0; i < n_jobs; i++) {
+            HEAR_CHECK_CUDA(cudaStreamCreateWithFlags(&cs[i], cudaStreamNonBlocking));
+            HEAR_CHECK_CUDA(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming));
+        }
+        const uint64_t launches0 = g_launches.load();
+        HEAR_CHECK_CUDA(cudaStreamBeginCapture(cs[0], cudaStreamCaptureModeThreadLocal));
+        try {
+            // fork: every job's stream joins the capture after its start, then runs its network
+            HEAR_CHECK_CUDA(cudaEventRecord(ev[0], cs[0]));
+            for (size_t i = 1; i < n_jobs; i++) HEAR_CHECK_CUDA(cudaStreamWaitEvent(cs[i], ev[0], 0));
+            for (size_t i = 0; i < n_jobs; i++) {
+                const hear_model *m = mu->models[i];
+                uint32_t lo;
+                double so;
+                DevBuf y = evaluate_batch(m, mu->evks[i], 0, m->layers.size(), mu->X[i].u64(), mu->n_ct[i], &lo,
+                                          mu->scale_in[i], &so, cs[i]);
+                HEAR_CHECK_CUDA(cudaMemcpyAsync(mu->Y[i].p, y.p, mu->Y[i].bytes, cudaMemcpyDeviceToDevice, cs[i]));
+            }
+            // join
+            for (size_t i = 1; i < n_jobs; i++) {
+                HEAR_CHECK_CUDA(cudaEventRecord(ev[i], cs[i]));
+                HEAR_CHECK_CUDA(cudaStreamWaitEvent(cs[0], ev[i], 0));
+            }
+        } catch (...) {
+            cudaStreamEndCapture(cs[0], &graph);
+            if (graph) cudaGraphDestroy(graph);
+            graph = nullptr;
+            throw;
+        }
+        HEAR_CHECK_CUDA(cudaStreamEndCapture(cs[0], &graph));
+        mu->launches = g_launches.load() - launches0;
+        cudaError_t e = cudaGraphInstantiate(&mu->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        HEAR_CHECK_CUDA(e);
+        HEAR_CHECK_CUDA(cudaEventCreateWithFlags(&mu->done, cudaEventDisableTiming));
+    } catch (...) {
+        cleanup();
+        throw;
+    }
+    cleanup();
+    return mu.release();
+}
+
 }  // namespace hear
+
+hear_multi::~hear_multi() {
+    if (!models.empty()) cudaSetDevice(models.front()->ctx->device);
+    if (done) cudaEventSynchronize(done);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (done) cudaEventDestroy(done);
+}
 
 hear_model::Plan::~Plan() {
     if (exec) cudaGraphExecDestroy(exec);

@@ -50,6 +50,20 @@ struct hear_model {
     std::vector<int32_t> rotations;
 };
 
+// Several networks (own contexts, possibly different ring sizes, one device) evaluated by one
+// CUDA graph whose branches -- one per job, captured on forked streams -- run concurrently.
+struct hear_multi {
+    std::vector<const hear_model *> models;
+    std::vector<const hear_eval_keys *> evks;
+    std::vector<uint32_t> n_ct, level_in, level_out;
+    std::vector<double> scale_in, scale_out;
+    std::vector<hear::DevBuf> X, Y;    // per job: input / output batches the graph reads / writes
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;        // the last launch finished with X / Y
+    uint64_t launches = 0;
+    ~hear_multi();
+};
+
 namespace hear {
 
 void forget_encoder(hear_context *ctx);
@@ -112,5 +126,9 @@ DevBuf evaluate_batch(const hear_model *m, const hear_eval_keys *evk, size_t l0,
 // then stream capture); the caller fills plan->X, launches plan->exec and reads plan->Y
 hear_model::Plan *graph_plan(const hear_model *m, const hear_eval_keys *evk, size_t l0, size_t l1, uint32_t n_ct,
                              double scale_in, cudaStream_t st, uint32_t slot = 0);
+// the one-launch graph of several whole-network jobs (see hear_multi); one direct warm-up run
+// of every job on `st` first (builds the tables the capture needs)
+hear_multi *multi_create(const hear_model *const *models, const hear_eval_keys *const *evks, size_t n_jobs,
+                         const uint32_t *n_ct, const double *scales, cudaStream_t st);
 
 }  // namespace hear

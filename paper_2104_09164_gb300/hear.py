@@ -141,6 +141,10 @@ def _load():
                                      ctypes.POINTER(_vp), _vp]),
         "hear_evaluate_host": (st, [_vp, _vp, _u64p, ctypes.c_size_t, ctypes.c_double, _u64p, ctypes.c_size_t,
                                     _szp, _u32p, _dp, _vp]),
+        "hear_multi_create": (st, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_size_t, _u32p, _dp,
+                                   ctypes.POINTER(_vp)]),
+        "hear_multi_evaluate": (st, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp]),
+        "hear_multi_destroy": (None, [_vp]),
         "hear_server_create": (st, [_vp, _vp, ctypes.POINTER(hear_server_config), ctypes.POINTER(_vp)]),
         "hear_server_submit": (st, [_vp, _u64p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_double,
                                     ctypes.POINTER(ctypes.c_uint64)]),
@@ -474,6 +478,31 @@ def hear_evaluate_host(m, evk, in_words, n_ct, scale, out=None, stream=None):
     _check(lib.hear_evaluate_host(m, evk, _p(w, _u64p), int(n_ct), float(scale), _p(out, _u64p), out.size,
                                   ctypes.byref(n), ctypes.byref(lv), ctypes.byref(sc), _stream(stream)))
     return out, lv.value, sc.value
+
+
+# ---------------------------------------------------------------- several networks, one launch
+def hear_multi_create(models, evks, n_ct, scales):
+    """one CUDA-graph launch evaluating job i = (models[i], evks[i]) on n_ct[i] ciphertexts"""
+    J = len(models)
+    m = (_vp * J)(*models)
+    k = (_vp * J)(*evks)
+    n = np.ascontiguousarray(n_ct, dtype=np.uint32)
+    s = np.ascontiguousarray(scales, dtype=np.float64)
+    h = _vp()
+    _check(lib.hear_multi_create(m, k, J, _p(n, _u32p), _p(s, _dp), ctypes.byref(h)))
+    return h.value
+
+
+def hear_multi_evaluate(mu, cts, stream=None):
+    """cts: the jobs' inputs concatenated -> their results in the same order"""
+    ins = (_vp * len(cts))(*cts)
+    outs = (_vp * len(cts))()
+    _check(lib.hear_multi_evaluate(mu, ins, outs, _stream(stream)))
+    return [o for o in outs]
+
+
+def hear_multi_destroy(mu):
+    lib.hear_multi_destroy(mu)
 
 
 # ---------------------------------------------------------------- slot-batched evaluation
