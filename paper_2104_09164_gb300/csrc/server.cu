@@ -112,13 +112,20 @@ void launch(hear_server *S, Slot &s, uint32_t slot_index) {
     s.busy = true;
 }
 
-// called with S->mu held
-void finish(hear_server *S, Slot &s) {
-    const auto now = Clock::now();
+// copies the results of a finished slot out of its pinned buffer; called without S->mu
+// (the requests stay in state 1 and the slot busy until finish() runs)
+void collect(hear_server *S, Slot &s) {
     uint64_t off = 0;
     for (auto &r : s.reqs) {
         r->out.assign(s.h_out + off, s.h_out + off + (uint64_t)r->n_ct * S->out_words);
         off += (uint64_t)r->n_ct * S->out_words;
+    }
+}
+
+// called with S->mu held, after collect()
+void finish(hear_server *S, Slot &s) {
+    const auto now = Clock::now();
+    for (auto &r : s.reqs) {
         r->t_done = now;
         r->state = 2;
         S->done_reqs++;
@@ -142,6 +149,9 @@ void worker_loop(hear_server *S) {
         try {
             for (auto &s : S->slots)
                 if (s.busy && cudaEventQuery(s.done) == cudaSuccess) {
+                    lk.unlock();
+                    collect(S, s);
+                    lk.lock();
                     finish(S, s);
                     progressed = true;
                 }
