@@ -163,11 +163,10 @@ def peaks():
 # the correction, add and subtract of 64-bit words: 10).
 ALU_PEAK_TOPS = 152 * 4 * 32 * 2.070e9 / 1e12
 OPS_PER_BUTTERFLY = 30
-# Multiply-pipe roofline of the slot-batched matrix product: a mad.wide.u32 (32 x 32 -> 64
-# bits plus a 64-bit addend) occupies the integer multiply (FMA-heavy) pipe for 4 cycles per
-# warp instruction (ncu on a throughput kernel of such multiply-adds: 0.19 warp instructions
-# per sub-partition cycle at 76 % heavy-pipe cycles), i.e. 8 lanes per cycle per sub-partition:
-# 152 SMs x 4 x 8 lanes x 2.07 GHz.
+# Multiply-pipe roofline of the slot-batched matrix product: each 32 x 32 -> 64-bit partial
+# product is one warp instruction of the integer multiply (FMA-heavy) pipe holding it 4 cycles
+# (ncu on the kernel: 2.47e9 such instructions for 2.42e9 partial products, 3.99 pipe cycles
+# each), i.e. 8 lanes per cycle per sub-partition: 152 SMs x 4 x 8 lanes x 2.07 GHz.
 MAD_WIDE_PEAK_TOPS = 152 * 4 * 8 * 2.070e9 / 1e12
 
 
@@ -602,8 +601,8 @@ def run_simd(H, torch, stream, device, plain_value, rows=SIMD_ROWS, steps=3, war
                     "roofline": {"bound": "alu", "kernel": "k_simd_fc (scalar matrix product, mad.wide.u32)",
                                  "achieved": achieved, "peak": peak, "unit": "T mad.wide.u32 lane-ops/s",
                                  "frac": achieved / peak if achieved else None, "traffic": None,
-                                 "peak_kind": "derived: 152 SMs x 32 lanes/clk x 2.07 GHz (mad.wide.u32 holds "
-                                              "the multiply pipe 4 cycles per warp instruction)",
+                                 "peak_kind": "derived: 152 SMs x 32 lanes/clk x 2.07 GHz (each partial product "
+                                              "holds the multiply pipe 4 cycles per warp instruction, ncu)",
                                  "probe_tops": probe},
                     "stages_ms_per_step": {k: v_[1] for k, v_ in sorted(prof.items(), key=lambda kv: -kv[1][1])[:6]}})
         del pin_in, pin_out
