@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-simd", action="store_true", help="skip the slot-batched (one clip per slot) rows")
     ap.add_argument("--no-fc-tune", action="store_true",
                     help="evaluate every network in the default FC form instead of the tuned one")
+    ap.add_argument("--fc-form", default=None,
+                    help="pin the headline network's FC form as 'n1,hoist' (e.g. 32,1) instead of tuning it "
+                         "(profiles pin the form the timed run chose, as HEAR_NTT_TABLE pins the NTT table)")
     ap.add_argument("--simd-rows", default="all",
                     help="slot-batched rows: all | comma-separated indices into small@top, small@level3, large@top")
     return ap.parse_args()
@@ -768,7 +771,11 @@ def main_gpu(a):
     from paper_2104_09164_gb300.workloads import make_workload
     stream = torch.cuda.Stream(device=device)
     w = make_workload(a.workload, a.clips)
-    S = Setup(H, w, stream, device, tune=not a.no_fc_tune)
+    if a.fc_form:
+        n1, dh = (int(x) for x in a.fc_form.split(","))
+        S = Setup(H, w, stream, device, fc_n1=n1, hoist_moddown=bool(dh))
+    else:
+        S = Setup(H, w, stream, device, tune=not a.no_fc_tune)
     total_ms, lat, launches, clocks = run_gpu(S, a.steps, a.warmup, dist, torch, stream, device)
     total_ms = dist.max(total_ms)
     value = dist.world * a.steps * S.clips_per_step / (total_ms / 1e3)
