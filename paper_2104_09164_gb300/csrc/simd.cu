@@ -15,7 +15,6 @@
 //    pair added into a 96-bit sum by one carry chain.
 // Both forms hold the multiply pipe the same number of cycles per partial product.
 #include <cmath>
-#include <mutex>
 #include "simd.h"
 #include "modarith.cuh"
 #include "launch.cuh"

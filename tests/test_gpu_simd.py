@@ -124,7 +124,7 @@ def test_toy_network_bit_exact_and_logits(H):
 
 def test_fc_square_fc_bit_exact(H):
     """separate FC 64->20 (ragged rows) -> x^2 -> FC 20->3 on a three-level chain with a
-    50-bit first prime (three-piece residues), 1000 clips"""
+    50-bit first prime (the 31-bit-piece form of the matrix product), 1000 clips"""
     log_n, q_bits, p_bits = 12, [50, 40, 40, 40], [50]
     rng = np.random.default_rng(77)
     X = rng.uniform(-1, 1, size=(1000, 64))
