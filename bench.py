@@ -446,7 +446,7 @@ def poisson_sweep(servers, mix, rates, seconds, seed):
     return out
 
 
-def run_served(H, S, rates, seconds=2.0, max_batch=32, n_slots=2, seed=601):
+def run_served(H, S, rates, seconds=2.0, max_batch=32, n_slots=3, seed=601):
     """Poisson request stream against the continuous-batching server: each request carries
     1-8 clips (uniform) of the small network (4 clips per ciphertext -> 1 or 2 ciphertexts);
     returns per-rate throughput and p50/p99 latency (submit -> result ready)."""
@@ -814,7 +814,7 @@ def main_gpu(a):
     if result is not None and not a.no_served and a.workload == "small" and a.clips is None and dist.world == 1:
         sweep = run_served(H, S, [float(x) for x in a.rates.split(",")])
         result["served"] = {"workload": "small network, Poisson arrivals, 1-8 clips per request, "
-                                        "continuous batching (max 32 ciphertexts, 2 batches in flight)",
+                                        "continuous batching (max 32 ciphertexts, 3 batches in flight)",
                             "note": "latency = client submit -> result read back (host), per rate",
                             "sweep": sweep}
     if result is not None and not a.no_served and a.workload == "small" and a.clips is None and dist.world == 1:
