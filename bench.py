@@ -72,16 +72,26 @@ def describe(w):
 
 # ------------------------------------------------------------------ distributed plumbing
 class Dist:
+    """Rank plumbing for torchrun: one replica per GPU, a barrier around the timed region and
+    the max over ranks of the measured times.  NCCL on GPUs; gloo when no GPU is visible
+    (or HEAR_DIST_BACKEND=gloo), which is how the host logic is tested on CPU."""
+
     def __init__(self):
         self.world = int(os.environ.get("WORLD_SIZE", "1"))
         self.rank = int(os.environ.get("RANK", "0"))
         self.local = int(os.environ.get("LOCAL_RANK", "0"))
         self.pg = None
+        self.device = "cpu"
         if self.world > 1:
             import torch
             import torch.distributed as dist
-            torch.cuda.set_device(self.local)
-            dist.init_process_group("nccl", device_id=torch.device("cuda", self.local))
+            backend = os.environ.get("HEAR_DIST_BACKEND") or ("nccl" if torch.cuda.is_available() else "gloo")
+            if backend == "nccl":
+                torch.cuda.set_device(self.local)
+                dist.init_process_group("nccl", device_id=torch.device("cuda", self.local))
+                self.device = "cuda"
+            else:
+                dist.init_process_group("gloo")
             self.pg = dist
 
     def barrier(self):
@@ -92,13 +102,19 @@ class Dist:
         if not self.pg:
             return x
         import torch
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        t = torch.tensor([x], dtype=torch.float64, device=self.device)
         self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
         return float(t.item())
 
     def close(self):
         if self.pg:
             self.pg.destroy_process_group()
+
+
+def replica_value(world, steps, clips_per_step, max_ms):
+    """whole-job throughput of `world` replicas: all ranks' clips over the slowest rank's
+    time for `steps` steps (weak scaling)"""
+    return world * steps * clips_per_step / (max_ms / 1e3)
 
 
 # ------------------------------------------------------------------ clocks
@@ -779,10 +795,10 @@ def main_gpu(a):
         S = Setup(H, w, stream, device, tune=not a.no_fc_tune)
     total_ms, lat, launches, clocks = run_gpu(S, a.steps, a.warmup, dist, torch, stream, device)
     total_ms = dist.max(total_ms)
-    value = dist.world * a.steps * S.clips_per_step / (total_ms / 1e3)
+    value = replica_value(dist.world, a.steps, S.clips_per_step, total_ms)
     stages, psteps = profile_stages(S, stream, torch)
     e2e_s, bi, bo = run_e2e(S, max(3, a.steps // 2), 1, torch, stream)
-    e2e_value = dist.world * max(3, a.steps // 2) * S.clips_per_step / dist.max(e2e_s)
+    e2e_value = replica_value(dist.world, max(3, a.steps // 2), S.clips_per_step, dist.max(e2e_s) * 1e3)
     result = None
     if dist.rank == 0:
         ntt = {k: v for k, v in stages.items() if k.startswith("ntt")}
@@ -835,7 +851,7 @@ def main_gpu(a):
         tms = dist.max(tms)
         bst, bps = profile_stages(SL, stream, torch, 1)
         if result is not None:
-            result["batched"] = {"workload": describe(wl), "value": dist.world * bsteps * SL.clips_per_step / (tms / 1e3),
+            result["batched"] = {"workload": describe(wl), "value": replica_value(dist.world, bsteps, SL.clips_per_step, tms),
                                  "unit": UNIT, "ms_per_step": tms / bsteps, "steps": bsteps,
                                  "p50_ms": blat[len(blat) // 2], "gpu_launches": bl, "clocks": bclk,
                                  "fc_form": SL.fc_form,
