@@ -485,6 +485,11 @@ hear_status hear_ntt_set_table(hear_context *ctx, const uint8_t *table);
 
 /* ---- debug: ring products through the NTT kernels (tests only) ---- */
 /* out = a * b in Z_q[X]/(X^N+1) for limb prime index `prime` (0..n_q+n_p-1), coefficient domain */
+/* the plaintext scalar of weight w at scale q (q a prime of the chain or any q < 2^62):
+ * round(w q) computed exactly, ties away from zero -- the coefficient the slot-batched FC
+ * layers multiply by.  Host only (no device needed).  HEAR_E_INVAL for a non-finite w or
+ * |w q| >= 2^62. */
+hear_status hear_dbg_round_scalar(double w, uint64_t q, int64_t *out);
 /* lane operations per second of an integer multiply-add form (kind 0: mad.wide.u32 --
  * 32 x 32 -> 64 bits plus a 64-bit addend, the step of the slot-batched matrix product;
  * kind 1: mad.lo.u32), from a throughput kernel of 8 independent chains per thread on every

@@ -1067,6 +1067,11 @@ hear_status hear_simd_evaluate_host(const hear_simd_model *m, const hear_eval_ke
     });
 }
 
+hear_status hear_dbg_round_scalar(double w, uint64_t q, int64_t *out) {
+    if (!out || q == 0 || q >= (1ull << 62)) return fail(HEAR_E_INVAL, "bad argument");
+    return guard(nullptr, [&] { *out = round_scalar(w, q); });
+}
+
 hear_status hear_dbg_imad_peak(hear_context *ctx, int kind, uint32_t iters, double *lane_ops_per_s) {
     if (!ctx || !lane_ops_per_s) return fail(HEAR_E_INVAL, "null argument");
     return guard(ctx, [&] { *lane_ops_per_s = imad_peak(ctx, kind, iters); });

@@ -187,6 +187,7 @@ def _load():
         "hear_ntt_get_table": (st, [_vp, ctypes.POINTER(ctypes.c_uint8)]),
         "hear_ntt_set_table": (st, [_vp, ctypes.POINTER(ctypes.c_uint8)]),
         "hear_dbg_imad_peak": (st, [_vp, ctypes.c_int, ctypes.c_uint32, _dp]),
+        "hear_dbg_round_scalar": (st, [ctypes.c_double, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int64)]),
         "hear_dbg_poly_mul": (st, [_vp, ctypes.c_uint32, _u64p, _u64p, _u64p]),
         "hear_dbg_ntt_roundtrip": (st, [_vp, _u64p, ctypes.c_size_t]),
         "hear_dbg_ntt_time": (st, [_vp, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
@@ -749,6 +750,13 @@ def hear_pdl_launch_count():
 
 
 # ---------------------------------------------------------------- debug
+def hear_dbg_round_scalar(w, q):
+    """round(w q) exactly, ties away from zero (host only)"""
+    v = ctypes.c_int64()
+    _check(lib.hear_dbg_round_scalar(float(w), int(q), ctypes.byref(v)))
+    return v.value
+
+
 def hear_dbg_imad_peak(ctx, kind=0, iters=4096):
     """lane operations per second of mad.wide.u32 (kind 0) or mad.lo.u32 (kind 1)"""
     v = ctypes.c_double()

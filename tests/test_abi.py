@@ -44,3 +44,32 @@ def test_errors_without_gpu_do_not_abort(libpath):
     assert lib.hear_context_create(None, 0, ctypes.byref(out)) == -1
     assert b"null" in lib.hear_last_error()
     assert lib.hear_ciphertext_info(None, None, None, None) == -1
+
+
+def test_scalar_rounding_is_exact(libpath):
+    """hear_dbg_round_scalar (host only) equals round(w q) in exact rational arithmetic, ties
+    away from zero -- the rule of the oracle's scalar_residues -- on random, tied, tiny and
+    boundary weights, and refuses non-finite or out-of-range ones."""
+    from fractions import Fraction
+    import numpy as np
+    from paper_2104_09164_gb300 import hear
+
+    def exact(w, q):
+        f = Fraction(w) * q
+        mag = (2 * abs(f.numerator) + f.denominator) // (2 * f.denominator)
+        return -mag if f.numerator < 0 else mag
+
+    rng = np.random.default_rng(9)
+    qs = [(1 << 40) - 87, (1 << 60) - 93, 1099511480321, 3]
+    ws = list(rng.normal(0, 0.3, 200)) + list(rng.normal(0, 1e3, 50)) + [0.0, -0.0, 0.5, -0.5, 1.5, -2.5,
+                                                                          2.0 ** -60, -(2.0 ** -70), 5e-324]
+    for q in qs:
+        for w in ws:
+            if abs(Fraction(w) * q) >= 2 ** 62:
+                continue
+            assert hear.hear_dbg_round_scalar(w, q) == exact(w, q), (w, q)
+    # half-integers round away from zero
+    assert hear.hear_dbg_round_scalar(0.5, 3) == 2 and hear.hear_dbg_round_scalar(-0.5, 3) == -2
+    for bad in (float("nan"), float("inf"), 2.0 ** 30):
+        with pytest.raises(hear.HearError):
+            hear.hear_dbg_round_scalar(bad, (1 << 40) - 87)
