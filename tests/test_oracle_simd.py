@@ -98,3 +98,19 @@ def test_simd_slots_are_independent(toy):
     keep = np.arange(20) != 4
     assert np.max(np.abs(a[keep] - b[keep])) < 2.0 ** -25
     assert np.max(np.abs(b[4] - X2[4] @ W.T)) < 2.0 ** -20
+
+
+def test_fc_square_fc_simd_matches_fp64():
+    """separate FC -> x^2 -> FC layers (three levels: q = 50 + 3x40 bits), 50 clips, ragged
+    dimensions; every clip's logits within 2^-15 of FP64, the unused slots stay empty"""
+    o = O.Oracle(12, [50, 40, 40, 40], [50], 3.2, threads=THREADS)
+    keys = o.keygen(12, [])
+    rng = np.random.default_rng(13)
+    X = rng.uniform(-1, 1, size=(50, 16))
+    W1, W2 = rng.normal(0, 0.2, size=(6, 16)), rng.normal(0, 0.4, size=(3, 6))
+    layers = [("fc", W1), ("square",), ("fc", W2)]
+    out = o.evaluate_simd(layers, o.encrypt_simd(keys.pk, X, 25, 2.0 ** 40), keys)
+    assert len(out) == 3 and out[0].level == 0
+    ref = ((X @ W1.T) ** 2) @ W2.T
+    assert np.max(np.abs(o.decrypt_simd(keys, out, 50) - ref)) <= 2.0 ** -15
+    assert np.max(np.abs(o.decrypt(keys, out[0])[50:])) <= 2.0 ** -15
