@@ -88,6 +88,16 @@ const char *hear_last_error(void);
 hear_status hear_context_create(const hear_params_desc *params, int cuda_device, hear_context **out);
 void hear_context_destroy(hear_context *ctx);
 /* primes in chain order q_0..q_{n_q-1}, p_0..p_{K-1} */
+/* Route the context's device allocations through the caller's allocator: while an ABI call
+ * of this context runs, every device allocation it makes on the calling thread calls
+ * alloc(bytes, stream, user) (stream = the CUDA stream the memory is for, null = synchronous
+ * use) and is released later by free(ptr, stream, user).  Memory a CUDA graph owns (allocated
+ * inside a stream capture) and the server worker thread's memory stay with the stream-ordered
+ * pool.  alloc returns null on failure: the call fails with HEAR_E_NOMEM and the context stays
+ * usable.  Both functions null = back to the pool; they must stay valid until the context and
+ * everything made with it are destroyed. */
+hear_status hear_set_allocator(hear_context *ctx, void *(*alloc)(size_t bytes, void *stream, void *user),
+                               void (*free)(void *ptr, void *stream, void *user), void *user);
 hear_status hear_context_primes(const hear_context *ctx, uint64_t *out, size_t cap, size_t *n);
 /* discrete-Gaussian CDT thresholds used by the samplers (for cross-checking) */
 hear_status hear_context_cdt(const hear_context *ctx, uint64_t *out, size_t cap, size_t *n);

@@ -23,6 +23,7 @@ hear_status guard(hear_context *ctx, F &&f) {
     if (ctx && ctx->poisoned) return fail(HEAR_E_CUDA, "context is poisoned by an earlier CUDA error");
     try {
         if (ctx) HEAR_CHECK_CUDA(cudaSetDevice(ctx->device));
+        AllocScope alloc_scope(ctx ? &ctx->allocator : nullptr);
         f();
         return HEAR_OK;
     } catch (const Error &e) {
@@ -131,6 +132,16 @@ void hear_context_destroy(hear_context *ctx) {
     ctx->d_cdt.reset();
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
+}
+
+hear_status hear_set_allocator(hear_context *ctx, void *(*alloc)(size_t, void *, void *),
+                               void (*free_fn)(void *, void *, void *), void *user) {
+    if (!ctx) return fail(HEAR_E_INVAL, "null context");
+    if (!alloc != !free_fn) return fail(HEAR_E_INVAL, "give both allocator functions or neither");
+    ctx->allocator.alloc = alloc;
+    ctx->allocator.free = free_fn;
+    ctx->allocator.user = user;
+    return HEAR_OK;
 }
 
 hear_status hear_context_primes(const hear_context *ctx, uint64_t *out, size_t cap, size_t *n) {

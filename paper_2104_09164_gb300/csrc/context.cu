@@ -16,8 +16,26 @@
 namespace hear {
 
 // ------------------------------------------------------------------ device memory
+thread_local const Allocator *tl_allocator = nullptr;
+
 DevBuf::DevBuf(size_t b, cudaStream_t st) : bytes(b), s(st) {
     if (b == 0) return;
+    if (const Allocator *a = tl_allocator) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (st && cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+            (void)cudaGetLastError();
+            cs = cudaStreamCaptureStatusNone;
+        }
+        if (cs == cudaStreamCaptureStatusNone) {
+            p = a->alloc(b, static_cast<void *>(st), a->user);
+            if (!p)
+                throw Error(HEAR_E_NOMEM, std::string("the allocator returned no memory for ") + std::to_string(b) +
+                                              " bytes");
+            free_fn = a->free;
+            free_user = a->user;
+            return;
+        }
+    }
     cudaError_t e = st ? cudaMallocAsync(&p, b, st) : cudaMalloc(&p, b);
     if (e != cudaSuccess) {
         p = nullptr;
@@ -28,18 +46,21 @@ DevBuf::DevBuf(size_t b, cudaStream_t st) : bytes(b), s(st) {
 }
 void DevBuf::reset() {
     if (p) {
-        if (s) cudaFreeAsync(p, s);
+        if (free_fn) free_fn(p, static_cast<void *>(s), free_user);
+        else if (s) cudaFreeAsync(p, s);
         else cudaFree(p);
     }
     p = nullptr;
     bytes = 0;
+    free_fn = nullptr;
+    free_user = nullptr;
 }
 DevBuf::~DevBuf() { reset(); }
 DevBuf &DevBuf::operator=(DevBuf &&o) noexcept {
     if (this != &o) {
         reset();
-        p = o.p; bytes = o.bytes; s = o.s;
-        o.p = nullptr; o.bytes = 0;
+        p = o.p; bytes = o.bytes; s = o.s; free_fn = o.free_fn; free_user = o.free_user;
+        o.p = nullptr; o.bytes = 0; o.free_fn = nullptr; o.free_user = nullptr;
     }
     return *this;
 }

@@ -44,11 +44,29 @@ struct DevPrime {
     uint64_t one_sh;     // Shoup companion of 1 = floor(2^64 / q)
 };
 
-// Device memory owned through the stream-ordered allocator.
+// A caller-supplied device allocator (hear_set_allocator): alloc(bytes, stream, user) and
+// free(ptr, stream, user).  While an ABI call of a context that has one runs, the calling
+// thread's allocations go through it (see AllocScope), except inside a stream capture,
+// whose memory the graph owns.
+struct Allocator {
+    void *(*alloc)(size_t, void *, void *) = nullptr;
+    void (*free)(void *, void *, void *) = nullptr;
+    void *user = nullptr;
+};
+extern thread_local const Allocator *tl_allocator;
+struct AllocScope {
+    const Allocator *prev;
+    explicit AllocScope(const Allocator *a) : prev(tl_allocator) { tl_allocator = (a && a->alloc) ? a : nullptr; }
+    ~AllocScope() { tl_allocator = prev; }
+};
+
+// Device memory owned through the stream-ordered allocator (or the caller's allocator).
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
     cudaStream_t s = nullptr;
+    void (*free_fn)(void *, void *, void *) = nullptr;   // set: p came from a caller's allocator
+    void *free_user = nullptr;
     DevBuf() = default;
     DevBuf(size_t b, cudaStream_t st);
     ~DevBuf();
@@ -116,6 +134,7 @@ inline uint32_t ntt_bucket(uint32_t n_limbs) {
 
 struct hear_context {
     int device = 0;
+    hear::Allocator allocator;                // hear_set_allocator (none = the stream-ordered pool)
     int ntt_force = -1;                       // debug: force one NTT variant (-1 = table)
     uint8_t ntt_choice[2][kNttBuckets];       // [forward, inverse][limb bucket] -> variant
     uint32_t log_n = 0, n = 0, n_q = 0, n_p = 0, L = 0, K = 0, alpha = 0;

@@ -82,10 +82,19 @@ class hear_cnn_op_info(ctypes.Structure):
                 ("n_babies", ctypes.c_uint32), ("n_giants", ctypes.c_uint32), ("n_keyswitch", ctypes.c_uint32)]
 
 
+HEAR_OK, HEAR_E_INVAL, HEAR_E_NOMEM, HEAR_E_CUDA, HEAR_E_LEVEL = 0, -1, -2, -3, -4
+HEAR_E_SCALE, HEAR_E_NOKEY, HEAR_E_STATE, HEAR_E_FORMAT, HEAR_E_UNSUPPORTED = -5, -6, -7, -8, -9
+
+
 class HearError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("hear error %d: %s" % (code, msg))
         self.code = code
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+_allocators = {}   # context -> the ctypes callbacks (kept alive while the context uses them)
 
 
 def _load():
@@ -98,6 +107,7 @@ def _load():
         "hear_last_error": (ctypes.c_char_p, []),
         "hear_context_create": (st, [ctypes.POINTER(hear_params_desc), ctypes.c_int, ctypes.POINTER(_vp)]),
         "hear_context_destroy": (None, [_vp]),
+        "hear_set_allocator": (st, [_vp, _ALLOC_FN, _FREE_FN, _vp]),
         "hear_context_primes": (st, [_vp, _u64p, ctypes.c_size_t, _szp]),
         "hear_context_cdt": (st, [_vp, _u64p, ctypes.c_size_t, _szp]),
         "hear_keygen": (st, [_vp, ctypes.c_uint64, _i32p, ctypes.c_size_t, ctypes.POINTER(_vp),
@@ -244,6 +254,18 @@ def _vec_out(fn, handle, dtype, ptr_t, *pre):
     out = np.empty(n.value, dtype=dtype)
     _check(fn(handle, *pre, _p(out, ptr_t), n.value, ctypes.byref(n)))
     return out
+
+
+def hear_set_allocator(ctx, alloc, free):
+    """alloc(bytes, stream) -> device pointer (int, 0 on failure), free(ptr, stream); both
+    None = back to the stream-ordered pool.  Streams are passed as integers (0 = none)."""
+    a = _ALLOC_FN(lambda n, st, u: alloc(int(n), int(st or 0)) or None) if alloc is not None else _ALLOC_FN()
+    f = _FREE_FN(lambda p, st, u: free(int(p), int(st or 0))) if free is not None else _FREE_FN()
+    _check(lib.hear_set_allocator(ctx, a, f, None))
+    if alloc is None:
+        _allocators.pop(ctx, None)
+    else:
+        _allocators[ctx] = (a, f)
 
 
 def hear_context_primes(ctx):

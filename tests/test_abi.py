@@ -73,3 +73,10 @@ def test_scalar_rounding_is_exact(libpath):
     for bad in (float("nan"), float("inf"), 2.0 ** 30):
         with pytest.raises(hear.HearError):
             hear.hear_dbg_round_scalar(bad, (1 << 40) - 87)
+
+
+def test_status_codes_match_the_header(libpath):
+    from paper_2104_09164_gb300 import hear
+    src = open(os.path.join(ROOT, "include", "hear.h")).read()
+    for name, val in re.findall(r"#define (HEAR_(?:OK|E_[A-Z]+))\s+\(?(-?\d+)\)?", src):
+        assert getattr(hear, name) == int(val), name
