@@ -64,3 +64,16 @@ def test_single_rank_needs_no_process_group(monkeypatch):
     d = bench.Dist()
     assert d.pg is None and d.max(3.5) == 3.5
     assert bench.replica_value(1, 20, 1, 1000.0) == pytest.approx(20.0)
+
+
+def test_bench_command_lines_parse(monkeypatch):
+    """the driver's command lines and the options the profiles pin"""
+    sys.path.insert(0, ROOT)
+    import bench
+    for argv in (["bench.py"], ["bench.py", "--gpus", "8", "--steps", "20", "--warmup", "3"],
+                 ["bench.py", "--impl", "reference", "--steps", "2", "--warmup", "1"],
+                 ["bench.py", "--fc-form", "32,1", "--simd-rows", "0,2", "--no-served"]):
+        monkeypatch.setattr(sys, "argv", argv)
+        a = bench.parse()
+        assert a.gpus >= 1 and a.steps >= 1 and a.warmup >= 0
+    assert a.fc_form == "32,1" and [bench.SIMD_ROWS[int(i)] for i in a.simd_rows.split(",")][1][0] == "large"
