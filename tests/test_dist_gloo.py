@@ -77,3 +77,17 @@ def test_bench_command_lines_parse(monkeypatch):
         a = bench.parse()
         assert a.gpus >= 1 and a.steps >= 1 and a.warmup >= 0
     assert a.fc_form == "32,1" and [bench.SIMD_ROWS[int(i)] for i in a.simd_rows.split(",")][1][0] == "large"
+
+
+def test_slot_batched_roofline_count():
+    """the algorithmic multiply-pipe work of the slot-batched network: three partial products
+    per (row, input, residue) of each FC, at the level the layer runs"""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2104_09164_gb300.workloads import make_workload
+    w = make_workload("small")
+    n = 1 << w.log_n
+    primes = [1 << 40] * 8                       # only the count of limbs matters
+    got = bench.simd_mad_lanes(primes, w.layers, 7, n)
+    want = 128 * 2048 * 2 * n * 3 * 8 + 2 * 128 * 2 * n * 3 * 6    # FC1 at level 7, FC2 at level 5
+    assert got == want
