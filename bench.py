@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--fc-form", default=None,
                     help="pin the headline network's FC form as 'n1,hoist' (e.g. 32,1) instead of tuning it "
                          "(profiles pin the form the timed run chose, as HEAR_NTT_TABLE pins the NTT table)")
+    ap.add_argument("--sections-out", default="bench_out/sections.json",
+                    help="file for the full result (every section); the last stdout line is the short headline")
     ap.add_argument("--simd-rows", default="all",
                     help="slot-batched rows: all | comma-separated indices into small@top, small@level3, large@top")
     return ap.parse_args()
@@ -733,11 +735,10 @@ def run_conv_table(H, torch, stream, device, rows, iters=5):
 
 def run_cnn(H, torch, stream, device, batches=(1, 16), iters=5):
     """the paper-shaped 1D-CNN-64 (2 x 32 x 15 inputs, N = 2^15): whole encrypted network"""
-    from paper_2104_09164_gb300.collapse import collapse_cnn
-    from paper_2104_09164_gb300.workloads import make_cnn
+    from paper_2104_09164_gb300.workloads import cnn_spec, make_cnn
     from paper_2104_09164_gb300.autotune import tune_cnn
     net = make_cnn("cnn1d64", n_samples=max(batches))
-    spec = collapse_cnn(net)
+    spec = cnn_spec(net)     # as trained: the library collapses it
     ctx = H.hear_context_create(net.log_n, net.q_bits, net.p_bits, net.log2_scale, net.sigma, device)
     t0 = time.perf_counter()
     strategies, tune_report = tune_cnn(H, ctx, spec, net.slots, len(net.q_bits) - 1, iters=3, stream=stream)
@@ -922,8 +923,95 @@ def main_gpu(a):
         v, cores, desc = oracle_sample(w, H_steps_for(w))
         result["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
     if result is not None:
-        print(json.dumps(result), flush=True)
+        path = write_sections(result, a.sections_out)
+        print(json.dumps(headline(result, path), separators=(",", ":")), flush=True)
     dist.close()
+
+
+def _r(x, nd=4):
+    """x rounded to nd significant digits (None stays None)"""
+    if x is None:
+        return None
+    return float("%.*g" % (nd, x))
+
+
+def write_sections(result, path):
+    """the full result (served sweeps, per-stage tables, CNN rows, ...) as one JSON file;
+    returns its path relative to the repository (None if it could not be written)"""
+    if not path:
+        return None
+    full = path if os.path.isabs(path) else os.path.join(ROOT, path)
+    try:
+        os.makedirs(os.path.dirname(full), exist_ok=True)
+        with open(full, "w") as f:
+            json.dump(result, f, indent=1)
+    except OSError:
+        return None
+    return os.path.relpath(full, ROOT)
+
+
+def headline(result, sections_path):
+    """the one short JSON line bench.py prints last: the metric on the quoted workload,
+    its end-to-end form, the dominant kernel's roofline, the CPU baseline, the clocks and
+    one number per section (the whole sections are in the file `sections_path`)"""
+    keep = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+            "scaling", "vs_baseline", "dtype", "data", "p50_ms", "p99_ms", "gpu_launches")
+    h = {k: result[k] for k in keep if k in result}
+    for k in ("value", "ms_per_step", "p50_ms", "p99_ms"):
+        h[k] = _r(h.get(k), 6)
+    cfg = result["config"]
+    h["config"] = {"workload": cfg["workload"], "parallelism": cfg["parallelism"],
+                   "l2": "no flush: per-step working set > 129 MB L2",
+                   "ntt_table": cfg.get("ntt_table"),
+                   "fc_form": {k: cfg["fc_form"].get(k) for k in ("fc_n1", "hoist_moddown")},
+                   "sections": sections_path}
+    e = result["e2e"]
+    h["e2e"] = {"value": _r(e["value"], 6), "unit": e["unit"], "h2d_bytes_per_step": e["h2d_bytes_per_step"],
+                "d2h_bytes_per_step": e["d2h_bytes_per_step"]}
+    rf = result["roofline"]
+    h["roofline"] = {k: (_r(rf.get(k)) if isinstance(rf.get(k), float) else rf.get(k))
+                     for k in ("bound", "kernel", "achieved", "peak", "unit", "frac", "traffic", "peak_kind",
+                               "algorithmic_bytes_per_call", "avg_call_us", "hbm_achieved_gbs", "hbm_peak_gbs",
+                               "hbm_frac") if k in rf}
+    if "cpu_baseline" in result:
+        cb = result["cpu_baseline"]
+        h["cpu_baseline"] = {"value": _r(cb["value"]), "unit": cb["unit"], "cores": cb["cores"], "kind": cb["kind"],
+                             "sample": cb["sample"]}
+    ck = result["clocks"]
+    h["clocks"] = {"sm_mhz": ck.get("sm_mhz"), "sm_max_mhz": ck.get("sm_max_mhz"), "reasons": ck.get("reasons")}
+    s = {}
+    if "batched" in result:
+        b = result["batched"]
+        s["batched_large_256clips"] = {"value": _r(b["value"]), "vs_plain": _r(b["vs_plain"], 3)}
+    if "batched_small" in result:
+        best = max(result["batched_small"]["rows"], key=lambda r: r["value"])
+        s["batched_small"] = {"clips": best["clips"], "value": _r(best["value"]), "vs_plain": _r(best["vs_plain"], 3)}
+    for key in ("served", "served_c5"):
+        if key in result:
+            rows = result[key]["sweep"]
+            top = max(rows, key=lambda r: r["inferences_s"])
+            s[key] = {"rate_req_s": top["rate_req_s"], "value": _r(top["inferences_s"]),
+                      "vs_plain": _r(top["inferences_s"] / result["value"], 3),
+                      "p50_ms": _r(top.get("p50_ms")), "p99_ms": _r(top.get("p99_ms"))}
+    if "served_mix" in result:
+        rows = result["served_mix"]["sweep"]
+        top = max(rows, key=lambda r: r["inferences_s"])
+        s["served_mix"] = {"rate_req_s": top["rate_req_s"], "value": _r(top["inferences_s"]),
+                           "p99_ms": {n["net"]: _r(n["p99_ms"]) for n in top["per_net"]}}
+    if "ragged_mix" in result:
+        s["ragged_mix"] = {"value": _r(result["ragged_mix"]["value"])}
+    if "min_start_level" in result:
+        s["min_start_level"] = {k: _r(v["value"]) for k, v in result["min_start_level"].items()}
+    if "batched_simd" in result:
+        rows = result["batched_simd"]["rows"]
+        s["batched_simd"] = [{"value": _r(r["value"]), "vs_plain": _r(r["vs_plain"], 3),
+                              "frac": _r(r["roofline"]["frac"], 3)} for r in rows]
+    if "cnn" in result:
+        s["cnn1d64_ms"] = [_r(b["ms"]) for b in result["cnn"]["batches"]]
+    if "conv_table1" in result:
+        s["conv_table1_speedup"] = [_r(r["speedup"], 3) for r in result["conv_table1"]["rows"]]
+    h["summary"] = s
+    return h
 
 
 def _key_mb(w, n_rot):

@@ -69,7 +69,9 @@ typedef struct hear_simd_batch hear_simd_batch;
  * L = n_q - 1); the n_p special primes p_0..p_{K-1} are used by key switching only.
  * Prime rule: for each bit size in the order q_0, q_1.., p_0.. take the largest prime
  * below 2^bits that is 1 mod 2N and not yet taken.  Hybrid key switching uses digits of
- * alpha = n_p consecutive limbs.  Supported: log_n in [10, 16], bit sizes in
+ * alpha consecutive limbs from q_0; alpha must equal n_p (0 selects that value; any other
+ * value returns HEAR_E_UNSUPPORTED, because a digit modulus above P multiplies the
+ * key-switching error by Q_j / P).  Supported: log_n in [11, 16], bit sizes in
  * [log_n + 2, 60], n_q + n_p <= 48.  sigma: standard deviation of the discrete Gaussian
  * errors (tail cut at floor(6 sigma)). */
 typedef struct hear_params_desc {
@@ -80,6 +82,7 @@ typedef struct hear_params_desc {
     const uint32_t *p_bits;
     double log2_scale;  /* encoding scale of fresh inputs, e.g. 40 */
     double sigma;       /* e.g. 3.2 */
+    uint32_t alpha;     /* limbs per key-switching digit: n_p, or 0 for n_p */
 } hear_params_desc;
 
 const char *hear_last_error(void);
@@ -94,8 +97,13 @@ void hear_context_destroy(hear_context *ctx);
  * use) and is released later by free(ptr, stream, user).  Memory a CUDA graph owns (allocated
  * inside a stream capture) and the server worker thread's memory stay with the stream-ordered
  * pool.  alloc returns null on failure: the call fails with HEAR_E_NOMEM and the context stays
- * usable.  Both functions null = back to the pool; they must stay valid until the context and
- * everything made with it are destroyed. */
+ * usable.  free is stream-ordered: work already queued on `stream` may still use the block
+ * when free(ptr, stream, user) is called, so the block may be handed out again only to work
+ * ordered after that stream's pending work (as PyTorch's caching allocator does); for a null
+ * stream the block must not be reused before the device is synchronised.  Both functions
+ * null = back to the pool; every pair installed must stay valid until the context and
+ * everything made with it are destroyed (memory allocated through a pair is released
+ * through it). */
 hear_status hear_set_allocator(hear_context *ctx, void *(*alloc)(size_t bytes, void *stream, void *user),
                                void (*free)(void *ptr, void *stream, void *user), void *user);
 hear_status hear_context_primes(const hear_context *ctx, uint64_t *out, size_t cap, size_t *n);
@@ -293,9 +301,19 @@ void hear_server_destroy(hear_server *s);
  * multiple of cbar); with c < cbar (cbar a multiple of c) one ciphertext holds copies,
  * block m = channel m mod c.
  *
- * Layers (the network must already be collapsed: bias, batch normalisation and the
- * activation of a block folded into one per-channel quadratic; the 1/2, 1/4 or 1/(h*w)
- * of average pooling folded into the next linear layer's weights):
+ * Layers.  A network may be given as trained (BN_QUAD, AVGPOOL, GAVGPOOL) and the library
+ * collapses it (Methods, "Non-convolutional layers"): a block's convolution bias, batch
+ * normalisation and quadratic activation become one per-channel quadratic, and the 1/2,
+ * 1/4 or 1/(h*w) of average pooling move into the next linear layer's weights, computed in
+ * IEEE double in the order A = (a*s)*s, B = ((2*a)*s)*t + b*s, C = ((a*t)*t + b*t) + c with
+ * s = gamma / sqrt(var + eps), t = s*(bias - mean) + beta, conv weights w*f and FC weights
+ * (w*f)/(h*w) (f = the pending pooling factor).  Or it may be given already collapsed
+ * (QUAD, POOL, GAP):
+ *   BN_QUAD  per channel of the preceding CONV: conv_bias (float64[c] or NULL = 0),
+ *         bn_gamma, bn_beta, bn_mean, bn_var (float64[c]), bn_eps, then the activation
+ *         act[0] z^2 + act[1] z + act[2]; becomes QUAD with (A, B, C) above.
+ *   AVGPOOL  POOL whose 1/2 (1D) or 1/4 (2D) multiplies the next CONV's weights.
+ *   GAVGPOOL GAP whose 1/(h*w) (map size at that point) divides the FC's weights.
  *   CONV  same-padded, stride-1 convolution, w = float64[c_out][c_in][f_h][f_w] (1D: f_h =
  *         1), c_out a multiple of cbar.  Rotation r + dist*l for tap (du, dv), r =
  *         stride*(du*pitch + dv), block shift l; the plaintexts carry the zero padding.
@@ -325,6 +343,9 @@ void hear_server_destroy(hear_server *s);
 #define HEAR_CNN_POOL 3
 #define HEAR_CNN_GAP 4
 #define HEAR_CNN_FC 5
+#define HEAR_CNN_BN_QUAD 6
+#define HEAR_CNN_AVGPOOL 7
+#define HEAR_CNN_GAVGPOOL 8
 #define HEAR_STRATEGY_HYBRID 0
 #define HEAR_STRATEGY_FULL 1
 #define HEAR_STRATEGY_BABY 2
@@ -346,6 +367,10 @@ typedef struct hear_cnn_layer {
     const double *a, *b, *c;    /* QUAD                                                 */
     uint32_t fast;              /* CONV                                                 */
     uint32_t strategy, n1;      /* CONV, FC (n1: HYBRID; 0 = min(4, block shifts))      */
+    const double *conv_bias;    /* BN_QUAD (or NULL)                                    */
+    const double *bn_gamma, *bn_beta, *bn_mean, *bn_var;   /* BN_QUAD                  */
+    double bn_eps;              /* BN_QUAD                                              */
+    double act[3];              /* BN_QUAD: act[0] z^2 + act[1] z + act[2]              */
 } hear_cnn_layer;
 /* The layers become a plan of slot-level operations; every ciphertext of a sample passes
  * through each operation.  Operation kinds: */
@@ -365,6 +390,12 @@ typedef struct hear_cnn_op_info {
 hear_status hear_cnn_create(hear_context *ctx, const hear_cnn_input *input, const hear_cnn_layer *layers,
                             size_t n_layers, hear_cnn **out);
 void hear_cnn_destroy(hear_cnn *m);
+/* Host only (no context, no GPU): the doubles the collapse of the layer list produces, in
+ * layer order -- each CONV's weights [c_out][c_in][f_h][f_w], each QUAD's A[c], B[c], C[c]
+ * (BN_QUAD layers after collapsing), the FC's weights [c_out][c] -- for auditing the
+ * collapse against the trained network. */
+hear_status hear_cnn_collapse(const hear_cnn_input *input, const hear_cnn_layer *layers, size_t n_layers,
+                              double *out, size_t cap, size_t *n);
 /* rotation steps (slots, in [1, N/2)) the plan needs keys for */
 hear_status hear_cnn_rotations(const hear_cnn *m, int32_t *steps, size_t cap, size_t *n);
 hear_status hear_cnn_ops(const hear_cnn *m, hear_cnn_op_info *ops, size_t cap, size_t *n);
@@ -426,19 +457,23 @@ hear_status hear_simd_decrypt(hear_context *ctx, const hear_secret_key *sk, cons
  * framework's caching allocator, a real-time loop that must not take the allocator's
  * locks or latency, a host that owns only pageable host memory and a stream.  It divides
  * a ciphertext by its last prime exactly like hear_rescale, from and to HOST arrays in the
- * coefficient domain: in = uint64[n_poly][level+1][N], out = uint64[n_poly][level][N]
- * (1 <= level <= L, 1 <= n_poly <= 3).  It allocates nothing: its device working memory is
- * a fixed 16 MiB array (2^21 words) inside the library, which every GPU that loads the
+ * coefficient domain: in = uint64[n_poly][level+1][N] (in_words words, every residue of
+ * limb i below q_i), out = uint64[n_poly][level][N] (capacity out_cap words), with
+ * 1 <= level <= L and 1 <= n_poly <= 3.  It allocates nothing: its device working memory
+ * is a fixed 16 MiB array (2^21 words) inside the library, which every GPU that loads the
  * library holds until the process exits; it calls no cudaMalloc, cudaFree or allocating
- * library routine.  Sizes with n_poly * (2*level + 1) * N > 2^21 words are rejected with
- * HEAR_E_UNSUPPORTED; a running profiler (hear_profile_begin) is rejected with
- * HEAR_E_STATE.  The first call on each device looks up the array's device address, so
- * make that first call before any stream capture.  Every call shares the array, which keeps
- * the last call's contents (each call overwrites everything it reads).  Calls that overlapped
- * on the GPU would race on the array, so the library takes a process-wide lock for the call
- * and synchronises `stream` before returning. */
-hear_status hear_rescale_noalloc(const hear_context *ctx, const uint64_t *in, uint32_t level, uint32_t n_poly,
-                                 uint64_t *out, void *stream);
+ * library routine.  Errors: in_words != n_poly*(level+1)*N or an unreduced residue ->
+ * HEAR_E_FORMAT; out_cap too small -> HEAR_E_INVAL; n_poly*(2*level+1)*N > 2^21 words ->
+ * HEAR_E_UNSUPPORTED; a running profiler (hear_profile_begin) or a `stream` that is being
+ * captured into a CUDA graph -> HEAR_E_STATE (the call synchronises `stream`); a CUDA
+ * error -> HEAR_E_CUDA and the context is poisoned.  The first call on each device looks
+ * up the array's device address.  Every call shares the array, which keeps the last call's
+ * contents (each call overwrites everything it reads).  Calls that overlapped on the GPU
+ * would race on the array, so the library takes a process-wide lock for the call and
+ * synchronises `stream` before returning.  The caller's current CUDA device is restored
+ * before the call returns. */
+hear_status hear_rescale_noalloc(hear_context *ctx, const uint64_t *in, size_t in_words, uint32_t level,
+                                 uint32_t n_poly, uint64_t *out, size_t out_cap, void *stream);
 
 /* ---- tracing: CUDA-event stage profiler and launch counter ---- */
 /* One entry per stage (kernel name): how many kernel launches it made, their summed

@@ -13,7 +13,9 @@ by pooling keeps position (y, x) at offset stride*(y*P + x) of its block.  The i
 ciphertext holds copies of the c_in input planes: block m carries plane m mod c_in.  With
 c >= cbar channels, ciphertext i block m carries channel cbar*i + m.
 
-A collapsed network (a dict as made by the package's ``collapse_cnn``) becomes a *plan*,
+A network as trained (convolutions, bias + batch normalisation + quadratic activation,
+average pooling, global average pooling, FC) is first collapsed by ``collapse`` (Methods,
+"Non-convolutional layers"); the collapsed network becomes a *plan*,
 a list of slot-level operations on the ciphertexts of one sample:
 
   ("diag", n_out, terms)   terms {(i, j, b, g): z}: output j receives z (.) rho^(b+g)(x_i).
@@ -45,6 +47,68 @@ from concurrent.futures import ThreadPoolExecutor
 import numpy as np
 
 from .oracle import Ct
+
+
+# ------------------------------------------------------------------ layer collapsing
+def collapse(spec):
+    """Layer collapsing (Methods, "Non-convolutional layers"): everything between two linear
+    layers that acts per feature map is folded into one polynomial per map, and the scale
+    of the average pooling is folded into the next linear layer.
+
+    * bias + BN + activation: batch normalisation of y + bias is the affine map
+      z = s*y + t with s = gamma / sqrt(var + eps) and t = s*(bias - mean) + beta; the
+      activation p(z) = a z^2 + b z + c then equals A y^2 + B y + C with
+      A = a s^2, B = 2 a s t + b s, C = a t^2 + b t + c (expand p(s y + t)).
+    * average pooling = (1/m) x the plain window sum of m = 2 (1D) or 4 (2D) slots; the
+      plain sum is what the ciphertexts compute (rotate-and-sum), and 1/m multiplies the
+      next convolution's weights.  Global average pooling = 1/(h w) x the sum over the map,
+      and 1/(h w) divides the FC weights (h, w = the map after the last pooling).
+
+    IEEE double, operations in the order written above from left to right (A = (a s) s,
+    B = ((2 a) s) t + b s, C = ((a t) t + b t) + c; conv weights w f, FC weights (w f)/(h w)
+    with f the pooling factor still pending), which is the library's order too: the
+    encoded plaintexts depend on every bit of these doubles.  Layers already in collapsed
+    form ("quad", "pool", "gap") are kept as they are."""
+    dims = spec["conv_dims"]
+    h, w = spec["h"], spec["w"]
+    out = dict(spec)
+    out["layers"] = []
+    factor = 1.0          # pending 1/m of average poolings
+    divisor = 1.0         # pending h*w of a global average pooling
+    for layer in spec["layers"]:
+        kind = layer[0]
+        if kind == "conv":
+            W = np.asarray(layer[1], dtype=np.float64)
+            out["layers"].append(("conv", W * factor if factor != 1.0 else W, layer[2]))
+            factor = 1.0
+        elif kind == "bn_quad":
+            bias, gamma, beta, mean, var, eps, act = layer[1:8]
+            gamma = np.asarray(gamma, dtype=np.float64)
+            bias = np.zeros_like(gamma) if bias is None else np.asarray(bias, dtype=np.float64)
+            s = gamma / np.sqrt(np.asarray(var, dtype=np.float64) + eps)
+            t = s * (bias - np.asarray(mean, dtype=np.float64)) + np.asarray(beta, dtype=np.float64)
+            a, b, c = (float(v) for v in act)
+            out["layers"].append(("quad", a * s * s, 2.0 * a * s * t + b * s, a * t * t + b * t + c))
+        elif kind in ("avgpool", "pool"):
+            if kind == "avgpool":
+                factor *= 0.5 if dims == 1 else 0.25
+            w //= 2
+            if dims == 2:
+                h //= 2
+            out["layers"].append(("pool",))
+        elif kind in ("gavgpool", "gap"):
+            if kind == "gavgpool":
+                divisor = float(h * w)
+            out["layers"].append(("gap",))
+        elif kind == "fc":
+            W = np.asarray(layer[1], dtype=np.float64)
+            if factor != 1.0 or divisor != 1.0:
+                W = (W * factor) / divisor
+            out["layers"].append(("fc", W) + tuple(layer[2:]))
+            factor = divisor = 1.0
+        else:
+            out["layers"].append(layer)
+    return out
 
 
 # ------------------------------------------------------------------ layout

@@ -19,8 +19,9 @@ import numpy as np
 
 def conv_layer_specs(spec):
     """[(index among the conv / FC layers, level drop before it, single-layer spec)] for every
-    convolution of a collapsed network: the map geometry, channel count and puncture at the
-    layer's input; the level drop counts the levels the network consumes before the layer."""
+    convolution of a network (as trained or collapsed): the map geometry, channel count and
+    puncture at the layer's input; the level drop counts the levels the network consumes
+    before the layer (timing only: the weights' pooling factors do not matter here)."""
     dims = spec["conv_dims"]
     c, h, w = spec["c_in"], spec["h"], spec["w"]
     pitch = spec.get("pitch") or w
@@ -38,9 +39,9 @@ def conv_layer_specs(spec):
             si += 1
             used += 2 if layer[2] else 1
             c = layer[1].shape[0]
-        elif kind == "quad":
+        elif kind in ("quad", "bn_quad"):
             used += 2
-        elif kind == "pool":
+        elif kind in ("pool", "avgpool"):
             stride *= 2
             w //= 2
             if dims == 2:

@@ -152,10 +152,99 @@ std::vector<Rot> rots_for(const hear_context *c, const hear_eval_keys *evk, cons
     return r;
 }
 
+// Layer collapsing (Methods, "Non-convolutional layers"): a block's convolution bias, batch
+// normalisation and quadratic activation become one quadratic per feature map, and the
+// 1/2 (1D) or 1/4 (2D) of each average pooling and the 1/(h*w) of the global average
+// pooling move into the weights of the next linear layer, so that pooling is a plain sum.
+// With BN(y + bias) = s*y + t, s = gamma / sqrt(var + eps), t = s*(bias - mean) + beta and
+// the activation a*z^2 + b*z + c:  A = a*s^2, B = 2*a*s*t + b*s, C = a*t^2 + b*t + c.
+// The doubles are formed in exactly the order written here (A = (a*s)*s,
+// B = ((2*a)*s)*t + b*s, C = ((a*t)*t + b*t) + c; conv weights w*scale, FC weights
+// (w*scale)/(h*w)), so every encoded plaintext is reproducible from the description.
+// Layers that are already collapsed pass through unchanged.
+struct Collapsed {
+    std::vector<hear_cnn_layer> layers;
+    std::vector<std::unique_ptr<std::vector<double>>> store;
+    const double *keep(std::vector<double> &&v) {
+        store.push_back(std::make_unique<std::vector<double>>(std::move(v)));
+        return store.back()->data();
+    }
+};
+
+Collapsed collapse_layers(const hear_cnn_input *in, const hear_cnn_layer *layers, size_t n_layers) {
+    Collapsed out;
+    const uint32_t dims = in->conv_dims;
+    uint32_t h = in->h, w = in->w, channels = in->c_in;
+    double scale = 1.0;        // pending average-pooling factor for the next linear layer
+    double divisor = 1.0;      // pending global-average-pooling divisor (h*w) for the FC
+    for (size_t li = 0; li < n_layers; li++) {
+        hear_cnn_layer d = layers[li];
+        if (d.kind == HEAR_CNN_CONV) {
+            HEAR_REQUIRE(d.w && d.c_out && d.f_h && d.f_w, HEAR_E_INVAL, "conv needs weights and filter sizes");
+            if (scale != 1.0) {
+                const size_t nw = (size_t)d.c_out * channels * d.f_h * d.f_w;
+                std::vector<double> v(nw);
+                for (size_t i = 0; i < nw; i++) v[i] = d.w[i] * scale;
+                d.w = out.keep(std::move(v));
+            }
+            scale = 1.0;
+            channels = d.c_out;
+        } else if (d.kind == HEAR_CNN_BN_QUAD) {
+            HEAR_REQUIRE(d.bn_gamma && d.bn_beta && d.bn_mean && d.bn_var, HEAR_E_INVAL,
+                         "batch normalisation needs gamma, beta, mean and var");
+            HEAR_REQUIRE(d.bn_eps >= 0.0, HEAR_E_INVAL, "batch-normalisation epsilon must be >= 0");
+            std::vector<double> A(channels), B(channels), C(channels);
+            const double a = d.act[0], b = d.act[1], cc = d.act[2];
+            for (uint32_t k = 0; k < channels; k++) {
+                HEAR_REQUIRE(d.bn_var[k] + d.bn_eps > 0.0, HEAR_E_INVAL, "batch-normalisation variance must be > 0");
+                const double sk = d.bn_gamma[k] / std::sqrt(d.bn_var[k] + d.bn_eps);
+                const double bias = d.conv_bias ? d.conv_bias[k] : 0.0;
+                const double tk = sk * (bias - d.bn_mean[k]) + d.bn_beta[k];
+                A[k] = a * sk * sk;
+                B[k] = 2.0 * a * sk * tk + b * sk;
+                C[k] = a * tk * tk + b * tk + cc;
+            }
+            hear_cnn_layer q{};
+            q.kind = HEAR_CNN_QUAD;
+            q.a = out.keep(std::move(A));
+            q.b = out.keep(std::move(B));
+            q.c = out.keep(std::move(C));
+            d = q;
+        } else if (d.kind == HEAR_CNN_AVGPOOL || d.kind == HEAR_CNN_POOL) {
+            if (d.kind == HEAR_CNN_AVGPOOL) scale *= dims == 1 ? 0.5 : 0.25;
+            d.kind = HEAR_CNN_POOL;
+            w /= 2;
+            if (dims == 2) h /= 2;
+        } else if (d.kind == HEAR_CNN_GAVGPOOL || d.kind == HEAR_CNN_GAP) {
+            if (d.kind == HEAR_CNN_GAVGPOOL) {
+                HEAR_REQUIRE(h >= 1 && w >= 1, HEAR_E_INVAL, "pooling an empty map");
+                divisor = (double)(h * w);
+            }
+            d.kind = HEAR_CNN_GAP;
+        } else if (d.kind == HEAR_CNN_FC) {
+            HEAR_REQUIRE(d.w && d.c_out, HEAR_E_INVAL, "FC needs weights");
+            if (scale != 1.0 || divisor != 1.0) {
+                const size_t nw = (size_t)d.c_out * channels;
+                std::vector<double> v(nw);
+                for (size_t i = 0; i < nw; i++) v[i] = (d.w[i] * scale) / divisor;
+                d.w = out.keep(std::move(v));
+            }
+            scale = divisor = 1.0;
+        } else {
+            HEAR_REQUIRE(d.kind == HEAR_CNN_QUAD, HEAR_E_INVAL, "unknown layer kind");
+        }
+        out.layers.push_back(d);
+    }
+    return out;
+}
+
 }  // namespace
 
-hear_cnn *cnn_create(hear_context *c, const hear_cnn_input *in, const hear_cnn_layer *layers, size_t n_layers) {
-    HEAR_REQUIRE(in && layers && n_layers, HEAR_E_INVAL, "no layers");
+hear_cnn *cnn_create(hear_context *c, const hear_cnn_input *in, const hear_cnn_layer *layers_in, size_t n_layers) {
+    HEAR_REQUIRE(in && layers_in && n_layers, HEAR_E_INVAL, "no layers");
+    HEAR_REQUIRE(in->conv_dims == 1 || in->conv_dims == 2, HEAR_E_INVAL, "conv_dims must be 1 or 2");
+    const Collapsed collapsed = collapse_layers(in, layers_in, n_layers);
+    const hear_cnn_layer *layers = collapsed.layers.data();
     HEAR_REQUIRE(in->conv_dims == 1 || in->conv_dims == 2, HEAR_E_INVAL, "conv_dims must be 1 or 2");
     HEAR_REQUIRE(in->c_in && in->h && in->w && in->stride, HEAR_E_INVAL, "empty input map");
     HEAR_REQUIRE(in->conv_dims == 2 || in->h == 1, HEAR_E_INVAL, "1D maps have h = 1");
@@ -630,4 +719,42 @@ std::vector<double> cnn_pack_input(const hear_cnn *m, const double *x) {
 hear_cnn::Plan::~Plan() {
     if (exec) cudaGraphExecDestroy(exec);
     if (done) cudaEventDestroy(done);
+}
+
+namespace hear {
+void set_last_error(const std::string &msg);   // capi.cu
+}
+
+// Host-only: the collapsed network's doubles (see collapse_layers), no context or GPU.
+extern "C" hear_status hear_cnn_collapse(const hear_cnn_input *in, const hear_cnn_layer *layers, size_t n_layers,
+                                         double *out, size_t cap, size_t *n) {
+    using namespace hear;
+    try {
+        HEAR_REQUIRE(in && layers && n_layers, HEAR_E_INVAL, "no layers");
+        HEAR_REQUIRE(in->conv_dims == 1 || in->conv_dims == 2, HEAR_E_INVAL, "conv_dims must be 1 or 2");
+        const Collapsed col = collapse_layers(in, layers, n_layers);
+        std::vector<double> v;
+        uint32_t channels = in->c_in;
+        for (const hear_cnn_layer &d : col.layers) {
+            if (d.kind == HEAR_CNN_CONV) {
+                v.insert(v.end(), d.w, d.w + (size_t)d.c_out * channels * d.f_h * d.f_w);
+                channels = d.c_out;
+            } else if (d.kind == HEAR_CNN_QUAD) {
+                HEAR_REQUIRE(d.a && d.b && d.c, HEAR_E_INVAL, "quad needs a, b, c");
+                for (const double *p : {d.a, d.b, d.c}) v.insert(v.end(), p, p + channels);
+            } else if (d.kind == HEAR_CNN_FC) {
+                v.insert(v.end(), d.w, d.w + (size_t)d.c_out * channels);
+            }
+        }
+        if (n) *n = v.size();
+        HEAR_REQUIRE(out && cap >= v.size(), HEAR_E_INVAL, "output capacity too small");
+        std::copy(v.begin(), v.end(), out);
+        return HEAR_OK;
+    } catch (const Error &e) {
+        set_last_error(e.what());
+        return e.code;
+    } catch (const std::exception &e) {
+        set_last_error(e.what());
+        return HEAR_E_INVAL;
+    }
 }

@@ -201,6 +201,10 @@ void build_context(hear_context *c, const hear_params_desc *d, int device) {
     c->n_p = d->n_p;
     c->L = d->n_q - 1;
     c->K = d->n_p;
+    // hybrid key switching: digits of alpha = K limbs (0 = that default); a digit modulus
+    // larger than P would let the key-switching error grow by Q_j / P
+    HEAR_REQUIRE(d->alpha == 0 || d->alpha == d->n_p, HEAR_E_UNSUPPORTED,
+                 "alpha (limbs per key-switching digit) must equal n_p (or be 0 for that default)");
     c->alpha = d->n_p;
     c->default_scale = std::ldexp(1.0, 0) * std::pow(2.0, d->log2_scale);
     c->sigma = d->sigma;

@@ -19,6 +19,7 @@ HEAR_LAYER_SQUARE = 2
 HEAR_LAYER_FC_SQ_FC = 3
 DEFAULT_ROTSUM_RADIX = 8
 HEAR_CNN_CONV, HEAR_CNN_QUAD, HEAR_CNN_POOL, HEAR_CNN_GAP, HEAR_CNN_FC = 1, 2, 3, 4, 5
+HEAR_CNN_BN_QUAD, HEAR_CNN_AVGPOOL, HEAR_CNN_GAVGPOOL = 6, 7, 8
 HEAR_STRATEGY_HYBRID, HEAR_STRATEGY_FULL, HEAR_STRATEGY_BABY, HEAR_STRATEGY_GIANT = 0, 1, 2, 3
 HEAR_CNN_OP_DIAG, HEAR_CNN_OP_PACK, HEAR_CNN_OP_ROTSUM, HEAR_CNN_OP_QUAD, HEAR_CNN_OP_BIAS = 1, 2, 3, 4, 5
 
@@ -35,7 +36,7 @@ _szp = ctypes.POINTER(ctypes.c_size_t)
 class hear_params_desc(ctypes.Structure):
     _fields_ = [("log_n", ctypes.c_uint32), ("n_q", ctypes.c_uint32), ("q_bits", _u32p),
                 ("n_p", ctypes.c_uint32), ("p_bits", _u32p), ("log2_scale", ctypes.c_double),
-                ("sigma", ctypes.c_double)]
+                ("sigma", ctypes.c_double), ("alpha", ctypes.c_uint32)]
 
 
 class hear_layer_desc(ctypes.Structure):
@@ -73,7 +74,9 @@ class hear_cnn_input(ctypes.Structure):
 class hear_cnn_layer(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_uint32), ("c_out", ctypes.c_uint32), ("f_h", ctypes.c_uint32),
                 ("f_w", ctypes.c_uint32), ("w", _dp), ("bias", _dp), ("a", _dp), ("b", _dp), ("c", _dp),
-                ("fast", ctypes.c_uint32), ("strategy", ctypes.c_uint32), ("n1", ctypes.c_uint32)]
+                ("fast", ctypes.c_uint32), ("strategy", ctypes.c_uint32), ("n1", ctypes.c_uint32),
+                ("conv_bias", _dp), ("bn_gamma", _dp), ("bn_beta", _dp), ("bn_mean", _dp), ("bn_var", _dp),
+                ("bn_eps", ctypes.c_double), ("act", ctypes.c_double * 3)]
 
 
 class hear_cnn_op_info(ctypes.Structure):
@@ -94,7 +97,10 @@ class HearError(RuntimeError):
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
-_allocators = {}   # context -> the ctypes callbacks (kept alive while the context uses them)
+# context -> every ctypes callback pair ever installed on it: buffers allocated through a
+# hook keep its free function after the hook is replaced, so each pair stays alive until
+# the context (and everything made with it) is destroyed
+_allocators = {}
 
 
 def _load():
@@ -161,6 +167,8 @@ def _load():
         "hear_server_poll": (st, [_vp, ctypes.c_uint64, _u64p, ctypes.c_size_t, _szp, ctypes.POINTER(ctypes.c_int)]),
         "hear_server_stats": (st, [_vp, ctypes.POINTER(hear_server_counters)]),
         "hear_server_destroy": (None, [_vp]),
+        "hear_cnn_collapse": (st, [ctypes.POINTER(hear_cnn_input), ctypes.POINTER(hear_cnn_layer), ctypes.c_size_t,
+                                   _dp, ctypes.c_size_t, _szp]),
         "hear_cnn_create": (st, [_vp, ctypes.POINTER(hear_cnn_input), ctypes.POINTER(hear_cnn_layer),
                                  ctypes.c_size_t, ctypes.POINTER(_vp)]),
         "hear_cnn_destroy": (None, [_vp]),
@@ -186,7 +194,8 @@ def _load():
         "hear_simd_evaluate_host": (st, [_vp, _vp, _u64p, ctypes.c_double, _u64p, ctypes.c_size_t, _szp, _u32p,
                                          _dp, _vp]),
         "hear_simd_decrypt": (st, [_vp, _vp, _vp, ctypes.c_size_t, _dp, ctypes.c_size_t, _szp]),
-        "hear_rescale_noalloc": (st, [_vp, _u64p, ctypes.c_uint32, ctypes.c_uint32, _u64p, _vp]),
+        "hear_rescale_noalloc": (st, [_vp, _u64p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_uint32, _u64p,
+                                      ctypes.c_size_t, _vp]),
         "hear_profile_begin": (st, [_vp]),
         "hear_profile_end": (st, [_vp, ctypes.POINTER(hear_profile_entry), ctypes.c_size_t, _szp]),
         "hear_launch_count": (ctypes.c_uint64, []),
@@ -235,10 +244,11 @@ def _p(a, t):
 
 
 # ---------------------------------------------------------------- context
-def hear_context_create(log_n, q_bits, p_bits, log2_scale=40.0, sigma=3.2, device=0):
+def hear_context_create(log_n, q_bits, p_bits, log2_scale=40.0, sigma=3.2, device=0, alpha=0):
     qb = _arr(q_bits, np.uint32)
     pb = _arr(p_bits, np.uint32)
-    d = hear_params_desc(log_n, len(qb), _p(qb, _u32p), len(pb), _p(pb, _u32p), float(log2_scale), float(sigma))
+    d = hear_params_desc(log_n, len(qb), _p(qb, _u32p), len(pb), _p(pb, _u32p), float(log2_scale), float(sigma),
+                         int(alpha))
     h = _vp()
     _check(lib.hear_context_create(ctypes.byref(d), int(device), ctypes.byref(h)))
     return h.value
@@ -246,6 +256,7 @@ def hear_context_create(log_n, q_bits, p_bits, log2_scale=40.0, sigma=3.2, devic
 
 def hear_context_destroy(ctx):
     lib.hear_context_destroy(ctx)
+    _allocators.pop(ctx, None)   # released only after the library has freed everything
 
 
 def _vec_out(fn, handle, dtype, ptr_t, *pre):
@@ -262,10 +273,8 @@ def hear_set_allocator(ctx, alloc, free):
     a = _ALLOC_FN(lambda n, st, u: alloc(int(n), int(st or 0)) or None) if alloc is not None else _ALLOC_FN()
     f = _FREE_FN(lambda p, st, u: free(int(p), int(st or 0))) if free is not None else _FREE_FN()
     _check(lib.hear_set_allocator(ctx, a, f, None))
-    if alloc is None:
-        _allocators.pop(ctx, None)
-    else:
-        _allocators[ctx] = (a, f)
+    if alloc is not None:
+        _allocators.setdefault(ctx, []).append((a, f))
 
 
 def hear_context_primes(ctx):
@@ -623,9 +632,29 @@ def _strategy(s):
 
 
 def hear_cnn_create(ctx, spec, strategies=None):
-    """spec: collapsed network dict {"conv_dims", "c_in", "h", "w", ["pitch", "stride"],
-    "layers": [("conv", W[c_out][c_in][fh][fw], fast) | ("quad", a, b, c) | ("pool",) |
-    ("gap",) | ("fc", W, bias)]}; strategies: one per conv / fc layer (see _strategy)"""
+    """spec: network dict {"conv_dims", "c_in", "h", "w", ["pitch", "stride"],
+    "layers": [("conv", W[c_out][c_in][fh][fw], fast) | ("bn_quad", conv_bias, gamma, beta,
+    mean, var, eps, (a, b, c)) | ("avgpool",) | ("gavgpool",) | ("quad", A, B, C) | ("pool",) |
+    ("gap",) | ("fc", W, bias)]}: as trained (the library collapses bn_quad / avgpool /
+    gavgpool) or already collapsed; strategies: one per conv / fc layer (see _strategy)"""
+    inp, descs, keep = _cnn_descs(spec, strategies)
+    h = _vp()
+    _check(lib.hear_cnn_create(ctx, ctypes.byref(inp), descs, len(descs), ctypes.byref(h)))
+    return h.value
+
+
+def hear_cnn_collapse(spec):
+    """host only: the collapsed network's doubles in layer order (CONV weights, QUAD A, B, C,
+    FC weights) as the library computes them"""
+    inp, descs, keep = _cnn_descs(spec, None)
+    n = ctypes.c_size_t(0)
+    lib.hear_cnn_collapse(ctypes.byref(inp), descs, len(descs), None, 0, ctypes.byref(n))
+    out = np.empty(n.value, dtype=np.float64)
+    _check(lib.hear_cnn_collapse(ctypes.byref(inp), descs, len(descs), _p(out, _dp), out.size, ctypes.byref(n)))
+    return out
+
+
+def _cnn_descs(spec, strategies):
     inp = hear_cnn_input(int(spec["conv_dims"]), int(spec["c_in"]), int(spec["h"]), int(spec["w"]),
                          int(spec.get("pitch", 0)), int(spec.get("stride", 1)), int(spec.get("level", 0)))
     layers = spec["layers"]
@@ -646,10 +675,19 @@ def hear_cnn_create(ctx, spec, strategies=None):
             a, b, c = (_arr(v, np.float64) for v in layer[1:4])
             keep += [a, b, c]
             d.kind, d.a, d.b, d.c = HEAR_CNN_QUAD, _p(a, _dp), _p(b, _dp), _p(c, _dp)
-        elif kind == "pool":
-            d.kind = HEAR_CNN_POOL
-        elif kind == "gap":
-            d.kind = HEAR_CNN_GAP
+        elif kind == "bn_quad":
+            bias, gamma, beta, mean, var = (None if v is None else _arr(v, np.float64) for v in layer[1:6])
+            keep += [v for v in (bias, gamma, beta, mean, var) if v is not None]
+            d.kind = HEAR_CNN_BN_QUAD
+            d.conv_bias = _p(bias, _dp) if bias is not None else None
+            d.bn_gamma, d.bn_beta, d.bn_mean, d.bn_var = (_p(v, _dp) for v in (gamma, beta, mean, var))
+            d.bn_eps = float(layer[6])
+            for i, v in enumerate(layer[7]):
+                d.act[i] = float(v)
+        elif kind in ("pool", "avgpool"):
+            d.kind = HEAR_CNN_POOL if kind == "pool" else HEAR_CNN_AVGPOOL
+        elif kind in ("gap", "gavgpool"):
+            d.kind = HEAR_CNN_GAP if kind == "gap" else HEAR_CNN_GAVGPOOL
         elif kind == "fc":
             W = _arr(layer[1], np.float64)
             keep.append(W)
@@ -662,9 +700,7 @@ def hear_cnn_create(ctx, spec, strategies=None):
             si += 1
         else:
             raise ValueError(kind)
-    h = _vp()
-    _check(lib.hear_cnn_create(ctx, ctypes.byref(inp), descs, len(layers), ctypes.byref(h)))
-    return h.value
+    return inp, descs, keep
 
 
 def hear_cnn_destroy(m):
@@ -740,12 +776,15 @@ def hear_server_destroy(s):
     lib.hear_server_destroy(s)
 
 
-def hear_rescale_noalloc(ctx, words, level, n_poly, stream=None):
-    """rescale from/to host arrays (coefficient domain) without device allocation"""
+def hear_rescale_noalloc(ctx, words, level, n_poly, stream=None, n=None):
+    """rescale from/to host arrays (coefficient domain) without device allocation; n = the
+    ring size N (default: from words.size); the library checks words.size itself"""
     w = _arr(words, np.uint64).reshape(-1)
-    n = w.size // (n_poly * (level + 1))
-    out = np.empty(n_poly * level * n, dtype=np.uint64)
-    _check(lib.hear_rescale_noalloc(ctx, _p(w, _u64p), int(level), int(n_poly), _p(out, _u64p), _stream(stream)))
+    if n is None:
+        n = max(1, w.size // (n_poly * (level + 1)))
+    out = np.empty(n_poly * max(level, 0) * n, dtype=np.uint64)
+    _check(lib.hear_rescale_noalloc(ctx, _p(w, _u64p), w.size, int(level), int(n_poly), _p(out, _u64p), out.size,
+                                    _stream(stream)))
     return out.reshape(n_poly, level, n)
 
 

@@ -273,6 +273,23 @@ def cnn_forward(net: CnnNet, clip, upto=None):
     return net.fc_w @ g + net.fc_b
 
 
+def cnn_spec(net: CnnNet) -> dict:
+    """The network as trained, in the layer vocabulary of hear_cnn_create: per block the
+    convolution, its bias with batch normalisation and the quadratic activation
+    ("bn_quad"), then average pooling (global after the last block), and the FC.  No
+    arithmetic: the collapse is done by the library (and, separately, by the oracle)."""
+    dims = net.conv_dims
+    h, w = (1, 480) if dims == 1 else (32, 15)
+    spec = {"conv_dims": dims, "c_in": 2, "h": h, "w": w, "layers": []}
+    for li, cv in enumerate(net.convs):
+        spec["layers"].append(("conv", cv["W"], bool(net.fast[li])))
+        spec["layers"].append(("bn_quad", cv["bias"], cv["gamma"], cv["beta"], cv["mean"], cv["var"], BN_EPS,
+                               tuple(cv["act"])))
+        spec["layers"].append(("avgpool",) if li < len(net.convs) - 1 else ("gavgpool",))
+    spec["layers"].append(("fc", net.fc_w, np.asarray(net.fc_b, dtype=np.float64)))
+    return spec
+
+
 _CNN_SETS = {
     # name: (log_n, q_bits, p_bits, conv dims, filters, fast per conv)
     # 12 levels: conv 1 + quad 2 per block, one mask level per fast conv, FC 1

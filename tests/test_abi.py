@@ -80,3 +80,22 @@ def test_status_codes_match_the_header(libpath):
     src = open(os.path.join(ROOT, "include", "hear.h")).read()
     for name, val in re.findall(r"#define (HEAR_(?:OK|E_[A-Z]+))\s+\(?(-?\d+)\)?", src):
         assert getattr(hear, name) == int(val), name
+
+
+def test_params_alpha_is_checked_before_any_device_work(libpath):
+    """hear_params_desc.alpha: 0 or n_p is accepted; any other digit size is refused with
+    HEAR_E_UNSUPPORTED before the library touches a device"""
+    from paper_2104_09164_gb300 import hear
+    for alpha in (1, 3):
+        with pytest.raises(hear.HearError) as e:
+            hear.hear_context_create(14, [60] + [40] * 7, [60, 60], alpha=alpha)
+        assert e.value.code == hear.HEAR_E_UNSUPPORTED and "alpha" in str(e.value)
+    # a struct with the field in place: the refusal is the alpha check, not a layout error
+    assert ctypes.sizeof(hear.hear_params_desc) >= 48
+
+
+def test_noalloc_refuses_bad_sizes_without_a_gpu(libpath):
+    """argument checks of hear_rescale_noalloc that need no device: a null context"""
+    from paper_2104_09164_gb300 import hear
+    lib = hear.lib
+    assert lib.hear_rescale_noalloc(None, None, 0, 1, 2, None, 0, None) == hear.HEAR_E_INVAL

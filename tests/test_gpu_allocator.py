@@ -82,6 +82,15 @@ def test_caller_allocator(H):
         keep.append(again)
         with pytest.raises(H.HearError):
             H.hear_set_allocator(ctx, alloc, None)         # one function without the other
+        # back to the pool: the handles made through the hook still release their memory
+        # through it when they are destroyed below (the callbacks must stay alive)
+        H.hear_set_allocator(ctx, None, None)
+        import gc
+        gc.collect()
+        n_alloc = calls["alloc"]
+        tmp = H.hear_evaluate(model, evk, [ct])[0]
+        assert calls["alloc"] == n_alloc                   # no longer through the hook
+        H.hear_ciphertext_destroy(tmp)
     finally:
         model, sk, pk, evk = keep[0], keep[1], keep[2], keep[3]
         for h in keep[4:]:

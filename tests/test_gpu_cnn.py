@@ -16,9 +16,8 @@ import pytest
 
 from oracle import cnn as OC
 from oracle import oracle as O
-from paper_2104_09164_gb300.collapse import collapse_cnn
-from paper_2104_09164_gb300.workloads import (CONV_BENCH_PARAMS, _conv_same, cnn_forward, conv_bench_layer,
-                                              make_cnn)
+from paper_2104_09164_gb300.workloads import (CONV_BENCH_PARAMS, _conv_same, cnn_forward, cnn_spec,
+                                              conv_bench_layer, make_cnn)
 
 pytestmark = pytest.mark.gpu
 
@@ -44,9 +43,10 @@ def _check_ops(H, m, ops):
 
 def _network(H, name, strategies, n_samples, oracle_samples):
     net = make_cnn(name, n_samples=n_samples)
-    spec = collapse_cnn(net)
+    spec = cnn_spec(net)               # as trained: the library collapses it
+    ospec = OC.collapse(spec)          # the oracle collapses it on its own
     S = net.slots
-    ops, out = OC.build_plan(spec, S, strategies)
+    ops, out = OC.build_plan(ospec, S, strategies)
     ctx = H.hear_context_create(net.log_n, net.q_bits, net.p_bits, net.log2_scale, net.sigma, 0)
     m = H.hear_cnn_create(ctx, spec, strategies)
     try:
@@ -64,7 +64,7 @@ def _network(H, name, strategies, n_samples, oracle_samples):
         keys = o.keygen(301, [O.galois_for_step(s, o.n) for s in steps])
         pool = ThreadPoolExecutor(max_workers=os.cpu_count() or 4)
         for s in oracle_samples:
-            ct = o.encrypt(keys.pk, OC.pack_input(spec, net.clips[s], S), 401, s, 2.0 ** net.log2_scale)
+            ct = o.encrypt(keys.pk, OC.pack_input(ospec, net.clips[s], S), 401, s, 2.0 ** net.log2_scale)
             r = OC.evaluate(o, ops, [ct], keys, pool)[0]
             lv, npoly, sc = H.hear_ciphertext_info(outs[s])
             assert (lv, npoly) == (r.level, 2) and sc == r.scale
@@ -146,7 +146,7 @@ def test_autotuned_strategies_bit_exact(H):
     """the tuner's per-layer choice evaluates bit-exactly like the oracle with that choice"""
     from paper_2104_09164_gb300.autotune import tune_cnn
     net = make_cnn("cnn_toy", n_samples=2)
-    spec = collapse_cnn(net)
+    spec = cnn_spec(net)
     ctx = H.hear_context_create(net.log_n, net.q_bits, net.p_bits, net.log2_scale, net.sigma, 0)
     try:
         strategies, report = tune_cnn(H, ctx, spec, net.slots, len(net.q_bits) - 1, iters=2)
@@ -160,7 +160,7 @@ def test_cnn_rejects_bad_inputs(H):
     """errors come back as status codes: a fast convolution on a dense input, channel counts
     that do not fill the blocks, missing rotation keys, inputs at the wrong level"""
     net = make_cnn("cnn_toy", n_samples=1)
-    spec = collapse_cnn(net)
+    spec = cnn_spec(net)
     ctx = H.hear_context_create(net.log_n, net.q_bits, net.p_bits, net.log2_scale, net.sigma, 0)
     try:
         bad = dict(spec, layers=[("conv", spec["layers"][0][1], True)] + spec["layers"][1:])

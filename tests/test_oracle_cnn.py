@@ -1,4 +1,5 @@
-"""CPU pins of the oracle's CNN part (oracle/cnn.py) and of the network collapse.
+"""CPU pins of the oracle's CNN part (oracle/cnn.py) and of the network collapse (the
+oracle's own, and the library's host-only one, which must agree to the bit).
 
 The plan builder (slot layouts, convolution plaintexts of Eq. conv, the fast
 convolution's packing and phase sums, pooling, global pooling, the FC on pooled features)
@@ -16,9 +17,8 @@ import pytest
 
 from oracle import cnn as OC
 from oracle import oracle as O
-from paper_2104_09164_gb300.collapse import collapse_cnn
-from paper_2104_09164_gb300.workloads import (TABLE1_LAYERS, _conv_same, cnn_forward, conv_bench_layer,
-                                              make_cnn)
+from paper_2104_09164_gb300.workloads import (TABLE1_LAYERS, _conv_same, cnn_forward, cnn_spec,
+                                              conv_bench_layer, make_cnn)
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -95,7 +95,7 @@ def test_diag_layer_matches_plain_rotations(toy):
 @pytest.mark.parametrize("strategy", [None, "full", "baby", "giant", ("hybrid", 2)])
 def test_plan_on_plain_slots_equals_fp64_network(name, strategy):
     net = make_cnn(name, n_samples=1)
-    spec = collapse_cnn(net)
+    spec = OC.collapse(cnn_spec(net))
     S = net.slots
     ops, out = OC.build_plan(spec, S, None if strategy is None else [strategy] * 4)
     got = OC.simulate(ops, [OC.pack_input(spec, net.clips[0], S)])[0][out]
@@ -103,11 +103,43 @@ def test_plan_on_plain_slots_equals_fp64_network(name, strategy):
     assert np.max(np.abs(got - ref)) < 1e-12
 
 
+def test_library_collapse_equals_the_oracle_collapse():
+    """the library's collapse (hear_cnn_collapse, host only) and the oracle's, from the
+    same trained network, give the same doubles bit for bit (the encoded plaintexts depend
+    on every bit), and a deliberately different order of the same formula does not"""
+    pytest.importorskip("ctypes")
+    from paper_2104_09164_gb300 import hear as H
+    def flat(collapsed):
+        out = []
+        for layer in collapsed["layers"]:
+            if layer[0] in ("conv", "fc"):
+                out.append(np.asarray(layer[1], dtype=np.float64).ravel())
+            elif layer[0] == "quad":
+                out += [np.asarray(v, dtype=np.float64).ravel() for v in layer[1:4]]
+        return np.concatenate(out)
+
+    for name in ("cnn_toy", "cnn2d_toy", "cnn1d64", "cnn2d64"):
+        spec = cnn_spec(make_cnn(name, n_samples=1))
+        got = H.hear_cnn_collapse(spec)
+        want = flat(OC.collapse(spec))
+        assert got.shape == want.shape
+        assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
+        # an already-collapsed network passes through the library's collapse unchanged
+        coll = OC.collapse(spec)
+        assert np.array_equal(H.hear_cnn_collapse(coll).view(np.uint64), want.view(np.uint64))
+    # B = 2 a s t + b s formed as 2 a (s t) + b s instead differs in some bits: the order matters
+    cv = make_cnn("cnn2d64", n_samples=1).convs[1]
+    s = cv["gamma"] / np.sqrt(cv["var"] + 1e-5)
+    t = s * (cv["bias"] - cv["mean"]) + cv["beta"]
+    a, b, _ = cv["act"]
+    assert not np.array_equal(2.0 * a * s * t + b * s, 2.0 * a * (s * t) + b * s)
+
+
 def test_collapse_keeps_the_network():
     """collapsed form evaluated plainly (no slots) = the uncollapsed network"""
     for name in ("cnn_toy", "cnn2d64"):
         net = make_cnn(name, n_samples=2)
-        spec = collapse_cnn(net)
+        spec = OC.collapse(cnn_spec(net))
         dims = spec["conv_dims"]
         for clip in net.clips:
             h = clip.reshape(2, -1) if dims == 1 else clip
@@ -187,7 +219,7 @@ def test_punctured_conv_layer_equals_fp64(idx):
 
 def test_encrypted_toy_cnn_matches_fp64():
     net = make_cnn("cnn_toy", n_samples=1)
-    spec = collapse_cnn(net)
+    spec = OC.collapse(cnn_spec(net))
     S = net.slots
     ops, out = OC.build_plan(spec, S)
     assert OC.plan_depth(ops) == len(net.q_bits) - 1
@@ -207,7 +239,7 @@ def test_autotune_layer_geometry_matches_the_network_plan():
     from paper_2104_09164_gb300.autotune import candidates, conv_layer_specs
     for name in ("cnn_toy", "cnn2d64"):
         net = make_cnn(name, n_samples=1)
-        spec = collapse_cnn(net)
+        spec = OC.collapse(cnn_spec(net))
         S = net.slots
         ops, _ = OC.build_plan(spec, S)
         depth_before = []

@@ -216,6 +216,32 @@ def test_gaussian_sampler_statistics(tiny):
     assert len(T) == 20 and T[-1] == 1 << 63 and all(a < b for a, b in zip(T, T[1:]))
 
 
+def test_cdt_thresholds_against_exact_discretised_normal(tiny):
+    """The CDT thresholds T_k = floor(S_k / S_19 * 2^63), S_k = sum over |x| <= k of
+    exp(-x^2 / (2 sigma^2)), evaluated in 200-bit arithmetic.  The oracle (like the library)
+    sums in double with libm exp, so its T_k may differ from the exact value in the low
+    bits: relative error of S_k / S_19 at most about 40 roundings of 2^-53, i.e. below 2^16
+    in absolute terms after the 2^63 scaling.  A wrong sigma, tail cut, missing factor 2
+    or shifted index moves a threshold by far more than that."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.prec = 200
+    sigma = mpmath.mpf("3.2")
+    B = int(mpmath.floor(6 * sigma))
+    assert B == 19
+    rho = [mpmath.exp(-mpmath.mpf(x) ** 2 / (2 * sigma ** 2)) for x in range(B + 1)]
+    S = [rho[0] + 2 * sum(rho[1:k + 1]) for k in range(B + 1)]
+    exact = [int(mpmath.floor(S[k] / S[B] * mpmath.mpf(2) ** 63)) for k in range(B)] + [1 << 63]
+    t = np.zeros(64, dtype=np.uint64)
+    cnt = np.zeros(1, dtype=np.uint32)
+    assert lib().or_cdt_table(tiny.h, P(t), 64, P(cnt, _u32p)) == 0
+    T = [int(v) for v in t[:int(cnt[0])]]
+    assert len(T) == B + 1
+    diffs = [abs(a - b) for a, b in zip(T, exact)]
+    assert max(diffs) < 1 << 16, diffs
+    # the first threshold is P(e = 0) = 1 / S_19 (about 0.1247 of 2^63)
+    assert abs(T[0] / 2.0 ** 63 - 0.12467) < 1e-4
+
+
 def test_ternary_and_uniform_samplers():
     n = 300000
     s = np.zeros(n, dtype=np.int8)

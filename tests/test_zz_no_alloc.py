@@ -46,6 +46,27 @@ def test_rescale_noalloc_equals_rescale(H):
             assert got.shape == want.shape
             assert np.array_equal(got, want)
             H.hear_ciphertext_destroy(ref)
+        # a buffer whose size does not match n_poly * (level + 1) * N is refused before any
+        # copy (the library reads and writes only what the sizes it is given allow)
+        level, n_poly, _ = H.hear_ciphertext_info(cases[0])
+        words = H.hear_ciphertext_export(cases[0]).reshape(-1)
+        with pytest.raises(H.HearError) as e:
+            H.hear_rescale_noalloc(ctx, words[: words.size // 2], level, n_poly, n=1 << log_n)
+        assert e.value.code == H.HEAR_E_FORMAT
+        with pytest.raises(H.HearError) as e:
+            H.hear_rescale_noalloc(ctx, np.concatenate([words, words]), level, n_poly, n=1 << log_n)
+        assert e.value.code == H.HEAR_E_FORMAT
+        # a residue that is not reduced mod its limb's prime is refused too
+        primes = H.hear_context_primes(ctx)
+        bad = words.copy()
+        bad[3 << log_n] = np.uint64(primes[3])
+        with pytest.raises(H.HearError) as e:
+            H.hear_rescale_noalloc(ctx, bad, level, n_poly)
+        assert e.value.code == H.HEAR_E_FORMAT
+        # and the array still serves a correct call after the refusals
+        ref = H.hear_rescale(cases[0])
+        assert np.array_equal(H.hear_rescale_noalloc(ctx, words, level, n_poly), H.hear_ciphertext_export(ref))
+        H.hear_ciphertext_destroy(ref)
         # a level-0 ciphertext has no prime left to divide by
         with pytest.raises(H.HearError) as e:
             H.hear_rescale_noalloc(ctx, np.zeros(2 << log_n, dtype=np.uint64), 0, 2)
