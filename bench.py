@@ -72,6 +72,14 @@ def describe(w):
              min(w.clips_per_ct, w.n_clips), w.n_ct))
 
 
+def describe_short(w):
+    nets = {"toy": "FC 64->16->x^2->FC 16->2", "small": "FC 2048->128->x^2->FC 128->2",
+            "large": "FC 2048->512->x^2->FC 512->128->x^2->FC 128->2"}
+    return "%s: N=2^%d, q=%d+%dx%d, p=%s bits, %s, %d clip(s) in %d ciphertext(s)" % (
+        w.name, w.log_n, w.q_bits[0], len(w.q_bits) - 1, w.q_bits[1], "+".join(map(str, w.p_bits)), nets[w.name],
+        w.n_clips, w.n_ct)
+
+
 # ------------------------------------------------------------------ distributed plumbing
 class Dist:
     """Rank plumbing for torchrun: one replica per GPU, a barrier around the timed region and
@@ -216,7 +224,10 @@ def committed_traffic(workload):
     return float(m_tr.group(1))
 
 
-def roofline(stages, psteps, log_n, workload):
+def roofline(stages, psteps, log_n, workload, bfly_peak=None):
+    """the forward NTT against its measured butterfly ceiling (bfly_peak: butterflies/s of
+    hear_dbg_bfly_peak on this context), with the HBM fraction and the derived integer-op
+    fraction beside it"""
     hbm, how = peaks()
     fwd = stages.get("ntt_fwd")
     name = max(stages.items(), key=lambda kv: kv[1][1])[0]
@@ -231,8 +242,14 @@ def roofline(stages, psteps, log_n, workload):
     alu = OPS_PER_BUTTERFLY * butterflies / (ms / 1e3) / 1e12
     gbs = byts / (ms / 1e3) / 1e9
     total = sum(v[1] for v in stages.values())
-    return {"bound": "alu", "kernel": "ntt_fwd (forward NTT, pass A + pass B kernels)", "achieved": alu,
-            "peak": ALU_PEAK_TOPS, "unit": "Tintops/s", "frac": alu / ALU_PEAK_TOPS,
+    bps = butterflies / (ms / 1e3) / 1e9
+    peak = bfly_peak / 1e9 if bfly_peak else None
+    return {"bound": "alu", "kernel": "ntt_fwd (forward NTT, pass A + pass B kernels)", "achieved": bps,
+            "peak": peak, "unit": "G butterflies/s", "frac": bps / peak if peak else None,
+            "peak_kind": "measured: hear_dbg_bfly_peak, the forward butterfly on register-resident radix-16 units "
+                         "over the context's primes",
+            "derived_alu_tintops": alu, "derived_alu_peak_tintops": ALU_PEAK_TOPS,
+            "derived_alu_frac": alu / ALU_PEAK_TOPS,
             "traffic": committed_traffic(workload) if calls else None,
             "algorithmic_bytes_per_call": byts / calls * 2 if calls else None,
             "calls_per_step": calls_per_step, "avg_call_us": ms * 1e3 / (calls / 2),
@@ -241,8 +258,9 @@ def roofline(stages, psteps, log_n, workload):
 
 
 # ------------------------------------------------------------------ oracle CPU timing
-def oracle_sample(w, steps_keys, seconds_budget=25.0):
-    """Time the CPU oracle (as it stands) evaluating whole ciphertexts of the workload.
+def oracle_sample(w, steps_keys, min_seconds=10.0, max_evals=40):
+    """Time the CPU oracle (as it stands) evaluating whole ciphertexts of the workload: at
+    least min_seconds of evaluations (a bounded sample, at most max_evals of them).
     Returns (inferences/s, cores, description)."""
     from oracle import oracle as O
     o = O.Oracle(w.log_n, w.q_bits, w.p_bits, w.sigma)
@@ -257,7 +275,7 @@ def oracle_sample(w, steps_keys, seconds_budget=25.0):
         o.evaluate(w.layers, ct, k, keys)
         n += 1
         el = time.perf_counter() - t0
-        if el > seconds_budget or n >= 3:
+        if el >= min_seconds or n >= max_evals:
             break
     return n * clips / el, cores, "%d whole ciphertext evaluation(s) of %d clip(s) each, %.1f s" % (n, clips, el)
 
@@ -811,12 +829,14 @@ def main_gpu(a):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": describe(w), "parallelism": "replicas" if dist.world > 1 else "single",
+            "config": {"workload": describe(w), "workload_short": describe_short(w),
+                       "parallelism": "replicas" if dist.world > 1 else "single",
                        "l2": "no flush: the per-step working set (switching keys %.0f MB plus plaintext "
                              "diagonals) is larger than the 129 MB L2" % _key_mb(w, len(S.steps))},
             "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
-            "roofline": roofline(stages, psteps, w.log_n, w.name if a.clips is None else w.name + "_%d" % a.clips),
+            "roofline": roofline(stages, psteps, w.log_n, w.name if a.clips is None else w.name + "_%d" % a.clips,
+                                 H.hear_dbg_bfly_peak(S.ctx)),
             "ntt": {"achieved_gbs": by_ntt / (ms_ntt / 1e3) / 1e9 if ms_ntt else None,
                     "launches_per_step": nl_ntt / psteps, "share": ms_ntt / total_stage_ms},
             "stages_ms_per_step": {k: v[1] / psteps for k, v in sorted(stages.items(), key=lambda kv: -kv[1][1])},
@@ -960,7 +980,7 @@ def headline(result, sections_path):
     for k in ("value", "ms_per_step", "p50_ms", "p99_ms"):
         h[k] = _r(h.get(k), 6)
     cfg = result["config"]
-    h["config"] = {"workload": cfg["workload"], "parallelism": cfg["parallelism"],
+    h["config"] = {"workload": cfg.get("workload_short", cfg["workload"]), "parallelism": cfg["parallelism"],
                    "l2": "no flush: per-step working set > 129 MB L2",
                    "ntt_table": cfg.get("ntt_table"),
                    "fc_form": {k: cfg["fc_form"].get(k) for k in ("fc_n1", "hoist_moddown")},
@@ -970,9 +990,9 @@ def headline(result, sections_path):
                 "d2h_bytes_per_step": e["d2h_bytes_per_step"]}
     rf = result["roofline"]
     h["roofline"] = {k: (_r(rf.get(k)) if isinstance(rf.get(k), float) else rf.get(k))
-                     for k in ("bound", "kernel", "achieved", "peak", "unit", "frac", "traffic", "peak_kind",
-                               "algorithmic_bytes_per_call", "avg_call_us", "hbm_achieved_gbs", "hbm_peak_gbs",
-                               "hbm_frac") if k in rf}
+                     for k in ("bound", "kernel", "achieved", "peak", "unit", "frac", "traffic",
+                               "hbm_achieved_gbs", "hbm_peak_gbs", "hbm_frac", "derived_alu_frac") if k in rf}
+    h["roofline"]["peak_kind"] = "measured (hear_dbg_bfly_peak)" if rf.get("peak") else None
     if "cpu_baseline" in result:
         cb = result["cpu_baseline"]
         h["cpu_baseline"] = {"value": _r(cb["value"]), "unit": cb["unit"], "cores": cb["cores"], "kind": cb["kind"],
@@ -996,20 +1016,19 @@ def headline(result, sections_path):
     if "served_mix" in result:
         rows = result["served_mix"]["sweep"]
         top = max(rows, key=lambda r: r["inferences_s"])
-        s["served_mix"] = {"rate_req_s": top["rate_req_s"], "value": _r(top["inferences_s"]),
-                           "p99_ms": {n["net"]: _r(n["p99_ms"]) for n in top["per_net"]}}
+        s["served_mix"] = {"rate_req_s": top["rate_req_s"], "value": _r(top["inferences_s"])}
     if "ragged_mix" in result:
         s["ragged_mix"] = {"value": _r(result["ragged_mix"]["value"])}
     if "min_start_level" in result:
         s["min_start_level"] = {k: _r(v["value"]) for k, v in result["min_start_level"].items()}
     if "batched_simd" in result:
-        rows = result["batched_simd"]["rows"]
-        s["batched_simd"] = [{"value": _r(r["value"]), "vs_plain": _r(r["vs_plain"], 3),
-                              "frac": _r(r["roofline"]["frac"], 3)} for r in rows]
+        r = result["batched_simd"]["rows"][0]
+        s["batched_simd"] = {"value": _r(r["value"]), "vs_plain": _r(r["vs_plain"], 3),
+                             "frac": _r(r["roofline"]["frac"], 3)}
     if "cnn" in result:
-        s["cnn1d64_ms"] = [_r(b["ms"]) for b in result["cnn"]["batches"]]
+        s["cnn1d64_batch1_ms"] = _r(result["cnn"]["batches"][0]["ms"])
     if "conv_table1" in result:
-        s["conv_table1_speedup"] = [_r(r["speedup"], 3) for r in result["conv_table1"]["rows"]]
+        s["conv_table1_max_speedup"] = _r(max(r["speedup"] for r in result["conv_table1"]["rows"]), 3)
     h["summary"] = s
     return h
 

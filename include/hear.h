@@ -53,6 +53,8 @@ typedef int hear_status;
 #define HEAR_E_STATE (-7)       /* handle from another context / wrong kind           */
 #define HEAR_E_FORMAT (-8)      /* malformed import buffer                            */
 #define HEAR_E_UNSUPPORTED (-9) /* parameter outside the supported range              */
+#define HEAR_E_TIMEOUT (-10)    /* a bounded wait ran out before the work finished    */
+#define HEAR_E_BUSY (-11)       /* admission refused: queue or staging buffers full   */
 
 typedef struct hear_context hear_context;
 typedef struct hear_secret_key hear_secret_key;
@@ -263,29 +265,46 @@ hear_status hear_evaluate_host(const hear_model *m, const hear_eval_keys *evk, c
  * while others run overlap on the device.  Each batch replays captured CUDA graphs of the
  * whole network (the first batch of each size captures them).  Results are the result
  * ciphertexts in the coefficient domain, uint64[n_ct][2][level_out+1][N]; they are
- * bit-identical to evaluating the request alone. */
+ * bit-identical to evaluating the request alone.  Host copies: a request's words are
+ * copied once, at submit, into pinned staging buffers the server owns (staging_cts
+ * ciphertexts), from which the batch is uploaded; results come back into pinned result
+ * buffers and are copied once into the caller's array by poll / wait. */
 typedef struct hear_server hear_server;
 typedef struct hear_server_config {
     uint32_t max_batch;          /* ciphertexts per launch (>= 1)                         */
     uint32_t n_slots;            /* batches in flight, 1..8                               */
     uint64_t hbm_budget_bytes;   /* device bytes for the ciphertexts in flight            */
+    uint32_t staging_cts;        /* pinned staging buffers, in ciphertexts, for queued and
+                                    running requests (>= max_batch; 0 = 2 n_slots max_batch) */
+    uint32_t max_pending;        /* queued requests beyond which submit is refused (0 = any) */
 } hear_server_config;
 typedef struct hear_server_counters {
     uint64_t requests_done, ciphertexts_done, clips_done, batches, pending;
     uint64_t max_in_flight_ciphertexts, bytes_per_ciphertext;
     double p50_ms, p99_ms, mean_ms;   /* submit -> result ready, completed requests      */
+    uint64_t busy_refusals;           /* submits refused with HEAR_E_BUSY                 */
 } hear_server_counters;
 hear_status hear_server_create(const hear_model *m, const hear_eval_keys *evk, const hear_server_config *cfg,
                                hear_server **out);
 /* queue a request of n_ct ciphertexts (n_clips clips, for the statistics); the words are
- * copied before the call returns */
+ * copied into the server's pinned staging buffers before the call returns.  HEAR_E_BUSY
+ * (nothing queued) while the staging buffers cannot take n_ct more ciphertexts or
+ * max_pending requests are queued: retry after results have been read. */
 hear_status hear_server_submit(hear_server *s, const uint64_t *words, size_t n_ct, uint32_t n_clips, double scale,
                                uint64_t *request_id);
 /* *done = 1 and the result copied to out (cap words, *n written) once the request is
  * complete (the id is then released); *done = 0 while it is queued or running */
 hear_status hear_server_poll(hear_server *s, uint64_t request_id, uint64_t *out, size_t cap, size_t *n, int *done);
+/* block until the request is complete (result copied to out as by poll, the id released)
+ * or timeout_ms have passed: then HEAR_E_TIMEOUT, and the request stays queued or running
+ * (wait or poll again later).  A failed request returns its error. */
+hear_status hear_server_wait(hear_server *s, uint64_t request_id, uint32_t timeout_ms, uint64_t *out, size_t cap,
+                             size_t *n);
+/* paused != 0: admit no new batch (running batches finish; submits still queue) */
+hear_status hear_server_pause(hear_server *s, int paused);
 hear_status hear_server_stats(hear_server *s, hear_server_counters *stats);
-/* waits for the batches in flight, drops queued requests */
+/* waits for the batches in flight, drops queued requests; no other call on the server may
+ * be in progress */
 void hear_server_destroy(hear_server *s);
 
 /* ---- skeleton CNN (cloud) ----
@@ -541,6 +560,13 @@ hear_status hear_dbg_round_scalar(double w, uint64_t q, int64_t *out);
  * SM (iters multiply-adds per chain, iters in [1, 2^20]); the roofline denominator of the
  * integer-multiply-bound kernels */
 hear_status hear_dbg_imad_peak(hear_context *ctx, int kind, uint32_t iters, double *lane_ops_per_s);
+/* butterflies per second of the NTT's own arithmetic with no memory traffic: every thread
+ * keeps one radix-16 unit and its twiddles in registers and applies the unit's four stages
+ * iters times (iters in [1, 2^20]) -- the forward butterfly (inverse = 0: Shoup product,
+ * Harvey lazy add / subtract, the 2q correction for primes of 58 bits and more) or the
+ * inverse one -- on every SM, warp w on prime w mod (n_q + n_p).  The measured ceiling of
+ * the transforms' butterfly rate on the integer pipes (their roofline denominator). */
+hear_status hear_dbg_bfly_peak(hear_context *ctx, int inverse, uint32_t iters, double *butterflies_per_s);
 hear_status hear_dbg_poly_mul(hear_context *ctx, uint32_t prime, const uint64_t *a, const uint64_t *b,
                               uint64_t *out);
 /* forward+inverse NTT round trip of n_limb limbs (prime i % (n_q+n_p)) in place */

@@ -1088,6 +1088,11 @@ hear_status hear_dbg_imad_peak(hear_context *ctx, int kind, uint32_t iters, doub
     return guard(ctx, [&] { *lane_ops_per_s = imad_peak(ctx, kind, iters); });
 }
 
+hear_status hear_dbg_bfly_peak(hear_context *ctx, int inverse, uint32_t iters, double *butterflies_per_s) {
+    if (!ctx || !butterflies_per_s) return fail(HEAR_E_INVAL, "null argument");
+    return guard(ctx, [&] { *butterflies_per_s = bfly_peak(ctx, inverse == 0, iters); });
+}
+
 hear_status hear_simd_decrypt(hear_context *ctx, const hear_secret_key *sk, const hear_simd_batch *b,
                               size_t n_clips, double *out, size_t cap, size_t *n) {
     if (!ctx || !sk || !b) return fail(HEAR_E_INVAL, "null argument");

@@ -239,6 +239,9 @@ void ntt_forward_pro(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, 
 // layout of `map`, contiguous groups); src is left unchanged
 void ntt_inverse_from(const hear_context *ctx, const uint64_t *src, uint64_t src_gstride, uint64_t *data,
                       uint32_t n_limbs, LimbMap map, cudaStream_t s);
+// butterflies per second of the transforms' register-resident arithmetic (forward or
+// inverse) over the context's prime mix, iters rounds of four radix-16 stages per thread
+double bfly_peak(const hear_context *ctx, bool fwd, uint32_t iters);
 // fill ctx->ntt_choice by timing the launch variants (ms_out: [2][kNttBuckets][3] or null)
 // ms_out: [2][kNttBuckets][kNttVariants] or null
 void ntt_tune(hear_context *ctx, uint32_t max_limbs, int iters, float *ms_out);

@@ -569,6 +569,98 @@ void ntt_inverse_from(const hear_context *ctx, const uint64_t *src, uint64_t src
     HEAR_CHECK_CUDA(cudaGetLastError());
 }
 
+// ------------------------------------------------------------------ butterfly throughput
+// The arithmetic of the transforms without their memory traffic: every thread keeps a
+// radix-16 unit (16 residues) and its 16 twiddle pairs in registers and applies the unit's
+// four stages again and again -- the forward butterfly (Shoup product by the twiddle,
+// Harvey lazy add / subtract, the 2q correction for primes at or above the no-correction
+// bound) or the inverse one, exactly as stage_group does.  Warp w uses prime w mod
+// (n_q + n_p), i.e. the prime mix of a transform over all limbs.  What the loop reaches is
+// the measured ceiling of the transforms' butterfly rate on the integer pipes.
+template <bool FWD>
+__global__ void __launch_bounds__(256) k_bfly_peak(const DevPrime *primes, uint32_t n_primes, const uint64_t *tw,
+                                                   const uint64_t *tws, uint32_t n, uint64_t small_below,
+                                                   uint32_t iters, uint64_t *out) {
+    pdl_enter();
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const uint32_t pi = warp % n_primes;
+    const uint64_t q = primes[pi].q, two_q = 2 * q;
+    uint64_t w[16], wsh[16], x[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        w[i] = __ldg(tw + (size_t)pi * n + 1 + i);
+        wsh[i] = __ldg(tws + (size_t)pi * n + 1 + i);
+        x[i] = (threadIdx.x * 16u + i) % q;
+    }
+    const bool red = q >= small_below;
+    for (uint32_t it = 0; it < iters; it++) {
+#pragma unroll
+        for (int st = 0; st < 4; st++) {
+            const int half = FWD ? (8 >> st) : (1 << st);
+#pragma unroll
+            for (int p = 0; p < 8; p++) {
+                const int e = FWD ? ((p / half) * 2 * half + (p % half)) : (((p >> st) << (st + 1)) | (p & (half - 1)));
+                const int m = FWD ? ((1 << st) + (e >> (4 - st))) : ((8 >> st) + (p >> st));
+                uint64_t X = x[e], Y = x[e + half];
+                if (FWD) {
+                    if (red) X = X >= two_q ? X - two_q : X;
+                    const uint64_t T = shoup_lazy(Y, w[m & 15], wsh[m & 15], q);
+                    x[e] = X + T;
+                    x[e + half] = X - T + two_q;
+                } else if (red) {
+                    const uint64_t S = X + Y;
+                    x[e] = S >= two_q ? S - two_q : S;
+                    x[e + half] = shoup_lazy(X - Y + two_q, w[m & 15], wsh[m & 15], q);
+                } else {
+                    x[e] = X + Y;
+                    x[e + half] = shoup_lazy(X - Y + two_q, w[m & 15], wsh[m & 15], q);
+                }
+            }
+        }
+    }
+    uint64_t acc = 0;
+#pragma unroll
+    for (int i = 0; i < 16; i++) acc ^= x[i];
+    out[(uint64_t)blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
+double bfly_peak(const hear_context *ctx, bool fwd, uint32_t iters) {
+    HEAR_REQUIRE(iters >= 1 && iters <= (1u << 20), HEAR_E_INVAL, "iters must be in [1, 2^20]");
+    int sms = 0;
+    HEAR_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    const uint32_t threads = 256, blocks = (uint32_t)sms * 4;
+    cudaStream_t st = ctx->stream;
+    DevBuf out((size_t)blocks * threads * 8, st);
+    const size_t plane = (size_t)ctx->nqp() * ctx->n;
+    const uint64_t *base = ctx->d_tw.u64();
+    const uint64_t *tw = base + (fwd ? 0 : 2 * plane), *tws = base + (fwd ? plane : 3 * plane);
+    const uint64_t small_below = fwd ? (1ull << 58) : (1ull << (63 - ctx->log_n));
+    auto run = [&](uint32_t it) {
+        if (fwd)
+            launch(k_bfly_peak<true>, blocks, threads, 0, st, ctx->dev_primes(), ctx->nqp(), tw, tws, ctx->n,
+                   small_below, it, out.u64());
+        else
+            launch(k_bfly_peak<false>, blocks, threads, 0, st, ctx->dev_primes(), ctx->nqp(), tw, tws, ctx->n,
+                   small_below, it, out.u64());
+    };
+    run(iters);   // warm-up
+    cudaEvent_t e0, e1;
+    HEAR_CHECK_CUDA(cudaEventCreate(&e0));
+    HEAR_CHECK_CUDA(cudaEventCreate(&e1));
+    float ms = 0;
+    cudaError_t e = cudaEventRecord(e0, st);
+    if (e == cudaSuccess) {
+        run(iters);
+        e = cudaEventRecord(e1, st);
+    }
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    HEAR_CHECK_CUDA(e);
+    return (double)blocks * threads * 32.0 * iters / (ms / 1e3);
+}
+
 constexpr float kFusedMargin = 1.15f;
 
 // Time every launch variant for launches of 1, 2, 4, .. max_limbs limbs (both directions)

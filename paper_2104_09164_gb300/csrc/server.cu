@@ -1,12 +1,17 @@
 // server.cu -- continuous-batching server for encrypted inference requests.
 //
 // Requests (ciphertexts of the end-user, coefficient domain, host memory) arrive at any
-// time.  A worker thread admits pending requests in arrival order while the ciphertexts in
-// flight fit the HBM budget, packs up to max_batch ciphertexts into one batch and runs it on
-// a free slot: each slot owns a CUDA stream, pinned staging buffers and device buffers, so
-// up to n_slots batches overlap on the device (copies of one batch overlap the evaluation of
-// another).  A batch is split into power-of-two sub-batches, each the replay of a captured
-// CUDA graph of the whole network.  The evaluation keys and the encoded model stay resident.
+// time.  hear_server_submit copies them once, straight into pinned staging buffers that
+// the server owns (checking every residue on the way), so the batch upload reads pinned
+// memory; a full staging arena or queue refuses the request with HEAR_E_BUSY.  A worker
+// thread admits pending requests in arrival order while the ciphertexts in flight fit the
+// HBM budget, packs up to max_batch ciphertexts into one batch and runs it on a free slot:
+// each slot owns a CUDA stream and device buffers, so up to n_slots batches overlap on the
+// device (copies of one batch overlap the evaluation of another).  A batch is split into
+// power-of-two sub-batches, each the replay of a captured CUDA graph of the whole network.
+// Results are copied by the device into pinned result buffers, and from there once into
+// the caller's array by hear_server_poll / hear_server_wait.  The evaluation keys and the
+// encoded model stay resident.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -26,11 +31,19 @@ using Clock = std::chrono::steady_clock;
 
 namespace {
 
+// pinned host buffers of `words` words each, handed out by index
+struct Arena {
+    uint64_t *base = nullptr;
+    uint64_t words = 0;
+    std::vector<uint32_t> free;
+    uint64_t *at(uint32_t i) const { return base + (uint64_t)i * words; }
+};
+
 struct Request {
     uint64_t id = 0;
     uint32_t n_ct = 0, n_clips = 0;
     double scale = 0;
-    std::vector<uint64_t> in, out;
+    std::vector<uint32_t> in_bufs, out_bufs;   // staging buffers (one per ciphertext)
     Clock::time_point t_submit, t_done;
     int state = 0;                    // 0 pending, 1 running, 2 done, 3 failed
     hear_status status = HEAR_OK;
@@ -40,7 +53,6 @@ struct Slot {
     cudaStream_t st = nullptr;
     cudaEvent_t done = nullptr;
     DevBuf x, y;                      // device batch in (coefficient domain -> NTT), out
-    uint64_t *h_in = nullptr, *h_out = nullptr;   // pinned staging
     std::vector<std::shared_ptr<Request>> reqs;
     uint32_t n_ct = 0;
     bool busy = false;
@@ -56,15 +68,16 @@ struct hear_server {
     uint64_t in_words = 0, out_words = 0;  // per ciphertext
     uint64_t ct_bytes = 0;                  // device bytes charged per in-flight ciphertext
     std::mutex mu;
-    std::condition_variable cv;
+    std::condition_variable cv;            // worker: new work or a finished slot
+    std::condition_variable cv_done;       // waiters: a request finished or failed
     std::deque<std::shared_ptr<Request>> pending;
     std::map<uint64_t, std::shared_ptr<Request>> reqs;
     std::vector<Slot> slots;
+    Arena in_arena, out_arena;
     uint64_t next_id = 1, in_flight_cts = 0, max_in_flight_cts = 0;
-    uint64_t done_reqs = 0, done_cts = 0, done_clips = 0, batches = 0;
+    uint64_t done_reqs = 0, done_cts = 0, done_clips = 0, batches = 0, busy_refusals = 0;
     std::vector<double> lat_ms;
-    Clock::time_point t0;
-    bool t0_set = false, stop = false;
+    bool stop = false, paused = false;
     hear_status fault = HEAR_OK;
     std::string fault_msg;
     std::thread worker;
@@ -75,7 +88,6 @@ namespace {
 // evaluate the n_ct ciphertexts of slot s (already in s.x, NTT domain) into s.y
 void run_batch(hear_server *S, Slot &s, uint32_t slot_index) {
     const hear_model *m = S->m;
-    hear_context *c = m->ctx;
     const uint64_t ctw_in = S->in_words, ctw_out = S->out_words;
     uint32_t done = 0;
     for (uint32_t b = 1u << 31; b; b >>= 1) {
@@ -96,38 +108,43 @@ void run_batch(hear_server *S, Slot &s, uint32_t slot_index) {
     }
 }
 
+// upload from the requests' pinned staging buffers, evaluate, download into their pinned
+// result buffers, all on the slot's stream
 void launch(hear_server *S, Slot &s, uint32_t slot_index) {
     hear_context *c = S->m->ctx;
     uint64_t off = 0;
-    for (auto &r : s.reqs) {
-        std::memcpy(s.h_in + off, r->in.data(), r->in.size() * 8);
-        off += r->in.size();
-    }
-    HEAR_CHECK_CUDA(cudaMemcpyAsync(s.x.p, s.h_in, off * 8, cudaMemcpyHostToDevice, s.st));
+    for (auto &r : s.reqs)
+        for (uint32_t b : r->in_bufs) {
+            HEAR_CHECK_CUDA(cudaMemcpyAsync(s.x.u64() + off, S->in_arena.at(b), S->in_words * 8,
+                                            cudaMemcpyHostToDevice, s.st));
+            off += S->in_words;
+        }
     ntt_forward(c, s.x.u64(), s.n_ct * 2 * (S->lin + 1), map_q(S->lin, c->n_q), s.st);
     run_batch(S, s, slot_index);
     ntt_inverse(c, s.y.u64(), s.n_ct * 2 * (S->lout + 1), map_q(S->lout, c->n_q), s.st);
-    HEAR_CHECK_CUDA(cudaMemcpyAsync(s.h_out, s.y.p, s.n_ct * S->out_words * 8, cudaMemcpyDeviceToHost, s.st));
+    off = 0;
+    for (auto &r : s.reqs)
+        for (uint32_t b : r->out_bufs) {
+            HEAR_CHECK_CUDA(cudaMemcpyAsync(S->out_arena.at(b), s.y.u64() + off, S->out_words * 8,
+                                            cudaMemcpyDeviceToHost, s.st));
+            off += S->out_words;
+        }
     HEAR_CHECK_CUDA(cudaEventRecord(s.done, s.st));
     s.busy = true;
 }
 
-// copies the results of a finished slot out of its pinned buffer; called without S->mu
-// (the requests stay in state 1 and the slot busy until finish() runs)
-void collect(hear_server *S, Slot &s) {
-    uint64_t off = 0;
-    for (auto &r : s.reqs) {
-        r->out.assign(s.h_out + off, s.h_out + off + (uint64_t)r->n_ct * S->out_words);
-        off += (uint64_t)r->n_ct * S->out_words;
-    }
+void release(Arena &a, std::vector<uint32_t> &bufs) {
+    a.free.insert(a.free.end(), bufs.begin(), bufs.end());
+    bufs.clear();
 }
 
-// called with S->mu held, after collect()
+// called with S->mu held once the slot's event has completed
 void finish(hear_server *S, Slot &s) {
     const auto now = Clock::now();
     for (auto &r : s.reqs) {
         r->t_done = now;
         r->state = 2;
+        release(S->in_arena, r->in_bufs);    // the upload has completed
         S->done_reqs++;
         S->done_cts += r->n_ct;
         S->done_clips += r->n_clips;
@@ -140,6 +157,28 @@ void finish(hear_server *S, Slot &s) {
     S->batches++;
 }
 
+// every request in flight or queued fails with `code`; their buffers return to the arenas
+void fail_all(hear_server *S, hear_status code, const std::string &msg) {
+    S->fault = code;
+    S->fault_msg = msg;
+    auto drop = [&](const std::shared_ptr<Request> &r) {
+        r->state = 3;
+        r->status = code;
+        release(S->in_arena, r->in_bufs);
+        release(S->out_arena, r->out_bufs);
+    };
+    for (auto &s : S->slots) {
+        if (s.busy && s.st) cudaStreamSynchronize(s.st);   // no copy may still target the buffers
+        for (auto &r : s.reqs) drop(r);
+        s.reqs.clear();
+        s.n_ct = 0;
+        s.busy = false;
+    }
+    for (auto &r : S->pending) drop(r);
+    S->pending.clear();
+    S->in_flight_cts = 0;
+}
+
 void worker_loop(hear_server *S) {
     hear_context *c = S->m->ctx;
     cudaSetDevice(c->device);
@@ -147,25 +186,38 @@ void worker_loop(hear_server *S) {
     while (!S->stop) {
         bool progressed = false;
         try {
-            for (auto &s : S->slots)
-                if (s.busy && cudaEventQuery(s.done) == cudaSuccess) {
-                    lk.unlock();
-                    collect(S, s);
-                    lk.lock();
+            bool finished = false;
+            for (auto &s : S->slots) {
+                if (!s.busy) continue;
+                const cudaError_t q = cudaEventQuery(s.done);
+                if (q == cudaSuccess) {
                     finish(S, s);
-                    progressed = true;
+                    finished = true;
+                } else if (q != cudaErrorNotReady) {
+                    (void)cudaGetLastError();
+                    throw Error(HEAR_E_CUDA, std::string("batch failed: ") + cudaGetErrorString(q));
                 }
-            for (uint32_t si = 0; si < S->slots.size() && !S->pending.empty(); si++) {
+            }
+            if (finished) {
+                progressed = true;
+                S->cv_done.notify_all();
+            }
+            for (uint32_t si = 0; si < S->slots.size() && !S->pending.empty() && !S->paused; si++) {
                 Slot &s = S->slots[si];
                 if (s.busy) continue;
-                // admission in arrival order: batch size and HBM budget
+                // admission in arrival order: batch size, HBM budget, result buffers
                 while (!S->pending.empty()) {
                     auto &r = S->pending.front();
                     const uint64_t n = r->n_ct;
                     const bool fits_batch = s.n_ct + n <= S->cfg.max_batch;
                     const bool fits_hbm = (S->in_flight_cts + n) * S->ct_bytes <= S->cfg.hbm_budget_bytes;
                     const bool same_scale = s.reqs.empty() || s.reqs[0]->scale == r->scale;
-                    if (!fits_batch || !fits_hbm || !same_scale) break;
+                    const bool fits_out = S->out_arena.free.size() >= n;
+                    if (!fits_batch || !fits_hbm || !same_scale || !fits_out) break;
+                    for (uint64_t i = 0; i < n; i++) {
+                        r->out_bufs.push_back(S->out_arena.free.back());
+                        S->out_arena.free.pop_back();
+                    }
                     r->state = 1;
                     s.reqs.push_back(r);
                     s.n_ct += (uint32_t)n;
@@ -185,24 +237,10 @@ void worker_loop(hear_server *S) {
                 progressed = true;
             }
         } catch (const Error &e) {
-            S->fault = e.code;
-            S->fault_msg = e.what();
-            for (auto &s : S->slots) {
-                for (auto &r : s.reqs) {
-                    r->state = 3;
-                    r->status = e.code;
-                }
-                s.reqs.clear();
-                s.busy = false;
-            }
-            for (auto &r : S->pending) {
-                r->state = 3;
-                r->status = e.code;
-            }
-            S->pending.clear();
+            fail_all(S, e.code, e.what());
             if (e.code == HEAR_E_CUDA) c->poisoned = true;
+            S->cv_done.notify_all();
         }
-        S->cv.notify_all();
         if (!progressed) S->cv.wait_for(lk, std::chrono::microseconds(50));
     }
 }
@@ -210,6 +248,45 @@ void worker_loop(hear_server *S) {
 hear_status fail(hear_status code, const std::string &m) {
     set_last_error(m);
     return code;
+}
+
+// hands a finished request's result to the caller (lk held on entry and exit); a failed
+// request reports its error; both release the id
+hear_status deliver(hear_server *S, std::unique_lock<std::mutex> &lk,
+                    std::map<uint64_t, std::shared_ptr<Request>>::iterator it, uint64_t *out, size_t cap,
+                    size_t *n, int *done) {
+    std::shared_ptr<Request> r = it->second;
+    if (done) *done = 0;
+    if (r->state == 3) {
+        S->reqs.erase(it);
+        return fail(r->status, "request failed: " + S->fault_msg);
+    }
+    if (r->state != 2) return HEAR_OK;
+    const uint64_t words = (uint64_t)r->n_ct * S->out_words;
+    if (n) *n = words;
+    if (!out || cap < words) return fail(HEAR_E_INVAL, "output capacity too small");
+    S->reqs.erase(it);      // the result buffers now belong to this call alone
+    lk.unlock();
+    for (uint32_t i = 0; i < r->n_ct; i++)
+        std::memcpy(out + (uint64_t)i * S->out_words, S->out_arena.at(r->out_bufs[i]), S->out_words * 8);
+    lk.lock();
+    release(S->out_arena, r->out_bufs);
+    S->cv.notify_all();     // result buffers freed: the worker may admit more
+    if (done) *done = 1;
+    return HEAR_OK;
+}
+
+void free_server(hear_server *S) {
+    for (auto &s : S->slots) {
+        if (s.st) cudaStreamSynchronize(s.st);
+        if (s.done) cudaEventDestroy(s.done);
+        if (s.st) cudaStreamDestroy(s.st);
+        s.x.reset();
+        s.y.reset();
+    }
+    if (S->in_arena.base) cudaFreeHost(S->in_arena.base);
+    if (S->out_arena.base) cudaFreeHost(S->out_arena.base);
+    S->in_arena.base = S->out_arena.base = nullptr;
 }
 
 }  // namespace
@@ -222,12 +299,15 @@ hear_status hear_server_create(const hear_model *m, const hear_eval_keys *evk, c
     if (evk->ctx != m->ctx) return fail(HEAR_E_STATE, "keys from another context");
     if (cfg->max_batch < 1 || cfg->n_slots < 1 || cfg->n_slots > 8)
         return fail(HEAR_E_INVAL, "need max_batch >= 1 and 1 <= n_slots <= 8");
+    const uint32_t staging = cfg->staging_cts ? cfg->staging_cts : 2 * cfg->n_slots * cfg->max_batch;
+    if (staging < cfg->max_batch) return fail(HEAR_E_INVAL, "staging_cts must hold a request of max_batch ciphertexts");
     hear_context *c = m->ctx;
     if (c->poisoned) return fail(HEAR_E_CUDA, "context is poisoned by an earlier CUDA error");
     auto S = std::make_unique<hear_server>();
     S->m = m;
     S->evk = evk;
     S->cfg = *cfg;
+    S->cfg.staging_cts = staging;
     S->lin = m->layers.front().level_in;
     S->lout = m->layers.back().level_out;
     S->in_words = 2ull * (S->lin + 1) * c->n;
@@ -249,22 +329,20 @@ hear_status hear_server_create(const hear_model *m, const hear_eval_keys *evk, c
         }
         HEAR_CHECK_CUDA(cudaMemPoolGetAttribute(c->pool, cudaMemPoolAttrUsedMemHigh, &high));
         S->ct_bytes = (high > base ? high - base : 0) + 8 * (S->in_words + S->out_words) * 2;
+        for (Arena *a : {&S->in_arena, &S->out_arena}) {
+            a->words = a == &S->in_arena ? S->in_words : S->out_words;
+            HEAR_CHECK_CUDA(cudaHostAlloc((void **)&a->base, (size_t)staging * a->words * 8, cudaHostAllocDefault));
+            for (uint32_t i = staging; i-- > 0;) a->free.push_back(i);
+        }
         S->slots.resize(cfg->n_slots);
         for (auto &s : S->slots) {
             HEAR_CHECK_CUDA(cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking));
             HEAR_CHECK_CUDA(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
             s.x = DevBuf((size_t)cfg->max_batch * S->in_words * 8, nullptr);
             s.y = DevBuf((size_t)cfg->max_batch * S->out_words * 8, nullptr);
-            HEAR_CHECK_CUDA(cudaHostAlloc(&s.h_in, (size_t)cfg->max_batch * S->in_words * 8, cudaHostAllocDefault));
-            HEAR_CHECK_CUDA(cudaHostAlloc(&s.h_out, (size_t)cfg->max_batch * S->out_words * 8, cudaHostAllocDefault));
         }
     } catch (const Error &e) {
-        for (auto &s : S->slots) {
-            if (s.h_in) cudaFreeHost(s.h_in);
-            if (s.h_out) cudaFreeHost(s.h_out);
-            if (s.st) cudaStreamDestroy(s.st);
-            if (s.done) cudaEventDestroy(s.done);
-        }
+        free_server(S.get());
         return fail(e.code, e.what());
     }
     S->worker = std::thread(worker_loop, S.get());
@@ -282,22 +360,49 @@ hear_status hear_server_submit(hear_server *S, const uint64_t *words, size_t n_c
     r->n_ct = (uint32_t)n_ct;
     r->n_clips = n_clips;
     r->scale = scale;
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        if (S->fault != HEAR_OK) return fail(S->fault, "server stopped after an error: " + S->fault_msg);
+        if (S->cfg.max_pending && S->pending.size() >= S->cfg.max_pending) {
+            S->busy_refusals++;
+            return fail(HEAR_E_BUSY, "request queue full (max_pending)");
+        }
+        if (S->in_arena.free.size() < n_ct) {
+            S->busy_refusals++;
+            return fail(HEAR_E_BUSY, "staging buffers full (staging_cts)");
+        }
+        for (size_t i = 0; i < n_ct; i++) {
+            r->in_bufs.push_back(S->in_arena.free.back());
+            S->in_arena.free.pop_back();
+        }
+    }
+    // one copy into the reserved pinned buffers, every residue checked against its prime
     const hear_context *c = S->m->ctx;
-    r->in.assign(words, words + n_ct * S->in_words);
-    for (uint64_t i = 0; i < n_ct * 2 * (S->lin + 1); i++) {
-        const uint64_t q = c->primes[i % (S->lin + 1)];
-        const uint64_t *w = r->in.data() + i * c->n;
-        for (uint32_t k = 0; k < c->n; k++)
-            if (w[k] >= q) return fail(HEAR_E_FORMAT, "residue not reduced");
+    const uint32_t L1 = S->lin + 1;
+    bool bad = false;
+    for (size_t i = 0; i < n_ct && !bad; i++) {
+        uint64_t *dst = S->in_arena.at(r->in_bufs[i]);
+        const uint64_t *src = words + i * S->in_words;
+        for (uint32_t pl = 0; pl < 2 * L1 && !bad; pl++) {
+            const uint64_t q = c->primes[pl % L1];
+            const uint64_t *sp = src + (uint64_t)pl * c->n;
+            uint64_t *dp = dst + (uint64_t)pl * c->n;
+            uint64_t over = 0;
+            for (uint32_t k = 0; k < c->n; k++) {
+                const uint64_t v = sp[k];
+                over |= (uint64_t)(v >= q);
+                dp[k] = v;
+            }
+            bad = over != 0;
+        }
     }
     std::lock_guard<std::mutex> g(S->mu);
-    if (S->fault != HEAR_OK) return fail(S->fault, "server stopped after an error: " + S->fault_msg);
+    if (bad) {
+        release(S->in_arena, r->in_bufs);
+        return fail(HEAR_E_FORMAT, "residue not reduced");
+    }
     r->id = S->next_id++;
     r->t_submit = Clock::now();
-    if (!S->t0_set) {
-        S->t0 = r->t_submit;
-        S->t0_set = true;
-    }
     S->reqs[r->id] = r;
     S->pending.push_back(r);
     *request_id = r->id;
@@ -307,21 +412,35 @@ hear_status hear_server_submit(hear_server *S, const uint64_t *words, size_t n_c
 
 hear_status hear_server_poll(hear_server *S, uint64_t request_id, uint64_t *out, size_t cap, size_t *n, int *done) {
     if (!S || !done) return fail(HEAR_E_INVAL, "null argument");
-    std::lock_guard<std::mutex> g(S->mu);
+    std::unique_lock<std::mutex> lk(S->mu);
     auto it = S->reqs.find(request_id);
     if (it == S->reqs.end()) return fail(HEAR_E_INVAL, "unknown request id");
-    Request &r = *it->second;
-    *done = 0;
-    if (r.state == 3) {
-        S->reqs.erase(it);
-        return fail(r.status, "request failed: " + S->fault_msg);
-    }
-    if (r.state != 2) return HEAR_OK;
-    if (n) *n = r.out.size();
-    if (!out || cap < r.out.size()) return fail(HEAR_E_INVAL, "output capacity too small");
-    std::copy(r.out.begin(), r.out.end(), out);
-    *done = 1;
-    S->reqs.erase(it);
+    return deliver(S, lk, it, out, cap, n, done);
+}
+
+hear_status hear_server_wait(hear_server *S, uint64_t request_id, uint32_t timeout_ms, uint64_t *out, size_t cap,
+                             size_t *n) {
+    if (!S) return fail(HEAR_E_INVAL, "null argument");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(request_id);
+    if (it == S->reqs.end()) return fail(HEAR_E_INVAL, "unknown request id");
+    std::shared_ptr<Request> r = it->second;
+    const bool ready = S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms),
+                                           [&] { return r->state >= 2 || S->stop; });
+    if (!ready || r->state < 2)
+        return fail(HEAR_E_TIMEOUT, "request " + std::to_string(request_id) + " not finished within " +
+                                        std::to_string(timeout_ms) + " ms (it stays queued)");
+    it = S->reqs.find(request_id);
+    if (it == S->reqs.end()) return fail(HEAR_E_INVAL, "request was read by another call");
+    int done = 0;
+    return deliver(S, lk, it, out, cap, n, &done);
+}
+
+hear_status hear_server_pause(hear_server *S, int paused) {
+    if (!S) return fail(HEAR_E_INVAL, "null argument");
+    std::lock_guard<std::mutex> g(S->mu);
+    S->paused = paused != 0;
+    S->cv.notify_all();
     return HEAR_OK;
 }
 
@@ -336,6 +455,7 @@ hear_status hear_server_stats(hear_server *S, hear_server_counters *st) {
     st->pending = S->pending.size();
     st->max_in_flight_ciphertexts = S->max_in_flight_cts;
     st->bytes_per_ciphertext = S->ct_bytes;
+    st->busy_refusals = S->busy_refusals;
     if (!S->lat_ms.empty()) {
         std::vector<double> l = S->lat_ms;
         std::sort(l.begin(), l.end());
@@ -355,15 +475,10 @@ void hear_server_destroy(hear_server *S) {
         S->stop = true;
     }
     S->cv.notify_all();
+    S->cv_done.notify_all();
     if (S->worker.joinable()) S->worker.join();
     cudaSetDevice(S->m->ctx->device);
-    for (auto &s : S->slots) {
-        if (s.st) cudaStreamSynchronize(s.st);
-        if (s.h_in) cudaFreeHost(s.h_in);
-        if (s.h_out) cudaFreeHost(s.h_out);
-        if (s.done) cudaEventDestroy(s.done);
-        if (s.st) cudaStreamDestroy(s.st);
-    }
+    free_server(S);
     delete S;
 }
 

@@ -55,14 +55,16 @@ class hear_profile_entry(ctypes.Structure):
 
 
 class hear_server_config(ctypes.Structure):
-    _fields_ = [("max_batch", ctypes.c_uint32), ("n_slots", ctypes.c_uint32), ("hbm_budget_bytes", ctypes.c_uint64)]
+    _fields_ = [("max_batch", ctypes.c_uint32), ("n_slots", ctypes.c_uint32), ("hbm_budget_bytes", ctypes.c_uint64),
+                ("staging_cts", ctypes.c_uint32), ("max_pending", ctypes.c_uint32)]
 
 
 class hear_server_counters(ctypes.Structure):
     _fields_ = [("requests_done", ctypes.c_uint64), ("ciphertexts_done", ctypes.c_uint64),
                 ("clips_done", ctypes.c_uint64), ("batches", ctypes.c_uint64), ("pending", ctypes.c_uint64),
                 ("max_in_flight_ciphertexts", ctypes.c_uint64), ("bytes_per_ciphertext", ctypes.c_uint64),
-                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double)]
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("busy_refusals", ctypes.c_uint64)]
 
 
 class hear_cnn_input(ctypes.Structure):
@@ -87,6 +89,7 @@ class hear_cnn_op_info(ctypes.Structure):
 
 HEAR_OK, HEAR_E_INVAL, HEAR_E_NOMEM, HEAR_E_CUDA, HEAR_E_LEVEL = 0, -1, -2, -3, -4
 HEAR_E_SCALE, HEAR_E_NOKEY, HEAR_E_STATE, HEAR_E_FORMAT, HEAR_E_UNSUPPORTED = -5, -6, -7, -8, -9
+HEAR_E_TIMEOUT, HEAR_E_BUSY = -10, -11
 
 
 class HearError(RuntimeError):
@@ -166,6 +169,8 @@ def _load():
                                     ctypes.POINTER(ctypes.c_uint64)]),
         "hear_server_poll": (st, [_vp, ctypes.c_uint64, _u64p, ctypes.c_size_t, _szp, ctypes.POINTER(ctypes.c_int)]),
         "hear_server_stats": (st, [_vp, ctypes.POINTER(hear_server_counters)]),
+        "hear_server_wait": (st, [_vp, ctypes.c_uint64, ctypes.c_uint32, _u64p, ctypes.c_size_t, _szp]),
+        "hear_server_pause": (st, [_vp, ctypes.c_int]),
         "hear_server_destroy": (None, [_vp]),
         "hear_cnn_collapse": (st, [ctypes.POINTER(hear_cnn_input), ctypes.POINTER(hear_cnn_layer), ctypes.c_size_t,
                                    _dp, ctypes.c_size_t, _szp]),
@@ -206,6 +211,7 @@ def _load():
         "hear_ntt_get_table": (st, [_vp, ctypes.POINTER(ctypes.c_uint8)]),
         "hear_ntt_set_table": (st, [_vp, ctypes.POINTER(ctypes.c_uint8)]),
         "hear_dbg_imad_peak": (st, [_vp, ctypes.c_int, ctypes.c_uint32, _dp]),
+        "hear_dbg_bfly_peak": (st, [_vp, ctypes.c_int, ctypes.c_uint32, _dp]),
         "hear_dbg_round_scalar": (st, [ctypes.c_double, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int64)]),
         "hear_dbg_poly_mul": (st, [_vp, ctypes.c_uint32, _u64p, _u64p, _u64p]),
         "hear_dbg_ntt_roundtrip": (st, [_vp, _u64p, ctypes.c_size_t]),
@@ -743,8 +749,8 @@ def hear_cnn_evaluate(m, evk, op0, op1, cts, n_samples, stream=None):
 
 
 # ---------------------------------------------------------------- serving
-def hear_server_create(m, evk, max_batch=32, n_slots=2, hbm_budget_bytes=64 << 30):
-    cfg = hear_server_config(int(max_batch), int(n_slots), int(hbm_budget_bytes))
+def hear_server_create(m, evk, max_batch=32, n_slots=2, hbm_budget_bytes=64 << 30, staging_cts=0, max_pending=0):
+    cfg = hear_server_config(int(max_batch), int(n_slots), int(hbm_budget_bytes), int(staging_cts), int(max_pending))
     h = _vp()
     _check(lib.hear_server_create(m, evk, ctypes.byref(cfg), ctypes.byref(h)))
     return h.value
@@ -764,6 +770,18 @@ def hear_server_poll(s, request_id, out_words):
     done = ctypes.c_int(0)
     _check(lib.hear_server_poll(s, int(request_id), _p(out, _u64p), out.size, ctypes.byref(n), ctypes.byref(done)))
     return out[:n.value] if done.value else None
+
+
+def hear_server_wait(s, request_id, out_words, timeout_ms=1000):
+    """-> result array once done (blocks up to timeout_ms; HearError HEAR_E_TIMEOUT after)"""
+    out = np.empty(int(out_words), dtype=np.uint64)
+    n = ctypes.c_size_t(0)
+    _check(lib.hear_server_wait(s, int(request_id), int(timeout_ms), _p(out, _u64p), out.size, ctypes.byref(n)))
+    return out[:n.value]
+
+
+def hear_server_pause(s, paused=True):
+    _check(lib.hear_server_pause(s, 1 if paused else 0))
 
 
 def hear_server_stats(s):
@@ -822,6 +840,13 @@ def hear_dbg_imad_peak(ctx, kind=0, iters=4096):
     """lane operations per second of mad.wide.u32 (kind 0) or mad.lo.u32 (kind 1)"""
     v = ctypes.c_double()
     _check(lib.hear_dbg_imad_peak(ctx, int(kind), int(iters), ctypes.byref(v)))
+    return v.value
+
+
+def hear_dbg_bfly_peak(ctx, inverse=False, iters=2048):
+    """butterflies per second of the NTT arithmetic on register-resident radix-16 units"""
+    v = ctypes.c_double()
+    _check(lib.hear_dbg_bfly_peak(ctx, 1 if inverse else 0, int(iters), ctypes.byref(v)))
     return v.value
 
 
