@@ -30,6 +30,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "encrypted inferences/s & p50/p99 latency (N=2^14/2^15), batched vs plain on GB300"
+# the serving configuration: Poisson request rates, counted seconds and warm-up per rate
+C5_RATES = [10.0, 30.0, 100.0, 300.0, 1000.0, 2000.0]
+C5_SECONDS = 60.0
+C5_WARMUP = 5.0
 UNIT = "inferences/s"
 
 
@@ -44,7 +48,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clips", type=int, default=None, help="clips in the batch (default: the workload's)")
     ap.add_argument("--no-served", action="store_true")
-    ap.add_argument("--rates", default="500,2000,8000", help="request rates (req/s) of the served sweep")
+    ap.add_argument("--rates", default="100,1000,2000", help="request rates (req/s) of the served sweep")
+    ap.add_argument("--served-seconds", type=float, default=4.0, help="counted seconds per served rate")
+    ap.add_argument("--served-warmup", type=float, default=1.0, help="uncounted warm-up seconds per served rate")
+    ap.add_argument("--c5", action="store_true",
+                    help="the serving configuration in full: Poisson rates 10-2000 req/s, 60 s each after a 5 s "
+                         "warm-up, small network and the 70/30 mix (about 13 minutes)")
     ap.add_argument("--no-cnn", action="store_true", help="skip the CNN sections (Table 1 layers, 1D-CNN-64)")
     ap.add_argument("--no-min-level", action="store_true", help="skip the minimal-start-level variant")
     ap.add_argument("--mix-rates", default="100,300,1000", help="request rates (req/s) of the mixed sweep")
@@ -53,7 +62,7 @@ def parse():
     ap.add_argument("--no-fc-tune", action="store_true",
                     help="evaluate every network in the default FC form instead of the tuned one")
     ap.add_argument("--fc-form", default=None,
-                    help="pin the headline network's FC form as 'n1,hoist' (e.g. 32,1) instead of tuning it "
+                    help="pin the headline network's FC form as 'n1,hoist[,sums]' (e.g. 32,1,1) instead of tuning it "
                          "(profiles pin the form the timed run chose, as HEAR_NTT_TABLE pins the NTT table)")
     ap.add_argument("--sections-out", default="bench_out/sections.json",
                     help="file for the full result (every section); the last stdout line is the short headline")
@@ -282,20 +291,25 @@ def oracle_sample(w, steps_keys, min_seconds=10.0, max_evals=40):
 
 # ------------------------------------------------------------------ GPU arm
 class Setup:
-    def __init__(self, H, w, stream, device, level=None, fc_n1=None, hoist_moddown=False, tune=False):
+    def __init__(self, H, w, stream, device, level=None, fc_n1=None, hoist_moddown=False, tune=False,
+                 hoist_sums=False):
         """level: evaluate from ciphertexts dropped to this level (None = the top level);
-        fc_n1 / hoist_moddown: the FC evaluation form (hear_model_opts); tune: pick the form by
-        timing the candidates at this batch size first (autotune.tune_fc)"""
+        fc_n1 / hoist_moddown / hoist_sums: the FC evaluation form (hear_model_opts); tune: pick
+        the form by timing the candidates at this batch size first (autotune.tune_fc)"""
         self.H, self.w = H, w
         self.ctx = H.hear_context_create(w.log_n, w.q_bits, w.p_bits, w.log2_scale, w.sigma, device)
         report = None
         if tune:
+            # launch forms of the key-switch inner product / BSGS inner sums per batch bucket
+            H.hear_ks_tune(self.ctx, 32, 3)
+        self.ks_table = H.hear_ks_get_table(self.ctx)
+        if tune:
             from paper_2104_09164_gb300.autotune import tune_fc
-            (fc_n1, hoist_moddown), report = tune_fc(H, self.ctx, w.layers, w.clip_dim, w.n_ct, w.slots, level,
-                                                     stream=stream)
-        self.fc_form = {"fc_n1": fc_n1, "hoist_moddown": hoist_moddown, "tuned": report}
+            (fc_n1, hoist_moddown, hoist_sums), report = tune_fc(H, self.ctx, w.layers, w.clip_dim, w.n_ct,
+                                                                 w.slots, level, stream=stream)
+        self.fc_form = {"fc_n1": fc_n1, "hoist_moddown": hoist_moddown, "hoist_sums": hoist_sums, "tuned": report}
         self.model = H.hear_model_create(self.ctx, w.layers, w.clip_dim, level, fc_n1=fc_n1,
-                                         hoist_moddown=hoist_moddown)
+                                         hoist_moddown=hoist_moddown, hoist_sums=hoist_sums)
         self.steps = H.hear_model_rotations(self.model)
         self.sk, self.pk, self.evk = H.hear_keygen(self.ctx, 301, self.steps)
         self.cts = [H.hear_encrypt_clips(self.ctx, self.pk, w.ct_clips(i), 401, i, stream) for i in range(w.n_ct)]
@@ -384,37 +398,61 @@ def run_e2e(S, steps, warmup, torch, stream):
 
 
 class Served:
-    """one continuous-batching server over a Setup, with every batch-size graph captured"""
+    """one continuous-batching server over a Setup, with every batch-size graph captured;
+    requests cycle through `n_distinct` different encrypted clips (distinct ciphertexts)"""
 
-    def __init__(self, H, S, max_batch, n_slots, budget):
+    def __init__(self, H, S, max_batch, n_slots, budget, n_distinct=8, stream=None):
         self.H, self.S = H, S
         w = S.w
         self.k = min(w.clips_per_ct, w.slots // w.clip_dim)
-        self.words1 = H.hear_ciphertext_export(S.cts[0]).reshape(-1)
         self.scale = 2.0 ** w.log2_scale
+        rng = np.random.default_rng(611)
+        self.words = []
+        for i in range(n_distinct):
+            x = np.clip(rng.normal(0.0, 1.0, (self.k, w.clip_dim)), -1.0, 1.0)
+            ct = H.hear_encrypt_clips(S.ctx, S.pk, x, 901, i, stream)
+            self.words.append(H.hear_ciphertext_export(ct).reshape(-1))
+            H.hear_ciphertext_destroy(ct)
         self.bufs = {}
-        self.out_words = H.hear_evaluate_host(S.model, S.evk, self.words1, 1, self.scale)[0].size
+        self.next = 0
+        self.out_words = H.hear_evaluate_host(S.model, S.evk, self.words[0], 1, self.scale)[0].size
         self.srv = H.hear_server_create(S.model, S.evk, max_batch=max_batch, n_slots=n_slots,
                                         hbm_budget_bytes=budget)
+        # capture the graph of every power-of-two batch size on every slot first
         ids = []
         for rep in range(2 * n_slots):
             b = max_batch
             while b >= 1:
-                ids.append((H.hear_server_submit(self.srv, np.tile(self.words1, b), b, b * self.k, self.scale), b))
+                ids.append((H.hear_server_submit(self.srv, self.request(b), b, b * self.k, self.scale), b))
                 b //= 2
-        done = set()
-        while len(done) < len(ids):
-            for rid, b in ids:
-                if rid not in done and H.hear_server_poll(self.srv, rid, b * self.out_words) is not None:
-                    done.add(rid)
-            time.sleep(0.0005)
+                if len(ids) % 4 == 0:
+                    self.drain_all(ids)
+                    ids = []
+        self.drain_all(ids)
+
+    def request(self, n_ct):
+        """words of a request of n_ct ciphertexts: consecutive distinct ciphertexts, the
+        start rotating from request to request (buffers built once per (size, start))"""
+        key = (n_ct, self.next)
+        self.next = (self.next + 1) % len(self.words)
+        buf = self.bufs.get(key)
+        if buf is None:
+            buf = self.bufs[key] = np.concatenate([self.words[(key[1] + i) % len(self.words)] for i in range(n_ct)])
+        return buf
+
+    def drain_all(self, ids):
+        for rid, b in ids:
+            self.H.hear_server_wait(self.srv, rid, b * self.out_words, timeout_ms=600000)
 
     def submit(self, n_clips):
+        """-> (request id or None if the server refused it as busy, n_ct)"""
         n_ct = (n_clips + self.k - 1) // self.k
-        buf = self.bufs.get(n_ct)
-        if buf is None:   # request buffers are built once per size (the server copies them)
-            buf = self.bufs[n_ct] = np.tile(self.words1, n_ct)
-        return self.H.hear_server_submit(self.srv, buf, n_ct, n_clips, self.scale), n_ct
+        try:
+            return self.H.hear_server_submit(self.srv, self.request(n_ct), n_ct, n_clips, self.scale), n_ct
+        except self.H.HearError as e:
+            if e.code == self.H.HEAR_E_BUSY:
+                return None, n_ct
+            raise
 
     def poll(self, rid, n_ct):
         return self.H.hear_server_poll(self.srv, rid, n_ct * self.out_words) is not None
@@ -423,77 +461,88 @@ class Served:
         self.H.hear_server_destroy(self.srv)
 
 
-def poisson_sweep(servers, mix, rates, seconds, seed):
-    """Poisson requests of 1-8 clips (uniform) at each rate; each request goes to server i
-    with probability mix[i]; per-server and total throughput, client-side p50/p99 latency
-    (submit -> result read back)."""
-    H = servers[0].H
+def poisson_sweep(servers, mix, rates, seconds, seed, warmup=1.0):
+    """Poisson requests of 1-8 clips (uniform) at each rate for warmup + seconds; each
+    request goes to server i with probability mix[i].  Requests submitted during the first
+    `warmup` seconds are served but not counted.  Per rate: offered and served inferences/s
+    (clips of the counted requests over the time from the end of the warm-up to the last
+    counted result), client-side p50/p99 latency (submit -> result read back), and the
+    requests the server refused as busy (load shedding under overload)."""
     rng = np.random.default_rng(seed)
     out = []
     for lam in rates:
-        base = [H.hear_server_stats(sv.srv) for sv in servers]
         t0 = time.perf_counter()
+        t_count = t0 + warmup
         t_next = t0
         pend = [{} for _ in servers]     # per server, in submission order
         lat = [[] for _ in servers]
-        clips = 0
+        clips = [0 for _ in servers]
+        refused = [0 for _ in servers]
+        offered = 0
+        t_last = t_count
 
         def drain(window=32):
+            nonlocal t_last
             # requests finish roughly in submission order: poll the oldest `window` per server
             for si, q in enumerate(pend):
                 for rid in list(q)[:window]:
-                    n_ct, ts = q[rid]
+                    n_ct, n_clips, ts = q[rid]
                     if servers[si].poll(rid, n_ct):
-                        lat[si].append((time.perf_counter() - ts) * 1e3)
+                        now = time.perf_counter()
+                        if ts >= t_count:
+                            lat[si].append((now - ts) * 1e3)
+                            clips[si] += n_clips
+                            t_last = max(t_last, now)
                         del q[rid]
         while True:
             now = time.perf_counter()
-            if now - t0 >= seconds:
+            if now - t0 >= warmup + seconds:
                 break
             while t_next <= now:
                 n_clips = int(rng.integers(1, 9))
                 si = int(rng.choice(len(servers), p=mix))
+                ts = time.perf_counter()
                 rid, n_ct = servers[si].submit(n_clips)
-                pend[si][rid] = (n_ct, time.perf_counter())
-                clips += n_clips
+                if ts >= t_count:
+                    offered += n_clips
+                if rid is None:
+                    refused[si] += ts >= t_count
+                else:
+                    pend[si][rid] = (n_ct, n_clips, ts)
                 t_next += rng.exponential(1.0 / lam)
             drain()
             time.sleep(0.0002)
         while any(pend):
             drain()
             time.sleep(0.0002)
-        el = time.perf_counter() - t0
-        row = {"rate_req_s": lam, "offered_inferences_s": clips / seconds, "inferences_s": 0.0, "per_net": []}
+        span = max(t_last - t_count, 1e-9)
+        row = {"rate_req_s": lam, "seconds": seconds, "warmup_s": warmup, "offered_inferences_s": offered / seconds,
+               "inferences_s": sum(clips) / span, "per_net": []}
         for si, sv in enumerate(servers):
-            st = H.hear_server_stats(sv.srv)
             l = sorted(lat[si])
-            v = (st["clips_done"] - base[si]["clips_done"]) / el
-            row["inferences_s"] += v
-            row["per_net"].append({"net": sv.S.w.name, "inferences_s": v,
-                                   "requests": st["requests_done"] - base[si]["requests_done"],
-                                   "batches": st["batches"] - base[si]["batches"],
-                                   "max_in_flight_ciphertexts": st["max_in_flight_ciphertexts"],
+            row["per_net"].append({"net": sv.S.w.name, "inferences_s": clips[si] / span, "requests": len(l),
+                                   "refused_busy": refused[si],
                                    "p50_ms": l[len(l) // 2] if l else None,
                                    "p99_ms": l[min(len(l) - 1, int(0.99 * len(l)))] if l else None})
         if len(servers) == 1:
-            row.update({k: row["per_net"][0][k] for k in ("requests", "batches", "p50_ms", "p99_ms")})
+            row.update({k: row["per_net"][0][k] for k in ("requests", "refused_busy", "p50_ms", "p99_ms")})
             del row["per_net"]
         out.append(row)
     return out
 
 
-def run_served(H, S, rates, seconds=2.0, max_batch=32, n_slots=3, seed=601):
+def run_served(H, S, rates, seconds=4.0, warmup=1.0, max_batch=32, n_slots=3, seed=601, stream=None):
     """Poisson request stream against the continuous-batching server: each request carries
     1-8 clips (uniform) of the small network (4 clips per ciphertext -> 1 or 2 ciphertexts);
-    returns per-rate throughput and p50/p99 latency (submit -> result ready)."""
-    sv = Served(H, S, max_batch, n_slots, 96 << 30)
+    returns per-rate throughput and p50/p99 latency (submit -> result read back)."""
+    sv = Served(H, S, max_batch, n_slots, 96 << 30, stream=stream)
     try:
-        return poisson_sweep([sv], [1.0], rates, seconds, seed)
+        return poisson_sweep([sv], [1.0], rates, seconds, seed, warmup)
     finally:
         sv.close()
 
 
-def run_served_mix(H, stream, device, rates, seconds=2.0, seed=602, tune=True):
+def run_served_mix(H, stream, device, rates, seconds=4.0, warmup=1.0, seed=602, tune=True):
     """70% small / 30% large requests from one Poisson stream, each network served by its
     own continuous-batching server (own context, keys resident in HBM, HBM budget for the
     ciphertexts in flight); both servers' batches share the GPU."""
@@ -502,9 +551,9 @@ def run_served_mix(H, stream, device, rates, seconds=2.0, seed=602, tune=True):
     Sl = Setup(H, make_workload("large", 8), stream, device, tune=tune)
     servers = []
     try:
-        servers.append(Served(H, Ss, 32, 2, 48 << 30))
-        servers.append(Served(H, Sl, 8, 2, 96 << 30))
-        return poisson_sweep(servers, [0.7, 0.3], rates, seconds, seed)
+        servers.append(Served(H, Ss, 32, 2, 48 << 30, stream=stream))
+        servers.append(Served(H, Sl, 8, 2, 96 << 30, stream=stream))
+        return poisson_sweep(servers, [0.7, 0.3], rates, seconds, seed, warmup)
     finally:
         for sv in servers:
             sv.close()
@@ -808,8 +857,8 @@ def main_gpu(a):
     stream = torch.cuda.Stream(device=device)
     w = make_workload(a.workload, a.clips)
     if a.fc_form:
-        n1, dh = (int(x) for x in a.fc_form.split(","))
-        S = Setup(H, w, stream, device, fc_n1=n1, hoist_moddown=bool(dh))
+        f = [int(x) for x in a.fc_form.split(",")] + [0]
+        S = Setup(H, w, stream, device, fc_n1=f[0], hoist_moddown=bool(f[1]), hoist_sums=bool(f[2]))
     else:
         S = Setup(H, w, stream, device, tune=not a.no_fc_tune)
     total_ms, lat, launches, clocks = run_gpu(S, a.steps, a.warmup, dist, torch, stream, device)
@@ -847,22 +896,30 @@ def main_gpu(a):
         result["config"]["ntt_table"] = H.hear_ntt_get_table(S.ctx)
         # the FC evaluation form (baby steps, hoisted ModDown) and how it was chosen
         result["config"]["fc_form"] = S.fc_form
+        # the key-switch / inner-sum launch forms (pin with HEAR_KS_TABLE to profile them)
+        result["config"]["ks_table"] = S.ks_table
         # kernels captured with programmatic dependent launch so far (HEAR_PDL=0: none)
         result["config"]["pdl_launches_captured"] = H.hear_pdl_launch_count()
-    if result is not None and not a.no_served and a.workload == "small" and a.clips is None and dist.world == 1:
-        sweep = run_served(H, S, [float(x) for x in a.rates.split(",")])
-        result["served"] = {"workload": "small network, Poisson arrivals, 1-8 clips per request, "
-                                        "continuous batching (max 32 ciphertexts, 3 batches in flight)",
-                            "note": "latency = client submit -> result read back (host), per rate",
-                            "sweep": sweep}
-    if result is not None and not a.no_served and a.workload == "small" and a.clips is None and dist.world == 1:
-        result["served_mix"] = {
+    serving = result is not None and not a.no_served and a.workload == "small" and a.clips is None and dist.world == 1
+    if serving:
+        if a.c5:
+            rates, mix_rates, secs, warm = C5_RATES, C5_RATES, C5_SECONDS, C5_WARMUP
+        else:
+            rates = [float(x) for x in a.rates.split(",")]
+            mix_rates = [float(x) for x in a.mix_rates.split(",")]
+            secs, warm = a.served_seconds, a.served_warmup
+        key = "served_c5" if a.c5 else "served"
+        result[key] = {"workload": "small network, Poisson arrivals, 1-8 clips per request (8 distinct encrypted "
+                                   "clips cycled), continuous batching (max 32 ciphertexts, 3 batches in flight)",
+                       "note": "latency = client submit -> result read back (host); %g s per rate after a %g s "
+                               "warm-up that is not counted" % (secs, warm),
+                       "sweep": run_served(H, S, rates, secs, warm, stream=stream)}
+        result[key + "_mix" if a.c5 else "served_mix"] = {
             "workload": "70% small (N=2^14) / 30% large (N=2^15) requests of 1-8 clips from one Poisson "
                         "stream; one continuous-batching server per network (max batch 32 / 8 "
                         "ciphertexts, 2 batches in flight each), both on one GPU",
             "note": "latency = client submit -> result read back (host), per rate and network",
-            "sweep": run_served_mix(H, stream, device, [float(x) for x in a.mix_rates.split(",")],
-                                    tune=not a.no_fc_tune)}
+            "sweep": run_served_mix(H, stream, device, mix_rates, secs, warm, tune=not a.no_fc_tune)}
     if not a.no_batched and a.workload == "small" and a.clips is None:
         S.close()
         wl = make_workload("large")
@@ -875,7 +932,7 @@ def main_gpu(a):
             result["batched"] = {"workload": describe(wl), "value": replica_value(dist.world, bsteps, SL.clips_per_step, tms),
                                  "unit": UNIT, "ms_per_step": tms / bsteps, "steps": bsteps,
                                  "p50_ms": blat[len(blat) // 2], "gpu_launches": bl, "clocks": bclk,
-                                 "fc_form": SL.fc_form,
+                                 "fc_form": SL.fc_form, "ks_table": SL.ks_table,
                                  "stages_ms_per_step": {k: v[1] / bps for k, v in
                                                         sorted(bst.items(), key=lambda kv: -kv[1][1])[:8]},
                                  # algorithmic bytes / stage time (HBM roofline of each stage)
@@ -898,6 +955,7 @@ def main_gpu(a):
             tms, blat, bl, bclk = run_gpu(SB, bsteps, 2, dist, torch, stream, device)
             v = bsteps * SB.clips_per_step / (tms / 1e3)
             rows.append({"clips": n_clips, "ciphertexts": wb.n_ct, "fc_n1": SB.fc_form["fc_n1"],
+                         "ks_table": SB.ks_table,
                          "hoist_moddown": SB.fc_form["hoist_moddown"], "fc_tuned": SB.fc_form["tuned"] is not None,
                          "value": v, "unit": UNIT,
                          "ms_per_step": tms / bsteps, "p50_ms": blat[len(blat) // 2], "gpu_launches": bl,
@@ -915,6 +973,7 @@ def main_gpu(a):
             SM = Setup(H, wl, stream, device, level, tune=not a.no_fc_tune)
             tms, mlat, ml, mclk = run_gpu(SM, steps, 2, dist, torch, stream, device)
             ms[name] = {"workload": describe(wl), "start_level": level, "fc_form": SM.fc_form,
+                        "ks_table": SM.ks_table,
                         "value": steps * SM.clips_per_step / (tms / 1e3), "unit": UNIT,
                         "ms_per_step": tms / steps, "p50_ms": mlat[len(mlat) // 2],
                         "p99_ms": mlat[min(len(mlat) - 1, int(0.99 * len(mlat)))], "gpu_launches": ml,
@@ -982,8 +1041,8 @@ def headline(result, sections_path):
     cfg = result["config"]
     h["config"] = {"workload": cfg.get("workload_short", cfg["workload"]), "parallelism": cfg["parallelism"],
                    "l2": "no flush: per-step working set > 129 MB L2",
-                   "ntt_table": cfg.get("ntt_table"),
-                   "fc_form": {k: cfg["fc_form"].get(k) for k in ("fc_n1", "hoist_moddown")},
+                   "ntt_table": cfg.get("ntt_table"), "ks_table": cfg.get("ks_table"),
+                   "fc_form": {k: cfg["fc_form"].get(k) for k in ("fc_n1", "hoist_moddown", "hoist_sums")},
                    "sections": sections_path}
     e = result["e2e"]
     h["e2e"] = {"value": _r(e["value"], 6), "unit": e["unit"], "h2d_bytes_per_step": e["h2d_bytes_per_step"],
@@ -1012,11 +1071,13 @@ def headline(result, sections_path):
             top = max(rows, key=lambda r: r["inferences_s"])
             s[key] = {"rate_req_s": top["rate_req_s"], "value": _r(top["inferences_s"]),
                       "vs_plain": _r(top["inferences_s"] / result["value"], 3),
-                      "p50_ms": _r(top.get("p50_ms")), "p99_ms": _r(top.get("p99_ms"))}
-    if "served_mix" in result:
-        rows = result["served_mix"]["sweep"]
-        top = max(rows, key=lambda r: r["inferences_s"])
-        s["served_mix"] = {"rate_req_s": top["rate_req_s"], "value": _r(top["inferences_s"])}
+                      "p50_ms": _r(top.get("p50_ms")), "p99_ms": _r(top.get("p99_ms")),
+                      "refused": top.get("refused_busy")}
+    for key in ("served_mix", "served_c5_mix"):
+        if key in result:
+            rows = result[key]["sweep"]
+            top = max(rows, key=lambda r: r["inferences_s"])
+            s[key] = {"rate_req_s": top["rate_req_s"], "value": _r(top["inferences_s"])}
     if "ragged_mix" in result:
         s["ragged_mix"] = {"value": _r(result["ragged_mix"]["value"])}
     if "min_start_level" in result:

@@ -220,6 +220,12 @@ typedef struct hear_model_opts {
     uint32_t hoist_moddown;  /* 1: FC baby rotations kept over Q_l u P (baby 0 = P x), inner sums
                               * with plaintexts over Q_l u P, one ModDown per giant-step sum --
                               * n2 instead of n1 ModDowns per ciphertext (FC layers only) */
+    uint32_t hoist_sums;     /* 1: rotations whose results are summed stay over Q_l u P and the
+                              * sum is ModDowned once -- the giant-step rotations of an FC layer
+                              * together with inner sum 0 (one ModDown instead of n2 - 1), and
+                              * each rotate-and-sum round (one instead of radix - 1); the same
+                              * rotation keys, results differ from the unhoisted form only by
+                              * ModDown rounding */
 } hear_model_opts;
 hear_status hear_model_create_ex(hear_context *ctx, const hear_layer_desc *layers, size_t n_layers,
                                  uint32_t clip_dim, const hear_model_opts *opts, hear_model **out);
@@ -275,7 +281,8 @@ typedef struct hear_server_config {
     uint32_t n_slots;            /* batches in flight, 1..8                               */
     uint64_t hbm_budget_bytes;   /* device bytes for the ciphertexts in flight            */
     uint32_t staging_cts;        /* pinned staging buffers, in ciphertexts, for queued and
-                                    running requests (>= max_batch; 0 = 2 n_slots max_batch) */
+                                    running requests (>= max_batch; 0 = the larger of
+                                    4 n_slots max_batch and 64)                              */
     uint32_t max_pending;        /* queued requests beyond which submit is refused (0 = any) */
 } hear_server_config;
 typedef struct hear_server_counters {
@@ -546,6 +553,33 @@ hear_status hear_ntt_set_variant(hear_context *ctx, int variant);
  * instead of tuning. */
 hear_status hear_ntt_get_table(const hear_context *ctx, uint8_t *table);
 hear_status hear_ntt_set_table(hear_context *ctx, const uint8_t *table);
+
+/* ---- key-switch inner product / BSGS inner-sum launch forms (autotuner) ----
+ * Three tables of launch forms, each indexed by the log2 bucket (1, 2-3, 4-7, .., 128+) of
+ * the batch, all forms bit-identical:
+ *   [0] k_ks_inner by ciphertexts per job: 0 = registers capped for 3 CTAs per SM, every
+ *       ciphertext in one thread (keys read once per coefficient); 1 = capped for 2 CTAs
+ *       (no register spills); 2 / 3 = forms 0 / 1 with the ciphertexts in chunks of 4 over
+ *       the grid (more CTAs, keys read once per chunk);
+ *   [1] k_ks_inner_rj (one ciphertext, its digits shared by all jobs) by jobs: 0 = 4 jobs
+ *       per thread, 1 = 2, 2 = 8;
+ *   [2] k_lincomb by ciphertexts: 0 = 4 giant-step accumulators per pass over the babies,
+ *       1 = 8 (registers of 2 CTAs per SM).
+ * Every table starts at form 0.  hear_ks_tune times every form at the top level on
+ * synthetic operands (inner products over 8 jobs for 1, 2, 4, .. max_ct ciphertexts, at
+ * most 64; shared-digit products for 2 .. 16 jobs; inner sums with 8 x 8 baby / giant
+ * steps) as replayed CUDA graphs of `iters` launches and keeps the fastest per bucket
+ * (larger buckets take the largest tuned bucket's form).  It allocates up to a few GB of
+ * scratch for the large parameter sets and must not run concurrently with other work on
+ * the context.  choice_out (optional): uint8_t[3][8]; ms_out (optional): float[3][8][4]
+ * milliseconds per launch (0 = not timed).  hear_ks_set_variant forces form v in every
+ * table (taken modulo the table's form count; -1 = back to the tables), for tests and
+ * measurements.  The table can be read and pinned (uint8_t[3][8]); the environment
+ * variable HEAR_KS_TABLE (24 digits) pins it at context creation. */
+hear_status hear_ks_tune(hear_context *ctx, uint32_t max_ct, int iters, uint8_t *choice_out, float *ms_out);
+hear_status hear_ks_get_table(const hear_context *ctx, uint8_t *table);
+hear_status hear_ks_set_table(hear_context *ctx, const uint8_t *table);
+hear_status hear_ks_set_variant(hear_context *ctx, int variant);
 
 /* ---- debug: ring products through the NTT kernels (tests only) ---- */
 /* out = a * b in Z_q[X]/(X^N+1) for limb prime index `prime` (0..n_q+n_p-1), coefficient domain */

@@ -471,12 +471,15 @@ class Oracle:
         """pos-space vector of size M -> N/2 slots, slot p*k + c holds v[p]"""
         return np.repeat(np.asarray(v, dtype=np.float64), k)
 
-    def fc(self, ct: Ct, W, k, keys: Keys, pool=None, radix=ROTSUM_RADIX, n1=None, dh=False):
+    def fc(self, ct: Ct, W, k, keys: Keys, pool=None, radix=ROTSUM_RADIX, n1=None, dh=False, hs=False):
         """Encrypted FC layer, BSGS diagonal form with hoisted baby steps and one lazy
         rescale, followed by rotate-and-sum; output replicated with period d_out.
         n1: baby steps (default bsgs_split); dh: hoisted ModDown -- the baby rotations stay
         over Q_l u P (P-scaled identity as baby 0), the inner sums are formed there with
-        plaintexts over Q_l u P and each giant-step sum is ModDowned once."""
+        plaintexts over Q_l u P and each giant-step sum is ModDowned once.
+        hs: hoisted sums -- the giant rotations of the inner sums j >= 1 are kept over
+        Q_l u P as (P sigma(c0) + u0, u1), added to inner sum 0 over Q_l u P (P-scaled when it
+        is over Q_l) and ModDowned once, and so is every rotate-and-sum round (rotsum)."""
         d_out, d_in = W.shape
         M = (self.n // 2) // k
         assert d_in <= M and M % d_in == 0 and d_in % d_out == 0
@@ -504,6 +507,7 @@ class Oracle:
             pool = ThreadPoolExecutor(max_workers=os.cpu_count() or 4)
         pts = dict(zip(jobs, pool.map(lambda jb: pt_for(*jb), jobs)))
         acc = None
+        acc_ext = None
         for j in range(n2):
             inner = None
             for b in range(n1):
@@ -515,24 +519,41 @@ class Oracle:
                 else:
                     prod = self.mulplain(babies[b], pts[(j, b)], ql)
                     inner = prod if inner is None else self.add(inner, prod)
+            if hs and j == 0:
+                # the sum over Q_l u P starts with inner sum 0 (P-scaled when over Q_l)
+                acc_ext = inner if dh else self.scale_p_ext(inner)
+                continue
             if dh:
                 data = np.stack([self.moddown(level, inner[p]) for p in range(2)])
                 inner = Ct(data, level, ct.scale * ql)
+            if hs:
+                rot = self.rotate_hoisted_ext(inner, [j * n1 * k], keys)[0]
+                acc_ext = self.add_ext(level, acc_ext, rot)
+                continue
             if j > 0:
                 inner = self.rotate(inner, j * n1 * k, keys)
             acc = inner if acc is None else self.add(acc, inner)
+        if hs:
+            acc = Ct(np.stack([self.moddown(level, acc_ext[p]) for p in range(2)]), level, ct.scale * ql)
         out = self.rescale(acc)
-        return self.rotsum(out, d_out, d_in // d_out, k, keys, radix)
+        return self.rotsum(out, d_out, d_in // d_out, k, keys, radix, hs)
 
-    def rotsum(self, ct: Ct, step, count, k, keys: Keys, radix):
+    def rotsum(self, ct: Ct, step, count, k, keys: Keys, radix, hs=False):
         """sum of the count (a power of two) copies rho^(j*step*k)(ct), j < count, folded in
         rounds of up to radix - 1 hoisted rotations: out <- out + sum_j rho^(j*s*k)(out),
-        s <- s*r (radix 2 is the plain rotate-and-sum tree)"""
+        s <- s*r (radix 2 is the plain rotate-and-sum tree).  hs: each round is summed over
+        Q_l u P -- P out + sum_j (P sigma_j(c0) + u0_j, u1_j) -- and ModDowned once."""
         while count > 1:
             r = min(radix, count)
-            rots = self.rotate_hoisted(ct, [j * step * k for j in range(1, r)], keys)
-            for x in rots:
-                ct = self.add(ct, x)
+            steps = [j * step * k for j in range(1, r)]
+            if hs:
+                acc = self.scale_p_ext(ct)
+                for x in self.rotate_hoisted_ext(ct, steps, keys):
+                    acc = self.add_ext(ct.level, acc, x)
+                ct = Ct(np.stack([self.moddown(ct.level, acc[p]) for p in range(2)]), ct.level, ct.scale)
+            else:
+                for x in self.rotate_hoisted(ct, steps, keys):
+                    ct = self.add(ct, x)
             step *= r
             count //= r
         return ct
@@ -540,26 +561,26 @@ class Oracle:
     def square(self, ct: Ct, keys: Keys):
         return self.mul_relin_rescale(ct, ct, keys)
 
-    def fc_sq_fc(self, ct: Ct, W1, W2, k, keys: Keys, pool=None, radix=ROTSUM_RADIX):
+    def fc_sq_fc(self, ct: Ct, W1, W2, k, keys: Keys, pool=None, radix=ROTSUM_RADIX, hs=False):
         """Collapsed FC -> x^2 -> FC: out_c = sum_r W2[c,r] y_r^2 with y = W1 x, as the
         product of y and u = U x, U[(c, r), :] = W2[c, r] W1[r, :], both at one level,
         then rotate-and-sum over r.  Logit c lands at pos c * d1."""
         d1 = W1.shape[0]
         d2 = W2.shape[0]
         U = (W2[:, :, None] * W1[None, :, :]).reshape(d2 * d1, W1.shape[1])
-        y = self.fc(ct, W1, k, keys, pool, radix)
-        u = self.fc(ct, U, k, keys, pool, radix)
+        y = self.fc(ct, W1, k, keys, pool, radix, hs=hs)
+        u = self.fc(ct, U, k, keys, pool, radix, hs=hs)
         z = self.mul_relin_rescale(y, u, keys)
-        return self.rotsum(z, 1, d1, k, keys, radix)
+        return self.rotsum(z, 1, d1, k, keys, radix, hs)
 
-    def evaluate(self, layers, ct: Ct, k, keys: Keys, pool=None, radix=ROTSUM_RADIX, n1=None, dh=False):
+    def evaluate(self, layers, ct: Ct, k, keys: Keys, pool=None, radix=ROTSUM_RADIX, n1=None, dh=False, hs=False):
         for layer in layers:
             if layer[0] == "fc":
-                ct = self.fc(ct, layer[1], k, keys, pool, radix, n1, dh)
+                ct = self.fc(ct, layer[1], k, keys, pool, radix, n1, dh, hs)
             elif layer[0] == "square":
                 ct = self.square(ct, keys)
             elif layer[0] == "fc_sq_fc":
-                ct = self.fc_sq_fc(ct, layer[1], layer[2], k, keys, pool, radix)
+                ct = self.fc_sq_fc(ct, layer[1], layer[2], k, keys, pool, radix, hs)
             else:
                 raise ValueError(layer[0])
         return ct

@@ -137,33 +137,39 @@ def _name(s):
 
 # ---------------------------------------------------------------- FC evaluation form
 def fc_candidates(layers):
-    """(fc_n1, hoist_moddown) forms to try for a network of FC / x^2 layers: baby-step counts
-    d/2, d and 2d around d = the smallest power of two with d^2 >= D of the widest FC (D = its
-    output dimension; each layer clamps n1 to its own D), each with and without hoisted ModDown"""
+    """(fc_n1, hoist_moddown, hoist_sums) forms to try for a network of FC / x^2 layers:
+    baby-step counts d/2, d and 2d around d = the smallest power of two with d^2 >= D of the
+    widest FC (D = its output dimension; each layer clamps n1 to its own D), each with and
+    without hoisted ModDown of the babies and with and without hoisted sums"""
     D = max(layer[1].shape[0] for layer in layers if layer[0] == "fc")
     d = 1
     while d * d < D:
         d *= 2
     n1s = sorted({max(2, d // 2), d, min(2 * d, D)})
-    return [(n1, dh) for n1 in n1s for dh in (False, True)]
+    return [(n1, dh, hs) for n1 in n1s for dh in (False, True) for hs in (False, True)]
 
 
 def tune_fc(H, ctx, layers, clip_dim, n_ct, slots, level=None, steps=3, warmup=1, stream=None, seed=7):
-    """-> ((fc_n1, hoist_moddown), report): the fastest FC evaluation form (Methods,
+    """-> ((fc_n1, hoist_moddown, hoist_sums), report): the fastest FC evaluation form (Methods,
     "Algorithmic and cryptographic optimizations": the baby-step / giant-step split and where
     the ModDown of the hoisted rotations happens) for whole-network evaluations of n_ct
     ciphertexts, timed through the C ABI (CUDA-graph replay, CUDA events on `stream`) on random
-    inputs with throw-away keys.  Every form computes the same network; the oracle evaluates
+    inputs with throw-away keys (one key set per baby-step count: the forms of one count
+    need the same rotations).  Every form computes the same network; the oracle evaluates
     each one bit-exactly."""
     import torch
     st = stream if stream is not None else torch.cuda.Stream()
     rng = np.random.default_rng(seed)
     report = []
-    for n1, dh in fc_candidates(layers):
+    by_n1 = {}
+    for n1, dh, hs in fc_candidates(layers):
+        by_n1.setdefault(n1, []).append((dh, hs))
+    for n1, forms in by_n1.items():
         t0 = time.perf_counter()
-        m = H.hear_model_create(ctx, layers, clip_dim, level, fc_n1=n1, hoist_moddown=dh)
+        models = [H.hear_model_create(ctx, layers, clip_dim, level, fc_n1=n1, hoist_moddown=dh, hoist_sums=hs)
+                  for dh, hs in forms]
         try:
-            sk, pk, evk = H.hear_keygen(ctx, 9001, H.hear_model_rotations(m))
+            sk, pk, evk = H.hear_keygen(ctx, 9001, H.hear_model_rotations(models[0]))
             cts = []
             for i in range(n_ct):
                 c = H.hear_encrypt(ctx, pk, rng.uniform(-1.0, 1.0, slots), 2.0 ** 40, 9002, i, st)
@@ -172,25 +178,29 @@ def tune_fc(H, ctx, layers, clip_dim, n_ct, slots, level=None, steps=3, warmup=1
                     H.hear_ciphertext_destroy(c)
                     c = low
                 cts.append(c)
-            for _ in range(warmup):
-                for o in H.hear_evaluate(m, evk, cts, st):
-                    H.hear_ciphertext_destroy(o)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(st)
-            for _ in range(steps):
-                for o in H.hear_evaluate(m, evk, cts, st):
-                    H.hear_ciphertext_destroy(o)
-            e1.record(st)
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / steps
+            setup_s = time.perf_counter() - t0
+            for m, (dh, hs) in zip(models, forms):
+                t1 = time.perf_counter()
+                for _ in range(warmup):
+                    for o in H.hear_evaluate(m, evk, cts, st):
+                        H.hear_ciphertext_destroy(o)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                for _ in range(steps):
+                    for o in H.hear_evaluate(m, evk, cts, st):
+                        H.hear_ciphertext_destroy(o)
+                e1.record(st)
+                torch.cuda.synchronize()
+                report.append({"fc_n1": n1, "hoist_moddown": dh, "hoist_sums": hs, "ms": e0.elapsed_time(e1) / steps,
+                               "tune_s": time.perf_counter() - t1 + setup_s / len(forms)})
             for c in cts:
                 H.hear_ciphertext_destroy(c)
             H.hear_eval_keys_destroy(evk)
             H.hear_public_key_destroy(pk)
             H.hear_secret_key_destroy(sk)
         finally:
-            H.hear_model_destroy(m)
-        report.append({"fc_n1": n1, "hoist_moddown": dh, "ms": ms, "tune_s": time.perf_counter() - t0})
+            for m in models:
+                H.hear_model_destroy(m)
     best = min(report, key=lambda r: r["ms"])
-    return (best["fc_n1"], best["hoist_moddown"]), report
+    return (best["fc_n1"], best["hoist_moddown"], best["hoist_sums"]), report

@@ -112,6 +112,17 @@ hear_status hear_context_create(const hear_params_desc *params, int cuda_device,
         } else if (!(v && *v == '0')) {
             ntt_tune(c, 1024, 8, nullptr);
         }
+        // a pinned table of key-switch / inner-sum launch forms (24 digits), e.g. to profile
+        // the forms a tuned run used; every form computes the same residues
+        const char *kt = std::getenv("HEAR_KS_TABLE");
+        if (kt && *kt) {
+            HEAR_REQUIRE(std::strlen(kt) == (size_t)kKsTables * kKsBuckets, HEAR_E_INVAL, "HEAR_KS_TABLE needs 24 digits");
+            for (int i = 0; i < kKsTables * kKsBuckets; i++) {
+                HEAR_REQUIRE(kt[i] >= '0' && kt[i] < '0' + kKsVariants[i / kKsBuckets], HEAR_E_INVAL,
+                             "bad HEAR_KS_TABLE digit");
+                c->ks_choice[i / kKsBuckets][i % kKsBuckets] = (uint8_t)(kt[i] - '0');
+            }
+        }
     });
     if (s != HEAR_OK) {
         delete c;
@@ -449,8 +460,9 @@ hear_status hear_model_create_ex(hear_context *ctx, const hear_layer_desc *layer
     const uint32_t radix = opts && opts->rotsum_radix ? opts->rotsum_radix : kDefaultRotsumRadix;
     const uint32_t n1 = opts ? opts->fc_n1 : 0;
     const bool dh = opts && opts->hoist_moddown;
+    const bool hs = opts && opts->hoist_sums;
     if (n1 && (n1 & (n1 - 1))) return fail(HEAR_E_INVAL, "fc_n1 must be a power of two");
-    return guard(ctx, [&] { *out = model_create(ctx, layers, n_layers, clip_dim, level, radix, n1, dh); });
+    return guard(ctx, [&] { *out = model_create(ctx, layers, n_layers, clip_dim, level, radix, n1, dh, hs); });
 }
 
 hear_status hear_model_levels(const hear_model *m, uint32_t *level_in, uint32_t *level_out) {
@@ -733,6 +745,37 @@ hear_status hear_ntt_set_table(hear_context *ctx, const uint8_t *table) {
     for (int i = 0; i < 2 * kNttBuckets; i++)
         if (table[i] >= kNttVariants) return fail(HEAR_E_INVAL, "bad variant in table");
     std::memcpy(ctx->ntt_choice, table, sizeof(ctx->ntt_choice));
+    return HEAR_OK;
+}
+
+hear_status hear_ks_tune(hear_context *ctx, uint32_t max_ct, int iters, uint8_t *choice_out, float *ms_out) {
+    if (!ctx) return fail(HEAR_E_INVAL, "null context");
+    return guard(ctx, [&] {
+        if (ms_out) std::fill(ms_out, ms_out + kKsTables * kKsBuckets * 4, 0.0f);
+        ks_tune(ctx, max_ct, iters, ms_out);
+        if (choice_out) std::memcpy(choice_out, ctx->ks_choice, sizeof(ctx->ks_choice));
+    });
+}
+
+hear_status hear_ks_get_table(const hear_context *ctx, uint8_t *table) {
+    if (!ctx || !table) return fail(HEAR_E_INVAL, "null argument");
+    std::memcpy(table, ctx->ks_choice, sizeof(ctx->ks_choice));
+    return HEAR_OK;
+}
+
+hear_status hear_ks_set_table(hear_context *ctx, const uint8_t *table) {
+    if (!ctx || !table) return fail(HEAR_E_INVAL, "null argument");
+    for (int t = 0; t < kKsTables; t++)
+        for (int b = 0; b < kKsBuckets; b++)
+            if (table[t * kKsBuckets + b] >= kKsVariants[t]) return fail(HEAR_E_INVAL, "form out of range");
+    std::memcpy(ctx->ks_choice, table, sizeof(ctx->ks_choice));
+    return HEAR_OK;
+}
+
+hear_status hear_ks_set_variant(hear_context *ctx, int variant) {
+    if (!ctx) return fail(HEAR_E_INVAL, "null context");
+    if (variant < -1 || variant > 3) return fail(HEAR_E_INVAL, "variant must be -1 or 0..3");
+    ctx->ks_force = variant;
     return HEAR_OK;
 }
 

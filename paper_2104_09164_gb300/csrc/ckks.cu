@@ -273,6 +273,16 @@ void rotate_each(hear_context *c, uint32_t level, uint32_t R, uint32_t C, const 
     moddown(c, level, n_ct, acc.u64(), out, x, ctw, 1u, false, jobs.gal(), C, tmp.u64(), st);
 }
 
+void rotate_each_ext(hear_context *c, uint32_t level, uint32_t R, uint32_t C, const uint64_t *x,
+                     const std::vector<Rot> &rots, uint64_t *out_ext, const uint64_t *pmod, cudaStream_t st) {
+    const uint32_t n = c->n, L1 = level + 1, W = L1 + c->K, dnum = c->dnum(level), n_ct = R * C;
+    const uint64_t plane = (uint64_t)L1 * n, ctw = 2 * plane;
+    DevBuf ext((size_t)n_ct * dnum * W * n * 8, st), tmp((size_t)n_ct * plane * 8, st);
+    modup(c, level, n_ct, x + plane, ctw, ext.u64(), tmp.u64(), st);
+    JobTable jobs = make_jobs(c, rots, st);
+    ks_inner(c, level, R, C, ext.u64(), true, jobs.keys(), jobs.ginv(), out_ext, x + plane, ctw, st, pmod);
+}
+
 void mul_relin(hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *a, const uint64_t *b,
                const uint64_t *relin_key, uint64_t *out, cudaStream_t st) {
     const uint64_t plane = (uint64_t)(level + 1) * c->n;
@@ -400,10 +410,12 @@ const uint64_t *need_key(const hear_eval_keys *evk, uint32_t g) {
 }
 
 // rotate-and-sum in rounds: x <- x + sum_s rho^s(x) over the steps of each round, the
-// rotations of a round sharing one ModUp of x (hoisting)
+// rotations of a round sharing one ModUp of x (hoisting).  pmod (hoisted sums): each round
+// is summed over Q_l u P -- P x + sum_s (P sigma_s(c0) + u0_s, u1_s) -- and ModDowned once.
 void rotsum(hear_context *c, const hear_eval_keys *evk, uint32_t level, uint32_t n_ct, uint64_t *x,
-            const std::vector<std::vector<int32_t>> &rounds, cudaStream_t st) {
-    const uint64_t ctw = 2ull * (level + 1) * c->n, batch = (uint64_t)n_ct * ctw;
+            const std::vector<std::vector<int32_t>> &rounds, cudaStream_t st, const uint64_t *pmod = nullptr) {
+    const uint32_t L1 = level + 1, W = L1 + c->K;
+    const uint64_t ctw = 2ull * L1 * c->n, batch = (uint64_t)n_ct * ctw, batch_e = (uint64_t)n_ct * 2 * W * c->n;
     for (auto &round : rounds) {
         std::vector<Rot> rots;
         for (int32_t s : round) {
@@ -411,6 +423,13 @@ void rotsum(hear_context *c, const hear_eval_keys *evk, uint32_t level, uint32_t
             rots.push_back(Rot{need_key(evk, g), g});
         }
         const uint32_t R = (uint32_t)rots.size();
+        if (pmod) {
+            DevBuf r((size_t)R * batch_e * 8, st), acc((size_t)batch_e * 8, st), tmp((size_t)batch * 8, st);
+            rotate_hoisted_ext(c, level, n_ct, x, rots, r.u64(), pmod, st);
+            sum_ext(c, level, 2 * n_ct, r.u64(), batch_e, R, x, nullptr, acc.u64(), pmod, st);
+            moddown(c, level, n_ct, acc.u64(), x, nullptr, 0, 0u, false, nullptr, 1, tmp.u64(), st);
+            continue;
+        }
         DevBuf r((size_t)R * batch * 8, st);
         rotate_hoisted(c, level, n_ct, x, rots, r.u64(), st);
         sum_add_ct(c, level, 2 * n_ct, r.u64(), batch, R, x, x, st);
@@ -427,19 +446,31 @@ DevBuf eval_fc(const hear_model *m, const hear_model::Fc &fc, const hear_eval_ke
         uint32_t g = galois_of(c, (int64_t)b * k);
         rots.push_back(Rot{need_key(evk, g), g});
     }
+    // hoisted sums: the giant rotations stay over Q_l u P and are added to inner sum 0 there
+    // (ModDowned once with them); pmod = ([P]_{q_t}, Shoup) for t <= level
+    const uint64_t *pmod = m->hoist_sums ? m->pmod_all.u64() : nullptr;
+    const uint32_t W = L1 + c->K;
+    const uint64_t batch_e = (uint64_t)n_ct * 2 * W * n;
     DevBuf G((size_t)n2 * batch * 8, st);
+    DevBuf G0e;   // hoisted sums with hoisted ModDown: inner sum 0 over Q_l u P
     if (fc.dh) {
         // hoisted ModDown: the babies stay over Q_l u P (slot 0 = P x), the inner sums are
         // formed there with plaintexts over Q_l u P, and each giant-step sum is ModDowned
         // once (ModDown(P a + b) = a + ModDown(b))
-        const uint32_t W = L1 + c->K;
-        const uint64_t batch_e = (uint64_t)n_ct * 2 * W * n;
         DevBuf babies((size_t)n1 * batch_e * 8, st);
         scale_p_ext(c, level, 2 * n_ct, x, babies.u64(), fc.pmod.u64(), st);
         rotate_hoisted_ext(c, level, n_ct, x, rots, babies.u64() + batch_e, fc.pmod.u64(), st);
         DevBuf Ge((size_t)n2 * batch_e * 8, st), tmp((size_t)n2 * batch * 8, st);
         lincomb_ext(c, level, n_ct, n1, n2, babies.u64(), fc.pts.u64(), Ge.u64(), st);
-        moddown(c, level, n2 * n_ct, Ge.u64(), G.u64(), nullptr, 0, 0u, false, nullptr, 1, tmp.u64(), st);
+        if (pmod && n2 > 1) {
+            // inner sums j >= 1 back to Q_l (they are rotated next); inner sum 0 stays extended
+            moddown(c, level, (n2 - 1) * n_ct, Ge.u64() + batch_e, G.u64() + batch, nullptr, 0, 0u, false, nullptr, 1,
+                    tmp.u64(), st);
+            G0e = DevBuf((size_t)batch_e * 8, st);
+            HEAR_CHECK_CUDA(cudaMemcpyAsync(G0e.p, Ge.p, batch_e * 8, cudaMemcpyDeviceToDevice, st));
+        } else {
+            moddown(c, level, n2 * n_ct, Ge.u64(), G.u64(), nullptr, 0, 0u, false, nullptr, 1, tmp.u64(), st);
+        }
     } else {
         // baby steps rho^(b k)(x), b < n1, hoisted; slot 0 holds x itself so that the inner
         // sums read one contiguous [n1][n_ct] batch
@@ -456,21 +487,30 @@ DevBuf eval_fc(const hear_model *m, const hear_model::Fc &fc, const hear_eval_ke
             uint32_t g = galois_of(c, (int64_t)j * n1 * k);
             gr.push_back(Rot{need_key(evk, g), g});
         }
-        DevBuf R((size_t)(n2 - 1) * batch * 8, st);
-        rotate_each(c, level, n2 - 1, n_ct, G.u64() + batch, gr, R.u64(), st);
-        sum_add_ct(c, level, 2 * n_ct, R.u64(), batch, n2 - 1, G.u64(), G.u64(), st);
+        if (pmod) {
+            DevBuf Re((size_t)(n2 - 1) * batch_e * 8, st), acc((size_t)batch_e * 8, st), tmp((size_t)batch * 8, st);
+            rotate_each_ext(c, level, n2 - 1, n_ct, G.u64() + batch, gr, Re.u64(), pmod, st);
+            if (fc.dh) sum_ext(c, level, 2 * n_ct, Re.u64(), batch_e, n2 - 1, nullptr, G0e.u64(), acc.u64(), pmod, st);
+            else sum_ext(c, level, 2 * n_ct, Re.u64(), batch_e, n2 - 1, G.u64(), nullptr, acc.u64(), pmod, st);
+            moddown(c, level, n_ct, acc.u64(), G.u64(), nullptr, 0, 0u, false, nullptr, 1, tmp.u64(), st);
+        } else {
+            DevBuf R((size_t)(n2 - 1) * batch * 8, st);
+            rotate_each(c, level, n2 - 1, n_ct, G.u64() + batch, gr, R.u64(), st);
+            sum_add_ct(c, level, 2 * n_ct, R.u64(), batch, n2 - 1, G.u64(), G.u64(), st);
+        }
     }
     // one rescale (lazy rescaling), then rotate-and-sum over the d_in / d_out blocks
     DevBuf Y((size_t)n_ct * 2 * level * n * 8, st), tmp((size_t)n_ct * 2 * level * n * 8, st);
     rescale(c, level, 2 * n_ct, G.u64(), Y.u64(), tmp.u64(), st);
-    rotsum(c, evk, level - 1, n_ct, Y.u64(), fc.rotsum, st);
+    rotsum(c, evk, level - 1, n_ct, Y.u64(), fc.rotsum, st, pmod);
     return Y;
 }
 
 }  // namespace
 
 hear_model *model_create(hear_context *c, const hear_layer_desc *layers, size_t n_layers, uint32_t clip_dim,
-                         uint32_t start_level, uint32_t rotsum_radix, uint32_t fc_n1, bool hoist_moddown) {
+                         uint32_t start_level, uint32_t rotsum_radix, uint32_t fc_n1, bool hoist_moddown,
+                         bool hoist_sums) {
     HEAR_REQUIRE(rotsum_radix >= 2 && (rotsum_radix & (rotsum_radix - 1)) == 0 && rotsum_radix <= 64, HEAR_E_INVAL,
                  "rotsum radix must be a power of two in [2, 64]");
     HEAR_REQUIRE(layers && n_layers > 0, HEAR_E_INVAL, "no layers");
@@ -484,6 +524,20 @@ hear_model *model_create(hear_context *c, const hear_layer_desc *layers, size_t 
     m->rotsum_radix = rotsum_radix;
     m->fc_n1 = fc_n1;
     m->hoist_moddown = hoist_moddown;
+    m->hoist_sums = hoist_sums;
+    {
+        // ([P]_{q_t}, Shoup) for every ciphertext prime (hoisted sums)
+        std::vector<uint64_t> pm;
+        for (uint32_t t = 0; t < c->n_q; t++) {
+            const uint64_t q = c->primes[t];
+            uint64_t v = 1;
+            for (uint32_t kk = 0; kk < c->K; kk++) v = hm::mulmod(v, c->primes[c->n_q + kk] % q, q);
+            pm.push_back(v);
+            pm.push_back(hm::shoup_companion(v, q));
+        }
+        m->pmod_all = DevBuf(pm.size() * 8, nullptr);
+        HEAR_CHECK_CUDA(cudaMemcpy(m->pmod_all.p, pm.data(), pm.size() * 8, cudaMemcpyHostToDevice));
+    }
     m->k = slots / clip_dim;
     m->M = clip_dim;
     uint32_t level = start_level, dim = clip_dim;
@@ -571,7 +625,8 @@ DevBuf evaluate_batch(const hear_model *m, const hear_eval_keys *evk, size_t l0,
             DevBuf tmp((size_t)n_ct * 2 * lv * n * 8, st);
             rescale(c, lv, 2 * n_ct, prod.u64(), next.u64(), tmp.u64(), st);
             scale = s1 * s1 / (double)c->primes[lv];
-            rotsum(c, evk, lv - 1, n_ct, next.u64(), L.final_rotsum, st);
+            rotsum(c, evk, lv - 1, n_ct, next.u64(), L.final_rotsum, st,
+                   m->hoist_sums ? m->pmod_all.u64() : nullptr);
         }
         level = L.level_out;
         cur = std::move(next);

@@ -43,6 +43,8 @@ struct hear_model {
     uint32_t rotsum_radix = 8;                      // copies folded per rotate-and-sum round
     uint32_t fc_n1 = 0;                             // FC baby steps (0 = smallest power of two with n1^2 >= D)
     bool hoist_moddown = false;                     // FC babies kept over Q_l u P, one ModDown per giant sum
+    bool hoist_sums = false;                        // giant sums and rotate-and-sum rounds ModDowned once
+    hear::DevBuf pmod_all;                          // ([P]_{q_t}, Shoup) for t < n_q
     mutable std::mutex plan_mu;
     mutable std::vector<std::unique_ptr<Plan>> plans;
     std::vector<Layer> layers;
@@ -100,6 +102,9 @@ void rotate_hoisted_ext(hear_context *c, uint32_t level, uint32_t n_ct, const ui
 // out[r*C + c] = rho_r(x[r*C + c]): job r rotates its C ciphertexts with rots[r]
 void rotate_each(hear_context *c, uint32_t level, uint32_t R, uint32_t C, const uint64_t *x,
                  const std::vector<Rot> &rots, uint64_t *out, cudaStream_t st);
+// the same before ModDown: out_ext [R][C][2][W][N] over Q_l u P holds (P sigma_r(c0) + u0, u1)
+void rotate_each_ext(hear_context *c, uint32_t level, uint32_t R, uint32_t C, const uint64_t *x,
+                     const std::vector<Rot> &rots, uint64_t *out_ext, const uint64_t *pmod, cudaStream_t st);
 // tensor + relinearise (no rescale): out [n_ct][2][level+1][N]
 void mul_relin(hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *a, const uint64_t *b,
                const uint64_t *relin_key, uint64_t *out, cudaStream_t st);
@@ -118,7 +123,7 @@ constexpr uint32_t kDefaultRotsumRadix = 8;
 // the level where it is used)
 hear_model *model_create(hear_context *c, const hear_layer_desc *layers, size_t n_layers, uint32_t clip_dim,
                          uint32_t start_level, uint32_t rotsum_radix = kDefaultRotsumRadix, uint32_t fc_n1 = 0,
-                         bool hoist_moddown = false);
+                         bool hoist_moddown = false, bool hoist_sums = false);
 // evaluate layers [l0, l1) on a batch x at the first layer's level; returns the output batch
 DevBuf evaluate_batch(const hear_model *m, const hear_eval_keys *evk, size_t l0, size_t l1, const uint64_t *x,
                       uint32_t n_ct, uint32_t *level_out, double scale_in, double *scale_out, cudaStream_t st);

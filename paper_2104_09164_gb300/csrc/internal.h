@@ -132,8 +132,24 @@ inline uint32_t ntt_bucket(uint32_t n_limbs) {
     return b;
 }
 
+// launch forms of the key-switch inner product and the BSGS inner sums (kernels.cu), per
+// log2 bucket of the batch: [0] k_ks_inner by ciphertexts per job (4 forms: register cap
+// for 3 or 2 CTAs per SM x all ciphertexts per thread or chunks of 4), [1] k_ks_inner_rj by
+// jobs (4, 2 or 8 jobs per thread), [2] k_lincomb by ciphertexts (4 or 8 accumulators per
+// thread); every form computes the same residues
+constexpr int kKsTables = 3;
+constexpr int kKsBuckets = 8;
+constexpr int kKsVariants[kKsTables] = {4, 3, 2};
+inline uint32_t ks_bucket(uint32_t n) {
+    uint32_t b = 0;
+    while ((2u << b) <= n && b + 1 < (uint32_t)kKsBuckets) b++;
+    return b;
+}
+
 struct hear_context {
     int device = 0;
+    int ks_force = -1;                        // debug: force one form in every table (-1 = tables)
+    uint8_t ks_choice[kKsTables][kKsBuckets] = {};   // 0 = the default form
     hear::Allocator allocator;                // hear_set_allocator (none = the stream-ordered pool)
     int ntt_force = -1;                       // debug: force one NTT variant (-1 = table)
     uint8_t ntt_choice[2][kNttBuckets];       // [forward, inverse][limb bucket] -> variant

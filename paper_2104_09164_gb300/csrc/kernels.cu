@@ -4,6 +4,7 @@
 // CTA, so every warp reads and writes 256 contiguous bytes), y and z cover limbs and
 // ciphertexts, so no thread ever divides a 64-bit index.  The NTT-domain ordering is that
 // of ntt.cu: index i holds the evaluation at psi^(2 brv(i) + 1).
+#include <functional>
 #include "kernels.cuh"
 #include "modarith.cuh"
 #include "launch.cuh"
@@ -202,6 +203,26 @@ __global__ void k_sum(const uint64_t *a, uint64_t stride, uint32_t cnt, const ui
     out[i] = s;
 }
 
+// out [.][W][N] over Q_l u P = B + sum_{j < cnt} a[j * stride]: B = [P]_{q_t} x_t on the Q
+// limbs and 0 on the special limbs (x over Q_l, [.][L1][N]; pmod = ([P]_{q_t}, Shoup) pairs),
+// or B = b (over Q_l u P), or 0.  y = limb t of W, z = polynomial.
+__global__ void k_sum_ext(const uint64_t *a, uint64_t stride, uint32_t cnt, const uint64_t *x, const uint64_t *b,
+                          uint64_t *out, uint32_t L1, uint32_t W, const uint64_t *pmod, const DevPrime *P,
+                          uint32_t n_q, uint32_t n) {
+    pdl_enter();
+    const uint32_t t = blockIdx.y, g = blockIdx.z, k = COEF();
+    const uint64_t i = ((uint64_t)g * W + t) * n + k;
+    const uint64_t q = P[t < L1 ? t : n_q + (t - L1)].q;
+    uint64_t v = 0;
+    if (x) {
+        if (t < L1) v = shoup(x[((uint64_t)g * L1 + t) * n + k], pmod[2 * t], pmod[2 * t + 1], q);
+    } else if (b) {
+        v = b[i];
+    }
+    for (uint32_t j = 0; j < cnt; j++) v = add_mod(v, a[j * stride + i], q);
+    out[i] = v;
+}
+
 // y = limb t, z = ciphertext
 __global__ void k_tensor(const uint64_t *a, const uint64_t *b, uint64_t *out, uint32_t L1, const DevPrime *P,
                          uint32_t n) {
@@ -271,12 +292,15 @@ __device__ __forceinline__ void fold(u128 &acc, uint64_t q) {
 // coefficients.  Grid x = group of 8 polynomials (fastest), y = coefficient tile, z = limb:
 // all CTAs of one (limb, tile) run back to back, so the plaintext tile they share comes
 // from HBM once and from L2 (and, within a CTA, L1) afterwards.  Each thread walks the
-// giant steps in chunks of four accumulators; its baby words stay in L1/L2 across chunks.
+// giant steps in chunks of JC accumulators; its baby words stay in L1/L2 across chunks.
 // With few ciphertexts (2C <= 4 polynomials, one CTA column) the warps beyond 2C would idle:
 // jw = 8 / 2C warps then share each polynomial, warp w taking polynomial w mod 2C and the
-// giant-step chunks (4 outputs each) jpart, jpart + jw, .. with jpart = w / 2C.
+// giant-step chunks (JC outputs each) jpart, jpart + jw, .. with jpart = w / 2C.
 // Limbs t >= lq are over the special primes (inner sums over Q_l u P): prime n_q + t - lq.
-__global__ void __launch_bounds__(256, 4) k_lincomb(uint32_t L1, uint32_t C, uint32_t n1, uint32_t n2,
+// JC = giant-step outputs accumulated per pass over the babies (4, or 8 with the registers of
+// two CTAs per SM)
+template <int JC>
+__global__ void __launch_bounds__(256, JC == 4 ? 4 : 2) k_lincomb(uint32_t L1, uint32_t C, uint32_t n1, uint32_t n2,
                                                  const uint64_t *__restrict__ baby, const uint64_t *__restrict__ pt,
                                                  uint64_t *__restrict__ out, const DevPrime *P, uint32_t n,
                                                  uint32_t jw, uint32_t lq, uint32_t n_q) {
@@ -298,24 +322,26 @@ __global__ void __launch_bounds__(256, 4) k_lincomb(uint32_t L1, uint32_t C, uin
     const uint64_t q = P[pi].q, qinv = P[pi].qinv;
     const uint64_t bstride = 2ull * C * plane;                    // between baby steps / giant outputs
     const uint64_t *bp = baby + (uint64_t)cp * plane + r;
-    for (uint32_t j0 = 4 * jpart; j0 < n2; j0 += 4 * jw) {
-        u128 acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    for (uint32_t j0 = JC * jpart; j0 < n2; j0 += JC * jw) {
+        u128 acc[JC];
+#pragma unroll
+        for (int jj = 0; jj < JC; jj++) acc[jj] = u128{0, 0};
         const uint64_t *pp = pt + ((uint64_t)j0 * n1) * plane + r;
-        const uint32_t jn = min(4u, n2 - j0);
+        const uint32_t jn = min((uint32_t)JC, n2 - j0);
         uint32_t b = 0;
         // two baby steps per iteration: ten independent loads in flight per thread
         for (; b + 2 <= n1; b += 2) {
             const uint64_t x0 = bp[(uint64_t)b * bstride], x1 = bp[(uint64_t)(b + 1) * bstride];
-            uint64_t w0[4], w1[4];
+            uint64_t w0[JC], w1[JC];
 #pragma unroll
-            for (int jj = 0; jj < 4; jj++) {
+            for (int jj = 0; jj < JC; jj++) {
                 if (jj < (int)jn) {
                     w0[jj] = __ldg(pp + ((uint64_t)jj * n1 + b) * plane);
                     w1[jj] = __ldg(pp + ((uint64_t)jj * n1 + b + 1) * plane);
                 }
             }
 #pragma unroll
-            for (int jj = 0; jj < 4; jj++) {
+            for (int jj = 0; jj < JC; jj++) {
                 if (jj < (int)jn) {
                     mac_raw(acc[jj], x0, w0[jj]);
                     mac_raw(acc[jj], x1, w1[jj]);
@@ -326,12 +352,12 @@ __global__ void __launch_bounds__(256, 4) k_lincomb(uint32_t L1, uint32_t C, uin
         for (; b < n1; b++) {
             const uint64_t x = bp[(uint64_t)b * bstride];
 #pragma unroll
-            for (int jj = 0; jj < 4; jj++)
+            for (int jj = 0; jj < JC; jj++)
                 if (jj < (int)jn) mac_lazy(acc[jj], x, __ldg(pp + ((uint64_t)jj * n1 + b) * plane), q);
         }
         uint64_t *op = out + (uint64_t)j0 * bstride + (uint64_t)cp * plane + r;
 #pragma unroll
-        for (int jj = 0; jj < 4; jj++)
+        for (int jj = 0; jj < JC; jj++)
             if (j0 + jj < n2) op[(uint64_t)jj * bstride] = mont_reduce(acc[jj], q, qinv);
     }
 }
@@ -402,15 +428,21 @@ __global__ void k_modup_conv(const uint64_t *c1, uint64_t c1_stride, const uint6
 // y = limb t of Q_l u P.
 // OWN (one-limb digits): digit j's own limb t = j is read from own + ct * own_stride (the
 // input's c1 in the NTT domain) instead of ext.
-template <int MAXD, bool OWN>
-__global__ void __launch_bounds__(256, 3) k_ks_inner(const uint64_t *ext, int ext_per_job, const uint64_t *const *keys, const uint32_t *ginv,
+// MINB: CTAs per SM the register allocation is capped for (3 or 2); c_chunk: ciphertexts
+// per thread (grid y = job x chunk; 0 = all C ciphertexts in one thread, the keys then
+// read once per coefficient)
+template <int MAXD, bool OWN, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_ks_inner(const uint64_t *ext, int ext_per_job, const uint64_t *const *keys, const uint32_t *ginv,
                            uint64_t *out, uint32_t C, uint32_t L1, uint32_t W, uint32_t dnum, uint32_t n_q,
                            uint32_t nqp, uint32_t log_n, const DevPrime *P, const uint64_t *own,
-                           uint64_t own_stride, const uint64_t *pc0, const uint64_t *pmod) {
+                           uint64_t own_stride, const uint64_t *pc0, const uint64_t *pmod, uint32_t c_chunk) {
     pdl_enter();
     // grid y = job (varies before the limb, so the jobs of one limb run together and
-    // share that limb's digit slice in L2), z = limb t of Q_l u P
-    const uint32_t n = 1u << log_n, k = COEF(), r = blockIdx.y, t = blockIdx.z;
+    // share that limb's digit slice in L2) and chunk of ciphertexts, z = limb t of Q_l u P
+    const uint32_t nch = c_chunk ? (C + c_chunk - 1) / c_chunk : 1;
+    const uint32_t n = 1u << log_n, k = COEF(), r = blockIdx.y / nch, t = blockIdx.z;
+    const uint32_t c_begin = c_chunk ? (blockIdx.y % nch) * c_chunk : 0;
+    const uint32_t c_end = c_chunk ? min(C, c_begin + c_chunk) : C;
     const uint32_t pt = t < L1 ? t : n_q + (t - L1);
     const uint64_t q = P[pt].q, qinv = P[pt].qinv;
     const uint64_t key_plane = (uint64_t)nqp * n;
@@ -426,7 +458,7 @@ __global__ void __launch_bounds__(256, 3) k_ks_inner(const uint64_t *ext, int ex
     const uint32_t g = ginv[r];
     const uint32_t kk = g == 1 ? k : auto_index(k, g, log_n);
     const uint64_t ext_ct = (uint64_t)dnum * W * n, out_ct = 2ull * W * n;
-    for (uint32_t c = 0; c < C; c++) {
+    for (uint32_t c = c_begin; c < c_end; c++) {
         const uint64_t cti = ext_per_job ? (uint64_t)r * C + c : c;
         const uint64_t *e = ext + cti * ext_ct + (uint64_t)t * n + k;
         uint64_t xs[MAXD];
@@ -604,6 +636,13 @@ void check_yz(uint32_t y, uint32_t z) {
 
 // launch with the profiler bracket; the stage name is the kernel's, `bytes` its algorithmic
 // HBM traffic (each residue it must read or write, once)
+// the launch form of table `tab` for a launch of `n` (ciphertexts or jobs): forced, or the
+// context's tuned table (0 = the default form)
+uint32_t ks_form(const hear_context *c, int tab, uint32_t n) {
+    if (c->ks_force >= 0) return (uint32_t)c->ks_force % kKsVariants[tab];
+    return c->ks_choice[tab][ks_bucket(n)] % kKsVariants[tab];
+}
+
 #define LAUNCH3(kernel, grid, block, st, bytes, ...)                                      \
     do {                                                                                  \
         ProfScope ps__(c, #kernel, st, (double)(bytes));                                   \
@@ -724,8 +763,12 @@ void lincomb(const hear_context *c, uint32_t level, uint32_t n_ct, uint32_t n1, 
     // algorithmic: every baby ciphertext, every plaintext and every output once
     const double bytes = 8.0 * L1 * c->n * (2.0 * n_ct * n1 + (double)n1 * n2 + 2.0 * n_ct * n2);
     const uint32_t jw = 2 * n_ct <= 4 ? 8 / (2 * n_ct) : 1;
-    LAUNCH3(k_lincomb, grid, 256, st, bytes, L1, n_ct, n1, n2, baby, pt, out, c->dev_primes(), c->n, jw, L1,
-            c->n_q);
+    if (ks_form(c, 2, n_ct) == 1)
+        LAUNCH3(k_lincomb<8>, grid, 256, st, bytes, L1, n_ct, n1, n2, baby, pt, out, c->dev_primes(), c->n, jw, L1,
+                c->n_q);
+    else
+        LAUNCH3(k_lincomb<4>, grid, 256, st, bytes, L1, n_ct, n1, n2, baby, pt, out, c->dev_primes(), c->n, jw, L1,
+                c->n_q);
 }
 void lincomb_ext(const hear_context *c, uint32_t level, uint32_t n_ct, uint32_t n1, uint32_t n2, const uint64_t *baby,
                  const uint64_t *pt, uint64_t *out, cudaStream_t st) {
@@ -734,8 +777,12 @@ void lincomb_ext(const hear_context *c, uint32_t level, uint32_t n_ct, uint32_t 
     HEAR_REQUIRE(grid.x < (1u << 31), HEAR_E_UNSUPPORTED, "launch too large");
     const double bytes = 8.0 * W * c->n * (2.0 * n_ct * n1 + (double)n1 * n2 + 2.0 * n_ct * n2);
     const uint32_t jw = 2 * n_ct <= 4 ? 8 / (2 * n_ct) : 1;
-    LAUNCH3(k_lincomb, grid, 256, st, bytes, W, n_ct, n1, n2, baby, pt, out, c->dev_primes(), c->n, jw, L1,
-            c->n_q);
+    if (ks_form(c, 2, n_ct) == 1)
+        LAUNCH3(k_lincomb<8>, grid, 256, st, bytes, W, n_ct, n1, n2, baby, pt, out, c->dev_primes(), c->n, jw, L1,
+                c->n_q);
+    else
+        LAUNCH3(k_lincomb<4>, grid, 256, st, bytes, W, n_ct, n1, n2, baby, pt, out, c->dev_primes(), c->n, jw, L1,
+                c->n_q);
 }
 void mulplain(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *ct, const uint64_t *pt,
               uint64_t *out, cudaStream_t st) {
@@ -790,41 +837,67 @@ void ks_inner(const hear_context *c, uint32_t level, uint32_t R, uint32_t C, con
     // with pmod: the outputs stay over Q_l u P and receive P sigma_g(c0), c0 = c1 - one plane
     const uint64_t *pc0 = pmod ? c1 - (uint64_t)(level + 1) * c->n : nullptr;
     const uint32_t L1 = level + 1, W = L1 + c->K, dnum = c->dnum(level);
-    check_yz(R, W);
     const double dn = dnum, wn = (double)W * c->n * 8.0;
     // algorithmic: each key once, each extended digit once (per job if not shared), each output once
     const double bytes = R * 2.0 * dn * wn + (ext_per_job ? (double)R * C : (double)C) * dn * wn + R * C * 2.0 * wn;
-    const dim3 grid = grid3(c->n, R, W);
-#define KS_LAUNCH(NAME, D, O)                                                                                    \
+    // the form of the k_ks_inner launch: register cap (3 CTAs per SM, or 2 with no spills) x
+    // ciphertexts per thread (all, or chunks of 4: more CTAs, keys read once per chunk)
+    const uint32_t form = ks_form(c, 0, C);
+    const uint32_t c_chunk = (form & 2) && C > 4 ? 4 : 0;
+    const uint32_t nch = c_chunk ? (C + c_chunk - 1) / c_chunk : 1;
+    check_yz(R * nch, W);
+    const dim3 grid = grid3(c->n, R * nch, W);
+#define KS_LAUNCH(NAME, D, O, MB)                                                                                 \
     do {                                                                                                          \
         ProfScope ps__(c, NAME, st, bytes);                                                                       \
-        launch(k_ks_inner<D, O>, grid, kBlock, 0, st, ext, (int)ext_per_job, d_keys, d_ginv, out, C, L1, W, dnum, \
-               c->n_q, c->nqp(), c->log_n, c->dev_primes(), own, c1_stride, pc0, pmod);                           \
+        launch(k_ks_inner<D, O, MB>, grid, kBlock, 0, st, ext, (int)ext_per_job, d_keys, d_ginv, out, C, L1, W,   \
+               dnum, c->n_q, c->nqp(), c->log_n, c->dev_primes(), own, c1_stride, pc0, pmod, c_chunk);            \
+    } while (0)
+#define KS_RJ(RJ)                                                                                                 \
+    do {                                                                                                          \
+        const dim3 g4(c->n / kBlock, (R + RJ - 1) / RJ, W);                                                      \
+        ProfScope ps__(c, "k_ks_inner<8>", st, bytes);                                                            \
+        if (own)                                                                                                  \
+            launch(k_ks_inner_rj<8, true, RJ>, g4, kBlock, 0, st, ext, d_keys, d_ginv, out, R, L1, W, dnum,       \
+                   c->n_q, c->nqp(), c->log_n, c->dev_primes(), own, pc0, pmod);                                  \
+        else                                                                                                      \
+            launch(k_ks_inner_rj<8, false, RJ>, g4, kBlock, 0, st, ext, d_keys, d_ginv, out, R, L1, W, dnum,      \
+                   c->n_q, c->nqp(), c->log_n, c->dev_primes(), own, pc0, pmod);                                  \
     } while (0)
     if (C == 1 && !ext_per_job && R >= 2 && dnum <= 8) {
-        constexpr int RJ = 4;
-        const dim3 g4(c->n / kBlock, (R + RJ - 1) / RJ, W);
-        ProfScope ps__(c, "k_ks_inner<8>", st, bytes);
-        if (own)
-            launch(k_ks_inner_rj<8, true, RJ>, g4, kBlock, 0, st, ext, d_keys, d_ginv, out, R, L1, W, dnum, c->n_q,
-                                                              c->nqp(), c->log_n, c->dev_primes(), own, pc0, pmod);
-        else
-            launch(k_ks_inner_rj<8, false, RJ>, g4, kBlock, 0, st, ext, d_keys, d_ginv, out, R, L1, W, dnum, c->n_q,
-                                                               c->nqp(), c->log_n, c->dev_primes(), own, pc0, pmod);
+        // one ciphertext whose digits all jobs share: RJ jobs per thread (4, 2 or 8)
+        switch (ks_form(c, 1, R)) {
+        case 1: KS_RJ(2); break;
+        case 2: KS_RJ(8); break;
+        default: KS_RJ(4);
+        }
         HEAR_CHECK_CUDA(cudaGetLastError());
         return;
     }
     if (dnum <= 8) {
-        if (own) KS_LAUNCH("k_ks_inner<8>", 8, true);
-        else KS_LAUNCH("k_ks_inner<8>", 8, false);
+        const bool mb2 = form & 1;
+        if (own && mb2) KS_LAUNCH("k_ks_inner<8>", 8, true, 2);
+        else if (own) KS_LAUNCH("k_ks_inner<8>", 8, true, 3);
+        else if (mb2) KS_LAUNCH("k_ks_inner<8>", 8, false, 2);
+        else KS_LAUNCH("k_ks_inner<8>", 8, false, 3);
     } else if (dnum <= 16) {
-        if (own) KS_LAUNCH("k_ks_inner<16>", 16, true);
-        else KS_LAUNCH("k_ks_inner<16>", 16, false);
+        if (own) KS_LAUNCH("k_ks_inner<16>", 16, true, 3);
+        else KS_LAUNCH("k_ks_inner<16>", 16, false, 3);
     } else {
-        if (own) KS_LAUNCH("k_ks_inner<48>", 48, true);
-        else KS_LAUNCH("k_ks_inner<48>", 48, false);
+        if (own) KS_LAUNCH("k_ks_inner<48>", 48, true, 3);
+        else KS_LAUNCH("k_ks_inner<48>", 48, false, 3);
     }
 #undef KS_LAUNCH
+#undef KS_RJ
+}
+
+void sum_ext(const hear_context *c, uint32_t level, uint32_t n_polys, const uint64_t *a, uint64_t stride,
+             uint32_t cnt, const uint64_t *x, const uint64_t *b, uint64_t *out, const uint64_t *pmod, cudaStream_t st) {
+    const uint32_t L1 = level + 1, W = L1 + c->K;
+    check_yz(W, n_polys);
+    const double base = x ? (double)L1 : (b ? (double)W : 0.0);
+    LAUNCH3(k_sum_ext, grid3(c->n, W, n_polys), kBlock, st, 8.0 * n_polys * c->n * (base + (double)(cnt + 1) * W),
+            a, stride, cnt, x, b, out, L1, W, pmod, c->dev_primes(), c->n_q, c->n);
 }
 
 void scale_p_ext(const hear_context *c, uint32_t level, uint32_t n_polys, const uint64_t *x, uint64_t *out,
@@ -883,6 +956,117 @@ void rescale(const hear_context *c, uint32_t level, uint32_t n_polys, uint64_t *
     check_yz(level, n_polys);
     LAUNCH3(k_rescale_combine, grid3(c->n, level, n_polys), kBlock, st, 24.0 * n_polys * level * c->n, in, tmp, out,
             L1, lc.d.u64() + lc.off_ql_inv, c->dev_primes(), c->n);
+}
+
+
+// Time every launch form of the key-switch inner product and the BSGS inner sums on
+// synthetic operands at the top level (the values do not change the work) for batches of
+// 1, 2, 4, .. max_ct ciphertexts (inner products over 8 jobs; shared-digit products over
+// 2 .. 16 jobs), each as a replayed CUDA graph of `iters` launches, and record the fastest
+// form per bucket.  Buckets above the tuned range keep the largest tuned bucket's form.
+void ks_tune(hear_context *c, uint32_t max_ct, int iters, float *ms_out) {
+    HEAR_REQUIRE(max_ct >= 1 && max_ct <= 64 && iters >= 1, HEAR_E_INVAL, "bad tuning range");
+    cudaStream_t st = c->stream;
+    const uint32_t level = c->L, L1 = level + 1, W = L1 + c->K, dnum = c->dnum(level), n = c->n;
+    const uint32_t R = 8, RMAX = 16, n1 = 8, n2 = 8;
+    const uint64_t plane = (uint64_t)n;
+    const uint64_t key_words = (uint64_t)c->dnum_max() * 2 * c->nqp() * plane;
+    DevBuf keys(RMAX * key_words * 8, st);
+    const uint64_t n_src = std::max(max_ct, R);   // ciphertexts whose digits are read
+    DevBuf ext(n_src * dnum * W * plane * 8, st);
+    DevBuf c1(n_src * 2 * L1 * plane * 8, st);
+    DevBuf out((uint64_t)std::max(max_ct * R, RMAX) * 2 * W * plane * 8, st);
+    DevBuf baby((uint64_t)n1 * max_ct * 2 * L1 * plane * 8, st);
+    DevBuf pts((uint64_t)n1 * n2 * L1 * plane * 8, st);
+    DevBuf sums((uint64_t)n2 * max_ct * 2 * L1 * plane * 8, st);
+    for (DevBuf *b : {&keys, &ext, &c1, &out, &baby, &pts, &sums}) HEAR_CHECK_CUDA(cudaMemsetAsync(b->p, 0, b->bytes, st));
+    std::vector<const uint64_t *> kp(RMAX);
+    std::vector<uint32_t> gi(RMAX);
+    uint64_t g = 1;
+    for (uint32_t r = 0; r < RMAX; r++) {
+        kp[r] = keys.u64() + r * key_words;
+        g = g * 5 % (2ull * n);
+        gi[r] = (uint32_t)g;
+    }
+    DevBuf d_kp(RMAX * sizeof(void *), st), d_gi(RMAX * 4, st);
+    HEAR_CHECK_CUDA(cudaMemcpyAsync(d_kp.p, kp.data(), RMAX * sizeof(void *), cudaMemcpyHostToDevice, st));
+    HEAR_CHECK_CUDA(cudaMemcpyAsync(d_gi.p, gi.data(), RMAX * 4, cudaMemcpyHostToDevice, st));
+    HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
+    const uint64_t *const *dk = static_cast<const uint64_t *const *>(d_kp.p);
+    const uint32_t *dg = static_cast<const uint32_t *>(d_gi.p);
+    cudaEvent_t e0, e1;
+    HEAR_CHECK_CUDA(cudaEventCreate(&e0));
+    HEAR_CHECK_CUDA(cudaEventCreate(&e1));
+    // ms of one launch of fn, timed as the second replay of a graph of `iters` launches
+    auto time_graph = [&](const std::function<void()> &fn) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        HEAR_CHECK_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        try {
+            for (int i = 0; i < iters; i++) fn();
+        } catch (...) {
+            cudaStreamEndCapture(st, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            throw;
+        }
+        HEAR_CHECK_CUDA(cudaStreamEndCapture(st, &graph));
+        cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        HEAR_CHECK_CUDA(e);
+        float ms = 0;
+        e = cudaGraphLaunch(exec, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        cudaGraphExecDestroy(exec);
+        HEAR_CHECK_CUDA(e);
+        return ms / iters;
+    };
+    const int saved = c->ks_force;
+    try {
+        for (int tab = 0; tab < kKsTables; tab++) {
+            uint32_t last = 0;
+            for (uint32_t b = 0; b < (uint32_t)kKsBuckets; b++) {
+                const uint32_t m = 1u << b;
+                if (tab == 1 ? (m < 2 || m > RMAX) : m > max_ct) continue;
+                float best = 0;
+                int best_v = 0;
+                for (int v = 0; v < kKsVariants[tab]; v++) {
+                    c->ks_force = v;
+                    float ms = 0;
+                    if (tab == 0)   // C = m ciphertexts per job (one ciphertext: digits per job)
+                        ms = time_graph([&] {
+                            ks_inner(c, level, R, m, ext.u64(), m == 1, dk, dg, out.u64(), c1.u64(),
+                                     2ull * L1 * plane, st);
+                        });
+                    else if (tab == 1)   // one ciphertext, m jobs sharing its digits
+                        ms = time_graph([&] {
+                            ks_inner(c, level, m, 1, ext.u64(), false, dk, dg, out.u64(), c1.u64(), 2ull * L1 * plane, st);
+                        });
+                    else
+                        ms = time_graph([&] { lincomb(c, level, m, n1, n2, baby.u64(), pts.u64(), sums.u64(), st); });
+                    if (ms_out) ms_out[((size_t)tab * kKsBuckets + b) * 4 + v] = ms;
+                    if (v == 0 || ms < best) {
+                        best = ms;
+                        best_v = v;
+                    }
+                }
+                c->ks_choice[tab][b] = (uint8_t)best_v;
+                last = b;
+            }
+            for (uint32_t b = last + 1; b < (uint32_t)kKsBuckets; b++) c->ks_choice[tab][b] = c->ks_choice[tab][last];
+        }
+    } catch (...) {
+        c->ks_force = saved;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    c->ks_force = saved;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
 }
 
 }  // namespace hear

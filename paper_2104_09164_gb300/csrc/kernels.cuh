@@ -92,11 +92,20 @@ void sum_ct(const hear_context *c, uint32_t level, uint32_t n_polys_total, const
 // out = base + sum of cnt batches a + j*stride (out may alias base)
 void sum_add_ct(const hear_context *c, uint32_t level, uint32_t n_polys_total, const uint64_t *a, uint64_t stride,
                 uint32_t cnt, const uint64_t *base, uint64_t *out, cudaStream_t st);
+// out [n_polys][W][N] over Q_l u P = base + sum of cnt batches a + j*stride (W limbs each):
+// base = P x (x over Q_l, [n_polys][l+1][N]) if x, else b (over Q_l u P) if b, else 0;
+// pmod = ([P]_{q_t}, Shoup) pairs for t <= l (used with x)
+void sum_ext(const hear_context *c, uint32_t level, uint32_t n_polys, const uint64_t *a, uint64_t stride,
+             uint32_t cnt, const uint64_t *x, const uint64_t *b, uint64_t *out, const uint64_t *pmod, cudaStream_t st);
 // out = a (.) b_mont over n_limbs limbs (Montgomery product: a * b)
 void pointwise_mont(const hear_context *c, uint32_t n_limbs, LimbMap m, const uint64_t *a, const uint64_t *b_mont,
                     uint64_t *out, cudaStream_t st);
 // rescale batch [n_polys][l+1][N] -> out [n_polys][l][N]; destroys limb l of `in`; tmp n_polys*l*N words
 void rescale(const hear_context *c, uint32_t level, uint32_t n_polys, uint64_t *in, uint64_t *out, uint64_t *tmp,
              cudaStream_t st);
+
+// time every launch form of the inner products / inner sums and fill c->ks_choice (ms_out:
+// [kKsTables][kKsBuckets][4] or null)
+void ks_tune(hear_context *c, uint32_t max_ct, int iters, float *ms_out);
 
 }  // namespace hear

@@ -299,7 +299,7 @@ hear_status hear_server_create(const hear_model *m, const hear_eval_keys *evk, c
     if (evk->ctx != m->ctx) return fail(HEAR_E_STATE, "keys from another context");
     if (cfg->max_batch < 1 || cfg->n_slots < 1 || cfg->n_slots > 8)
         return fail(HEAR_E_INVAL, "need max_batch >= 1 and 1 <= n_slots <= 8");
-    const uint32_t staging = cfg->staging_cts ? cfg->staging_cts : 2 * cfg->n_slots * cfg->max_batch;
+    const uint32_t staging = cfg->staging_cts ? cfg->staging_cts : std::max(4 * cfg->n_slots * cfg->max_batch, 64u);
     if (staging < cfg->max_batch) return fail(HEAR_E_INVAL, "staging_cts must hold a request of max_batch ciphertexts");
     hear_context *c = m->ctx;
     if (c->poisoned) return fail(HEAR_E_CUDA, "context is poisoned by an earlier CUDA error");

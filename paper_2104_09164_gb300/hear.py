@@ -46,7 +46,7 @@ class hear_layer_desc(ctypes.Structure):
 
 class hear_model_opts(ctypes.Structure):
     _fields_ = [("level", ctypes.c_uint32), ("rotsum_radix", ctypes.c_uint32), ("fc_n1", ctypes.c_uint32),
-                ("hoist_moddown", ctypes.c_uint32)]
+                ("hoist_moddown", ctypes.c_uint32), ("hoist_sums", ctypes.c_uint32)]
 
 
 class hear_profile_entry(ctypes.Structure):
@@ -208,6 +208,11 @@ def _load():
         "hear_ntt_tune": (st, [_vp, ctypes.c_uint32, ctypes.c_int, ctypes.POINTER(ctypes.c_uint8),
                                ctypes.POINTER(ctypes.c_float)]),
         "hear_ntt_set_variant": (st, [_vp, ctypes.c_int]),
+        "hear_ks_tune": (st, [_vp, ctypes.c_uint32, ctypes.c_int, ctypes.POINTER(ctypes.c_uint8),
+                              ctypes.POINTER(ctypes.c_float)]),
+        "hear_ks_get_table": (st, [_vp, ctypes.POINTER(ctypes.c_uint8)]),
+        "hear_ks_set_table": (st, [_vp, ctypes.POINTER(ctypes.c_uint8)]),
+        "hear_ks_set_variant": (st, [_vp, ctypes.c_int]),
         "hear_ntt_get_table": (st, [_vp, ctypes.POINTER(ctypes.c_uint8)]),
         "hear_ntt_set_table": (st, [_vp, ctypes.POINTER(ctypes.c_uint8)]),
         "hear_dbg_imad_peak": (st, [_vp, ctypes.c_int, ctypes.c_uint32, _dp]),
@@ -443,14 +448,16 @@ def _layer_descs(layers):
     return descs, keep
 
 
-def hear_model_create(ctx, layers, clip_dim, level=None, rotsum_radix=None, fc_n1=None, hoist_moddown=False):
+def hear_model_create(ctx, layers, clip_dim, level=None, rotsum_radix=None, fc_n1=None, hoist_moddown=False,
+                      hoist_sums=False):
     """layers: sequence of ("fc", W) | ("square",) | ("fc_sq_fc", W1, W2) with float64 matrices;
-    level: input level (None = the top level); rotsum_radix, fc_n1, hoist_moddown: see
-    hear_model_opts"""
+    level: input level (None = the top level); rotsum_radix, fc_n1, hoist_moddown, hoist_sums:
+    see hear_model_opts"""
     descs, keep = _layer_descs(layers)
     h = _vp()
-    if rotsum_radix is not None or fc_n1 is not None or hoist_moddown:
-        opts = hear_model_opts(int(level or 0), int(rotsum_radix or 0), int(fc_n1 or 0), int(bool(hoist_moddown)))
+    if rotsum_radix is not None or fc_n1 is not None or hoist_moddown or hoist_sums:
+        opts = hear_model_opts(int(level or 0), int(rotsum_radix or 0), int(fc_n1 or 0), int(bool(hoist_moddown)),
+                               int(bool(hoist_sums)))
         _check(lib.hear_model_create_ex(ctx, descs, len(layers), int(clip_dim), ctypes.byref(opts), ctypes.byref(h)))
     elif level is None:
         _check(lib.hear_model_create(ctx, descs, len(layers), int(clip_dim), ctypes.byref(h)))
@@ -872,6 +879,31 @@ def hear_ntt_get_table(ctx):
 def hear_ntt_set_table(ctx, table):
     t = np.array([int(ch) for ch in table], dtype=np.uint8)
     _check(lib.hear_ntt_set_table(ctx, _p(t, ctypes.POINTER(ctypes.c_uint8))))
+
+
+def hear_ks_tune(ctx, max_ct=32, iters=5):
+    """time the key-switch / inner-sum launch forms; returns (choice uint8[3][8], ms float32[3][8][4])"""
+    choice = np.zeros((3, 8), dtype=np.uint8)
+    ms = np.zeros((3, 8, 4), dtype=np.float32)
+    _check(lib.hear_ks_tune(ctx, int(max_ct), int(iters), _p(choice, ctypes.POINTER(ctypes.c_uint8)),
+                            _p(ms, ctypes.POINTER(ctypes.c_float))))
+    return choice, ms
+
+
+def hear_ks_get_table(ctx):
+    """-> the form table as a 24-character string (inner products, shared-digit products, inner sums)"""
+    t = np.zeros(24, dtype=np.uint8)
+    _check(lib.hear_ks_get_table(ctx, _p(t, ctypes.POINTER(ctypes.c_uint8))))
+    return "".join(str(int(x)) for x in t)
+
+
+def hear_ks_set_table(ctx, table):
+    t = np.array([int(ch) for ch in table], dtype=np.uint8)
+    _check(lib.hear_ks_set_table(ctx, _p(t, ctypes.POINTER(ctypes.c_uint8))))
+
+
+def hear_ks_set_variant(ctx, variant):
+    _check(lib.hear_ks_set_variant(ctx, int(variant)))
 
 
 def hear_ntt_set_variant(ctx, variant):

@@ -27,12 +27,13 @@ def test_tuned_fc_form_bit_exact(H):
     ctx = H.hear_context_create(w.log_n, w.q_bits, w.p_bits, w.log2_scale, w.sigma, 0)
     try:
         st = torch.cuda.Stream()
-        (n1, dh), report = tune_fc(H, ctx, w.layers, w.clip_dim, w.n_ct, w.slots, steps=2, stream=st)
-        assert [(r["fc_n1"], r["hoist_moddown"]) for r in report] == fc_candidates(w.layers)
-        assert (16, False) in fc_candidates(w.layers)          # the default split is a candidate
+        (n1, dh, hs), report = tune_fc(H, ctx, w.layers, w.clip_dim, w.n_ct, w.slots, steps=2, stream=st)
+        assert [(r["fc_n1"], r["hoist_moddown"], r["hoist_sums"]) for r in report] == fc_candidates(w.layers)
+        assert (16, False, False) in fc_candidates(w.layers)   # the default split is a candidate
         assert all(r["ms"] > 0 for r in report)
-        assert min(r["ms"] for r in report) == [r["ms"] for r in report if (r["fc_n1"], r["hoist_moddown"]) == (n1, dh)][0]
-        model = H.hear_model_create(ctx, w.layers, w.clip_dim, fc_n1=n1, hoist_moddown=dh)
+        assert min(r["ms"] for r in report) == [r["ms"] for r in report
+                                                if (r["fc_n1"], r["hoist_moddown"], r["hoist_sums"]) == (n1, dh, hs)][0]
+        model = H.hear_model_create(ctx, w.layers, w.clip_dim, fc_n1=n1, hoist_moddown=dh, hoist_sums=hs)
         steps = H.hear_model_rotations(model)
         sk, pk, evk = H.hear_keygen(ctx, 301, steps)
         ct = H.hear_encrypt_clips(ctx, pk, w.ct_clips(0), 401, 0)
@@ -40,7 +41,7 @@ def test_tuned_fc_form_bit_exact(H):
         o = O.Oracle(w.log_n, w.q_bits, w.p_bits, w.sigma, threads=os.cpu_count() or 0)
         keys = o.keygen(301, [O.galois_for_step(s, o.n) for s in steps])
         z, kk = O.pack_clips(w.ct_clips(0), w.slots)
-        r = o.evaluate(w.layers, o.encrypt(keys.pk, z, 401, 0, 2.0 ** w.log2_scale), kk, keys, n1=n1, dh=dh)
+        r = o.evaluate(w.layers, o.encrypt(keys.pk, z, 401, 0, 2.0 ** w.log2_scale), kk, keys, n1=n1, dh=dh, hs=hs)
         assert np.array_equal(H.hear_ciphertext_export(out), o.to_coeff(r))
         for h in (ct, out):
             H.hear_ciphertext_destroy(h)

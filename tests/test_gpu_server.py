@@ -156,3 +156,57 @@ def test_two_networks_served_together_equal_alone():
             H.hear_public_key_destroy(pk)
             H.hear_secret_key_destroy(sk)
             H.hear_context_destroy(n["ctx"])
+
+
+def test_busy_timeout_and_pause(setup):
+    """bounded waits and refusals, made deterministic with the pause switch: while paused
+    nothing is admitted, so a wait runs out (HEAR_E_TIMEOUT, the request stays queued), a
+    submit beyond the staging buffers or the queue limit is refused (HEAR_E_BUSY, nothing
+    queued); after resuming every queued request completes bit-identical to alone"""
+    H, w, ctx, model, evk, reqs = setup
+    scale = 2.0 ** w.log2_scale
+    two = [r for r in reqs if r[0] == 2]
+    one = [r for r in reqs if r[0] == 1]
+    alone2 = H.hear_evaluate_host(model, evk, two[0][1], 2, scale)[0]
+    alone1 = H.hear_evaluate_host(model, evk, one[0][1], 1, scale)[0]
+    out1 = alone1.size
+    srv = H.hear_server_create(model, evk, max_batch=4, n_slots=1, hbm_budget_bytes=8 << 30, staging_cts=4,
+                               max_pending=3)
+    try:
+        H.hear_server_pause(srv, True)
+        a = H.hear_server_submit(srv, two[0][1], 2, 2, scale)
+        b = H.hear_server_submit(srv, one[0][1], 1, 1, scale)
+        t0 = time.time()
+        with pytest.raises(H.HearError) as e:
+            H.hear_server_wait(srv, a, 2 * out1, timeout_ms=50)
+        assert e.value.code == H.HEAR_E_TIMEOUT
+        assert time.time() - t0 >= 0.045
+        # 3 of 4 staging buffers are taken: a 2-ciphertext request does not fit
+        with pytest.raises(H.HearError) as e:
+            H.hear_server_submit(srv, two[0][1], 2, 2, scale)
+        assert e.value.code == H.HEAR_E_BUSY
+        c = H.hear_server_submit(srv, one[0][1], 1, 1, scale)
+        # the queue holds max_pending = 3 requests now
+        with pytest.raises(H.HearError) as e:
+            H.hear_server_submit(srv, one[0][1], 1, 1, scale)
+        assert e.value.code == H.HEAR_E_BUSY
+        st = H.hear_server_stats(srv)
+        assert st["pending"] == 3 and st["busy_refusals"] == 2 and st["requests_done"] == 0
+        H.hear_server_pause(srv, False)
+        assert np.array_equal(H.hear_server_wait(srv, a, 2 * out1, timeout_ms=60000), alone2)
+        assert np.array_equal(H.hear_server_wait(srv, b, out1, timeout_ms=60000), alone1)
+        assert np.array_equal(H.hear_server_wait(srv, c, out1, timeout_ms=60000), alone1)
+        # buffers came back: the refused request is accepted now
+        d = H.hear_server_submit(srv, two[0][1], 2, 2, scale)
+        assert np.array_equal(H.hear_server_wait(srv, d, 2 * out1, timeout_ms=60000), alone2)
+        with pytest.raises(H.HearError):
+            H.hear_server_wait(srv, d, 2 * out1, timeout_ms=10)     # the id was released
+        # an unreduced residue is refused without queueing anything
+        bad = one[0][1].copy()
+        bad[5] = np.uint64(H.hear_context_primes(ctx)[0])
+        with pytest.raises(H.HearError) as e:
+            H.hear_server_submit(srv, bad, 1, 1, scale)
+        assert e.value.code == H.HEAR_E_FORMAT
+        assert H.hear_server_stats(srv)["pending"] == 0
+    finally:
+        H.hear_server_destroy(srv)

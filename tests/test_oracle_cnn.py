@@ -269,5 +269,7 @@ def test_fc_form_candidates():
     """the FC-form candidates bracket the default baby-step count of the widest FC layer"""
     from paper_2104_09164_gb300.autotune import fc_candidates
     from paper_2104_09164_gb300.workloads import make_workload
-    assert fc_candidates(make_workload("small").layers) == [(n, d) for n in (8, 16, 32) for d in (False, True)]
-    assert fc_candidates(make_workload("large").layers) == [(n, d) for n in (16, 32, 64) for d in (False, True)]
+    assert fc_candidates(make_workload("small").layers) == [(n, d, h) for n in (8, 16, 32) for d in (False, True)
+                                                            for h in (False, True)]
+    assert fc_candidates(make_workload("large").layers) == [(n, d, h) for n in (16, 32, 64) for d in (False, True)
+                                                            for h in (False, True)]

@@ -622,3 +622,37 @@ def test_hoisted_moddown_fc_matches_plain_product():
     lifted = o.scale_p_ext(ct)
     back = np.stack([o.moddown(ct.level, lifted[p]) for p in range(2)])
     assert np.array_equal(back, ct.data)
+
+
+def test_hoisted_sums_fc_and_rotsum():
+    """hoisted sums (one ModDown per giant-step sum and per rotate-and-sum round, the
+    rotations kept over Q_l u P): with one rotation per round and at most two giant steps it
+    is bit-identical to the per-rotation ModDown form (ModDown(P a + b) = a + ModDown(b)
+    exactly); with more rotations per sum it differs only by ModDown rounding and still
+    decrypts to W x, with and without hoisted ModDown of the babies"""
+    from oracle import oracle as O
+    o = O.Oracle(12, [50, 40, 40], [50], 3.2)
+    S = o.n // 2
+    rng = np.random.default_rng(18)
+    k = 16
+    M = S // k
+    W = rng.normal(0, 0.1, size=(16, M))
+    steps = set()
+    for n1, radix in ((8, 2), (2, 8), (4, 8)):
+        steps.update(O.rotation_steps([("fc", W)], M, k, radix, n1))
+    keys = o.keygen(19, [O.galois_for_step(s, o.n) for s in steps])
+    x = rng.uniform(-1, 1, M)
+    ct = o.encrypt(keys.pk, np.repeat(x, k), 13, 0, 2.0 ** 40)
+    want = W @ x
+    # n1 = 8 of D = 16: two giant steps; radix 2: one rotation per round
+    a = o.fc(ct, W, k, keys, radix=2, n1=8, hs=True)
+    b = o.fc(ct, W, k, keys, radix=2, n1=8, hs=False)
+    assert np.array_equal(a.data, b.data) and a.scale == b.scale
+    for n1, radix, dh in ((2, 8, False), (4, 8, True), (2, 8, True)):
+        r_hs = o.fc(ct, W, k, keys, radix=radix, n1=n1, dh=dh, hs=True)
+        r = o.fc(ct, W, k, keys, radix=radix, n1=n1, dh=dh, hs=False)
+        assert r_hs.level == r.level and r_hs.scale == r.scale
+        assert not np.array_equal(r_hs.data, r.data), (n1, radix, dh)
+        got = o.decrypt(keys, r_hs)[::k][:16]
+        assert np.max(np.abs(got - want)) < 2.0 ** -20, (n1, radix, dh)
+        assert np.max(np.abs(got - o.decrypt(keys, r)[::k][:16])) < 2.0 ** -20
