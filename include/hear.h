@@ -189,7 +189,9 @@ typedef struct hear_layer_desc {
     uint32_t kind;
     uint32_t d_out, d_in;   /* W: d_out x d_in; powers of two with d_out | d_in            */
     const double *w;        /* row-major                                                   */
-    const double *bias;     /* d_out values or NULL (FC only)                              */
+    const double *bias;     /* d_out values or NULL (FC only): added after the rotate-and-
+                             * sum as a plaintext b[p mod d_out] in every slot p*k + c,
+                             * encoded at the output's level and scale                    */
     uint32_t d_out2;        /* FC_SQ_FC: W2 is d_out2 x d_out                               */
     const double *w2;
 } hear_layer_desc;

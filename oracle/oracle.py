@@ -471,7 +471,7 @@ class Oracle:
         """pos-space vector of size M -> N/2 slots, slot p*k + c holds v[p]"""
         return np.repeat(np.asarray(v, dtype=np.float64), k)
 
-    def fc(self, ct: Ct, W, k, keys: Keys, pool=None, radix=ROTSUM_RADIX, n1=None, dh=False, hs=False):
+    def fc(self, ct: Ct, W, k, keys: Keys, pool=None, radix=ROTSUM_RADIX, n1=None, dh=False, hs=False, bias=None):
         """Encrypted FC layer, BSGS diagonal form with hoisted baby steps and one lazy
         rescale, followed by rotate-and-sum; output replicated with period d_out.
         n1: baby steps (default bsgs_split); dh: hoisted ModDown -- the baby rotations stay
@@ -479,7 +479,9 @@ class Oracle:
         plaintexts over Q_l u P and each giant-step sum is ModDowned once.
         hs: hoisted sums -- the giant rotations of the inner sums j >= 1 are kept over
         Q_l u P as (P sigma(c0) + u0, u1), added to inner sum 0 over Q_l u P (P-scaled when it
-        is over Q_l) and ModDowned once, and so is every rotate-and-sum round (rotsum)."""
+        is over Q_l) and ModDowned once, and so is every rotate-and-sum round (rotsum).
+        bias (d_out values): added after the rotate-and-sum as the plaintext b[p mod d_out] in
+        every slot p*k + c, encoded at the output's scale and level."""
         d_out, d_in = W.shape
         M = (self.n // 2) // k
         assert d_in <= M and M % d_in == 0 and d_in % d_out == 0
@@ -536,7 +538,11 @@ class Oracle:
         if hs:
             acc = Ct(np.stack([self.moddown(level, acc_ext[p]) for p in range(2)]), level, ct.scale * ql)
         out = self.rescale(acc)
-        return self.rotsum(out, d_out, d_in // d_out, k, keys, radix, hs)
+        out = self.rotsum(out, d_out, d_in // d_out, k, keys, radix, hs)
+        if bias is not None:
+            b = np.asarray(bias, dtype=np.float64)[np.arange(M) % d_out]
+            out = self.add_plain(out, self.encode_pt(self.expand(b, k), out.scale, out.level))
+        return out
 
     def rotsum(self, ct: Ct, step, count, k, keys: Keys, radix, hs=False):
         """sum of the count (a power of two) copies rho^(j*step*k)(ct), j < count, folded in
@@ -576,7 +582,7 @@ class Oracle:
     def evaluate(self, layers, ct: Ct, k, keys: Keys, pool=None, radix=ROTSUM_RADIX, n1=None, dh=False, hs=False):
         for layer in layers:
             if layer[0] == "fc":
-                ct = self.fc(ct, layer[1], k, keys, pool, radix, n1, dh, hs)
+                ct = self.fc(ct, layer[1], k, keys, pool, radix, n1, dh, hs, layer[2] if len(layer) > 2 else None)
             elif layer[0] == "square":
                 ct = self.square(ct, keys)
             elif layer[0] == "fc_sq_fc":
@@ -661,6 +667,8 @@ class Oracle:
     def evaluate_simd(self, layers, cts, keys: Keys):
         for layer in layers:
             if layer[0] == "fc":
+                if len(layer) > 2 and layer[2] is not None:
+                    raise ValueError("the slot-batched form has no FC bias")
                 cts = self.fc_simd(cts, layer[1])
             elif layer[0] == "square":
                 cts = [self.square(c, keys) for c in cts]

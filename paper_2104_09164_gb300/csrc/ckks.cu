@@ -2,6 +2,7 @@
 // operations the encrypted network is made of, composed from the kernels of ntt.cu and
 // kernels.cu.  Everything between the host encode and the host CRT lift runs on the GPU.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <set>
 #include "ckks.h"
@@ -189,7 +190,7 @@ void decrypt_slots(hear_context *c, const hear_secret_key *sk, const hear_cipher
     decode_double(c->log_n, v.data(), out);
 }
 
-DevBuf encode_plain(hear_context *c, const double *z, double scale, uint32_t level, cudaStream_t st) {
+DevBuf encode_plain(hear_context *c, const double *z, double scale, uint32_t level, cudaStream_t st, bool mont) {
     const uint32_t n = c->n, L1 = level + 1;
     std::vector<int64_t> m(n);
     encode_dd(*encoder(c), z, scale, m.data());
@@ -197,7 +198,7 @@ DevBuf encode_plain(hear_context *c, const double *z, double scale, uint32_t lev
     DevBuf pt((size_t)L1 * n * 8, nullptr);
     i64_to_limbs(c, (const int64_t *)dm.p, pt.u64(), L1, map_q(level, c->n_q), st);
     ntt_forward(c, pt.u64(), L1, map_q(level, c->n_q), st);
-    to_mont(c, pt.u64(), L1, map_q(level, c->n_q), st);
+    if (mont) to_mont(c, pt.u64(), L1, map_q(level, c->n_q), st);
     HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
     return pt;
 }
@@ -549,8 +550,11 @@ hear_model *model_create(hear_context *c, const hear_layer_desc *layers, size_t 
         L.level_in = level;
         if (d.kind == HEAR_LAYER_FC) {
             HEAR_REQUIRE(d.w && d.d_in == dim, HEAR_E_INVAL, "FC input dimension mismatch");
-            HEAR_REQUIRE(!d.bias, HEAR_E_UNSUPPORTED, "bias is not supported");
             build_fc(c, L.fc, d.w, d.d_out, d.d_in, level, m->k, m->M, rotsum_radix, fc_n1, hoist_moddown);
+            if (d.bias) {
+                L.fc.bias.assign(d.bias, d.bias + d.d_out);
+                for (double b : L.fc.bias) HEAR_REQUIRE(std::isfinite(b), HEAR_E_INVAL, "bias is not finite");
+            }
             fc_rotations(L.fc, m->k, rots);
             level -= 1;
             dim = d.d_out;
@@ -589,10 +593,50 @@ hear_model *model_create(hear_context *c, const hear_layer_desc *layers, size_t 
     return m.release();
 }
 
+namespace {
+// the bias plaintext of FC layer li for an output at `scale`: b[p mod d_out] in every slot
+// p*k + c, encoded at that scale with the output level's limbs (normal NTT form)
+const uint64_t *bias_pt(const hear_model *m, size_t li, double scale, cudaStream_t st) {
+    const hear_model::Fc &fc = m->layers[li].fc;
+    uint64_t bits;
+    std::memcpy(&bits, &scale, 8);
+    std::lock_guard<std::mutex> g(m->bias_mu);
+    auto key = std::make_pair(li, bits);
+    auto it = m->bias_pts.find(key);
+    if (it != m->bias_pts.end()) return it->second.u64();
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    HEAR_CHECK_CUDA(cudaStreamIsCapturing(st, &cs));
+    HEAR_REQUIRE(cs == cudaStreamCaptureStatusNone, HEAR_E_STATE, "bias plaintext missing during capture");
+    hear_context *c = m->ctx;
+    std::vector<double> z(c->n / 2);
+    for (uint32_t p = 0; p < m->M; p++)
+        for (uint32_t cc = 0; cc < m->k; cc++) z[(size_t)p * m->k + cc] = fc.bias[p % fc.d_out];
+    DevBuf pt = encode_plain(c, z.data(), scale, m->layers[li].level_out, c->stream, false);
+    return m->bias_pts.emplace(key, std::move(pt)).first->second.u64();
+}
+}  // namespace
+
 DevBuf evaluate_batch(const hear_model *m, const hear_eval_keys *evk, size_t l0, size_t l1, const uint64_t *x,
                       uint32_t n_ct, uint32_t *level_out, double scale_in, double *scale_out, cudaStream_t st) {
     hear_context *c = m->ctx;
     const uint32_t n = c->n;
+    {
+        // every scale-dependent plaintext before the first launch (none inside a capture)
+        double s = scale_in;
+        for (size_t li = l0; li < l1; li++) {
+            const hear_model::Layer &L = m->layers[li];
+            if (L.kind == HEAR_LAYER_FC) {
+                const double ql = (double)c->primes[L.fc.level];
+                s = s * ql / ql;
+                if (!L.fc.bias.empty()) bias_pt(m, li, s, st);
+            } else if (L.kind == HEAR_LAYER_SQUARE) {
+                s = s * s / (double)c->primes[L.level_in];
+            } else {
+                const double ql = (double)c->primes[L.fc.level], s1 = s * ql / ql;
+                s = s1 * s1 / (double)c->primes[L.level_in - 1];
+            }
+        }
+    }
     DevBuf cur;
     const uint64_t *xin = x;
     double scale = scale_in;
@@ -604,6 +648,8 @@ DevBuf evaluate_batch(const hear_model *m, const hear_eval_keys *evk, size_t l0,
             const double ql = (double)c->primes[L.fc.level];
             next = eval_fc(m, L.fc, evk, xin, n_ct, st);
             scale = scale * ql / ql;
+            if (!L.fc.bias.empty())
+                add_plain(c, L.level_out, n_ct, n_ct, next.u64(), bias_pt(m, li, scale, st), st);
         } else if (L.kind == HEAR_LAYER_SQUARE) {
             const uint64_t *rk = need_key(evk, 1);
             DevBuf prod((size_t)n_ct * 2 * (level + 1) * n * 8, st);

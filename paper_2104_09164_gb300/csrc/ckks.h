@@ -1,5 +1,6 @@
 // ckks.h -- batched RNS-CKKS operations and the encoded network (internal).
 #pragma once
+#include <map>
 #include <memory>
 #include <mutex>
 #include <vector>
@@ -15,7 +16,8 @@ struct hear_model {
         bool dh = false;                            // hoisted ModDown: babies and inner sums over Q_l u P
         hear::DevBuf pts;                           // [n2*n1][level+1 (+K if dh)][N] Montgomery, zero = no diagonal
         hear::DevBuf pmod;                          // dh: ([P]_{q_t}, Shoup) for t <= level
-        hear::DevBuf bias;                          // plaintext at level-1 (Montgomery), or empty
+        std::vector<double> bias;                   // d_out bias values (empty: none), added after the
+                                                    // rotate-and-sum at the output level and scale
         std::vector<std::vector<int32_t>> rotsum;   // rotate-and-sum rounds (slot steps, hoisted per round)
     };
     struct Layer {
@@ -45,6 +47,10 @@ struct hear_model {
     bool hoist_moddown = false;                     // FC babies kept over Q_l u P, one ModDown per giant sum
     bool hoist_sums = false;                        // giant sums and rotate-and-sum rounds ModDowned once
     hear::DevBuf pmod_all;                          // ([P]_{q_t}, Shoup) for t < n_q
+    // bias plaintexts (normal NTT form at the FC's output level) per (layer, output scale):
+    // built before the first launch of an evaluation at that scale, never inside a capture
+    mutable std::mutex bias_mu;
+    mutable std::map<std::pair<size_t, uint64_t>, hear::DevBuf> bias_pts;
     mutable std::mutex plan_mu;
     mutable std::vector<std::unique_ptr<Plan>> plans;
     std::vector<Layer> layers;
@@ -113,7 +119,8 @@ void relin3(hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *d3, 
             uint64_t *out, cudaStream_t st);
 
 // encoded plaintext helpers
-DevBuf encode_plain(hear_context *c, const double *z, double scale, uint32_t level, cudaStream_t st);
+DevBuf encode_plain(hear_context *c, const double *z, double scale, uint32_t level, cudaStream_t st,
+                    bool mont = true);
 
 // network
 // copies folded per rotate-and-sum round by default (measured on the small network at batch

@@ -436,6 +436,12 @@ def _layer_descs(layers):
             W = _arr(layer[1], np.float64)
             keep.append(W)
             d.kind, d.d_out, d.d_in, d.w = HEAR_LAYER_FC, W.shape[0], W.shape[1], _p(W, _dp)
+            if len(layer) > 2 and layer[2] is not None:
+                b = _arr(layer[2], np.float64).reshape(-1)
+                if b.size != W.shape[0]:
+                    raise ValueError("FC bias needs d_out values")
+                keep.append(b)
+                d.bias = _p(b, _dp)
         elif layer[0] == "square":
             d.kind = HEAR_LAYER_SQUARE
         elif layer[0] == "fc_sq_fc":
@@ -450,7 +456,7 @@ def _layer_descs(layers):
 
 def hear_model_create(ctx, layers, clip_dim, level=None, rotsum_radix=None, fc_n1=None, hoist_moddown=False,
                       hoist_sums=False):
-    """layers: sequence of ("fc", W) | ("square",) | ("fc_sq_fc", W1, W2) with float64 matrices;
+    """layers: sequence of ("fc", W[, bias]) | ("square",) | ("fc_sq_fc", W1, W2) with float64 matrices;
     level: input level (None = the top level); rotsum_radix, fc_n1, hoist_moddown, hoist_sums:
     see hear_model_opts"""
     descs, keep = _layer_descs(layers)

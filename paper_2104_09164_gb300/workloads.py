@@ -64,6 +64,8 @@ class Workload:
         for layer in self.layers:
             if layer[0] == "fc":
                 h = h @ layer[1].T
+                if len(layer) > 2 and layer[2] is not None:
+                    h = h + layer[2]
             elif layer[0] == "square":
                 h = h * h
             elif layer[0] == "fc_sq_fc":

@@ -656,3 +656,27 @@ def test_hoisted_sums_fc_and_rotsum():
         got = o.decrypt(keys, r_hs)[::k][:16]
         assert np.max(np.abs(got - want)) < 2.0 ** -20, (n1, radix, dh)
         assert np.max(np.abs(got - o.decrypt(keys, r)[::k][:16])) < 2.0 ** -20
+
+
+def test_fc_bias_is_added_after_the_rotate_and_sum():
+    """an FC layer with bias decrypts to W x + b in every replicated position (the bias is
+    not multiplied by the rotate-and-sum's copy count); the residues differ from the bias-free
+    layer by exactly the encoded bias plaintext"""
+    from oracle import oracle as O
+    o = O.Oracle(12, [50, 40, 40], [50], 3.2)
+    S = o.n // 2
+    rng = np.random.default_rng(28)
+    k = 16
+    M = S // k
+    W = rng.normal(0, 0.1, size=(16, M))
+    b = rng.normal(0, 0.3, 16)
+    keys = o.keygen(29, [O.galois_for_step(s, o.n) for s in O.rotation_steps([("fc", W)], M, k)])
+    x = rng.uniform(-1, 1, M)
+    ct = o.encrypt(keys.pk, np.repeat(x, k), 14, 0, 2.0 ** 40)
+    r_b = o.fc(ct, W, k, keys, bias=b)
+    r = o.fc(ct, W, k, keys)
+    got = o.decrypt(keys, r_b)
+    want = np.repeat((W @ x + b)[np.arange(M) % 16], k)
+    assert np.max(np.abs(got - want)) < 2.0 ** -20
+    pt = o.encode_pt(o.expand(b[np.arange(M) % 16], k), r.scale, r.level)
+    assert np.array_equal(r_b.data, o.add_plain(r, pt).data) and r_b.scale == r.scale
