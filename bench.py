@@ -889,6 +889,9 @@ def main_gpu(a):
             "ntt": {"achieved_gbs": by_ntt / (ms_ntt / 1e3) / 1e9 if ms_ntt else None,
                     "launches_per_step": nl_ntt / psteps, "share": ms_ntt / total_stage_ms},
             "stages_ms_per_step": {k: v[1] / psteps for k, v in sorted(stages.items(), key=lambda kv: -kv[1][1])},
+            # algorithmic bytes / stage time (each residue a stage must read or write, once)
+            "stages_algorithmic_gbs": {k: v[2] / (v[1] / 1e3) / 1e9 for k, v in stages.items() if v[1] > 0},
+            "stages_launches_per_step": {k: v[0] / psteps for k, v in stages.items()},
             "clocks": clocks, "gpu_launches": launches,
         }
         # the NTT launch-variant table this run used (pin it with HEAR_NTT_TABLE to profile

@@ -133,6 +133,8 @@ void keygen(hear_context *c, uint64_t seed, const int32_t *steps, size_t n_steps
             automorphism(c, nqp - 1, dnum * 2, galois_inverse(c, g), key.u64(), perm.u64(), st);
             key = std::move(perm);
         }
+        // the inner product reads the words of the limbs below 2^42 in two pieces
+        split_pieces(c, key.u64(), dnum * 2 * nqp, km, true, st);
         evk->keys.emplace(g, std::move(key));
     }
     HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
@@ -394,6 +396,9 @@ void build_fc(hear_context *c, hear_model::Fc &fc, const double *W, uint32_t d_o
         }
         HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
     }
+    // the inner sums read the words of the limbs below 2^42 in two pieces
+    split_pieces(c, fc.pts.u64(), fc.n2 * n1 * L1, pmap, true, st);
+    HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
     fc.rotsum = rotsum_rounds(d_out, d_in / d_out, k, radix);
 }
 
@@ -425,10 +430,10 @@ void rotsum(hear_context *c, const hear_eval_keys *evk, uint32_t level, uint32_t
         }
         const uint32_t R = (uint32_t)rots.size();
         if (pmod) {
-            DevBuf r((size_t)R * batch_e * 8, st), acc((size_t)batch_e * 8, st), tmp((size_t)batch * 8, st);
+            // ModDown(P x + sum_s r_s) = x + ModDown(sum_s r_s): the sum is read by the ModDown
+            DevBuf r((size_t)R * batch_e * 8, st), tmp((size_t)batch * 8, st);
             rotate_hoisted_ext(c, level, n_ct, x, rots, r.u64(), pmod, st);
-            sum_ext(c, level, 2 * n_ct, r.u64(), batch_e, R, x, nullptr, acc.u64(), pmod, st);
-            moddown(c, level, n_ct, acc.u64(), x, nullptr, 0, 0u, false, nullptr, 1, tmp.u64(), st);
+            moddown(c, level, n_ct, r.u64(), x, x, ctw, 3u, false, nullptr, 1, tmp.u64(), st, R, batch_e);
             continue;
         }
         DevBuf r((size_t)R * batch * 8, st);
@@ -453,7 +458,10 @@ DevBuf eval_fc(const hear_model *m, const hear_model::Fc &fc, const hear_eval_ke
     const uint32_t W = L1 + c->K;
     const uint64_t batch_e = (uint64_t)n_ct * 2 * W * n;
     DevBuf G((size_t)n2 * batch * 8, st);
-    DevBuf G0e;   // hoisted sums with hoisted ModDown: inner sum 0 over Q_l u P
+    // hoisted sums: the giant rotations over Q_l u P in slots 1 .. n2-1 of Re (slot 0: inner
+    // sum 0 over Q_l u P with hoisted ModDown of the babies), ModDowned together
+    DevBuf Re;
+    if (pmod && n2 > 1) Re = DevBuf((size_t)n2 * batch_e * 8, st);
     if (fc.dh) {
         // hoisted ModDown: the babies stay over Q_l u P (slot 0 = P x), the inner sums are
         // formed there with plaintexts over Q_l u P, and each giant-step sum is ModDowned
@@ -467,8 +475,7 @@ DevBuf eval_fc(const hear_model *m, const hear_model::Fc &fc, const hear_eval_ke
             // inner sums j >= 1 back to Q_l (they are rotated next); inner sum 0 stays extended
             moddown(c, level, (n2 - 1) * n_ct, Ge.u64() + batch_e, G.u64() + batch, nullptr, 0, 0u, false, nullptr, 1,
                     tmp.u64(), st);
-            G0e = DevBuf((size_t)batch_e * 8, st);
-            HEAR_CHECK_CUDA(cudaMemcpyAsync(G0e.p, Ge.p, batch_e * 8, cudaMemcpyDeviceToDevice, st));
+            HEAR_CHECK_CUDA(cudaMemcpyAsync(Re.p, Ge.p, batch_e * 8, cudaMemcpyDeviceToDevice, st));
         } else {
             moddown(c, level, n2 * n_ct, Ge.u64(), G.u64(), nullptr, 0, 0u, false, nullptr, 1, tmp.u64(), st);
         }
@@ -489,11 +496,14 @@ DevBuf eval_fc(const hear_model *m, const hear_model::Fc &fc, const hear_eval_ke
             gr.push_back(Rot{need_key(evk, g), g});
         }
         if (pmod) {
-            DevBuf Re((size_t)(n2 - 1) * batch_e * 8, st), acc((size_t)batch_e * 8, st), tmp((size_t)batch * 8, st);
-            rotate_each_ext(c, level, n2 - 1, n_ct, G.u64() + batch, gr, Re.u64(), pmod, st);
-            if (fc.dh) sum_ext(c, level, 2 * n_ct, Re.u64(), batch_e, n2 - 1, nullptr, G0e.u64(), acc.u64(), pmod, st);
-            else sum_ext(c, level, 2 * n_ct, Re.u64(), batch_e, n2 - 1, G.u64(), nullptr, acc.u64(), pmod, st);
-            moddown(c, level, n_ct, acc.u64(), G.u64(), nullptr, 0, 0u, false, nullptr, 1, tmp.u64(), st);
+            DevBuf tmp((size_t)batch * 8, st);
+            rotate_each_ext(c, level, n2 - 1, n_ct, G.u64() + batch, gr, Re.u64() + batch_e, pmod, st);
+            if (fc.dh)   // ModDown(inner sum 0 + sum_j r_j), inner sum 0 over Q_l u P in slot 0
+                moddown(c, level, n_ct, Re.u64(), G.u64(), nullptr, 0, 0u, false, nullptr, 1, tmp.u64(), st, n2,
+                        batch_e);
+            else         // inner sum 0 over Q_l: G_0 + ModDown(sum_j r_j)
+                moddown(c, level, n_ct, Re.u64() + batch_e, G.u64(), G.u64(), ctw, 3u, false, nullptr, 1, tmp.u64(),
+                        st, n2 - 1, batch_e);
         } else {
             DevBuf R((size_t)(n2 - 1) * batch * 8, st);
             rotate_each(c, level, n2 - 1, n_ct, G.u64() + batch, gr, R.u64(), st);

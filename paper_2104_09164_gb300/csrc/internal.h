@@ -252,9 +252,11 @@ void ntt_inverse(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, Limb
 void ntt_forward_pro(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, LimbMap map, const uint64_t *pro,
                      uint64_t pro_gstride, cudaStream_t s, uint64_t pro_center = 0);
 // inverse NTT from src (limb b of group g at src + g * src_gstride + b' * N) into data (the
-// layout of `map`, contiguous groups); src is left unchanged
+// layout of `map`, contiguous groups); src is left unchanged.  src_count > 1: the transform of
+// the sum mod q of src_count sources, source r at src + r * src_cstride
 void ntt_inverse_from(const hear_context *ctx, const uint64_t *src, uint64_t src_gstride, uint64_t *data,
-                      uint32_t n_limbs, LimbMap map, cudaStream_t s);
+                      uint32_t n_limbs, LimbMap map, cudaStream_t s, uint32_t src_count = 1,
+                      uint64_t src_cstride = 0);
 // butterflies per second of the transforms' register-resident arithmetic (forward or
 // inverse) over the context's prime mix, iters rounds of four radix-16 stages per thread
 double bfly_peak(const hear_context *ctx, bool fwd, uint32_t iters);

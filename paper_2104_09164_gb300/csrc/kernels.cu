@@ -18,14 +18,6 @@ constexpr int kBlock = 256;
 inline dim3 grid3(uint32_t n, uint32_t ny, uint32_t nz) { return dim3(n / kBlock, ny, nz); }
 #define COEF() (blockIdx.x * kBlock + threadIdx.x)
 
-// NTT-domain index of sigma_g: (sigma_g a)[i] = a[auto_index(i, g)]
-__device__ __forceinline__ uint32_t auto_index(uint32_t i, uint32_t galois, uint32_t log_n) {
-    const uint32_t n2 = 2u << log_n;
-    uint32_t e = 2 * (__brev(i) >> (32 - log_n)) + 1;
-    uint32_t e2 = (uint32_t)(((uint64_t)e * galois) & (n2 - 1));
-    return __brev((e2 - 1) >> 1) >> (32 - log_n);
-}
-
 // limb index of a LimbMap launch: y + z * gridDim.y
 __device__ __forceinline__ uint32_t limb_yz() { return blockIdx.y + blockIdx.z * gridDim.y; }
 
@@ -203,26 +195,6 @@ __global__ void k_sum(const uint64_t *a, uint64_t stride, uint32_t cnt, const ui
     out[i] = s;
 }
 
-// out [.][W][N] over Q_l u P = B + sum_{j < cnt} a[j * stride]: B = [P]_{q_t} x_t on the Q
-// limbs and 0 on the special limbs (x over Q_l, [.][L1][N]; pmod = ([P]_{q_t}, Shoup) pairs),
-// or B = b (over Q_l u P), or 0.  y = limb t of W, z = polynomial.
-__global__ void k_sum_ext(const uint64_t *a, uint64_t stride, uint32_t cnt, const uint64_t *x, const uint64_t *b,
-                          uint64_t *out, uint32_t L1, uint32_t W, const uint64_t *pmod, const DevPrime *P,
-                          uint32_t n_q, uint32_t n) {
-    pdl_enter();
-    const uint32_t t = blockIdx.y, g = blockIdx.z, k = COEF();
-    const uint64_t i = ((uint64_t)g * W + t) * n + k;
-    const uint64_t q = P[t < L1 ? t : n_q + (t - L1)].q;
-    uint64_t v = 0;
-    if (x) {
-        if (t < L1) v = shoup(x[((uint64_t)g * L1 + t) * n + k], pmod[2 * t], pmod[2 * t + 1], q);
-    } else if (b) {
-        v = b[i];
-    }
-    for (uint32_t j = 0; j < cnt; j++) v = add_mod(v, a[j * stride + i], q);
-    out[i] = v;
-}
-
 // y = limb t, z = ciphertext
 __global__ void k_tensor(const uint64_t *a, const uint64_t *b, uint64_t *out, uint32_t L1, const DevPrime *P,
                          uint32_t n) {
@@ -286,6 +258,58 @@ __device__ __forceinline__ void fold(u128 &acc, uint64_t q) {
     if (acc.hi >= q) acc.hi -= q;
 }
 
+// Piece-wise products for the primes below 2^42 (the 40-bit chain primes).  Switching-key and
+// diagonal-plaintext words of such limbs are stored as their two 21-bit pieces, y0 | y1 << 32
+// (y = y0 + 2^21 y1, still Montgomery form); a residue x < 2^42 is cut the same way at run
+// time.  A product is then three 32 x 32 -> 64-bit multiply-adds (Karatsuba):
+//   A0 += x0 y0,  A2 += x1 y1,  Am += (x0 + x1)(y0 + y1),
+// and a sum of products is S = A0 + (Am - A0 - A2) 2^21 + A2 2^42 exactly (each term of Am is
+// below 2^44, so each A stays below 2^64 for fewer than 2^20 terms, and S below q 2^64),
+// reduced once by the same Montgomery step as the 64-bit products:
+// the residues are identical, with three multiply-pipe instructions per product instead of
+// eight 32-bit multiply-adds.
+constexpr uint64_t kPieceBelow = 1ull << 42;
+constexpr uint64_t kPieceMask = (1ull << 21) - 1;
+struct Acc3 {
+    uint64_t a0, am, a2;
+};
+__device__ __forceinline__ void mad_wide(uint64_t &acc, uint32_t a, uint32_t b) {
+    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
+}
+struct Pieces {
+    uint32_t x0, x1, xs;
+};
+__device__ __forceinline__ Pieces cut(uint64_t x) {
+    Pieces p;
+    p.x0 = (uint32_t)(x & kPieceMask);
+    p.x1 = (uint32_t)(x >> 21);
+    p.xs = p.x0 + p.x1;
+    return p;
+}
+__device__ __forceinline__ void mac_pieces(Acc3 &acc, const Pieces &x, uint64_t y) {
+    const uint32_t y0 = (uint32_t)y, y1 = (uint32_t)(y >> 32);
+    mad_wide(acc.a0, x.x0, y0);
+    mad_wide(acc.a2, x.x1, y1);
+    mad_wide(acc.am, x.xs, y0 + y1);
+}
+__device__ __forceinline__ uint64_t reduce_pieces(const Acc3 &a, uint64_t q, uint64_t qinv) {
+    const uint64_t a1 = a.am - a.a0 - a.a2;
+    u128 s{a.a0, 0};
+    add_to(s, u128{a1 << 21, a1 >> 43});
+    add_to(s, u128{a.a2 << 42, a.a2 >> 22});
+    return mont_reduce(s, q, qinv);
+}
+
+// y <-> y0 | y1 << 32 for every word of the limbs whose prime is below 2^42
+__global__ void k_split_pieces(uint64_t *d, uint32_t n_limbs, LimbMap m, const DevPrime *P, uint32_t n, int to_split) {
+    pdl_enter();
+    uint32_t b = limb_yz(), pi;
+    if (b >= n_limbs || !m.resolve(b, &pi)) return;
+    if (P[pi].q >= kPieceBelow) return;
+    uint64_t &x = d[m.offset(b, n) + COEF()];
+    x = to_split ? ((x & kPieceMask) | ((x >> 21) << 32)) : ((x & 0xffffffffull) | ((x >> 32) << 21));
+}
+
 // BSGS inner sums out[j][c] = sum_b pt[j][b] (.) baby[b][c] on contiguous storage:
 // baby [n1][C][2][L1][N], pt [n2*n1][L1][N] (Montgomery), out [n2][C][2][L1][N].
 // CTA = 8 warps, each one polynomial (c, poly) of the batch; lanes over 32 consecutive
@@ -297,10 +321,10 @@ __device__ __forceinline__ void fold(u128 &acc, uint64_t q) {
 // jw = 8 / 2C warps then share each polynomial, warp w taking polynomial w mod 2C and the
 // giant-step chunks (JC outputs each) jpart, jpart + jw, .. with jpart = w / 2C.
 // Limbs t >= lq are over the special primes (inner sums over Q_l u P): prime n_q + t - lq.
-// JC = giant-step outputs accumulated per pass over the babies (4, or 8 with the registers of
-// two CTAs per SM)
+// JC = giant-step outputs accumulated per pass over the babies (4 with the registers of three
+// CTAs per SM, or 8 with those of two)
 template <int JC>
-__global__ void __launch_bounds__(256, JC == 4 ? 4 : 2) k_lincomb(uint32_t L1, uint32_t C, uint32_t n1, uint32_t n2,
+__global__ void __launch_bounds__(256, JC == 4 ? 3 : 2) k_lincomb(uint32_t L1, uint32_t C, uint32_t n1, uint32_t n2,
                                                  const uint64_t *__restrict__ baby, const uint64_t *__restrict__ pt,
                                                  uint64_t *__restrict__ out, const DevPrime *P, uint32_t n,
                                                  uint32_t jw, uint32_t lq, uint32_t n_q) {
@@ -322,6 +346,32 @@ __global__ void __launch_bounds__(256, JC == 4 ? 4 : 2) k_lincomb(uint32_t L1, u
     const uint64_t q = P[pi].q, qinv = P[pi].qinv;
     const uint64_t bstride = 2ull * C * plane;                    // between baby steps / giant outputs
     const uint64_t *bp = baby + (uint64_t)cp * plane + r;
+    if (q < kPieceBelow) {
+        // plaintext words in pieces (see kPieceBelow)
+        for (uint32_t j0 = JC * jpart; j0 < n2; j0 += JC * jw) {
+            Acc3 acc[JC];
+#pragma unroll
+            for (int jj = 0; jj < JC; jj++) acc[jj] = Acc3{0, 0, 0};
+            const uint64_t *pp = pt + ((uint64_t)j0 * n1) * plane + r;
+            const uint32_t jn = min((uint32_t)JC, n2 - j0);
+#pragma unroll 2
+            for (uint32_t b = 0; b < n1; b++) {
+                const Pieces x = cut(bp[(uint64_t)b * bstride]);
+                uint64_t w[JC];
+#pragma unroll
+                for (int jj = 0; jj < JC; jj++)
+                    if (jj < (int)jn) w[jj] = __ldg(pp + ((uint64_t)jj * n1 + b) * plane);
+#pragma unroll
+                for (int jj = 0; jj < JC; jj++)
+                    if (jj < (int)jn) mac_pieces(acc[jj], x, w[jj]);
+            }
+            uint64_t *op = out + (uint64_t)j0 * bstride + (uint64_t)cp * plane + r;
+#pragma unroll
+            for (int jj = 0; jj < JC; jj++)
+                if (j0 + jj < n2) op[(uint64_t)jj * bstride] = reduce_pieces(acc[jj], q, qinv);
+        }
+        return;
+    }
     for (uint32_t j0 = JC * jpart; j0 < n2; j0 += JC * jw) {
         u128 acc[JC];
 #pragma unroll
@@ -458,6 +508,7 @@ __global__ void __launch_bounds__(256, MINB) k_ks_inner(const uint64_t *ext, int
     const uint32_t g = ginv[r];
     const uint32_t kk = g == 1 ? k : auto_index(k, g, log_n);
     const uint64_t ext_ct = (uint64_t)dnum * W * n, out_ct = 2ull * W * n;
+    const bool pieces = q < kPieceBelow;   // key words in pieces (see kPieceBelow)
     for (uint32_t c = c_begin; c < c_end; c++) {
         const uint64_t cti = ext_per_job ? (uint64_t)r * C + c : c;
         const uint64_t *e = ext + cti * ext_ct + (uint64_t)t * n + k;
@@ -466,27 +517,43 @@ __global__ void __launch_bounds__(256, MINB) k_ks_inner(const uint64_t *ext, int
         for (int j = 0; j < MAXD; j++)      // all digit loads issued before the products
             if (j < (int)dnum) xs[j] = (OWN && j == (int)t) ? own[cti * own_stride + (uint64_t)t * n + k]
                                                             : e[(uint64_t)j * W * n];
-        u128 a0{0, 0}, a1{0, 0};
+        uint64_t v0, v1;
+        if (pieces) {
+            Acc3 a0{0, 0, 0}, a1{0, 0, 0};
 #pragma unroll
-        for (int j = 0; j < MAXD; j++) {
-            if (j < (int)dnum) {
-                mac_raw(a0, xs[j], k0[j]);
-                mac_raw(a1, xs[j], k1[j]);
-                if ((j & 7) == 7) {
-                    fold(a0, q);
-                    fold(a1, q);
+            for (int j = 0; j < MAXD; j++) {
+                if (j < (int)dnum) {
+                    const Pieces x = cut(xs[j]);
+                    mac_pieces(a0, x, k0[j]);
+                    mac_pieces(a1, x, k1[j]);
                 }
             }
+            v0 = reduce_pieces(a0, q, qinv);
+            v1 = reduce_pieces(a1, q, qinv);
+        } else {
+            u128 a0{0, 0}, a1{0, 0};
+#pragma unroll
+            for (int j = 0; j < MAXD; j++) {
+                if (j < (int)dnum) {
+                    mac_raw(a0, xs[j], k0[j]);
+                    mac_raw(a1, xs[j], k1[j]);
+                    if ((j & 7) == 7) {
+                        fold(a0, q);
+                        fold(a1, q);
+                    }
+                }
+            }
+            fold(a0, q);
+            fold(a1, q);
+            v0 = mont_reduce(a0, q, qinv);
+            v1 = mont_reduce(a1, q, qinv);
         }
-        fold(a0, q);
-        fold(a1, q);
         uint64_t *o = out + ((uint64_t)r * C + c) * out_ct + (uint64_t)t * n + kk;
-        uint64_t v0 = mont_reduce(a0, q, qinv);
         // pc0 (outputs kept over Q_l u P): + P sigma_g(c0) = P c0[k] at position kk
         if (pc0 && t < L1) v0 = add_mod(v0, shoup(pc0[cti * own_stride + (uint64_t)t * n + k], pmod[2 * t],
                                                   pmod[2 * t + 1], q), q);
         o[0] = v0;
-        o[(uint64_t)W * n] = mont_reduce(a1, q, qinv);
+        o[(uint64_t)W * n] = v1;
     }
 }
 
@@ -509,6 +576,7 @@ __global__ void __launch_bounds__(256, 3) k_ks_inner_rj(const uint64_t *ext, con
 #pragma unroll
     for (int j = 0; j < MAXD; j++)
         if (j < (int)dnum) xs[j] = (OWN && j == (int)t) ? own[(uint64_t)t * n + k] : e[(uint64_t)j * W * n];
+    const bool pieces = q < kPieceBelow;   // key words in pieces (see kPieceBelow)
 #pragma unroll 1
     for (int rr = 0; rr < RJ; rr++) {
         const uint32_t r = r0 + rr;
@@ -522,27 +590,43 @@ __global__ void __launch_bounds__(256, 3) k_ks_inner_rj(const uint64_t *ext, con
                 k1[j] = __ldg(key + (uint64_t)j * 2 * key_plane + key_plane);
             }
         }
-        u128 a0{0, 0}, a1{0, 0};
+        uint64_t v0, v1;
+        if (pieces) {
+            Acc3 a0{0, 0, 0}, a1{0, 0, 0};
 #pragma unroll
-        for (int j = 0; j < MAXD; j++) {
-            if (j < (int)dnum) {
-                mac_raw(a0, xs[j], k0[j]);
-                mac_raw(a1, xs[j], k1[j]);
-                if ((j & 7) == 7) {
-                    fold(a0, q);
-                    fold(a1, q);
+            for (int j = 0; j < MAXD; j++) {
+                if (j < (int)dnum) {
+                    const Pieces x = cut(xs[j]);
+                    mac_pieces(a0, x, k0[j]);
+                    mac_pieces(a1, x, k1[j]);
                 }
             }
+            v0 = reduce_pieces(a0, q, qinv);
+            v1 = reduce_pieces(a1, q, qinv);
+        } else {
+            u128 a0{0, 0}, a1{0, 0};
+#pragma unroll
+            for (int j = 0; j < MAXD; j++) {
+                if (j < (int)dnum) {
+                    mac_raw(a0, xs[j], k0[j]);
+                    mac_raw(a1, xs[j], k1[j]);
+                    if ((j & 7) == 7) {
+                        fold(a0, q);
+                        fold(a1, q);
+                    }
+                }
+            }
+            fold(a0, q);
+            fold(a1, q);
+            v0 = mont_reduce(a0, q, qinv);
+            v1 = mont_reduce(a1, q, qinv);
         }
-        fold(a0, q);
-        fold(a1, q);
         const uint32_t g = ginv[r];
         const uint32_t kk = g == 1 ? k : auto_index(k, g, log_n);
         uint64_t *o = out + (uint64_t)r * out_ct + (uint64_t)t * n + kk;
-        uint64_t v0 = mont_reduce(a0, q, qinv);
         if (pc0 && t < L1) v0 = add_mod(v0, shoup(pc0[(uint64_t)t * n + k], pmod[2 * t], pmod[2 * t + 1], q), q);
         o[0] = v0;
-        o[(uint64_t)W * n] = mont_reduce(a1, q, qinv);
+        o[(uint64_t)W * n] = v1;
     }
 }
 
@@ -559,7 +643,8 @@ __global__ void k_scale_p_ext(const uint64_t *x, uint64_t *out, uint32_t L1, uin
 // ModDown conversion, one thread per (group = y + z*gridDim.y, coefficient):
 // y_k = [x_{p_k} * phat_inv_k]_{p_k} once, conv_i = sum_k y_k * [P/p_k]_{q_i} mod q_i for
 // every i < L1 (x_P in the coefficient domain).
-__global__ void k_moddown_conv(const uint64_t *acc, uint64_t *tmp, uint32_t n_groups, uint32_t L1, uint32_t W,
+// the P limbs of group g: xp + g * xp_gstride + kk * n (coefficient domain)
+__global__ void k_moddown_conv(const uint64_t *xp, uint64_t xp_gstride, uint64_t *tmp, uint32_t n_groups, uint32_t L1,
                                uint32_t K, uint32_t n_q, const uint64_t *phat_inv, const uint64_t *phat_mod,
                                const DevPrime *P, uint32_t n) {
     pdl_enter();
@@ -570,7 +655,8 @@ __global__ void k_moddown_conv(const uint64_t *acc, uint64_t *tmp, uint32_t n_gr
     for (int kk = 0; kk < 4; kk++) {
         if (kk < (int)K) {
             const DevPrime pk = P[n_q + kk];
-            ys[kk] = shoup(acc[((uint64_t)g * W + L1 + kk) * n + k], phat_inv[2 * kk], phat_inv[2 * kk + 1], pk.q);
+            ys[kk] = shoup(xp[(uint64_t)g * xp_gstride + (uint64_t)kk * n + k], phat_inv[2 * kk], phat_inv[2 * kk + 1],
+                           pk.q);
         }
     }
     for (uint32_t t = 0; t < L1; t++) {
@@ -587,16 +673,19 @@ __global__ void k_moddown_conv(const uint64_t *acc, uint64_t *tmp, uint32_t n_gr
     }
 }
 
-// out = (x_i - conv_i) * P^-1 (+ addend gathered through sigma_g); y = limb, z = group
+// out = (x_i - conv_i) * P^-1 (+ addend gathered through sigma_g); y = limb, z = group.
+// acc_count > 1: x is the sum mod q_t of acc_count inputs, input r at acc + r * acc_cstride
 __global__ void k_moddown_combine(const uint64_t *acc, const uint64_t *tmp, uint64_t *out, const uint64_t *addend,
                                   uint64_t add_stride, uint32_t add_mask, uint32_t add_shared, const uint32_t *gal,
                                   uint32_t cts_per_job, uint32_t L1, uint32_t W, const uint64_t *p_inv,
-                                  const DevPrime *P, uint32_t log_n) {
+                                  const DevPrime *P, uint32_t log_n, uint32_t acc_count, uint64_t acc_cstride) {
     pdl_enter();
     const uint32_t n = 1u << log_n, k = COEF(), t = blockIdx.y, g = blockIdx.z;
     const DevPrime p = P[t];
     const uint64_t i = ((uint64_t)g * L1 + t) * n + k;
-    const uint64_t x = acc[((uint64_t)g * W + t) * n + k];
+    const uint64_t ai = ((uint64_t)g * W + t) * n + k;
+    uint64_t x = acc[ai];
+    for (uint32_t r = 1; r < acc_count; r++) x = add_mod(x, acc[r * acc_cstride + ai], p.q);
     uint64_t v = shoup(x + p.q - tmp[i], p_inv[2 * t], p_inv[2 * t + 1], p.q);
     const uint32_t poly = g & 1, c = g >> 1;
     if (addend && (add_mask >> poly & 1)) {
@@ -649,6 +738,12 @@ uint32_t ks_form(const hear_context *c, int tab, uint32_t n) {
         launch(kernel, grid, block, 0, st, __VA_ARGS__);                                   \
     } while (0)
 
+void split_pieces(const hear_context *c, uint64_t *d, uint32_t n_limbs, LimbMap m, bool to_split, cudaStream_t s) {
+    uint32_t ny, nz;
+    split_yz(n_limbs, ny, nz);
+    LAUNCH3(k_split_pieces, grid3(c->n, ny, nz), kBlock, s, 16.0 * n_limbs * c->n, d, n_limbs, m, c->dev_primes(),
+            c->n, to_split ? 1 : 0);
+}
 void to_mont(const hear_context *c, uint64_t *d, uint32_t n_limbs, LimbMap m, cudaStream_t s) {
     uint32_t ny, nz;
     split_yz(n_limbs, ny, nz);
@@ -891,15 +986,6 @@ void ks_inner(const hear_context *c, uint32_t level, uint32_t R, uint32_t C, con
 #undef KS_RJ
 }
 
-void sum_ext(const hear_context *c, uint32_t level, uint32_t n_polys, const uint64_t *a, uint64_t stride,
-             uint32_t cnt, const uint64_t *x, const uint64_t *b, uint64_t *out, const uint64_t *pmod, cudaStream_t st) {
-    const uint32_t L1 = level + 1, W = L1 + c->K;
-    check_yz(W, n_polys);
-    const double base = x ? (double)L1 : (b ? (double)W : 0.0);
-    LAUNCH3(k_sum_ext, grid3(c->n, W, n_polys), kBlock, st, 8.0 * n_polys * c->n * (base + (double)(cnt + 1) * W),
-            a, stride, cnt, x, b, out, L1, W, pmod, c->dev_primes(), c->n_q, c->n);
-}
-
 void scale_p_ext(const hear_context *c, uint32_t level, uint32_t n_polys, const uint64_t *x, uint64_t *out,
                  const uint64_t *pmod, cudaStream_t st) {
     const uint32_t L1 = level + 1, W = L1 + c->K;
@@ -909,33 +995,51 @@ void scale_p_ext(const hear_context *c, uint32_t level, uint32_t n_polys, const 
 }
 void moddown(const hear_context *c, uint32_t level, uint32_t n_ct, uint64_t *acc, uint64_t *out,
              const uint64_t *addend, uint64_t add_stride, uint32_t add_mask, bool add_shared, const uint32_t *d_gal,
-             uint32_t cts_per_job, uint64_t *tmp, cudaStream_t st) {
+             uint32_t cts_per_job, uint64_t *tmp, cudaStream_t st, uint32_t acc_count, uint64_t acc_cstride) {
     const uint32_t L1 = level + 1, W = L1 + c->K, groups = n_ct * 2;
     const LevelConsts &lc = *c->levels[level];
     HEAR_REQUIRE(c->K <= 4, HEAR_E_UNSUPPORTED, "at most 4 special primes");
-    LimbMap pm;
-    pm.per_group = c->K;
-    pm.q_count = 0;
-    pm.n_q = c->n_q;
-    pm.group_stride = (uint64_t)W * c->n;
-    ntt_inverse(c, acc + (uint64_t)L1 * c->n, groups * c->K, pm, st);
+    HEAR_REQUIRE(acc_count >= 1, HEAR_E_INVAL, "ModDown of no input");
+    // the P limbs in the coefficient domain: in place (one input) or, for a sum of inputs,
+    // the inverse transform of their sum into a buffer of its own
+    const uint64_t *xp = acc + (uint64_t)L1 * c->n;
+    uint64_t xp_gstride = (uint64_t)W * c->n;
+    DevBuf psum;
+    if (acc_count == 1) {
+        LimbMap pm;
+        pm.per_group = c->K;
+        pm.q_count = 0;
+        pm.n_q = c->n_q;
+        pm.group_stride = (uint64_t)W * c->n;
+        ntt_inverse(c, acc + (uint64_t)L1 * c->n, groups * c->K, pm, st);
+    } else {
+        LimbMap pm;
+        pm.per_group = c->K;
+        pm.q_count = 0;
+        pm.n_q = c->n_q;
+        psum = DevBuf((size_t)groups * c->K * c->n * 8, st);
+        ntt_inverse_from(c, acc + (uint64_t)L1 * c->n, (uint64_t)W * c->n, psum.u64(), groups * c->K, pm, st, acc_count,
+                         acc_cstride);
+        xp = psum.u64();
+        xp_gstride = (uint64_t)c->K * c->n;
+    }
     if (c->K == 1) {
         // one special prime: the conversion P -> q_t is [x_P]_t, folded into the load of the
         // forward transform
-        ntt_forward_pro(c, tmp, groups * L1, map_q(level, c->n_q), acc + (uint64_t)L1 * c->n, (uint64_t)W * c->n,
-                        st);
+        ntt_forward_pro(c, tmp, groups * L1, map_q(level, c->n_q), xp, xp_gstride, st);
     } else {
-    uint32_t ny, nz;
-    split_yz(groups, ny, nz);
-    LAUNCH3(k_moddown_conv, grid3(c->n, ny, nz), kBlock, st, 8.0 * groups * ((double)c->K + L1) * c->n, acc, tmp,
-            groups, L1, W, c->K, c->n_q, lc.d.u64() + lc.off_phat_inv, lc.d.u64() + lc.off_phat_mod, c->dev_primes(),
-            c->n);
-    ntt_forward(c, tmp, groups * L1, map_q(level, c->n_q), st);
+        uint32_t ny, nz;
+        split_yz(groups, ny, nz);
+        LAUNCH3(k_moddown_conv, grid3(c->n, ny, nz), kBlock, st, 8.0 * groups * ((double)c->K + L1) * c->n, xp,
+                xp_gstride, tmp, groups, L1, c->K, c->n_q, lc.d.u64() + lc.off_phat_inv, lc.d.u64() + lc.off_phat_mod,
+                c->dev_primes(), c->n);
+        ntt_forward(c, tmp, groups * L1, map_q(level, c->n_q), st);
     }
     check_yz(L1, groups);
     LAUNCH3(k_moddown_combine, grid3(c->n, L1, groups), kBlock, st,
-            8.0 * groups * L1 * c->n * (3.0 + (addend ? 1.0 : 0.0)), acc, tmp, out, addend, add_stride, add_mask,
-            (uint32_t)add_shared, d_gal, cts_per_job, L1, W, lc.d.u64() + lc.off_p_inv, c->dev_primes(), c->log_n);
+            8.0 * groups * L1 * c->n * (2.0 + acc_count + (addend ? 1.0 : 0.0)), acc, tmp, out, addend, add_stride,
+            add_mask, (uint32_t)add_shared, d_gal, cts_per_job, L1, W, lc.d.u64() + lc.off_p_inv, c->dev_primes(),
+            c->log_n, acc_count, acc_cstride);
 }
 
 void rescale(const hear_context *c, uint32_t level, uint32_t n_polys, uint64_t *in, uint64_t *out, uint64_t *tmp,

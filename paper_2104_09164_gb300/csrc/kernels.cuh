@@ -9,6 +9,9 @@ enum SmallKind { kTernary = 0, kGauss = 1 };
 // ---- representation changes ----
 void to_mont(const hear_context *c, uint64_t *d, uint32_t n_limbs, LimbMap m, cudaStream_t s);
 void from_mont(const hear_context *c, uint64_t *d, uint32_t n_limbs, LimbMap m, cudaStream_t s);
+// switching-key / diagonal-plaintext words of the limbs whose prime is below 2^42 to (or back
+// from) the two-piece form y0 | y1 << 32 the inner products read (kernels.cu, kPieceBelow)
+void split_pieces(const hear_context *c, uint64_t *d, uint32_t n_limbs, LimbMap m, bool to_split, cudaStream_t s);
 void small_to_limbs(const hear_context *c, const int8_t *e, uint64_t *out, uint32_t n_limbs, LimbMap m,
                     cudaStream_t s);
 void i64_to_limbs(const hear_context *c, const int64_t *v, uint64_t *out, uint32_t n_limbs, LimbMap m,
@@ -83,20 +86,17 @@ void ks_inner(const hear_context *c, uint32_t level, uint32_t R, uint32_t C, con
 // addend ciphertext (ciphertext index c, or c mod cts_per_job if add_shared, at addend +
 // index*add_stride, polys [2][l+1][N]; poly p only if add_mask bit p) gathered through
 // sigma_g with g = d_gal[c / cts_per_job] (d_gal null = identity).  tmp: n_ct*2*(l+1)*N words
+// acc_count > 1: the ModDown of the sum of acc_count such inputs, input r at acc + r * acc_cstride
+// (each left unchanged)
 void moddown(const hear_context *c, uint32_t level, uint32_t n_ct, uint64_t *acc, uint64_t *out,
              const uint64_t *addend, uint64_t add_stride, uint32_t add_mask, bool add_shared, const uint32_t *d_gal,
-             uint32_t cts_per_job, uint64_t *tmp, cudaStream_t st);
+             uint32_t cts_per_job, uint64_t *tmp, cudaStream_t st, uint32_t acc_count = 1, uint64_t acc_cstride = 0);
 // out = sum of cnt batches a + j*stride (n_polys_total polynomials at level)
 void sum_ct(const hear_context *c, uint32_t level, uint32_t n_polys_total, const uint64_t *a, uint64_t stride,
             uint32_t cnt, uint64_t *out, cudaStream_t st);
 // out = base + sum of cnt batches a + j*stride (out may alias base)
 void sum_add_ct(const hear_context *c, uint32_t level, uint32_t n_polys_total, const uint64_t *a, uint64_t stride,
                 uint32_t cnt, const uint64_t *base, uint64_t *out, cudaStream_t st);
-// out [n_polys][W][N] over Q_l u P = base + sum of cnt batches a + j*stride (W limbs each):
-// base = P x (x over Q_l, [n_polys][l+1][N]) if x, else b (over Q_l u P) if b, else 0;
-// pmod = ([P]_{q_t}, Shoup) pairs for t <= l (used with x)
-void sum_ext(const hear_context *c, uint32_t level, uint32_t n_polys, const uint64_t *a, uint64_t stride,
-             uint32_t cnt, const uint64_t *x, const uint64_t *b, uint64_t *out, const uint64_t *pmod, cudaStream_t st);
 // out = a (.) b_mont over n_limbs limbs (Montgomery product: a * b)
 void pointwise_mont(const hear_context *c, uint32_t n_limbs, LimbMap m, const uint64_t *a, const uint64_t *b_mont,
                     uint64_t *out, cudaStream_t st);

@@ -87,4 +87,13 @@ __device__ __forceinline__ uint64_t reduce64(uint64_t x, const DevPrime &p) {
     return shoup(x, 1, p.one_sh, p.q);
 }
 
+// NTT-domain index of sigma_g: (sigma_g a)[i] = a[auto_index(i, g)] (index i holds the
+// evaluation at psi^(2 brv(i) + 1))
+__device__ __forceinline__ uint32_t auto_index(uint32_t i, uint32_t galois, uint32_t log_n) {
+    const uint32_t n2 = 2u << log_n;
+    uint32_t e = 2 * (__brev(i) >> (32 - log_n)) + 1;
+    uint32_t e2 = (uint32_t)(((uint64_t)e * galois) & (n2 - 1));
+    return __brev((e2 - 1) >> 1) >> (32 - log_n);
+}
+
 }  // namespace hear

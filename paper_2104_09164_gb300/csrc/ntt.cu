@@ -34,6 +34,8 @@ struct PassArgs {
     // (b % per_group) * N instead of from data (out-of-place start), null = in place
     const uint64_t *src;
     uint64_t src_gstride;
+    uint32_t src_count;      // > 1: the first pass reads the sum mod q of src_count sources,
+    uint64_t src_cstride;    //   source r at src + r * src_cstride (same layout)
     // forward only: the first pass reads limb b's values from pro + (b / per_group) *
     // pro_gstride (coefficient domain, any residue below 2^64) reduced mod the limb's
     // prime -- a basis extension by one source limb folded into the transform's load
@@ -223,6 +225,22 @@ __device__ __forceinline__ void load_rows(uint64_t *s, const uint64_t *g) {
         }
     }
 }
+// s[i] += g[r * cstride + i] mod q for the sources r = 1 .. count - 1 of a tile load_rows read
+// from source 0 (the sum of several inputs folded into a transform's first load)
+template <int TILE, int THREADS>
+__device__ __forceinline__ void add_rows(uint64_t *s, const uint64_t *g, uint32_t count, uint64_t cstride, uint64_t q) {
+    constexpr int PER = TILE / 2 / THREADS;
+    for (uint32_t r = 1; r < count; r++) {
+        const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(g + r * cstride);
+#pragma unroll
+        for (int k = 0; k < PER; k++) {
+            const int i = threadIdx.x + k * THREADS;
+            const ulonglong2 v = src[i];
+            s[swz(2 * i)] = add_mod(s[swz(2 * i)], v.x, q);
+            s[swz(2 * i + 1)] = add_mod(s[swz(2 * i + 1)], v.y, q);
+        }
+    }
+}
 // the 2^LOGR pass-A twiddles (and companions) of a prime into shared memory
 template <int LOGR, int THREADS>
 __device__ __forceinline__ void load_twiddles(uint64_t *stw, const uint64_t *tw, const uint64_t *tws) {
@@ -277,7 +295,8 @@ __global__ void __launch_bounds__(Tile<LOGR, MODE>::THREADS, Tile<LOGR, MODE>::M
 }
 
 // Pass B: contiguous blocks of R words, stages s_off..s_off+LOGR-1.
-template <int LOGR, bool FWD, int MODE>
+// SUM (inverse): the first pass reads the sum of a.src_count sources
+template <int LOGR, bool FWD, int MODE, bool SUM = false>
 __global__ void __launch_bounds__(Tile<LOGR, MODE>::THREADS, Tile<LOGR, MODE>::MIN_CTAS) ntt_pass_b(PassArgs a,
                                                                                                uint32_t s_off) {
     pdl_enter();
@@ -298,6 +317,7 @@ __global__ void __launch_bounds__(Tile<LOGR, MODE>::THREADS, Tile<LOGR, MODE>::M
         gin = a.src + (uint64_t)(limb / a.map.per_group) * a.src_gstride + (uint64_t)(limb % a.map.per_group) * a.n +
               (size_t)tile * TILE;
     load_rows<TILE, THREADS>(s, gin);
+    if (!FWD && SUM) add_rows<TILE, THREADS>(s, gin, a.src_count, a.src_cstride, P.q);
     __syncthreads();
     const uint64_t *tw = a.tw + (size_t)pi * a.n, *tws = a.tw_sh + (size_t)pi * a.n;
     const bool small = P.q < a.small_below;
@@ -340,7 +360,8 @@ template <int LA, int LB, int CL> struct Fused {
     static_assert(CA >= 1 && SB >= 1, "cluster too large for this ring size");
 };
 
-template <int LA, int LB, bool FWD, int CL>
+// SUM: as for ntt_pass_b (inverse: summed sources)
+template <int LA, int LB, bool FWD, int CL, bool SUM = false>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(Fused<LA, LB, CL>::THREADS, 512 / Fused<LA, LB, CL>::THREADS)
 ntt_fused(PassArgs a) {
     pdl_enter();
@@ -403,6 +424,7 @@ ntt_fused(PassArgs a) {
                                           (uint64_t)(limb % a.map.per_group) * a.n
                                     : g;
         load_rows<TILE, THREADS>(sB, gin + (size_t)r * TILE);
+        if (SUM) add_rows<TILE, THREADS>(sB, gin + (size_t)r * TILE, a.src_count, a.src_cstride, q);
         __syncthreads();
         if (small) all_groups<LB, false, false, TILE, false, 0>(sB, LA, r * SB, tw, tws, q);
         else all_groups<LB, false, false, TILE, true, 0>(sB, LA, r * SB, tw, tws, q);
@@ -427,17 +449,22 @@ ntt_fused(PassArgs a) {
 
 constexpr int kCluster = 8;
 
-template <int LA, int LB, bool FWD>
-void launch_fused(const PassArgs &a, cudaStream_t st) {
+template <int LA, int LB, bool FWD, bool SUM = false>
+void launch_fused_e(const PassArgs &a, cudaStream_t st) {
     using F = Fused<LA, LB, kCluster>;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
-        attr_err = cudaFuncSetAttribute(ntt_fused<LA, LB, FWD, kCluster>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)F::SMEM);
+        attr_err = cudaFuncSetAttribute(ntt_fused<LA, LB, FWD, kCluster, SUM>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F::SMEM);
     });
     HEAR_CHECK_CUDA(attr_err);
-    launch(ntt_fused<LA, LB, FWD, kCluster>, a.n_limbs * kCluster, F::THREADS, F::SMEM, st, a);
+    launch(ntt_fused<LA, LB, FWD, kCluster, SUM>, a.n_limbs * kCluster, F::THREADS, F::SMEM, st, a);
+}
+template <int LA, int LB, bool FWD>
+void launch_fused(const PassArgs &a, cudaStream_t st) {
+    if (!FWD && a.src_count > 1) launch_fused_e<LA, LB, FWD, true>(a, st);
+    else launch_fused_e<LA, LB, FWD, false>(a, st);
 }
 
 // a launch whose wide tiles would not give every SM two CTAs runs the narrow variant
@@ -451,8 +478,12 @@ void launch_fwd_t(const PassArgs &a, cudaStream_t st) {
 }
 template <int A, int B, int MODE>
 void launch_inv_t(const PassArgs &a, cudaStream_t st) {
-    launch(ntt_pass_b<B, false, MODE>, a.n_limbs * (a.n / Tile<B, MODE>::WORDS), Tile<B, MODE>::THREADS, 0, st, a,
-           (uint32_t)A);
+    if (a.src_count > 1)
+        launch(ntt_pass_b<B, false, MODE, true>, a.n_limbs * (a.n / Tile<B, MODE>::WORDS), Tile<B, MODE>::THREADS, 0,
+               st, a, (uint32_t)A);
+    else
+        launch(ntt_pass_b<B, false, MODE>, a.n_limbs * (a.n / Tile<B, MODE>::WORDS), Tile<B, MODE>::THREADS, 0, st, a,
+               (uint32_t)A);
     launch(ntt_pass_a<A, false, MODE, B>, a.n_limbs * (a.n / Tile<A, MODE>::WORDS), Tile<A, MODE>::THREADS, 0, st, a);
 }
 // variant of a launch of n_limbs limbs: the context's table (filled by the tuner) or the
@@ -505,6 +536,8 @@ PassArgs make_args(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, Li
     a.small_below = fwd ? (1ull << 58) : (1ull << (63 - ctx->log_n));
     a.src = nullptr;
     a.src_gstride = 0;
+    a.src_count = 1;
+    a.src_cstride = 0;
     a.pro = nullptr;
     a.pro_gstride = 0;
     a.pro_center = 0;
@@ -550,13 +583,17 @@ void ntt_inverse(const hear_context *ctx, uint64_t *data, uint32_t n_limbs, Limb
 }
 
 void ntt_inverse_from(const hear_context *ctx, const uint64_t *src, uint64_t src_gstride, uint64_t *data,
-                      uint32_t n_limbs, LimbMap map, cudaStream_t s) {
+                      uint32_t n_limbs, LimbMap map, cudaStream_t s, uint32_t src_count, uint64_t src_cstride) {
     if (n_limbs == 0) return;
     HEAR_REQUIRE(!src || map.group_stride == 0, HEAR_E_INVAL, "out-of-place NTT needs contiguous groups");
-    ProfScope ps(ctx, "ntt_inv", s, ntt_bytes(ctx, n_limbs, map), launches_of(ctx, false, n_limbs));
+    HEAR_REQUIRE(src_count >= 1 && (src_count == 1 || src), HEAR_E_INVAL, "summed sources need an out-of-place NTT");
+    ProfScope ps(ctx, "ntt_inv", s, ntt_bytes(ctx, n_limbs, map) * (1.0 + (src_count - 1) * 0.5),
+                 launches_of(ctx, false, n_limbs));
     PassArgs a = make_args(ctx, data, n_limbs, map, false);
     a.src = src;
     a.src_gstride = src_gstride;
+    a.src_count = src_count;
+    a.src_cstride = src_cstride;
     switch (ctx->log_n) {
     case 11: launch_inv<6, 5>(ctx, a, s); break;
     case 12: launch_inv<6, 6>(ctx, a, s); break;
