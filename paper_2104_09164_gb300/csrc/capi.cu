@@ -230,7 +230,6 @@ hear_status hear_eval_key_export(const hear_eval_keys *evk, uint32_t galois, uin
             automorphism(c, c->nqp() - 1, c->dnum_max() * 2, galois, t.u64(), u.u64(), st);
             HEAR_CHECK_CUDA(cudaMemcpyAsync(t.p, u.p, words * 8, cudaMemcpyDeviceToDevice, st));
         }
-        split_pieces(c, t.u64(), limbs, m, false, st);   // back from the two-piece storage
         from_mont(c, t.u64(), limbs, m, st);
         ntt_inverse(c, t.u64(), limbs, m, st);
         HEAR_CHECK_CUDA(cudaMemcpyAsync(out, t.p, words * 8, cudaMemcpyDeviceToHost, st));

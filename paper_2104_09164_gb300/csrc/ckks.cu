@@ -133,8 +133,6 @@ void keygen(hear_context *c, uint64_t seed, const int32_t *steps, size_t n_steps
             automorphism(c, nqp - 1, dnum * 2, galois_inverse(c, g), key.u64(), perm.u64(), st);
             key = std::move(perm);
         }
-        // the inner product reads the words of the limbs below 2^42 in two pieces
-        split_pieces(c, key.u64(), dnum * 2 * nqp, km, true, st);
         evk->keys.emplace(g, std::move(key));
     }
     HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
@@ -396,9 +394,6 @@ void build_fc(hear_context *c, hear_model::Fc &fc, const double *W, uint32_t d_o
         }
         HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
     }
-    // the inner sums read the words of the limbs below 2^42 in two pieces
-    split_pieces(c, fc.pts.u64(), fc.n2 * n1 * L1, pmap, true, st);
-    HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
     fc.rotsum = rotsum_rounds(d_out, d_in / d_out, k, radix);
 }
 

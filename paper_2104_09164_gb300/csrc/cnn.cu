@@ -135,9 +135,6 @@ void build_diag(hear_context *c, hear_cnn::Op &op, const std::vector<std::tuple<
         }
         encode_into(c, zr.data(), cnt, scales.data(), op.level_in, true, op.pts.u64() + q0 * plane, st);
     }
-    // the inner sums read the words of the limbs below 2^42 in two pieces
-    split_pieces(c, op.pts.u64(), (uint32_t)(n_pt * L1), map_q(op.level_in, c->n_q), true, st);
-    HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
 }
 
 const uint64_t *need_key(const hear_eval_keys *evk, uint32_t g) {

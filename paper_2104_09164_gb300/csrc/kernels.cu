@@ -258,58 +258,6 @@ __device__ __forceinline__ void fold(u128 &acc, uint64_t q) {
     if (acc.hi >= q) acc.hi -= q;
 }
 
-// Piece-wise products for the primes below 2^42 (the 40-bit chain primes).  Switching-key and
-// diagonal-plaintext words of such limbs are stored as their two 21-bit pieces, y0 | y1 << 32
-// (y = y0 + 2^21 y1, still Montgomery form); a residue x < 2^42 is cut the same way at run
-// time.  A product is then three 32 x 32 -> 64-bit multiply-adds (Karatsuba):
-//   A0 += x0 y0,  A2 += x1 y1,  Am += (x0 + x1)(y0 + y1),
-// and a sum of products is S = A0 + (Am - A0 - A2) 2^21 + A2 2^42 exactly (each term of Am is
-// below 2^44, so each A stays below 2^64 for fewer than 2^20 terms, and S below q 2^64),
-// reduced once by the same Montgomery step as the 64-bit products:
-// the residues are identical, with three multiply-pipe instructions per product instead of
-// eight 32-bit multiply-adds.
-constexpr uint64_t kPieceBelow = 1ull << 42;
-constexpr uint64_t kPieceMask = (1ull << 21) - 1;
-struct Acc3 {
-    uint64_t a0, am, a2;
-};
-__device__ __forceinline__ void mad_wide(uint64_t &acc, uint32_t a, uint32_t b) {
-    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
-}
-struct Pieces {
-    uint32_t x0, x1, xs;
-};
-__device__ __forceinline__ Pieces cut(uint64_t x) {
-    Pieces p;
-    p.x0 = (uint32_t)(x & kPieceMask);
-    p.x1 = (uint32_t)(x >> 21);
-    p.xs = p.x0 + p.x1;
-    return p;
-}
-__device__ __forceinline__ void mac_pieces(Acc3 &acc, const Pieces &x, uint64_t y) {
-    const uint32_t y0 = (uint32_t)y, y1 = (uint32_t)(y >> 32);
-    mad_wide(acc.a0, x.x0, y0);
-    mad_wide(acc.a2, x.x1, y1);
-    mad_wide(acc.am, x.xs, y0 + y1);
-}
-__device__ __forceinline__ uint64_t reduce_pieces(const Acc3 &a, uint64_t q, uint64_t qinv) {
-    const uint64_t a1 = a.am - a.a0 - a.a2;
-    u128 s{a.a0, 0};
-    add_to(s, u128{a1 << 21, a1 >> 43});
-    add_to(s, u128{a.a2 << 42, a.a2 >> 22});
-    return mont_reduce(s, q, qinv);
-}
-
-// y <-> y0 | y1 << 32 for every word of the limbs whose prime is below 2^42
-__global__ void k_split_pieces(uint64_t *d, uint32_t n_limbs, LimbMap m, const DevPrime *P, uint32_t n, int to_split) {
-    pdl_enter();
-    uint32_t b = limb_yz(), pi;
-    if (b >= n_limbs || !m.resolve(b, &pi)) return;
-    if (P[pi].q >= kPieceBelow) return;
-    uint64_t &x = d[m.offset(b, n) + COEF()];
-    x = to_split ? ((x & kPieceMask) | ((x >> 21) << 32)) : ((x & 0xffffffffull) | ((x >> 32) << 21));
-}
-
 // BSGS inner sums out[j][c] = sum_b pt[j][b] (.) baby[b][c] on contiguous storage:
 // baby [n1][C][2][L1][N], pt [n2*n1][L1][N] (Montgomery), out [n2][C][2][L1][N].
 // CTA = 8 warps, each one polynomial (c, poly) of the batch; lanes over 32 consecutive
@@ -321,10 +269,10 @@ __global__ void k_split_pieces(uint64_t *d, uint32_t n_limbs, LimbMap m, const D
 // jw = 8 / 2C warps then share each polynomial, warp w taking polynomial w mod 2C and the
 // giant-step chunks (JC outputs each) jpart, jpart + jw, .. with jpart = w / 2C.
 // Limbs t >= lq are over the special primes (inner sums over Q_l u P): prime n_q + t - lq.
-// JC = giant-step outputs accumulated per pass over the babies (4 with the registers of three
-// CTAs per SM, or 8 with those of two)
+// JC = giant-step outputs accumulated per pass over the babies (4, or 8 with the registers of
+// two CTAs per SM)
 template <int JC>
-__global__ void __launch_bounds__(256, JC == 4 ? 3 : 2) k_lincomb(uint32_t L1, uint32_t C, uint32_t n1, uint32_t n2,
+__global__ void __launch_bounds__(256, JC == 4 ? 4 : 2) k_lincomb(uint32_t L1, uint32_t C, uint32_t n1, uint32_t n2,
                                                  const uint64_t *__restrict__ baby, const uint64_t *__restrict__ pt,
                                                  uint64_t *__restrict__ out, const DevPrime *P, uint32_t n,
                                                  uint32_t jw, uint32_t lq, uint32_t n_q) {
@@ -346,32 +294,6 @@ __global__ void __launch_bounds__(256, JC == 4 ? 3 : 2) k_lincomb(uint32_t L1, u
     const uint64_t q = P[pi].q, qinv = P[pi].qinv;
     const uint64_t bstride = 2ull * C * plane;                    // between baby steps / giant outputs
     const uint64_t *bp = baby + (uint64_t)cp * plane + r;
-    if (q < kPieceBelow) {
-        // plaintext words in pieces (see kPieceBelow)
-        for (uint32_t j0 = JC * jpart; j0 < n2; j0 += JC * jw) {
-            Acc3 acc[JC];
-#pragma unroll
-            for (int jj = 0; jj < JC; jj++) acc[jj] = Acc3{0, 0, 0};
-            const uint64_t *pp = pt + ((uint64_t)j0 * n1) * plane + r;
-            const uint32_t jn = min((uint32_t)JC, n2 - j0);
-#pragma unroll 2
-            for (uint32_t b = 0; b < n1; b++) {
-                const Pieces x = cut(bp[(uint64_t)b * bstride]);
-                uint64_t w[JC];
-#pragma unroll
-                for (int jj = 0; jj < JC; jj++)
-                    if (jj < (int)jn) w[jj] = __ldg(pp + ((uint64_t)jj * n1 + b) * plane);
-#pragma unroll
-                for (int jj = 0; jj < JC; jj++)
-                    if (jj < (int)jn) mac_pieces(acc[jj], x, w[jj]);
-            }
-            uint64_t *op = out + (uint64_t)j0 * bstride + (uint64_t)cp * plane + r;
-#pragma unroll
-            for (int jj = 0; jj < JC; jj++)
-                if (j0 + jj < n2) op[(uint64_t)jj * bstride] = reduce_pieces(acc[jj], q, qinv);
-        }
-        return;
-    }
     for (uint32_t j0 = JC * jpart; j0 < n2; j0 += JC * jw) {
         u128 acc[JC];
 #pragma unroll
@@ -508,7 +430,6 @@ __global__ void __launch_bounds__(256, MINB) k_ks_inner(const uint64_t *ext, int
     const uint32_t g = ginv[r];
     const uint32_t kk = g == 1 ? k : auto_index(k, g, log_n);
     const uint64_t ext_ct = (uint64_t)dnum * W * n, out_ct = 2ull * W * n;
-    const bool pieces = q < kPieceBelow;   // key words in pieces (see kPieceBelow)
     for (uint32_t c = c_begin; c < c_end; c++) {
         const uint64_t cti = ext_per_job ? (uint64_t)r * C + c : c;
         const uint64_t *e = ext + cti * ext_ct + (uint64_t)t * n + k;
@@ -517,37 +438,22 @@ __global__ void __launch_bounds__(256, MINB) k_ks_inner(const uint64_t *ext, int
         for (int j = 0; j < MAXD; j++)      // all digit loads issued before the products
             if (j < (int)dnum) xs[j] = (OWN && j == (int)t) ? own[cti * own_stride + (uint64_t)t * n + k]
                                                             : e[(uint64_t)j * W * n];
-        uint64_t v0, v1;
-        if (pieces) {
-            Acc3 a0{0, 0, 0}, a1{0, 0, 0};
+        u128 a0{0, 0}, a1{0, 0};
 #pragma unroll
-            for (int j = 0; j < MAXD; j++) {
-                if (j < (int)dnum) {
-                    const Pieces x = cut(xs[j]);
-                    mac_pieces(a0, x, k0[j]);
-                    mac_pieces(a1, x, k1[j]);
+        for (int j = 0; j < MAXD; j++) {
+            if (j < (int)dnum) {
+                mac_raw(a0, xs[j], k0[j]);
+                mac_raw(a1, xs[j], k1[j]);
+                if ((j & 7) == 7) {
+                    fold(a0, q);
+                    fold(a1, q);
                 }
             }
-            v0 = reduce_pieces(a0, q, qinv);
-            v1 = reduce_pieces(a1, q, qinv);
-        } else {
-            u128 a0{0, 0}, a1{0, 0};
-#pragma unroll
-            for (int j = 0; j < MAXD; j++) {
-                if (j < (int)dnum) {
-                    mac_raw(a0, xs[j], k0[j]);
-                    mac_raw(a1, xs[j], k1[j]);
-                    if ((j & 7) == 7) {
-                        fold(a0, q);
-                        fold(a1, q);
-                    }
-                }
-            }
-            fold(a0, q);
-            fold(a1, q);
-            v0 = mont_reduce(a0, q, qinv);
-            v1 = mont_reduce(a1, q, qinv);
         }
+        fold(a0, q);
+        fold(a1, q);
+        uint64_t v0 = mont_reduce(a0, q, qinv);
+        const uint64_t v1 = mont_reduce(a1, q, qinv);
         uint64_t *o = out + ((uint64_t)r * C + c) * out_ct + (uint64_t)t * n + kk;
         // pc0 (outputs kept over Q_l u P): + P sigma_g(c0) = P c0[k] at position kk
         if (pc0 && t < L1) v0 = add_mod(v0, shoup(pc0[cti * own_stride + (uint64_t)t * n + k], pmod[2 * t],
@@ -576,7 +482,6 @@ __global__ void __launch_bounds__(256, 3) k_ks_inner_rj(const uint64_t *ext, con
 #pragma unroll
     for (int j = 0; j < MAXD; j++)
         if (j < (int)dnum) xs[j] = (OWN && j == (int)t) ? own[(uint64_t)t * n + k] : e[(uint64_t)j * W * n];
-    const bool pieces = q < kPieceBelow;   // key words in pieces (see kPieceBelow)
 #pragma unroll 1
     for (int rr = 0; rr < RJ; rr++) {
         const uint32_t r = r0 + rr;
@@ -590,37 +495,22 @@ __global__ void __launch_bounds__(256, 3) k_ks_inner_rj(const uint64_t *ext, con
                 k1[j] = __ldg(key + (uint64_t)j * 2 * key_plane + key_plane);
             }
         }
-        uint64_t v0, v1;
-        if (pieces) {
-            Acc3 a0{0, 0, 0}, a1{0, 0, 0};
+        u128 a0{0, 0}, a1{0, 0};
 #pragma unroll
-            for (int j = 0; j < MAXD; j++) {
-                if (j < (int)dnum) {
-                    const Pieces x = cut(xs[j]);
-                    mac_pieces(a0, x, k0[j]);
-                    mac_pieces(a1, x, k1[j]);
+        for (int j = 0; j < MAXD; j++) {
+            if (j < (int)dnum) {
+                mac_raw(a0, xs[j], k0[j]);
+                mac_raw(a1, xs[j], k1[j]);
+                if ((j & 7) == 7) {
+                    fold(a0, q);
+                    fold(a1, q);
                 }
             }
-            v0 = reduce_pieces(a0, q, qinv);
-            v1 = reduce_pieces(a1, q, qinv);
-        } else {
-            u128 a0{0, 0}, a1{0, 0};
-#pragma unroll
-            for (int j = 0; j < MAXD; j++) {
-                if (j < (int)dnum) {
-                    mac_raw(a0, xs[j], k0[j]);
-                    mac_raw(a1, xs[j], k1[j]);
-                    if ((j & 7) == 7) {
-                        fold(a0, q);
-                        fold(a1, q);
-                    }
-                }
-            }
-            fold(a0, q);
-            fold(a1, q);
-            v0 = mont_reduce(a0, q, qinv);
-            v1 = mont_reduce(a1, q, qinv);
         }
+        fold(a0, q);
+        fold(a1, q);
+        uint64_t v0 = mont_reduce(a0, q, qinv);
+        const uint64_t v1 = mont_reduce(a1, q, qinv);
         const uint32_t g = ginv[r];
         const uint32_t kk = g == 1 ? k : auto_index(k, g, log_n);
         uint64_t *o = out + (uint64_t)r * out_ct + (uint64_t)t * n + kk;
@@ -738,12 +628,6 @@ uint32_t ks_form(const hear_context *c, int tab, uint32_t n) {
         launch(kernel, grid, block, 0, st, __VA_ARGS__);                                   \
     } while (0)
 
-void split_pieces(const hear_context *c, uint64_t *d, uint32_t n_limbs, LimbMap m, bool to_split, cudaStream_t s) {
-    uint32_t ny, nz;
-    split_yz(n_limbs, ny, nz);
-    LAUNCH3(k_split_pieces, grid3(c->n, ny, nz), kBlock, s, 16.0 * n_limbs * c->n, d, n_limbs, m, c->dev_primes(),
-            c->n, to_split ? 1 : 0);
-}
 void to_mont(const hear_context *c, uint64_t *d, uint32_t n_limbs, LimbMap m, cudaStream_t s) {
     uint32_t ny, nz;
     split_yz(n_limbs, ny, nz);

@@ -9,9 +9,6 @@ enum SmallKind { kTernary = 0, kGauss = 1 };
 // ---- representation changes ----
 void to_mont(const hear_context *c, uint64_t *d, uint32_t n_limbs, LimbMap m, cudaStream_t s);
 void from_mont(const hear_context *c, uint64_t *d, uint32_t n_limbs, LimbMap m, cudaStream_t s);
-// switching-key / diagonal-plaintext words of the limbs whose prime is below 2^42 to (or back
-// from) the two-piece form y0 | y1 << 32 the inner products read (kernels.cu, kPieceBelow)
-void split_pieces(const hear_context *c, uint64_t *d, uint32_t n_limbs, LimbMap m, bool to_split, cudaStream_t s);
 void small_to_limbs(const hear_context *c, const int8_t *e, uint64_t *out, uint32_t n_limbs, LimbMap m,
                     cudaStream_t s);
 void i64_to_limbs(const hear_context *c, const int64_t *v, uint64_t *out, uint32_t n_limbs, LimbMap m,
