@@ -266,6 +266,27 @@ def roofline(stages, psteps, log_n, workload, bfly_peak=None):
             "stage_share": ms / total, "dominant_stage": name}
 
 
+def ks_roofline(stages, psteps):
+    """the key-switch inner product (every k_ks_inner launch form) against the HBM copy
+    peak: algorithmic bytes (each stored key byte, each extended digit and each output
+    residue once) over the stage time"""
+    hbm, how = peaks()
+    ks = [v for k, v in stages.items() if k.startswith("k_ks_inner")]
+    if not ks:
+        return None
+    calls = sum(v[0] for v in ks)
+    ms = sum(v[1] for v in ks)
+    byts = sum(v[2] for v in ks)
+    if ms <= 0:
+        return None
+    gbs = byts / (ms / 1e3) / 1e9
+    total = sum(v[1] for v in stages.values())
+    return {"bound": "hbm", "kernel": "k_ks_inner (key-switch inner product)",
+            "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "peak_kind": how,
+            "algorithmic_bytes_per_call": byts / calls, "calls_per_step": calls / psteps,
+            "avg_call_us": ms * 1e3 / calls, "stage_share": ms / total}
+
+
 # ------------------------------------------------------------------ oracle CPU timing
 def oracle_sample(w, steps_keys, min_seconds=10.0, max_evals=40):
     """Time the CPU oracle (as it stands) evaluating whole ciphertexts of the workload: at
@@ -886,6 +907,7 @@ def main_gpu(a):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo},
             "roofline": roofline(stages, psteps, w.log_n, w.name if a.clips is None else w.name + "_%d" % a.clips,
                                  H.hear_dbg_bfly_peak(S.ctx)),
+            "roofline_keyswitch": ks_roofline(stages, psteps),
             "ntt": {"achieved_gbs": by_ntt / (ms_ntt / 1e3) / 1e9 if ms_ntt else None,
                     "launches_per_step": nl_ntt / psteps, "share": ms_ntt / total_stage_ms},
             "stages_ms_per_step": {k: v[1] / psteps for k, v in sorted(stages.items(), key=lambda kv: -kv[1][1])},
@@ -1055,6 +1077,10 @@ def headline(result, sections_path):
                      for k in ("bound", "kernel", "achieved", "peak", "unit", "frac", "traffic",
                                "hbm_achieved_gbs", "hbm_peak_gbs", "hbm_frac", "derived_alu_frac") if k in rf}
     h["roofline"]["peak_kind"] = "measured (hear_dbg_bfly_peak)" if rf.get("peak") else None
+    if result.get("roofline_keyswitch"):
+        kr = result["roofline_keyswitch"]
+        h["roofline_keyswitch"] = {k: (_r(kr[k]) if isinstance(kr[k], float) else kr[k])
+                                   for k in ("bound", "achieved", "peak", "unit", "frac", "peak_kind")}
     if "cpu_baseline" in result:
         cb = result["cpu_baseline"]
         h["cpu_baseline"] = {"value": _r(cb["value"]), "unit": cb["unit"], "cores": cb["cores"], "kind": cb["kind"],

@@ -566,7 +566,8 @@ hear_status hear_ntt_set_table(hear_context *ctx, const uint8_t *table);
  *   [1] k_ks_inner_rj (one ciphertext, its digits shared by all jobs) by jobs: 0 = 4 jobs
  *       per thread, 1 = 2, 2 = 8;
  *   [2] k_lincomb by ciphertexts: 0 = 4 giant-step accumulators per pass over the babies,
- *       1 = 8 (registers of 2 CTAs per SM).
+ *       1 = 8 (registers of 2 CTAs per SM), 2 = 2, 3 = 1 (more passes over the babies,
+ *       more chunks of giant steps to spread over the warps).
  * Every table starts at form 0.  hear_ks_tune times every form at the top level on
  * synthetic operands (inner products over 8 jobs for 1, 2, 4, .. max_ct ciphertexts, at
  * most 64; shared-digit products for 2 .. 16 jobs; inner sums with 8 x 8 baby / giant

@@ -269,10 +269,11 @@ __device__ __forceinline__ void fold(u128 &acc, uint64_t q) {
 // jw = 8 / 2C warps then share each polynomial, warp w taking polynomial w mod 2C and the
 // giant-step chunks (JC outputs each) jpart, jpart + jw, .. with jpart = w / 2C.
 // Limbs t >= lq are over the special primes (inner sums over Q_l u P): prime n_q + t - lq.
-// JC = giant-step outputs accumulated per pass over the babies (4, or 8 with the registers of
-// two CTAs per SM)
+// JC = giant-step outputs accumulated per pass over the babies (4, 2 or 1; or 8 with the
+// registers of two CTAs per SM): fewer accumulators re-read the babies more often but leave
+// more chunks to spread over the warps when there are few ciphertexts
 template <int JC>
-__global__ void __launch_bounds__(256, JC == 4 ? 4 : 2) k_lincomb(uint32_t L1, uint32_t C, uint32_t n1, uint32_t n2,
+__global__ void __launch_bounds__(256, JC == 8 ? 2 : 4) k_lincomb(uint32_t L1, uint32_t C, uint32_t n1, uint32_t n2,
                                                  const uint64_t *__restrict__ baby, const uint64_t *__restrict__ pt,
                                                  uint64_t *__restrict__ out, const DevPrime *P, uint32_t n,
                                                  uint32_t jw, uint32_t lq, uint32_t n_q) {
@@ -734,6 +735,21 @@ void automorphism(const hear_context *c, uint32_t level, uint32_t n_polys_total,
     split_yz(limbs, ny, nz);
     LAUNCH3(k_automorphism, grid3(c->n, ny, nz), kBlock, st, 16.0 * limbs * c->n, in, out, limbs, galois, c->log_n);
 }
+// the k_lincomb form of table 2 for n_ct ciphertexts: 0 -> 4 accumulators, 1 -> 8, 2 -> 2, 3 -> 1
+#define LINCOMB_FORMS(LIMBS)                                                                                     \
+    do {                                                                                                         \
+        switch (ks_form(c, 2, n_ct)) {                                                                           \
+        case 1: LAUNCH3(k_lincomb<8>, grid, 256, st, bytes, LIMBS, n_ct, n1, n2, baby, pt, out, c->dev_primes(), \
+                        c->n, jw, L1, c->n_q); break;                                                            \
+        case 2: LAUNCH3(k_lincomb<2>, grid, 256, st, bytes, LIMBS, n_ct, n1, n2, baby, pt, out, c->dev_primes(), \
+                        c->n, jw, L1, c->n_q); break;                                                            \
+        case 3: LAUNCH3(k_lincomb<1>, grid, 256, st, bytes, LIMBS, n_ct, n1, n2, baby, pt, out, c->dev_primes(), \
+                        c->n, jw, L1, c->n_q); break;                                                            \
+        default: LAUNCH3(k_lincomb<4>, grid, 256, st, bytes, LIMBS, n_ct, n1, n2, baby, pt, out,                 \
+                         c->dev_primes(), c->n, jw, L1, c->n_q);                                                 \
+        }                                                                                                        \
+    } while (0)
+
 void lincomb(const hear_context *c, uint32_t level, uint32_t n_ct, uint32_t n1, uint32_t n2, const uint64_t *baby,
              const uint64_t *pt, uint64_t *out, cudaStream_t st) {
     const uint32_t L1 = level + 1;
@@ -742,12 +758,7 @@ void lincomb(const hear_context *c, uint32_t level, uint32_t n_ct, uint32_t n1, 
     // algorithmic: every baby ciphertext, every plaintext and every output once
     const double bytes = 8.0 * L1 * c->n * (2.0 * n_ct * n1 + (double)n1 * n2 + 2.0 * n_ct * n2);
     const uint32_t jw = 2 * n_ct <= 4 ? 8 / (2 * n_ct) : 1;
-    if (ks_form(c, 2, n_ct) == 1)
-        LAUNCH3(k_lincomb<8>, grid, 256, st, bytes, L1, n_ct, n1, n2, baby, pt, out, c->dev_primes(), c->n, jw, L1,
-                c->n_q);
-    else
-        LAUNCH3(k_lincomb<4>, grid, 256, st, bytes, L1, n_ct, n1, n2, baby, pt, out, c->dev_primes(), c->n, jw, L1,
-                c->n_q);
+    LINCOMB_FORMS(L1);
 }
 void lincomb_ext(const hear_context *c, uint32_t level, uint32_t n_ct, uint32_t n1, uint32_t n2, const uint64_t *baby,
                  const uint64_t *pt, uint64_t *out, cudaStream_t st) {
@@ -756,12 +767,7 @@ void lincomb_ext(const hear_context *c, uint32_t level, uint32_t n_ct, uint32_t 
     HEAR_REQUIRE(grid.x < (1u << 31), HEAR_E_UNSUPPORTED, "launch too large");
     const double bytes = 8.0 * W * c->n * (2.0 * n_ct * n1 + (double)n1 * n2 + 2.0 * n_ct * n2);
     const uint32_t jw = 2 * n_ct <= 4 ? 8 / (2 * n_ct) : 1;
-    if (ks_form(c, 2, n_ct) == 1)
-        LAUNCH3(k_lincomb<8>, grid, 256, st, bytes, W, n_ct, n1, n2, baby, pt, out, c->dev_primes(), c->n, jw, L1,
-                c->n_q);
-    else
-        LAUNCH3(k_lincomb<4>, grid, 256, st, bytes, W, n_ct, n1, n2, baby, pt, out, c->dev_primes(), c->n, jw, L1,
-                c->n_q);
+    LINCOMB_FORMS(W);
 }
 void mulplain(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *ct, const uint64_t *pt,
               uint64_t *out, cudaStream_t st) {

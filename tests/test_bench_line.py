@@ -32,6 +32,9 @@ def _full_result():
                      "unit": "G butterflies/s", "frac": 0.3134, "traffic": 9.18e6, "peak_kind": "measured " * 20,
                      "derived_alu_frac": 0.17, "hbm_achieved_gbs": 542.0, "hbm_peak_gbs": 6800.0,
                      "hbm_frac": 0.0797, "algorithmic_bytes_per_call": 1.262e7, "avg_call_us": 23.3},
+        "roofline_keyswitch": {"bound": "hbm", "kernel": "k_ks_inner", "achieved": 4480.123, "peak": 6800.0,
+                               "unit": "GB/s", "frac": 0.6588, "peak_kind": "fallback",
+                               "algorithmic_bytes_per_call": 5.1e7, "calls_per_step": 8.0},
         "ntt": {"achieved_gbs": 300.0}, "stages_ms_per_step": stages,
         "clocks": {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 30},
         "cpu_baseline": {"value": 1.76, "unit": bench.UNIT, "cores": 16, "kind": "oracle",
@@ -62,6 +65,18 @@ def test_headline_is_short_and_complete(tmp_path):
         assert k in h, k
     assert h["config"]["workload"].startswith("small")
     assert set(h["roofline"]) >= {"bound", "achieved", "peak", "unit", "frac", "traffic"}
+    assert h["roofline_keyswitch"]["bound"] == "hbm" and h["roofline_keyswitch"]["frac"] == 0.6588
     assert h["e2e"]["h2d_bytes_per_step"] == 2097152
     assert h["summary"]["served_c5"]["rate_req_s"] == 2000.0
     assert h["value"] == full["value"]
+
+
+def test_keyswitch_roofline_sums_every_form():
+    # stages: name -> (launches, ms, algorithmic bytes) over psteps profiled steps
+    stages = {"k_ks_inner<8>": (8, 0.5, 2.0e9), "k_ks_inner<16>": (2, 0.5, 1.0e9), "ntt_fwd": (40, 1.0, 1.0e9)}
+    r = bench.ks_roofline(stages, 2)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert abs(r["achieved"] - 3.0e9 / 1e-3 / 1e9) < 1e-6          # 3 GB in 1 ms
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+    assert r["calls_per_step"] == 5.0 and abs(r["stage_share"] - 0.5) < 1e-12
+    assert bench.ks_roofline({"ntt_fwd": (1, 1.0, 1.0)}, 1) is None
