@@ -564,7 +564,10 @@ hear_status hear_ntt_set_table(hear_context *ctx, const uint8_t *table);
  *       (no register spills); 2 / 3 = forms 0 / 1 with the ciphertexts in chunks of 4 over
  *       the grid (more CTAs, keys read once per chunk);
  *   [1] k_ks_inner_rj (one ciphertext, its digits shared by all jobs) by jobs: 0 = 4 jobs
- *       per thread, 1 = 2, 2 = 8;
+ *       per thread, 1 = 2, 2 = 8; 3 / 4 = 4 / 8 jobs per CTA with each job's key planes
+ *       streamed into shared memory by 1-D bulk asynchronous copies (the TMA engine,
+ *       double-buffered over the jobs, completion on mbarriers with bounded waits: see
+ *       hear_async_status);
  *   [2] k_lincomb by ciphertexts: 0 = 4 giant-step accumulators per pass over the babies,
  *       1 = 8 (registers of 2 CTAs per SM), 2 = 2, 3 = 1 (more passes over the babies,
  *       more chunks of giant steps to spread over the warps).
@@ -574,8 +577,8 @@ hear_status hear_ntt_set_table(hear_context *ctx, const uint8_t *table);
  * steps) as replayed CUDA graphs of `iters` launches and keeps the fastest per bucket
  * (larger buckets take the largest tuned bucket's form).  It allocates up to a few GB of
  * scratch for the large parameter sets and must not run concurrently with other work on
- * the context.  choice_out (optional): uint8_t[3][8]; ms_out (optional): float[3][8][4]
- * milliseconds per launch (0 = not timed).  hear_ks_set_variant forces form v in every
+ * the context.  choice_out (optional): uint8_t[3][8]; ms_out (optional): float[3][8][8]
+ * milliseconds per launch (0 = not timed).  hear_ks_set_variant forces form v (0..7) in every
  * table (taken modulo the table's form count; -1 = back to the tables), for tests and
  * measurements.  The table can be read and pinned (uint8_t[3][8]); the environment
  * variable HEAR_KS_TABLE (24 digits) pins it at context creation. */
@@ -583,6 +586,22 @@ hear_status hear_ks_tune(hear_context *ctx, uint32_t max_ct, int iters, uint8_t 
 hear_status hear_ks_get_table(const hear_context *ctx, uint8_t *table);
 hear_status hear_ks_set_table(hear_context *ctx, const uint8_t *table);
 hear_status hear_ks_set_variant(hear_context *ctx, int variant);
+
+/* ---- bounded device waits ----
+ * Kernels that wait on the device (the bulk-copy key inner products wait on shared-memory
+ * mbarriers for their copies) give up after about a second of SM cycles: the CTA counts the
+ * timeout in a process-wide device counter, lets its copies in flight land and returns, its
+ * outputs left unwritten.  hear_async_status synchronises the context's default stream,
+ * reads and clears that counter of the context's device: HEAR_OK if no wait ran out,
+ * HEAR_E_TIMEOUT (and *timeouts = how many, optional) if some did -- results computed since
+ * the last check are then not to be trusted.  The context stays usable either way.  No
+ * device fault or hang is involved: a wait that runs out is an ordinary return. */
+hear_status hear_async_status(hear_context *ctx, uint32_t *timeouts);
+/* debug: one CTA waits on an mbarrier that nothing completes, with a limit of limit_cycles SM
+ * cycles (>= 0), on the context's default stream; *timed_out = 1 when the wait ran out (it
+ * is then counted for hear_async_status like any other), 0 when it completed.  Tests the
+ * bounded-wait path without a fault. */
+hear_status hear_dbg_wait_probe(hear_context *ctx, long long limit_cycles, uint32_t *timed_out);
 
 /* ---- debug: ring products through the NTT kernels (tests only) ---- */
 /* out = a * b in Z_q[X]/(X^N+1) for limb prime index `prime` (0..n_q+n_p-1), coefficient domain */

@@ -98,6 +98,7 @@ hear_status hear_context_create(const hear_params_desc *params, int cuda_device,
     auto c = new hear_context();
     hear_status s = guard(nullptr, [&] {
         build_context(c, params, cuda_device);
+        ks_bulk_setup();
         // pick the NTT launch variant per launch size by timing them (HEAR_NTT_TUNE=0 keeps
         // the fixed rule); every variant computes the same residues
         const char *t = std::getenv("HEAR_NTT_TABLE");
@@ -751,7 +752,7 @@ hear_status hear_ntt_set_table(hear_context *ctx, const uint8_t *table) {
 hear_status hear_ks_tune(hear_context *ctx, uint32_t max_ct, int iters, uint8_t *choice_out, float *ms_out) {
     if (!ctx) return fail(HEAR_E_INVAL, "null context");
     return guard(ctx, [&] {
-        if (ms_out) std::fill(ms_out, ms_out + kKsTables * kKsBuckets * 4, 0.0f);
+        if (ms_out) std::fill(ms_out, ms_out + kKsTables * kKsBuckets * kKsMaxForms, 0.0f);
         ks_tune(ctx, max_ct, iters, ms_out);
         if (choice_out) std::memcpy(choice_out, ctx->ks_choice, sizeof(ctx->ks_choice));
     });
@@ -774,9 +775,26 @@ hear_status hear_ks_set_table(hear_context *ctx, const uint8_t *table) {
 
 hear_status hear_ks_set_variant(hear_context *ctx, int variant) {
     if (!ctx) return fail(HEAR_E_INVAL, "null context");
-    if (variant < -1 || variant > 3) return fail(HEAR_E_INVAL, "variant must be -1 or 0..3");
+    if (variant < -1 || variant >= kKsMaxForms) return fail(HEAR_E_INVAL, "variant must be -1 or 0..7");
     ctx->ks_force = variant;
     return HEAR_OK;
+}
+
+hear_status hear_async_status(hear_context *ctx, uint32_t *timeouts) {
+    if (!ctx) return fail(HEAR_E_INVAL, "null context");
+    uint32_t v = 0;
+    hear_status s = guard(ctx, [&] {
+        HEAR_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+        v = async_timeouts(true);
+    });
+    if (timeouts) *timeouts = v;
+    if (s != HEAR_OK) return s;
+    return v ? fail(HEAR_E_TIMEOUT, std::to_string(v) + " bounded device wait(s) ran out") : HEAR_OK;
+}
+
+hear_status hear_dbg_wait_probe(hear_context *ctx, long long limit_cycles, uint32_t *timed_out) {
+    if (!ctx || !timed_out || limit_cycles < 0) return fail(HEAR_E_INVAL, "bad argument");
+    return guard(ctx, [&] { *timed_out = wait_probe(limit_cycles, ctx->stream); });
 }
 
 hear_status hear_ntt_set_variant(hear_context *ctx, int variant) {

@@ -135,11 +135,13 @@ inline uint32_t ntt_bucket(uint32_t n_limbs) {
 // launch forms of the key-switch inner product and the BSGS inner sums (kernels.cu), per
 // log2 bucket of the batch: [0] k_ks_inner by ciphertexts per job (4 forms: register cap
 // for 3 or 2 CTAs per SM x all ciphertexts per thread or chunks of 4), [1] k_ks_inner_rj by
-// jobs (4, 2 or 8 jobs per thread), [2] k_lincomb by ciphertexts (4, 8, 2 or 1 accumulators
-// per thread); every form computes the same residues
+// jobs (4, 2 or 8 jobs per thread; 4 or 8 jobs per CTA with the keys streamed by bulk
+// copies), [2] k_lincomb by ciphertexts (4, 8, 2 or 1 accumulators per thread); every form
+// computes the same residues
 constexpr int kKsTables = 3;
 constexpr int kKsBuckets = 8;
-constexpr int kKsVariants[kKsTables] = {4, 3, 4};
+constexpr int kKsMaxForms = 8;     // hear_ks_tune's ms_out: [kKsTables][kKsBuckets][kKsMaxForms]
+constexpr int kKsVariants[kKsTables] = {4, 5, 4};
 inline uint32_t ks_bucket(uint32_t n) {
     uint32_t b = 0;
     while ((2u << b) <= n && b + 1 < (uint32_t)kKsBuckets) b++;

@@ -521,6 +521,160 @@ __global__ void __launch_bounds__(256, 3) k_ks_inner_rj(const uint64_t *ext, con
     }
 }
 
+// ---- 1-D bulk asynchronous copies (the TMA engine) completing on shared-memory mbarriers.
+// A copy engine transfer keeps its bytes in flight without registers or L1 miss slots, which
+// is what bounds the register-staged key reads of the shared-digit inner product at batch 1.
+// Every wait is bounded: after kWaitLimit SM cycles (about a second) the CTA counts the
+// timeout in g_wait_timeouts, waits (bounded again) for its own copies and returns; the host
+// reads the count with hear_async_status.
+__device__ unsigned int g_wait_timeouts;
+constexpr long long kWaitLimit = 2000000000ll;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+// the barrier's initialisation visible to the copy engine (the async proxy)
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// one arrival that also announces `bytes` of copies completing on the barrier
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
+                 "r"(bytes)
+                 : "memory");
+}
+// global -> shared copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+// wait for the phase of parity `parity` to complete; false after `limit` SM cycles
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit) {
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity))
+        if (clock64() - t0 > limit) return false;
+    return true;
+}
+
+// k_ks_inner_rj with the keys streamed by the copy engine: a CTA owns kBlock coefficients of
+// limb t for RJ jobs; the 2 dnum key planes of a job (kBlock contiguous words each) come into
+// one of two shared-memory buffers as bulk copies, the next job's keys landing while the
+// current job's products run.  Same sums and outputs as k_ks_inner_rj.  Dynamic shared
+// memory: 2 buffers x 2 dnum x kBlock words.
+template <int MAXD, bool OWN, int RJ>
+__global__ void __launch_bounds__(256, 3) k_ks_inner_rj_bulk(const uint64_t *ext, const uint64_t *const *keys,
+                                                             const uint32_t *ginv, uint64_t *out, uint32_t R,
+                                                             uint32_t L1, uint32_t W, uint32_t dnum, uint32_t n_q,
+                                                             uint32_t nqp, uint32_t log_n, const DevPrime *P,
+                                                             const uint64_t *own, const uint64_t *pc0,
+                                                             const uint64_t *pmod) {
+    extern __shared__ __align__(128) uint64_t skey[];
+    __shared__ __align__(8) uint64_t bars[2];
+    pdl_enter();
+    const uint32_t n = 1u << log_n, k = COEF(), r0 = blockIdx.y * RJ, t = blockIdx.z;
+    const uint32_t k_base = blockIdx.x * kBlock;
+    const uint32_t pt = t < L1 ? t : n_q + (t - L1);
+    const uint64_t q = P[pt].q, qinv = P[pt].qinv;
+    const uint64_t key_plane = (uint64_t)nqp * n, out_ct = 2ull * W * n;
+    const uint32_t planes = 2 * dnum, jobs = min((uint32_t)RJ, R - r0);
+    // thread 0: the keys of job r0 + rr into buffer rr & 1
+    auto issue = [&](uint32_t rr) {
+        const uint32_t b = rr & 1, bar = smem_addr(&bars[b]);
+        const uint64_t *src = keys[r0 + rr] + (uint64_t)pt * n + k_base;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bar, planes * kBlock * 8);
+        for (uint32_t p = 0; p < planes; p++)
+            bulk_g2s(smem_addr(skey + ((uint64_t)b * planes + p) * kBlock), src + (uint64_t)p * key_plane, kBlock * 8,
+                     bar);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(smem_addr(&bars[0]), 1);
+        mbar_init(smem_addr(&bars[1]), 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        issue(0);
+        if (jobs > 1) issue(1);
+    }
+    uint64_t xs[MAXD];
+    const uint64_t *e = ext + (uint64_t)t * n + k;
+#pragma unroll
+    for (int j = 0; j < MAXD; j++)
+        if (j < (int)dnum) xs[j] = (OWN && j == (int)t) ? own[(uint64_t)t * n + k] : e[(uint64_t)j * W * n];
+#pragma unroll 1
+    for (uint32_t rr = 0; rr < jobs; rr++) {
+        const uint32_t b = rr & 1;
+        if (!__syncthreads_and(mbar_wait(smem_addr(&bars[b]), (rr >> 1) & 1, kWaitLimit))) {
+            if (threadIdx.x == 0) {     // give up: count it, let the copies in flight land, return
+                atomicAdd(&g_wait_timeouts, 1u);
+                mbar_wait(smem_addr(&bars[b]), (rr >> 1) & 1, kWaitLimit);
+                if (rr + 1 < jobs) mbar_wait(smem_addr(&bars[b ^ 1]), ((rr + 1) >> 1) & 1, kWaitLimit);
+            }
+            return;
+        }
+        const uint64_t *sk = skey + (uint64_t)b * planes * kBlock + threadIdx.x;
+        uint64_t k0[MAXD], k1[MAXD];
+#pragma unroll
+        for (int j = 0; j < MAXD; j++) {
+            if (j < (int)dnum) {
+                k0[j] = sk[(2u * j) * kBlock];
+                k1[j] = sk[(2u * j + 1) * kBlock];
+            }
+        }
+        __syncthreads();                // buffer b is read: refill it with job rr + 2
+        if (threadIdx.x == 0 && rr + 2 < jobs) issue(rr + 2);
+        u128 a0{0, 0}, a1{0, 0};
+#pragma unroll
+        for (int j = 0; j < MAXD; j++) {
+            if (j < (int)dnum) {
+                mac_raw(a0, xs[j], k0[j]);
+                mac_raw(a1, xs[j], k1[j]);
+                if ((j & 7) == 7) {
+                    fold(a0, q);
+                    fold(a1, q);
+                }
+            }
+        }
+        fold(a0, q);
+        fold(a1, q);
+        uint64_t v0 = mont_reduce(a0, q, qinv);
+        const uint64_t v1 = mont_reduce(a1, q, qinv);
+        const uint32_t r = r0 + rr, g = ginv[r];
+        const uint32_t kk = g == 1 ? k : auto_index(k, g, log_n);
+        uint64_t *o = out + (uint64_t)r * out_ct + (uint64_t)t * n + kk;
+        if (pc0 && t < L1) v0 = add_mod(v0, shoup(pc0[(uint64_t)t * n + k], pmod[2 * t], pmod[2 * t + 1], q), q);
+        o[0] = v0;
+        o[(uint64_t)W * n] = v1;
+    }
+}
+
+// A wait that nothing completes: one CTA initialises a barrier, expects one arrival that
+// never comes and waits with a limit of `limit` cycles; *status = 1 if the wait ran out (and
+// the timeout was counted), 0 if it completed.
+__global__ void k_wait_probe(long long limit, uint32_t *status) {
+    __shared__ __align__(8) uint64_t bar;
+    pdl_enter();
+    if (threadIdx.x == 0) {
+        mbar_init(smem_addr(&bar), 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const bool ok = mbar_wait(smem_addr(&bar), 0, limit);
+        if (!ok) atomicAdd(&g_wait_timeouts, 1u);
+        *status = ok ? 0u : 1u;
+    }
+}
+
 // P x over Q_l u P: limb t < L1 is [P]_{q_t} x_t (pmod = (value, Shoup) pairs), the special
 // limbs are zero.  y = limb t of W, z = polynomial.
 __global__ void k_scale_p_ext(const uint64_t *x, uint64_t *out, uint32_t L1, uint32_t W, const uint64_t *pmod,
@@ -849,11 +1003,26 @@ void ks_inner(const hear_context *c, uint32_t level, uint32_t R, uint32_t C, con
             launch(k_ks_inner_rj<8, false, RJ>, g4, kBlock, 0, st, ext, d_keys, d_ginv, out, R, L1, W, dnum,      \
                    c->n_q, c->nqp(), c->log_n, c->dev_primes(), own, pc0, pmod);                                  \
     } while (0)
+#define KS_RJ_BULK(RJ)                                                                                            \
+    do {                                                                                                          \
+        const dim3 g4(c->n / kBlock, (R + RJ - 1) / RJ, W);                                                      \
+        const size_t smem = 2ull * 2 * dnum * kBlock * 8;                                                         \
+        ProfScope ps__(c, "k_ks_inner<8>", st, bytes);                                                            \
+        if (own)                                                                                                  \
+            launch(k_ks_inner_rj_bulk<8, true, RJ>, g4, kBlock, smem, st, ext, d_keys, d_ginv, out, R, L1, W,     \
+                   dnum, c->n_q, c->nqp(), c->log_n, c->dev_primes(), own, pc0, pmod);                            \
+        else                                                                                                      \
+            launch(k_ks_inner_rj_bulk<8, false, RJ>, g4, kBlock, smem, st, ext, d_keys, d_ginv, out, R, L1, W,    \
+                   dnum, c->n_q, c->nqp(), c->log_n, c->dev_primes(), own, pc0, pmod);                            \
+    } while (0)
     if (C == 1 && !ext_per_job && R >= 2 && dnum <= 8) {
-        // one ciphertext whose digits all jobs share: RJ jobs per thread (4, 2 or 8)
+        // one ciphertext whose digits all jobs share: RJ jobs per thread (4, 2 or 8), or RJ
+        // jobs per CTA with the keys streamed by bulk copies (4 or 8)
         switch (ks_form(c, 1, R)) {
         case 1: KS_RJ(2); break;
         case 2: KS_RJ(8); break;
+        case 3: KS_RJ_BULK(4); break;
+        case 4: KS_RJ_BULK(8); break;
         default: KS_RJ(4);
         }
         HEAR_CHECK_CUDA(cudaGetLastError());
@@ -874,6 +1043,35 @@ void ks_inner(const hear_context *c, uint32_t level, uint32_t R, uint32_t C, con
     }
 #undef KS_LAUNCH
 #undef KS_RJ
+#undef KS_RJ_BULK
+}
+
+// dynamic shared memory of the bulk-copy inner products (64 KB at 8 digits) on the current device
+void ks_bulk_setup() {
+    const int smem = 2 * 2 * 8 * kBlock * 8;
+    HEAR_CHECK_CUDA(cudaFuncSetAttribute(k_ks_inner_rj_bulk<8, true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    HEAR_CHECK_CUDA(cudaFuncSetAttribute(k_ks_inner_rj_bulk<8, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    HEAR_CHECK_CUDA(cudaFuncSetAttribute(k_ks_inner_rj_bulk<8, true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    HEAR_CHECK_CUDA(cudaFuncSetAttribute(k_ks_inner_rj_bulk<8, false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+}
+
+uint32_t async_timeouts(bool clear) {
+    uint32_t v = 0;
+    HEAR_CHECK_CUDA(cudaMemcpyFromSymbol(&v, g_wait_timeouts, sizeof(v)));
+    if (clear && v) {
+        const uint32_t z = 0;
+        HEAR_CHECK_CUDA(cudaMemcpyToSymbol(g_wait_timeouts, &z, sizeof(z)));
+    }
+    return v;
+}
+
+uint32_t wait_probe(long long limit_cycles, cudaStream_t st) {
+    DevBuf d(4, st);
+    launch(k_wait_probe, dim3(1), dim3(32), 0, st, limit_cycles, static_cast<uint32_t *>(d.p));
+    uint32_t v = 0;
+    HEAR_CHECK_CUDA(cudaMemcpyAsync(&v, d.p, 4, cudaMemcpyDeviceToHost, st));
+    HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
+    return v;
 }
 
 void scale_p_ext(const hear_context *c, uint32_t level, uint32_t n_polys, const uint64_t *x, uint64_t *out,
@@ -1041,7 +1239,7 @@ void ks_tune(hear_context *c, uint32_t max_ct, int iters, float *ms_out) {
                         });
                     else
                         ms = time_graph([&] { lincomb(c, level, m, n1, n2, baby.u64(), pts.u64(), sums.u64(), st); });
-                    if (ms_out) ms_out[((size_t)tab * kKsBuckets + b) * 4 + v] = ms;
+                    if (ms_out) ms_out[((size_t)tab * kKsBuckets + b) * kKsMaxForms + v] = ms;
                     if (v == 0 || ms < best) {
                         best = ms;
                         best_v = v;

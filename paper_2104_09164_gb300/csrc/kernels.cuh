@@ -69,6 +69,15 @@ void add_plain(const hear_context *c, uint32_t level, uint32_t n_ct, uint32_t ct
 // ext [n_ct][dnum][W][N] from c1 (NTT, [n_ct] polys at stride c1_stride words); tmp: n_ct*(l+1)*N words
 void modup(const hear_context *c, uint32_t level, uint32_t n_ct, const uint64_t *c1, uint64_t c1_stride,
            uint64_t *ext, uint64_t *tmp, cudaStream_t st);
+// Set-up of the bulk-copy key inner products (their dynamic shared memory) on the current
+// device; called once per context at creation.
+void ks_bulk_setup();
+// Bounded device waits that ran out since the last clear (process-wide counter on the
+// current device); clear = reset it to zero.
+uint32_t async_timeouts(bool clear);
+// One wait on an mbarrier that nothing completes, limited to limit_cycles SM cycles: 1 if it
+// ran out (counted like any other), 0 if it completed.  Synchronises `st`.
+uint32_t wait_probe(long long limit_cycles, cudaStream_t st);
 // Key inner product, R jobs of C ciphertexts: out[r*C + c] ([2][W][N]) =
 //   sum_j sigma_{g_r}(ext_j) (.) key_r[j],  ext = ext[c] (shared) or ext[r*C + c] (per job).
 // d_keys[r]: switching key stored sigma_{g_r}^{-1}-permuted; d_ginv[r] = g_r^{-1} mod 2N.

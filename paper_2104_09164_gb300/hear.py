@@ -217,6 +217,8 @@ def _load():
         "hear_ntt_set_table": (st, [_vp, ctypes.POINTER(ctypes.c_uint8)]),
         "hear_dbg_imad_peak": (st, [_vp, ctypes.c_int, ctypes.c_uint32, _dp]),
         "hear_dbg_bfly_peak": (st, [_vp, ctypes.c_int, ctypes.c_uint32, _dp]),
+        "hear_async_status": (st, [_vp, ctypes.POINTER(ctypes.c_uint32)]),
+        "hear_dbg_wait_probe": (st, [_vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_uint32)]),
         "hear_dbg_round_scalar": (st, [ctypes.c_double, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int64)]),
         "hear_dbg_poly_mul": (st, [_vp, ctypes.c_uint32, _u64p, _u64p, _u64p]),
         "hear_dbg_ntt_roundtrip": (st, [_vp, _u64p, ctypes.c_size_t]),
@@ -888,9 +890,9 @@ def hear_ntt_set_table(ctx, table):
 
 
 def hear_ks_tune(ctx, max_ct=32, iters=5):
-    """time the key-switch / inner-sum launch forms; returns (choice uint8[3][8], ms float32[3][8][4])"""
+    """time the key-switch / inner-sum launch forms; returns (choice uint8[3][8], ms float32[3][8][8])"""
     choice = np.zeros((3, 8), dtype=np.uint8)
-    ms = np.zeros((3, 8, 4), dtype=np.float32)
+    ms = np.zeros((3, 8, 8), dtype=np.float32)
     _check(lib.hear_ks_tune(ctx, int(max_ct), int(iters), _p(choice, ctypes.POINTER(ctypes.c_uint8)),
                             _p(ms, ctypes.POINTER(ctypes.c_float))))
     return choice, ms
@@ -910,6 +912,23 @@ def hear_ks_set_table(ctx, table):
 
 def hear_ks_set_variant(ctx, variant):
     _check(lib.hear_ks_set_variant(ctx, int(variant)))
+
+
+def hear_async_status(ctx):
+    """-> bounded device waits that ran out since the last check (0 = none); the C call
+    returns HEAR_E_TIMEOUT when some did, reported here as the count"""
+    n = ctypes.c_uint32()
+    s = lib.hear_async_status(ctx, ctypes.byref(n))
+    if s not in (0, HEAR_E_TIMEOUT):
+        _check(s)
+    return int(n.value)
+
+
+def hear_dbg_wait_probe(ctx, limit_cycles):
+    """one bounded wait on an mbarrier nothing completes: True if it ran out"""
+    v = ctypes.c_uint32()
+    _check(lib.hear_dbg_wait_probe(ctx, int(limit_cycles), ctypes.byref(v)))
+    return bool(v.value)
 
 
 def hear_ntt_set_variant(ctx, variant):

@@ -58,11 +58,12 @@ def test_every_form_is_bit_exact(env):
         want = o.to_coeff(o.evaluate(w.layers, fresh, k, keys, n1=n1, dh=dh))
         assert np.array_equal(ref1[0], want), fi
         assert np.array_equal(ref6[0], want), fi
-        for v in (1, 2, 3):
+        for v in (1, 2, 3, 4):
             H.hear_ks_set_variant(ctx, v)
             assert all(np.array_equal(a, b) for a, b in zip(_eval(H, model, evk, cts[:1]), ref1)), (fi, v)
             assert all(np.array_equal(a, b) for a, b in zip(_eval(H, model, evk, cts), ref6)), (fi, v)
     H.hear_ks_set_variant(ctx, -1)
+    assert H.hear_async_status(ctx) == 0          # no bounded wait of the bulk-copy forms ran out
 
 
 def test_tuner_table_is_valid_and_exact(env):
@@ -72,12 +73,30 @@ def test_tuner_table_is_valid_and_exact(env):
     H.hear_ks_set_variant(ctx, -1)
     choice, ms = H.hear_ks_tune(ctx, 8, 2)
     assert choice.shape == (3, 8)
-    assert np.all(choice[0] < 4) and np.all(choice[1] < 3) and np.all(choice[2] < 4)
-    assert np.all(ms[0, :4, :4] > 0) and np.all(ms[1, 1:5, :3] > 0) and np.all(ms[2, :4, :4] > 0)
+    assert np.all(choice[0] < 4) and np.all(choice[1] < 5) and np.all(choice[2] < 4)
+    assert np.all(ms[0, :4, :4] > 0) and np.all(ms[1, 1:5, :5] > 0) and np.all(ms[2, :4, :4] > 0)
     table = H.hear_ks_get_table(ctx)
     assert len(table) == 24
     assert all(np.array_equal(a, b) for a, b in zip(_eval(H, models[1], evk, cts), ref))
     H.hear_ks_set_table(ctx, "0" * 24)
     assert H.hear_ks_get_table(ctx) == "0" * 24
     with pytest.raises(H.HearError):
-        H.hear_ks_set_table(ctx, "3" * 24)          # table 1 has 3 forms
+        H.hear_ks_set_table(ctx, "5" * 24)          # tables 0 and 2 have 4 forms, table 1 has 5
+
+
+def test_bounded_wait_runs_out_and_is_reported(env):
+    """a wait on an mbarrier that nothing completes returns after its limit (no hang, no
+    fault), is counted, reported once by hear_async_status and cleared; the context stays
+    usable and evaluates bit-identically afterwards"""
+    H, w, ctx, models, steps, evk, cts = env
+    assert H.hear_async_status(ctx) == 0
+    assert H.hear_dbg_wait_probe(ctx, 20000) is True
+    assert H.hear_dbg_wait_probe(ctx, 0) is True
+    assert H.hear_async_status(ctx) == 2
+    assert H.hear_async_status(ctx) == 0
+    H.hear_ks_set_variant(ctx, 0)
+    ref = _eval(H, models[0], evk, cts[:1])
+    H.hear_ks_set_variant(ctx, 4)
+    assert np.array_equal(_eval(H, models[0], evk, cts[:1])[0], ref[0])
+    H.hear_ks_set_variant(ctx, -1)
+    assert H.hear_async_status(ctx) == 0
