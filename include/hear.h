@@ -570,11 +570,13 @@ hear_status hear_ntt_set_table(hear_context *ctx, const uint8_t *table);
  *       hear_async_status);
  *   [2] k_lincomb by ciphertexts: 0 = 4 giant-step accumulators per pass over the babies,
  *       1 = 8 (registers of 2 CTAs per SM), 2 = 2, 3 = 1 (more passes over the babies,
- *       more chunks of giant steps to spread over the warps).
+ *       more chunks of giant steps to spread over the warps), 4 = the baby steps split over
+ *       the 8 warps of a CTA, every polynomial of the batch in one thread and the partial
+ *       sums added in shared memory (up to 4 ciphertexts; more take form 0).
  * Every table starts at form 0.  hear_ks_tune times every form at the top level on
  * synthetic operands (inner products over 8 jobs for 1, 2, 4, .. max_ct ciphertexts, at
- * most 64; shared-digit products for 2 .. 16 jobs; inner sums with 8 x 8 baby / giant
- * steps) as replayed CUDA graphs of `iters` launches and keeps the fastest per bucket
+ * most 64; shared-digit products for 2 .. 16 jobs; inner sums with 32 x 4 baby / giant
+ * steps up to 4 ciphertexts, 8 x 8 above) as replayed CUDA graphs of `iters` launches and keeps the fastest per bucket
  * (larger buckets take the largest tuned bucket's form).  It allocates up to a few GB of
  * scratch for the large parameter sets and must not run concurrently with other work on
  * the context.  choice_out (optional): uint8_t[3][8]; ms_out (optional): float[3][8][8]

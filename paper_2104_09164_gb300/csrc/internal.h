@@ -136,12 +136,12 @@ inline uint32_t ntt_bucket(uint32_t n_limbs) {
 // log2 bucket of the batch: [0] k_ks_inner by ciphertexts per job (4 forms: register cap
 // for 3 or 2 CTAs per SM x all ciphertexts per thread or chunks of 4), [1] k_ks_inner_rj by
 // jobs (4, 2 or 8 jobs per thread; 4 or 8 jobs per CTA with the keys streamed by bulk
-// copies), [2] k_lincomb by ciphertexts (4, 8, 2 or 1 accumulators per thread); every form
-// computes the same residues
+// copies), [2] k_lincomb by ciphertexts (4, 8, 2 or 1 accumulators per thread; the baby
+// steps split over the warps for up to 4 ciphertexts); every form computes the same residues
 constexpr int kKsTables = 3;
 constexpr int kKsBuckets = 8;
 constexpr int kKsMaxForms = 8;     // hear_ks_tune's ms_out: [kKsTables][kKsBuckets][kKsMaxForms]
-constexpr int kKsVariants[kKsTables] = {4, 5, 4};
+constexpr int kKsVariants[kKsTables] = {4, 5, 5};
 inline uint32_t ks_bucket(uint32_t n) {
     uint32_t b = 0;
     while ((2u << b) <= n && b + 1 < (uint32_t)kKsBuckets) b++;

@@ -335,6 +335,83 @@ __global__ void __launch_bounds__(256, JC == 8 ? 2 : 4) k_lincomb(uint32_t L1, u
     }
 }
 
+// BSGS inner sums for a batch of C <= 4 ciphertexts (P2 = 2C polynomials): a CTA owns 32
+// coefficients of one limb and its 8 warps split the baby steps (warp w takes b = w, w + 8,
+// ..); for a chunk of JS = max(1, 8 / P2) giant-step outputs every thread accumulates all P2
+// polynomials, so a plaintext word is loaded once per CTA, and it keeps the P2 + JS loads of
+// two baby steps in flight at a time.  The warps' partial 128-bit sums (each with hi < q) meet in
+// shared memory; warp i adds the 8 partials of output pair i (hi < 8q, brought below q by
+// subtracting multiples of q 2^64) and reduces.  Same residues as k_lincomb.
+template <int C>
+__global__ void __launch_bounds__(256, 3) k_lincomb_split(uint32_t L1, uint32_t n1, uint32_t n2,
+                                                          const uint64_t *__restrict__ baby,
+                                                          const uint64_t *__restrict__ pt, uint64_t *__restrict__ out,
+                                                          const DevPrime *P, uint32_t n, uint32_t lq, uint32_t n_q) {
+    constexpr int P2 = 2 * C, JS = P2 >= 8 ? 1 : 8 / P2, NP = JS * P2;   // NP <= 8 output pairs
+    __shared__ u128 part[8][NP][32];
+    pdl_enter();
+    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t t = blockIdx.y, k = blockIdx.x * 32 + lane;
+    const uint64_t plane = (uint64_t)L1 * n, r = (uint64_t)t * n + k;
+    const uint32_t pi = t < lq ? t : n_q + (t - lq);
+    const uint64_t q = P[pi].q, qinv = P[pi].qinv;
+    const uint64_t bstride = (uint64_t)P2 * plane;        // between baby steps / giant outputs
+    for (uint32_t j0 = 0; j0 < n2; j0 += JS) {
+        const uint32_t jn = min((uint32_t)JS, n2 - j0);
+        u128 acc[NP];
+#pragma unroll
+        for (int i = 0; i < NP; i++) acc[i] = u128{0, 0};
+        // two of the warp's baby steps (b, b + 8) per iteration: all their loads in flight at once
+        for (uint32_t b = w; b < n1; b += 16) {
+            const bool two = b + 8 < n1;
+            uint64_t x[2][P2], y[2][JS];
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const uint32_t bb = b + 8 * h;
+                if (h == 0 || two) {
+#pragma unroll
+                    for (int cp = 0; cp < P2; cp++) x[h][cp] = baby[(uint64_t)bb * bstride + (uint64_t)cp * plane + r];
+#pragma unroll
+                    for (int jj = 0; jj < JS; jj++)
+                        if (jj < (int)jn) y[h][jj] = __ldg(pt + ((uint64_t)(j0 + jj) * n1 + bb) * plane + r);
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; h++)
+                if (h == 0 || two)
+#pragma unroll
+                    for (int jj = 0; jj < JS; jj++)
+                        if (jj < (int)jn)
+#pragma unroll
+                            for (int cp = 0; cp < P2; cp++) mac_raw(acc[jj * P2 + cp], x[h][cp], y[h][jj]);
+#pragma unroll
+            for (int i = 0; i < NP; i++) fold(acc[i], q);      // after at most two products
+        }
+#pragma unroll
+        for (int i = 0; i < NP; i++) {
+            fold(acc[i], q);
+            part[w][i][lane] = acc[i];
+        }
+        __syncthreads();
+        if (w < jn * P2) {
+            u128 sum = part[0][w][lane];
+#pragma unroll
+            for (int v = 1; v < 8; v++) {
+                const u128 a = part[v][w][lane];
+                const uint64_t lo = sum.lo + a.lo;
+                sum.hi += a.hi + (lo < sum.lo ? 1 : 0);
+                sum.lo = lo;
+            }
+            if (sum.hi >= 4 * q) sum.hi -= 4 * q;
+            if (sum.hi >= 2 * q) sum.hi -= 2 * q;
+            if (sum.hi >= q) sum.hi -= q;
+            const uint32_t jj = w / P2, cp = w % P2;
+            out[(uint64_t)(j0 + jj) * bstride + (uint64_t)cp * plane + r] = mont_reduce(sum, q, qinv);
+        }
+        __syncthreads();
+    }
+}
+
 // y = poly*L1 + limb, z = ciphertext; ciphertext z meets plaintext z / cts_per_pt
 __global__ void k_mulplain(const uint64_t *ct, const uint64_t *pt, uint64_t *out, uint32_t L1, const DevPrime *P,
                            uint32_t n, uint32_t cts_per_pt) {
@@ -889,10 +966,28 @@ void automorphism(const hear_context *c, uint32_t level, uint32_t n_polys_total,
     split_yz(limbs, ny, nz);
     LAUNCH3(k_automorphism, grid3(c->n, ny, nz), kBlock, st, 16.0 * limbs * c->n, in, out, limbs, galois, c->log_n);
 }
-// the k_lincomb form of table 2 for n_ct ciphertexts: 0 -> 4 accumulators, 1 -> 8, 2 -> 2, 3 -> 1
+#define LC_SPLIT(C, LIMBS)                                                                                        \
+    do {                                                                                                         \
+        ProfScope ps__(c, "k_lincomb_split<" #C ">", st, bytes);                                                 \
+        launch(k_lincomb_split<C>, gs, 256, 0, st, LIMBS, n1, n2, baby, pt, out, c->dev_primes(), c->n, L1,     \
+               c->n_q);                                                                                          \
+    } while (0)
+// the k_lincomb form of table 2 for n_ct ciphertexts: 0 -> 4 accumulators, 1 -> 8, 2 -> 2, 3 -> 1,
+// 4 -> baby steps split over the warps (k_lincomb_split, up to 4 ciphertexts; 4 accumulators above)
 #define LINCOMB_FORMS(LIMBS)                                                                                     \
     do {                                                                                                         \
-        switch (ks_form(c, 2, n_ct)) {                                                                           \
+        const dim3 gs(c->n / 32, LIMBS);                                                                         \
+        uint32_t form__ = ks_form(c, 2, n_ct);                                                                   \
+        if (form__ == 4 && n_ct > 4) form__ = 0;                                                                 \
+        switch (form__) {                                                                                        \
+        case 4:                                                                                                  \
+            switch (n_ct) {                                                                                      \
+            case 1: LC_SPLIT(1, LIMBS); break;                                           \
+            case 2: LC_SPLIT(2, LIMBS); break;                                           \
+            case 3: LC_SPLIT(3, LIMBS); break;                                           \
+            default: LC_SPLIT(4, LIMBS);                                                 \
+            }                                                                                                    \
+            break;                                                                                               \
         case 1: LAUNCH3(k_lincomb<8>, grid, 256, st, bytes, LIMBS, n_ct, n1, n2, baby, pt, out, c->dev_primes(), \
                         c->n, jw, L1, c->n_q); break;                                                            \
         case 2: LAUNCH3(k_lincomb<2>, grid, 256, st, bytes, LIMBS, n_ct, n1, n2, baby, pt, out, c->dev_primes(), \
@@ -1154,13 +1249,20 @@ void rescale(const hear_context *c, uint32_t level, uint32_t n_polys, uint64_t *
 // Time every launch form of the key-switch inner product and the BSGS inner sums on
 // synthetic operands at the top level (the values do not change the work) for batches of
 // 1, 2, 4, .. max_ct ciphertexts (inner products over 8 jobs; shared-digit products over
-// 2 .. 16 jobs), each as a replayed CUDA graph of `iters` launches, and record the fastest
-// form per bucket.  Buckets above the tuned range keep the largest tuned bucket's form.
+// 2 .. 16 jobs; inner sums over 32 x 4 baby / giant steps up to 4 ciphertexts, 8 x 8
+// above), each as a replayed CUDA graph of `iters` launches, and record the fastest form
+// per bucket.  Buckets above the tuned range keep the largest tuned bucket's form.
 void ks_tune(hear_context *c, uint32_t max_ct, int iters, float *ms_out) {
     HEAR_REQUIRE(max_ct >= 1 && max_ct <= 64 && iters >= 1, HEAR_E_INVAL, "bad tuning range");
     cudaStream_t st = c->stream;
     const uint32_t level = c->L, L1 = level + 1, W = L1 + c->K, dnum = c->dnum(level), n = c->n;
-    const uint32_t R = 8, RMAX = 16, n1 = 8, n2 = 8;
+    const uint32_t R = 8, RMAX = 16;
+    // inner sums: 32 baby x 4 giant steps for up to 4 ciphertexts (the shape of an FC layer of
+    // 128 diagonals at batch 1, where the warp-split form applies), 8 x 8 above
+    auto bsgs = [](uint32_t m) { return m <= 4 ? std::make_pair(32u, 4u) : std::make_pair(8u, 8u); };
+    const uint64_t baby_planes = std::max<uint64_t>(32ull * 4, 8ull * max_ct);     // n1 x ciphertexts
+    const uint64_t pt_planes = 32ull * 4;                                          // n1 x n2 (>= 8 x 8)
+    const uint64_t sum_planes = std::max<uint64_t>(4ull * 4, 8ull * max_ct);       // n2 x ciphertexts
     const uint64_t plane = (uint64_t)n;
     const uint64_t key_words = (uint64_t)c->dnum_max() * 2 * c->nqp() * plane;
     DevBuf keys(RMAX * key_words * 8, st);
@@ -1168,9 +1270,9 @@ void ks_tune(hear_context *c, uint32_t max_ct, int iters, float *ms_out) {
     DevBuf ext(n_src * dnum * W * plane * 8, st);
     DevBuf c1(n_src * 2 * L1 * plane * 8, st);
     DevBuf out((uint64_t)std::max(max_ct * R, RMAX) * 2 * W * plane * 8, st);
-    DevBuf baby((uint64_t)n1 * max_ct * 2 * L1 * plane * 8, st);
-    DevBuf pts((uint64_t)n1 * n2 * L1 * plane * 8, st);
-    DevBuf sums((uint64_t)n2 * max_ct * 2 * L1 * plane * 8, st);
+    DevBuf baby(baby_planes * 2 * L1 * plane * 8, st);
+    DevBuf pts(pt_planes * L1 * plane * 8, st);
+    DevBuf sums(sum_planes * 2 * L1 * plane * 8, st);
     for (DevBuf *b : {&keys, &ext, &c1, &out, &baby, &pts, &sums}) HEAR_CHECK_CUDA(cudaMemsetAsync(b->p, 0, b->bytes, st));
     std::vector<const uint64_t *> kp(RMAX);
     std::vector<uint32_t> gi(RMAX);
@@ -1238,7 +1340,9 @@ void ks_tune(hear_context *c, uint32_t max_ct, int iters, float *ms_out) {
                             ks_inner(c, level, m, 1, ext.u64(), false, dk, dg, out.u64(), c1.u64(), 2ull * L1 * plane, st);
                         });
                     else
-                        ms = time_graph([&] { lincomb(c, level, m, n1, n2, baby.u64(), pts.u64(), sums.u64(), st); });
+                        ms = time_graph([&] {
+                            lincomb(c, level, m, bsgs(m).first, bsgs(m).second, baby.u64(), pts.u64(), sums.u64(), st);
+                        });
                     if (ms_out) ms_out[((size_t)tab * kKsBuckets + b) * kKsMaxForms + v] = ms;
                     if (v == 0 || ms < best) {
                         best = ms;

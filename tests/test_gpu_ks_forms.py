@@ -73,15 +73,15 @@ def test_tuner_table_is_valid_and_exact(env):
     H.hear_ks_set_variant(ctx, -1)
     choice, ms = H.hear_ks_tune(ctx, 8, 2)
     assert choice.shape == (3, 8)
-    assert np.all(choice[0] < 4) and np.all(choice[1] < 5) and np.all(choice[2] < 4)
-    assert np.all(ms[0, :4, :4] > 0) and np.all(ms[1, 1:5, :5] > 0) and np.all(ms[2, :4, :4] > 0)
+    assert np.all(choice[0] < 4) and np.all(choice[1] < 5) and np.all(choice[2] < 5)
+    assert np.all(ms[0, :4, :4] > 0) and np.all(ms[1, 1:5, :5] > 0) and np.all(ms[2, :4, :5] > 0)
     table = H.hear_ks_get_table(ctx)
     assert len(table) == 24
     assert all(np.array_equal(a, b) for a, b in zip(_eval(H, models[1], evk, cts), ref))
     H.hear_ks_set_table(ctx, "0" * 24)
     assert H.hear_ks_get_table(ctx) == "0" * 24
     with pytest.raises(H.HearError):
-        H.hear_ks_set_table(ctx, "5" * 24)          # tables 0 and 2 have 4 forms, table 1 has 5
+        H.hear_ks_set_table(ctx, "5" * 24)          # table 0 has 4 forms, tables 1 and 2 have 5
 
 
 def test_bounded_wait_runs_out_and_is_reported(env):
