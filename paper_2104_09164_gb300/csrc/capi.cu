@@ -616,16 +616,15 @@ hear_status hear_evaluate_host(const hear_model *m, const hear_eval_keys *evk, c
         const uint64_t ctw = 2ull * (lin + 1) * c->n;
         if (use_graphs(c)) {
             std::lock_guard<std::mutex> g(m->plan_mu);
-            hear_model::Plan *p = graph_plan(m, evk, 0, m->layers.size(), (uint32_t)n_ct, scale, st);
+            // the graph takes the coefficient-domain input and gives the coefficient-domain
+            // output: one H2D copy, one graph launch, one D2H copy
+            hear_model::Plan *p = graph_plan(m, evk, 0, m->layers.size(), (uint32_t)n_ct, scale, st, 0, true);
             HEAR_CHECK_CUDA(cudaStreamWaitEvent(st, p->done, 0));
-            to_device_ntt(c, in_words, lin, (uint32_t)(2 * n_ct), p->X.u64(), st);
+            HEAR_CHECK_CUDA(cudaMemcpyAsync(p->X.p, in_words, (size_t)n_ct * ctw * 8, cudaMemcpyHostToDevice, st));
             HEAR_CHECK_CUDA(cudaGraphLaunch(p->exec, st));
             g_launches += p->launches;
-            DevBuf Y(out_words_n * 8, st);
-            HEAR_CHECK_CUDA(cudaMemcpyAsync(Y.p, p->Y.p, out_words_n * 8, cudaMemcpyDeviceToDevice, st));
+            HEAR_CHECK_CUDA(cudaMemcpyAsync(out_words, p->Y.p, out_words_n * 8, cudaMemcpyDeviceToHost, st));
             HEAR_CHECK_CUDA(cudaEventRecord(p->done, st));
-            ntt_inverse(c, Y.u64(), (uint32_t)(2 * n_ct) * (p->level_out + 1), map_q(p->level_out, c->n_q), st);
-            HEAR_CHECK_CUDA(cudaMemcpyAsync(out_words, Y.p, out_words_n * 8, cudaMemcpyDeviceToHost, st));
             HEAR_CHECK_CUDA(cudaStreamSynchronize(st));
             if (level_out) *level_out = p->level_out;
             if (scale_out) *scale_out = p->scale_out;

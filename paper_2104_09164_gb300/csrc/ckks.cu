@@ -689,15 +689,16 @@ DevBuf evaluate_batch(const hear_model *m, const hear_eval_keys *evk, size_t l0,
 }
 
 hear_model::Plan *graph_plan(const hear_model *m, const hear_eval_keys *evk, size_t l0, size_t l1, uint32_t n_ct,
-                             double scale_in, cudaStream_t st, uint32_t slot) {
+                             double scale_in, cudaStream_t st, uint32_t slot, bool host_io) {
     for (auto &p : m->plans)
         if (p->evk_serial == evk->serial && p->l0 == l0 && p->l1 == l1 && p->n_ct == n_ct && p->scale_in == scale_in &&
-            p->slot == slot)
+            p->slot == slot && p->host_io == host_io)
             return p.get();
     hear_context *c = m->ctx;
     auto plan = std::make_unique<hear_model::Plan>();
     plan->evk_serial = evk->serial;
     plan->slot = slot;
+    plan->host_io = host_io;
     plan->l0 = l0;
     plan->l1 = l1;
     plan->n_ct = n_ct;
@@ -723,9 +724,14 @@ hear_model::Plan *graph_plan(const hear_model *m, const hear_eval_keys *evk, siz
     try {
         uint32_t lo;
         double so;
+        if (host_io) ntt_forward(c, plan->X.u64(), n_ct * 2 * (lin + 1), map_q(lin, c->n_q), cs);
         DevBuf y = evaluate_batch(m, evk, l0, l1, plan->X.u64(), n_ct, &lo, scale_in, &so, cs);
         plan->scale_out = so;
-        HEAR_CHECK_CUDA(cudaMemcpyAsync(plan->Y.p, y.p, out_words * 8, cudaMemcpyDeviceToDevice, cs));
+        if (host_io)
+            ntt_inverse_from(c, y.u64(), (uint64_t)(lo + 1) * c->n, plan->Y.u64(), n_ct * 2 * (lo + 1),
+                             map_q(lo, c->n_q), cs);
+        else
+            HEAR_CHECK_CUDA(cudaMemcpyAsync(plan->Y.p, y.p, out_words * 8, cudaMemcpyDeviceToDevice, cs));
     } catch (...) {
         cudaStreamEndCapture(cs, &graph);
         if (graph) cudaGraphDestroy(graph);

@@ -33,6 +33,7 @@ struct hear_model {
         size_t l0 = 0, l1 = 0;
         uint32_t n_ct = 0, level_out = 0;
         uint32_t slot = 0;         // independent copies for concurrent users (server slots)
+        bool host_io = false;      // X / Y in the coefficient domain (graph_plan)
         double scale_in = 0, scale_out = 0;
         hear::DevBuf X, Y;
         cudaGraphExec_t exec = nullptr;
@@ -135,9 +136,12 @@ hear_model *model_create(hear_context *c, const hear_layer_desc *layers, size_t 
 DevBuf evaluate_batch(const hear_model *m, const hear_eval_keys *evk, size_t l0, size_t l1, const uint64_t *x,
                       uint32_t n_ct, uint32_t *level_out, double scale_in, double *scale_out, cudaStream_t st);
 // graph plan for (evk, l0, l1, n_ct, scale_in): built on first use (one direct warm-up run,
-// then stream capture); the caller fills plan->X, launches plan->exec and reads plan->Y
+// then stream capture); the caller fills plan->X, launches plan->exec and reads plan->Y.
+// host_io: X and Y hold coefficient-domain ciphertexts (the forward NTT of X and the inverse
+// NTT into Y are part of the graph, X is transformed in place), for callers that copy from
+// and to host memory
 hear_model::Plan *graph_plan(const hear_model *m, const hear_eval_keys *evk, size_t l0, size_t l1, uint32_t n_ct,
-                             double scale_in, cudaStream_t st, uint32_t slot = 0);
+                             double scale_in, cudaStream_t st, uint32_t slot = 0, bool host_io = false);
 // the one-launch graph of several whole-network jobs (see hear_multi); one direct warm-up run
 // of every job on `st` first (builds the tables the capture needs)
 hear_multi *multi_create(const hear_model *const *models, const hear_eval_keys *const *evks, size_t n_jobs,

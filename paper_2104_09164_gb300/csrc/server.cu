@@ -52,7 +52,6 @@ struct Request {
 struct Slot {
     cudaStream_t st = nullptr;
     cudaEvent_t done = nullptr;
-    DevBuf x, y;                      // device batch in (coefficient domain -> NTT), out
     std::vector<std::shared_ptr<Request>> reqs;
     uint32_t n_ct = 0;
     bool busy = false;
@@ -85,50 +84,35 @@ struct hear_server {
 
 namespace {
 
-// evaluate the n_ct ciphertexts of slot s (already in s.x, NTT domain) into s.y
-void run_batch(hear_server *S, Slot &s, uint32_t slot_index) {
+// run the batch of slot s on its stream: the ciphertexts, in request order, go in power-of-
+// two sub-batches through captured graphs that take and give the coefficient domain (the
+// NTT conversions are graph nodes); each sub-batch is uploaded from the requests' pinned
+// staging buffers straight into the graph's input and downloaded from its output into their
+// pinned result buffers
+void launch(hear_server *S, Slot &s, uint32_t slot_index) {
     const hear_model *m = S->m;
-    const uint64_t ctw_in = S->in_words, ctw_out = S->out_words;
+    std::vector<std::pair<uint32_t, uint32_t>> io;      // (staging buffer, result buffer) per ciphertext
+    for (auto &r : s.reqs)
+        for (size_t i = 0; i < r->in_bufs.size(); i++) io.emplace_back(r->in_bufs[i], r->out_bufs[i]);
     uint32_t done = 0;
     for (uint32_t b = 1u << 31; b; b >>= 1) {
         while (S->cfg.max_batch >= b && s.n_ct - done >= b) {
             hear_model::Plan *p;
             {
                 std::lock_guard<std::mutex> g(m->plan_mu);
-                p = graph_plan(m, S->evk, 0, m->layers.size(), b, s.reqs[0]->scale, s.st, 1 + slot_index);
+                p = graph_plan(m, S->evk, 0, m->layers.size(), b, s.reqs[0]->scale, s.st, 1 + slot_index, true);
             }
-            HEAR_CHECK_CUDA(cudaMemcpyAsync(p->X.p, s.x.u64() + done * ctw_in, b * ctw_in * 8,
-                                            cudaMemcpyDeviceToDevice, s.st));
+            for (uint32_t i = 0; i < b; i++)
+                HEAR_CHECK_CUDA(cudaMemcpyAsync(p->X.u64() + (uint64_t)i * S->in_words, S->in_arena.at(io[done + i].first),
+                                                S->in_words * 8, cudaMemcpyHostToDevice, s.st));
             HEAR_CHECK_CUDA(cudaGraphLaunch(p->exec, s.st));
             g_launches += p->launches;
-            HEAR_CHECK_CUDA(cudaMemcpyAsync(s.y.u64() + done * ctw_out, p->Y.p, b * ctw_out * 8,
-                                            cudaMemcpyDeviceToDevice, s.st));
+            for (uint32_t i = 0; i < b; i++)
+                HEAR_CHECK_CUDA(cudaMemcpyAsync(S->out_arena.at(io[done + i].second), p->Y.u64() + (uint64_t)i * S->out_words,
+                                                S->out_words * 8, cudaMemcpyDeviceToHost, s.st));
             done += b;
         }
     }
-}
-
-// upload from the requests' pinned staging buffers, evaluate, download into their pinned
-// result buffers, all on the slot's stream
-void launch(hear_server *S, Slot &s, uint32_t slot_index) {
-    hear_context *c = S->m->ctx;
-    uint64_t off = 0;
-    for (auto &r : s.reqs)
-        for (uint32_t b : r->in_bufs) {
-            HEAR_CHECK_CUDA(cudaMemcpyAsync(s.x.u64() + off, S->in_arena.at(b), S->in_words * 8,
-                                            cudaMemcpyHostToDevice, s.st));
-            off += S->in_words;
-        }
-    ntt_forward(c, s.x.u64(), s.n_ct * 2 * (S->lin + 1), map_q(S->lin, c->n_q), s.st);
-    run_batch(S, s, slot_index);
-    ntt_inverse(c, s.y.u64(), s.n_ct * 2 * (S->lout + 1), map_q(S->lout, c->n_q), s.st);
-    off = 0;
-    for (auto &r : s.reqs)
-        for (uint32_t b : r->out_bufs) {
-            HEAR_CHECK_CUDA(cudaMemcpyAsync(S->out_arena.at(b), s.y.u64() + off, S->out_words * 8,
-                                            cudaMemcpyDeviceToHost, s.st));
-            off += S->out_words;
-        }
     HEAR_CHECK_CUDA(cudaEventRecord(s.done, s.st));
     s.busy = true;
 }
@@ -281,8 +265,6 @@ void free_server(hear_server *S) {
         if (s.st) cudaStreamSynchronize(s.st);
         if (s.done) cudaEventDestroy(s.done);
         if (s.st) cudaStreamDestroy(s.st);
-        s.x.reset();
-        s.y.reset();
     }
     if (S->in_arena.base) cudaFreeHost(S->in_arena.base);
     if (S->out_arena.base) cudaFreeHost(S->out_arena.base);
@@ -338,8 +320,6 @@ hear_status hear_server_create(const hear_model *m, const hear_eval_keys *evk, c
         for (auto &s : S->slots) {
             HEAR_CHECK_CUDA(cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking));
             HEAR_CHECK_CUDA(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
-            s.x = DevBuf((size_t)cfg->max_batch * S->in_words * 8, nullptr);
-            s.y = DevBuf((size_t)cfg->max_batch * S->out_words * 8, nullptr);
         }
     } catch (const Error &e) {
         free_server(S.get());

@@ -306,7 +306,18 @@ def test_small_network_per_layer_bit_exact(small):
     words, lv, sc = H.hear_evaluate_host(model, small.evk, H.hear_ciphertext_export(c0), 1, 2.0 ** 40)
     assert lv == r.level and sc == r.scale
     assert np.array_equal(words.reshape(2, lv + 1, -1), o.to_coeff(r))
-    for h in (g, c0, whole):
+    # the host path again (its captured graph replayed) on two other ciphertexts in one call:
+    # each equals the NTT-domain path's result
+    c1 = H.hear_encrypt_clips(small.ctx, small.pk, w.ct_clips(0), 402, 1)
+    c2 = H.hear_encrypt_clips(small.ctx, small.pk, w.ct_clips(0), 403, 2)
+    for _ in range(2):
+        words2, _, _ = H.hear_evaluate_host(model, small.evk, np.concatenate(
+            [H.hear_ciphertext_export(c).reshape(-1) for c in (c1, c2)]), 2, 2.0 ** 40)
+        dev = H.hear_evaluate(model, small.evk, [c1, c2])
+        assert np.array_equal(words2.reshape(2, -1), np.stack([H.hear_ciphertext_export(d).reshape(-1) for d in dev]))
+        for d in dev:
+            H.hear_ciphertext_destroy(d)
+    for h in (g, c0, c1, c2, whole):
         H.hear_ciphertext_destroy(h)
     H.hear_model_destroy(model)
 
