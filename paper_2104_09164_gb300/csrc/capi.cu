@@ -7,6 +7,7 @@
 #include <mutex>
 #include <string>
 #include "ckks.h"
+#include "simd.h"
 
 using namespace hear;
 
@@ -99,6 +100,7 @@ hear_status hear_context_create(const hear_params_desc *params, int cuda_device,
     hear_status s = guard(nullptr, [&] {
         build_context(c, params, cuda_device);
         ks_bulk_setup();
+        simd_setup();
         // pick the NTT launch variant per launch size by timing them (HEAR_NTT_TUNE=0 keeps
         // the fixed rule); every variant computes the same residues
         const char *t = std::getenv("HEAR_NTT_TABLE");
@@ -968,7 +970,6 @@ hear_status hear_cnn_evaluate(const hear_cnn *m, const hear_eval_keys *evk, size
 }  // extern "C"
 
 // ------------------------------------------------------------------ slot-batched evaluation
-#include "simd.h"
 #include "encode.h"
 
 namespace {

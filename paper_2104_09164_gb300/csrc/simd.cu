@@ -90,100 +90,16 @@ __device__ __forceinline__ uint64_t reduce96(uint32_t x0, uint32_t x1, uint32_t 
     return add_mod(shoup(lo, 1, pr.one_sh, pr.q), shoup(x2, k.c[2], k.c_sh[2], pr.q), pr.q);
 }
 
-// y[m][poly][t][j] = sum_k A_t[m][k] x[k][poly][t][j] mod q_t for the limbs of `limbs`
-// (blockIdx.y), rows m0 = blockIdx.z * TM .., columns (poly, j) = blockIdx.x * TX ..
+// the reduction of a thread's RM x CM sums mod q_t and their store
 template <int KIND>
-__global__ void __launch_bounds__(kGemmThreads, Gemm<KIND>::MINB)
-k_simd_fc(const uint64_t *__restrict__ x, uint64_t *__restrict__ y, const uint32_t *__restrict__ a,
-          const uint64_t *__restrict__ a_off, const PieceConsts *__restrict__ pc, LimbSet limbs, uint32_t M,
-          uint32_t Mpad, uint32_t K, uint32_t L1, uint32_t n, const DevPrime *__restrict__ P) {
-    pdl_enter();
+__device__ __forceinline__ void store_outputs(const uint64_t (&acc)[Gemm<KIND>::RM][Gemm<KIND>::CM][KIND == 0 ? kPlanes : 1],
+                                              const uint32_t (&acw)[Gemm<KIND>::RM][Gemm<KIND>::CM][KIND == 1 ? 3 * kPlanes : 1],
+                                              uint64_t *__restrict__ y, const DevPrime *__restrict__ P,
+                                              const PieceConsts *__restrict__ pc, uint32_t t, uint32_t m0, uint32_t M,
+                                              uint32_t poly, uint32_t L1, uint32_t n, uint32_t j0, uint32_t tx,
+                                              uint32_t ty) {
     using G = Gemm<KIND>;
-    constexpr int PL = kPlanes, TM = G::TM, TX = G::TX, RM = G::RM, CM = G::CM, KC = G::KC;
-    static_assert(TM == 16 * RM && TX == 16 * CM, "16 x 16 threads");
-    __shared__ __align__(16) uint32_t sa[PL][KC][TM];
-    __shared__ __align__(16) uint32_t sb[PL][KC][TX];
-    const uint32_t t = limbs.t[blockIdx.y];
-    const uint32_t m0 = blockIdx.z * TM;
-    const uint32_t col0 = blockIdx.x * TX;
-    const uint32_t poly = col0 / n, j0 = col0 % n;
-    const uint32_t tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const uint64_t xrow = 2ull * L1 * n;                                // words per input ciphertext
-    const uint64_t *xb = x + ((uint64_t)poly * L1 + t) * n + j0;      // inner index k at xb + k * xrow
-    const uint32_t *ab = a + a_off[t] + m0;                            // plane p, index k: + (p K + k) Mpad
-
-    // KIND 0: 64-bit sums s00, s11, sm; KIND 1: three 96-bit sums as 32-bit words
-    uint64_t acc[RM][CM][KIND == 0 ? PL : 1];
-    uint32_t acw[RM][CM][KIND == 1 ? 3 * PL : 1];
-#pragma unroll
-    for (int r = 0; r < RM; r++)
-#pragma unroll
-        for (int c = 0; c < CM; c++) {
-#pragma unroll
-            for (int p = 0; p < (KIND == 0 ? PL : 1); p++) acc[r][c][p] = 0;
-#pragma unroll
-            for (int p = 0; p < (KIND == 1 ? 3 * PL : 1); p++) acw[r][c][p] = 0;
-        }
-
-    constexpr int WPT = KC * TX / kGemmThreads;    // residues of x per thread per round
-    constexpr int TPR = TX / WPT;                  // threads per inner index
-    static_assert(WPT % 2 == 0 && TPR * WPT == TX, "x tile split");
-    constexpr int A4 = PL * KC * TM / 4;           // uint4 of pieces per round
-    for (uint32_t k0 = 0; k0 < K; k0 += KC) {
-        {   // x: KC inner indices x TX residues, cut into pieces
-            const uint32_t r = threadIdx.x / TPR, c = (threadIdx.x % TPR) * WPT;
-            uint64_t v[WPT];            if (k0 + r < K) {
-                const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(xb + (uint64_t)(k0 + r) * xrow + c);
-#pragma unroll
-                for (int w = 0; w < WPT / 2; w++) {
-                    const ulonglong2 u = src[w];
-                    v[2 * w] = u.x;
-                    v[2 * w + 1] = u.y;
-                }
-            } else {
-#pragma unroll
-                for (int w = 0; w < WPT; w++) v[w] = 0;
-            }
-#pragma unroll
-            for (int w = 0; w < WPT; w++) {
-                uint32_t pcs[PL];
-                split_pieces<KIND>(v[w], pcs);
-#pragma unroll
-                for (int p = 0; p < PL; p++) sb[p][r][c + w] = pcs[p];
-            }
-        }
-        // the scalars' pieces (zero past K)
-        for (int i = threadIdx.x; i < A4; i += kGemmThreads) {
-            const int p = i / (KC * TM / 4), rem = i % (KC * TM / 4);
-            const int r = rem / (TM / 4), c4 = rem % (TM / 4);
-            uint4 val = make_uint4(0, 0, 0, 0);
-            if (k0 + r < K) val = *reinterpret_cast<const uint4 *>(ab + ((uint64_t)p * K + k0 + r) * Mpad + c4 * 4);
-            *reinterpret_cast<uint4 *>(&sa[p][r][c4 * 4]) = val;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < KC; kk++) {
-            uint32_t av[PL][RM], bv[PL][CM];
-#pragma unroll
-            for (int p = 0; p < PL; p++) {
-                load_vec<CM>(&sb[p][kk][tx * CM], bv[p]);
-                load_vec<RM>(&sa[p][kk][ty * RM], av[p]);
-            }
-#pragma unroll
-            for (int r = 0; r < RM; r++)
-#pragma unroll
-                for (int c = 0; c < CM; c++)
-#pragma unroll
-                    for (int p = 0; p < PL; p++) {
-                        if constexpr (KIND == 0)
-                            acc[r][c][p] += (uint64_t)av[p][r] * bv[p][c];
-                        else
-                            mac96(av[p][r], bv[p][c], acw[r][c][3 * p], acw[r][c][3 * p + 1], acw[r][c][3 * p + 2]);
-                    }
-        }
-        __syncthreads();
-    }
-
+    constexpr int RM = G::RM, CM = G::CM;
     const DevPrime pr = P[t];
     const PieceConsts k = pc[t];
     const uint64_t q = pr.q;
@@ -223,6 +139,131 @@ k_simd_fc(const uint64_t *__restrict__ x, uint64_t *__restrict__ y, const uint32
 #pragma unroll
         for (int c = 0; c < CM; c += 2) dst[c / 2] = make_ulonglong2(o[c], o[c + 1]);
     }
+}
+
+// 16-byte asynchronous global -> shared copy; src_bytes = 0 fills the 16 bytes with zeros
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+
+// y[m][poly][t][j] = sum_k A_t[m][k] x[k][poly][t][j] mod q_t for the limbs of `limbs`
+// (blockIdx.y), rows m0 = blockIdx.z * TM .., columns (poly, j) = blockIdx.x * TX ..
+// The global loads run one round ahead: while round k0 (KC inner indices) is computed from
+// one pair of piece buffers, cp.async brings round k0 + KC's scalar pieces into the other
+// scalar buffer and its raw residues into a staging buffer; after the round the staged
+// residues are cut into the other residue-piece buffer.  Dynamic shared memory: 2 x 3 KC TM
+// + 2 x 3 KC TX pieces (32-bit) + KC TX residues (64-bit).
+template <int KIND>
+__global__ void __launch_bounds__(kGemmThreads, Gemm<KIND>::MINB)
+k_simd_fc(const uint64_t *__restrict__ x, uint64_t *__restrict__ y, const uint32_t *__restrict__ a,
+               const uint64_t *__restrict__ a_off, const PieceConsts *__restrict__ pc, LimbSet limbs, uint32_t M,
+               uint32_t Mpad, uint32_t K, uint32_t L1, uint32_t n, const DevPrime *__restrict__ P) {
+    using G = Gemm<KIND>;
+    constexpr int PL = kPlanes, TM = G::TM, TX = G::TX, RM = G::RM, CM = G::CM, KC = G::KC;
+    constexpr int SA = PL * KC * TM, SB = PL * KC * TX;
+    static_assert(TM == 16 * RM && TX == 16 * CM, "16 x 16 threads");
+    extern __shared__ __align__(16) uint8_t smem[];
+    uint32_t *const sa_base = reinterpret_cast<uint32_t *>(smem);               // [2][PL][KC][TM]
+    uint32_t *const sb_base = sa_base + 2 * SA;                                 // [2][PL][KC][TX]
+    uint64_t *const sraw = reinterpret_cast<uint64_t *>(sb_base + 2 * SB);      // [KC][TX]
+    pdl_enter();
+    const uint32_t t = limbs.t[blockIdx.y];
+    const uint32_t m0 = blockIdx.z * TM;
+    const uint32_t col0 = blockIdx.x * TX;
+    const uint32_t poly = col0 / n, j0 = col0 % n;
+    const uint32_t tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const uint64_t xrow = 2ull * L1 * n;
+    const uint64_t *xb = x + ((uint64_t)poly * L1 + t) * n + j0;
+    const uint32_t *ab = a + a_off[t] + m0;
+
+    // round k0: scalar pieces into scalar buffer b, raw residues into the staging buffer
+    auto issue = [&](uint32_t k0, int b) {
+        uint32_t *sa = sa_base + b * SA;
+#pragma unroll 1
+        for (int i = threadIdx.x; i < PL * KC * TM / 4; i += kGemmThreads) {
+            const int p = i / (KC * TM / 4), rem = i % (KC * TM / 4);
+            const int r = rem / (TM / 4), c4 = rem % (TM / 4);
+            const bool ok = k0 + r < K;
+            cp_async16(sa + (p * KC + r) * TM + c4 * 4, ok ? ab + ((uint64_t)p * K + k0 + r) * Mpad + c4 * 4 : ab,
+                       ok ? 16u : 0u);
+        }
+#pragma unroll 1
+        for (int i = threadIdx.x; i < KC * TX / 2; i += kGemmThreads) {
+            const int r = i / (TX / 2), c2 = i % (TX / 2);
+            const bool ok = k0 + r < K;
+            cp_async16(sraw + r * TX + 2 * c2, ok ? xb + (uint64_t)(k0 + r) * xrow + 2 * c2 : xb, ok ? 16u : 0u);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    // the staged residues cut into residue-piece buffer b (each thread its own residues)
+    auto cut = [&](int b) {
+        uint32_t *sb = sb_base + b * SB;
+#pragma unroll 1
+        for (int i = threadIdx.x; i < KC * TX; i += kGemmThreads) {
+            uint32_t pcs[PL];
+            split_pieces<KIND>(sraw[i], pcs);
+#pragma unroll
+            for (int p = 0; p < PL; p++) sb[p * KC * TX + i] = pcs[p];
+        }
+    };
+
+    uint64_t acc[RM][CM][KIND == 0 ? PL : 1];
+    uint32_t acw[RM][CM][KIND == 1 ? 3 * PL : 1];
+#pragma unroll
+    for (int r = 0; r < RM; r++)
+#pragma unroll
+        for (int c = 0; c < CM; c++) {
+#pragma unroll
+            for (int p = 0; p < (KIND == 0 ? PL : 1); p++) acc[r][c][p] = 0;
+#pragma unroll
+            for (int p = 0; p < (KIND == 1 ? 3 * PL : 1); p++) acw[r][c][p] = 0;
+        }
+
+    issue(0, 0);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    cut(0);
+    int b = 0;
+    for (uint32_t k0 = 0; k0 < K; k0 += KC, b ^= 1) {
+        __syncthreads();                                  // buffers b are complete, sraw is free
+        const bool more = k0 + KC < K;
+        if (more) issue(k0 + KC, b ^ 1);
+        const uint32_t *sa = sa_base + b * SA;
+        const uint32_t *sb = sb_base + b * SB;
+#pragma unroll
+        for (int kk = 0; kk < KC; kk++) {
+            uint32_t av[PL][RM], bv[PL][CM];
+#pragma unroll
+            for (int p = 0; p < PL; p++) {
+                load_vec<CM>(&sb[(p * KC + kk) * TX + tx * CM], bv[p]);
+                load_vec<RM>(&sa[(p * KC + kk) * TM + ty * RM], av[p]);
+            }
+#pragma unroll
+            for (int r = 0; r < RM; r++)
+#pragma unroll
+                for (int c = 0; c < CM; c++)
+#pragma unroll
+                    for (int p = 0; p < PL; p++) {
+                        if constexpr (KIND == 0)
+                            acc[r][c][p] += (uint64_t)av[p][r] * bv[p][c];
+                        else
+                            mac96(av[p][r], bv[p][c], acw[r][c][3 * p], acw[r][c][3 * p + 1], acw[r][c][3 * p + 2]);
+                    }
+        }
+        if (more) {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");   // round k0 + KC has landed
+            __syncthreads();                                       // ... for every thread's copies
+            cut(b ^ 1);
+        }
+    }
+    store_outputs<KIND>(acc, acw, y, P, pc, t, m0, M, poly, L1, n, j0, tx, ty);
+}
+// dynamic shared memory of k_simd_fc (112 KB for KIND 0, 56 KB for KIND 1)
+template <int KIND> constexpr size_t gemm_smem() {
+    return 2ull * kPlanes * Gemm<KIND>::KC * (Gemm<KIND>::TM + Gemm<KIND>::TX) * 4 +
+           8ull * Gemm<KIND>::KC * Gemm<KIND>::TX;
 }
 
 // Throughput of the integer multiply-add forms on this GPU: every thread runs 8 independent
@@ -322,8 +363,8 @@ void launch_gemm(const hear_context *c, const hear_simd_model::Layer &L, const s
     LimbSet s{};
     s.n = (uint32_t)limbs.size();
     for (uint32_t i = 0; i < s.n; i++) s.t[i] = limbs[i];
-    launch(k_simd_fc<KIND>, dim3(2 * c->n / Gemm<KIND>::TX, s.n, L.Mpad / Gemm<KIND>::TM), kGemmThreads, 0, st, x,
-           y, static_cast<const uint32_t *>(L.a.p), static_cast<const uint64_t *>(L.a_off.p),
+    launch(k_simd_fc<KIND>, dim3(2 * c->n / Gemm<KIND>::TX, s.n, L.Mpad / Gemm<KIND>::TM), kGemmThreads,
+           gemm_smem<KIND>(), st, x, y, static_cast<const uint32_t *>(L.a.p), static_cast<const uint64_t *>(L.a_off.p),
            static_cast<const PieceConsts *>(L.consts.p), s, L.M, L.Mpad, L.K, L1, c->n, c->dev_primes());
 }
 
@@ -383,6 +424,13 @@ int64_t round_scalar(double w, uint64_t q) {
     }
     HEAR_REQUIRE((r >> 62) == 0, HEAR_E_INVAL, "weight too large for the scale");
     return w < 0 ? -(int64_t)r : (int64_t)r;
+}
+
+void simd_setup() {
+    HEAR_CHECK_CUDA(cudaFuncSetAttribute(k_simd_fc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)gemm_smem<0>()));
+    HEAR_CHECK_CUDA(cudaFuncSetAttribute(k_simd_fc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)gemm_smem<1>()));
 }
 
 hear_simd_model *simd_model_create(hear_context *c, const hear_layer_desc *layers, size_t n_layers,

@@ -40,6 +40,9 @@ double imad_peak(hear_context *c, int kind, uint32_t iters);
 // exact round(w * q) with ties away from zero (|w q| < 2^62)
 int64_t round_scalar(double w, uint64_t q);
 
+// dynamic shared memory of the matrix-product kernels on the current device; called once
+// per context at creation
+void simd_setup();
 hear_simd_model *simd_model_create(hear_context *c, const hear_layer_desc *layers, size_t n_layers,
                                    uint32_t level);
 // evaluate the network on x [d_in][2][level_in+1][N]; returns [d_out][2][level_out+1][N]
