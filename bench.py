@@ -1064,23 +1064,25 @@ def headline(result, sections_path):
     for k in ("value", "ms_per_step", "p50_ms", "p99_ms"):
         h[k] = _r(h.get(k), 6)
     cfg = result["config"]
+    ff = cfg["fc_form"]
     h["config"] = {"workload": cfg.get("workload_short", cfg["workload"]), "parallelism": cfg["parallelism"],
-                   "l2": "no flush: per-step working set > 129 MB L2",
-                   "ntt_table": cfg.get("ntt_table"), "ks_table": cfg.get("ks_table"),
-                   "fc_form": {k: cfg["fc_form"].get(k) for k in ("fc_n1", "hoist_moddown", "hoist_sums")},
+                   "l2": "no flush: working set > L2",
+                   "fc_form": "n1=%s%s%s" % (ff.get("fc_n1"), " hoist_moddown" if ff.get("hoist_moddown") else "",
+                                             " hoist_sums" if ff.get("hoist_sums") else ""),
                    "sections": sections_path}
     e = result["e2e"]
     h["e2e"] = {"value": _r(e["value"], 6), "unit": e["unit"], "h2d_bytes_per_step": e["h2d_bytes_per_step"],
                 "d2h_bytes_per_step": e["d2h_bytes_per_step"]}
     rf = result["roofline"]
     h["roofline"] = {k: (_r(rf.get(k)) if isinstance(rf.get(k), float) else rf.get(k))
-                     for k in ("bound", "kernel", "achieved", "peak", "unit", "frac", "traffic",
-                               "hbm_achieved_gbs", "hbm_peak_gbs", "hbm_frac", "derived_alu_frac") if k in rf}
-    h["roofline"]["peak_kind"] = "measured (hear_dbg_bfly_peak)" if rf.get("peak") else None
+                     for k in ("bound", "achieved", "peak", "unit", "frac", "traffic", "hbm_peak_gbs", "hbm_frac",
+                               "derived_alu_frac") if k in rf}
+    h["roofline"]["kernel"] = "ntt_fwd"
+    h["roofline"]["peak_kind"] = "measured bfly probe" if rf.get("peak") else None
     if result.get("roofline_keyswitch"):
         kr = result["roofline_keyswitch"]
         h["roofline_keyswitch"] = {k: (_r(kr[k]) if isinstance(kr[k], float) else kr[k])
-                                   for k in ("bound", "achieved", "peak", "unit", "frac", "peak_kind")}
+                                   for k in ("bound", "achieved", "peak", "unit", "frac")}
     if "cpu_baseline" in result:
         cb = result["cpu_baseline"]
         h["cpu_baseline"] = {"value": _r(cb["value"]), "unit": cb["unit"], "cores": cb["cores"], "kind": cb["kind"],
@@ -1090,7 +1092,7 @@ def headline(result, sections_path):
     s = {}
     if "batched" in result:
         b = result["batched"]
-        s["batched_large_256clips"] = {"value": _r(b["value"]), "vs_plain": _r(b["vs_plain"], 3)}
+        s["batched_large"] = {"value": _r(b["value"]), "vs_plain": _r(b["vs_plain"], 3)}
     if "batched_small" in result:
         best = max(result["batched_small"]["rows"], key=lambda r: r["value"])
         s["batched_small"] = {"clips": best["clips"], "value": _r(best["value"]), "vs_plain": _r(best["vs_plain"], 3)}
@@ -1099,9 +1101,7 @@ def headline(result, sections_path):
             rows = result[key]["sweep"]
             top = max(rows, key=lambda r: r["inferences_s"])
             s[key] = {"rate_req_s": top["rate_req_s"], "value": _r(top["inferences_s"]),
-                      "vs_plain": _r(top["inferences_s"] / result["value"], 3),
-                      "p50_ms": _r(top.get("p50_ms")), "p99_ms": _r(top.get("p99_ms")),
-                      "refused": top.get("refused_busy")}
+                      "vs_plain": _r(top["inferences_s"] / result["value"], 3), "p99_ms": _r(top.get("p99_ms"))}
     for key in ("served_mix", "served_c5_mix"):
         if key in result:
             rows = result[key]["sweep"]
