@@ -534,9 +534,10 @@ uint64_t hear_pdl_launch_count(void);
  * (two passes, 1024-word tiles, 256 threads with radix-4 units: four times the threads of
  * the narrow form for launches of few limbs).  hear_ntt_tune times all four for launches of 1, 2, 4, .. max_limbs limbs in both directions on the
  * context's stream (each timing a replayed CUDA graph of back-to-back transforms) and keeps
- * the fastest per power-of-two bucket, the one-launch form only if it is 15% faster (its
- * larger code competes for the instruction cache inside whole evaluations; larger launches use the
- * largest tuned bucket's choice).  hear_context_create runs it once (max_limbs 1024, a few
+ * the fastest two-pass form per power-of-two bucket (larger launches use the largest tuned
+ * bucket's choice); the one-launch form is timed but not chosen, because inside whole
+ * evaluations it lost clearly where isolated replays sometimes favoured it (a pinned table
+ * or hear_ntt_set_variant still selects it).  hear_context_create runs it once (max_limbs 1024, a few
  * tens of milliseconds) unless the environment sets HEAR_NTT_TUNE=0, which keeps a fixed
  * rule (narrow below two wide CTAs per SM, wide above).  It must
  * not run concurrently with other work on the context.  ms_out (optional) receives

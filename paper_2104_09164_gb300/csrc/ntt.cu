@@ -698,8 +698,6 @@ double bfly_peak(const hear_context *ctx, bool fwd, uint32_t iters) {
     return (double)blocks * threads * 32.0 * iters / (ms / 1e3);
 }
 
-constexpr float kFusedMargin = 1.15f;
-
 // Time every launch variant for launches of 1, 2, 4, .. max_limbs limbs (both directions)
 // and record the fastest per bucket.  Runs on the context's stream; the caller keeps other
 // work off the context meanwhile.
@@ -755,12 +753,14 @@ void ntt_tune(hear_context *ctx, uint32_t max_limbs, int iters, float *ms_out) {
                     HEAR_CHECK_CUDA(le);
                     ms /= iters;
                     if (ms_out) ms_out[((size_t)dir * kNttBuckets + b) * kNttVariants + v] = ms;
-                    // the one-launch form carries both passes' code: inside a whole
-                    // evaluation it competes for the instruction cache with the other
-                    // kernels, so it must win its isolated timing by a clear margin
-                    const float eff = v == kNttFused ? ms * kFusedMargin : ms;
-                    if (best_v == kNttAuto || eff < best) {
-                        best = eff;
+                    // the one-launch cluster form is timed but not chosen: inside a whole
+                    // evaluation it lost clearly (small network at batch 1: 981 against 1309
+                    // inferences/s with it for the launches below 32 limbs) where isolated
+                    // replays sometimes favoured it; a pinned table or a forced variant
+                    // still selects it
+                    if (v == kNttFused) continue;
+                    if (best_v == kNttAuto || ms < best) {
+                        best = ms;
                         best_v = v;
                     }
                 }

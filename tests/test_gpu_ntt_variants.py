@@ -46,7 +46,7 @@ def test_variants_compute_the_same_transform(H, log_n, qb, pb):
                 assert np.array_equal(H.hear_dbg_ntt_roundtrip(ctx, limbs), limbs), (n_limbs, v)
         H.hear_ntt_set_variant(ctx, -1)
         choice, ms = H.hear_ntt_tune(ctx, 64, 2)
-        assert set(np.unique(choice)) <= {0, 1, 2, 3}
+        assert set(np.unique(choice)) <= {0, 1, 3}          # the one-launch form is timed, not chosen
         assert np.all(ms[:, :7, :] > 0)
     finally:
         H.hear_context_destroy(ctx)
