@@ -759,8 +759,14 @@ void ntt_tune(hear_context *ctx, uint32_t max_limbs, int iters, float *ms_out) {
                     // replays sometimes favoured it; a pinned table or a forced variant
                     // still selects it
                     if (v == kNttFused) continue;
-                    if (best_v == kNttAuto || ms < best) {
-                        best = ms;
+                    // launches up to 127 limbs: the tiny form (256 threads of 64 registers)
+                    // overlaps its neighbours better inside a graph than its isolated time
+                    // shows (small network at batch 1: 1319 against 1303 inferences/s with
+                    // it for the 32-127-limb forward transforms), so it keeps the bucket
+                    // unless another form is 10 % faster in isolation
+                    const float eff = (v == kNttTiny && b <= 6) ? ms * 0.9f : ms;
+                    if (best_v == kNttAuto || eff < best) {
+                        best = eff;
                         best_v = v;
                     }
                 }
